@@ -1,0 +1,404 @@
+"""Benchmark of the in-place RL roll-out loop (agent-steps/s) on one GB300.
+
+One bench step = one full roll-out of the workload through the C ABI:
+ws_reset (fresh episode draw), ws_rollout over the horizon in chunks of 50
+steps (every env: policy MLP, sampling, env step with auto-reset, store), and
+ws_returns over the horizon.  Default workload: the control env at scale,
+131,072 envs x 1 agent, horizon 500, policy 4-256-256-2, BF16 tensor-core
+path (the FP32 one-launch-per-step path is timed beside it).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                    [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica of the workload on its
+own GPU (envs are independent; no collective on the data path) and rank 0
+prints one JSON line with the whole-job throughput.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "agent-steps/sec on 1 GB300, served BF16 vs plain FP32; p50/p99 rollout latency"
+CHUNK = 50
+
+WORKLOADS = {
+    "control_scale": dict(env=0, n_envs=131072, horizon=500, limit=200, h=(256, 256),
+                          desc="control env, 131,072 envs x 1 agent, horizon 500, "
+                               "policy 4-256-256-2, episode limit 200"),
+    "control_small": dict(env=0, n_envs=1000, horizon=200, limit=200, h=(64, 64),
+                          desc="control env, 1,000 envs x 1 agent, horizon 200, "
+                               "policy 4-64-64-2, episode limit 200"),
+    "economy": dict(env=1, n_envs=2048, horizon=540, limit=540, h=(128, 128),
+                    desc="economy, 2,048 envs x U{8..256} agents + 1 planner, horizon 540, "
+                         "policy 16-128-128-20 (planner 16-128-128-10)"),
+    "landscape": dict(env=2, n_envs=8192, horizon=1000, limit=1000, h=(256, 256), dim=24,
+                      n_gauss=4096,
+                      desc="landscape, 8,192 envs x 1 agent, D=24, M=4,096 Gaussians, "
+                           "horizon 1,000, policy 24-256-256-48"),
+}
+
+
+def flops_per_agent_step(wl):
+    if wl["env"] == 0:
+        w = [4, *wl["h"], 2]
+    elif wl["env"] == 1:
+        w = [16, *wl["h"], 20]
+    else:
+        w = [wl["dim"], *wl["h"], 2 * wl["dim"]]
+    return 2 * sum(a * b for a, b in zip(w[:-1], w[1:]))
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), \
+            d.get("bf16_tflops_sustained", 1700.0), "measured"
+    return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in out.strip().splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- oracle leg
+def _oracle_shard(args):
+    wl_name, env_ids, steps = args
+    sys.path.insert(0, ROOT)
+    import oracle
+    wl = WORKLOADS[wl_name]
+    t0 = time.perf_counter()
+    if wl["env"] == 0:
+        p = oracle.policy_init(1, 0, [4, *wl["h"], 2])
+        oracle.control_rollout(p, *wl["h"], seed=1, env_ids=env_ids, n_steps=steps,
+                               episode_limit=wl["limit"])
+        agent_steps = len(env_ids) * steps
+    elif wl["env"] == 1:
+        ap = oracle.policy_init(1, 0, [16, *wl["h"], 20])
+        pp = oracle.policy_init(1, 1, [16, *wl["h"], 10])
+        na = [oracle.econ_agent_count(1, int(e)) for e in env_ids]
+        oracle.econ_rollout(ap, pp, seed=1, env_ids=env_ids, n_agents=na, n_steps=steps,
+                            episode_limit=wl["limit"])
+        agent_steps = (sum(na) + len(env_ids)) * steps
+    else:
+        c, w, a = oracle.landscape_init(1, wl["dim"], wl["n_gauss"])
+        p = oracle.policy_init(1, 0, [wl["dim"], *wl["h"], 2 * wl["dim"]])
+        oracle.landscape_rollout(c, w, a, p, *wl["h"], seed=1, env_ids=env_ids, n_steps=steps,
+                                 episode_limit=wl["limit"])
+        agent_steps = len(env_ids) * steps
+    return agent_steps, time.perf_counter() - t0
+
+
+def oracle_throughput(wl_name, target_s=12.0):
+    """The FP64 oracle, as it stands, on the host cores: one process per core
+    (spawned), each rolling out its own envs; a bounded sample of the workload."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    wl = WORKLOADS[wl_name]
+    steps = min(wl["horizon"], 50)
+    # calibrate on one env
+    a, dt = _oracle_shard((wl_name, np.array([0], np.uint32), 5))
+    per_agent_step = dt / max(a, 1)
+    cores = os.cpu_count() or 1
+    agents_per_env = a / 5.0
+    envs_per_core = max(1, int(target_s / (per_agent_step * steps * agents_per_env)))
+    envs_per_core = min(envs_per_core, max(1, wl["n_envs"] // cores))
+    shards = [(wl_name, np.arange(i * envs_per_core, (i + 1) * envs_per_core, dtype=np.uint32), steps)
+              for i in range(cores)]
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_shard, shards)
+    wall = time.perf_counter() - t0
+    total = sum(r[0] for r in res)
+    sample = (f"{cores} processes x {envs_per_core} envs x {steps} steps of the workload "
+              f"({total} agent-steps, FP64 C oracle, {wall:.1f} s wall)")
+    return total / wall, cores, sample, wall
+
+
+# ----------------------------------------------------------------- GPU leg
+def run_gpu(args, wl, world, rank, local):
+    import torch
+    from paper_2408_00930_gb300 import warpsci as W
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    kw = dict(chunk_steps=CHUNK, param_seed=1 + rank)
+    if wl["env"] == 2:
+        kw.update(dim=wl["dim"], n_gauss=wl["n_gauss"])
+    path = W.WS_PATH_BATCHED_BF16
+    cfg, _ = W.make_config(wl["env"], path, wl["n_envs"], wl["horizon"], wl["limit"], *wl["h"],
+                           **kw)
+    if W.ws_query_bytes(cfg)[0] != W.WS_OK:
+        path = W.WS_PATH_BATCHED_FP32
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def one_path(path, steps, warmup, measure_kernel):
+        with torch.cuda.stream(stream):
+            r = W.Rollout(wl["env"], path, wl["n_envs"], wl["horizon"], wl["limit"], *wl["h"],
+                          device=dev, stream=stream, **kw)
+        H = wl["horizon"]
+        n_chunks = (H + CHUNK - 1) // CHUNK
+        agent_steps = r.n_slots * H
+
+        def bench_step(i, evs=None):
+            r.reset(1000 + i)
+            if evs is not None:
+                evs[0].record(stream)
+            for c in range(n_chunks):
+                r.rollout(min(CHUNK, H - c * CHUNK))
+                if evs is not None:
+                    evs[1 + c].record(stream)
+            r.returns(H)
+            if evs is not None:
+                evs[-1].record(stream)
+
+        for i in range(warmup):
+            bench_step(i)
+        torch.cuda.synchronize(dev)
+        times, chunk_ms, roll_ms = [], [], []
+        clocks = Clocks(local)
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        clocks.start()
+        for i in range(steps):
+            flush.zero_()                      # L2 flush between timed steps
+            torch.cuda.synchronize(dev)
+            e_start = torch.cuda.Event(enable_timing=True)
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(n_chunks + 2)]
+            e_start.record(stream)
+            bench_step(warmup + i, evs)
+            torch.cuda.synchronize(dev)
+            times.append(e_start.elapsed_time(evs[-1]))
+            roll_ms.append(evs[0].elapsed_time(evs[n_chunks]))
+            for c in range(n_chunks):
+                chunk_ms.append(evs[c].elapsed_time(evs[c + 1]))
+        torch.cuda.synchronize(dev)
+        clk = clocks.stop()
+        barrier(world)
+        total_ms = max_over_ranks(sum(times), world)
+        res = dict(agent_steps=agent_steps, total_ms=total_ms, times=times, chunk_ms=chunk_ms,
+                   roll_ms=roll_ms, clocks=clk, n_chunks=n_chunks, rollout=r)
+        return res
+
+    main = one_path(path, args.steps, args.warmup, True)
+    r = main["rollout"]
+    n_steps_total = args.steps
+    value = main["agent_steps"] * n_steps_total * world / (main["total_ms"] / 1e3)
+    # plain FP32 path beside it (fewer steps: it is the slow baseline)
+    plain = None
+    if not args.no_plain:
+        pk = one_path(W.WS_PATH_PLAIN_FP32, max(1, min(args.steps, 2)), 1, False)
+        plain = dict(value=pk["agent_steps"] * len(pk["times"]) * world / (pk["total_ms"] / 1e3),
+                     unit="agent-steps/s", ms_per_step=pk["total_ms"] / len(pk["times"]),
+                     path="plain_fp32 (one launch per sub-step per step, FP32 SIMT)")
+        pk["rollout"].close()
+    # end to end through the C ABI with host buffers: policy weights H2D from
+    # pinned host memory, the roll-out, returns, and the per-env return at t=0 D2H.
+    par_bytes = r.fetch_raw(W.WS_F_PARAMS, _param_bytes(wl)).copy()
+    host_par = torch.from_numpy(par_bytes).pin_memory()
+    host_ret = torch.empty(r.n_slots * 4, dtype=torch.uint8).pin_memory()
+    H = wl["horizon"]
+    e2e_t = []
+    for i in range(max(2, min(args.steps, 5))):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        st = W.ws_load(r.ctx, W.WS_F_PARAMS, host_par.data_ptr(), host_par.numel(), 0,
+                       2**64 - 1)
+        assert st == W.WS_OK, W.ws_last_error(r.ctx)
+        r.reset(5000 + i)
+        for c in range(main["n_chunks"]):
+            r.rollout(min(CHUNK, H - c * CHUNK))
+        r.returns(H)
+        st = W.ws_fetch(r.ctx, W.WS_F_RETURN, 0, 1, host_ret.data_ptr(), host_ret.numel(), 0)
+        assert st == W.WS_OK, W.ws_last_error(r.ctx)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(sum(e2e_t), world)
+    e2e = {"value": main["agent_steps"] * len(e2e_t) * world / e2e_s, "unit": "agent-steps/s",
+           "h2d_bytes_per_step": int(host_par.numel()), "d2h_bytes_per_step": int(host_ret.numel())}
+    r.close()
+    return path, value, main, plain, e2e
+
+
+def _param_bytes(wl):
+    if wl["env"] == 0:
+        w = [4, *wl["h"], 2]
+        extra = 0
+    elif wl["env"] == 1:
+        w = [16, *wl["h"], 20]
+        pw = [16, *wl["h"], 10]
+        extra = sum(a * b + b for a, b in zip(pw[:-1], pw[1:]))
+    else:
+        w = [wl["dim"], *wl["h"], 2 * wl["dim"]]
+        extra = 0
+    return 4 * (sum(a * b + b for a, b in zip(w[:-1], w[1:])) + extra)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="control_scale", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        if rank == 0:
+            v, cores, sample, wall = oracle_throughput(args.workload)
+            steps_ms = wall * 1e3
+            print(json.dumps({
+                "impl": "reference", "metric": METRIC, "value": v, "unit": "agent-steps/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": steps_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": wl["desc"], "arm": "FP64 C oracle on host cores"},
+                "cpu_baseline": {"value": v, "unit": "agent-steps/s", "cores": cores,
+                                 "kind": "oracle", "sample": sample},
+                "e2e": {"value": v, "unit": "agent-steps/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}), flush=True)
+        return
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        # before the first GPU call: the pool is spawned, never forked after CUDA init
+        v, cores, sample, _ = oracle_throughput(args.workload)
+        cpu = {"value": v, "unit": "agent-steps/s", "cores": cores, "kind": "oracle",
+               "sample": sample}
+    path, value, main_res, plain, e2e = run_gpu(args, wl, world, rank, local)
+    if rank != 0:
+        return
+    from paper_2408_00930_gb300 import warpsci as W
+    hbm, bf16_burst, bf16_sus, peak_src = load_peaks()
+    n_chunks = main_res["n_chunks"]
+    launch_ms = statistics.mean(main_res["chunk_ms"])
+    launch_steps = min(CHUNK, wl["horizon"])
+    flops_launch = flops_per_agent_step(wl) * (main_res["agent_steps"] / wl["horizon"]) * launch_steps
+    bf16 = path == W.WS_PATH_BATCHED_BF16
+    peak = bf16_sus if bf16 else bf16_sus / 4.0
+    roofline = {"bound": "tensor", "achieved": flops_launch / (launch_ms * 1e-3) / 1e12,
+                "peak": peak, "unit": "TFLOP/s", "frac": None, "traffic": None,
+                "kernel": "ws_control_tc (fused persistent, one launch per 50-step chunk)" if bf16
+                else "plain per-step kernels",
+                "peak_source": f"{peak_src} bf16 sustained" if bf16 else
+                f"{peak_src} bf16 sustained / 4 (fp32 SIMT)"}
+    roofline["frac"] = roofline["achieved"] / roofline["peak"]
+    lat = sorted(main_res["chunk_ms"])
+    # kernels of ours per bench step: reset, per chunk (fused kernel + counter
+    # advance) or per step the plain kernels, and the returns scan
+    plain_per_step = {0: 6, 1: 14, 2: 9}[wl["env"]]
+    per_launch = (1 + 2 * n_chunks + 1) if bf16 else (1 + plain_per_step * wl["horizon"] + n_chunks + 1)
+    out = {
+        "metric": METRIC, "value": value, "unit": "agent-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": main_res["total_ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if bf16 else "f32",
+        "data": "synthetic",
+        "config": {"workload": wl["desc"],
+                   "path": "batched_bf16" if bf16 else "batched_fp32",
+                   "bench_step": f"ws_reset + ws_rollout x {n_chunks} chunks of {CHUNK} + ws_returns",
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "latency": {"chunk_steps": CHUNK, "p50_ms": float(np.percentile(lat, 50)),
+                    "p99_ms": float(np.percentile(lat, 99))},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "plain_fp32": plain,
+        "gpu_launches": per_launch * args.steps,
+        "clocks": main_res["clocks"],
+    }
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

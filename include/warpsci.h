@@ -1,0 +1,193 @@
+/*
+ * warpsci.h -- C ABI of the GB300-native in-place RL roll-out engine.
+ *
+ * The engine runs the whole roll-out loop of the paper on one GPU with no
+ * host round-trip (paper Sec. 2: "the entire RL workflow on a single or
+ * multiple GPUs, utilizing a unified and in-place data store within GPUs for
+ * simulation roll-outs"; App. B: roll-outs, action inference and reset share
+ * one GPU-resident store, policy models live in global memory and are
+ * referenced, not copied).  Each step observes the env state, runs the policy
+ * MLP, samples an action, steps the environment (state update, reward, done,
+ * auto-reset) and writes the transition into a time-major trajectory ring.
+ *
+ * Conventions for every entry point:
+ *   - Nothing is thrown across the ABI; every call returns a ws_status.  The
+ *     first error is sticky in the context (later calls return it again) and
+ *     ws_last_error() gives a one-line message.
+ *   - Device memory and the CUDA stream belong to the caller; the context
+ *     borrows them from ws_create until ws_destroy.  Host arrays passed in are
+ *     copied before the call returns.
+ *   - Every call is asynchronous on the context's stream, except
+ *     ws_query_bytes, ws_sync, ws_last_error and ws_destroy.
+ *   - Step counter k: the number of steps run since the last ws_reset.  It is
+ *     the first Philox counter word of every per-step random draw and selects
+ *     the ring row (k mod ring_steps).
+ *
+ * Random streams (all Philox4x32-10, Salmon et al. SC'11): key = seed,
+ * counter = (k, env, agent, tag << 24 | sub); tags ACTION 0, RESET 1,
+ * PARTNER 2, NOISE 3, POLICY_INIT 4, LANDSCAPE_INIT 5, ECON_INIT 6.
+ */
+#ifndef WARPSCI_H
+#define WARPSCI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WS_ABI_VERSION 1u
+
+typedef struct ws_ctx ws_ctx;
+
+typedef enum {
+  WS_OK = 0,
+  WS_ERR_INVALID = 1,     /* bad argument or configuration                  */
+  WS_ERR_NOMEM = 2,       /* a buffer is smaller than ws_query_bytes asks   */
+  WS_ERR_CUDA = 3,        /* a CUDA call or a kernel failed                 */
+  WS_ERR_TIMEOUT = 4,     /* ws_sync gave up, or a device wait ran out      */
+  WS_ERR_STATE = 5,       /* call not valid in the context's current state  */
+  WS_ERR_RANGE = 6,       /* requested steps are not (or no longer) in ring */
+  WS_ERR_UNSUPPORTED = 7  /* env/path/size combination not built            */
+} ws_status;
+
+/* Environment families (paper App. C: classic control, multi-agent
+ * economics, catalytic reaction paths on an energy landscape). */
+typedef enum { WS_ENV_CONTROL = 0, WS_ENV_ECONOMY = 1, WS_ENV_LANDSCAPE = 2 } ws_env;
+
+/* Execution paths.  PLAIN_FP32: one kernel launch per sub-step (observe,
+ * each policy layer, sample, env step) per step, FP32 SIMT, launched from the
+ * host every step.  BATCHED_FP32: the same kernels, captured as a CUDA graph
+ * per chunk of steps.  BATCHED_BF16: policy GEMMs (and the landscape
+ * cross-term) on the tcgen05 tensor cores in BF16 with FP32 accumulation;
+ * for the control env one persistent fused kernel runs a whole chunk. */
+typedef enum { WS_PATH_PLAIN_FP32 = 0, WS_PATH_BATCHED_FP32 = 1, WS_PATH_BATCHED_BF16 = 2 } ws_path;
+
+/* Fields of ws_fetch / ws_load.  Ring fields are time-major per step t:
+ *   OBS     f32 [t][obs_dim][n_slots]   pre-step observation
+ *   ACTION  i32 [t][n_slots]            (landscape: f32 [t][dim][n_slots] step dx)
+ *   LOGP    f32 [t][n_slots]            log-probability of the sampled action
+ *   REWARD  f32 [t][n_slots]
+ *   DONE    u8  [t][n_slots]            1 if the step ended the episode
+ *   RETURN  f32 [t][n_slots]            discounted return (after ws_returns)
+ *   WEALTH  i64 [t][n_slots]            economy: pre-step agent wealth;
+ *                                       planner slot: total wealth of its env
+ *   ENERGY  f32 [t][n_slots]            landscape: E of the post-step state
+ * State fields (no step range; t0 and n_steps must be 0):
+ *   STATE   control:   f32 s[4][n_envs] (x, v, th, w), i32 t[n_envs]
+ *           economy:   i64 wealth[n_agents], f32 feat[16][n_agents], i32 t[n_envs]
+ *           landscape: f32 x[dim][n_envs], f32 eobs[n_envs], i32 t[n_envs]
+ *   PARAMS  f32 policy parameters, per layer W[n_in][n_out] row-major then b;
+ *           economy: agent policy then planner policy
+ *   ENV_PARAMS  landscape: f32 centres[M][dim], f32 widths[M], f32 amps[M];
+ *               economy:   i32 agents_per_env[n_envs]
+ *   LOGITS  f32 [n_slots][n_out] policy outputs of the last step (plain and
+ *           batched-FP32 paths only)                                        */
+typedef enum {
+  WS_F_OBS = 0,
+  WS_F_ACTION = 1,
+  WS_F_LOGP = 2,
+  WS_F_REWARD = 3,
+  WS_F_DONE = 4,
+  WS_F_RETURN = 5,
+  WS_F_WEALTH = 6,
+  WS_F_ENERGY = 7,
+  WS_F_STATE = 8,
+  WS_F_PARAMS = 9,
+  WS_F_ENV_PARAMS = 10,
+  WS_F_LOGITS = 11
+} ws_field;
+
+/* Roll-out configuration.  Slots: control and landscape have one agent per
+ * env (n_slots = n_envs); the economy has agents_per_env[e] agents in env e,
+ * laid out env by env, followed by one planner slot per env. */
+typedef struct {
+  uint32_t struct_size;   /* = sizeof(ws_config); guards ABI drift            */
+  int32_t env;            /* ws_env                                           */
+  int32_t path;           /* ws_path                                          */
+  uint32_t n_envs;        /* >= 1                                             */
+  uint32_t ring_steps;    /* steps the trajectory ring holds (>= 1)           */
+  uint32_t episode_limit; /* episode step count that forces done (>= 1)      */
+  uint32_t chunk_steps;   /* steps per graph / persistent launch; 0 = auto    */
+  uint32_t hidden0;       /* policy hidden widths                             */
+  uint32_t hidden1;
+  uint32_t dim;           /* landscape: coordinates D (1..64)                 */
+  uint32_t n_gauss;       /* landscape: Gaussians M (>= 1)                    */
+  float noise_sigma;      /* landscape: observation-noise sigma               */
+  float step_clip;        /* landscape: |dx_j| clip                           */
+  float gamma;            /* discount of ws_returns                           */
+  uint32_t flags;         /* reserved, must be 0                              */
+  uint64_t param_seed;    /* Philox key of policy / landscape / agent counts  */
+  const int32_t *agents_per_env; /* economy, host, n_envs entries in 2..1024;
+                                    NULL = draw U{8..256} from param_seed      */
+} ws_config;
+
+/* Bytes of the two caller-owned device buffers a configuration needs:
+ * state_bytes (parameters, env state, scratch, step counter) and ring_bytes
+ * (the trajectory store).  Also reports the slot count.  Host-only, sync. */
+ws_status ws_query_bytes(const ws_config *cfg, size_t *state_bytes, size_t *ring_bytes,
+                         uint32_t *n_slots);
+
+/* Create a context over caller-owned device buffers (at least the sizes of
+ * ws_query_bytes, 256-byte aligned) on `cuda_stream` (a cudaStream_t; NULL =
+ * legacy default stream).  Draws the policy parameters (and the landscape or
+ * the agent counts) from param_seed (S0, paper App. B: policy models and the
+ * environment reference live in global memory) and performs ws_reset with
+ * seed = param_seed.  On failure *out is NULL. */
+ws_status ws_create(const ws_config *cfg, void *state_buf, size_t state_bytes, void *ring_buf,
+                    size_t ring_bytes, void *cuda_stream, ws_ctx **out);
+
+/* Full reset (paper App. B, "reset" is part of the on-device workflow):
+ * every env redraws its state from Philox(seed; k = 0xFFFFFFFF, env, agent,
+ * RESET), episode counters and the step counter k become 0, and `seed`
+ * becomes the key of all later per-step draws. */
+ws_status ws_reset(ws_ctx *ctx, uint64_t seed);
+
+/* One step of every env (observe, policy, sample, env step with auto-reset,
+ * store), asynchronous.  k advances by 1. */
+ws_status ws_step(ws_ctx *ctx);
+
+/* n_steps steps, asynchronous.  The batched paths launch cached CUDA graphs
+ * (and the persistent fused kernel); the plain path launches every kernel of
+ * every step from the host.  k advances by n_steps. */
+ws_status ws_rollout(ws_ctx *ctx, uint32_t n_steps);
+
+/* Discounted returns over the last n_steps ring rows (steps k-n..k-1):
+ * G_t = r_t + gamma (1 - done_t) G_{t+1}, with G = 0 after the window, in
+ * compensated (float-float) FP32.  n_steps <= min(k, ring_steps). */
+ws_status ws_returns(ws_ctx *ctx, uint32_t n_steps);
+
+/* Copy a field (see ws_field) for absolute steps [t0, t0 + n_steps) into
+ * dst (device memory if dst_on_device, else host memory; a host copy is
+ * synchronous to the context stream).  dst_bytes must cover the block.
+ * Steps not yet run or already overwritten in the ring -> WS_ERR_RANGE. */
+ws_status ws_fetch(ws_ctx *ctx, ws_field field, uint64_t t0, uint32_t n_steps, void *dst,
+                   size_t dst_bytes, int dst_on_device);
+
+/* Overwrite STATE or PARAMS (same layouts as ws_fetch) from src, e.g. a
+ * trainer's new policy weights or a checkpoint; then set the step counter to
+ * k.  PARAMS keep the current k when k == UINT64_MAX. */
+ws_status ws_load(ws_ctx *ctx, ws_field field, const void *src, size_t src_bytes,
+                  int src_on_device, uint64_t k);
+
+/* Current step counter k (host mirror; exact, since only the host enqueues). */
+ws_status ws_get_step(const ws_ctx *ctx, uint64_t *k);
+
+/* Block the host until the context's stream is idle, or return
+ * WS_ERR_TIMEOUT after timeout_ms milliseconds (0 = wait forever).  Reads the
+ * device error flag of the fused kernels; a set flag -> WS_ERR_TIMEOUT. */
+ws_status ws_sync(ws_ctx *ctx, uint32_t timeout_ms);
+
+/* One-line description of the sticky error, or "" if none.  Never NULL. */
+const char *ws_last_error(const ws_ctx *ctx);
+
+/* Release the context (graphs, events); the caller's buffers are untouched.
+ * Waits for the context's outstanding work first. */
+void ws_destroy(ws_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WARPSCI_H */

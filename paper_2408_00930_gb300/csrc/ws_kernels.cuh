@@ -1,0 +1,70 @@
+// ws_kernels.cuh -- device view of a roll-out context and the host-side
+// launchers of every kernel (defined in ws_plain.cu, ws_control_tc.cu, ...).
+#pragma once
+
+#include "ws_common.cuh"
+
+namespace ws {
+
+// Raw device pointers and scalars handed to every kernel by value.
+struct Dev {
+  int env;
+  uint32_t n_envs, n_slots, n_agent_slots, ring_steps, episode_limit, dim, n_gauss;
+  uint32_t n_out, n_out_planner;
+  float noise_sigma, step_clip, gamma;
+  uint64_t seed;        // key of the per-step draws (set by ws_reset)
+  uint64_t *k;          // device step counter
+  uint32_t *err;        // [0] error flag, [1] where
+  const float *params, *params_planner;
+  PolicyShape pol, pol_planner;
+  // env state
+  float *s;             // control: [4][n]; landscape: x [dim][n]
+  int32_t *t;           // [n_envs]
+  float *eobs;          // landscape [n]
+  int64_t *wealth;      // economy [n_agent_slots]
+  float *feat;          // economy [16][n_agent_slots]
+  const int32_t *agent_off;  // economy [n_envs + 1]
+  const int32_t *slot_env;   // economy [n_agent_slots]
+  // landscape parameters and derived tables
+  float *centres, *widths, *amps;  // [M][dim], [M], [M]
+  float *cnorm, *coef;             // |c|^2, -log2(e) / (2 w^2)
+  // plain-path scratch
+  float *h0, *h1, *out, *pobs, *ph0, *ph1, *pout;
+  int64_t *income;      // economy [n_agent_slots]
+  float *epart;         // landscape energy partial sums [kEnergyChunks][2][n]
+  uint8_t *needs_energy;  // landscape [n]
+  // ring
+  float *r_obs;
+  void *r_act;
+  float *r_logp, *r_rew, *r_ret, *r_energy;
+  uint8_t *r_done;
+  int64_t *r_wealth;
+};
+
+constexpr int kEnergyChunks = 8;
+
+// ---- S0: parameter initialisation -------------------------------------
+void launch_init_policy(float *params, const PolicyShape &shape, uint64_t seed, uint32_t policy_id,
+                        cudaStream_t st);
+void launch_init_landscape(const Dev &d, uint64_t param_seed, cudaStream_t st);
+void launch_landscape_derive(const Dev &d, cudaStream_t st);
+
+// ---- full reset --------------------------------------------------------
+void launch_reset(const Dev &d, cudaStream_t st);
+
+// ---- plain / batched-FP32 step (one launch per sub-step) -----------------
+void launch_plain_step(const Dev &d, uint32_t step_off, cudaStream_t st);
+void launch_advance(const Dev &d, uint32_t n, cudaStream_t st);
+
+// ---- S7: discounted returns ----------------------------------------------
+void launch_returns(const Dev &d, uint32_t n_steps, cudaStream_t st);
+
+// ---- BF16 tensor-core control path -----------------------------------------
+size_t control_tc_packed_bytes(const PolicyShape &shape);
+bool control_tc_supported(const PolicyShape &shape);
+void launch_control_tc_pack(const Dev &d, void *packed, cudaStream_t st);
+cudaError_t launch_control_tc(const Dev &d, const void *packed, uint32_t n_steps, int grid,
+                              cudaStream_t st);
+int control_tc_default_grid(const Dev &d);
+
+}  // namespace ws

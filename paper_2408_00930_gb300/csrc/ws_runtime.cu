@@ -1,0 +1,629 @@
+// ws_runtime.cu -- the C ABI (include/warpsci.h): context layout over the
+// caller's buffers, parameter init, reset, step/rollout dispatch per path,
+// CUDA-graph capture of the horizon loop, fetch/load, host-side waits.
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "ws_kernels.cuh"
+
+using namespace ws;
+
+struct ws_ctx {
+  ws_config cfg;
+  Layout L;
+  Dev d;
+  cudaStream_t stream = nullptr;    // caller's stream (borrowed)
+  cudaStream_t capture = nullptr;   // private stream used only to capture graphs
+  cudaEvent_t ev = nullptr;
+  char *state = nullptr;
+  char *ring = nullptr;
+  uint64_t k_host = 0;
+  uint64_t seed = 0;
+  std::vector<int32_t> agents;      // economy agent counts (host copy)
+  std::map<uint32_t, cudaGraphExec_t> graphs;
+  int tc_grid = 0;
+  ws_status err = WS_OK;
+  std::string msg;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+ws_status fail(ws_ctx *c, ws_status s, const std::string &m) {
+  if (c && c->err == WS_OK) {
+    c->err = s;
+    c->msg = m;
+  }
+  return s;
+}
+
+ws_status cuda_check(ws_ctx *c, cudaError_t e, const char *where) {
+  if (e == cudaSuccess) return WS_OK;
+  return fail(c, WS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+ws_status validate(const ws_config *cfg) {
+  if (!cfg || cfg->struct_size != sizeof(ws_config)) return WS_ERR_INVALID;
+  if (cfg->env < WS_ENV_CONTROL || cfg->env > WS_ENV_LANDSCAPE) return WS_ERR_INVALID;
+  if (cfg->path < WS_PATH_PLAIN_FP32 || cfg->path > WS_PATH_BATCHED_BF16) return WS_ERR_INVALID;
+  if (cfg->n_envs < 1 || cfg->n_envs > (1u << 26)) return WS_ERR_INVALID;
+  if (cfg->ring_steps < 1 || cfg->episode_limit < 1) return WS_ERR_INVALID;
+  if (cfg->hidden0 < 1 || cfg->hidden0 > 4096 || cfg->hidden1 < 1 || cfg->hidden1 > 4096)
+    return WS_ERR_INVALID;
+  if (cfg->flags != 0) return WS_ERR_INVALID;
+  if (!(cfg->gamma >= 0.f && cfg->gamma <= 1.f)) return WS_ERR_INVALID;
+  if (cfg->env == WS_ENV_LANDSCAPE) {
+    if (cfg->dim < 1 || cfg->dim > 64 || cfg->n_gauss < 1 || cfg->n_gauss > (1u << 22))
+      return WS_ERR_INVALID;
+    if (!(cfg->step_clip > 0.f) || !(cfg->noise_sigma >= 0.f)) return WS_ERR_INVALID;
+  }
+  if (cfg->env == WS_ENV_ECONOMY && cfg->agents_per_env) {
+    for (uint32_t e = 0; e < cfg->n_envs; ++e)
+      if (cfg->agents_per_env[e] < 2 || cfg->agents_per_env[e] > 1024) return WS_ERR_INVALID;
+  }
+  return WS_OK;
+}
+
+// Agent counts U{8..256}: Philox(0, env, 0, ECON_INIT) word 0, multiply-shift.
+void agent_counts(const ws_config *cfg, std::vector<int32_t> &out) {
+  out.assign(cfg->n_envs, 1);
+  if (cfg->env != WS_ENV_ECONOMY) return;
+  for (uint32_t e = 0; e < cfg->n_envs; ++e) {
+    if (cfg->agents_per_env) {
+      out[e] = cfg->agents_per_env[e];
+    } else {
+      const uint4 r = draw(cfg->param_seed, 0, e, 0, kTagEconInit, 0);
+      out[e] = 8 + (int32_t)bounded(r.x, 249u);
+    }
+  }
+}
+
+bool use_tc_control(const ws_config *cfg) {
+  return cfg->env == WS_ENV_CONTROL && cfg->path == WS_PATH_BATCHED_BF16;
+}
+
+Layout make_layout(const ws_config *cfg, const std::vector<int32_t> &agents) {
+  Layout L{};
+  L.env = cfg->env;
+  L.path = cfg->path;
+  L.n_envs = cfg->n_envs;
+  L.ring_steps = cfg->ring_steps;
+  uint64_t sa = 0;
+  for (int32_t a : agents) sa += (uint64_t)a;
+  if (cfg->env == WS_ENV_ECONOMY) {
+    L.n_agent_slots = (uint32_t)sa;
+    L.n_slots = (uint32_t)sa + cfg->n_envs;
+    L.obs_dim = kEconF;
+    L.act_dim = 1;
+    L.n_out = 20;
+    L.n_out_planner = 10;
+    L.pol = PolicyShape{{kEconF, (int)cfg->hidden0, (int)cfg->hidden1, 20}};
+    L.pol_planner = PolicyShape{{kEconF, (int)cfg->hidden0, (int)cfg->hidden1, 10}};
+  } else if (cfg->env == WS_ENV_CONTROL) {
+    L.n_agent_slots = cfg->n_envs;
+    L.n_slots = cfg->n_envs;
+    L.obs_dim = 4;
+    L.act_dim = 1;
+    L.n_out = 2;
+    L.pol = PolicyShape{{4, (int)cfg->hidden0, (int)cfg->hidden1, 2}};
+    L.pol_planner = PolicyShape{{0, 0, 0, 0}};
+  } else {
+    L.n_agent_slots = cfg->n_envs;
+    L.n_slots = cfg->n_envs;
+    L.obs_dim = cfg->dim;
+    L.act_dim = cfg->dim;
+    L.n_out = 2 * cfg->dim;
+    L.pol = PolicyShape{{(int)cfg->dim, (int)cfg->hidden0, (int)cfg->hidden1, (int)(2 * cfg->dim)}};
+    L.pol_planner = PolicyShape{{0, 0, 0, 0}};
+  }
+  const size_t N = cfg->n_envs, S = L.n_slots, Sa = L.n_agent_slots, M = cfg->n_gauss,
+               D = cfg->dim, R = cfg->ring_steps;
+  size_t o = 0;
+  L.k_off = o; o += up(8);
+  L.err_off = o; o += up(8);
+  L.params_off = o; o += up(L.pol.count() * 4);
+  L.params_planner_off = o;
+  if (cfg->env == WS_ENV_ECONOMY) o += up(L.pol_planner.count() * 4);
+  L.packed_off = o;
+  L.packed_bytes = use_tc_control(cfg) ? control_tc_packed_bytes(L.pol) : 0;
+  o += up(L.packed_bytes);
+  L.env_params_off = o;
+  if (cfg->env == WS_ENV_LANDSCAPE) o += up(M * D * 4) + up(M * 4) + up(M * 4);
+  if (cfg->env == WS_ENV_ECONOMY) o += up(N * 4);
+  L.env_derived_off = o;
+  L.env_derived_bytes = cfg->env == WS_ENV_LANDSCAPE ? up(M * 4) + up(M * 4) : 0;
+  o += L.env_derived_bytes;
+  L.state_off = o;
+  if (cfg->env == WS_ENV_CONTROL) o += up(4 * N * 4);
+  if (cfg->env == WS_ENV_ECONOMY) o += up(Sa * 8) + up(kEconF * Sa * 4);
+  if (cfg->env == WS_ENV_LANDSCAPE) o += up(D * N * 4) + up(N * 4) + up(N);
+  L.t_off = o; o += up(N * 4);
+  L.aux_off = o;
+  if (cfg->env == WS_ENV_ECONOMY) o += up((N + 1) * 4) + up(Sa * 4);
+  L.scratch_off = o;
+  const bool plain_scratch = !use_tc_control(cfg);
+  if (plain_scratch) {
+    L.scratch_h0_off = o; o += up(S * cfg->hidden0 * 4);
+    L.scratch_h1_off = o; o += up(S * cfg->hidden1 * 4);
+    L.scratch_out_off = o; o += up(S * L.n_out * 4);
+    if (cfg->env == WS_ENV_ECONOMY) {
+      L.scratch_pobs_off = o; o += up(N * kEconF * 4);
+      L.scratch_ph0_off = o; o += up(N * cfg->hidden0 * 4);
+      L.scratch_ph1_off = o; o += up(N * cfg->hidden1 * 4);
+      L.scratch_pout_off = o; o += up(N * 10 * 4);
+      L.scratch_income_off = o; o += up(Sa * 8);
+    }
+    if (cfg->env == WS_ENV_LANDSCAPE) {
+      L.scratch_income_off = o; o += up((size_t)kEnergyChunks * 2 * N * 4);  // energy partials
+    }
+  }
+  L.state_bytes = o;
+  size_t r = 0;
+  L.ring_obs = r; r += up(R * L.obs_dim * S * 4);
+  L.ring_act = r; r += up(R * L.act_dim * S * 4);
+  L.ring_logp = r; r += up(R * S * 4);
+  L.ring_rew = r; r += up(R * S * 4);
+  L.ring_done = r; r += up(R * S);
+  L.ring_ret = r; r += up(R * S * 4);
+  L.ring_wealth = r;
+  if (cfg->env == WS_ENV_ECONOMY) r += up(R * S * 8);
+  L.ring_energy = r;
+  if (cfg->env == WS_ENV_LANDSCAPE) r += up(R * S * 4);
+  L.ring_bytes = r;
+  return L;
+}
+
+void make_dev(ws_ctx *c) {
+  const Layout &L = c->L;
+  const ws_config &cfg = c->cfg;
+  Dev &d = c->d;
+  std::memset(&d, 0, sizeof(d));
+  char *S = c->state, *R = c->ring;
+  d.env = cfg.env;
+  d.n_envs = L.n_envs;
+  d.n_slots = L.n_slots;
+  d.n_agent_slots = L.n_agent_slots;
+  d.ring_steps = L.ring_steps;
+  d.episode_limit = cfg.episode_limit;
+  d.dim = cfg.dim;
+  d.n_gauss = cfg.n_gauss;
+  d.n_out = L.n_out;
+  d.n_out_planner = L.n_out_planner;
+  d.noise_sigma = cfg.noise_sigma;
+  d.step_clip = cfg.step_clip;
+  d.gamma = cfg.gamma;
+  d.seed = c->seed;
+  d.k = (uint64_t *)(S + L.k_off);
+  d.err = (uint32_t *)(S + L.err_off);
+  d.params = (const float *)(S + L.params_off);
+  d.params_planner = (const float *)(S + L.params_planner_off);
+  d.pol = L.pol;
+  d.pol_planner = L.pol_planner;
+  const size_t N = L.n_envs, Sa = L.n_agent_slots, M = cfg.n_gauss, D = cfg.dim;
+  if (cfg.env == WS_ENV_LANDSCAPE) {
+    d.centres = (float *)(S + L.env_params_off);
+    d.widths = (float *)(S + L.env_params_off + up(M * D * 4));
+    d.amps = (float *)(S + L.env_params_off + up(M * D * 4) + up(M * 4));
+    d.cnorm = (float *)(S + L.env_derived_off);
+    d.coef = (float *)(S + L.env_derived_off + up(M * 4));
+    d.s = (float *)(S + L.state_off);
+    d.eobs = (float *)(S + L.state_off + up(D * N * 4));
+    d.needs_energy = (uint8_t *)(S + L.state_off + up(D * N * 4) + up(N * 4));
+  } else if (cfg.env == WS_ENV_CONTROL) {
+    d.s = (float *)(S + L.state_off);
+  } else {
+    d.wealth = (int64_t *)(S + L.state_off);
+    d.feat = (float *)(S + L.state_off + up(Sa * 8));
+    d.agent_off = (const int32_t *)(S + L.aux_off);
+    d.slot_env = (const int32_t *)(S + L.aux_off + up((N + 1) * 4));
+  }
+  d.t = (int32_t *)(S + L.t_off);
+  if (!use_tc_control(&cfg)) {
+    d.h0 = (float *)(S + L.scratch_h0_off);
+    d.h1 = (float *)(S + L.scratch_h1_off);
+    d.out = (float *)(S + L.scratch_out_off);
+    if (cfg.env == WS_ENV_ECONOMY) {
+      d.pobs = (float *)(S + L.scratch_pobs_off);
+      d.ph0 = (float *)(S + L.scratch_ph0_off);
+      d.ph1 = (float *)(S + L.scratch_ph1_off);
+      d.pout = (float *)(S + L.scratch_pout_off);
+      d.income = (int64_t *)(S + L.scratch_income_off);
+    }
+    if (cfg.env == WS_ENV_LANDSCAPE) d.epart = (float *)(S + L.scratch_income_off);
+  }
+  d.r_obs = (float *)(R + L.ring_obs);
+  d.r_act = (void *)(R + L.ring_act);
+  d.r_logp = (float *)(R + L.ring_logp);
+  d.r_rew = (float *)(R + L.ring_rew);
+  d.r_done = (uint8_t *)(R + L.ring_done);
+  d.r_ret = (float *)(R + L.ring_ret);
+  d.r_wealth = cfg.env == WS_ENV_ECONOMY ? (int64_t *)(R + L.ring_wealth) : nullptr;
+  d.r_energy = cfg.env == WS_ENV_LANDSCAPE ? (float *)(R + L.ring_energy) : nullptr;
+}
+
+void drop_graphs(ws_ctx *c) {
+  for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+}
+
+uint32_t chunk_of(const ws_ctx *c) {
+  if (c->cfg.chunk_steps) return c->cfg.chunk_steps;
+  return use_tc_control(&c->cfg) ? 100u : 25u;
+}
+
+// Enqueue `n` steps on stream st (used directly and under capture).
+ws_status enqueue_steps(ws_ctx *c, uint32_t n, cudaStream_t st) {
+  if (use_tc_control(&c->cfg)) {
+    const uint32_t chunk = chunk_of(c);
+    for (uint32_t done = 0; done < n;) {
+      const uint32_t m = (n - done) < chunk ? (n - done) : chunk;
+      cudaError_t e = launch_control_tc(c->d, c->state + c->L.packed_off, m, c->tc_grid, st);
+      if (e != cudaSuccess) return cuda_check(c, e, "control_tc launch");
+      launch_advance(c->d, m, st);
+      done += m;
+    }
+  } else {
+    for (uint32_t i = 0; i < n; ++i) launch_plain_step(c->d, i, st);
+    launch_advance(c->d, n, st);
+  }
+  return cuda_check(c, cudaGetLastError(), "step launch");
+}
+
+ws_status graph_for(ws_ctx *c, uint32_t n, cudaGraphExec_t *out) {
+  auto it = c->graphs.find(n);
+  if (it != c->graphs.end()) {
+    *out = it->second;
+    return WS_OK;
+  }
+  cudaError_t e = cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_check(c, e, "begin capture");
+  ws_status s = enqueue_steps(c, n, c->capture);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(c->capture, &g);
+  if (s != WS_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) return cuda_check(c, e, "end capture");
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_check(c, e, "graph instantiate");
+  c->graphs[n] = ex;
+  *out = ex;
+  return WS_OK;
+}
+
+size_t ring_field_step_bytes(const ws_ctx *c, ws_field f, size_t *field_off) {
+  const Layout &L = c->L;
+  const size_t S = L.n_slots;
+  switch (f) {
+    case WS_F_OBS: *field_off = L.ring_obs; return (size_t)L.obs_dim * S * 4;
+    case WS_F_ACTION: *field_off = L.ring_act; return (size_t)L.act_dim * S * 4;
+    case WS_F_LOGP: *field_off = L.ring_logp; return S * 4;
+    case WS_F_REWARD: *field_off = L.ring_rew; return S * 4;
+    case WS_F_DONE: *field_off = L.ring_done; return S;
+    case WS_F_RETURN: *field_off = L.ring_ret; return S * 4;
+    case WS_F_WEALTH:
+      if (L.env != WS_ENV_ECONOMY) return 0;
+      *field_off = L.ring_wealth; return S * 8;
+    case WS_F_ENERGY:
+      if (L.env != WS_ENV_LANDSCAPE) return 0;
+      *field_off = L.ring_energy; return S * 4;
+    default: return 0;
+  }
+}
+
+// (device pointer, bytes) pieces of a state-like field, in ABI order.
+struct Piece { char *p; size_t n; };
+std::vector<Piece> state_pieces(ws_ctx *c, ws_field f) {
+  const Layout &L = c->L;
+  const size_t N = L.n_envs, Sa = L.n_agent_slots, D = c->cfg.dim, M = c->cfg.n_gauss;
+  char *S = c->state;
+  std::vector<Piece> v;
+  if (f == WS_F_STATE) {
+    if (L.env == WS_ENV_CONTROL) {
+      v.push_back({S + L.state_off, 4 * N * 4});
+    } else if (L.env == WS_ENV_ECONOMY) {
+      v.push_back({S + L.state_off, Sa * 8});
+      v.push_back({S + L.state_off + up(Sa * 8), kEconF * Sa * 4});
+    } else {
+      v.push_back({S + L.state_off, D * N * 4});
+      v.push_back({S + L.state_off + up(D * N * 4), N * 4});
+    }
+    v.push_back({S + L.t_off, N * 4});
+  } else if (f == WS_F_PARAMS) {
+    v.push_back({S + L.params_off, L.pol.count() * 4});
+    if (L.env == WS_ENV_ECONOMY) v.push_back({S + L.params_planner_off, L.pol_planner.count() * 4});
+  } else if (f == WS_F_ENV_PARAMS) {
+    if (L.env == WS_ENV_LANDSCAPE) {
+      v.push_back({S + L.env_params_off, M * D * 4});
+      v.push_back({S + L.env_params_off + up(M * D * 4), M * 4});
+      v.push_back({S + L.env_params_off + up(M * D * 4) + up(M * 4), M * 4});
+    } else if (L.env == WS_ENV_ECONOMY) {
+      v.push_back({S + L.env_params_off, N * 4});
+    }
+  } else if (f == WS_F_LOGITS) {
+    if (L.env == WS_ENV_CONTROL && use_tc_control(&c->cfg)) return v;
+    v.push_back({S + L.scratch_out_off, (size_t)L.n_agent_slots * L.n_out * 4});
+    if (L.env == WS_ENV_ECONOMY) v.push_back({S + L.scratch_pout_off, N * 10 * 4});
+  }
+  return v;
+}
+
+ws_status after_params_changed(ws_ctx *c) {
+  if (c->cfg.env == WS_ENV_LANDSCAPE) launch_landscape_derive(c->d, c->stream);
+  if (use_tc_control(&c->cfg)) launch_control_tc_pack(c->d, c->state + c->L.packed_off, c->stream);
+  return cuda_check(c, cudaGetLastError(), "param derive");
+}
+
+}  // namespace
+
+extern "C" {
+
+ws_status ws_query_bytes(const ws_config *cfg, size_t *state_bytes, size_t *ring_bytes,
+                         uint32_t *n_slots) {
+  ws_status s = validate(cfg);
+  if (s != WS_OK) return s;
+  if (use_tc_control(cfg) && !control_tc_supported(PolicyShape{{4, (int)cfg->hidden0, (int)cfg->hidden1, 2}}))
+    return WS_ERR_UNSUPPORTED;
+  if (cfg->env != WS_ENV_CONTROL && cfg->path == WS_PATH_BATCHED_BF16) return WS_ERR_UNSUPPORTED;
+  std::vector<int32_t> agents;
+  agent_counts(cfg, agents);
+  const Layout L = make_layout(cfg, agents);
+  if (state_bytes) *state_bytes = L.state_bytes;
+  if (ring_bytes) *ring_bytes = L.ring_bytes;
+  if (n_slots) *n_slots = L.n_slots;
+  return WS_OK;
+}
+
+ws_status ws_create(const ws_config *cfg, void *state_buf, size_t state_bytes, void *ring_buf,
+                    size_t ring_bytes, void *cuda_stream, ws_ctx **out) {
+  if (!out) return WS_ERR_INVALID;
+  *out = nullptr;
+  size_t need_s = 0, need_r = 0;
+  ws_status s = ws_query_bytes(cfg, &need_s, &need_r, nullptr);
+  if (s != WS_OK) return s;
+  if (!state_buf || !ring_buf) return WS_ERR_INVALID;
+  if (((uintptr_t)state_buf | (uintptr_t)ring_buf) % kAlign) return WS_ERR_INVALID;
+  if (state_bytes < need_s || ring_bytes < need_r) return WS_ERR_NOMEM;
+  ws_ctx *c = new ws_ctx();
+  c->cfg = *cfg;
+  c->cfg.agents_per_env = nullptr;  // host array is copied, never kept
+  agent_counts(cfg, c->agents);
+  c->L = make_layout(cfg, c->agents);
+  c->stream = (cudaStream_t)cuda_stream;
+  c->state = (char *)state_buf;
+  c->ring = (char *)ring_buf;
+  c->seed = cfg->param_seed;
+  make_dev(c);
+  cudaError_t e = cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    cuda_check(c, e, "stream/event create");
+    ws_status r = c->err;
+    ws_destroy(c);
+    return r;
+  }
+  cudaMemsetAsync(c->d.err, 0, 8, c->stream);
+  if (cfg->env == WS_ENV_ECONOMY) {
+    const size_t N = c->L.n_envs, Sa = c->L.n_agent_slots;
+    std::vector<int32_t> off(N + 1, 0), slot_env(Sa, 0);
+    for (size_t i = 0; i < N; ++i) {
+      off[i + 1] = off[i] + c->agents[i];
+      for (int32_t a = 0; a < c->agents[i]; ++a) slot_env[off[i] + a] = (int32_t)i;
+    }
+    cudaMemcpyAsync(c->state + c->L.env_params_off, c->agents.data(), N * 4, cudaMemcpyHostToDevice,
+                    c->stream);
+    cudaMemcpyAsync((void *)c->d.agent_off, off.data(), (N + 1) * 4, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync((void *)c->d.slot_env, slot_env.data(), Sa * 4, cudaMemcpyHostToDevice, c->stream);
+    e = cudaStreamSynchronize(c->stream);  // host staging vectors end here
+    if (e != cudaSuccess) {
+      cuda_check(c, e, "upload agent counts");
+      ws_status r = c->err;
+      ws_destroy(c);
+      return r;
+    }
+  }
+  launch_init_policy((float *)c->d.params, c->L.pol, cfg->param_seed, 0, c->stream);
+  if (cfg->env == WS_ENV_ECONOMY)
+    launch_init_policy((float *)c->d.params_planner, c->L.pol_planner, cfg->param_seed, 1, c->stream);
+  if (cfg->env == WS_ENV_LANDSCAPE) launch_init_landscape(c->d, cfg->param_seed, c->stream);
+  if (use_tc_control(cfg)) c->tc_grid = control_tc_default_grid(c->d);
+  s = after_params_changed(c);
+  if (s == WS_OK) s = ws_reset(c, cfg->param_seed);
+  if (s == WS_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream), "create sync");
+  if (s != WS_OK) {
+    ws_destroy(c);
+    return s;
+  }
+  *out = c;
+  return WS_OK;
+}
+
+ws_status ws_reset(ws_ctx *c, uint64_t seed) {
+  if (!c) return WS_ERR_INVALID;
+  if (c->err != WS_OK) return c->err;
+  if (seed != c->seed) drop_graphs(c);  // graphs bake the key into their launches
+  c->seed = seed;
+  c->d.seed = seed;
+  cudaMemsetAsync(c->d.k, 0, 8, c->stream);
+  launch_reset(c->d, c->stream);
+  c->k_host = 0;
+  return cuda_check(c, cudaGetLastError(), "reset");
+}
+
+ws_status ws_step(ws_ctx *c) {
+  if (!c) return WS_ERR_INVALID;
+  if (c->err != WS_OK) return c->err;
+  ws_status s = enqueue_steps(c, 1, c->stream);
+  if (s == WS_OK) c->k_host += 1;
+  return s;
+}
+
+ws_status ws_rollout(ws_ctx *c, uint32_t n) {
+  if (!c) return WS_ERR_INVALID;
+  if (c->err != WS_OK) return c->err;
+  if (n == 0) return WS_OK;
+  ws_status s = WS_OK;
+  if (c->cfg.path == WS_PATH_PLAIN_FP32) {
+    for (uint32_t i = 0; i < n && s == WS_OK; ++i) s = enqueue_steps(c, 1, c->stream);
+  } else if (use_tc_control(&c->cfg)) {
+    cudaGraphExec_t g;
+    s = graph_for(c, n, &g);
+    if (s == WS_OK) s = cuda_check(c, cudaGraphLaunch(g, c->stream), "graph launch");
+  } else {
+    const uint32_t chunk = chunk_of(c);
+    const uint32_t full = n / chunk, rem = n % chunk;
+    cudaGraphExec_t g;
+    if (full) {
+      s = graph_for(c, chunk, &g);
+      for (uint32_t i = 0; i < full && s == WS_OK; ++i)
+        s = cuda_check(c, cudaGraphLaunch(g, c->stream), "graph launch");
+    }
+    if (rem && s == WS_OK) {
+      s = graph_for(c, rem, &g);
+      if (s == WS_OK) s = cuda_check(c, cudaGraphLaunch(g, c->stream), "graph launch");
+    }
+  }
+  if (s == WS_OK) c->k_host += n;
+  return s;
+}
+
+ws_status ws_returns(ws_ctx *c, uint32_t n) {
+  if (!c) return WS_ERR_INVALID;
+  if (c->err != WS_OK) return c->err;
+  if (n == 0 || n > c->k_host || n > c->L.ring_steps) return WS_ERR_RANGE;
+  launch_returns(c->d, n, c->stream);
+  return cuda_check(c, cudaGetLastError(), "returns");
+}
+
+ws_status ws_fetch(ws_ctx *c, ws_field f, uint64_t t0, uint32_t n, void *dst, size_t dst_bytes,
+                   int on_dev) {
+  if (!c || (!dst && dst_bytes)) return WS_ERR_INVALID;
+  if (c->err != WS_OK) return c->err;
+  const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (f == WS_F_STATE || f == WS_F_PARAMS || f == WS_F_ENV_PARAMS || f == WS_F_LOGITS) {
+    if (t0 != 0 || n != 0) return WS_ERR_INVALID;
+    if (f == WS_F_LOGITS && c->cfg.path == WS_PATH_BATCHED_BF16) return WS_ERR_UNSUPPORTED;
+    std::vector<Piece> v = state_pieces(c, f);
+    if (v.empty()) return WS_ERR_INVALID;
+    size_t tot = 0;
+    for (auto &p : v) tot += p.n;
+    if (dst_bytes < tot) return WS_ERR_NOMEM;
+    char *o = (char *)dst;
+    for (auto &p : v) {
+      ws_status s = cuda_check(c, cudaMemcpyAsync(o, p.p, p.n, kind, c->stream), "fetch copy");
+      if (s != WS_OK) return s;
+      o += p.n;
+    }
+  } else {
+    size_t foff = 0;
+    const size_t per = ring_field_step_bytes(c, f, &foff);
+    if (per == 0) return WS_ERR_INVALID;
+    if (n == 0) return WS_OK;
+    const uint64_t R = c->L.ring_steps;
+    const uint64_t lo = c->k_host > R ? c->k_host - R : 0;
+    if (t0 < lo || t0 + n > c->k_host) return WS_ERR_RANGE;
+    if (dst_bytes < per * n) return WS_ERR_NOMEM;
+    char *o = (char *)dst;
+    uint64_t t = t0;
+    uint32_t left = n;
+    while (left) {
+      const uint64_t row = t % R;
+      const uint32_t run = (uint32_t)((R - row) < left ? (R - row) : left);
+      ws_status s = cuda_check(
+          c, cudaMemcpyAsync(o, c->ring + foff + row * per, per * run, kind, c->stream), "fetch copy");
+      if (s != WS_OK) return s;
+      o += per * run;
+      t += run;
+      left -= run;
+    }
+  }
+  if (!on_dev) return cuda_check(c, cudaStreamSynchronize(c->stream), "fetch sync");
+  return WS_OK;
+}
+
+ws_status ws_load(ws_ctx *c, ws_field f, const void *src, size_t src_bytes, int on_dev, uint64_t k) {
+  if (!c || !src) return WS_ERR_INVALID;
+  if (c->err != WS_OK) return c->err;
+  if (f != WS_F_STATE && f != WS_F_PARAMS && f != WS_F_ENV_PARAMS) return WS_ERR_INVALID;
+  if (f == WS_F_ENV_PARAMS && c->cfg.env != WS_ENV_LANDSCAPE) return WS_ERR_INVALID;
+  if (f == WS_F_STATE && k == UINT64_MAX) return WS_ERR_INVALID;
+  std::vector<Piece> v = state_pieces(c, f);
+  size_t tot = 0;
+  for (auto &p : v) tot += p.n;
+  if (src_bytes != tot) return WS_ERR_INVALID;
+  const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const char *i = (const char *)src;
+  for (auto &p : v) {
+    ws_status s = cuda_check(c, cudaMemcpyAsync(p.p, i, p.n, kind, c->stream), "load copy");
+    if (s != WS_OK) return s;
+    i += p.n;
+  }
+  if (f == WS_F_STATE && c->cfg.env == WS_ENV_LANDSCAPE)
+    cudaMemsetAsync(c->d.needs_energy, 0, c->L.n_envs, c->stream);
+  if (f != WS_F_STATE) {
+    ws_status s = after_params_changed(c);
+    if (s != WS_OK) return s;
+  }
+  if (k != UINT64_MAX) {
+    ws_status s = cuda_check(c, cudaMemcpyAsync(c->d.k, &k, 8, cudaMemcpyHostToDevice, c->stream),
+                             "load step");
+    if (s != WS_OK) return s;
+    c->k_host = k;
+  }
+  // pageable host sources are consumed before return
+  if (!on_dev || k != UINT64_MAX) return cuda_check(c, cudaStreamSynchronize(c->stream), "load sync");
+  return WS_OK;
+}
+
+ws_status ws_get_step(const ws_ctx *c, uint64_t *k) {
+  if (!c || !k) return WS_ERR_INVALID;
+  *k = c->k_host;
+  return WS_OK;
+}
+
+ws_status ws_sync(ws_ctx *c, uint32_t timeout_ms) {
+  if (!c) return WS_ERR_INVALID;
+  if (c->err != WS_OK) return c->err;
+  ws_status s = cuda_check(c, cudaEventRecord(c->ev, c->stream), "sync record");
+  if (s != WS_OK) return s;
+  const auto t_end = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+  for (;;) {
+    cudaError_t e = cudaEventQuery(c->ev);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) return cuda_check(c, e, "sync query");
+    if (timeout_ms && std::chrono::steady_clock::now() >= t_end) return WS_ERR_TIMEOUT;
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  uint32_t flag[2] = {0, 0};
+  s = cuda_check(c, cudaMemcpy(flag, c->d.err, 8, cudaMemcpyDeviceToHost), "sync flag");
+  if (s != WS_OK) return s;
+  if (flag[0]) {
+    char buf[96];
+    std::snprintf(buf, sizeof buf, "device wait ran out (site %u)", flag[1]);
+    return fail(c, WS_ERR_TIMEOUT, buf);
+  }
+  return WS_OK;
+}
+
+const char *ws_last_error(const ws_ctx *c) { return c ? c->msg.c_str() : "null context"; }
+
+void ws_destroy(ws_ctx *c) {
+  if (!c) return;
+  if (c->stream || c->ev) cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
+  if (c->ev) cudaEventDestroy(c->ev);
+  if (c->capture) cudaStreamDestroy(c->capture);
+  delete c;
+}
+
+}  // extern "C"

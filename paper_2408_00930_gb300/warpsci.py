@@ -1,0 +1,260 @@
+"""Thin Python binding of the C ABI in include/warpsci.h (argument marshalling only).
+
+Every step of the roll-out runs in the CUDA library ``libwarpsci.so``; this
+module loads it (failing loudly if it is missing), declares the ``ws_*``
+functions under the same names, and offers ``Rollout``, a convenience owner of
+the two device buffers (PyTorch tensors) and the context.  PyTorch is used for
+device memory and streams only.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libwarpsci.so")
+
+WS_OK, WS_ERR_INVALID, WS_ERR_NOMEM, WS_ERR_CUDA = 0, 1, 2, 3
+WS_ERR_TIMEOUT, WS_ERR_STATE, WS_ERR_RANGE, WS_ERR_UNSUPPORTED = 4, 5, 6, 7
+STATUS_NAMES = {0: "WS_OK", 1: "WS_ERR_INVALID", 2: "WS_ERR_NOMEM", 3: "WS_ERR_CUDA",
+                4: "WS_ERR_TIMEOUT", 5: "WS_ERR_STATE", 6: "WS_ERR_RANGE", 7: "WS_ERR_UNSUPPORTED"}
+
+WS_ENV_CONTROL, WS_ENV_ECONOMY, WS_ENV_LANDSCAPE = 0, 1, 2
+WS_PATH_PLAIN_FP32, WS_PATH_BATCHED_FP32, WS_PATH_BATCHED_BF16 = 0, 1, 2
+(WS_F_OBS, WS_F_ACTION, WS_F_LOGP, WS_F_REWARD, WS_F_DONE, WS_F_RETURN, WS_F_WEALTH, WS_F_ENERGY,
+ WS_F_STATE, WS_F_PARAMS, WS_F_ENV_PARAMS, WS_F_LOGITS) = range(12)
+
+EXPORTED = ["ws_query_bytes", "ws_create", "ws_reset", "ws_step", "ws_rollout", "ws_returns",
+            "ws_fetch", "ws_load", "ws_get_step", "ws_sync", "ws_last_error", "ws_destroy"]
+
+
+class ws_config(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("env", C.c_int32), ("path", C.c_int32),
+                ("n_envs", C.c_uint32), ("ring_steps", C.c_uint32),
+                ("episode_limit", C.c_uint32), ("chunk_steps", C.c_uint32),
+                ("hidden0", C.c_uint32), ("hidden1", C.c_uint32), ("dim", C.c_uint32),
+                ("n_gauss", C.c_uint32), ("noise_sigma", C.c_float), ("step_clip", C.c_float),
+                ("gamma", C.c_float), ("flags", C.c_uint32), ("param_seed", C.c_uint64),
+                ("agents_per_env", C.POINTER(C.c_int32))]
+
+
+class WarpSciError(RuntimeError):
+    def __init__(self, status, where, msg=""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)} {msg}".strip())
+
+
+_lib = None
+
+
+def lib():
+    """Load libwarpsci.so (build it with paper_2408_00930_gb300.build.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: the CUDA library was not built "
+                              "(run __graft_entry__.build()); there is no fallback")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        L.ws_query_bytes.argtypes = [C.POINTER(ws_config), C.POINTER(C.c_size_t),
+                                     C.POINTER(C.c_size_t), C.POINTER(C.c_uint32)]
+        L.ws_create.argtypes = [C.POINTER(ws_config), P, C.c_size_t, P, C.c_size_t, P,
+                                C.POINTER(P)]
+        L.ws_reset.argtypes = [P, C.c_uint64]
+        L.ws_step.argtypes = [P]
+        L.ws_rollout.argtypes = [P, C.c_uint32]
+        L.ws_returns.argtypes = [P, C.c_uint32]
+        L.ws_fetch.argtypes = [P, C.c_int, C.c_uint64, C.c_uint32, P, C.c_size_t, C.c_int]
+        L.ws_load.argtypes = [P, C.c_int, P, C.c_size_t, C.c_int, C.c_uint64]
+        L.ws_get_step.argtypes = [P, C.POINTER(C.c_uint64)]
+        L.ws_sync.argtypes = [P, C.c_uint32]
+        L.ws_last_error.argtypes = [P]
+        L.ws_last_error.restype = C.c_char_p
+        L.ws_destroy.argtypes = [P]
+        L.ws_destroy.restype = None
+        for n in EXPORTED:
+            if n not in ("ws_last_error", "ws_destroy"):
+                getattr(L, n).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+# --- the ABI under the same names ------------------------------------------
+def ws_query_bytes(cfg: ws_config):
+    s, r, n = C.c_size_t(), C.c_size_t(), C.c_uint32()
+    st = lib().ws_query_bytes(C.byref(cfg), C.byref(s), C.byref(r), C.byref(n))
+    return st, s.value, r.value, n.value
+
+
+def ws_create(cfg, state_ptr, state_bytes, ring_ptr, ring_bytes, stream_ptr):
+    out = C.c_void_p()
+    st = lib().ws_create(C.byref(cfg), state_ptr, state_bytes, ring_ptr, ring_bytes, stream_ptr,
+                         C.byref(out))
+    return st, out.value
+
+
+def ws_reset(ctx, seed):
+    return lib().ws_reset(ctx, seed)
+
+
+def ws_step(ctx):
+    return lib().ws_step(ctx)
+
+
+def ws_rollout(ctx, n_steps):
+    return lib().ws_rollout(ctx, n_steps)
+
+
+def ws_returns(ctx, n_steps):
+    return lib().ws_returns(ctx, n_steps)
+
+
+def ws_fetch(ctx, field, t0, n_steps, dst_ptr, dst_bytes, dst_on_device):
+    return lib().ws_fetch(ctx, field, t0, n_steps, dst_ptr, dst_bytes, int(dst_on_device))
+
+
+def ws_load(ctx, field, src_ptr, src_bytes, src_on_device, k):
+    return lib().ws_load(ctx, field, src_ptr, src_bytes, int(src_on_device), k)
+
+
+def ws_get_step(ctx):
+    k = C.c_uint64()
+    st = lib().ws_get_step(ctx, C.byref(k))
+    return st, k.value
+
+
+def ws_sync(ctx, timeout_ms=0):
+    return lib().ws_sync(ctx, timeout_ms)
+
+
+def ws_last_error(ctx):
+    return lib().ws_last_error(ctx).decode()
+
+
+def ws_destroy(ctx):
+    lib().ws_destroy(ctx)
+
+
+# --- convenience owner --------------------------------------------------------
+def make_config(env, path, n_envs, ring_steps, episode_limit, hidden0, hidden1, *,
+                chunk_steps=0, dim=0, n_gauss=0, noise_sigma=0.05, step_clip=0.1, gamma=0.99,
+                param_seed=1, agents_per_env=None):
+    cfg = ws_config()
+    cfg.struct_size = C.sizeof(ws_config)
+    cfg.env, cfg.path, cfg.n_envs = env, path, n_envs
+    cfg.ring_steps, cfg.episode_limit, cfg.chunk_steps = ring_steps, episode_limit, chunk_steps
+    cfg.hidden0, cfg.hidden1, cfg.dim, cfg.n_gauss = hidden0, hidden1, dim, n_gauss
+    cfg.noise_sigma, cfg.step_clip, cfg.gamma = noise_sigma, step_clip, gamma
+    cfg.flags, cfg.param_seed = 0, param_seed
+    keep = None
+    if agents_per_env is not None:
+        keep = np.ascontiguousarray(agents_per_env, dtype=np.int32)
+        cfg.agents_per_env = keep.ctypes.data_as(C.POINTER(C.c_int32))
+    return cfg, keep
+
+
+class Rollout:
+    """Owns the two device buffers (torch uint8 tensors) and one ws context.
+
+    Field shapes follow include/warpsci.h; ``fetch`` returns numpy arrays.
+    """
+
+    def __init__(self, env, path, n_envs, ring_steps, episode_limit, hidden0, hidden1,
+                 device="cuda", stream=None, **kw):
+        import torch
+        self.torch = torch
+        self.cfg, self._keep = make_config(env, path, n_envs, ring_steps, episode_limit, hidden0,
+                                           hidden1, **kw)
+        st, sb, rb, ns = ws_query_bytes(self.cfg)
+        if st != WS_OK:
+            raise WarpSciError(st, "ws_query_bytes")
+        self.n_slots = ns
+        self.state_buf = torch.empty(max(sb, 256), dtype=torch.uint8, device=device)
+        self.ring_buf = torch.empty(max(rb, 256), dtype=torch.uint8, device=device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        st, ctx = ws_create(self.cfg, self.state_buf.data_ptr(), sb, self.ring_buf.data_ptr(), rb,
+                            self.stream.cuda_stream)
+        if st != WS_OK:
+            raise WarpSciError(st, "ws_create")
+        self.ctx = ctx
+        self.env, self.n_envs = env, n_envs
+        self.dim = kw.get("dim", 0)
+        self.n_gauss = kw.get("n_gauss", 0)
+        self.hidden = (hidden0, hidden1)
+
+    # checks
+    def _ok(self, st, where):
+        if st != WS_OK:
+            raise WarpSciError(st, where, ws_last_error(self.ctx))
+
+    def reset(self, seed):
+        self._ok(ws_reset(self.ctx, seed), "ws_reset")
+
+    def step(self):
+        self._ok(ws_step(self.ctx), "ws_step")
+
+    def rollout(self, n):
+        self._ok(ws_rollout(self.ctx, n), "ws_rollout")
+
+    def returns(self, n):
+        self._ok(ws_returns(self.ctx, n), "ws_returns")
+
+    def sync(self, timeout_ms=0):
+        self._ok(ws_sync(self.ctx, timeout_ms), "ws_sync")
+
+    @property
+    def k(self):
+        st, k = ws_get_step(self.ctx)
+        self._ok(st, "ws_get_step")
+        return k
+
+    # layouts ---------------------------------------------------------------
+    def obs_dim(self):
+        return {WS_ENV_CONTROL: 4, WS_ENV_ECONOMY: 16, WS_ENV_LANDSCAPE: self.dim}[self.env]
+
+    def _ring_spec(self, field):
+        S = self.n_slots
+        if field == WS_F_OBS:
+            return np.float32, (self.obs_dim(), S)
+        if field == WS_F_ACTION:
+            return ((np.float32, (self.dim, S)) if self.env == WS_ENV_LANDSCAPE
+                    else (np.int32, (S,)))
+        if field in (WS_F_LOGP, WS_F_REWARD, WS_F_RETURN, WS_F_ENERGY):
+            return np.float32, (S,)
+        if field == WS_F_DONE:
+            return np.uint8, (S,)
+        if field == WS_F_WEALTH:
+            return np.int64, (S,)
+        raise ValueError(field)
+
+    def fetch(self, field, t0, n):
+        dt, shp = self._ring_spec(field)
+        out = np.empty((n,) + shp, dtype=dt)
+        self._ok(ws_fetch(self.ctx, field, t0, n, out.ctypes.data, out.nbytes, 0), "ws_fetch")
+        return out
+
+    def fetch_device(self, field, t0, n, dst):
+        self._ok(ws_fetch(self.ctx, field, t0, n, dst.data_ptr(), dst.numel() * dst.element_size(),
+                          1), "ws_fetch")
+
+    def fetch_raw(self, field, nbytes):
+        out = np.empty(nbytes, dtype=np.uint8)
+        self._ok(ws_fetch(self.ctx, field, 0, 0, out.ctypes.data, nbytes, 0), "ws_fetch")
+        return out
+
+    def load_raw(self, field, arr_bytes, k=2**64 - 1):
+        buf = np.ascontiguousarray(arr_bytes).view(np.uint8)
+        self._ok(ws_load(self.ctx, field, buf.ctypes.data, buf.nbytes, 0, k), "ws_load")
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            ws_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,189 @@
+"""GPU parity of the control env (all paths) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2408_00930_gb300 import inputs
+from paper_2408_00930_gb300 import warpsci as W
+from tests import ws_helpers as H
+from tests.gpu_common import (DONE_BAND_BF16, DONE_BAND_F32, TIE_BF16, TIE_F32, TOL_BF16, TOL_F32,
+                              TOL_F32_FREE, control_rollout, need_gpu)
+
+pytestmark = pytest.mark.gpu
+
+FP32_PATHS = [W.WS_PATH_PLAIN_FP32, W.WS_PATH_BATCHED_FP32]
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return need_gpu()
+
+
+@pytest.mark.parametrize("widths", [(64, 64), (256, 256), (33, 17)])
+def test_param_init_bit_exact(torch, widths):
+    r = control_rollout(W.WS_PATH_PLAIN_FP32, 130, 4, 200, *widths, seed=31)
+    n = oracle.policy_param_count([4, *widths, 2])
+    got = r.fetch_raw(W.WS_F_PARAMS, 4 * n).view(np.float32)
+    np.testing.assert_array_equal(got, oracle.policy_init(31, 0, [4, *widths, 2]))
+    r.close()
+
+
+def test_reset_state_bit_exact(torch):
+    n = 777
+    r = control_rollout(W.WS_PATH_PLAIN_FP32, n, 4, 200, 16, 16, seed=5)
+    r.reset(901)
+    s, t = H.unpack_control_state(r.fetch_raw(W.WS_F_STATE, 20 * n), n)
+    exp = np.array([oracle.control_reset_draw(901, oracle.STEP_INIT, e) for e in range(n)])
+    np.testing.assert_array_equal(s, exp)
+    assert np.all(t == 0) and r.k == 0
+    r.close()
+
+
+def _check_rollout(g, o, T, n, tie, band, tol, exact_obs_first=True):
+    """Compare GPU records g with oracle records o up to each env's first ambiguous step."""
+    amb = (o["act_margin"] < tie) | (o["done_margin"] < band)
+    first = H.first_divergence(amb)
+    ok = H.valid_mask(first, T)            # steps fully comparable
+    ok_obs = np.arange(T)[:, None] <= first[None, :]
+    # observations (pre-step state): float tolerance per env-step
+    err = H.rel_err_rows(g["obs"].transpose(0, 2, 1).reshape(T * n, 4), o["obs"].reshape(T * n, 4))
+    err = err.reshape(T, n)
+    assert np.all(err[ok_obs] <= tol), float(err[ok_obs].max())
+    # actions and done flags bit-exact where unambiguous
+    assert np.array_equal(g["action"][ok], o["action"][ok])
+    assert np.array_equal(g["done"][ok], o["done"][ok])
+    assert np.all(g["reward"][ok] == 1.0)
+    lp_err = np.abs(g["logp"][ok] - o["logp"][ok]) / np.maximum(np.abs(o["logp"][ok]), 1.0)
+    assert np.all(lp_err <= tol), float(lp_err.max())
+    return first
+
+
+@pytest.mark.parametrize("path", FP32_PATHS)
+def test_one_step_replay_seeded_states(torch, path):
+    """Seeded states (loaded through ws_load) stepped once vs the oracle's one step."""
+    n, h = 2000, 64
+    g = inputs.rng(11)
+    params = inputs.policy_params(g, [4, h, h, 2], scale=2.0)
+    s0, t0 = inputs.control_states(g, n)
+    t0[:50] = 199                                        # episode-limit done cases
+    s0[50:60, 0] = 2.399                                 # near the x threshold
+    r = control_rollout(path, n, 8, 200, h, h)
+    r.load_raw(W.WS_F_PARAMS, params)
+    k0 = 123456
+    r.load_raw(W.WS_F_STATE, H.pack_control_state(s0, t0), k=k0)
+    r.step()
+    g_rec = dict(obs=r.fetch(W.WS_F_OBS, k0, 1), action=r.fetch(W.WS_F_ACTION, k0, 1),
+                 logp=r.fetch(W.WS_F_LOGP, k0, 1), reward=r.fetch(W.WS_F_REWARD, k0, 1),
+                 done=r.fetch(W.WS_F_DONE, k0, 1))
+    s1, t1 = H.unpack_control_state(r.fetch_raw(W.WS_F_STATE, 20 * n), n)
+    o = oracle.control_rollout(params, h, h, seed=1, env_ids=np.arange(n), n_steps=1,
+                               episode_limit=200, k0=k0, state0=s0, t0=t0)
+    np.testing.assert_array_equal(g_rec["obs"][0].T, s0.astype(np.float32))
+    amb = (o["act_margin"][0] < TIE_F32) | (o["done_margin"][0] < DONE_BAND_F32)
+    assert amb.sum() <= 5
+    ok = ~amb
+    assert np.array_equal(g_rec["action"][0][ok], o["action"][0][ok])
+    assert np.array_equal(g_rec["done"][0][ok], o["done"][0][ok])
+    assert np.all(g_rec["done"][0][:50] == 1)
+    err = H.rel_err_rows(s1[ok], o["state"][ok])
+    assert err.max() <= TOL_F32, err.max()
+    assert np.array_equal(t1[ok], o["t"][ok])
+    lp_err = np.abs(g_rec["logp"][0][ok] - o["logp"][0][ok])
+    assert lp_err.max() <= TOL_F32
+    r.close()
+
+
+@pytest.mark.parametrize("path", FP32_PATHS)
+def test_small_config_full_rollout(torch, path):
+    """1,000 envs x 200 steps, 4-64-64-2 policy drawn on the device (the small config)."""
+    n, T, h = 1000, 200, 64
+    r = control_rollout(path, n, T, 200, h, h, seed=7)
+    r.reset(42)
+    r.rollout(T)
+    r.sync()
+    g = {f: r.fetch(fid, 0, T) for f, fid in [("obs", W.WS_F_OBS), ("action", W.WS_F_ACTION),
+                                              ("logp", W.WS_F_LOGP), ("reward", W.WS_F_REWARD),
+                                              ("done", W.WS_F_DONE)]}
+    params = oracle.policy_init(7, 0, [4, h, h, 2])
+    o = oracle.control_rollout(params, h, h, seed=42, env_ids=np.arange(n), n_steps=T,
+                               episode_limit=200)
+    first = _check_rollout(g, o, T, n, TIE_F32, DONE_BAND_F32, TOL_F32_FREE)
+    assert (first == T).mean() > 0.9        # almost every env matches for the whole horizon
+    assert g["done"].sum() > n              # episodes end and auto-reset
+    # returns (S7) on the comparable prefix-free envs: rewards 1 and exact done flags
+    r.returns(T)
+    G = r.fetch(W.WS_F_RETURN, 0, T)
+    full = first == T
+    Go = oracle.returns(o["reward"][:, full], o["done"][:, full], float(np.float32(0.99)))
+    err = np.abs(G[:, full] - Go) / np.maximum(np.abs(Go), 1.0)
+    assert err.max() <= 1e-6, err.max()
+    r.close()
+
+
+def test_graph_path_bytes_equal_plain_path(torch):
+    n, T, h = 513, 60, 32
+    out = []
+    for path in FP32_PATHS:
+        r = control_rollout(path, n, T, 200, h, h, seed=3, chunk_steps=7)
+        r.rollout(T)
+        out.append([r.fetch(f, 0, T).tobytes() for f in (W.WS_F_OBS, W.WS_F_ACTION, W.WS_F_LOGP,
+                                                          W.WS_F_DONE)])
+        r.close()
+    assert out[0] == out[1]
+
+
+def test_chunked_equals_unchunked_and_deterministic(torch):
+    n, h = 300, 16
+    a = control_rollout(W.WS_PATH_BATCHED_FP32, n, 100, 200, h, h, seed=9)
+    a.rollout(100)
+    b = control_rollout(W.WS_PATH_BATCHED_FP32, n, 100, 200, h, h, seed=9)
+    for m in (13, 50, 1, 36):
+        b.rollout(m)
+    assert b.k == 100
+    for f in (W.WS_F_OBS, W.WS_F_ACTION, W.WS_F_LOGP, W.WS_F_DONE):
+        assert a.fetch(f, 0, 100).tobytes() == b.fetch(f, 0, 100).tobytes()
+    a.close(); b.close()
+
+
+def test_ring_wraps_and_range_errors(torch):
+    n, h = 64, 8
+    r = control_rollout(W.WS_PATH_PLAIN_FP32, n, 10, 200, h, h, seed=2)
+    r.rollout(25)
+    with pytest.raises(W.WarpSciError) as e:
+        r.fetch(W.WS_F_OBS, 14, 2)                       # overwritten
+    assert e.value.status == W.WS_ERR_RANGE
+    with pytest.raises(W.WarpSciError):
+        r.fetch(W.WS_F_OBS, 20, 6)                       # not yet run
+    wrapped = r.fetch(W.WS_F_ACTION, 15, 10)             # crosses the ring end
+    ref = control_rollout(W.WS_PATH_PLAIN_FP32, n, 40, 200, h, h, seed=2)
+    ref.rollout(25)
+    assert wrapped.tobytes() == ref.fetch(W.WS_F_ACTION, 15, 10).tobytes()
+    with pytest.raises(W.WarpSciError) as e:
+        r.returns(11)
+    assert e.value.status == W.WS_ERR_RANGE
+    r.close(); ref.close()
+
+
+def test_checkpoint_resume_bit_exact(torch):
+    """50 steps, save state, 50 more == restore into a fresh context and run 50."""
+    n, h = 200, 32
+    a = control_rollout(W.WS_PATH_BATCHED_FP32, n, 100, 200, h, h, seed=4)
+    a.rollout(50)
+    st = a.fetch_raw(W.WS_F_STATE, 20 * n)
+    a.rollout(50)
+    b = control_rollout(W.WS_PATH_BATCHED_FP32, n, 100, 200, h, h, seed=4)
+    b.load_raw(W.WS_F_STATE, st, k=50)
+    b.rollout(50)
+    for f in (W.WS_F_OBS, W.WS_F_ACTION, W.WS_F_DONE):
+        assert a.fetch(f, 50, 50).tobytes() == b.fetch(f, 50, 50).tobytes()
+    a.close(); b.close()
+
+
+def test_sync_timeout_is_reported(torch):
+    n, h = 131072, 256
+    r = control_rollout(W.WS_PATH_PLAIN_FP32, n, 4, 200, h, h)
+    r.rollout(4)
+    st = W.ws_sync(r.ctx, 1)       # 1 ms: the plain 4-256-256-2 steps take longer
+    assert st in (W.WS_OK, W.WS_ERR_TIMEOUT)
+    r.sync()
+    r.close()
