@@ -1,12 +1,427 @@
-// ws_control_tc.cu -- fused persistent BF16 tensor-core control kernel.
+// ws_control_tc.cu -- fused persistent BF16 tensor-core roll-out kernel of the
+// control env: one launch runs a whole chunk of steps for every env, with the
+// env state held in registers and nothing but the transition records leaving
+// the SM (paper Sec. 2 / App. B: roll-out, inference, reset and the in-place
+// store all on the GPU; envs independent, policy referenced from GPU memory).
+//
+// Work split: a CTA holds two warpgroups; each owns a tile of 128 envs, one
+// env per thread (thread r of the warpgroup = TMEM lane r = MMA row r).
+// Per step and tile:
+//   layer 1  z1 = s W1 + b1 on the tensor core, K = 16: the row
+//            [s_hi, s_lo, s_hi, 1, 1, 0, 0] against [W1_hi; W1_hi; W1_lo; b1_hi;
+//            b1_lo] keeps FP32-level accuracy (missing term s_lo W1_lo ~ 2^-16)
+//   act 1    h1 = tanh(z1) in packed bf16x2 (the BF16 A operand of layer 2)
+//   layer 2  z2 = h1 W2, K = H0 streamed 64 at a time through two 16 KB
+//            128B-swizzled slots while W2^T stays resident in shared memory
+//   act 2/3  logits = tanh(z2 + b2) W3 + b3 in FP32 registers (TMEM row)
+//   then     categorical sample (Philox), Euler step, reward, done, auto-reset,
+//            and the time-major record write.
+// Both layers accumulate in the same 256 TMEM columns of the warpgroup: z1 is
+// fully read (into registers) before the first layer-2 MMA overwrites it.
 #include "ws_kernels.cuh"
+#include "ws_tc.cuh"
 
 namespace ws {
-size_t control_tc_packed_bytes(const PolicyShape &) { return 0; }
-bool control_tc_supported(const PolicyShape &) { return false; }
-void launch_control_tc_pack(const Dev &, void *, cudaStream_t) {}
-cudaError_t launch_control_tc(const Dev &, const void *, uint32_t, int, cudaStream_t) {
-  return cudaErrorNotSupported;
+
+namespace {
+
+constexpr int kTile = 128;
+constexpr int kWG = 2;
+constexpr int kThreads = kTile * kWG;
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s, far above any MMA completion time
+constexpr uint32_t kTmemCols = 512;
+
+template <int H0, int H1>
+struct CtrlTc {
+  static_assert(H0 % 64 == 0 && H0 <= 256, "layer-2 K must be a multiple of 64, <= 256");
+  static_assert(H1 % 16 == 0 && H1 >= 16 && H1 <= 256, "layer-2 N must be 16..256, step 16");
+  static constexpr int KB = H0 / 64;
+  static constexpr int W2_BYTES = KB * H1 * 128;  // B of layer 2, SW128, K-blocks of 64
+  static constexpr int B1_BYTES = H0 * 32;        // B of layer 1, no swizzle, K = 16
+  static constexpr int EP_BYTES = H1 * 16 + 16;   // {b2, W3[c][0], W3[c][1], 0}, then b3
+  static constexpr int PACKED = W2_BYTES + B1_BYTES + EP_BYTES;
+  static constexpr int SLOT = 128 * 128;          // one A K-block: 128 rows x 128 B
+  static constexpr int OFF_W2 = 0;
+  static constexpr int OFF_A2 = W2_BYTES;
+  static constexpr int OFF_B1 = OFF_A2 + kWG * 2 * SLOT;
+  static constexpr int OFF_A1 = OFF_B1 + B1_BYTES;
+  static constexpr int OFF_EP = OFF_A1 + kWG * 128 * 32;
+  static constexpr int OFF_BAR = (OFF_EP + EP_BYTES + 15) / 16 * 16;
+  static constexpr int N_BAR = 4;  // per warpgroup: layer 1, slot 0, slot 1, drain
+  static constexpr int OFF_TM = OFF_BAR + kWG * N_BAR * 8;
+  // + slack for 1024-byte alignment; at least 120 KB so that one CTA owns an SM
+  // (its 512 TMEM columns are then never contended)
+  static constexpr int SMEM_NEED = OFF_TM + 16 + 1024;
+  static constexpr int SMEM = SMEM_NEED > 120 * 1024 ? SMEM_NEED : 120 * 1024;
+};
+
+__device__ __forceinline__ uint16_t bf16_bits(float f) {
+  return (uint16_t)(tc::pack_bf16x2(f, 0.f) & 0xFFFFu);
 }
-int control_tc_default_grid(const Dev &) { return 0; }
+__device__ __forceinline__ float bf16_val(float f) { return tc::bf16_lo(tc::pack_bf16x2(f, 0.f)); }
+
+// Pack the FP32 policy into the shared-memory byte images the kernel copies
+// verbatim: W2^T (SW128, K-major), the layer-1 hi/lo B operand, and the
+// epilogue table.
+template <int H0, int H1>
+__global__ void k_ctrl_tc_pack(const float *__restrict__ params, uint8_t *__restrict__ packed) {
+  using C = CtrlTc<H0, H1>;
+  const float *W1 = params;        // [4][H0]
+  const float *b1 = W1 + 4 * H0;   // [H0]
+  const float *W2 = b1 + H0;       // [H0][H1]
+  const float *b2 = W2 + H0 * H1;  // [H1]
+  const float *W3 = b2 + H1;       // [H1][2]
+  const float *b3 = W3 + 2 * H1;   // [2]
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  for (int i = tid; i < H0 * H1; i += stride) {
+    const int n = i / H0, k = i % H0;
+    const int kb = k / 64, kk = k % 64;
+    const int off = kb * (H1 * 128) + n * 128 + (((kk >> 3) ^ (n & 7)) << 4) + (kk & 7) * 2;
+    *(uint16_t *)(packed + off) = bf16_bits(W2[(size_t)k * H1 + n]);
+  }
+  for (int i = tid; i < H0 * 16; i += stride) {
+    const int n = i / 16, q = i % 16;
+    float v = 0.f;
+    if (q < 8) {
+      v = bf16_val(W1[(q & 3) * H0 + n]);
+    } else if (q < 12) {
+      const float w = W1[(q - 8) * H0 + n];
+      v = bf16_val(w - bf16_val(w));
+    } else if (q == 12) {
+      v = bf16_val(b1[n]);
+    } else if (q == 13) {
+      v = bf16_val(b1[n] - bf16_val(b1[n]));
+    }
+    const int off = C::W2_BYTES + (n >> 3) * 256 + (q >> 3) * 128 + (n & 7) * 16 + (q & 7) * 2;
+    *(uint16_t *)(packed + off) = bf16_bits(v);
+  }
+  float4 *ep = (float4 *)(packed + C::W2_BYTES + C::B1_BYTES);
+  for (int c = tid; c < H1; c += stride) ep[c] = make_float4(b2[c], W3[2 * c], W3[2 * c + 1], 0.f);
+  if (tid == 0) ep[H1] = make_float4(b3[0], b3[1], 0.f, 0.f);
+}
+
+template <int H0, int H1>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_ctrl_tc(Dev d, const uint8_t *__restrict__ packed, uint32_t n_steps) {
+  using C = CtrlTc<H0, H1>;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = tc::smem_u32(smem_raw);
+  uint8_t *sm = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+  const uint32_t sb = tc::smem_u32(sm);
+  const int tid = threadIdx.x, wg = tid >> 7, r = tid & 127, warp = tid >> 5;
+  uint64_t *bars = (uint64_t *)(sm + C::OFF_BAR) + wg * C::N_BAR;
+  uint64_t *bar_l1 = bars, *bar_slot = bars + 1, *bar_drain = bars + 3;
+  uint32_t *tm_holder = (uint32_t *)(sm + C::OFF_TM);
+
+  // Stage the packed weights (W2^T, layer-1 B, epilogue table) into smem.
+  {
+    const uint4 *src = (const uint4 *)packed;
+    uint4 *w2 = (uint4 *)(sm + C::OFF_W2);
+    for (int i = tid; i < C::W2_BYTES / 16; i += kThreads) w2[i] = __ldg(src + i);
+    src += C::W2_BYTES / 16;
+    uint4 *b1 = (uint4 *)(sm + C::OFF_B1);
+    for (int i = tid; i < C::B1_BYTES / 16; i += kThreads) b1[i] = __ldg(src + i);
+    src += C::B1_BYTES / 16;
+    uint4 *ep = (uint4 *)(sm + C::OFF_EP);
+    for (int i = tid; i < C::EP_BYTES / 16; i += kThreads) ep[i] = __ldg(src + i);
+  }
+  if (tid == 0) {
+    uint64_t *all = (uint64_t *)(sm + C::OFF_BAR);
+    for (int i = 0; i < kWG * C::N_BAR; ++i) tc::mbar_init(all + i, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tc::tmem_alloc(tm_holder, kTmemCols);
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+
+  const uint32_t tmem = *tm_holder + (uint32_t)wg * 256u;
+  const uint32_t lane = (uint32_t)((warp & 3) * 32) << 16;
+  const uint32_t bar_id = 1u + (uint32_t)wg;
+  const uint32_t a1 = sb + C::OFF_A1 + wg * 128 * 32;
+  const uint32_t a2 = sb + C::OFF_A2 + wg * 2 * C::SLOT;
+  const uint64_t desc_a1 = tc::smem_desc(a1, 128, 256, tc::kSwizzleNone);
+  const uint64_t desc_b1 = tc::smem_desc(sb + C::OFF_B1, 128, 256, tc::kSwizzleNone);
+  constexpr uint32_t idesc1 = tc::idesc_bf16_f32(128, H0);
+  constexpr uint32_t idesc2 = tc::idesc_bf16_f32(128, H1);
+  const float4 *ep = (const float4 *)(sm + C::OFF_EP);
+  const float4 b3 = ep[H1];
+  const uint32_t a1_row = a1 + (uint32_t)(r >> 3) * 256u + (uint32_t)(r & 7) * 16u;
+  const uint32_t swz = (uint32_t)(r & 7);
+
+  uint32_t ph_l1 = 0, ph_s0 = 0, ph_s1 = 0;
+  bool ok = true;
+  uint32_t fail_site = 0;
+  const uint64_t k0 = d.k[0];
+  const uint32_t R = d.ring_steps;
+  const uint32_t row0 = (uint32_t)(k0 % R);
+  const uint32_t N = d.n_envs, S = d.n_slots;
+  const int n_tiles = (int)((N + kTile - 1) / kTile);
+  const int n_workers = (int)gridDim.x * kWG;
+
+  for (int tile = (int)blockIdx.x * kWG + wg; ok && tile < n_tiles; tile += n_workers) {
+    const uint32_t e = (uint32_t)tile * kTile + (uint32_t)r;
+    const bool valid = e < N;
+    float x = 0.f, v = 0.f, th = 0.f, w = 0.f;
+    int tep = 0;
+    if (valid) {
+      x = d.s[e];
+      v = d.s[N + e];
+      th = d.s[2 * N + e];
+      w = d.s[3 * N + e];
+      tep = d.t[e];
+    }
+    uint32_t row = row0;
+    for (uint32_t j = 0; j < n_steps; ++j) {
+      const uint32_t k = (uint32_t)(k0 + j);
+      // ---- layer 1 operand row: [s_hi | s_lo | s_hi | 1 1 0 0]
+      {
+        const float xh = bf16_val(x), vh = bf16_val(v), thh = bf16_val(th), wh = bf16_val(w);
+        const uint32_t hi01 = tc::pack_bf16x2(xh, vh), hi23 = tc::pack_bf16x2(thh, wh);
+        const uint32_t lo01 = tc::pack_bf16x2(x - xh, v - vh), lo23 = tc::pack_bf16x2(th - thh, w - wh);
+        tc::sts128(a1_row, hi01, hi23, lo01, lo23);
+        tc::sts128(a1_row + 128, hi01, hi23, tc::pack_bf16x2(1.f, 1.f), 0u);
+      }
+      tc::fence_async_smem();
+      tc::fence_before_sync();
+      tc::wg_sync(bar_id);
+      if (r == 0) {
+        tc::fence_after_sync();
+        tc::mma_bf16(tmem, desc_a1, desc_b1, idesc1, false);
+        tc::mma_commit(bar_l1);
+      }
+      ok = tc::wg_all(bar_id, tc::mbar_wait(bar_l1, ph_l1, kWaitNs));
+      ph_l1 ^= 1u;
+      if (!ok) { fail_site = 1; break; }
+      tc::fence_after_sync();
+      // ---- act 1: h1 = tanh(z1) in packed bf16x2.  K-blocks 0 and 1 go straight
+      // into their (free) slots; later K-blocks wait in registers until z1 has
+      // been read completely (layer 2 accumulates into the same columns).
+      constexpr int KH = C::KB > 2 ? C::KB - 2 : 1;
+      uint32_t hold[KH][32];
+#pragma unroll
+      for (int kb = 0; kb < C::KB; ++kb) {
+        uint32_t hp[32];
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          uint32_t z[32];
+          tc::tmem_ld32(tmem + lane + (uint32_t)(kb * 64 + half * 32), z);
+          tc::tmem_wait_ld();
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            hp[half * 16 + i] = tc::tanh_bf16x2(
+                tc::pack_bf16x2(__uint_as_float(z[2 * i]), __uint_as_float(z[2 * i + 1])));
+        }
+        if (kb < 2) {
+          const uint32_t rowa = a2 + (uint32_t)kb * C::SLOT + (uint32_t)r * 128u;
+#pragma unroll
+          for (int ch = 0; ch < 8; ++ch)
+            tc::sts128(rowa + (((uint32_t)ch ^ swz) << 4), hp[ch * 4 + 0], hp[ch * 4 + 1],
+                       hp[ch * 4 + 2], hp[ch * 4 + 3]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) hold[kb - 2][i] = hp[i];
+        }
+      }
+      tc::fence_async_smem();
+      tc::fence_before_sync();
+      tc::wg_sync(bar_id);  // every lane has read z1 and written K-blocks 0, 1
+      // ---- layer 2, one K-block of 64 at a time through the two slots
+#pragma unroll
+      for (int kb = 0; kb < C::KB; ++kb) {
+        const int s = kb & 1;
+        const uint32_t slot = a2 + (uint32_t)s * C::SLOT;
+        if (kb >= 2) {
+          uint32_t &ph = s ? ph_s1 : ph_s0;
+          ok = tc::wg_all(bar_id, tc::mbar_wait(bar_slot + s, ph, kWaitNs));
+          ph ^= 1u;
+          if (!ok) { fail_site = 2; break; }
+          const uint32_t rowa = slot + (uint32_t)r * 128u;
+#pragma unroll
+          for (int ch = 0; ch < 8; ++ch)
+            tc::sts128(rowa + (((uint32_t)ch ^ swz) << 4), hold[kb - 2][ch * 4 + 0],
+                       hold[kb - 2][ch * 4 + 1], hold[kb - 2][ch * 4 + 2], hold[kb - 2][ch * 4 + 3]);
+          tc::fence_async_smem();
+          tc::wg_sync(bar_id);
+        }
+        if (r == 0) {
+          tc::fence_after_sync();
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t da = tc::smem_desc(slot + kk * 32, 16, 1024, tc::kSwizzle128B);
+            const uint64_t db = tc::smem_desc(sb + C::OFF_W2 + kb * (H1 * 128) + kk * 32, 16, 1024,
+                                              tc::kSwizzle128B);
+            tc::mma_bf16(tmem, da, db, idesc2, (kb | kk) != 0);
+          }
+          tc::mma_commit(bar_slot + s);
+        }
+      }
+      if (!ok) break;
+      // drain both slots (the last commit covers every MMA of this step)
+      if (C::KB >= 2) {
+        const int s = (C::KB - 2) & 1;
+        uint32_t &ph = s ? ph_s1 : ph_s0;
+        ok = tc::wg_all(bar_id, tc::mbar_wait(bar_slot + s, ph, kWaitNs));
+        ph ^= 1u;
+        if (!ok) { fail_site = 3; break; }
+      }
+      {
+        const int s = (C::KB - 1) & 1;
+        uint32_t &ph = s ? ph_s1 : ph_s0;
+        ok = tc::wg_all(bar_id, tc::mbar_wait(bar_slot + s, ph, kWaitNs));
+        ph ^= 1u;
+        if (!ok) { fail_site = 4; break; }
+      }
+      tc::fence_after_sync();
+      // ---- act 2 and layer 3: logits = tanh(z2 + b2) W3 + b3
+      float l0 = b3.x, l1 = b3.y;
+#pragma unroll
+      for (int c0 = 0; c0 < H1; c0 += 32) {
+        uint32_t z[32];
+        tc::tmem_ld32(tmem + lane + (uint32_t)c0, z);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const float4 p = ep[c0 + 2 * i], q = ep[c0 + 2 * i + 1];
+          const uint32_t hh = tc::tanh_bf16x2(
+              tc::pack_bf16x2(__uint_as_float(z[2 * i]) + p.x, __uint_as_float(z[2 * i + 1]) + q.x));
+          const float ha = tc::bf16_lo(hh), hb = tc::bf16_hi(hh);
+          l0 = fmaf(ha, p.y, l0);
+          l1 = fmaf(ha, p.z, l1);
+          l0 = fmaf(hb, q.y, l0);
+          l1 = fmaf(hb, q.z, l1);
+        }
+      }
+      // ---- sample: a = 0 iff u S < exp(l0 - m)
+      const float u = u01(draw(d.seed, k, e, 0, kTagAction, 0).x);
+      const float m = fmaxf(l0, l1);
+      const float e0 = expf(l0 - m), e1 = expf(l1 - m);
+      const float Ssum = e0 + e1;
+      const int a = (u * Ssum < e0) ? 0 : 1;
+      const float lp = ((a ? l1 : l0) - m) - logf(Ssum);
+      // ---- env step (explicit Euler, dt = 0.02), reward, done, auto-reset
+      const float uf = a ? 10.0f : -10.0f;
+      const float xacc = uf - 0.5f * x - 0.1f * v;
+      const float thacc = 9.8f * sinf(th) - 0.3f * cosf(th) * uf;
+      const float x2 = x + 0.02f * v, v2 = v + 0.02f * xacc;
+      const float th2 = th + 0.02f * w, w2 = w + 0.02f * thacc;
+      const int t2 = tep + 1;
+      const bool done = fabsf(x2) > 2.4f || fabsf(th2) > 0.21f || t2 >= (int)d.episode_limit;
+      if (valid) {
+        const size_t o = (size_t)row * S + e;
+        float *ob = d.r_obs + (size_t)row * 4 * S + e;
+        ob[0] = x;
+        ob[S] = v;
+        ob[2 * (size_t)S] = th;
+        ob[3 * (size_t)S] = w;
+        ((int32_t *)d.r_act)[o] = a;
+        d.r_logp[o] = lp;
+        d.r_rew[o] = 1.0f;
+        d.r_done[o] = (uint8_t)done;
+      }
+      if (done) {
+        const uint4 rr = draw(d.seed, k, e, 0, kTagReset, 0);
+        x = uniform(rr.x, -0.05f, 0.05f);
+        v = uniform(rr.y, -0.05f, 0.05f);
+        th = uniform(rr.z, -0.05f, 0.05f);
+        w = uniform(rr.w, -0.05f, 0.05f);
+        tep = 0;
+      } else {
+        x = x2;
+        v = v2;
+        th = th2;
+        w = w2;
+        tep = t2;
+      }
+      row = (row + 1 == R) ? 0 : row + 1;
+    }
+    if (valid) {
+      d.s[e] = x;
+      d.s[N + e] = v;
+      d.s[2 * N + e] = th;
+      d.s[3 * N + e] = w;
+      d.t[e] = tep;
+    }
+  }
+  if (!ok) {
+    if (r == 0) {
+      // let any MMA still in flight finish before the columns are released
+      tc::mma_commit(bar_drain);
+      tc::mbar_wait(bar_drain, 0, kWaitNs);
+      atomicExch(d.err, 1u);
+      atomicExch(d.err + 1, 100u + fail_site);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(*tm_holder, kTmemCols);
+  }
+}
+
+template <int H0, int H1>
+struct Shape {
+  static void pack(const Dev &d, void *packed, cudaStream_t st) {
+    k_ctrl_tc_pack<H0, H1><<<64, 256, 0, st>>>(d.params, (uint8_t *)packed);
+  }
+  static cudaError_t run(const Dev &d, const void *packed, uint32_t n, int grid, cudaStream_t st) {
+    k_ctrl_tc<H0, H1><<<grid, kThreads, CtrlTc<H0, H1>::SMEM, st>>>(d, (const uint8_t *)packed, n);
+    return cudaGetLastError();
+  }
+  static cudaError_t attr() {
+    return cudaFuncSetAttribute(k_ctrl_tc<H0, H1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                CtrlTc<H0, H1>::SMEM);
+  }
+};
+
+template <typename F>
+bool dispatch(const PolicyShape &sh, F &&f) {
+  if (sh.w[0] != 4 || sh.w[3] != 2) return false;
+  if (sh.w[1] == 256 && sh.w[2] == 256) return f(Shape<256, 256>()), true;
+  if (sh.w[1] == 128 && sh.w[2] == 128) return f(Shape<128, 128>()), true;
+  if (sh.w[1] == 64 && sh.w[2] == 64) return f(Shape<64, 64>()), true;
+  return false;
+}
+
+}  // namespace
+
+size_t control_tc_packed_bytes(const PolicyShape &sh) {
+  size_t n = 0;
+  dispatch(sh, [&](auto s) {
+    using S = decltype(s);
+    (void)sizeof(S);
+    if (sh.w[1] == 256) n = CtrlTc<256, 256>::PACKED;
+    if (sh.w[1] == 128) n = CtrlTc<128, 128>::PACKED;
+    if (sh.w[1] == 64) n = CtrlTc<64, 64>::PACKED;
+  });
+  return n;
+}
+
+bool control_tc_supported(const PolicyShape &sh) {
+  return dispatch(sh, [](auto) {});
+}
+
+void launch_control_tc_pack(const Dev &d, void *packed, cudaStream_t st) {
+  dispatch(d.pol, [&](auto s) { s.pack(d, packed, st); });
+}
+
+cudaError_t launch_control_tc(const Dev &d, const void *packed, uint32_t n_steps, int grid,
+                              cudaStream_t st) {
+  cudaError_t e = cudaErrorNotSupported;
+  dispatch(d.pol, [&](auto s) { e = s.run(d, packed, n_steps, grid, st); });
+  return e;
+}
+
+int control_tc_default_grid(const Dev &d) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  dispatch(d.pol, [](auto s) { s.attr(); });
+  const int tiles = (int)((d.n_envs + kTile - 1) / kTile);
+  const int want = (tiles + kWG - 1) / kWG;
+  return want < sms ? want : sms;
+}
+
 }  // namespace ws

@@ -187,3 +187,140 @@ def test_sync_timeout_is_reported(torch):
     assert st in (W.WS_OK, W.WS_ERR_TIMEOUT)
     r.sync()
     r.close()
+
+
+# ----------------------------------------------------------- BF16 tensor-core path
+BF16 = W.WS_PATH_BATCHED_BF16
+ORACLE_BF16_LAYERS = 0b010   # layer 2 runs in BF16 (operands rounded); layers 1, 3 FP32
+
+
+@pytest.mark.parametrize("h", [64, 128, 256])
+def test_bf16_one_step_replay_seeded_states(torch, h):
+    n = 3000                                  # 24 tiles, ragged tail of 56 envs
+    g = inputs.rng(21 + h)
+    params = inputs.policy_params(g, [4, h, h, 2], scale=2.0)
+    s0, t0 = inputs.control_states(g, n)
+    t0[:40] = 199
+    r = control_rollout(BF16, n, 8, 200, h, h)
+    r.load_raw(W.WS_F_PARAMS, params)
+    k0 = 777
+    r.load_raw(W.WS_F_STATE, H.pack_control_state(s0, t0), k=k0)
+    r.step()
+    r.sync()
+    act = r.fetch(W.WS_F_ACTION, k0, 1)[0]
+    lp = r.fetch(W.WS_F_LOGP, k0, 1)[0]
+    dn = r.fetch(W.WS_F_DONE, k0, 1)[0]
+    obs = r.fetch(W.WS_F_OBS, k0, 1)[0]
+    s1, t1 = H.unpack_control_state(r.fetch_raw(W.WS_F_STATE, 20 * n), n)
+    o = oracle.control_rollout(params, h, h, seed=1, env_ids=np.arange(n), n_steps=1,
+                               episode_limit=200, k0=k0, state0=s0, t0=t0,
+                               bf16_layers=ORACLE_BF16_LAYERS)
+    np.testing.assert_array_equal(obs.T, s0.astype(np.float32))
+    amb = (o["act_margin"][0] < TIE_BF16) | (o["done_margin"][0] < DONE_BAND_F32)
+    ok = ~amb
+    assert ok.mean() > 0.9
+    assert np.array_equal(act[ok], o["action"][0][ok])
+    assert np.array_equal(dn[ok], o["done"][0][ok])
+    assert np.all(dn[:40] == 1)
+    lp_err = np.abs(lp[ok] - o["logp"][0][ok]) / np.maximum(np.abs(o["logp"][0][ok]), 1.0)
+    assert lp_err.max() <= TOL_BF16, lp_err.max()
+    # the env step itself is FP32: once the action agrees, the state agrees to FP32 level
+    err = H.rel_err_rows(s1[ok], o["state"][ok])
+    assert err.max() <= TOL_F32, err.max()
+    assert np.array_equal(t1[ok], o["t"][ok])
+    r.close()
+
+
+def test_bf16_small_config_rollout(torch):
+    """1,000 envs x 200 steps, 4-64-64-2 on the tensor-core path, vs the oracle in
+    BF16-operand mode, compared up to each env's first tie-band draw."""
+    n, T, h = 1000, 200, 64
+    r = control_rollout(BF16, n, T, 200, h, h, seed=7, chunk_steps=50)
+    r.reset(42)
+    r.rollout(T)
+    r.sync()
+    g = {f: r.fetch(fid, 0, T) for f, fid in [("obs", W.WS_F_OBS), ("action", W.WS_F_ACTION),
+                                              ("logp", W.WS_F_LOGP), ("reward", W.WS_F_REWARD),
+                                              ("done", W.WS_F_DONE)]}
+    params = oracle.policy_init(7, 0, [4, h, h, 2])
+    o = oracle.control_rollout(params, h, h, seed=42, env_ids=np.arange(n), n_steps=T,
+                               episode_limit=200, bf16_layers=ORACLE_BF16_LAYERS)
+    first = _check_rollout(g, o, T, n, TIE_BF16, DONE_BAND_F32, TOL_BF16)
+    assert first.mean() > 10
+    np.testing.assert_array_equal(g["obs"][0].T, o["obs"][0].astype(np.float32))
+    r.close()
+
+
+def test_bf16_graph_is_deterministic_and_chunk_invariant(torch):
+    n, h = 700, 64
+    a = control_rollout(BF16, n, 120, 200, h, h, seed=5, chunk_steps=40)
+    a.rollout(120)
+    b = control_rollout(BF16, n, 120, 200, h, h, seed=5, chunk_steps=7)
+    for m in (50, 1, 69):
+        b.rollout(m)
+    c = control_rollout(BF16, n, 120, 200, h, h, seed=5, chunk_steps=40)
+    c.rollout(120)
+    for f in (W.WS_F_OBS, W.WS_F_ACTION, W.WS_F_LOGP, W.WS_F_DONE):
+        x = a.fetch(f, 0, 120).tobytes()
+        assert x == b.fetch(f, 0, 120).tobytes()
+        assert x == c.fetch(f, 0, 120).tobytes()
+    a.close(); b.close(); c.close()
+
+
+def test_bf16_scale_config_sampled(torch):
+    """131,072 envs x 500 steps, 4-256-256-2, chunks of 50 (the launch shape the bench
+    times): initial draws exact for every env, sampled envs against the oracle."""
+    n, T, h = 131072, 500, 256
+    r = control_rollout(BF16, n, T, 200, h, h, seed=1, chunk_steps=50)
+    r.reset(1000)
+    for _ in range(T // 50):
+        r.rollout(50)
+    r.sync()
+    act = r.fetch(W.WS_F_ACTION, 0, T)
+    dn = r.fetch(W.WS_F_DONE, 0, T)
+    obs0 = r.fetch(W.WS_F_OBS, 0, 1)[0]
+    g_rng = np.random.default_rng(0)
+    ids = np.sort(g_rng.choice(n, 48, replace=False))
+    ids[-1] = n - 1
+    exp0 = np.array([oracle.control_reset_draw(1000, oracle.STEP_INIT, e) for e in range(0, n, 97)])
+    np.testing.assert_array_equal(obs0[:, ::97].T, exp0.astype(np.float32))
+    obs = r.fetch(W.WS_F_OBS, 0, T)[:, :, ids]
+    lp = r.fetch(W.WS_F_LOGP, 0, T)[:, ids]
+    params = oracle.policy_init(1, 0, [4, h, h, 2])
+    o = oracle.control_rollout(params, h, h, seed=1000, env_ids=ids, n_steps=T, episode_limit=200,
+                               bf16_layers=ORACLE_BF16_LAYERS)
+    g = dict(obs=obs, action=act[:, ids], logp=lp, reward=np.ones((T, len(ids)), np.float32),
+             done=dn[:, ids])
+    first = _check_rollout(g, o, T, len(ids), TIE_BF16, DONE_BAND_F32, TOL_BF16)
+    assert first.mean() > 10
+    # every done leads to the Philox reset draw (checked on a sample of done events)
+    tt, ee = np.nonzero(dn[:-1])
+    pick = g_rng.choice(len(tt), min(300, len(tt)), replace=False)
+    nxt = r.fetch(W.WS_F_OBS, 0, T)
+    for i in pick:
+        t, e = int(tt[i]), int(ee[i])
+        np.testing.assert_array_equal(nxt[t + 1, :, e],
+                                      oracle.control_reset_draw(1000, t, e).astype(np.float32))
+    # episode statistics of the random policy: dones happen, actions are balanced
+    assert 0.2 < act.mean() < 0.8
+    assert dn.mean() > 0.01
+    r.close()
+
+
+def test_bf16_param_load_takes_effect(torch):
+    n, h = 256, 128
+    r = control_rollout(BF16, n, 4, 200, h, h, seed=2)
+    g = inputs.rng(3)
+    for trial in range(2):
+        params = inputs.policy_params(g, [4, h, h, 2], scale=3.0)
+        r.load_raw(W.WS_F_PARAMS, params)
+        s0, t0 = inputs.control_states(g, n)
+        r.load_raw(W.WS_F_STATE, H.pack_control_state(s0, t0), k=10 * trial)
+        r.step()
+        act = r.fetch(W.WS_F_ACTION, 10 * trial, 1)[0]
+        o = oracle.control_rollout(params, h, h, seed=2, env_ids=np.arange(n), n_steps=1,
+                                   episode_limit=200, k0=10 * trial, state0=s0, t0=t0,
+                                   bf16_layers=ORACLE_BF16_LAYERS)
+        ok = o["act_margin"][0] >= TIE_BF16
+        assert np.array_equal(act[ok], o["action"][0][ok])
+    r.close()
