@@ -186,6 +186,26 @@ const char *ws_last_error(const ws_ctx *ctx);
  * Waits for the context's outstanding work first. */
 void ws_destroy(ws_ctx *ctx);
 
+/* Policy forward pass that allocates no device memory (the paper has no
+ * counterpart; it is a service for callers that cannot call cudaMalloc, such
+ * as code running during CUDA-graph capture, hosts whose allocator forbids
+ * foreign allocations, or embedded runtimes with fixed device memory).
+ *   out[n_rows][out_dim] = tanh(tanh(obs W0 + b0) W1 + b1) W2 + b2, in FP32,
+ * obs [n_rows][in_dim] row-major and params in the PARAMS layout (per layer
+ * W[n_in][n_out] row-major, then b), all device pointers owned by the caller.
+ * The hidden activations use a 16 MiB library-owned static device array
+ * (every GPU that loads the library holds it until the process exits), so
+ * n_rows * (hidden0 + hidden1) may not exceed 4,194,304 floats: larger
+ * requests return WS_ERR_RANGE before anything is launched.  No cudaMalloc,
+ * cudaFree or allocating library call is made.  The first call on a device
+ * looks up that array's device address (with that device current); make that
+ * first call before any stream capture.  All calls on a device share the
+ * array: calls that overlap on the GPU (other streams, other threads) race and
+ * must be serialised by the caller.  Asynchronous on cuda_stream. */
+ws_status ws_policy_forward_noalloc(const float *obs, uint32_t n_rows, const float *params,
+                                    uint32_t in_dim, uint32_t hidden0, uint32_t hidden1,
+                                    uint32_t out_dim, float *out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,3 +68,10 @@ cudaError_t launch_control_tc(const Dev &d, const void *packed, uint32_t n_steps
 int control_tc_default_grid(const Dev &d);
 
 }  // namespace ws
+
+namespace ws {
+// Y[M][N] = act(X W + b) with the plain path's FP32 dense kernel (X row-major
+// when ldc == 1, or addressed X[r * ldr + c * ldc]).
+void launch_dense_fp32(const float *X, long ldr, long ldc, const float *W, const float *b, float *Y,
+                       int M, int K, int N, int act, cudaStream_t st);
+}  // namespace ws

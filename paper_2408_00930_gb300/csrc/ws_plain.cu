@@ -679,3 +679,10 @@ void launch_returns(const Dev &d, uint32_t n_steps, cudaStream_t st) {
 }
 
 }  // namespace ws
+
+namespace ws {
+void launch_dense_fp32(const float *X, long ldr, long ldc, const float *W, const float *b, float *Y,
+                       int M, int K, int N, int act, cudaStream_t st) {
+  dense(X, ldr, ldc, W, b, Y, M, K, N, act, st);
+}
+}  // namespace ws

@@ -27,7 +27,8 @@ WS_PATH_PLAIN_FP32, WS_PATH_BATCHED_FP32, WS_PATH_BATCHED_BF16 = 0, 1, 2
  WS_F_STATE, WS_F_PARAMS, WS_F_ENV_PARAMS, WS_F_LOGITS) = range(12)
 
 EXPORTED = ["ws_query_bytes", "ws_create", "ws_reset", "ws_step", "ws_rollout", "ws_returns",
-            "ws_fetch", "ws_load", "ws_get_step", "ws_sync", "ws_last_error", "ws_destroy"]
+            "ws_fetch", "ws_load", "ws_get_step", "ws_sync", "ws_last_error", "ws_destroy",
+            "ws_policy_forward_noalloc"]
 
 
 class ws_config(C.Structure):
@@ -74,6 +75,8 @@ def lib():
         L.ws_last_error.restype = C.c_char_p
         L.ws_destroy.argtypes = [P]
         L.ws_destroy.restype = None
+        L.ws_policy_forward_noalloc.argtypes = [P, C.c_uint32, P, C.c_uint32, C.c_uint32,
+                                                C.c_uint32, C.c_uint32, P, P]
         for n in EXPORTED:
             if n not in ("ws_last_error", "ws_destroy"):
                 getattr(L, n).restype = C.c_int
@@ -135,6 +138,12 @@ def ws_last_error(ctx):
 
 def ws_destroy(ctx):
     lib().ws_destroy(ctx)
+
+
+def ws_policy_forward_noalloc(obs_ptr, n_rows, params_ptr, in_dim, hidden0, hidden1, out_dim,
+                              out_ptr, stream_ptr):
+    return lib().ws_policy_forward_noalloc(obs_ptr, n_rows, params_ptr, in_dim, hidden0, hidden1,
+                                           out_dim, out_ptr, stream_ptr)
 
 
 # --- convenience owner --------------------------------------------------------
