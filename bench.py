@@ -175,7 +175,7 @@ def _oracle_shard(args):
     return agent_steps, time.perf_counter() - t0
 
 
-def oracle_throughput(wl_name, target_s=12.0):
+def oracle_throughput(wl_name, target_s=20.0):
     """The FP64 oracle, as it stands, on the host cores: one process per core
     (spawned), each rolling out its own envs; a bounded sample of the workload."""
     import multiprocessing as mp

@@ -442,7 +442,11 @@ void or_econ_env_step(const float *agent_params, const float *planner_params, ui
     wealth[i] -= tax;
     T += tax;
   }
-  int64_t share = T / n, rem = T % n;
+  int64_t share = T / n, rem = T % n; /* floor division, any sign of the pool */
+  if (rem < 0) {
+    rem += n;
+    share -= 1;
+  }
   for (int i = 0; i < n; ++i) wealth[i] += share + (i < rem ? 1 : 0);
   /* features and rewards */
   double rsum = 0.0;

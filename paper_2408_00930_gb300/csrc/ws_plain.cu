@@ -421,7 +421,12 @@ __global__ __launch_bounds__(kEconThreads) void k_econ_finish(Dev d, uint32_t of
     tsum += tax;
   }
   const long long T = block_sum(tsum, shi);
-  const int64_t share = T / n, rem = T % n;
+  // floor(T / n) and T - n floor(T / n) in [0, n), for a pool of either sign
+  int64_t share = T / n, rem = T % n;
+  if (rem < 0) {
+    rem += n;
+    share -= 1;
+  }
   const int t2 = d.t[e] + 1;
   const bool done = t2 >= (int)d.episode_limit;
   const float inv_ln_1e6 = 0.0723824136505f;

@@ -455,6 +455,9 @@ ws_status ws_reset(ws_ctx *c, uint64_t seed) {
   c->seed = seed;
   c->d.seed = seed;
   cudaMemsetAsync(c->d.k, 0, 8, c->stream);
+  // the economy's per-step income accumulator must start at zero (every step
+  // clears it after use; a fresh caller buffer holds arbitrary bytes)
+  if (c->d.income) cudaMemsetAsync(c->d.income, 0, (size_t)c->L.n_agent_slots * 8, c->stream);
   launch_reset(c->d, c->stream);
   c->k_host = 0;
   return cuda_check(c, cudaGetLastError(), "reset");

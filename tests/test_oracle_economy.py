@@ -149,3 +149,18 @@ def test_econ_agent_counts_range(orc):
     c = [orc.econ_agent_count(11, e) for e in range(4000)]
     assert min(c) == 8 and max(c) == 256
     assert abs(np.mean(c) - 132) < 3
+
+
+def test_econ_pool_split_is_floor_for_negative_pools(orc):
+    """With negative wealth the transfers, incomes and the tax pool turn negative; the
+    split floor(T/n) plus the remainder T - n floor(T/n) in [0, n) still conserves."""
+    ap = _forced_agent_params(orc, const=19)
+    pp = _forced_planner_params(orc, 9)
+    n = 7
+    w = np.array([-50_003, -120_007, -9_999, 40_001, -77_777, -3_001, -1_000_000], np.int64)
+    f = np.zeros((n, 16))
+    r = orc.econ_rollout(ap, pp, seed=2, env_ids=[0], n_agents=[n], n_steps=3, episode_limit=540,
+                         wealth0=w, feat0=f, t0=[0])
+    for t in range(3):
+        assert r["wealth"][t, :n].sum() == w.sum()
+    assert r["wealth_out"].sum() == w.sum()
