@@ -330,8 +330,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--horizon", type=int, default=0,
+                    help="override the horizon (smaller cases for profiling captures)")
+    ap.add_argument("--n-envs", type=int, default=0, help="override the env count")
     args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.horizon:
+        wl["horizon"] = args.horizon
+        wl["desc"] += f" [horizon overridden to {args.horizon}]"
+    if args.n_envs:
+        wl["n_envs"] = args.n_envs
+        wl["desc"] += f" [envs overridden to {args.n_envs}]"
     world, rank, local = dist_init()
     if args.impl == "reference":
         if rank == 0:
