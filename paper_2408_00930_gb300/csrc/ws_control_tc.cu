@@ -7,17 +7,22 @@
 // Work split: a CTA holds two warpgroups; each owns a tile of 128 envs, one
 // env per thread (thread r of the warpgroup = TMEM lane r = MMA row r).
 // Per step and tile:
-//   layer 1  z1 = s W1 + b1 on the tensor core, K = 16: the row
+//   layer 1  z1 = s W1 + b1 on the tensor core, K = 16: the operand row
 //            [s_hi, s_lo, s_hi, 1, 1, 0, 0] against [W1_hi; W1_hi; W1_lo; b1_hi;
 //            b1_lo] keeps FP32-level accuracy (missing term s_lo W1_lo ~ 2^-16)
 //   act 1    h1 = tanh(z1) in packed bf16x2 (the BF16 A operand of layer 2)
-//   layer 2  z2 = h1 W2, K = H0 streamed 64 at a time through two 16 KB
-//            128B-swizzled slots while W2^T stays resident in shared memory
-//   act 2/3  logits = tanh(z2 + b2) W3 + b3 in FP32 registers (TMEM row)
+//   layer 2  z2 = h1 W2 + b2: one K = 16 MMA of the same operand row against
+//            [0 x 12, b2_hi, b2_lo, 0, 0] (its constant-one columns), then K = H0
+//            streamed 64 at a time through two 16 KB 128B-swizzled slots while
+//            W2^T stays resident in shared memory
+//   act 2    h2 = tanh(z2) in packed bf16x2, streamed back through the slots
+//   layer 3  logits = h2 W3 on the tensor core, N = 16 with W3 split hi/lo
+//            (columns W3_hi[:,0], W3_hi[:,1], W3_lo[:,0], W3_lo[:,1]); + b3
 //   then     categorical sample (Philox), Euler step, reward, done, auto-reset,
 //            and the time-major record write.
-// Both layers accumulate in the same 256 TMEM columns of the warpgroup: z1 is
-// fully read (into registers) before the first layer-2 MMA overwrites it.
+// All three layers accumulate in the same 256 TMEM columns of the warpgroup:
+// z1 is fully read before the first layer-2 MMA overwrites it, and layer 3
+// writes only columns 0..15 after every lane has read them.
 #include "ws_kernels.cuh"
 #include "ws_tc.cuh"
 
@@ -34,25 +39,39 @@ constexpr uint32_t kTmemCols = 512;
 template <int H0, int H1>
 struct CtrlTc {
   static_assert(H0 % 64 == 0 && H0 <= 256, "layer-2 K must be a multiple of 64, <= 256");
-  static_assert(H1 % 16 == 0 && H1 >= 16 && H1 <= 256, "layer-2 N must be 16..256, step 16");
-  static constexpr int KB = H0 / 64;
-  static constexpr int W2_BYTES = KB * H1 * 128;  // B of layer 2, SW128, K-blocks of 64
-  static constexpr int B1_BYTES = H0 * 32;        // B of layer 1, no swizzle, K = 16
-  static constexpr int EP_BYTES = H1 * 16 + 16;   // {b2, W3[c][0], W3[c][1], 0}, then b3
-  static constexpr int PACKED = W2_BYTES + B1_BYTES + EP_BYTES;
-  static constexpr int SLOT = 128 * 128;          // one A K-block: 128 rows x 128 B
+  static_assert(H1 % 64 == 0 && H1 <= 256, "layer-3 K (= H1) must be a multiple of 64, <= 256");
+  static constexpr int KB = H0 / 64;               // layer-2 K-blocks
+  static constexpr int KB3 = H1 / 64;              // layer-3 K-blocks
+  static constexpr int W2_BYTES = KB * H1 * 128;   // B of layer 2, SW128, K-blocks of 64
+  static constexpr int B3_BYTES = KB3 * 16 * 128;  // B of layer 3 (N = 16), SW128
+  static constexpr int B1_BYTES = H0 * 32;         // B of layer 1, no swizzle, K = 16
+  static constexpr int BB_BYTES = H1 * 32;         // B of the b2 MMA, no swizzle, K = 16
+  static constexpr int B3V_BYTES = 16;             // b3 (2 floats, padded)
+  // packed global image: [W2 | B3 | B1 | BB | b3]
+  static constexpr int PK_W2 = 0;
+  static constexpr int PK_B3 = PK_W2 + W2_BYTES;
+  static constexpr int PK_B1 = PK_B3 + B3_BYTES;
+  static constexpr int PK_BB = PK_B1 + B1_BYTES;
+  static constexpr int PK_B3V = PK_BB + BB_BYTES;
+  static constexpr int PACKED = PK_B3V + B3V_BYTES;
+  // shared memory (from a 1024-aligned base)
+  static constexpr int SLOT = 128 * 128;  // one A K-block: 128 rows x 128 B
   static constexpr int OFF_W2 = 0;
-  static constexpr int OFF_A2 = W2_BYTES;
+  static constexpr int OFF_B3 = OFF_W2 + W2_BYTES;
+  static constexpr int OFF_A2 = OFF_B3 + B3_BYTES;
   static constexpr int OFF_B1 = OFF_A2 + kWG * 2 * SLOT;
-  static constexpr int OFF_A1 = OFF_B1 + B1_BYTES;
-  static constexpr int OFF_EP = OFF_A1 + kWG * 128 * 32;
-  static constexpr int OFF_BAR = (OFF_EP + EP_BYTES + 15) / 16 * 16;
+  static constexpr int OFF_BB = OFF_B1 + B1_BYTES;
+  static constexpr int OFF_A1 = OFF_BB + BB_BYTES;
+  static constexpr int OFF_B3V = OFF_A1 + kWG * 128 * 32;
+  static constexpr int OFF_BAR = OFF_B3V + B3V_BYTES;
   static constexpr int N_BAR = 4;  // per warpgroup: layer 1, slot 0, slot 1, drain
   static constexpr int OFF_TM = OFF_BAR + kWG * N_BAR * 8;
   // + slack for 1024-byte alignment; at least 120 KB so that one CTA owns an SM
   // (its 512 TMEM columns are then never contended)
   static constexpr int SMEM_NEED = OFF_TM + 16 + 1024;
   static constexpr int SMEM = SMEM_NEED > 120 * 1024 ? SMEM_NEED : 120 * 1024;
+  static_assert(SMEM_NEED <= 232448, "shared memory over the 227 KB per-CTA limit");
+  static_assert(OFF_A2 % 1024 == 0 && OFF_B3 % 1024 == 0, "SW128 operands need 1 KB alignment");
 };
 
 __device__ __forceinline__ uint16_t bf16_bits(float f) {
@@ -60,9 +79,19 @@ __device__ __forceinline__ uint16_t bf16_bits(float f) {
 }
 __device__ __forceinline__ float bf16_val(float f) { return tc::bf16_lo(tc::pack_bf16x2(f, 0.f)); }
 
-// Pack the FP32 policy into the shared-memory byte images the kernel copies
-// verbatim: W2^T (SW128, K-major), the layer-1 hi/lo B operand, and the
-// epilogue table.
+// Byte offset of element (row n, k) in a 128B-swizzled K-major operand of
+// `rows` rows and K-blocks of 64 elements.
+__device__ __forceinline__ int sw128_off(int n, int k, int rows) {
+  const int kb = k >> 6, kk = k & 63;
+  return kb * (rows * 128) + n * 128 + (((kk >> 3) ^ (n & 7)) << 4) + (kk & 7) * 2;
+}
+// Byte offset of element (row n, q) in a K = 16 operand without swizzle
+// (8-row core matrices of 16 B rows; K-adjacent core matrices 128 B apart).
+__device__ __forceinline__ int k16_off(int n, int q) {
+  return (n >> 3) * 256 + (q >> 3) * 128 + (n & 7) * 16 + (q & 7) * 2;
+}
+
+// Pack the FP32 policy into the byte images the kernel copies verbatim.
 template <int H0, int H1>
 __global__ void k_ctrl_tc_pack(const float *__restrict__ params, uint8_t *__restrict__ packed) {
   using C = CtrlTc<H0, H1>;
@@ -73,12 +102,24 @@ __global__ void k_ctrl_tc_pack(const float *__restrict__ params, uint8_t *__rest
   const float *W3 = b2 + H1;       // [H1][2]
   const float *b3 = W3 + 2 * H1;   // [2]
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  // layer 2: B row n (output unit), K = input unit
   for (int i = tid; i < H0 * H1; i += stride) {
     const int n = i / H0, k = i % H0;
-    const int kb = k / 64, kk = k % 64;
-    const int off = kb * (H1 * 128) + n * 128 + (((kk >> 3) ^ (n & 7)) << 4) + (kk & 7) * 2;
-    *(uint16_t *)(packed + off) = bf16_bits(W2[(size_t)k * H1 + n]);
+    *(uint16_t *)(packed + C::PK_W2 + sw128_off(n, k, H1)) = bf16_bits(W2[(size_t)k * H1 + n]);
   }
+  // layer 3: rows W3_hi[:,0], W3_hi[:,1], W3_lo[:,0], W3_lo[:,1], zeros
+  for (int i = tid; i < 16 * H1; i += stride) {
+    const int n = i / H1, k = i % H1;
+    float v = 0.f;
+    if (n < 2) {
+      v = bf16_val(W3[2 * k + n]);
+    } else if (n < 4) {
+      const float w = W3[2 * k + (n - 2)];
+      v = bf16_val(w - bf16_val(w));
+    }
+    *(uint16_t *)(packed + C::PK_B3 + sw128_off(n, k, 16)) = bf16_bits(v);
+  }
+  // layer 1 row n: [W1_hi[0..3][n], W1_hi[0..3][n], W1_lo[0..3][n], b1_hi, b1_lo, 0, 0]
   for (int i = tid; i < H0 * 16; i += stride) {
     const int n = i / 16, q = i % 16;
     float v = 0.f;
@@ -92,12 +133,51 @@ __global__ void k_ctrl_tc_pack(const float *__restrict__ params, uint8_t *__rest
     } else if (q == 13) {
       v = bf16_val(b1[n] - bf16_val(b1[n]));
     }
-    const int off = C::W2_BYTES + (n >> 3) * 256 + (q >> 3) * 128 + (n & 7) * 16 + (q & 7) * 2;
-    *(uint16_t *)(packed + off) = bf16_bits(v);
+    *(uint16_t *)(packed + C::PK_B1 + k16_off(n, q)) = bf16_bits(v);
   }
-  float4 *ep = (float4 *)(packed + C::W2_BYTES + C::B1_BYTES);
-  for (int c = tid; c < H1; c += stride) ep[c] = make_float4(b2[c], W3[2 * c], W3[2 * c + 1], 0.f);
-  if (tid == 0) ep[H1] = make_float4(b3[0], b3[1], 0.f, 0.f);
+  // b2 row n: [0 x 12, b2_hi, b2_lo, 0, 0]
+  for (int i = tid; i < H1 * 16; i += stride) {
+    const int n = i / 16, q = i % 16;
+    float v = 0.f;
+    if (q == 12) v = bf16_val(b2[n]);
+    if (q == 13) v = bf16_val(b2[n] - bf16_val(b2[n]));
+    *(uint16_t *)(packed + C::PK_BB + k16_off(n, q)) = bf16_bits(v);
+  }
+  if (tid == 0) *(float4 *)(packed + C::PK_B3V) = make_float4(b3[0], b3[1], 0.f, 0.f);
+}
+
+// Eight 16-byte chunks of one operand row (64 bf16) into a 128B-swizzled slot.
+__device__ __forceinline__ void store_row_sw128(uint32_t row_addr, uint32_t swz,
+                                                const uint32_t (&p)[32]) {
+#pragma unroll
+  for (int ch = 0; ch < 8; ++ch)
+    tc::sts128(row_addr + (((uint32_t)ch ^ swz) << 4), p[ch * 4 + 0], p[ch * 4 + 1], p[ch * 4 + 2],
+               p[ch * 4 + 3]);
+}
+
+// tanh of 64 accumulator columns, packed bf16x2.
+__device__ __forceinline__ void tanh_block64(uint32_t taddr, uint32_t (&hp)[32]) {
+  uint32_t z0[32], z1[32];
+  tc::tmem_ld32(taddr, z0);
+  tc::tmem_ld32(taddr + 32, z1);
+  tc::tmem_wait_ld();
+#pragma unroll
+  for (int i = 0; i < 16; ++i)
+    hp[i] = tc::tanh_bf16x2(tc::pack_bf16x2(__uint_as_float(z0[2 * i]), __uint_as_float(z0[2 * i + 1])));
+#pragma unroll
+  for (int i = 0; i < 16; ++i)
+    hp[16 + i] =
+        tc::tanh_bf16x2(tc::pack_bf16x2(__uint_as_float(z1[2 * i]), __uint_as_float(z1[2 * i + 1])));
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
 }
 
 template <int H0, int H1>
@@ -113,17 +193,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t *bar_l1 = bars, *bar_slot = bars + 1, *bar_drain = bars + 3;
   uint32_t *tm_holder = (uint32_t *)(sm + C::OFF_TM);
 
-  // Stage the packed weights (W2^T, layer-1 B, epilogue table) into smem.
+  // Stage the packed operands into shared memory.
   {
-    const uint4 *src = (const uint4 *)packed;
-    uint4 *w2 = (uint4 *)(sm + C::OFF_W2);
-    for (int i = tid; i < C::W2_BYTES / 16; i += kThreads) w2[i] = __ldg(src + i);
-    src += C::W2_BYTES / 16;
-    uint4 *b1 = (uint4 *)(sm + C::OFF_B1);
-    for (int i = tid; i < C::B1_BYTES / 16; i += kThreads) b1[i] = __ldg(src + i);
-    src += C::B1_BYTES / 16;
-    uint4 *ep = (uint4 *)(sm + C::OFF_EP);
-    for (int i = tid; i < C::EP_BYTES / 16; i += kThreads) ep[i] = __ldg(src + i);
+    const uint4 *src = (const uint4 *)(packed + C::PK_W2);
+    uint4 *dst = (uint4 *)(sm + C::OFF_W2);  // W2 then B3, contiguous in both
+    for (int i = tid; i < (C::W2_BYTES + C::B3_BYTES) / 16; i += kThreads) dst[i] = __ldg(src + i);
+    src = (const uint4 *)(packed + C::PK_B1);
+    dst = (uint4 *)(sm + C::OFF_B1);  // B1 then BB, contiguous in both
+    for (int i = tid; i < (C::B1_BYTES + C::BB_BYTES) / 16; i += kThreads) dst[i] = __ldg(src + i);
+    if (tid == 0) *(uint4 *)(sm + C::OFF_B3V) = __ldg((const uint4 *)(packed + C::PK_B3V));
   }
   if (tid == 0) {
     uint64_t *all = (uint64_t *)(sm + C::OFF_BAR);
@@ -143,10 +221,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t a2 = sb + C::OFF_A2 + wg * 2 * C::SLOT;
   const uint64_t desc_a1 = tc::smem_desc(a1, 128, 256, tc::kSwizzleNone);
   const uint64_t desc_b1 = tc::smem_desc(sb + C::OFF_B1, 128, 256, tc::kSwizzleNone);
+  const uint64_t desc_bb = tc::smem_desc(sb + C::OFF_BB, 128, 256, tc::kSwizzleNone);
   constexpr uint32_t idesc1 = tc::idesc_bf16_f32(128, H0);
   constexpr uint32_t idesc2 = tc::idesc_bf16_f32(128, H1);
-  const float4 *ep = (const float4 *)(sm + C::OFF_EP);
-  const float4 b3 = ep[H1];
+  constexpr uint32_t idesc3 = tc::idesc_bf16_f32(128, 16);
+  const float4 b3 = *(const float4 *)(sm + C::OFF_B3V);
   const uint32_t a1_row = a1 + (uint32_t)(r >> 3) * 256u + (uint32_t)(r & 7) * 16u;
   const uint32_t swz = (uint32_t)(r & 7);
 
@@ -159,6 +238,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t N = d.n_envs, S = d.n_slots;
   const int n_tiles = (int)((N + kTile - 1) / kTile);
   const int n_workers = (int)gridDim.x * kWG;
+
+  // Wait for the next completion on slot s (every commit is waited exactly once).
+#define WS_WAIT_SLOT(s, site)                                                   \
+  {                                                                             \
+    uint32_t &ph_ = (s) ? ph_s1 : ph_s0;                                        \
+    ok = tc::wg_all(bar_id, tc::mbar_wait(bar_slot + (s), ph_, kWaitNs));       \
+    ph_ ^= 1u;                                                                  \
+    if (!ok) {                                                                  \
+      fail_site = (site);                                                       \
+      break;                                                                    \
+    }                                                                           \
+  }
 
   for (int tile = (int)blockIdx.x * kWG + wg; ok && tile < n_tiles; tile += n_workers) {
     const uint32_t e = (uint32_t)tile * kTile + (uint32_t)r;
@@ -195,30 +286,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       ph_l1 ^= 1u;
       if (!ok) { fail_site = 1; break; }
       tc::fence_after_sync();
-      // ---- act 1: h1 = tanh(z1) in packed bf16x2.  K-blocks 0 and 1 go straight
-      // into their (free) slots; later K-blocks wait in registers until z1 has
-      // been read completely (layer 2 accumulates into the same columns).
+      // ---- act 1.  K-blocks 0 and 1 go straight into their (free) slots; later
+      // K-blocks wait in registers until z1 has been read completely.
       constexpr int KH = C::KB > 2 ? C::KB - 2 : 1;
       uint32_t hold[KH][32];
 #pragma unroll
       for (int kb = 0; kb < C::KB; ++kb) {
         uint32_t hp[32];
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          uint32_t z[32];
-          tc::tmem_ld32(tmem + lane + (uint32_t)(kb * 64 + half * 32), z);
-          tc::tmem_wait_ld();
-#pragma unroll
-          for (int i = 0; i < 16; ++i)
-            hp[half * 16 + i] = tc::tanh_bf16x2(
-                tc::pack_bf16x2(__uint_as_float(z[2 * i]), __uint_as_float(z[2 * i + 1])));
-        }
+        tanh_block64(tmem + lane + (uint32_t)(kb * 64), hp);
         if (kb < 2) {
-          const uint32_t rowa = a2 + (uint32_t)kb * C::SLOT + (uint32_t)r * 128u;
-#pragma unroll
-          for (int ch = 0; ch < 8; ++ch)
-            tc::sts128(rowa + (((uint32_t)ch ^ swz) << 4), hp[ch * 4 + 0], hp[ch * 4 + 1],
-                       hp[ch * 4 + 2], hp[ch * 4 + 3]);
+          store_row_sw128(a2 + (uint32_t)kb * C::SLOT + (uint32_t)r * 128u, swz, hp);
         } else {
 #pragma unroll
           for (int i = 0; i < 32; ++i) hold[kb - 2][i] = hp[i];
@@ -227,71 +304,69 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::fence_async_smem();
       tc::fence_before_sync();
       tc::wg_sync(bar_id);  // every lane has read z1 and written K-blocks 0, 1
-      // ---- layer 2, one K-block of 64 at a time through the two slots
+      // ---- layer 2: bias MMA, then one K-block of 64 at a time through the slots
 #pragma unroll
       for (int kb = 0; kb < C::KB; ++kb) {
         const int s = kb & 1;
         const uint32_t slot = a2 + (uint32_t)s * C::SLOT;
         if (kb >= 2) {
-          uint32_t &ph = s ? ph_s1 : ph_s0;
-          ok = tc::wg_all(bar_id, tc::mbar_wait(bar_slot + s, ph, kWaitNs));
-          ph ^= 1u;
-          if (!ok) { fail_site = 2; break; }
-          const uint32_t rowa = slot + (uint32_t)r * 128u;
-#pragma unroll
-          for (int ch = 0; ch < 8; ++ch)
-            tc::sts128(rowa + (((uint32_t)ch ^ swz) << 4), hold[kb - 2][ch * 4 + 0],
-                       hold[kb - 2][ch * 4 + 1], hold[kb - 2][ch * 4 + 2], hold[kb - 2][ch * 4 + 3]);
+          WS_WAIT_SLOT(s, 2);
+          store_row_sw128(slot + (uint32_t)r * 128u, swz, hold[kb - 2]);
           tc::fence_async_smem();
           tc::wg_sync(bar_id);
         }
         if (r == 0) {
           tc::fence_after_sync();
+          if (kb == 0) tc::mma_bf16(tmem, desc_a1, desc_bb, idesc2, false);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             const uint64_t da = tc::smem_desc(slot + kk * 32, 16, 1024, tc::kSwizzle128B);
             const uint64_t db = tc::smem_desc(sb + C::OFF_W2 + kb * (H1 * 128) + kk * 32, 16, 1024,
                                               tc::kSwizzle128B);
-            tc::mma_bf16(tmem, da, db, idesc2, (kb | kk) != 0);
+            tc::mma_bf16(tmem, da, db, idesc2, true);
           }
           tc::mma_commit(bar_slot + s);
         }
       }
       if (!ok) break;
-      // drain both slots (the last commit covers every MMA of this step)
-      if (C::KB >= 2) {
-        const int s = (C::KB - 2) & 1;
-        uint32_t &ph = s ? ph_s1 : ph_s0;
-        ok = tc::wg_all(bar_id, tc::mbar_wait(bar_slot + s, ph, kWaitNs));
-        ph ^= 1u;
-        if (!ok) { fail_site = 3; break; }
-      }
-      {
-        const int s = (C::KB - 1) & 1;
-        uint32_t &ph = s ? ph_s1 : ph_s0;
-        ok = tc::wg_all(bar_id, tc::mbar_wait(bar_slot + s, ph, kWaitNs));
-        ph ^= 1u;
-        if (!ok) { fail_site = 4; break; }
-      }
+      if (C::KB >= 2) WS_WAIT_SLOT((C::KB - 2) & 1, 3);
+      WS_WAIT_SLOT((C::KB - 1) & 1, 4);
       tc::fence_after_sync();
-      // ---- act 2 and layer 3: logits = tanh(z2 + b2) W3 + b3
-      float l0 = b3.x, l1 = b3.y;
+      // ---- act 2 + layer 3, one K-block of h2 at a time through the slots
 #pragma unroll
-      for (int c0 = 0; c0 < H1; c0 += 32) {
-        uint32_t z[32];
-        tc::tmem_ld32(tmem + lane + (uint32_t)c0, z);
-        tc::tmem_wait_ld();
+      for (int kb = 0; kb < C::KB3; ++kb) {
+        const int s = kb & 1;
+        const uint32_t slot = a2 + (uint32_t)s * C::SLOT;
+        uint32_t hp[32];
+        tanh_block64(tmem + lane + (uint32_t)(kb * 64), hp);
+        if (kb >= 2) WS_WAIT_SLOT(s, 5);
+        store_row_sw128(slot + (uint32_t)r * 128u, swz, hp);
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        tc::wg_sync(bar_id);  // lanes have read columns kb*64.. (and 0..15 at kb = 0)
+        if (r == 0) {
+          tc::fence_after_sync();
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const float4 p = ep[c0 + 2 * i], q = ep[c0 + 2 * i + 1];
-          const uint32_t hh = tc::tanh_bf16x2(
-              tc::pack_bf16x2(__uint_as_float(z[2 * i]) + p.x, __uint_as_float(z[2 * i + 1]) + q.x));
-          const float ha = tc::bf16_lo(hh), hb = tc::bf16_hi(hh);
-          l0 = fmaf(ha, p.y, l0);
-          l1 = fmaf(ha, p.z, l1);
-          l0 = fmaf(hb, q.y, l0);
-          l1 = fmaf(hb, q.z, l1);
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t da = tc::smem_desc(slot + kk * 32, 16, 1024, tc::kSwizzle128B);
+            const uint64_t db = tc::smem_desc(sb + C::OFF_B3 + kb * (16 * 128) + kk * 32, 16, 1024,
+                                              tc::kSwizzle128B);
+            tc::mma_bf16(tmem, da, db, idesc3, (kb | kk) != 0);
+          }
+          tc::mma_commit(bar_slot + s);
         }
+      }
+      if (!ok) break;
+      if (C::KB3 >= 2) WS_WAIT_SLOT((C::KB3 - 2) & 1, 6);
+      WS_WAIT_SLOT((C::KB3 - 1) & 1, 7);
+      tc::fence_after_sync();
+      float l0, l1;
+      {
+        uint32_t o[16];
+        tmem_ld16(tmem + lane, o);
+        tc::tmem_wait_ld();
+        l0 = (__uint_as_float(o[0]) + __uint_as_float(o[2])) + b3.x;
+        l1 = (__uint_as_float(o[1]) + __uint_as_float(o[3])) + b3.y;
       }
       // ---- sample: a = 0 iff u S < exp(l0 - m)
       const float u = u01(draw(d.seed, k, e, 0, kTagAction, 0).x);
@@ -335,6 +410,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tep = t2;
       }
       row = (row + 1 == R) ? 0 : row + 1;
+      tc::fence_before_sync();  // the TMEM read above precedes the next layer-1 MMA
     }
     if (valid) {
       d.s[e] = x;
@@ -344,6 +420,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       d.t[e] = tep;
     }
   }
+#undef WS_WAIT_SLOT
   if (!ok) {
     if (r == 0) {
       // let any MMA still in flight finish before the columns are released
@@ -363,6 +440,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 template <int H0, int H1>
 struct Shape {
+  static constexpr size_t packed_bytes = CtrlTc<H0, H1>::PACKED;
   static void pack(const Dev &d, void *packed, cudaStream_t st) {
     k_ctrl_tc_pack<H0, H1><<<64, 256, 0, st>>>(d.params, (uint8_t *)packed);
   }
@@ -389,13 +467,7 @@ bool dispatch(const PolicyShape &sh, F &&f) {
 
 size_t control_tc_packed_bytes(const PolicyShape &sh) {
   size_t n = 0;
-  dispatch(sh, [&](auto s) {
-    using S = decltype(s);
-    (void)sizeof(S);
-    if (sh.w[1] == 256) n = CtrlTc<256, 256>::PACKED;
-    if (sh.w[1] == 128) n = CtrlTc<128, 128>::PACKED;
-    if (sh.w[1] == 64) n = CtrlTc<64, 64>::PACKED;
-  });
+  dispatch(sh, [&](auto s) { n = decltype(s)::packed_bytes; });
   return n;
 }
 
