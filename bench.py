@@ -307,6 +307,69 @@ def run_gpu(args, wl, world, rank, local):
     return path, value, main, plain, e2e
 
 
+def run_serving(args, world, rank, local):
+    """Serving mix: Poisson arrivals (200 req/s) of requests across the three env
+    types, admitted under a 150 GB budget, delivered in chunks of 50 steps."""
+    import torch
+    from paper_2408_00930_gb300 import serving_mix
+    from paper_2408_00930_gb300 import warpsci as W
+    torch.cuda.set_device(local)
+    budget = int(args.serve_budget_gb * (1 << 30))
+    stream = list(serving_mix.request_stream(1234 + rank, args.serve_requests, rate=200.0))
+    out = {}
+    for label, bf16 in (("served", True), ("plain_fp32", False)):
+        if not bf16 and args.no_plain:
+            continue
+        srv = W.Server(budget)
+        t0 = time.perf_counter()
+        keep = []
+        rejected = 0
+        for r in stream:
+            dt = r["t_arrival"] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            if bf16:
+                path = W.WS_PATH_BATCHED_BF16 if r["env"] == 0 else W.WS_PATH_BATCHED_FP32
+            else:
+                path = W.WS_PATH_PLAIN_FP32
+            q, k = W.make_request(r["env"], path, r["n_envs"], r["horizon"], CHUNK,
+                                  r["episode_limit"], *r["hidden"], dim=r["dim"],
+                                  n_gauss=r["n_gauss"], seed=r["seed"],
+                                  flags=W.WS_REQ_CONSUME_ON_READY)
+            keep.append(k)
+            st, _ = srv.submit(q)
+            if st != W.WS_OK:
+                rejected += 1
+        while True:
+            s_ = srv.stats()
+            if s_["completed"] + s_["rejected"] + s_["failed"] >= len(stream):
+                break
+            if time.perf_counter() - t0 > args.serve_timeout_s:
+                break
+            time.sleep(0.005)
+        wall = time.perf_counter() - t0
+        s_ = srv.stats()
+        srv.close()
+        out[label] = {"value": s_["agent_steps"] / wall, "unit": "agent-steps/s",
+                      "p50_ms": s_["p50_ms"], "p99_ms": s_["p99_ms"], "wall_s": wall,
+                      "requests": len(stream), "rejected": rejected, "failed": s_["failed"],
+                      "completed": s_["completed"], "chunks": s_["chunks"],
+                      "peak_bytes": s_["peak_bytes"], "agent_steps": s_["agent_steps"]}
+    if rank == 0:
+        sv = out["served"]
+        print(json.dumps({
+            "metric": METRIC, "value": sv["value"], "unit": "agent-steps/s", "n_gpus": world,
+            "steps": args.serve_requests, "warmup": 0, "ms_per_step": sv["wall_s"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic",
+            "config": {"workload": "serving mix: Poisson 200 req/s across control / economy / "
+                                   "landscape, 256-65,536 envs, horizons 100-1,000, chunks of 50, "
+                                   f"{args.serve_budget_gb:g} GB admission budget",
+                       "paths": "control BF16 tensor-core; economy and landscape batched FP32"},
+            "latency": {"chunk_steps": CHUNK, "p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"]},
+            "serving": out}), flush=True)
+
+
 def _param_bytes(wl):
     if wl["env"] == 0:
         w = [4, *wl["h"], 2]
@@ -326,14 +389,21 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="control_scale", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="control_scale", choices=sorted(WORKLOADS) + ["serving"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--horizon", type=int, default=0,
                     help="override the horizon (smaller cases for profiling captures)")
     ap.add_argument("--n-envs", type=int, default=0, help="override the env count")
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0)
+    ap.add_argument("--serve-timeout-s", type=float, default=600.0)
     args = ap.parse_args()
+    if args.workload == "serving":
+        world, rank, local = dist_init()
+        run_serving(args, world, rank, local)
+        return
     wl = dict(WORKLOADS[args.workload])
     if args.horizon:
         wl["horizon"] = args.horizon

@@ -186,6 +186,77 @@ const char *ws_last_error(const ws_ctx *ctx);
  * Waits for the context's outstanding work first. */
 void ws_destroy(ws_ctx *ctx);
 
+/* ------------------------------------------------------------------------
+ * Serving: a request loop with continuous batching over roll-out contexts.
+ * Clients (trainers) submit roll-out requests of any env type and size.  A
+ * request is admitted as soon as its device bytes (env state, parameters,
+ * scratch and a trajectory ring of two chunks) fit in the server's budget;
+ * it then keeps its env state resident on the device and advances one chunk
+ * of chunk_steps steps at a time on a stream of its own, concurrently with the
+ * other admitted requests.  A finished or released request frees its bytes.
+ * All functions are thread-safe; ws_server_wait_chunk and ws_server_fetch
+ * (host destination) block the calling thread only.
+ * ------------------------------------------------------------------------ */
+typedef struct ws_server ws_server;
+
+#define WS_REQ_CONSUME_ON_READY 1u /* chunks need no ack; ring rows are reused at once
+                                      and the request is released when done      */
+
+typedef struct {
+  uint32_t struct_size;   /* = sizeof(ws_request)                           */
+  int32_t env, path;      /* ws_env, ws_path                                */
+  uint32_t n_envs;
+  uint32_t horizon;       /* total steps of the request                     */
+  uint32_t chunk_steps;   /* steps per delivered chunk (>= 1)               */
+  uint32_t episode_limit;
+  uint32_t hidden0, hidden1, dim, n_gauss;
+  uint32_t flags;         /* WS_REQ_* bits                                  */
+  uint64_t seed;          /* parameter and roll-out key                     */
+  const int32_t *agents_per_env; /* economy, host, copied; NULL = drawn     */
+} ws_request;
+
+typedef struct {
+  uint32_t struct_size;   /* = sizeof(ws_server_stats), set by the caller   */
+  uint64_t submitted, admitted, completed, rejected, failed, chunks;
+  double agent_steps;     /* agent-steps of all delivered chunks            */
+  double elapsed_s;       /* first submission to last delivered chunk       */
+  double p50_ms, p99_ms;  /* chunk latency: chunk k ready - chunk k-1 ready
+                             (chunk 0: from submission)                     */
+  size_t used_bytes, peak_bytes, budget_bytes;
+  uint32_t active, pending;
+} ws_server_stats;
+
+/* Create a server owning one device arena of budget_bytes (cudaMalloc on the
+ * current device) and its scheduler thread.  WS_ERR_NOMEM if the arena cannot
+ * be allocated. */
+ws_status ws_server_create(size_t budget_bytes, ws_server **out);
+
+/* Queue a request; *id names it.  WS_ERR_NOMEM if it can never fit the
+ * budget, WS_ERR_INVALID / WS_ERR_UNSUPPORTED for a bad configuration. */
+ws_status ws_server_submit(ws_server *s, const ws_request *req, uint64_t *id);
+
+/* Block until chunk `chunk` of request id is ready, or WS_ERR_TIMEOUT after
+ * timeout_ms (0 = no limit).  A failed request returns its error. */
+ws_status ws_server_wait_chunk(ws_server *s, uint64_t id, uint32_t chunk, uint32_t timeout_ms);
+
+/* Copy a ring field (ws_fetch layouts) of a ready, not yet acknowledged chunk
+ * into dst (device or host memory); returns when the copy is complete. */
+ws_status ws_server_fetch(ws_server *s, uint64_t id, ws_field field, uint32_t chunk, void *dst,
+                          size_t dst_bytes, int dst_on_device);
+
+/* Acknowledge chunks up to and including `chunk`: their ring rows may be
+ * reused.  Without WS_REQ_CONSUME_ON_READY at most two chunks run ahead of
+ * the last acknowledgement. */
+ws_status ws_server_ack(ws_server *s, uint64_t id, uint32_t chunk);
+
+/* Cancel (if running) and forget a request, freeing its bytes. */
+ws_status ws_server_release(ws_server *s, uint64_t id);
+
+ws_status ws_server_get_stats(ws_server *s, ws_server_stats *out);
+
+/* Stop the scheduler, release every request and free the arena. */
+void ws_server_destroy(ws_server *s);
+
 /* Policy forward pass that allocates no device memory (the paper has no
  * counterpart; it is a service for callers that cannot call cudaMalloc, such
  * as code running during CUDA-graph capture, hosts whose allocator forbids

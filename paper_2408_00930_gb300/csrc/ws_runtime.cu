@@ -508,8 +508,12 @@ ws_status ws_returns(ws_ctx *c, uint32_t n) {
   return cuda_check(c, cudaGetLastError(), "returns");
 }
 
-ws_status ws_fetch(ws_ctx *c, ws_field f, uint64_t t0, uint32_t n, void *dst, size_t dst_bytes,
-                   int on_dev) {
+}  // extern "C"
+
+// Fetch on an explicit stream, without waiting (the copy is ordered after the
+// work already enqueued on that stream only).
+ws_status ws_fetch_async(ws_ctx *c, ws_field f, uint64_t t0, uint32_t n, void *dst,
+                         size_t dst_bytes, int on_dev, cudaStream_t st) {
   if (!c || (!dst && dst_bytes)) return WS_ERR_INVALID;
   if (c->err != WS_OK) return c->err;
   const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -523,33 +527,43 @@ ws_status ws_fetch(ws_ctx *c, ws_field f, uint64_t t0, uint32_t n, void *dst, si
     if (dst_bytes < tot) return WS_ERR_NOMEM;
     char *o = (char *)dst;
     for (auto &p : v) {
-      ws_status s = cuda_check(c, cudaMemcpyAsync(o, p.p, p.n, kind, c->stream), "fetch copy");
+      ws_status s = cuda_check(c, cudaMemcpyAsync(o, p.p, p.n, kind, st), "fetch copy");
       if (s != WS_OK) return s;
       o += p.n;
     }
-  } else {
-    size_t foff = 0;
-    const size_t per = ring_field_step_bytes(c, f, &foff);
-    if (per == 0) return WS_ERR_INVALID;
-    if (n == 0) return WS_OK;
-    const uint64_t R = c->L.ring_steps;
-    const uint64_t lo = c->k_host > R ? c->k_host - R : 0;
-    if (t0 < lo || t0 + n > c->k_host) return WS_ERR_RANGE;
-    if (dst_bytes < per * n) return WS_ERR_NOMEM;
-    char *o = (char *)dst;
-    uint64_t t = t0;
-    uint32_t left = n;
-    while (left) {
-      const uint64_t row = t % R;
-      const uint32_t run = (uint32_t)((R - row) < left ? (R - row) : left);
-      ws_status s = cuda_check(
-          c, cudaMemcpyAsync(o, c->ring + foff + row * per, per * run, kind, c->stream), "fetch copy");
-      if (s != WS_OK) return s;
-      o += per * run;
-      t += run;
-      left -= run;
-    }
+    return WS_OK;
   }
+  size_t foff = 0;
+  const size_t per = ring_field_step_bytes(c, f, &foff);
+  if (per == 0) return WS_ERR_INVALID;
+  if (n == 0) return WS_OK;
+  const uint64_t R = c->L.ring_steps;
+  const uint64_t lo = c->k_host > R ? c->k_host - R : 0;
+  if (t0 < lo || t0 + n > c->k_host) return WS_ERR_RANGE;
+  if (dst_bytes < per * n) return WS_ERR_NOMEM;
+  char *o = (char *)dst;
+  uint64_t t = t0;
+  uint32_t left = n;
+  while (left) {
+    const uint64_t row = t % R;
+    const uint32_t run = (uint32_t)((R - row) < left ? (R - row) : left);
+    ws_status s = cuda_check(
+        c, cudaMemcpyAsync(o, c->ring + foff + row * per, per * run, kind, st), "fetch copy");
+    if (s != WS_OK) return s;
+    o += per * run;
+    t += run;
+    left -= run;
+  }
+  return WS_OK;
+}
+
+extern "C" {
+
+ws_status ws_fetch(ws_ctx *c, ws_field f, uint64_t t0, uint32_t n, void *dst, size_t dst_bytes,
+                   int on_dev) {
+  if (!c) return WS_ERR_INVALID;
+  ws_status s = ws_fetch_async(c, f, t0, n, dst, dst_bytes, on_dev, c->stream);
+  if (s != WS_OK) return s;
   if (!on_dev) return cuda_check(c, cudaStreamSynchronize(c->stream), "fetch sync");
   return WS_OK;
 }

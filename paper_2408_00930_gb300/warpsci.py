@@ -28,7 +28,10 @@ WS_PATH_PLAIN_FP32, WS_PATH_BATCHED_FP32, WS_PATH_BATCHED_BF16 = 0, 1, 2
 
 EXPORTED = ["ws_query_bytes", "ws_create", "ws_reset", "ws_step", "ws_rollout", "ws_returns",
             "ws_fetch", "ws_load", "ws_get_step", "ws_sync", "ws_last_error", "ws_destroy",
-            "ws_policy_forward_noalloc"]
+            "ws_policy_forward_noalloc", "ws_server_create", "ws_server_submit",
+            "ws_server_wait_chunk", "ws_server_fetch", "ws_server_ack", "ws_server_release",
+            "ws_server_get_stats", "ws_server_destroy"]
+WS_REQ_CONSUME_ON_READY = 1
 
 
 class ws_config(C.Structure):
@@ -39,6 +42,23 @@ class ws_config(C.Structure):
                 ("n_gauss", C.c_uint32), ("noise_sigma", C.c_float), ("step_clip", C.c_float),
                 ("gamma", C.c_float), ("flags", C.c_uint32), ("param_seed", C.c_uint64),
                 ("agents_per_env", C.POINTER(C.c_int32))]
+
+
+class ws_request(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("env", C.c_int32), ("path", C.c_int32),
+                ("n_envs", C.c_uint32), ("horizon", C.c_uint32), ("chunk_steps", C.c_uint32),
+                ("episode_limit", C.c_uint32), ("hidden0", C.c_uint32), ("hidden1", C.c_uint32),
+                ("dim", C.c_uint32), ("n_gauss", C.c_uint32), ("flags", C.c_uint32),
+                ("seed", C.c_uint64), ("agents_per_env", C.POINTER(C.c_int32))]
+
+
+class ws_server_stats(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("submitted", C.c_uint64), ("admitted", C.c_uint64),
+                ("completed", C.c_uint64), ("rejected", C.c_uint64), ("failed", C.c_uint64),
+                ("chunks", C.c_uint64),
+                ("agent_steps", C.c_double), ("elapsed_s", C.c_double), ("p50_ms", C.c_double),
+                ("p99_ms", C.c_double), ("used_bytes", C.c_size_t), ("peak_bytes", C.c_size_t),
+                ("budget_bytes", C.c_size_t), ("active", C.c_uint32), ("pending", C.c_uint32)]
 
 
 class WarpSciError(RuntimeError):
@@ -77,8 +97,17 @@ def lib():
         L.ws_destroy.restype = None
         L.ws_policy_forward_noalloc.argtypes = [P, C.c_uint32, P, C.c_uint32, C.c_uint32,
                                                 C.c_uint32, C.c_uint32, P, P]
+        L.ws_server_create.argtypes = [C.c_size_t, C.POINTER(P)]
+        L.ws_server_submit.argtypes = [P, C.POINTER(ws_request), C.POINTER(C.c_uint64)]
+        L.ws_server_wait_chunk.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint32]
+        L.ws_server_fetch.argtypes = [P, C.c_uint64, C.c_int, C.c_uint32, P, C.c_size_t, C.c_int]
+        L.ws_server_ack.argtypes = [P, C.c_uint64, C.c_uint32]
+        L.ws_server_release.argtypes = [P, C.c_uint64]
+        L.ws_server_get_stats.argtypes = [P, C.POINTER(ws_server_stats)]
+        L.ws_server_destroy.argtypes = [P]
+        L.ws_server_destroy.restype = None
         for n in EXPORTED:
-            if n not in ("ws_last_error", "ws_destroy"):
+            if n not in ("ws_last_error", "ws_destroy", "ws_server_destroy"):
                 getattr(L, n).restype = C.c_int
         _lib = L
     return _lib
@@ -261,6 +290,68 @@ class Rollout:
         if getattr(self, "ctx", None):
             ws_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --- serving --------------------------------------------------------------------
+def make_request(env, path, n_envs, horizon, chunk_steps, episode_limit, hidden0, hidden1, *,
+                 dim=0, n_gauss=0, seed=1, flags=0, agents_per_env=None):
+    q = ws_request()
+    q.struct_size = C.sizeof(ws_request)
+    q.env, q.path, q.n_envs, q.horizon, q.chunk_steps = env, path, n_envs, horizon, chunk_steps
+    q.episode_limit, q.hidden0, q.hidden1, q.dim, q.n_gauss = episode_limit, hidden0, hidden1, dim, n_gauss
+    q.flags, q.seed = flags, seed
+    keep = None
+    if agents_per_env is not None:
+        keep = np.ascontiguousarray(agents_per_env, dtype=np.int32)
+        q.agents_per_env = keep.ctypes.data_as(C.POINTER(C.c_int32))
+    return q, keep
+
+
+class Server:
+    """Owner of a ws_server (device arena of budget_bytes on the current device)."""
+
+    def __init__(self, budget_bytes):
+        out = C.c_void_p()
+        st = lib().ws_server_create(budget_bytes, C.byref(out))
+        if st != WS_OK:
+            raise WarpSciError(st, "ws_server_create")
+        self.s = out.value
+
+    def submit(self, q):
+        rid = C.c_uint64()
+        st = lib().ws_server_submit(self.s, C.byref(q), C.byref(rid))
+        return st, rid.value
+
+    def wait_chunk(self, rid, chunk, timeout_ms=0):
+        return lib().ws_server_wait_chunk(self.s, rid, chunk, timeout_ms)
+
+    def fetch(self, rid, field, chunk, out):
+        return lib().ws_server_fetch(self.s, rid, field, chunk, out.ctypes.data, out.nbytes, 0)
+
+    def ack(self, rid, chunk):
+        return lib().ws_server_ack(self.s, rid, chunk)
+
+    def release(self, rid):
+        return lib().ws_server_release(self.s, rid)
+
+    def stats(self):
+        st = ws_server_stats()
+        st.struct_size = C.sizeof(ws_server_stats)
+        rc = lib().ws_server_get_stats(self.s, C.byref(st))
+        if rc != WS_OK:
+            raise WarpSciError(rc, "ws_server_get_stats")
+        return {f: getattr(st, f) for f, _ in ws_server_stats._fields_ if f != "struct_size"}
+
+    def close(self):
+        if getattr(self, "s", None):
+            lib().ws_server_destroy(self.s)
+            self.s = None
 
     def __del__(self):
         try:

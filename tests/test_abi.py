@@ -32,25 +32,27 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(names) == set(W.EXPORTED) | set(n for n in names if n not in W.EXPORTED)
 
 
-def test_struct_layout_matches_header(lib, tmp_path):
-    """The ctypes mirror of ws_config has the C compiler's size and offsets."""
+@pytest.mark.parametrize("struct", ["ws_config", "ws_request", "ws_server_stats"])
+def test_struct_layout_matches_header(lib, tmp_path, struct):
+    """Each ctypes mirror has the C compiler's size and field offsets."""
     import shutil
     import subprocess
     if shutil.which("gcc") is None:
         pytest.skip("gcc not available")
-    fields = [f for f, _ in W.ws_config._fields_]
+    cls = getattr(W, struct)
+    fields = [f for f, _ in cls._fields_]
     src = tmp_path / "layout.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "warpsci.h"\nint main(void){\n'
-                   'printf("%zu\\n", sizeof(ws_config));\n' +
-                   "".join(f'printf("%zu\\n", offsetof(ws_config, {f}));\n' for f in fields) +
+                   f'printf("%zu\\n", sizeof({struct}));\n' +
+                   "".join(f'printf("%zu\\n", offsetof({struct}, {f}));\n' for f in fields) +
                    "return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
                                             check=True).stdout.split()]
-    assert vals[0] == C.sizeof(W.ws_config)
+    assert vals[0] == C.sizeof(cls)
     for f, off in zip(fields, vals[1:]):
-        assert getattr(W.ws_config, f).offset == off, f
+        assert getattr(cls, f).offset == off, f
 
 
 def test_query_bytes_validation(lib):
