@@ -33,6 +33,9 @@ struct Dev {
   int64_t *income;      // economy [n_agent_slots]
   float *epart;         // landscape energy partial sums [kEnergyChunks][2][n]
   uint8_t *needs_energy;  // landscape [n]
+  // BF16 tensor-core policy layers (economy / landscape): packed W^T images
+  int tc_mlp;
+  const uint8_t *pk[2][3];  // [agent, planner][layer]
   // ring
   float *r_obs;
   void *r_act;
@@ -70,6 +73,16 @@ int control_tc_default_grid(const Dev &d);
 }  // namespace ws
 
 namespace ws {
+// ---- BF16 tensor-core dense layer (ws_dense_tc.cu) ----------------------------
+size_t dense_tc_packed_bytes(int K, int N);
+bool dense_tc_supported(int K, int N);
+void launch_dense_tc_pack(const float *W, const float *b, int K, int N, void *packed,
+                          cudaStream_t st);
+cudaError_t launch_dense_tc(const void *X, long ldr, long ldc, int x_bf16, int K,
+                            const void *packed, int N, void *Y, int y_bf16, int act, long M,
+                            uint32_t *err, cudaStream_t st);
+void dense_tc_init();
+
 // Y[M][N] = act(X W + b) with the plain path's FP32 dense kernel (X row-major
 // when ldc == 1, or addressed X[r * ldr + c * ldc]).
 void launch_dense_fp32(const float *X, long ldr, long ldc, const float *W, const float *b, float *Y,

@@ -221,6 +221,23 @@ void mlp3(const float *X, long ldr, long ldc, const float *params, const PolicyS
   dense(h1, sh.w[2], 1, W2, W2 + (size_t)sh.w[2] * sh.w[3], out, M, sh.w[2], sh.w[3], 0, st);
 }
 
+// BF16 tensor-core variant: hidden activations in BF16 row-major, logits FP32.
+void tc_mlp3(const Dev &d, const float *X, long ldr, long ldc, const PolicyShape &sh, int pid,
+             void *h0, void *h1, float *out, long M, cudaStream_t st) {
+  launch_dense_tc(X, ldr, ldc, 0, sh.w[0], d.pk[pid][0], sh.w[1], h0, 1, 1, M, d.err, st);
+  launch_dense_tc(h0, 0, 0, 1, sh.w[1], d.pk[pid][1], sh.w[2], h1, 1, 1, M, d.err, st);
+  launch_dense_tc(h1, 0, 0, 1, sh.w[2], d.pk[pid][2], sh.w[3], out, 0, 0, M, d.err, st);
+}
+
+void policy(const Dev &d, const float *X, long ldr, long ldc, const float *params,
+            const PolicyShape &sh, int pid, float *h0, float *h1, float *out, int M,
+            cudaStream_t st) {
+  if (d.tc_mlp)
+    tc_mlp3(d, X, ldr, ldc, sh, pid, h0, h1, out, M, st);
+  else
+    mlp3(X, ldr, ldc, params, sh, h0, h1, out, M, st);
+}
+
 // ------------------------------------------------- S1/S6 observation store
 // ring.obs[row][j][slot_base + i] = src[j * ld + i]
 __global__ void k_store_obs(Dev d, uint32_t off, const float *src, int dim, uint32_t n, size_t ld,
@@ -653,13 +670,15 @@ void launch_reset(const Dev &d, cudaStream_t st) {
 void launch_plain_step(const Dev &d, uint32_t off, cudaStream_t st) {
   if (d.env == WS_ENV_CONTROL) {
     k_store_obs<<<blocks(d.n_envs, 256), 256, 0, st>>>(d, off, d.s, 4, d.n_envs, d.n_envs, 0);
-    mlp3(d.s, 1, d.n_envs, d.params, d.pol, d.h0, d.h1, d.out, (int)d.n_envs, st);
+    policy(d, d.s, 1, d.n_envs, d.params, d.pol, 0, d.h0, d.h1, d.out, (int)d.n_envs, st);
     k_sample_cat<<<blocks(d.n_envs, 256), 256, 0, st>>>(d, off, d.out, 2, 0, d.n_envs, 0);
     k_control_step<<<blocks(d.n_envs, 256), 256, 0, st>>>(d, off);
   } else if (d.env == WS_ENV_ECONOMY) {
     k_econ_observe<<<d.n_envs, kEconThreads, 0, st>>>(d, off);
-    mlp3(d.feat, 1, d.n_agent_slots, d.params, d.pol, d.h0, d.h1, d.out, (int)d.n_agent_slots, st);
-    mlp3(d.pobs, kEconF, 1, d.params_planner, d.pol_planner, d.ph0, d.ph1, d.pout, (int)d.n_envs, st);
+    policy(d, d.feat, 1, d.n_agent_slots, d.params, d.pol, 0, d.h0, d.h1, d.out,
+           (int)d.n_agent_slots, st);
+    policy(d, d.pobs, kEconF, 1, d.params_planner, d.pol_planner, 1, d.ph0, d.ph1, d.pout,
+           (int)d.n_envs, st);
     k_sample_cat<<<blocks(d.n_agent_slots, 256), 256, 0, st>>>(d, off, d.out, (int)d.n_out, 1,
                                                                 d.n_agent_slots, 0);
     k_sample_cat<<<blocks(d.n_envs, 256), 256, 0, st>>>(d, off, d.pout, (int)d.n_out_planner, 2,
@@ -668,7 +687,7 @@ void launch_plain_step(const Dev &d, uint32_t off, cudaStream_t st) {
     k_econ_finish<<<d.n_envs, kEconThreads, 0, st>>>(d, off);
   } else {
     k_store_obs<<<blocks(d.n_envs, 256), 256, 0, st>>>(d, off, d.s, (int)d.dim, d.n_envs, d.n_envs, 0);
-    mlp3(d.s, 1, d.n_envs, d.params, d.pol, d.h0, d.h1, d.out, (int)d.n_envs, st);
+    policy(d, d.s, 1, d.n_envs, d.params, d.pol, 0, d.h0, d.h1, d.out, (int)d.n_envs, st);
     k_sample_gauss<<<blocks(d.n_envs, 128), 128, 0, st>>>(d, off);
     landscape_energy(d, off, 0, st);
     k_landscape_step<<<blocks(d.n_envs, 256), 256, 0, st>>>(d, off);

@@ -89,6 +89,23 @@ bool use_tc_control(const ws_config *cfg) {
   return cfg->env == WS_ENV_CONTROL && cfg->path == WS_PATH_BATCHED_BF16;
 }
 
+// Economy / landscape on the BF16 path: per-layer tensor-core policy kernels.
+bool use_tc_layers(const ws_config *cfg) {
+  return cfg->env != WS_ENV_CONTROL && cfg->path == WS_PATH_BATCHED_BF16;
+}
+
+bool tc_layers_supported(const PolicyShape &p) {
+  for (int l = 0; l < kMaxLayers; ++l)
+    if (!dense_tc_supported(p.w[l], p.w[l + 1])) return false;
+  return p.w[1] % 8 == 0 && p.w[2] % 8 == 0;
+}
+
+size_t tc_layers_bytes(const PolicyShape &p) {
+  size_t n = 0;
+  for (int l = 0; l < kMaxLayers; ++l) n += up(dense_tc_packed_bytes(p.w[l], p.w[l + 1]));
+  return n;
+}
+
 Layout make_layout(const ws_config *cfg, const std::vector<int32_t> &agents) {
   Layout L{};
   L.env = cfg->env;
@@ -133,6 +150,9 @@ Layout make_layout(const ws_config *cfg, const std::vector<int32_t> &agents) {
   if (cfg->env == WS_ENV_ECONOMY) o += up(L.pol_planner.count() * 4);
   L.packed_off = o;
   L.packed_bytes = use_tc_control(cfg) ? control_tc_packed_bytes(L.pol) : 0;
+  if (use_tc_layers(cfg))
+    L.packed_bytes = tc_layers_bytes(L.pol) +
+                     (cfg->env == WS_ENV_ECONOMY ? tc_layers_bytes(L.pol_planner) : 0);
   o += up(L.packed_bytes);
   L.env_params_off = o;
   if (cfg->env == WS_ENV_LANDSCAPE) o += up(M * D * 4) + up(M * 4) + up(M * 4);
@@ -225,6 +245,17 @@ void make_dev(ws_ctx *c) {
     d.slot_env = (const int32_t *)(S + L.aux_off + up((N + 1) * 4));
   }
   d.t = (int32_t *)(S + L.t_off);
+  if (use_tc_layers(&cfg)) {
+    d.tc_mlp = 1;
+    size_t o = L.packed_off;
+    for (int pid = 0; pid < (cfg.env == WS_ENV_ECONOMY ? 2 : 1); ++pid) {
+      const PolicyShape &p = pid ? L.pol_planner : L.pol;
+      for (int l = 0; l < kMaxLayers; ++l) {
+        d.pk[pid][l] = (const uint8_t *)(S + o);
+        o += up(dense_tc_packed_bytes(p.w[l], p.w[l + 1]));
+      }
+    }
+  }
   if (!use_tc_control(&cfg)) {
     d.h0 = (float *)(S + L.scratch_h0_off);
     d.h1 = (float *)(S + L.scratch_h1_off);
@@ -361,6 +392,17 @@ std::vector<Piece> state_pieces(ws_ctx *c, ws_field f) {
 ws_status after_params_changed(ws_ctx *c) {
   if (c->cfg.env == WS_ENV_LANDSCAPE) launch_landscape_derive(c->d, c->stream);
   if (use_tc_control(&c->cfg)) launch_control_tc_pack(c->d, c->state + c->L.packed_off, c->stream);
+  if (use_tc_layers(&c->cfg)) {
+    for (int pid = 0; pid < (c->cfg.env == WS_ENV_ECONOMY ? 2 : 1); ++pid) {
+      const PolicyShape &p = pid ? c->L.pol_planner : c->L.pol;
+      const float *par = pid ? c->d.params_planner : c->d.params;
+      for (int l = 0; l < kMaxLayers; ++l) {
+        const float *W = par + p.layer_offset(l);
+        launch_dense_tc_pack(W, W + (size_t)p.w[l] * p.w[l + 1], p.w[l], p.w[l + 1],
+                             (void *)c->d.pk[pid][l], c->stream);
+      }
+    }
+  }
   return cuda_check(c, cudaGetLastError(), "param derive");
 }
 
@@ -374,10 +416,12 @@ ws_status ws_query_bytes(const ws_config *cfg, size_t *state_bytes, size_t *ring
   if (s != WS_OK) return s;
   if (use_tc_control(cfg) && !control_tc_supported(PolicyShape{{4, (int)cfg->hidden0, (int)cfg->hidden1, 2}}))
     return WS_ERR_UNSUPPORTED;
-  if (cfg->env != WS_ENV_CONTROL && cfg->path == WS_PATH_BATCHED_BF16) return WS_ERR_UNSUPPORTED;
   std::vector<int32_t> agents;
   agent_counts(cfg, agents);
   const Layout L = make_layout(cfg, agents);
+  if (use_tc_layers(cfg) &&
+      !(tc_layers_supported(L.pol) && (cfg->env != WS_ENV_ECONOMY || tc_layers_supported(L.pol_planner))))
+    return WS_ERR_UNSUPPORTED;
   if (state_bytes) *state_bytes = L.state_bytes;
   if (ring_bytes) *ring_bytes = L.ring_bytes;
   if (n_slots) *n_slots = L.n_slots;
@@ -437,6 +481,7 @@ ws_status ws_create(const ws_config *cfg, void *state_buf, size_t state_bytes, v
     launch_init_policy((float *)c->d.params_planner, c->L.pol_planner, cfg->param_seed, 1, c->stream);
   if (cfg->env == WS_ENV_LANDSCAPE) launch_init_landscape(c->d, cfg->param_seed, c->stream);
   if (use_tc_control(cfg)) c->tc_grid = control_tc_default_grid(c->d);
+  if (use_tc_layers(cfg)) dense_tc_init();
   s = after_params_changed(c);
   if (s == WS_OK) s = ws_reset(c, cfg->param_seed);
   if (s == WS_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream), "create sync");
@@ -519,7 +564,7 @@ ws_status ws_fetch_async(ws_ctx *c, ws_field f, uint64_t t0, uint32_t n, void *d
   const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (f == WS_F_STATE || f == WS_F_PARAMS || f == WS_F_ENV_PARAMS || f == WS_F_LOGITS) {
     if (t0 != 0 || n != 0) return WS_ERR_INVALID;
-    if (f == WS_F_LOGITS && c->cfg.path == WS_PATH_BATCHED_BF16) return WS_ERR_UNSUPPORTED;
+    if (f == WS_F_LOGITS && use_tc_control(&c->cfg)) return WS_ERR_UNSUPPORTED;
     std::vector<Piece> v = state_pieces(c, f);
     if (v.empty()) return WS_ERR_INVALID;
     size_t tot = 0;
