@@ -329,7 +329,7 @@ def run_serving(args, world, rank, local):
             if dt > 0:
                 time.sleep(dt)
             if bf16:
-                path = W.WS_PATH_BATCHED_BF16 if r["env"] == 0 else W.WS_PATH_BATCHED_FP32
+                path = W.WS_PATH_BATCHED_BF16
             else:
                 path = W.WS_PATH_PLAIN_FP32
             q, k = W.make_request(r["env"], path, r["n_envs"], r["horizon"], CHUNK,
@@ -365,7 +365,9 @@ def run_serving(args, world, rank, local):
             "config": {"workload": "serving mix: Poisson 200 req/s across control / economy / "
                                    "landscape, 256-65,536 envs, horizons 100-1,000, chunks of 50, "
                                    f"{args.serve_budget_gb:g} GB admission budget",
-                       "paths": "control BF16 tensor-core; economy and landscape batched FP32"},
+                       "paths": "served: BF16 tensor-core paths (control fused kernel; economy and "
+                                "landscape per-layer policy GEMMs + hi/lo energy cross-term); "
+                                "plain_fp32: one launch per sub-step per step"},
             "latency": {"chunk_steps": CHUNK, "p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"]},
             "serving": out}), flush=True)
 

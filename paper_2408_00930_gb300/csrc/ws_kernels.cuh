@@ -36,6 +36,7 @@ struct Dev {
   // BF16 tensor-core policy layers (economy / landscape): packed W^T images
   int tc_mlp;
   const uint8_t *pk[2][3];  // [agent, planner][layer]
+  const uint8_t *eimg;      // landscape: packed hi/lo centre image + table (BF16 energy)
   // ring
   float *r_obs;
   void *r_act;
@@ -82,6 +83,13 @@ cudaError_t launch_dense_tc(const void *X, long ldr, long ldc, int x_bf16, int K
                             const void *packed, int N, void *Y, int y_bf16, int act, long M,
                             uint32_t *err, cudaStream_t st);
 void dense_tc_init();
+
+// ---- BF16 tensor-core landscape energy (ws_energy_tc.cu) -------------------------
+size_t energy_tc_bytes(int D, int M);
+bool energy_tc_supported(int D, int M);
+void launch_energy_tc_pack(const Dev &d, void *buf, cudaStream_t st);
+void launch_energy_tc(const Dev &d, const void *buf, uint32_t off, int mode, cudaStream_t st);
+void energy_tc_init(int M);
 
 // Y[M][N] = act(X W + b) with the plain path's FP32 dense kernel (X row-major
 // when ldc == 1, or addressed X[r * ldr + c * ldc]).

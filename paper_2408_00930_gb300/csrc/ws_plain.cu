@@ -596,6 +596,10 @@ size_t energy_smem(const Dev &d) {
 }
 
 void landscape_energy(const Dev &d, uint32_t off, int mode, cudaStream_t st) {
+  if (d.eimg) {  // BF16 path: hi/lo cross-term on the tensor cores
+    launch_energy_tc(d, d.eimg, off, mode, st);
+    return;
+  }
   dim3 grid((d.n_envs + kEnergyThreads - 1) / kEnergyThreads, kEnergyChunks);
   k_energy_partial<<<grid, kEnergyThreads, energy_smem(d), st>>>(d, off, mode);
 }

@@ -159,6 +159,8 @@ Layout make_layout(const ws_config *cfg, const std::vector<int32_t> &agents) {
   if (cfg->env == WS_ENV_ECONOMY) o += up(N * 4);
   L.env_derived_off = o;
   L.env_derived_bytes = cfg->env == WS_ENV_LANDSCAPE ? up(M * 4) + up(M * 4) : 0;
+  if (cfg->env == WS_ENV_LANDSCAPE && cfg->path == WS_PATH_BATCHED_BF16)
+    L.env_derived_bytes += up(energy_tc_bytes((int)D, (int)M));
   o += L.env_derived_bytes;
   L.state_off = o;
   if (cfg->env == WS_ENV_CONTROL) o += up(4 * N * 4);
@@ -233,6 +235,8 @@ void make_dev(ws_ctx *c) {
     d.amps = (float *)(S + L.env_params_off + up(M * D * 4) + up(M * 4));
     d.cnorm = (float *)(S + L.env_derived_off);
     d.coef = (float *)(S + L.env_derived_off + up(M * 4));
+    if (cfg.path == WS_PATH_BATCHED_BF16)
+      d.eimg = (const uint8_t *)(S + L.env_derived_off + up(M * 4) + up(M * 4));
     d.s = (float *)(S + L.state_off);
     d.eobs = (float *)(S + L.state_off + up(D * N * 4));
     d.needs_energy = (uint8_t *)(S + L.state_off + up(D * N * 4) + up(N * 4));
@@ -391,6 +395,7 @@ std::vector<Piece> state_pieces(ws_ctx *c, ws_field f) {
 
 ws_status after_params_changed(ws_ctx *c) {
   if (c->cfg.env == WS_ENV_LANDSCAPE) launch_landscape_derive(c->d, c->stream);
+  if (c->d.eimg) launch_energy_tc_pack(c->d, (void *)c->d.eimg, c->stream);
   if (use_tc_control(&c->cfg)) launch_control_tc_pack(c->d, c->state + c->L.packed_off, c->stream);
   if (use_tc_layers(&c->cfg)) {
     for (int pid = 0; pid < (c->cfg.env == WS_ENV_ECONOMY ? 2 : 1); ++pid) {
@@ -421,6 +426,9 @@ ws_status ws_query_bytes(const ws_config *cfg, size_t *state_bytes, size_t *ring
   const Layout L = make_layout(cfg, agents);
   if (use_tc_layers(cfg) &&
       !(tc_layers_supported(L.pol) && (cfg->env != WS_ENV_ECONOMY || tc_layers_supported(L.pol_planner))))
+    return WS_ERR_UNSUPPORTED;
+  if (use_tc_layers(cfg) && cfg->env == WS_ENV_LANDSCAPE &&
+      !energy_tc_supported((int)cfg->dim, (int)cfg->n_gauss))
     return WS_ERR_UNSUPPORTED;
   if (state_bytes) *state_bytes = L.state_bytes;
   if (ring_bytes) *ring_bytes = L.ring_bytes;
@@ -482,6 +490,7 @@ ws_status ws_create(const ws_config *cfg, void *state_buf, size_t state_bytes, v
   if (cfg->env == WS_ENV_LANDSCAPE) launch_init_landscape(c->d, cfg->param_seed, c->stream);
   if (use_tc_control(cfg)) c->tc_grid = control_tc_default_grid(c->d);
   if (use_tc_layers(cfg)) dense_tc_init();
+  if (use_tc_layers(cfg) && cfg->env == WS_ENV_LANDSCAPE) energy_tc_init((int)cfg->n_gauss);
   s = after_params_changed(c);
   if (s == WS_OK) s = ws_reset(c, cfg->param_seed);
   if (s == WS_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream), "create sync");
