@@ -136,6 +136,11 @@ def barrier(world):
         dist.barrier()
 
 
+def job_throughput(units_per_rank_step, steps, world, max_ms):
+    """Whole-job rate: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank_step * steps * world / (max_ms / 1e3)
+
+
 def max_over_ranks(v, world):
     if world == 1:
         return v
@@ -271,7 +276,7 @@ def run_gpu(args, wl, world, rank, local):
     main = one_path(path, args.steps, args.warmup, True)
     r = main["rollout"]
     n_steps_total = args.steps
-    value = main["agent_steps"] * n_steps_total * world / (main["total_ms"] / 1e3)
+    value = job_throughput(main["agent_steps"], n_steps_total, world, main["total_ms"])
     # plain FP32 path beside it (fewer steps: it is the slow baseline)
     plain = None
     if not args.no_plain:
