@@ -32,6 +32,11 @@ constexpr int kABytes = kKB * kRows * 128;
 constexpr int kBBytes = kKB * kBlockG * 128;
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr uint32_t kTmemCols = 512;
+// Gaussian chunks per env tile: each CTA sweeps Mp / kTcChunks Gaussians in
+// 256-wide blocks through its double-buffered pipeline (long enough to
+// amortise its set-up); partial sums land in the first kTcChunks of the
+// kEnergyChunks slots, whose others are kept at zero.
+constexpr int kTcChunks = 2;
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
                                          uint64_t *bar) {
@@ -261,9 +266,9 @@ size_t smem_for(int per_chunk) {
 
 // Padded Gaussian count (a multiple of kEnergyChunks * 256) and its chunk size.
 void energy_tc_shape(int M, int *Mp, int *per_chunk) {
-  const int blk = kEnergyChunks * kBlockG;
+  const int blk = kTcChunks * kBlockG;
   *Mp = (M + blk - 1) / blk * blk;
-  *per_chunk = *Mp / kEnergyChunks;
+  *per_chunk = *Mp / kTcChunks;
 }
 
 size_t energy_tc_bytes(int D, int M) {
@@ -299,7 +304,7 @@ void launch_energy_tc(const Dev &d, const void *buf, uint32_t off, int mode, cud
   energy_tc_shape((int)d.n_gauss, &Mp, &pc);
   const uint8_t *img = (const uint8_t *)buf;
   const float4 *tab = (const float4 *)(img + (size_t)Mp * kKB * 128);
-  dim3 grid((d.n_envs + kRows - 1) / kRows, kEnergyChunks);
+  dim3 grid((d.n_envs + kRows - 1) / kRows, kTcChunks);
   k_energy_tc<<<grid, kThreads, smem_for(pc), st>>>(d, off, mode, img, tab, Mp, pc);
 }
 

@@ -512,6 +512,9 @@ ws_status ws_reset(ws_ctx *c, uint64_t seed) {
   // the economy's per-step income accumulator must start at zero (every step
   // clears it after use; a fresh caller buffer holds arbitrary bytes)
   if (c->d.income) cudaMemsetAsync(c->d.income, 0, (size_t)c->L.n_agent_slots * 8, c->stream);
+  // landscape energy partials: the tensor-core path fills only the first slots
+  if (c->d.epart)
+    cudaMemsetAsync(c->d.epart, 0, (size_t)kEnergyChunks * 2 * c->L.n_envs * 4, c->stream);
   launch_reset(c->d, c->stream);
   c->k_host = 0;
   return cuda_check(c, cudaGetLastError(), "reset");
