@@ -157,8 +157,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(DenseArgs a) {
       tc::wg_sync(bar_id);
       if (r == 0) {
         tc::fence_after_sync();
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
+        // only the K16 steps that hold real K (the rest of the block is zero)
+        const int kk_n = min(4, (a.K - kb * 64 + 15) / 16);
+        for (int kk = 0; kk < kk_n; ++kk) {
           const uint64_t da = tc::smem_desc(slot + kk * 32, 16, 1024, tc::kSwizzle128B);
           const uint64_t db = tc::smem_desc(sb + kb * (a.Np * 128) + kk * 32, 16, 1024,
                                             tc::kSwizzle128B);

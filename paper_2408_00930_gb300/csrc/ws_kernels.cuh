@@ -57,7 +57,13 @@ void launch_landscape_derive(const Dev &d, cudaStream_t st);
 void launch_reset(const Dev &d, cudaStream_t st);
 
 // ---- plain / batched-FP32 step (one launch per sub-step) -----------------
-void launch_plain_step(const Dev &d, uint32_t step_off, cudaStream_t st);
+// `aux` (with its fork/join events) lets the economy run the planner's policy
+// beside the agents' as a parallel branch (also inside a captured graph).
+struct Branch {
+  cudaStream_t aux;
+  cudaEvent_t fork, join;
+};
+void launch_plain_step(const Dev &d, uint32_t step_off, cudaStream_t st, const Branch *br);
 void launch_advance(const Dev &d, uint32_t n, cudaStream_t st);
 
 // ---- S7: discounted returns ----------------------------------------------

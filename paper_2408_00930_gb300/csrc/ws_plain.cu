@@ -346,56 +346,76 @@ __global__ void k_control_step(Dev d, uint32_t off) {
 }
 
 // -------------------------------------------------------- economy (S1..S5)
+// Fixed-order block reduction: xor-shuffle tree inside each warp, then the
+// warp partials summed in warp order by every thread (deterministic for floats).
 template <typename T>
 __device__ T block_sum(T v, T *sh) {
-  // fixed-order tree: deterministic for floats
-  const int tid = threadIdx.x;
-  sh[tid] = v;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) sh[wid] = v;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (tid < s) sh[tid] += sh[tid + s];
-    __syncthreads();
-  }
-  const T r = sh[0];
+  T r = sh[0];
+  for (int i = 1; i < nw; ++i) r += sh[i];
   __syncthreads();
   return r;
 }
 
-constexpr int kEconThreads = 256;
+constexpr int kEconThreads = 128;
 
 // Per env: planner observation = mean agent features; store agent and
 // planner observations and pre-step wealth (planner slot: env total).
 __global__ __launch_bounds__(kEconThreads) void k_econ_observe(Dev d, uint32_t off) {
-  __shared__ float shf[kEconThreads];
-  __shared__ long long shi[kEconThreads];
+  __shared__ float shf[kEconF][kEconThreads / 32];
+  __shared__ long long shi[kEconThreads / 32];
   const uint32_t e = blockIdx.x;
   const int a0 = d.agent_off[e], n = d.agent_off[e + 1] - a0;
   const uint32_t row = ring_row(d, step_k(d, off));
   float *obs = d.r_obs + (size_t)row * kEconF * d.n_slots;
   const uint32_t ps = d.n_agent_slots + e;
-  for (int j = 0; j < kEconF; ++j) {
-    float s = 0.f;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const float f = d.feat[(size_t)j * d.n_agent_slots + a0 + i];
-      s += f;
-      obs[(size_t)j * d.n_slots + a0 + i] = f;
-    }
-    const float tot = block_sum(s, shf);
-    if (threadIdx.x == 0) {
-      const float mean = tot / (float)n;
-      d.pobs[(size_t)e * kEconF + j] = mean;
-      obs[(size_t)j * d.n_slots + ps] = mean;
-    }
-  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float s[kEconF];
+#pragma unroll
+  for (int j = 0; j < kEconF; ++j) s[j] = 0.f;
   long long ws = 0;
   int64_t *wrec = d.r_wealth + (size_t)row * d.n_slots;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < kEconF; ++j) {
+      const float f = d.feat[(size_t)j * d.n_agent_slots + a0 + i];
+      s[j] += f;
+      obs[(size_t)j * d.n_slots + a0 + i] = f;
+    }
     const int64_t w = d.wealth[a0 + i];
     wrec[a0 + i] = w;
     ws += w;
   }
-  const long long tot = block_sum(ws, shi);
-  if (threadIdx.x == 0) wrec[ps] = tot;
+#pragma unroll
+  for (int j = 0; j < kEconF; ++j) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s[j] += __shfl_xor_sync(0xffffffffu, s[j], o);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, o);
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < kEconF; ++j) shf[j][wid] = s[j];
+    shi[wid] = ws;
+  }
+  __syncthreads();
+  if (threadIdx.x < kEconF) {
+    const int j = threadIdx.x;
+    float tot = shf[j][0];
+    for (int q = 1; q < kEconThreads / 32; ++q) tot += shf[j][q];
+    const float mean = tot / (float)n;
+    d.pobs[(size_t)e * kEconF + j] = mean;
+    obs[(size_t)j * d.n_slots + ps] = mean;
+  }
+  if (threadIdx.x == 32) {
+    long long tot = shi[0];
+    for (int q = 1; q < kEconThreads / 32; ++q) tot += shi[q];
+    wrec[ps] = tot;
+  }
 }
 
 // Transfers t_i = floor(w_i a_i / 400) from pre-step wealth to partner
@@ -422,8 +442,8 @@ __global__ void k_econ_transfer(Dev d, uint32_t off) {
 // Per env: tax on income, even redistribution (remainder to low indices),
 // feature drift, rewards, planner reward (mean), done and auto-reset.
 __global__ __launch_bounds__(kEconThreads) void k_econ_finish(Dev d, uint32_t off) {
-  __shared__ float shf[kEconThreads];
-  __shared__ long long shi[kEconThreads];
+  __shared__ float shf[kEconThreads / 32];
+  __shared__ long long shi[kEconThreads / 32];
   const uint32_t e = blockIdx.x;
   const uint64_t k = step_k(d, off);
   const uint32_t row = ring_row(d, k);
@@ -671,7 +691,7 @@ void launch_reset(const Dev &d, cudaStream_t st) {
   }
 }
 
-void launch_plain_step(const Dev &d, uint32_t off, cudaStream_t st) {
+void launch_plain_step(const Dev &d, uint32_t off, cudaStream_t st, const Branch *br) {
   if (d.env == WS_ENV_CONTROL) {
     k_store_obs<<<blocks(d.n_envs, 256), 256, 0, st>>>(d, off, d.s, 4, d.n_envs, d.n_envs, 0);
     policy(d, d.s, 1, d.n_envs, d.params, d.pol, 0, d.h0, d.h1, d.out, (int)d.n_envs, st);
@@ -679,14 +699,25 @@ void launch_plain_step(const Dev &d, uint32_t off, cudaStream_t st) {
     k_control_step<<<blocks(d.n_envs, 256), 256, 0, st>>>(d, off);
   } else if (d.env == WS_ENV_ECONOMY) {
     k_econ_observe<<<d.n_envs, kEconThreads, 0, st>>>(d, off);
+    // the planner's policy and draw are independent of the agents': side branch
+    cudaStream_t ps = st;
+    if (br) {
+      cudaEventRecord(br->fork, st);
+      cudaStreamWaitEvent(br->aux, br->fork, 0);
+      ps = br->aux;
+    }
+    policy(d, d.pobs, kEconF, 1, d.params_planner, d.pol_planner, 1, d.ph0, d.ph1, d.pout,
+           (int)d.n_envs, ps);
+    k_sample_cat<<<blocks(d.n_envs, 256), 256, 0, ps>>>(d, off, d.pout, (int)d.n_out_planner, 2,
+                                                         d.n_envs, d.n_agent_slots);
     policy(d, d.feat, 1, d.n_agent_slots, d.params, d.pol, 0, d.h0, d.h1, d.out,
            (int)d.n_agent_slots, st);
-    policy(d, d.pobs, kEconF, 1, d.params_planner, d.pol_planner, 1, d.ph0, d.ph1, d.pout,
-           (int)d.n_envs, st);
     k_sample_cat<<<blocks(d.n_agent_slots, 256), 256, 0, st>>>(d, off, d.out, (int)d.n_out, 1,
                                                                 d.n_agent_slots, 0);
-    k_sample_cat<<<blocks(d.n_envs, 256), 256, 0, st>>>(d, off, d.pout, (int)d.n_out_planner, 2,
-                                                         d.n_envs, d.n_agent_slots);
+    if (br) {
+      cudaEventRecord(br->join, br->aux);
+      cudaStreamWaitEvent(st, br->join, 0);
+    }
     k_econ_transfer<<<blocks(d.n_agent_slots, 256), 256, 0, st>>>(d, off);
     k_econ_finish<<<d.n_envs, kEconThreads, 0, st>>>(d, off);
   } else {

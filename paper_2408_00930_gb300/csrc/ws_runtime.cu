@@ -20,6 +20,7 @@ struct ws_ctx {
   cudaStream_t stream = nullptr;    // caller's stream (borrowed)
   cudaStream_t capture = nullptr;   // private stream used only to capture graphs
   cudaEvent_t ev = nullptr;
+  Branch br{nullptr, nullptr, nullptr};  // economy: planner branch
   char *state = nullptr;
   char *ring = nullptr;
   uint64_t k_host = 0;
@@ -305,7 +306,8 @@ ws_status enqueue_steps(ws_ctx *c, uint32_t n, cudaStream_t st) {
       done += m;
     }
   } else {
-    for (uint32_t i = 0; i < n; ++i) launch_plain_step(c->d, i, st);
+    const Branch *br = c->br.aux ? &c->br : nullptr;
+    for (uint32_t i = 0; i < n; ++i) launch_plain_step(c->d, i, st, br);
     launch_advance(c->d, n, st);
   }
   return cuda_check(c, cudaGetLastError(), "step launch");
@@ -458,6 +460,11 @@ ws_status ws_create(const ws_config *cfg, void *state_buf, size_t state_bytes, v
   make_dev(c);
   cudaError_t e = cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming);
+  if (e == cudaSuccess && cfg->env == WS_ENV_ECONOMY) {
+    e = cudaStreamCreateWithFlags(&c->br.aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->br.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->br.join, cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
     cuda_check(c, e, "stream/event create");
     ws_status r = c->err;
@@ -695,6 +702,10 @@ void ws_destroy(ws_ctx *c) {
   if (!c) return;
   if (c->stream || c->ev) cudaStreamSynchronize(c->stream);
   drop_graphs(c);
+  if (c->br.aux) cudaStreamSynchronize(c->br.aux);
+  if (c->br.fork) cudaEventDestroy(c->br.fork);
+  if (c->br.join) cudaEventDestroy(c->br.join);
+  if (c->br.aux) cudaStreamDestroy(c->br.aux);
   if (c->ev) cudaEventDestroy(c->ev);
   if (c->capture) cudaStreamDestroy(c->capture);
   delete c;
