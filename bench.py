@@ -84,7 +84,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
@@ -253,6 +253,7 @@ def run_gpu(args, wl, world, rank, local):
         barrier(world)
         torch.cuda.synchronize(dev)
         clocks.start()
+        time.sleep(0.3)  # let the sampler start before the timed region
         for i in range(steps):
             flush.zero_()                      # L2 flush between timed steps
             torch.cuda.synchronize(dev)
@@ -394,7 +395,7 @@ def _param_bytes(wl):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="control_scale", choices=sorted(WORKLOADS) + ["serving"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -458,6 +459,11 @@ def main():
                 "peak_source": f"{peak_src} bf16 sustained" if bf16 else
                 f"{peak_src} bf16 sustained / 4 (fp32 SIMT)"}
     roofline["frac"] = roofline["achieved"] / roofline["peak"]
+    if bf16 and args.workload == "control_scale" and not args.horizon and not args.n_envs:
+        # DRAM bytes (read + write) of one 50-step launch of this kernel, from the
+        # ncu capture summarised in profiles/control_tc_ncu_full_control_50steps.md
+        roofline["traffic"] = (3.000832 + 133.212928) * 1e6
+        roofline["traffic_algorithmic"] = 29.0 * wl["n_envs"] * launch_steps
     lat = sorted(main_res["chunk_ms"])
     # kernels of ours per bench step: reset, per chunk (fused kernel + counter
     # advance) or per step the plain kernels, and the returns scan

@@ -138,7 +138,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(DenseArgs a) {
   uint32_t fail_site = 0;
   const long n_tiles = (a.M + kTile - 1) / kTile;
 
-  for (long tile = (long)blockIdx.x * kWG + wg; ok && tile < n_tiles; tile += (long)gridDim.x * kWG) {
+  // warpgroup wg of CTA b takes tiles b + wg * grid, + 2 grid, ...: with fewer
+  // tiles than SMs every tile gets an SM of its own
+  for (long tile = (long)blockIdx.x + (long)wg * gridDim.x; ok && tile < n_tiles;
+       tile += (long)gridDim.x * kWG) {
     const long row = tile * kTile + r;
     const bool valid = row < a.M;
     for (int kb = 0; kb < a.KB; ++kb) {
@@ -295,8 +298,7 @@ cudaError_t launch_dense_tc(const void *X, long ldr, long ldc, int x_bf16, int K
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long tiles = (M + kTile - 1) / kTile;
-  long grid = (tiles + kWG - 1) / kWG;
-  if (grid > sms) grid = sms;
+  const long grid = tiles < sms ? tiles : sms;
   size_t smem = smem_bytes(a.KB, a.Np);
   if (smem < 120 * 1024) smem = 120 * 1024;  // one CTA per SM: its 512 TMEM columns uncontended
   k_dense_tc<<<(unsigned)grid, kThreads, smem, st>>>(a);
