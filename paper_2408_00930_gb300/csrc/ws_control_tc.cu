@@ -4,25 +4,26 @@
 // the SM (paper Sec. 2 / App. B: roll-out, inference, reset and the in-place
 // store all on the GPU; envs independent, policy referenced from GPU memory).
 //
-// Work split: a CTA holds two warpgroups; each owns a tile of 128 envs, one
-// env per thread (thread r of the warpgroup = TMEM lane r = MMA row r).
-// Per step and tile:
+// Work split: a CTA holds two groups of 256 threads; each group owns a tile of
+// 128 envs.  Env row r of a tile is served by two threads ("halves" h = 0, 1;
+// both in warps that may reach TMEM lane r), which split the row's hidden
+// units: half h owns the 64-unit K-blocks h and h + 2.  Per step and tile:
 //   layer 1  z1 = s W1 + b1 on the tensor core, K = 16: the operand row
 //            [s_hi, s_lo, s_hi, 1, 1, 0, 0] against [W1_hi; W1_hi; W1_lo; b1_hi;
-//            b1_lo] keeps FP32-level accuracy (missing term s_lo W1_lo ~ 2^-16)
-//   act 1    h1 = tanh(z1) in packed bf16x2 (the BF16 A operand of layer 2)
-//   layer 2  z2 = h1 W2 + b2: one K = 16 MMA of the same operand row against
-//            [0 x 12, b2_hi, b2_lo, 0, 0] (its constant-one columns), then K = H0
-//            streamed 64 at a time through two 16 KB 128B-swizzled slots while
-//            W2^T stays resident in shared memory
-//   act 2    h2 = tanh(z2) in packed bf16x2, streamed back through the slots
-//   layer 3  logits = h2 W3 on the tensor core, N = 16 with W3 split hi/lo
-//            (columns W3_hi[:,0], W3_hi[:,1], W3_lo[:,0], W3_lo[:,1]); + b3
-//   then     categorical sample (Philox), Euler step, reward, done, auto-reset,
-//            and the time-major record write.
-// All three layers accumulate in the same 256 TMEM columns of the warpgroup:
-// z1 is fully read before the first layer-2 MMA overwrites it, and layer 3
-// writes only columns 0..15 after every lane has read them.
+//            b1_lo] keeps FP32-level accuracy (missing term s_lo W1_lo ~ 2^-16);
+//            h1 = tanh(z1) as packed bf16x2 into two 16 KB 128B-swizzled slots
+//   layer 2  z2 = h1 W2 + b2 on the tensor core into the same 256 TMEM columns:
+//            b2 by one K = 16 MMA of the operand row's constant columns against
+//            [0 x 12, b2_hi, b2_lo, 0, 0], then the K-blocks of h1 as their
+//            slots fill; W2^T stays resident in shared memory
+//   layer 3  logits = tanh(z2) W3: h2 = tanh(z2) streamed back through the slots,
+//            N = 16 MMA with W3 split hi/lo (rows W3_hi[:,0], W3_hi[:,1],
+//            W3_lo[:,0], W3_lo[:,1]) into TMEM columns already read; + b3
+//   then     categorical sample (Philox), Euler step, reward, done, auto-reset
+//            (both halves, identically: each keeps the state it needs) and the
+//            time-major record write (half 0).
+// Two threads per row give 16 warps per SM, so that one warp's MUFU/TMEM
+// latency overlaps another's work; the per-thread epilogue work halves.
 #include "ws_kernels.cuh"
 #include "ws_tc.cuh"
 
@@ -31,22 +32,25 @@ namespace ws {
 namespace {
 
 constexpr int kTile = 128;
-constexpr int kWG = 2;
-constexpr int kThreads = kTile * kWG;
+constexpr int kGroups = 2;
+constexpr int kGroupThreads = 2 * kTile;
+constexpr int kThreads = kGroups * kGroupThreads;
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s, far above any MMA completion time
 constexpr uint32_t kTmemCols = 512;
 
 template <int H0, int H1>
 struct CtrlTc {
-  static_assert(H0 % 64 == 0 && H0 <= 256, "layer-2 K must be a multiple of 64, <= 256");
-  static_assert(H1 % 64 == 0 && H1 <= 256, "layer-3 K (= H1) must be a multiple of 64, <= 256");
-  static constexpr int KB = H0 / 64;               // layer-2 K-blocks
-  static constexpr int KB3 = H1 / 64;              // layer-3 K-blocks
+  static_assert(H0 == 64 || H0 == 128 || H0 == 256, "layer-2 K must be 64, 128 or 256");
+  static_assert(H1 == 64 || H1 == 128 || H1 == 256, "layer-3 K (= H1) must be 64, 128 or 256");
+  static constexpr int KB = H0 / 64;               // layer-2 K-blocks (1, 2 or 4)
+  static constexpr int KB3 = H1 / 64;              // layer-3 K-blocks (1, 2 or 4)
+  static constexpr int KBF = KB < 2 ? KB : 2;      // K-blocks in flight at first (slots)
+  static constexpr int KBF3 = KB3 < 2 ? KB3 : 2;
   static constexpr int W2_BYTES = KB * H1 * 128;   // B of layer 2, SW128, K-blocks of 64
   static constexpr int B3_BYTES = KB3 * 16 * 128;  // B of layer 3 (N = 16), SW128
   static constexpr int B1_BYTES = H0 * 32;         // B of layer 1, no swizzle, K = 16
   static constexpr int BB_BYTES = H1 * 32;         // B of the b2 MMA, no swizzle, K = 16
-  static constexpr int B3V_BYTES = 16;             // b3 (2 floats, padded)
+  static constexpr int B3V_BYTES = 16;             // b3
   // packed global image: [W2 | B3 | B1 | BB | b3]
   static constexpr int PK_W2 = 0;
   static constexpr int PK_B3 = PK_W2 + W2_BYTES;
@@ -55,23 +59,22 @@ struct CtrlTc {
   static constexpr int PK_B3V = PK_BB + BB_BYTES;
   static constexpr int PACKED = PK_B3V + B3V_BYTES;
   // shared memory (from a 1024-aligned base)
-  static constexpr int SLOT = 128 * 128;  // one A K-block: 128 rows x 128 B
+  static constexpr int SLOT = 128 * 128;
   static constexpr int OFF_W2 = 0;
   static constexpr int OFF_B3 = OFF_W2 + W2_BYTES;
-  static constexpr int OFF_A2 = OFF_B3 + B3_BYTES;
-  static constexpr int OFF_B1 = OFF_A2 + kWG * 2 * SLOT;
-  static constexpr int OFF_BB = OFF_B1 + B1_BYTES;
-  static constexpr int OFF_A1 = OFF_BB + BB_BYTES;
-  static constexpr int OFF_B3V = OFF_A1 + kWG * 128 * 32;
+  static constexpr int OFF_SL = OFF_B3 + B3_BYTES;  // [group][2 slots]
+  static constexpr int OFF_B1 = OFF_SL + kGroups * 2 * SLOT;
+  static constexpr int OFF_BB = OFF_B1 + B1_BYTES;  // B1 then BB, contiguous as packed
+  static constexpr int OFF_A1 = OFF_BB + BB_BYTES;  // [group] layer-1 operand, 4 KB each
+  static constexpr int OFF_B3V = OFF_A1 + kGroups * 128 * 32;
   static constexpr int OFF_BAR = OFF_B3V + B3V_BYTES;
-  static constexpr int N_BAR = 4;  // per warpgroup: layer 1, slot 0, slot 1, drain
-  static constexpr int OFF_TM = OFF_BAR + kWG * N_BAR * 8;
-  // + slack for 1024-byte alignment; at least 120 KB so that one CTA owns an SM
-  // (its 512 TMEM columns are then never contended)
+  static constexpr int N_BAR = 4;  // per group: layer 1, slot 0, slot 1, drain
+  static constexpr int OFF_TM = OFF_BAR + kGroups * N_BAR * 8;
   static constexpr int SMEM_NEED = OFF_TM + 16 + 1024;
+  // at least 120 KB: one CTA per SM, so its 512 TMEM columns are uncontended
   static constexpr int SMEM = SMEM_NEED > 120 * 1024 ? SMEM_NEED : 120 * 1024;
   static_assert(SMEM_NEED <= 232448, "shared memory over the 227 KB per-CTA limit");
-  static_assert(OFF_A2 % 1024 == 0 && OFF_B3 % 1024 == 0, "SW128 operands need 1 KB alignment");
+  static_assert(OFF_SL % 1024 == 0 && OFF_B3 % 1024 == 0, "SW128 operands need 1 KB alignment");
 };
 
 __device__ __forceinline__ uint16_t bf16_bits(float f) {
@@ -155,19 +158,18 @@ __device__ __forceinline__ void store_row_sw128(uint32_t row_addr, uint32_t swz,
                p[ch * 4 + 3]);
 }
 
-// tanh of 64 accumulator columns, packed bf16x2.
+// tanh of 64 accumulator columns at taddr, packed bf16x2 (two 32-column loads).
 __device__ __forceinline__ void tanh_block64(uint32_t taddr, uint32_t (&hp)[32]) {
-  uint32_t z0[32], z1[32];
-  tc::tmem_ld32(taddr, z0);
-  tc::tmem_ld32(taddr + 32, z1);
-  tc::tmem_wait_ld();
 #pragma unroll
-  for (int i = 0; i < 16; ++i)
-    hp[i] = tc::tanh_bf16x2(tc::pack_bf16x2(__uint_as_float(z0[2 * i]), __uint_as_float(z0[2 * i + 1])));
+  for (int half = 0; half < 2; ++half) {
+    uint32_t z[32];
+    tc::tmem_ld32(taddr + half * 32, z);
+    tc::tmem_wait_ld();
 #pragma unroll
-  for (int i = 0; i < 16; ++i)
-    hp[16 + i] =
-        tc::tanh_bf16x2(tc::pack_bf16x2(__uint_as_float(z1[2 * i]), __uint_as_float(z1[2 * i + 1])));
+    for (int i = 0; i < 16; ++i)
+      hp[half * 16 + i] =
+          tc::tanh_bf16x2(tc::pack_bf16x2(__uint_as_float(z[2 * i]), __uint_as_float(z[2 * i + 1])));
+  }
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
@@ -180,6 +182,23 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
       : "r"(taddr));
 }
 
+// Group-wide barrier (256 threads) and AND-vote.
+__device__ __forceinline__ void grp_sync(uint32_t id) {
+  asm volatile("bar.sync %0, 256;" ::"r"(id) : "memory");
+}
+__device__ __forceinline__ bool grp_all(uint32_t id, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, %2, 256, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id)
+      : "memory");
+  return r != 0;
+}
+
 template <int H0, int H1>
 __global__ void __launch_bounds__(kThreads, 1)
     k_ctrl_tc(Dev d, const uint8_t *__restrict__ packed, uint32_t n_steps) {
@@ -188,8 +207,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t raw = tc::smem_u32(smem_raw);
   uint8_t *sm = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
   const uint32_t sb = tc::smem_u32(sm);
-  const int tid = threadIdx.x, wg = tid >> 7, r = tid & 127, warp = tid >> 5;
-  uint64_t *bars = (uint64_t *)(sm + C::OFF_BAR) + wg * C::N_BAR;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int g = tid >> 8, h = (tid >> 7) & 1, r = tid & 127;
+  uint64_t *bars = (uint64_t *)(sm + C::OFF_BAR) + g * C::N_BAR;
   uint64_t *bar_l1 = bars, *bar_slot = bars + 1, *bar_drain = bars + 3;
   uint32_t *tm_holder = (uint32_t *)(sm + C::OFF_TM);
 
@@ -205,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (tid == 0) {
     uint64_t *all = (uint64_t *)(sm + C::OFF_BAR);
-    for (int i = 0; i < kWG * C::N_BAR; ++i) tc::mbar_init(all + i, 1);
+    for (int i = 0; i < kGroups * C::N_BAR; ++i) tc::mbar_init(all + i, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tc::tmem_alloc(tm_holder, kTmemCols);
@@ -214,11 +234,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc::fence_after_sync();
 
-  const uint32_t tmem = *tm_holder + (uint32_t)wg * 256u;
+  const uint32_t tmem = *tm_holder + (uint32_t)g * 256u;
   const uint32_t lane = (uint32_t)((warp & 3) * 32) << 16;
-  const uint32_t bar_id = 1u + (uint32_t)wg;
-  const uint32_t a1 = sb + C::OFF_A1 + wg * 128 * 32;
-  const uint32_t a2 = sb + C::OFF_A2 + wg * 2 * C::SLOT;
+  const uint32_t bar_id = 1u + (uint32_t)g;
+  const uint32_t slots = sb + C::OFF_SL + (uint32_t)g * 2 * C::SLOT;
+  const uint32_t swz = (uint32_t)(r & 7);
+  const uint32_t my_row = (uint32_t)r * 128u;
+  const uint32_t a1 = sb + C::OFF_A1 + (uint32_t)g * 128 * 32;
+  const uint32_t a1_row = a1 + (uint32_t)(r >> 3) * 256u + (uint32_t)(r & 7) * 16u;
   const uint64_t desc_a1 = tc::smem_desc(a1, 128, 256, tc::kSwizzleNone);
   const uint64_t desc_b1 = tc::smem_desc(sb + C::OFF_B1, 128, 256, tc::kSwizzleNone);
   const uint64_t desc_bb = tc::smem_desc(sb + C::OFF_BB, 128, 256, tc::kSwizzleNone);
@@ -226,10 +249,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr uint32_t idesc2 = tc::idesc_bf16_f32(128, H1);
   constexpr uint32_t idesc3 = tc::idesc_bf16_f32(128, 16);
   const float4 b3 = *(const float4 *)(sm + C::OFF_B3V);
-  const uint32_t a1_row = a1 + (uint32_t)(r >> 3) * 256u + (uint32_t)(r & 7) * 16u;
-  const uint32_t swz = (uint32_t)(r & 7);
+  const bool issuer = (r == 0 && h == 0);
 
-  uint32_t ph_l1 = 0, ph_s0 = 0, ph_s1 = 0;
+  uint32_t ph_l1 = 0u, ph[2] = {0u, 0u};
   bool ok = true;
   uint32_t fail_site = 0;
   const uint64_t k0 = d.k[0];
@@ -237,21 +259,19 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t row0 = (uint32_t)(k0 % R);
   const uint32_t N = d.n_envs, S = d.n_slots;
   const int n_tiles = (int)((N + kTile - 1) / kTile);
-  const int n_workers = (int)gridDim.x * kWG;
 
-  // Wait for the next completion on slot s (every commit is waited exactly once).
-#define WS_WAIT_SLOT(s, site)                                                   \
-  {                                                                             \
-    uint32_t &ph_ = (s) ? ph_s1 : ph_s0;                                        \
-    ok = tc::wg_all(bar_id, tc::mbar_wait(bar_slot + (s), ph_, kWaitNs));       \
-    ph_ ^= 1u;                                                                  \
-    if (!ok) {                                                                  \
-      fail_site = (site);                                                       \
-      break;                                                                    \
-    }                                                                           \
+#define WS_WAIT_SLOT(s, site)                                                         \
+  {                                                                                   \
+    ok = grp_all(bar_id, tc::mbar_wait(bar_slot + (s), ph[(s)], kWaitNs));            \
+    ph[(s)] ^= 1u;                                                                    \
+    if (!ok) {                                                                        \
+      fail_site = (site);                                                             \
+      break;                                                                          \
+    }                                                                                 \
   }
 
-  for (int tile = (int)blockIdx.x * kWG + wg; ok && tile < n_tiles; tile += n_workers) {
+  for (int tile = (int)blockIdx.x * kGroups + g; ok && tile < n_tiles;
+       tile += (int)gridDim.x * kGroups) {
     const uint32_t e = (uint32_t)tile * kTile + (uint32_t)r;
     const bool valid = e < N;
     float x = 0.f, v = 0.f, th = 0.f, w = 0.f;
@@ -266,115 +286,144 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t row = row0;
     for (uint32_t j = 0; j < n_steps; ++j) {
       const uint32_t k = (uint32_t)(k0 + j);
-      // ---- layer 1 operand row: [s_hi | s_lo | s_hi | 1 1 0 0]
+      // ---- layer 1 operand row [s_hi | s_lo | s_hi | 1 1 0 0] (half h writes core h)
       {
         const float xh = bf16_val(x), vh = bf16_val(v), thh = bf16_val(th), wh = bf16_val(w);
         const uint32_t hi01 = tc::pack_bf16x2(xh, vh), hi23 = tc::pack_bf16x2(thh, wh);
-        const uint32_t lo01 = tc::pack_bf16x2(x - xh, v - vh), lo23 = tc::pack_bf16x2(th - thh, w - wh);
-        tc::sts128(a1_row, hi01, hi23, lo01, lo23);
-        tc::sts128(a1_row + 128, hi01, hi23, tc::pack_bf16x2(1.f, 1.f), 0u);
+        if (h == 0) {
+          tc::sts128(a1_row, hi01, hi23, tc::pack_bf16x2(x - xh, v - vh),
+                     tc::pack_bf16x2(th - thh, w - wh));
+        } else {
+          tc::sts128(a1_row + 128, hi01, hi23, tc::pack_bf16x2(1.f, 1.f), 0u);
+        }
       }
       tc::fence_async_smem();
-      tc::fence_before_sync();
-      tc::wg_sync(bar_id);
-      if (r == 0) {
+      tc::fence_before_sync();  // (also orders the last step's TMEM reads before the MMA)
+      grp_sync(bar_id);
+      if (issuer) {
         tc::fence_after_sync();
         tc::mma_bf16(tmem, desc_a1, desc_b1, idesc1, false);
         tc::mma_commit(bar_l1);
       }
-      ok = tc::wg_all(bar_id, tc::mbar_wait(bar_l1, ph_l1, kWaitNs));
+      ok = grp_all(bar_id, tc::mbar_wait(bar_l1, ph_l1, kWaitNs));
       ph_l1 ^= 1u;
       if (!ok) { fail_site = 1; break; }
       tc::fence_after_sync();
-      // ---- act 1.  K-blocks 0 and 1 go straight into their (free) slots; later
-      // K-blocks wait in registers until z1 has been read completely.
-      constexpr int KH = C::KB > 2 ? C::KB - 2 : 1;
-      uint32_t hold[KH][32];
-#pragma unroll
-      for (int kb = 0; kb < C::KB; ++kb) {
+      // ---- act 1: first owned block (h) into slot h, second (h + 2) held
+      uint32_t hold[32];
+      if (h < C::KB) {
         uint32_t hp[32];
-        tanh_block64(tmem + lane + (uint32_t)(kb * 64), hp);
-        if (kb < 2) {
-          store_row_sw128(a2 + (uint32_t)kb * C::SLOT + (uint32_t)r * 128u, swz, hp);
-        } else {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) hold[kb - 2][i] = hp[i];
-        }
+        tanh_block64(tmem + lane + (uint32_t)(h * 64), hp);
+        store_row_sw128(slots + (uint32_t)h * C::SLOT + my_row, swz, hp);
+        if (C::KB == 4) tanh_block64(tmem + lane + (uint32_t)((h + 2) * 64), hold);
       }
       tc::fence_async_smem();
       tc::fence_before_sync();
-      tc::wg_sync(bar_id);  // every lane has read z1 and written K-blocks 0, 1
-      // ---- layer 2: bias MMA, then one K-block of 64 at a time through the slots
+      grp_sync(bar_id);  // every lane has read z1; K-blocks 0, 1 are in their slots
+      if (issuer) {
+        tc::fence_after_sync();
+        tc::mma_bf16(tmem, desc_a1, desc_bb, idesc2, false);  // + b2
 #pragma unroll
-      for (int kb = 0; kb < C::KB; ++kb) {
-        const int s = kb & 1;
-        const uint32_t slot = a2 + (uint32_t)s * C::SLOT;
-        if (kb >= 2) {
+        for (int kb = 0; kb < C::KBF; ++kb) {
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            tc::mma_bf16(tmem,
+                         tc::smem_desc(slots + kb * C::SLOT + kk * 32, 16, 1024, tc::kSwizzle128B),
+                         tc::smem_desc(sb + C::OFF_W2 + kb * (H1 * 128) + kk * 32, 16, 1024,
+                                       tc::kSwizzle128B),
+                         idesc2, true);
+          tc::mma_commit(bar_slot + kb);
+        }
+      }
+      if (C::KB == 4) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
           WS_WAIT_SLOT(s, 2);
-          store_row_sw128(slot + (uint32_t)r * 128u, swz, hold[kb - 2]);
+          if (h == s) store_row_sw128(slots + (uint32_t)s * C::SLOT + my_row, swz, hold);
           tc::fence_async_smem();
-          tc::wg_sync(bar_id);
-        }
-        if (r == 0) {
-          tc::fence_after_sync();
-          if (kb == 0) tc::mma_bf16(tmem, desc_a1, desc_bb, idesc2, false);
+          grp_sync(bar_id);
+          if (issuer) {
+            tc::fence_after_sync();
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint64_t da = tc::smem_desc(slot + kk * 32, 16, 1024, tc::kSwizzle128B);
-            const uint64_t db = tc::smem_desc(sb + C::OFF_W2 + kb * (H1 * 128) + kk * 32, 16, 1024,
-                                              tc::kSwizzle128B);
-            tc::mma_bf16(tmem, da, db, idesc2, true);
+            for (int kk = 0; kk < 4; ++kk)
+              tc::mma_bf16(tmem,
+                           tc::smem_desc(slots + s * C::SLOT + kk * 32, 16, 1024, tc::kSwizzle128B),
+                           tc::smem_desc(sb + C::OFF_W2 + (s + 2) * (H1 * 128) + kk * 32, 16, 1024,
+                                         tc::kSwizzle128B),
+                           idesc2, true);
+            tc::mma_commit(bar_slot + s);
           }
-          tc::mma_commit(bar_slot + s);
         }
+        if (!ok) break;
       }
-      if (!ok) break;
-      if (C::KB >= 2) WS_WAIT_SLOT((C::KB - 2) & 1, 3);
-      WS_WAIT_SLOT((C::KB - 1) & 1, 4);
+      // drain: the last commits on the used slots cover every MMA of layer 2
+      WS_WAIT_SLOT(0, 3);
+      if (C::KBF == 2) WS_WAIT_SLOT(1, 4);
       tc::fence_after_sync();
-      // ---- act 2 + layer 3, one K-block of h2 at a time through the slots
-#pragma unroll
-      for (int kb = 0; kb < C::KB3; ++kb) {
-        const int s = kb & 1;
-        const uint32_t slot = a2 + (uint32_t)s * C::SLOT;
+      // ---- act 2 + layer 3: first owned block (h) into slot h
+      if (h < C::KB3) {
         uint32_t hp[32];
-        tanh_block64(tmem + lane + (uint32_t)(kb * 64), hp);
-        if (kb >= 2) WS_WAIT_SLOT(s, 5);
-        store_row_sw128(slot + (uint32_t)r * 128u, swz, hp);
-        tc::fence_async_smem();
-        tc::fence_before_sync();
-        tc::wg_sync(bar_id);  // lanes have read columns kb*64.. (and 0..15 at kb = 0)
-        if (r == 0) {
-          tc::fence_after_sync();
+        tanh_block64(tmem + lane + (uint32_t)(h * 64), hp);
+        store_row_sw128(slots + (uint32_t)h * C::SLOT + my_row, swz, hp);
+      }
+      tc::fence_async_smem();
+      tc::fence_before_sync();
+      grp_sync(bar_id);  // columns 0..127 read: layer 3 may write columns 0..15
+      if (issuer) {
+        tc::fence_after_sync();
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint64_t da = tc::smem_desc(slot + kk * 32, 16, 1024, tc::kSwizzle128B);
-            const uint64_t db = tc::smem_desc(sb + C::OFF_B3 + kb * (16 * 128) + kk * 32, 16, 1024,
-                                              tc::kSwizzle128B);
-            tc::mma_bf16(tmem, da, db, idesc3, (kb | kk) != 0);
-          }
-          tc::mma_commit(bar_slot + s);
+        for (int kb = 0; kb < C::KBF3; ++kb) {
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            tc::mma_bf16(tmem,
+                         tc::smem_desc(slots + kb * C::SLOT + kk * 32, 16, 1024, tc::kSwizzle128B),
+                         tc::smem_desc(sb + C::OFF_B3 + kb * (16 * 128) + kk * 32, 16, 1024,
+                                       tc::kSwizzle128B),
+                         idesc3, (kb | kk) != 0);
+          tc::mma_commit(bar_slot + kb);
         }
       }
-      if (!ok) break;
-      if (C::KB3 >= 2) WS_WAIT_SLOT((C::KB3 - 2) & 1, 6);
-      WS_WAIT_SLOT((C::KB3 - 1) & 1, 7);
+      if (C::KB3 == 4) {
+        uint32_t hp[32];
+        tanh_block64(tmem + lane + (uint32_t)((h + 2) * 64), hp);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          WS_WAIT_SLOT(s, 5);
+          if (h == s) store_row_sw128(slots + (uint32_t)s * C::SLOT + my_row, swz, hp);
+          tc::fence_async_smem();
+          tc::fence_before_sync();
+          grp_sync(bar_id);
+          if (issuer) {
+            tc::fence_after_sync();
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              tc::mma_bf16(tmem,
+                           tc::smem_desc(slots + s * C::SLOT + kk * 32, 16, 1024, tc::kSwizzle128B),
+                           tc::smem_desc(sb + C::OFF_B3 + (s + 2) * (16 * 128) + kk * 32, 16, 1024,
+                                         tc::kSwizzle128B),
+                           idesc3, true);
+            tc::mma_commit(bar_slot + s);
+          }
+        }
+        if (!ok) break;
+      }
+      WS_WAIT_SLOT(0, 6);
+      if (C::KBF3 == 2) WS_WAIT_SLOT(1, 7);
       tc::fence_after_sync();
-      float l0, l1;
+      float l0, l1v;
       {
         uint32_t o[16];
         tmem_ld16(tmem + lane, o);
         tc::tmem_wait_ld();
         l0 = (__uint_as_float(o[0]) + __uint_as_float(o[2])) + b3.x;
-        l1 = (__uint_as_float(o[1]) + __uint_as_float(o[3])) + b3.y;
+        l1v = (__uint_as_float(o[1]) + __uint_as_float(o[3])) + b3.y;
       }
-      // ---- sample: a = 0 iff u S < exp(l0 - m)
+      // ---- sample: a = 0 iff u S < exp(l0 - m)  (both halves, identically)
       const float u = u01(draw(d.seed, k, e, 0, kTagAction, 0).x);
-      const float m = fmaxf(l0, l1);
-      const float e0 = expf(l0 - m), e1 = expf(l1 - m);
+      const float m = fmaxf(l0, l1v);
+      const float e0 = expf(l0 - m), e1 = expf(l1v - m);
       const float Ssum = e0 + e1;
       const int a = (u * Ssum < e0) ? 0 : 1;
-      const float lp = ((a ? l1 : l0) - m) - logf(Ssum);
       // ---- env step (explicit Euler, dt = 0.02), reward, done, auto-reset
       const float uf = a ? 10.0f : -10.0f;
       const float xacc = uf - 0.5f * x - 0.1f * v;
@@ -383,7 +432,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const float th2 = th + 0.02f * w, w2 = w + 0.02f * thacc;
       const int t2 = tep + 1;
       const bool done = fabsf(x2) > 2.4f || fabsf(th2) > 0.21f || t2 >= (int)d.episode_limit;
-      if (valid) {
+      if (valid && h == 0) {
+        const float lp = ((a ? l1v : l0) - m) - logf(Ssum);
         const size_t o = (size_t)row * S + e;
         float *ob = d.r_obs + (size_t)row * 4 * S + e;
         ob[0] = x;
@@ -410,9 +460,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         tep = t2;
       }
       row = (row + 1 == R) ? 0 : row + 1;
-      tc::fence_before_sync();  // the TMEM read above precedes the next layer-1 MMA
     }
-    if (valid) {
+    if (valid && h == 0) {
       d.s[e] = x;
       d.s[N + e] = v;
       d.s[2 * N + e] = th;
@@ -421,14 +470,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   }
 #undef WS_WAIT_SLOT
-  if (!ok) {
-    if (r == 0) {
-      // let any MMA still in flight finish before the columns are released
-      tc::mma_commit(bar_drain);
-      tc::mbar_wait(bar_drain, 0, kWaitNs);
-      atomicExch(d.err, 1u);
-      atomicExch(d.err + 1, 100u + fail_site);
-    }
+  if (!ok && issuer) {
+    // let any MMA still in flight finish before the columns are released
+    tc::mma_commit(bar_drain);
+    tc::mbar_wait(bar_drain, 0, kWaitNs);
+    atomicExch(d.err, 1u);
+    atomicExch(d.err + 1, 100u + fail_site);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -492,7 +539,7 @@ int control_tc_default_grid(const Dev &d) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   dispatch(d.pol, [](auto s) { s.attr(); });
   const int tiles = (int)((d.n_envs + kTile - 1) / kTile);
-  const int want = (tiles + kWG - 1) / kWG;
+  const int want = (tiles + kGroups - 1) / kGroups;
   return want < sms ? want : sms;
 }
 
