@@ -37,6 +37,7 @@ struct Dev {
   int tc_mlp;
   const uint8_t *pk[2][3];  // [agent, planner][layer]
   const uint8_t *eimg;      // landscape: packed hi/lo centre image + table (BF16 energy)
+  int mlp3;                 // economy: whole-MLP tensor-core kernel (images in pk[pid][0])
   // ring
   float *r_obs;
   void *r_act;
@@ -89,6 +90,14 @@ cudaError_t launch_dense_tc(const void *X, long ldr, long ldc, int x_bf16, int K
                             const void *packed, int N, void *Y, int y_bf16, int act, long M,
                             uint32_t *err, cudaStream_t st);
 void dense_tc_init();
+
+// ---- BF16 tensor-core three-layer MLP (ws_mlp3_tc.cu) ------------------------------
+bool mlp3_tc_supported(const PolicyShape &p);
+size_t mlp3_tc_packed_bytes(const PolicyShape &p);
+void launch_mlp3_tc_pack(const float *params, const PolicyShape &p, void *packed, cudaStream_t st);
+void launch_mlp3_tc(const float *X, long ldr, long ldc, const void *packed, const PolicyShape &p,
+                    float *out, long M, uint32_t *err, cudaStream_t st);
+void mlp3_tc_init();
 
 // ---- BF16 tensor-core landscape energy (ws_energy_tc.cu) -------------------------
 size_t energy_tc_bytes(int D, int M);

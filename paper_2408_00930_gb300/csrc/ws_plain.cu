@@ -232,7 +232,9 @@ void tc_mlp3(const Dev &d, const float *X, long ldr, long ldc, const PolicyShape
 void policy(const Dev &d, const float *X, long ldr, long ldc, const float *params,
             const PolicyShape &sh, int pid, float *h0, float *h1, float *out, int M,
             cudaStream_t st) {
-  if (d.tc_mlp)
+  if (d.mlp3)
+    launch_mlp3_tc(X, ldr, ldc, d.pk[pid][0], sh, out, M, d.err, st);
+  else if (d.tc_mlp)
     tc_mlp3(d, X, ldr, ldc, sh, pid, h0, h1, out, M, st);
   else
     mlp3(X, ldr, ldc, params, sh, h0, h1, out, M, st);

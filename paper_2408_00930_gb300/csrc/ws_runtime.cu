@@ -101,6 +101,13 @@ bool tc_layers_supported(const PolicyShape &p) {
   return p.w[1] % 8 == 0 && p.w[2] % 8 == 0;
 }
 
+// The economy's policies fit the whole-MLP kernel (all three weight images in
+// shared memory); the landscape's 256-wide layers run one layer per kernel.
+bool use_mlp3(const ws_config *cfg, const PolicyShape &p, const PolicyShape &pp) {
+  return use_tc_layers(cfg) && cfg->env == WS_ENV_ECONOMY && mlp3_tc_supported(p) &&
+         mlp3_tc_supported(pp);
+}
+
 size_t tc_layers_bytes(const PolicyShape &p) {
   size_t n = 0;
   for (int l = 0; l < kMaxLayers; ++l) n += up(dense_tc_packed_bytes(p.w[l], p.w[l + 1]));
@@ -154,6 +161,8 @@ Layout make_layout(const ws_config *cfg, const std::vector<int32_t> &agents) {
   if (use_tc_layers(cfg))
     L.packed_bytes = tc_layers_bytes(L.pol) +
                      (cfg->env == WS_ENV_ECONOMY ? tc_layers_bytes(L.pol_planner) : 0);
+  if (use_mlp3(cfg, L.pol, L.pol_planner))
+    L.packed_bytes = up(mlp3_tc_packed_bytes(L.pol)) + up(mlp3_tc_packed_bytes(L.pol_planner));
   o += up(L.packed_bytes);
   L.env_params_off = o;
   if (cfg->env == WS_ENV_LANDSCAPE) o += up(M * D * 4) + up(M * 4) + up(M * 4);
@@ -250,7 +259,12 @@ void make_dev(ws_ctx *c) {
     d.slot_env = (const int32_t *)(S + L.aux_off + up((N + 1) * 4));
   }
   d.t = (int32_t *)(S + L.t_off);
-  if (use_tc_layers(&cfg)) {
+  if (use_mlp3(&cfg, L.pol, L.pol_planner)) {
+    d.tc_mlp = 1;
+    d.mlp3 = 1;
+    d.pk[0][0] = (const uint8_t *)(S + L.packed_off);
+    d.pk[1][0] = (const uint8_t *)(S + L.packed_off + up(mlp3_tc_packed_bytes(L.pol)));
+  } else if (use_tc_layers(&cfg)) {
     d.tc_mlp = 1;
     size_t o = L.packed_off;
     for (int pid = 0; pid < (cfg.env == WS_ENV_ECONOMY ? 2 : 1); ++pid) {
@@ -399,7 +413,10 @@ ws_status after_params_changed(ws_ctx *c) {
   if (c->cfg.env == WS_ENV_LANDSCAPE) launch_landscape_derive(c->d, c->stream);
   if (c->d.eimg) launch_energy_tc_pack(c->d, (void *)c->d.eimg, c->stream);
   if (use_tc_control(&c->cfg)) launch_control_tc_pack(c->d, c->state + c->L.packed_off, c->stream);
-  if (use_tc_layers(&c->cfg)) {
+  if (c->d.mlp3) {
+    launch_mlp3_tc_pack(c->d.params, c->L.pol, (void *)c->d.pk[0][0], c->stream);
+    launch_mlp3_tc_pack(c->d.params_planner, c->L.pol_planner, (void *)c->d.pk[1][0], c->stream);
+  } else if (use_tc_layers(&c->cfg)) {
     for (int pid = 0; pid < (c->cfg.env == WS_ENV_ECONOMY ? 2 : 1); ++pid) {
       const PolicyShape &p = pid ? c->L.pol_planner : c->L.pol;
       const float *par = pid ? c->d.params_planner : c->d.params;
@@ -497,6 +514,7 @@ ws_status ws_create(const ws_config *cfg, void *state_buf, size_t state_bytes, v
   if (cfg->env == WS_ENV_LANDSCAPE) launch_init_landscape(c->d, cfg->param_seed, c->stream);
   if (use_tc_control(cfg)) c->tc_grid = control_tc_default_grid(c->d);
   if (use_tc_layers(cfg)) dense_tc_init();
+  if (c->d.mlp3) mlp3_tc_init();
   if (use_tc_layers(cfg) && cfg->env == WS_ENV_LANDSCAPE) energy_tc_init((int)cfg->n_gauss);
   s = after_params_changed(c);
   if (s == WS_OK) s = ws_reset(c, cfg->param_seed);
