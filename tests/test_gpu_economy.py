@@ -160,3 +160,35 @@ def test_graph_path_bytes_equal_plain_path(torch):
                                                           W.WS_F_OBS, W.WS_F_REWARD)])
         r.close()
     assert out[0] == out[1]
+
+
+def test_returns_horizon_1000_compensated_fp32_within_1e6(torch):
+    """Returns over a 1,000-step window with no episode end: the float-float scan
+    stays within 1e-6 of the FP64 oracle (relative to sum_t gamma^t |r_t|), so no
+    FP64 is needed on the device.  Saturated policies make every reward
+    deterministic, isolating the scan's own rounding."""
+    counts = np.array([8, 40], np.int32)
+    ap, pp = _forced(7, 3)
+    T = 1000
+    r = econ(W.WS_PATH_BATCHED_FP32, counts=counts, ring=T, limit=5000, seed=5, chunk_steps=100)
+    r.load_raw(W.WS_F_PARAMS, np.concatenate([ap, pp]))
+    r.reset(31)
+    r.rollout(T)
+    r.returns(T)
+    r.sync()
+    G = r.fetch(W.WS_F_RETURN, 0, T).astype(np.float64)
+    rew = r.fetch(W.WS_F_REWARD, 0, T).astype(np.float64)
+    dn = r.fetch(W.WS_F_DONE, 0, T)
+    assert dn.sum() == 0
+    o = oracle.econ_rollout(ap, pp, seed=31, env_ids=np.arange(2), n_agents=counts, n_steps=T,
+                            episode_limit=5000)
+    assert np.array_equal(r.fetch(W.WS_F_WEALTH, 0, T), o["wealth"])
+    gam = float(np.float32(0.99))
+    # end to end against the oracle's FP64 rewards and FP64 scan; the FP32
+    # rounding of each reward contributes ~3e-8 of the scale, the rest is the scan
+    Go = oracle.returns(o["reward"], o["done"], gam)
+    scale = oracle.returns(np.abs(o["reward"]), o["done"], gam)
+    err = np.abs(G - Go) / np.maximum(scale, 1.0)
+    assert err.max() <= 1e-6, err.max()
+    np.testing.assert_allclose(rew, o["reward"], rtol=1e-6, atol=1e-7)
+    r.close()
