@@ -16,14 +16,16 @@
 //            b2 by one K = 16 MMA of the operand row's constant columns against
 //            [0 x 12, b2_hi, b2_lo, 0, 0], then the K-blocks of h1 as their
 //            slots fill; W2^T stays resident in shared memory
-//   layer 3  logits = tanh(z2) W3: h2 = tanh(z2) streamed back through the slots,
-//            N = 16 MMA with W3 split hi/lo (rows W3_hi[:,0], W3_hi[:,1],
-//            W3_lo[:,0], W3_lo[:,1]) into TMEM columns already read; + b3
-//   then     categorical sample (Philox), Euler step, reward, done, auto-reset
-//            (both halves, identically: each keeps the state it needs) and the
-//            time-major record write (half 0).
+//   layer 3  logits = tanh(z2) W3 + b3 on the CUDA cores: each half reads its
+//            blocks of z2 from TMEM, applies tanh (bf16x2) and accumulates its
+//            partial dot products with W3 (FP32, packed f32x2 FMAs, W3 read as
+//            shared-memory broadcasts); half 1 hands its partial to half 0
+//   then     half 0: categorical sample (Philox), Euler step, reward, done,
+//            auto-reset, the time-major record write and the next operand row.
 // Two threads per row give 16 warps per SM, so that one warp's MUFU/TMEM
 // latency overlaps another's work; the per-thread epilogue work halves.
+// Tiles go to CTAs round-robin, group 0's turn first, so that every SM
+// receives either floor or ceil of tiles / SMs.
 #include "ws_kernels.cuh"
 #include "ws_tc.cuh"
 
@@ -45,36 +47,38 @@ struct CtrlTc {
   static constexpr int KB = H0 / 64;               // layer-2 K-blocks (1, 2 or 4)
   static constexpr int KB3 = H1 / 64;              // layer-3 K-blocks (1, 2 or 4)
   static constexpr int KBF = KB < 2 ? KB : 2;      // K-blocks in flight at first (slots)
-  static constexpr int KBF3 = KB3 < 2 ? KB3 : 2;
   static constexpr int W2_BYTES = KB * H1 * 128;   // B of layer 2, SW128, K-blocks of 64
-  static constexpr int B3_BYTES = KB3 * 16 * 128;  // B of layer 3 (N = 16), SW128
   static constexpr int B1_BYTES = H0 * 32;         // B of layer 1, no swizzle, K = 16
   static constexpr int BB_BYTES = H1 * 32;         // B of the b2 MMA, no swizzle, K = 16
+  static constexpr int W3_BYTES = H1 * 8;          // W3 as float4 per unit pair (FP32)
   static constexpr int B3V_BYTES = 16;             // b3
-  // packed global image: [W2 | B3 | B1 | BB | b3]
+  // packed global image: [W2 | B1 | BB | W3 | b3]
   static constexpr int PK_W2 = 0;
-  static constexpr int PK_B3 = PK_W2 + W2_BYTES;
-  static constexpr int PK_B1 = PK_B3 + B3_BYTES;
+  static constexpr int PK_B1 = PK_W2 + W2_BYTES;
   static constexpr int PK_BB = PK_B1 + B1_BYTES;
-  static constexpr int PK_B3V = PK_BB + BB_BYTES;
+  static constexpr int PK_W3 = PK_BB + BB_BYTES;
+  static constexpr int PK_B3V = PK_W3 + W3_BYTES;
   static constexpr int PACKED = PK_B3V + B3V_BYTES;
   // shared memory (from a 1024-aligned base)
   static constexpr int SLOT = 128 * 128;
   static constexpr int OFF_W2 = 0;
-  static constexpr int OFF_B3 = OFF_W2 + W2_BYTES;
-  static constexpr int OFF_SL = OFF_B3 + B3_BYTES;  // [group][2 slots]
-  static constexpr int OFF_B1 = OFF_SL + kGroups * 2 * SLOT;
-  static constexpr int OFF_BB = OFF_B1 + B1_BYTES;  // B1 then BB, contiguous as packed
-  static constexpr int OFF_A1 = OFF_BB + BB_BYTES;  // [group] layer-1 operand, 4 KB each
-  static constexpr int OFF_B3V = OFF_A1 + kGroups * 128 * 32;
-  static constexpr int OFF_BAR = OFF_B3V + B3V_BYTES;
-  static constexpr int N_BAR = 4;  // per group: layer 1, slot 0, slot 1, drain
+  static constexpr int OFF_SL = OFF_W2 + W2_BYTES;  // [group][2 slots]
+  static constexpr int OFF_A1 = OFF_SL + kGroups * 2 * SLOT;  // [group] layer-1 operand, 4 KB each
+  static constexpr int OFF_B1 = OFF_A1 + kGroups * 128 * 32;
+  static constexpr int OFF_BB = OFF_B1 + B1_BYTES;  // B1, BB, W3, b3 contiguous as packed
+  static constexpr int OFF_W3 = OFF_BB + BB_BYTES;
+  static constexpr int OFF_B3V = OFF_W3 + W3_BYTES;
+  static constexpr int OFF_XCH = OFF_B3V + B3V_BYTES;  // [group][row] half 1's logits
+  static constexpr int OFF_BAR = OFF_XCH + kGroups * 128 * 8;
+  static constexpr int N_BAR = 5;  // per group: layer 1, slot 0, slot 1, layer 2 done, error drain
   static constexpr int OFF_TM = OFF_BAR + kGroups * N_BAR * 8;
   static constexpr int SMEM_NEED = OFF_TM + 16 + 1024;
   // at least 120 KB: one CTA per SM, so its 512 TMEM columns are uncontended
   static constexpr int SMEM = SMEM_NEED > 120 * 1024 ? SMEM_NEED : 120 * 1024;
   static_assert(SMEM_NEED <= 232448, "shared memory over the 227 KB per-CTA limit");
-  static_assert(OFF_SL % 1024 == 0 && OFF_B3 % 1024 == 0, "SW128 operands need 1 KB alignment");
+  static_assert(OFF_SL % 1024 == 0, "SW128 operands need 1 KB alignment");
+  static_assert(OFF_A1 % 128 == 0 && OFF_B1 % 128 == 0 && OFF_BB % 128 == 0 && OFF_W3 % 16 == 0,
+                "operand alignment");
 };
 
 __device__ __forceinline__ uint16_t bf16_bits(float f) {
@@ -110,17 +114,14 @@ __global__ void k_ctrl_tc_pack(const float *__restrict__ params, uint8_t *__rest
     const int n = i / H0, k = i % H0;
     *(uint16_t *)(packed + C::PK_W2 + sw128_off(n, k, H1)) = bf16_bits(W2[(size_t)k * H1 + n]);
   }
-  // layer 3: rows W3_hi[:,0], W3_hi[:,1], W3_lo[:,0], W3_lo[:,1], zeros
-  for (int i = tid; i < 16 * H1; i += stride) {
-    const int n = i / H1, k = i % H1;
-    float v = 0.f;
-    if (n < 2) {
-      v = bf16_val(W3[2 * k + n]);
-    } else if (n < 4) {
-      const float w = W3[2 * k + (n - 2)];
-      v = bf16_val(w - bf16_val(w));
-    }
-    *(uint16_t *)(packed + C::PK_B3 + sw128_off(n, k, 16)) = bf16_bits(v);
+  // layer 3: float4 {W3[2i][0], W3[2i+1][0], W3[2i][1], W3[2i+1][1]} per unit pair i
+  for (int i = tid; i < H1 / 2; i += stride) {
+    float4 q;
+    q.x = W3[2 * (2 * i) + 0];
+    q.y = W3[2 * (2 * i + 1) + 0];
+    q.z = W3[2 * (2 * i) + 1];
+    q.w = W3[2 * (2 * i + 1) + 1];
+    *(float4 *)(packed + C::PK_W3 + 16 * i) = q;
   }
   // layer 1 row n: [W1_hi[0..3][n], W1_hi[0..3][n], W1_lo[0..3][n], b1_hi, b1_lo, 0, 0]
   for (int i = tid; i < H0 * 16; i += stride) {
@@ -172,14 +173,60 @@ __device__ __forceinline__ void tanh_block64(uint32_t taddr, uint32_t (&hp)[32])
   }
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
+// 64 accumulator columns at taddr rounded to packed bf16x2 (tanh applied later).
+__device__ __forceinline__ void pack_block64(uint32_t taddr, uint32_t (&zp)[32]) {
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    uint32_t z[32];
+    tc::tmem_ld32(taddr + half * 32, z);
+    tc::tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      zp[half * 16 + i] = tc::pack_bf16x2(__uint_as_float(z[2 * i]), __uint_as_float(z[2 * i + 1]));
+  }
+}
+
+__device__ __forceinline__ uint64_t f2(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 unf2(uint64_t v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ float4 lds128f(uint32_t addr) {
+  float4 v;
+  asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+  return v;
+}
+
+// Layer 3 over one 64-unit block: tanh of the block's z2 columns (bf16x2)
+// against W3 in FP32.  acc0 / acc1 hold (even-unit, odd-unit) partial sums of
+// logit 0 / logit 1; w3 is the block's 32 float4 {W3[k][0], W3[k+1][0],
+// W3[k][1], W3[k+1][1]} (k even).
+__device__ __forceinline__ void layer3_block(uint32_t taddr, uint32_t w3, uint64_t &acc0,
+                                             uint64_t &acc1) {
+  uint32_t hp[32];
+  tanh_block64(taddr, hp);
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const float4 q = lds128f(w3 + 16u * (uint32_t)j);
+    const uint64_t hv = f2(tc::bf16_lo(hp[j]), tc::bf16_hi(hp[j]));
+    acc0 = fma2(hv, f2(q.x, q.y), acc0);
+    acc1 = fma2(hv, f2(q.z, q.w), acc1);
+  }
+}
+
+// Barrier of the two warps (one per half) that serve the same 32 rows.
+__device__ __forceinline__ void pair_sync(uint32_t id) {
+  asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
 }
 
 // Group-wide barrier (256 threads) and AND-vote.
@@ -210,18 +257,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int tid = threadIdx.x, warp = tid >> 5;
   const int g = tid >> 8, h = (tid >> 7) & 1, r = tid & 127;
   uint64_t *bars = (uint64_t *)(sm + C::OFF_BAR) + g * C::N_BAR;
-  uint64_t *bar_l1 = bars, *bar_slot = bars + 1, *bar_drain = bars + 3;
+  uint64_t *bar_l1 = bars, *bar_slot = bars + 1, *bar_fin = bars + 3, *bar_drain = bars + 4;
   uint32_t *tm_holder = (uint32_t *)(sm + C::OFF_TM);
 
   // Stage the packed operands into shared memory.
   {
     const uint4 *src = (const uint4 *)(packed + C::PK_W2);
-    uint4 *dst = (uint4 *)(sm + C::OFF_W2);  // W2 then B3, contiguous in both
-    for (int i = tid; i < (C::W2_BYTES + C::B3_BYTES) / 16; i += kThreads) dst[i] = __ldg(src + i);
+    uint4 *dst = (uint4 *)(sm + C::OFF_W2);
+    for (int i = tid; i < C::W2_BYTES / 16; i += kThreads) dst[i] = __ldg(src + i);
     src = (const uint4 *)(packed + C::PK_B1);
-    dst = (uint4 *)(sm + C::OFF_B1);  // B1 then BB, contiguous in both
-    for (int i = tid; i < (C::B1_BYTES + C::BB_BYTES) / 16; i += kThreads) dst[i] = __ldg(src + i);
-    if (tid == 0) *(uint4 *)(sm + C::OFF_B3V) = __ldg((const uint4 *)(packed + C::PK_B3V));
+    dst = (uint4 *)(sm + C::OFF_B1);  // B1, BB, W3, b3: contiguous in both
+    constexpr int kSmall = (C::B1_BYTES + C::BB_BYTES + C::W3_BYTES + C::B3V_BYTES) / 16;
+    for (int i = tid; i < kSmall; i += kThreads) dst[i] = __ldg(src + i);
   }
   if (tid == 0) {
     uint64_t *all = (uint64_t *)(sm + C::OFF_BAR);
@@ -237,21 +284,23 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = *tm_holder + (uint32_t)g * 256u;
   const uint32_t lane = (uint32_t)((warp & 3) * 32) << 16;
   const uint32_t bar_id = 1u + (uint32_t)g;
+  const uint32_t pair_id = 3u + 4u * (uint32_t)g + (uint32_t)(warp & 3);
   const uint32_t slots = sb + C::OFF_SL + (uint32_t)g * 2 * C::SLOT;
   const uint32_t swz = (uint32_t)(r & 7);
   const uint32_t my_row = (uint32_t)r * 128u;
   const uint32_t a1 = sb + C::OFF_A1 + (uint32_t)g * 128 * 32;
   const uint32_t a1_row = a1 + (uint32_t)(r >> 3) * 256u + (uint32_t)(r & 7) * 16u;
+  const uint32_t w3s = sb + C::OFF_W3;
+  const uint32_t xch = sb + C::OFF_XCH + (uint32_t)g * 128 * 8 + (uint32_t)r * 8;
   const uint64_t desc_a1 = tc::smem_desc(a1, 128, 256, tc::kSwizzleNone);
   const uint64_t desc_b1 = tc::smem_desc(sb + C::OFF_B1, 128, 256, tc::kSwizzleNone);
   const uint64_t desc_bb = tc::smem_desc(sb + C::OFF_BB, 128, 256, tc::kSwizzleNone);
   constexpr uint32_t idesc1 = tc::idesc_bf16_f32(128, H0);
   constexpr uint32_t idesc2 = tc::idesc_bf16_f32(128, H1);
-  constexpr uint32_t idesc3 = tc::idesc_bf16_f32(128, 16);
   const float4 b3 = *(const float4 *)(sm + C::OFF_B3V);
   const bool issuer = (r == 0 && h == 0);
 
-  uint32_t ph_l1 = 0u, ph[2] = {0u, 0u};
+  uint32_t ph_l1 = 0u, ph_fin = 0u, ph[2] = {0u, 0u};
   bool ok = true;
   uint32_t fail_site = 0;
   const uint64_t k0 = d.k[0];
@@ -270,13 +319,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     }                                                                                 \
   }
 
-  for (int tile = (int)blockIdx.x * kGroups + g; ok && tile < n_tiles;
-       tile += (int)gridDim.x * kGroups) {
+  for (int tile = (int)blockIdx.x + (int)gridDim.x * g; ok && tile < n_tiles;
+       tile += kGroups * (int)gridDim.x) {
     const uint32_t e = (uint32_t)tile * kTile + (uint32_t)r;
     const bool valid = e < N;
     float x = 0.f, v = 0.f, th = 0.f, w = 0.f;
     int tep = 0;
-    if (valid) {
+    if (valid && h == 0) {
       x = d.s[e];
       v = d.s[N + e];
       th = d.s[2 * N + e];
@@ -286,16 +335,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t row = row0;
     for (uint32_t j = 0; j < n_steps; ++j) {
       const uint32_t k = (uint32_t)(k0 + j);
-      // ---- layer 1 operand row [s_hi | s_lo | s_hi | 1 1 0 0] (half h writes core h)
-      {
+      // ---- layer 1 operand row [s_hi | s_lo | s_hi | 1 1 0 0] (half 0 holds the state)
+      if (h == 0) {
         const float xh = bf16_val(x), vh = bf16_val(v), thh = bf16_val(th), wh = bf16_val(w);
         const uint32_t hi01 = tc::pack_bf16x2(xh, vh), hi23 = tc::pack_bf16x2(thh, wh);
-        if (h == 0) {
-          tc::sts128(a1_row, hi01, hi23, tc::pack_bf16x2(x - xh, v - vh),
-                     tc::pack_bf16x2(th - thh, w - wh));
-        } else {
-          tc::sts128(a1_row + 128, hi01, hi23, tc::pack_bf16x2(1.f, 1.f), 0u);
-        }
+        tc::sts128(a1_row, hi01, hi23, tc::pack_bf16x2(x - xh, v - vh),
+                   tc::pack_bf16x2(th - thh, w - wh));
+        tc::sts128(a1_row + 128, hi01, hi23, tc::pack_bf16x2(1.f, 1.f), 0u);
       }
       tc::fence_async_smem();
       tc::fence_before_sync();  // (also orders the last step's TMEM reads before the MMA)
@@ -309,13 +355,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       ph_l1 ^= 1u;
       if (!ok) { fail_site = 1; break; }
       tc::fence_after_sync();
-      // ---- act 1: first owned block (h) into slot h, second (h + 2) held
+      // ---- act 1: first owned block (h) into slot h; the second (h + 2) is read
+      // now (layer 2 overwrites these columns) and its tanh taken while the
+      // first layer-2 MMAs run
       uint32_t hold[32];
       if (h < C::KB) {
         uint32_t hp[32];
         tanh_block64(tmem + lane + (uint32_t)(h * 64), hp);
         store_row_sw128(slots + (uint32_t)h * C::SLOT + my_row, swz, hp);
-        if (C::KB == 4) tanh_block64(tmem + lane + (uint32_t)((h + 2) * 64), hold);
+        if (C::KB == 4) pack_block64(tmem + lane + (uint32_t)((h + 2) * 64), hold);
       }
       tc::fence_async_smem();
       tc::fence_before_sync();
@@ -332,10 +380,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                          tc::smem_desc(sb + C::OFF_W2 + kb * (H1 * 128) + kk * 32, 16, 1024,
                                        tc::kSwizzle128B),
                          idesc2, true);
-          tc::mma_commit(bar_slot + kb);
+          if (C::KB == 4) tc::mma_commit(bar_slot + kb);  // the slot may be refilled
         }
+        if (C::KB != 4) tc::mma_commit(bar_fin);
       }
       if (C::KB == 4) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) hold[i] = tc::tanh_bf16x2(hold[i]);
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
           WS_WAIT_SLOT(s, 2);
@@ -351,113 +402,72 @@ __global__ void __launch_bounds__(kThreads, 1)
                            tc::smem_desc(sb + C::OFF_W2 + (s + 2) * (H1 * 128) + kk * 32, 16, 1024,
                                          tc::kSwizzle128B),
                            idesc2, true);
-            tc::mma_commit(bar_slot + s);
+            if (s == 1) tc::mma_commit(bar_fin);  // covers every MMA of layer 2
           }
         }
         if (!ok) break;
       }
-      // drain: the last commits on the used slots cover every MMA of layer 2
-      WS_WAIT_SLOT(0, 3);
-      if (C::KBF == 2) WS_WAIT_SLOT(1, 4);
+      // drain: the one commit after the last MMA covers every MMA of layer 2
+      ok = grp_all(bar_id, tc::mbar_wait(bar_fin, ph_fin, kWaitNs));
+      ph_fin ^= 1u;
+      if (!ok) { fail_site = 3; break; }
       tc::fence_after_sync();
-      // ---- act 2 + layer 3: first owned block (h) into slot h
-      if (h < C::KB3) {
-        uint32_t hp[32];
-        tanh_block64(tmem + lane + (uint32_t)(h * 64), hp);
-        store_row_sw128(slots + (uint32_t)h * C::SLOT + my_row, swz, hp);
-      }
-      tc::fence_async_smem();
-      tc::fence_before_sync();
-      grp_sync(bar_id);  // columns 0..127 read: layer 3 may write columns 0..15
-      if (issuer) {
-        tc::fence_after_sync();
-#pragma unroll
-        for (int kb = 0; kb < C::KBF3; ++kb) {
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk)
-            tc::mma_bf16(tmem,
-                         tc::smem_desc(slots + kb * C::SLOT + kk * 32, 16, 1024, tc::kSwizzle128B),
-                         tc::smem_desc(sb + C::OFF_B3 + kb * (16 * 128) + kk * 32, 16, 1024,
-                                       tc::kSwizzle128B),
-                         idesc3, (kb | kk) != 0);
-          tc::mma_commit(bar_slot + kb);
+      // ---- act 2 + layer 3 on the CUDA cores: blocks h and h + 2
+      uint64_t acc0 = 0ull, acc1 = 0ull;  // (+0.f, +0.f) pairs
+      if (h < C::KB3)
+        layer3_block(tmem + lane + (uint32_t)(h * 64), w3s + (uint32_t)h * 512u, acc0, acc1);
+      if (h + 2 < C::KB3)
+        layer3_block(tmem + lane + (uint32_t)((h + 2) * 64), w3s + (uint32_t)(h + 2) * 512u, acc0,
+                     acc1);
+      const float2 pa = unf2(acc0), pb = unf2(acc1);
+      const float p0 = pa.x + pa.y, p1 = pb.x + pb.y;
+      if (h == 1) asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(xch), "f"(p0), "f"(p1) : "memory");
+      pair_sync(pair_id);
+      if (h == 0) {
+        float q0, q1;
+        asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(q0), "=f"(q1) : "r"(xch) : "memory");
+        const float l0 = (p0 + q0) + b3.x, l1v = (p1 + q1) + b3.y;
+        // ---- sample: a = 0 iff u S < exp(l0 - m)
+        const float u = u01(draw(d.seed, k, e, 0, kTagAction, 0).x);
+        const float m = fmaxf(l0, l1v);
+        const float e0 = expf(l0 - m), e1 = expf(l1v - m);
+        const float Ssum = e0 + e1;
+        const int a = (u * Ssum < e0) ? 0 : 1;
+        // ---- env step (explicit Euler, dt = 0.02), reward, done, auto-reset
+        const float uf = a ? 10.0f : -10.0f;
+        const float xacc = uf - 0.5f * x - 0.1f * v;
+        const float thacc = 9.8f * sinf(th) - 0.3f * cosf(th) * uf;
+        const float x2 = x + 0.02f * v, v2 = v + 0.02f * xacc;
+        const float th2 = th + 0.02f * w, w2 = w + 0.02f * thacc;
+        const int t2 = tep + 1;
+        const bool done = fabsf(x2) > 2.4f || fabsf(th2) > 0.21f || t2 >= (int)d.episode_limit;
+        if (valid) {
+          const float lp = ((a ? l1v : l0) - m) - logf(Ssum);
+          const size_t o = (size_t)row * S + e;
+          float *ob = d.r_obs + (size_t)row * 4 * S + e;
+          ob[0] = x;
+          ob[S] = v;
+          ob[2 * (size_t)S] = th;
+          ob[3 * (size_t)S] = w;
+          ((int32_t *)d.r_act)[o] = a;
+          d.r_logp[o] = lp;
+          d.r_rew[o] = 1.0f;
+          d.r_done[o] = (uint8_t)done;
         }
-      }
-      if (C::KB3 == 4) {
-        uint32_t hp[32];
-        tanh_block64(tmem + lane + (uint32_t)((h + 2) * 64), hp);
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          WS_WAIT_SLOT(s, 5);
-          if (h == s) store_row_sw128(slots + (uint32_t)s * C::SLOT + my_row, swz, hp);
-          tc::fence_async_smem();
-          tc::fence_before_sync();
-          grp_sync(bar_id);
-          if (issuer) {
-            tc::fence_after_sync();
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-              tc::mma_bf16(tmem,
-                           tc::smem_desc(slots + s * C::SLOT + kk * 32, 16, 1024, tc::kSwizzle128B),
-                           tc::smem_desc(sb + C::OFF_B3 + (s + 2) * (16 * 128) + kk * 32, 16, 1024,
-                                         tc::kSwizzle128B),
-                           idesc3, true);
-            tc::mma_commit(bar_slot + s);
-          }
+        if (done) {
+          const uint4 rr = draw(d.seed, k, e, 0, kTagReset, 0);
+          x = uniform(rr.x, -0.05f, 0.05f);
+          v = uniform(rr.y, -0.05f, 0.05f);
+          th = uniform(rr.z, -0.05f, 0.05f);
+          w = uniform(rr.w, -0.05f, 0.05f);
+          tep = 0;
+        } else {
+          x = x2;
+          v = v2;
+          th = th2;
+          w = w2;
+          tep = t2;
         }
-        if (!ok) break;
-      }
-      WS_WAIT_SLOT(0, 6);
-      if (C::KBF3 == 2) WS_WAIT_SLOT(1, 7);
-      tc::fence_after_sync();
-      float l0, l1v;
-      {
-        uint32_t o[16];
-        tmem_ld16(tmem + lane, o);
-        tc::tmem_wait_ld();
-        l0 = (__uint_as_float(o[0]) + __uint_as_float(o[2])) + b3.x;
-        l1v = (__uint_as_float(o[1]) + __uint_as_float(o[3])) + b3.y;
-      }
-      // ---- sample: a = 0 iff u S < exp(l0 - m)  (both halves, identically)
-      const float u = u01(draw(d.seed, k, e, 0, kTagAction, 0).x);
-      const float m = fmaxf(l0, l1v);
-      const float e0 = expf(l0 - m), e1 = expf(l1v - m);
-      const float Ssum = e0 + e1;
-      const int a = (u * Ssum < e0) ? 0 : 1;
-      // ---- env step (explicit Euler, dt = 0.02), reward, done, auto-reset
-      const float uf = a ? 10.0f : -10.0f;
-      const float xacc = uf - 0.5f * x - 0.1f * v;
-      const float thacc = 9.8f * sinf(th) - 0.3f * cosf(th) * uf;
-      const float x2 = x + 0.02f * v, v2 = v + 0.02f * xacc;
-      const float th2 = th + 0.02f * w, w2 = w + 0.02f * thacc;
-      const int t2 = tep + 1;
-      const bool done = fabsf(x2) > 2.4f || fabsf(th2) > 0.21f || t2 >= (int)d.episode_limit;
-      if (valid && h == 0) {
-        const float lp = ((a ? l1v : l0) - m) - logf(Ssum);
-        const size_t o = (size_t)row * S + e;
-        float *ob = d.r_obs + (size_t)row * 4 * S + e;
-        ob[0] = x;
-        ob[S] = v;
-        ob[2 * (size_t)S] = th;
-        ob[3 * (size_t)S] = w;
-        ((int32_t *)d.r_act)[o] = a;
-        d.r_logp[o] = lp;
-        d.r_rew[o] = 1.0f;
-        d.r_done[o] = (uint8_t)done;
-      }
-      if (done) {
-        const uint4 rr = draw(d.seed, k, e, 0, kTagReset, 0);
-        x = uniform(rr.x, -0.05f, 0.05f);
-        v = uniform(rr.y, -0.05f, 0.05f);
-        th = uniform(rr.z, -0.05f, 0.05f);
-        w = uniform(rr.w, -0.05f, 0.05f);
-        tep = 0;
-      } else {
-        x = x2;
-        v = v2;
-        th = th2;
-        w = w2;
-        tep = t2;
       }
       row = (row + 1 == R) ? 0 : row + 1;
     }
@@ -539,8 +549,7 @@ int control_tc_default_grid(const Dev &d) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   dispatch(d.pol, [](auto s) { s.attr(); });
   const int tiles = (int)((d.n_envs + kTile - 1) / kTile);
-  const int want = (tiles + kGroups - 1) / kGroups;
-  return want < sms ? want : sms;
+  return tiles < sms ? tiles : sms;
 }
 
 }  // namespace ws
