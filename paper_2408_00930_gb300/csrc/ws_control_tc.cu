@@ -5,27 +5,30 @@
 // store all on the GPU; envs independent, policy referenced from GPU memory).
 //
 // Work split: a CTA holds two groups of 256 threads; each group owns a tile of
-// 128 envs.  Env row r of a tile is served by two threads ("halves" h = 0, 1;
-// both in warps that may reach TMEM lane r), which split the row's hidden
-// units: half h owns the 64-unit K-blocks h and h + 2.  Per step and tile:
+// 128 envs and 256 of the CTA's 512 TMEM columns.  Env row r of a tile is served
+// by two threads ("halves" h = 0, 1; both in warps that may reach TMEM lane r),
+// which split the row's hidden units by 64-unit blocks.  Per step and tile:
 //   layer 1  z1 = s W1 + b1 on the tensor core, K = 16: the operand row
 //            [s_hi, s_lo, s_hi, 1, 1, 0, 0] against [W1_hi; W1_hi; W1_lo; b1_hi;
 //            b1_lo] keeps FP32-level accuracy (missing term s_lo W1_lo ~ 2^-16);
-//            h1 = tanh(z1) as packed bf16x2 into two 16 KB 128B-swizzled slots
-//   layer 2  z2 = h1 W2 + b2 on the tensor core into the same 256 TMEM columns:
-//            b2 by one K = 16 MMA of the operand row's constant columns against
-//            [0 x 12, b2_hi, b2_lo, 0, 0], then the K-blocks of h1 as their
-//            slots fill; W2^T stays resident in shared memory
-//   layer 3  logits = tanh(z2) W3 + b3 on the CUDA cores: each half reads its
-//            blocks of z2 from TMEM, applies tanh (bf16x2) and accumulates its
+//            z1 lands in TMEM columns [0, H0)
+//   act 1    h1 = tanh(z1) as packed bf16x2, written back into TMEM columns
+//            [128, 128 + H0/2): the A operand of layer 2 stays in tensor memory
+//            (two bf16 per 32-bit column), so it never touches shared memory
+//   layer 2  z2 = h1 W2 + b2 in passes of up to 128 output units into TMEM
+//            columns [0, 128): b2 by one K = 16 MMA of the operand row's constant
+//            columns against [0 x 12, b2_hi, b2_lo, 0, 0], then H0 / 16 MMAs with
+//            A read from tensor memory and W2^T resident in shared memory
+//   layer 3  logits = tanh(z2) W3 + b3 on the CUDA cores after each pass: each
+//            half reads its block of z2, applies tanh (bf16x2) and accumulates its
 //            partial dot products with W3 (FP32, packed f32x2 FMAs, W3 read as
 //            shared-memory broadcasts); half 1 hands its partial to half 0
 //   then     half 0: categorical sample (Philox), Euler step, reward, done,
 //            auto-reset, the time-major record write and the next operand row.
 // Two threads per row give 16 warps per SM, so that one warp's MUFU/TMEM
-// latency overlaps another's work; the per-thread epilogue work halves.
-// Tiles go to CTAs round-robin, group 0's turn first, so that every SM
-// receives either floor or ceil of tiles / SMs.
+// latency overlaps another's work, and the two groups' tensor and tanh phases
+// interleave.  Tiles go to CTAs round-robin, group 0's turn first, so that
+// every SM receives either floor or ceil of tiles / SMs.
 #include "ws_kernels.cuh"
 #include "ws_tc.cuh"
 
@@ -44,14 +47,16 @@ template <int H0, int H1>
 struct CtrlTc {
   static_assert(H0 == 64 || H0 == 128 || H0 == 256, "layer-2 K must be 64, 128 or 256");
   static_assert(H1 == 64 || H1 == 128 || H1 == 256, "layer-3 K (= H1) must be 64, 128 or 256");
-  static constexpr int KB = H0 / 64;               // layer-2 K-blocks (1, 2 or 4)
-  static constexpr int KB3 = H1 / 64;              // layer-3 K-blocks (1, 2 or 4)
-  static constexpr int KBF = KB < 2 ? KB : 2;      // K-blocks in flight at first (slots)
-  static constexpr int W2_BYTES = KB * H1 * 128;   // B of layer 2, SW128, K-blocks of 64
-  static constexpr int B1_BYTES = H0 * 32;         // B of layer 1, no swizzle, K = 16
-  static constexpr int BB_BYTES = H1 * 32;         // B of the b2 MMA, no swizzle, K = 16
-  static constexpr int W3_BYTES = H1 * 8;          // W3 as float4 per unit pair (FP32)
-  static constexpr int B3V_BYTES = 16;             // b3
+  static constexpr int KB = H0 / 64;                // layer-2 K-blocks (1, 2 or 4)
+  static constexpr int NP = H1 > 128 ? 2 : 1;       // layer-2 passes
+  static constexpr int NPW = H1 / NP;               // output units per pass (64 or 128)
+  static constexpr int KBP = NPW / 64;              // 64-unit blocks per pass (1 or 2)
+  static constexpr uint32_t A_COL = 128;            // TMEM column of the layer-2 A operand
+  static constexpr int W2_BYTES = KB * H1 * 128;    // B of layer 2, SW128, K-blocks of 64
+  static constexpr int B1_BYTES = H0 * 32;          // B of layer 1, no swizzle, K = 16
+  static constexpr int BB_BYTES = H1 * 32;          // B of the b2 MMA, no swizzle, K = 16
+  static constexpr int W3_BYTES = H1 * 8;           // W3 as float4 per unit pair (FP32)
+  static constexpr int B3V_BYTES = 16;              // b3
   // packed global image: [W2 | B1 | BB | W3 | b3]
   static constexpr int PK_W2 = 0;
   static constexpr int PK_B1 = PK_W2 + W2_BYTES;
@@ -60,25 +65,25 @@ struct CtrlTc {
   static constexpr int PK_B3V = PK_W3 + W3_BYTES;
   static constexpr int PACKED = PK_B3V + B3V_BYTES;
   // shared memory (from a 1024-aligned base)
-  static constexpr int SLOT = 128 * 128;
   static constexpr int OFF_W2 = 0;
-  static constexpr int OFF_SL = OFF_W2 + W2_BYTES;  // [group][2 slots]
-  static constexpr int OFF_A1 = OFF_SL + kGroups * 2 * SLOT;  // [group] layer-1 operand, 4 KB each
+  static constexpr int OFF_A1 = OFF_W2 + W2_BYTES;  // [group] layer-1 operand, 4 KB each
   static constexpr int OFF_B1 = OFF_A1 + kGroups * 128 * 32;
   static constexpr int OFF_BB = OFF_B1 + B1_BYTES;  // B1, BB, W3, b3 contiguous as packed
   static constexpr int OFF_W3 = OFF_BB + BB_BYTES;
   static constexpr int OFF_B3V = OFF_W3 + W3_BYTES;
   static constexpr int OFF_XCH = OFF_B3V + B3V_BYTES;  // [group][row] half 1's logits
   static constexpr int OFF_BAR = OFF_XCH + kGroups * 128 * 8;
-  static constexpr int N_BAR = 5;  // per group: layer 1, slot 0, slot 1, layer 2 done, error drain
-  static constexpr int OFF_TM = OFF_BAR + kGroups * N_BAR * 8;
+  static constexpr int N_BAR = 3;  // per group: layer 1, layer-2 pass, error drain
+  static constexpr int OFF_TOK = OFF_BAR + kGroups * N_BAR * 8;  // [group] SFU token barrier
+  static constexpr int OFF_DONE = OFF_TOK + kGroups * 8;         // [group] finished flag
+  static constexpr int OFF_TM = OFF_DONE + kGroups * 4;
   static constexpr int SMEM_NEED = OFF_TM + 16 + 1024;
   // at least 120 KB: one CTA per SM, so its 512 TMEM columns are uncontended
   static constexpr int SMEM = SMEM_NEED > 120 * 1024 ? SMEM_NEED : 120 * 1024;
   static_assert(SMEM_NEED <= 232448, "shared memory over the 227 KB per-CTA limit");
-  static_assert(OFF_SL % 1024 == 0, "SW128 operands need 1 KB alignment");
-  static_assert(OFF_A1 % 128 == 0 && OFF_B1 % 128 == 0 && OFF_BB % 128 == 0 && OFF_W3 % 16 == 0,
+  static_assert(OFF_A1 % 1024 == 0 && OFF_B1 % 128 == 0 && OFF_BB % 128 == 0 && OFF_W3 % 16 == 0,
                 "operand alignment");
+  static_assert(A_COL + H0 / 2 <= 256, "the A operand must fit the group's TMEM columns");
 };
 
 __device__ __forceinline__ uint16_t bf16_bits(float f) {
@@ -150,13 +155,34 @@ __global__ void k_ctrl_tc_pack(const float *__restrict__ params, uint8_t *__rest
   if (tid == 0) *(float4 *)(packed + C::PK_B3V) = make_float4(b3[0], b3[1], 0.f, 0.f);
 }
 
-// Eight 16-byte chunks of one operand row (64 bf16) into a 128B-swizzled slot.
-__device__ __forceinline__ void store_row_sw128(uint32_t row_addr, uint32_t swz,
-                                                const uint32_t (&p)[32]) {
-#pragma unroll
-  for (int ch = 0; ch < 8; ++ch)
-    tc::sts128(row_addr + (((uint32_t)ch ^ swz) << 4), p[ch * 4 + 0], p[ch * 4 + 1], p[ch * 4 + 2],
-               p[ch * 4 + 3]);
+// 32 consecutive 32-bit TMEM columns of this thread's lane from registers.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+      "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
+      "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
+      "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// D[tmem] (+)= A[tmem] * B[smem]^T, issued by one thread.  A: M = 128 rows in
+// the TMEM lanes, K along the columns, two bf16 per 32-bit column (lower K in
+// the low half).
+__device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
+                                            uint32_t idesc, bool accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"((uint32_t)accumulate)
+      : "memory");
 }
 
 // tanh of 64 accumulator columns at taddr, packed bf16x2 (two 32-column loads).
@@ -170,19 +196,6 @@ __device__ __forceinline__ void tanh_block64(uint32_t taddr, uint32_t (&hp)[32])
     for (int i = 0; i < 16; ++i)
       hp[half * 16 + i] =
           tc::tanh_bf16x2(tc::pack_bf16x2(__uint_as_float(z[2 * i]), __uint_as_float(z[2 * i + 1])));
-  }
-}
-
-// 64 accumulator columns at taddr rounded to packed bf16x2 (tanh applied later).
-__device__ __forceinline__ void pack_block64(uint32_t taddr, uint32_t (&zp)[32]) {
-#pragma unroll
-  for (int half = 0; half < 2; ++half) {
-    uint32_t z[32];
-    tc::tmem_ld32(taddr + half * 32, z);
-    tc::tmem_wait_ld();
-#pragma unroll
-    for (int i = 0; i < 16; ++i)
-      zp[half * 16 + i] = tc::pack_bf16x2(__uint_as_float(z[2 * i]), __uint_as_float(z[2 * i + 1]));
   }
 }
 
@@ -224,6 +237,42 @@ __device__ __forceinline__ void layer3_block(uint32_t taddr, uint32_t w3, uint64
   }
 }
 
+// The SFU token.  The two groups of a CTA take turns in their tanh phases (act 1
+// and the layer-3 epilogues): one group's tanh work then runs while the other
+// waits on its tensor-core passes, instead of both groups competing for the SFU
+// at the same time.  tok[g] completes a phase when the other group's eight warps
+// have handed the token over; a group that leaves its tile loop raises its done
+// flag (and hands over once more), after which the other group runs alone.
+struct SfuToken {
+  uint32_t mine, theirs;       // shared addresses of tok[g], tok[1 - g]
+  const volatile uint32_t *their_done;
+  uint32_t ph;
+  bool solo;
+};
+__device__ __forceinline__ void tok_take(SfuToken &t, uint64_t limit_ns) {
+  if (t.solo) return;
+  uint32_t res = 1;  // 1: token, 2: the other group finished, 0: wait limit reached
+  if ((threadIdx.x & 31) == 0) {
+    uint64_t *bar = (uint64_t *)__cvta_shared_to_generic(t.mine);
+    if (!tc::mbar_try_wait(bar, t.ph)) {
+      const uint64_t t0 = tc::global_ns();
+      for (;;) {
+        if (tc::mbar_try_wait(bar, t.ph)) break;
+        if (*t.their_done) { res = 2; break; }
+        if (tc::global_ns() - t0 > limit_ns) { res = 0; break; }
+      }
+    }
+  }
+  res = __shfl_sync(0xffffffffu, res, 0);
+  if (res == 1) t.ph ^= 1u;
+  else t.solo = true;  // the other group is gone (or stuck): no more turns to wait for
+}
+__device__ __forceinline__ void tok_give(const SfuToken &t) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0)
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(t.theirs) : "memory");
+}
+
 // Barrier of the two warps (one per half) that serve the same 32 rows.
 __device__ __forceinline__ void pair_sync(uint32_t id) {
   asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
@@ -257,7 +306,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int tid = threadIdx.x, warp = tid >> 5;
   const int g = tid >> 8, h = (tid >> 7) & 1, r = tid & 127;
   uint64_t *bars = (uint64_t *)(sm + C::OFF_BAR) + g * C::N_BAR;
-  uint64_t *bar_l1 = bars, *bar_slot = bars + 1, *bar_fin = bars + 3, *bar_drain = bars + 4;
+  uint64_t *bar_l1 = bars, *bar_l2 = bars + 1, *bar_drain = bars + 2;
   uint32_t *tm_holder = (uint32_t *)(sm + C::OFF_TM);
 
   // Stage the packed operands into shared memory.
@@ -273,6 +322,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (tid == 0) {
     uint64_t *all = (uint64_t *)(sm + C::OFF_BAR);
     for (int i = 0; i < kGroups * C::N_BAR; ++i) tc::mbar_init(all + i, 1);
+    for (int i = 0; i < kGroups; ++i) {
+      tc::mbar_init((uint64_t *)(sm + C::OFF_TOK) + i, kGroupThreads / 32);
+      ((volatile uint32_t *)(sm + C::OFF_DONE))[i] = 0u;
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tc::tmem_alloc(tm_holder, kTmemCols);
@@ -282,25 +335,25 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc::fence_after_sync();
 
   const uint32_t tmem = *tm_holder + (uint32_t)g * 256u;
+  const uint32_t a_tm = tmem + C::A_COL;  // layer-2 A operand (h1), lane 0
   const uint32_t lane = (uint32_t)((warp & 3) * 32) << 16;
   const uint32_t bar_id = 1u + (uint32_t)g;
   const uint32_t pair_id = 3u + 4u * (uint32_t)g + (uint32_t)(warp & 3);
-  const uint32_t slots = sb + C::OFF_SL + (uint32_t)g * 2 * C::SLOT;
-  const uint32_t swz = (uint32_t)(r & 7);
-  const uint32_t my_row = (uint32_t)r * 128u;
   const uint32_t a1 = sb + C::OFF_A1 + (uint32_t)g * 128 * 32;
   const uint32_t a1_row = a1 + (uint32_t)(r >> 3) * 256u + (uint32_t)(r & 7) * 16u;
   const uint32_t w3s = sb + C::OFF_W3;
   const uint32_t xch = sb + C::OFF_XCH + (uint32_t)g * 128 * 8 + (uint32_t)r * 8;
   const uint64_t desc_a1 = tc::smem_desc(a1, 128, 256, tc::kSwizzleNone);
   const uint64_t desc_b1 = tc::smem_desc(sb + C::OFF_B1, 128, 256, tc::kSwizzleNone);
-  const uint64_t desc_bb = tc::smem_desc(sb + C::OFF_BB, 128, 256, tc::kSwizzleNone);
   constexpr uint32_t idesc1 = tc::idesc_bf16_f32(128, H0);
-  constexpr uint32_t idesc2 = tc::idesc_bf16_f32(128, H1);
+  constexpr uint32_t idesc2 = tc::idesc_bf16_f32(128, C::NPW);
   const float4 b3 = *(const float4 *)(sm + C::OFF_B3V);
   const bool issuer = (r == 0 && h == 0);
 
-  uint32_t ph_l1 = 0u, ph_fin = 0u, ph[2] = {0u, 0u};
+  uint32_t ph_l1 = 0u, ph_l2 = 0u;
+  // group 0 holds the token first (parity 1 of a fresh barrier reads as complete)
+  SfuToken tok{sb + C::OFF_TOK + 8u * (uint32_t)g, sb + C::OFF_TOK + 8u * (uint32_t)(g ^ 1),
+               (const volatile uint32_t *)(sm + C::OFF_DONE) + (g ^ 1), g == 0 ? 1u : 0u, false};
   bool ok = true;
   uint32_t fail_site = 0;
   const uint64_t k0 = d.k[0];
@@ -308,16 +361,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t row0 = (uint32_t)(k0 % R);
   const uint32_t N = d.n_envs, S = d.n_slots;
   const int n_tiles = (int)((N + kTile - 1) / kTile);
-
-#define WS_WAIT_SLOT(s, site)                                                         \
-  {                                                                                   \
-    ok = grp_all(bar_id, tc::mbar_wait(bar_slot + (s), ph[(s)], kWaitNs));            \
-    ph[(s)] ^= 1u;                                                                    \
-    if (!ok) {                                                                        \
-      fail_site = (site);                                                             \
-      break;                                                                          \
-    }                                                                                 \
-  }
 
   for (int tile = (int)blockIdx.x + (int)gridDim.x * g; ok && tile < n_tiles;
        tile += kGroups * (int)gridDim.x) {
@@ -355,70 +398,58 @@ __global__ void __launch_bounds__(kThreads, 1)
       ph_l1 ^= 1u;
       if (!ok) { fail_site = 1; break; }
       tc::fence_after_sync();
-      // ---- act 1: first owned block (h) into slot h; the second (h + 2) is read
-      // now (layer 2 overwrites these columns) and its tanh taken while the
-      // first layer-2 MMAs run
-      uint32_t hold[32];
+      // ---- act 1: h1 block kb -> TMEM columns A_COL + 32 kb.  With H0 = 256, z1
+      // blocks 2 and 3 share columns with the A operand: both halves read them
+      // (and the pair barrier orders those reads) before anything is written.
+      tok_take(tok, kWaitNs);
+      if (C::KB == 4) {
+        uint32_t hp[32];
+        tanh_block64(tmem + lane + (uint32_t)((h + 2) * 64), hp);
+        pair_sync(pair_id);
+        tmem_st32(a_tm + lane + (uint32_t)((h + 2) * 32), hp);
+      }
       if (h < C::KB) {
         uint32_t hp[32];
         tanh_block64(tmem + lane + (uint32_t)(h * 64), hp);
-        store_row_sw128(slots + (uint32_t)h * C::SLOT + my_row, swz, hp);
-        if (C::KB == 4) pack_block64(tmem + lane + (uint32_t)((h + 2) * 64), hold);
+        tmem_st32(a_tm + lane + (uint32_t)(h * 32), hp);
       }
-      tc::fence_async_smem();
-      tc::fence_before_sync();
-      grp_sync(bar_id);  // every lane has read z1; K-blocks 0, 1 are in their slots
-      if (issuer) {
-        tc::fence_after_sync();
-        tc::mma_bf16(tmem, desc_a1, desc_bb, idesc2, false);  // + b2
+      tok_give(tok);
+      tmem_wait_st();
+      // ---- layer 2 in passes of NPW output units; layer 3 after each pass
+      uint64_t acc0 = 0ull, acc1 = 0ull;  // (+0.f, +0.f) pairs
 #pragma unroll
-        for (int kb = 0; kb < C::KBF; ++kb) {
+      for (int p = 0; p < C::NP; ++p) {
+        tc::fence_before_sync();
+        grp_sync(bar_id);  // A complete (p = 0) / the last pass's columns read (p = 1)
+        if (issuer) {
+          tc::fence_after_sync();
+          tc::mma_bf16(tmem, desc_a1,
+                       tc::smem_desc(sb + C::OFF_BB + (uint32_t)(p * C::NPW * 32), 128, 256,
+                                     tc::kSwizzleNone),
+                       idesc2, false);  // b2
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk)
-            tc::mma_bf16(tmem,
-                         tc::smem_desc(slots + kb * C::SLOT + kk * 32, 16, 1024, tc::kSwizzle128B),
-                         tc::smem_desc(sb + C::OFF_W2 + kb * (H1 * 128) + kk * 32, 16, 1024,
-                                       tc::kSwizzle128B),
-                         idesc2, true);
-          if (C::KB == 4) tc::mma_commit(bar_slot + kb);  // the slot may be refilled
-        }
-        if (C::KB != 4) tc::mma_commit(bar_fin);
-      }
-      if (C::KB == 4) {
-#pragma unroll
-        for (int i = 0; i < 32; ++i) hold[i] = tc::tanh_bf16x2(hold[i]);
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          WS_WAIT_SLOT(s, 2);
-          if (h == s) store_row_sw128(slots + (uint32_t)s * C::SLOT + my_row, swz, hold);
-          tc::fence_async_smem();
-          grp_sync(bar_id);
-          if (issuer) {
-            tc::fence_after_sync();
+          for (int kb = 0; kb < C::KB; ++kb) {
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)
-              tc::mma_bf16(tmem,
-                           tc::smem_desc(slots + s * C::SLOT + kk * 32, 16, 1024, tc::kSwizzle128B),
-                           tc::smem_desc(sb + C::OFF_W2 + (s + 2) * (H1 * 128) + kk * 32, 16, 1024,
-                                         tc::kSwizzle128B),
-                           idesc2, true);
-            if (s == 1) tc::mma_commit(bar_fin);  // covers every MMA of layer 2
+              mma_bf16_ts(tmem, a_tm + (uint32_t)(kb * 32 + kk * 8),
+                          tc::smem_desc(sb + C::OFF_W2 + (uint32_t)(kb * (H1 * 128) +
+                                                                   p * C::NPW * 128 + kk * 32),
+                                        16, 1024, tc::kSwizzle128B),
+                          idesc2, true);
           }
+          tc::mma_commit(bar_l2);
         }
-        if (!ok) break;
+        ok = grp_all(bar_id, tc::mbar_wait(bar_l2, ph_l2, kWaitNs));
+        ph_l2 ^= 1u;
+        if (!ok) { fail_site = 2 + (uint32_t)p; break; }
+        tc::fence_after_sync();
+        tok_take(tok, kWaitNs);
+        if (h < C::KBP)
+          layer3_block(tmem + lane + (uint32_t)(h * 64),
+                       w3s + (uint32_t)((p * C::NPW + h * 64) * 8), acc0, acc1);
+        tok_give(tok);
       }
-      // drain: the one commit after the last MMA covers every MMA of layer 2
-      ok = grp_all(bar_id, tc::mbar_wait(bar_fin, ph_fin, kWaitNs));
-      ph_fin ^= 1u;
-      if (!ok) { fail_site = 3; break; }
-      tc::fence_after_sync();
-      // ---- act 2 + layer 3 on the CUDA cores: blocks h and h + 2
-      uint64_t acc0 = 0ull, acc1 = 0ull;  // (+0.f, +0.f) pairs
-      if (h < C::KB3)
-        layer3_block(tmem + lane + (uint32_t)(h * 64), w3s + (uint32_t)h * 512u, acc0, acc1);
-      if (h + 2 < C::KB3)
-        layer3_block(tmem + lane + (uint32_t)((h + 2) * 64), w3s + (uint32_t)(h + 2) * 512u, acc0,
-                     acc1);
+      if (!ok) break;
       const float2 pa = unf2(acc0), pb = unf2(acc1);
       const float p0 = pa.x + pa.y, p1 = pb.x + pb.y;
       if (h == 1) asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(xch), "f"(p0), "f"(p1) : "memory");
@@ -479,7 +510,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       d.t[e] = tep;
     }
   }
-#undef WS_WAIT_SLOT
+  // this group is finished: release the other group from the turn-taking
+  __syncwarp();
+  if ((tid & 31) == 0) {
+    ((volatile uint32_t *)(sm + C::OFF_DONE))[g] = 1u;
+    __threadfence_block();
+  }
+  tok_give(tok);
   if (!ok && issuer) {
     // let any MMA still in flight finish before the columns are released
     tc::mma_commit(bar_drain);
