@@ -71,8 +71,10 @@ struct CtrlTc {
   static constexpr int OFF_BB = OFF_B1 + B1_BYTES;  // B1, BB, W3, b3 contiguous as packed
   static constexpr int OFF_W3 = OFF_BB + BB_BYTES;
   static constexpr int OFF_B3V = OFF_W3 + W3_BYTES;
-  static constexpr int OFF_XCH = OFF_B3V + B3V_BYTES;  // [group][row] half 1's logits
-  static constexpr int OFF_BAR = OFF_XCH + kGroups * 128 * 8;
+  // [group][row] from half 1 to half 0: two logit partials, the action uniform
+  // and the four reset words (8 words, 32 B)
+  static constexpr int OFF_XCH = OFF_B3V + B3V_BYTES;
+  static constexpr int OFF_BAR = OFF_XCH + kGroups * 128 * 32;
   static constexpr int N_BAR = 3;  // per group: layer 1, layer-2 pass, error drain
   static constexpr int OFF_TOK = OFF_BAR + kGroups * N_BAR * 8;  // [group] SFU token barrier
   static constexpr int OFF_DONE = OFF_TOK + kGroups * 8;         // [group] finished flag
@@ -342,9 +344,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t a1 = sb + C::OFF_A1 + (uint32_t)g * 128 * 32;
   const uint32_t a1_row = a1 + (uint32_t)(r >> 3) * 256u + (uint32_t)(r & 7) * 16u;
   const uint32_t w3s = sb + C::OFF_W3;
-  const uint32_t xch = sb + C::OFF_XCH + (uint32_t)g * 128 * 8 + (uint32_t)r * 8;
+  const uint32_t xch = sb + C::OFF_XCH + (uint32_t)g * 128 * 32 + (uint32_t)r * 32;
   const uint64_t desc_a1 = tc::smem_desc(a1, 128, 256, tc::kSwizzleNone);
   const uint64_t desc_b1 = tc::smem_desc(sb + C::OFF_B1, 128, 256, tc::kSwizzleNone);
+  const uint64_t desc_bb0 = tc::smem_desc(sb + C::OFF_BB, 128, 256, tc::kSwizzleNone);
+  const uint64_t desc_w20 = tc::smem_desc(sb + C::OFF_W2, 16, 1024, tc::kSwizzle128B);
   constexpr uint32_t idesc1 = tc::idesc_bf16_f32(128, H0);
   constexpr uint32_t idesc2 = tc::idesc_bf16_f32(128, C::NPW);
   const float4 b3 = *(const float4 *)(sm + C::OFF_B3V);
@@ -417,27 +421,44 @@ __global__ void __launch_bounds__(kThreads, 1)
       tmem_wait_st();
       // ---- layer 2 in passes of NPW output units; layer 3 after each pass
       uint64_t acc0 = 0ull, acc1 = 0ull;  // (+0.f, +0.f) pairs
+      float sin_th = 0.f, cos_th = 0.f;
 #pragma unroll
       for (int p = 0; p < C::NP; ++p) {
         tc::fence_before_sync();
         grp_sync(bar_id);  // A complete (p = 0) / the last pass's columns read (p = 1)
         if (issuer) {
           tc::fence_after_sync();
-          tc::mma_bf16(tmem, desc_a1,
-                       tc::smem_desc(sb + C::OFF_BB + (uint32_t)(p * C::NPW * 32), 128, 256,
-                                     tc::kSwizzleNone),
-                       idesc2, false);  // b2
+          // descriptors as base + offset (the start address field is the low 14 bits,
+          // in 16 B units); the empty asm keeps the compiler from holding all of them
+          // in registers across the step loop
+          uint64_t dbb = desc_bb0, dw2 = desc_w20;
+          asm volatile("" : "+l"(dbb), "+l"(dw2));
+          tc::mma_bf16(tmem, desc_a1, dbb + (uint64_t)((p * C::NPW * 32) >> 4), idesc2,
+                       false);  // b2
 #pragma unroll
           for (int kb = 0; kb < C::KB; ++kb) {
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)
               mma_bf16_ts(tmem, a_tm + (uint32_t)(kb * 32 + kk * 8),
-                          tc::smem_desc(sb + C::OFF_W2 + (uint32_t)(kb * (H1 * 128) +
-                                                                   p * C::NPW * 128 + kk * 32),
-                                        16, 1024, tc::kSwizzle128B),
+                          dw2 + (uint64_t)((kb * (H1 * 128) + p * C::NPW * 128 + kk * 32) >> 4),
                           idesc2, true);
           }
           tc::mma_commit(bar_l2);
+        }
+        if (p == 0) {
+          // while the pass runs: half 1 draws this step's action uniform and reset
+          // words for half 0; half 0 takes sin / cos of the pole angle
+          if (h == 1) {
+            const float ud = u01(draw(d.seed, k, e, 0, kTagAction, 0).x);
+            const uint4 rr = draw(d.seed, k, e, 0, kTagReset, 0);
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(xch + 16), "r"(rr.x),
+                         "r"(rr.y), "r"(rr.z), "r"(rr.w)
+                         : "memory");
+            asm volatile("st.shared.f32 [%0], %1;" ::"r"(xch + 8), "f"(ud) : "memory");
+          } else {
+            sin_th = sinf(th);
+            cos_th = cosf(th);
+          }
         }
         ok = grp_all(bar_id, tc::mbar_wait(bar_l2, ph_l2, kWaitNs));
         ph_l2 ^= 1u;
@@ -455,11 +476,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (h == 1) asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(xch), "f"(p0), "f"(p1) : "memory");
       pair_sync(pair_id);
       if (h == 0) {
-        float q0, q1;
+        float q0, q1, u;
         asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(q0), "=f"(q1) : "r"(xch) : "memory");
+        asm volatile("ld.shared.f32 %0, [%1];" : "=f"(u) : "r"(xch + 8) : "memory");
         const float l0 = (p0 + q0) + b3.x, l1v = (p1 + q1) + b3.y;
         // ---- sample: a = 0 iff u S < exp(l0 - m)
-        const float u = u01(draw(d.seed, k, e, 0, kTagAction, 0).x);
         const float m = fmaxf(l0, l1v);
         const float e0 = expf(l0 - m), e1 = expf(l1v - m);
         const float Ssum = e0 + e1;
@@ -467,7 +488,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---- env step (explicit Euler, dt = 0.02), reward, done, auto-reset
         const float uf = a ? 10.0f : -10.0f;
         const float xacc = uf - 0.5f * x - 0.1f * v;
-        const float thacc = 9.8f * sinf(th) - 0.3f * cosf(th) * uf;
+        const float thacc = 9.8f * sin_th - 0.3f * cos_th * uf;
         const float x2 = x + 0.02f * v, v2 = v + 0.02f * xacc;
         const float th2 = th + 0.02f * w, w2 = w + 0.02f * thacc;
         const int t2 = tep + 1;
@@ -486,7 +507,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           d.r_done[o] = (uint8_t)done;
         }
         if (done) {
-          const uint4 rr = draw(d.seed, k, e, 0, kTagReset, 0);
+          uint4 rr;
+          asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                       : "=r"(rr.x), "=r"(rr.y), "=r"(rr.z), "=r"(rr.w)
+                       : "r"(xch + 16)
+                       : "memory");
           x = uniform(rr.x, -0.05f, 0.05f);
           v = uniform(rr.y, -0.05f, 0.05f);
           th = uniform(rr.z, -0.05f, 0.05f);
