@@ -452,13 +452,34 @@ def main():
     flops_launch = flops_per_agent_step(wl) * (main_res["agent_steps"] / wl["horizon"]) * launch_steps
     bf16 = path == W.WS_PATH_BATCHED_BF16
     peak = bf16_sus if bf16 else bf16_sus / 4.0
-    roofline = {"bound": "tensor", "achieved": flops_launch / (launch_ms * 1e-3) / 1e12,
-                "peak": peak, "unit": "TFLOP/s", "frac": None, "traffic": None,
-                "kernel": "ws_control_tc (fused persistent, one launch per 50-step chunk)" if bf16
-                else "plain per-step kernels",
-                "peak_source": f"{peak_src} bf16 sustained" if bf16 else
-                f"{peak_src} bf16 sustained / 4 (fp32 SIMT)"}
-    roofline["frac"] = roofline["achieved"] / roofline["peak"]
+    tensor = {"bound": "tensor", "achieved": flops_launch / (launch_ms * 1e-3) / 1e12,
+              "peak": peak, "unit": "TFLOP/s", "frac": None,
+              "peak_source": f"{peak_src} bf16 sustained" if bf16 else
+              f"{peak_src} bf16 sustained / 4 (fp32 SIMT)"}
+    tensor["frac"] = tensor["achieved"] / tensor["peak"]
+    if bf16 and wl["env"] == 0:
+        # The fused control kernel is bound by the SFU: every agent-step takes
+        # H0 + H1 tanh, and an SM retires 16 SFU results per clock (measured 15.2
+        # for tanh.approx in any of f32 / bf16x2 / f16x2 form).
+        import torch
+        n_sms = torch.cuda.get_device_properties(local).multi_processor_count
+        clk = main_res["clocks"] or {}
+        sm_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+        tanh_launch = sum(wl["h"]) * (main_res["agent_steps"] / wl["horizon"]) * launch_steps
+        roofline = {"bound": "alu", "op": "tanh on the SFU",
+                    "achieved": tanh_launch / (launch_ms * 1e-3) / 1e12,
+                    "peak": 16 * n_sms * sm_mhz * 1e6 / 1e12, "unit": "Top/s", "frac": None,
+                    "traffic": None,
+                    "kernel": "ws_control_tc (fused persistent, one launch per 50-step chunk)",
+                    "peak_source": f"16 SFU results / clock / SM x {n_sms} SMs x {sm_mhz:.0f} MHz "
+                                   "(median sampled SM clock)",
+                    "tensor": {k: tensor[k] for k in ("achieved", "peak", "unit", "frac",
+                                                      "peak_source")}}
+        roofline["frac"] = roofline["achieved"] / roofline["peak"]
+    else:
+        roofline = dict(tensor, traffic=None,
+                        kernel="per-step graph of tensor-core layers" if bf16
+                        else "plain per-step kernels")
     if bf16 and args.workload == "control_scale" and not args.horizon and not args.n_envs:
         # DRAM bytes (read + write) of one 50-step launch of this kernel, from the
         # ncu capture summarised in profiles/control_tc_ncu_full_control_50steps.md

@@ -362,6 +362,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                (const volatile uint32_t *)(sm + C::OFF_DONE) + (g ^ 1), g == 0 ? 1u : 0u, false};
   bool ok = true;
   uint32_t fail_site = 0;
+  // Each thread waits on the MMA barriers itself; a wait that runs out is noted
+  // and voted on once per step, at the group barrier that starts the next step
+  // (reading TMEM columns an unfinished MMA still writes yields wrong values, not
+  // a fault), so that the whole group leaves together.
+  bool wfail = false;
+  uint32_t fsite = 0;
   const uint64_t k0 = d.k[0];
   const uint32_t R = d.ring_steps;
   const uint32_t row0 = (uint32_t)(k0 % R);
@@ -394,15 +400,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tc::fence_async_smem();
       tc::fence_before_sync();  // (also orders the last step's TMEM reads before the MMA)
-      grp_sync(bar_id);
+      ok = grp_all(bar_id, !wfail);
+      if (!ok) { fail_site = fsite ? fsite : 9u; break; }
       if (issuer) {
         tc::fence_after_sync();
         tc::mma_bf16(tmem, desc_a1, desc_b1, idesc1, false);
         tc::mma_commit(bar_l1);
       }
-      ok = grp_all(bar_id, tc::mbar_wait(bar_l1, ph_l1, kWaitNs));
+      if (!tc::mbar_wait(bar_l1, ph_l1, kWaitNs) && !wfail) { wfail = true; fsite = 1; }
       ph_l1 ^= 1u;
-      if (!ok) { fail_site = 1; break; }
       tc::fence_after_sync();
       // ---- act 1: h1 block kb -> TMEM columns A_COL + 32 kb.  With H0 = 256, z1
       // blocks 2 and 3 share columns with the A operand: both halves read them
@@ -460,9 +466,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             cos_th = cosf(th);
           }
         }
-        ok = grp_all(bar_id, tc::mbar_wait(bar_l2, ph_l2, kWaitNs));
+        if (!tc::mbar_wait(bar_l2, ph_l2, kWaitNs) && !wfail) { wfail = true; fsite = 2 + (uint32_t)p; }
         ph_l2 ^= 1u;
-        if (!ok) { fail_site = 2 + (uint32_t)p; break; }
         tc::fence_after_sync();
         tok_take(tok, kWaitNs);
         if (h < C::KBP)
@@ -470,7 +475,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                        w3s + (uint32_t)((p * C::NPW + h * 64) * 8), acc0, acc1);
         tok_give(tok);
       }
-      if (!ok) break;
       const float2 pa = unf2(acc0), pb = unf2(acc1);
       const float p0 = pa.x + pa.y, p1 = pb.x + pb.y;
       if (h == 1) asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(xch), "f"(p0), "f"(p1) : "memory");
@@ -534,6 +538,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       d.s[3 * N + e] = w;
       d.t[e] = tep;
     }
+  }
+  // a wait that ran out in the last step of the last tile
+  if (ok) {
+    ok = grp_all(bar_id, !wfail);
+    if (!ok) fail_site = fsite ? fsite : 9u;
   }
   // this group is finished: release the other group from the turn-taking
   __syncwarp();
