@@ -20,8 +20,8 @@
 //            columns against [0 x 12, b2_hi, b2_lo, 0, 0], then H0 / 16 MMAs with
 //            A read from tensor memory and W2^T resident in shared memory
 //   layer 3  logits = tanh(z2) W3 + b3 on the CUDA cores after each pass: each
-//            half reads its block of z2, applies tanh (bf16x2) and accumulates its
-//            partial dot products with W3 (FP32, packed f32x2 FMAs, W3 read as
+//            half reads its block of z2, applies tanh (FP32, SFU) and accumulates
+//            its partial dot products with W3 (FP32, packed f32x2 FMAs, W3 read as
 //            shared-memory broadcasts); half 1 hands its partial to half 0
 //   then     half 0: categorical sample (Philox), Euler step, reward, done,
 //            auto-reset, the time-major record write and the next operand row.
@@ -222,20 +222,26 @@ __device__ __forceinline__ float4 lds128f(uint32_t addr) {
   return v;
 }
 
-// Layer 3 over one 64-unit block: tanh of the block's z2 columns (bf16x2)
+// Layer 3 over one 64-unit block: tanh of the block's z2 columns (FP32 SFU
+// tanh; the same SFU rate per value as the packed bf16x2 form, and no packing)
 // against W3 in FP32.  acc0 / acc1 hold (even-unit, odd-unit) partial sums of
 // logit 0 / logit 1; w3 is the block's 32 float4 {W3[k][0], W3[k+1][0],
 // W3[k][1], W3[k+1][1]} (k even).
 __device__ __forceinline__ void layer3_block(uint32_t taddr, uint32_t w3, uint64_t &acc0,
                                              uint64_t &acc1) {
-  uint32_t hp[32];
-  tanh_block64(taddr, hp);
 #pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    const float4 q = lds128f(w3 + 16u * (uint32_t)j);
-    const uint64_t hv = f2(tc::bf16_lo(hp[j]), tc::bf16_hi(hp[j]));
-    acc0 = fma2(hv, f2(q.x, q.y), acc0);
-    acc1 = fma2(hv, f2(q.z, q.w), acc1);
+  for (int half = 0; half < 2; ++half) {
+    uint32_t z[32];
+    tc::tmem_ld32(taddr + half * 32, z);
+    tc::tmem_wait_ld();
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const float4 q = lds128f(w3 + 16u * (uint32_t)(half * 16 + j));
+      const uint64_t hv = f2(tc::tanh_fast(__uint_as_float(z[2 * j])),
+                             tc::tanh_fast(__uint_as_float(z[2 * j + 1])));
+      acc0 = fma2(hv, f2(q.x, q.y), acc0);
+      acc1 = fma2(hv, f2(q.z, q.w), acc1);
+    }
   }
 }
 
