@@ -483,7 +483,7 @@ def main():
     if bf16 and args.workload == "control_scale" and not args.horizon and not args.n_envs:
         # DRAM bytes (read + write) of one 50-step launch of this kernel, from the
         # ncu capture summarised in profiles/control_tc_ncu_full_control_50steps.md
-        roofline["traffic"] = (3.109632 + 134.541824) * 1e6
+        roofline["traffic"] = (3.461888 + 135.865344) * 1e6
         roofline["traffic_algorithmic"] = 29.0 * wl["n_envs"] * launch_steps
     lat = sorted(main_res["chunk_ms"])
     # kernels of ours per bench step: reset, per chunk (fused kernel + counter
