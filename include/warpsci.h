@@ -61,7 +61,9 @@ typedef enum { WS_ENV_CONTROL = 0, WS_ENV_ECONOMY = 1, WS_ENV_LANDSCAPE = 2 } ws
  * host every step.  BATCHED_FP32: the same kernels, captured as a CUDA graph
  * per chunk of steps.  BATCHED_BF16: policy GEMMs (and the landscape
  * cross-term) on the tcgen05 tensor cores in BF16 with FP32 accumulation;
- * for the control env one persistent fused kernel runs a whole chunk. */
+ * for the control env, and for the economy with 16-128-128-20 / -10 policies
+ * and at most 384 agents per env, one persistent fused kernel runs a whole
+ * chunk (the economy's over a device work queue of env groups). */
 typedef enum { WS_PATH_PLAIN_FP32 = 0, WS_PATH_BATCHED_FP32 = 1, WS_PATH_BATCHED_BF16 = 2 } ws_path;
 
 /* Fields of ws_fetch / ws_load.  Ring fields are time-major per step t:
@@ -83,7 +85,8 @@ typedef enum { WS_PATH_PLAIN_FP32 = 0, WS_PATH_BATCHED_FP32 = 1, WS_PATH_BATCHED
  *   ENV_PARAMS  landscape: f32 centres[M][dim], f32 widths[M], f32 amps[M];
  *               economy:   i32 agents_per_env[n_envs]
  *   LOGITS  f32 [n_slots][n_out] policy outputs of the last step (plain and
- *           batched-FP32 paths only)                                        */
+ *           batched-FP32 paths, the economy's per-layer BF16 path, and its
+ *           fused kernel with WS_FLAG_DEBUG_LOGITS)                         */
 typedef enum {
   WS_F_OBS = 0,
   WS_F_ACTION = 1,
@@ -98,6 +101,11 @@ typedef enum {
   WS_F_ENV_PARAMS = 10,
   WS_F_LOGITS = 11
 } ws_field;
+
+/* ws_config.flags: the fused kernels (economy on the BF16 path) also write each
+ * step's policy outputs to the LOGITS field (costs HBM bandwidth; for tests
+ * and debugging).  The per-step paths always keep them. */
+#define WS_FLAG_DEBUG_LOGITS 1u
 
 /* Roll-out configuration.  Slots: control and landscape have one agent per
  * env (n_slots = n_envs); the economy has agents_per_env[e] agents in env e,
@@ -117,7 +125,7 @@ typedef struct {
   float noise_sigma;      /* landscape: observation-noise sigma               */
   float step_clip;        /* landscape: |dx_j| clip                           */
   float gamma;            /* discount of ws_returns                           */
-  uint32_t flags;         /* reserved, must be 0                              */
+  uint32_t flags;         /* WS_FLAG_* bits, others must be 0                 */
   uint64_t param_seed;    /* Philox key of policy / landscape / agent counts  */
   const int32_t *agents_per_env; /* economy, host, n_envs entries in 2..1024;
                                     NULL = draw U{8..256} from param_seed      */

@@ -38,6 +38,12 @@ struct Dev {
   const uint8_t *pk[2][3];  // [agent, planner][layer]
   const uint8_t *eimg;      // landscape: packed hi/lo centre image + table (BF16 energy)
   int mlp3;                 // economy: whole-MLP tensor-core kernel (images in pk[pid][0])
+  // economy on the fused persistent kernel: work items {first agent slot, rows,
+  // first env, envs} and the work-queue counters {next item, CTAs finished}
+  const int32_t *items;
+  uint32_t n_items;
+  uint32_t *queue;
+  int dbg_logits;           // fused kernels also write each step's logits to out / pout
   // ring
   float *r_obs;
   void *r_act;
@@ -98,6 +104,16 @@ void launch_mlp3_tc_pack(const float *params, const PolicyShape &p, void *packed
 void launch_mlp3_tc(const float *X, long ldr, long ldc, const void *packed, const PolicyShape &p,
                     float *out, long M, uint32_t *err, cudaStream_t st);
 void mlp3_tc_init();
+
+// ---- fused persistent economy kernel (ws_econ_tc.cu) --------------------------------
+bool econ_tc_supported(const PolicyShape &p, const PolicyShape &pp);
+size_t econ_tc_packed_bytes();
+int econ_tc_max_envs_per_item();
+void launch_econ_tc_pack(const float *agent_params, const float *planner_params, void *packed,
+                         cudaStream_t st);
+void econ_tc_init();
+cudaError_t launch_econ_tc(const Dev &d, const void *packed, uint32_t n_steps, int tiles, int grid,
+                           cudaStream_t st);
 
 // ---- BF16 tensor-core landscape energy (ws_energy_tc.cu) -------------------------
 size_t energy_tc_bytes(int D, int M);

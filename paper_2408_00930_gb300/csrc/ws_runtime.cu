@@ -1,6 +1,7 @@
 // ws_runtime.cu -- the C ABI (include/warpsci.h): context layout over the
 // caller's buffers, parameter init, reset, step/rollout dispatch per path,
 // CUDA-graph capture of the horizon loop, fetch/load, host-side waits.
+#include <algorithm>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -28,6 +29,9 @@ struct ws_ctx {
   std::vector<int32_t> agents;      // economy agent counts (host copy)
   std::map<uint32_t, cudaGraphExec_t> graphs;
   int tc_grid = 0;
+  int econ_tiles = 3;               // fused economy kernel: agent tiles per work item
+  int econ_lpt = 1;                 // work items queued largest first
+  std::vector<int32_t> items;       // fused economy kernel: host copy of the work items
   ws_status err = WS_OK;
   std::string msg;
 };
@@ -58,7 +62,7 @@ ws_status validate(const ws_config *cfg) {
   if (cfg->ring_steps < 1 || cfg->episode_limit < 1) return WS_ERR_INVALID;
   if (cfg->hidden0 < 1 || cfg->hidden0 > 4096 || cfg->hidden1 < 1 || cfg->hidden1 > 4096)
     return WS_ERR_INVALID;
-  if (cfg->flags != 0) return WS_ERR_INVALID;
+  if (cfg->flags & ~WS_FLAG_DEBUG_LOGITS) return WS_ERR_INVALID;
   if (!(cfg->gamma >= 0.f && cfg->gamma <= 1.f)) return WS_ERR_INVALID;
   if (cfg->env == WS_ENV_LANDSCAPE) {
     if (cfg->dim < 1 || cfg->dim > 64 || cfg->n_gauss < 1 || cfg->n_gauss > (1u << 22))
@@ -106,6 +110,51 @@ bool tc_layers_supported(const PolicyShape &p) {
 bool use_mlp3(const ws_config *cfg, const PolicyShape &p, const PolicyShape &pp) {
   return use_tc_layers(cfg) && cfg->env == WS_ENV_ECONOMY && mlp3_tc_supported(p) &&
          mlp3_tc_supported(pp);
+}
+
+// Economy on the BF16 path: the fused persistent kernel when both policies
+// have its shape (16-128-128-20 / -10) and every env fits one work item
+// (at most three tiles of 128 agent rows).
+constexpr int kEconMaxTiles = 3;
+bool use_econ_fused(const ws_config *cfg, const PolicyShape &p, const PolicyShape &pp,
+                    const std::vector<int32_t> &agents) {
+  if (cfg->env != WS_ENV_ECONOMY || cfg->path != WS_PATH_BATCHED_BF16) return false;
+  if (!econ_tc_supported(p, pp)) return false;
+  for (int32_t a : agents)
+    if (a > kEconMaxTiles * 128) return false;
+  return true;
+}
+
+// Work items of the fused economy kernel: runs of consecutive envs with at most
+// cap_rows agents and max_envs envs each, as {first agent slot, rows, first env,
+// envs}; largest first when lpt (the queue then hands the long items out early).
+std::vector<int32_t> econ_items(const std::vector<int32_t> &agents, int cap_rows, int max_envs,
+                                bool lpt) {
+  struct It { int32_t slot0, rows, env0, n; };
+  std::vector<It> v;
+  int32_t slot = 0;
+  size_t e = 0;
+  while (e < agents.size()) {
+    It it{slot, 0, (int32_t)e, 0};
+    while (e < agents.size() && it.n < max_envs && it.rows + agents[e] <= cap_rows) {
+      it.rows += agents[e];
+      slot += agents[e];
+      ++it.n;
+      ++e;
+    }
+    v.push_back(it);
+  }
+  if (lpt)
+    std::stable_sort(v.begin(), v.end(), [](const It &a, const It &b) { return a.rows > b.rows; });
+  std::vector<int32_t> out;
+  out.reserve(v.size() * 4);
+  for (const It &it : v) {
+    out.push_back(it.slot0);
+    out.push_back(it.rows);
+    out.push_back(it.env0);
+    out.push_back(it.n);
+  }
+  return out;
 }
 
 size_t tc_layers_bytes(const PolicyShape &p) {
@@ -156,6 +205,7 @@ Layout make_layout(const ws_config *cfg, const std::vector<int32_t> &agents) {
   L.params_off = o; o += up(L.pol.count() * 4);
   L.params_planner_off = o;
   if (cfg->env == WS_ENV_ECONOMY) o += up(L.pol_planner.count() * 4);
+  L.econ_fused = use_econ_fused(cfg, L.pol, L.pol_planner, agents) ? 1 : 0;
   L.packed_off = o;
   L.packed_bytes = use_tc_control(cfg) ? control_tc_packed_bytes(L.pol) : 0;
   if (use_tc_layers(cfg))
@@ -163,6 +213,7 @@ Layout make_layout(const ws_config *cfg, const std::vector<int32_t> &agents) {
                      (cfg->env == WS_ENV_ECONOMY ? tc_layers_bytes(L.pol_planner) : 0);
   if (use_mlp3(cfg, L.pol, L.pol_planner))
     L.packed_bytes = up(mlp3_tc_packed_bytes(L.pol)) + up(mlp3_tc_packed_bytes(L.pol_planner));
+  if (L.econ_fused) L.packed_bytes = econ_tc_packed_bytes();
   o += up(L.packed_bytes);
   L.env_params_off = o;
   if (cfg->env == WS_ENV_LANDSCAPE) o += up(M * D * 4) + up(M * 4) + up(M * 4);
@@ -179,8 +230,16 @@ Layout make_layout(const ws_config *cfg, const std::vector<int32_t> &agents) {
   L.t_off = o; o += up(N * 4);
   L.aux_off = o;
   if (cfg->env == WS_ENV_ECONOMY) o += up((N + 1) * 4) + up(Sa * 4);
+  L.items_off = o;
+  if (L.econ_fused) o += up(N * 16);
+  L.queue_off = o;
+  if (L.econ_fused) o += up(8);
   L.scratch_off = o;
-  const bool plain_scratch = !use_tc_control(cfg);
+  const bool plain_scratch = !use_tc_control(cfg) && !L.econ_fused;
+  if (L.econ_fused && (cfg->flags & WS_FLAG_DEBUG_LOGITS)) {
+    L.scratch_out_off = o; o += up(Sa * L.n_out * 4);
+    L.scratch_pout_off = o; o += up(N * 10 * 4);
+  }
   if (plain_scratch) {
     L.scratch_h0_off = o; o += up(S * cfg->hidden0 * 4);
     L.scratch_h1_off = o; o += up(S * cfg->hidden1 * 4);
@@ -259,7 +318,16 @@ void make_dev(ws_ctx *c) {
     d.slot_env = (const int32_t *)(S + L.aux_off + up((N + 1) * 4));
   }
   d.t = (int32_t *)(S + L.t_off);
-  if (use_mlp3(&cfg, L.pol, L.pol_planner)) {
+  if (L.econ_fused) {
+    d.items = (const int32_t *)(S + L.items_off);
+    d.queue = (uint32_t *)(S + L.queue_off);
+    d.n_items = (uint32_t)(c->items.size() / 4);
+    d.dbg_logits = (cfg.flags & WS_FLAG_DEBUG_LOGITS) ? 1 : 0;
+    if (d.dbg_logits) {
+      d.out = (float *)(S + L.scratch_out_off);
+      d.pout = (float *)(S + L.scratch_pout_off);
+    }
+  } else if (use_mlp3(&cfg, L.pol, L.pol_planner)) {
     d.tc_mlp = 1;
     d.mlp3 = 1;
     d.pk[0][0] = (const uint8_t *)(S + L.packed_off);
@@ -275,7 +343,7 @@ void make_dev(ws_ctx *c) {
       }
     }
   }
-  if (!use_tc_control(&cfg)) {
+  if (!use_tc_control(&cfg) && !L.econ_fused) {
     d.h0 = (float *)(S + L.scratch_h0_off);
     d.h1 = (float *)(S + L.scratch_h1_off);
     d.out = (float *)(S + L.scratch_out_off);
@@ -303,9 +371,33 @@ void drop_graphs(ws_ctx *c) {
   c->graphs.clear();
 }
 
+// Paths whose chunks run as one persistent kernel launch each.
+bool fused(const ws_ctx *c) { return use_tc_control(&c->cfg) || c->L.econ_fused; }
+
 uint32_t chunk_of(const ws_ctx *c) {
   if (c->cfg.chunk_steps) return c->cfg.chunk_steps;
-  return use_tc_control(&c->cfg) ? 100u : 25u;
+  return fused(c) ? 100u : 25u;
+}
+
+int econ_grid(const ws_ctx *c) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int n = (int)c->d.n_items;
+  return n < sms ? n : sms;
+}
+
+// (Re)build the fused economy kernel's work items for the context's tile count
+// and upload them (stream-ordered; the host copy lives in the context).
+ws_status set_econ_items(ws_ctx *c) {
+  c->items = econ_items(c->agents, c->econ_tiles * 128, econ_tc_max_envs_per_item(),
+                        c->econ_lpt != 0);
+  c->d.n_items = (uint32_t)(c->items.size() / 4);
+  cudaError_t e = cudaMemcpyAsync((void *)c->d.items, c->items.data(), c->items.size() * 4,
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d.queue, 0, 8, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return cuda_check(c, e, "upload work items");
 }
 
 // Enqueue `n` steps on stream st (used directly and under capture).
@@ -316,6 +408,16 @@ ws_status enqueue_steps(ws_ctx *c, uint32_t n, cudaStream_t st) {
       const uint32_t m = (n - done) < chunk ? (n - done) : chunk;
       cudaError_t e = launch_control_tc(c->d, c->state + c->L.packed_off, m, c->tc_grid, st);
       if (e != cudaSuccess) return cuda_check(c, e, "control_tc launch");
+      launch_advance(c->d, m, st);
+      done += m;
+    }
+  } else if (c->L.econ_fused) {
+    const uint32_t chunk = chunk_of(c);
+    const int grid = econ_grid(c);
+    for (uint32_t done = 0; done < n;) {
+      const uint32_t m = (n - done) < chunk ? (n - done) : chunk;
+      cudaError_t e = launch_econ_tc(c->d, c->state + c->L.packed_off, m, c->econ_tiles, grid, st);
+      if (e != cudaSuccess) return cuda_check(c, e, "econ_tc launch");
       launch_advance(c->d, m, st);
       done += m;
     }
@@ -403,6 +505,7 @@ std::vector<Piece> state_pieces(ws_ctx *c, ws_field f) {
     }
   } else if (f == WS_F_LOGITS) {
     if (L.env == WS_ENV_CONTROL && use_tc_control(&c->cfg)) return v;
+    if (L.econ_fused && !c->d.dbg_logits) return v;
     v.push_back({S + L.scratch_out_off, (size_t)L.n_agent_slots * L.n_out * 4});
     if (L.env == WS_ENV_ECONOMY) v.push_back({S + L.scratch_pout_off, N * 10 * 4});
   }
@@ -413,7 +516,9 @@ ws_status after_params_changed(ws_ctx *c) {
   if (c->cfg.env == WS_ENV_LANDSCAPE) launch_landscape_derive(c->d, c->stream);
   if (c->d.eimg) launch_energy_tc_pack(c->d, (void *)c->d.eimg, c->stream);
   if (use_tc_control(&c->cfg)) launch_control_tc_pack(c->d, c->state + c->L.packed_off, c->stream);
-  if (c->d.mlp3) {
+  if (c->L.econ_fused) {
+    launch_econ_tc_pack(c->d.params, c->d.params_planner, c->state + c->L.packed_off, c->stream);
+  } else if (c->d.mlp3) {
     launch_mlp3_tc_pack(c->d.params, c->L.pol, (void *)c->d.pk[0][0], c->stream);
     launch_mlp3_tc_pack(c->d.params_planner, c->L.pol_planner, (void *)c->d.pk[1][0], c->stream);
   } else if (use_tc_layers(&c->cfg)) {
@@ -501,6 +606,14 @@ ws_status ws_create(const ws_config *cfg, void *state_buf, size_t state_bytes, v
     cudaMemcpyAsync((void *)c->d.agent_off, off.data(), (N + 1) * 4, cudaMemcpyHostToDevice, c->stream);
     cudaMemcpyAsync((void *)c->d.slot_env, slot_env.data(), Sa * 4, cudaMemcpyHostToDevice, c->stream);
     e = cudaStreamSynchronize(c->stream);  // host staging vectors end here
+    if (e == cudaSuccess && c->L.econ_fused) {
+      econ_tc_init();
+      if (set_econ_items(c) != WS_OK) {
+        ws_status r = c->err;
+        ws_destroy(c);
+        return r;
+      }
+    }
     if (e != cudaSuccess) {
       cuda_check(c, e, "upload agent counts");
       ws_status r = c->err;
@@ -560,7 +673,7 @@ ws_status ws_rollout(ws_ctx *c, uint32_t n) {
   ws_status s = WS_OK;
   if (c->cfg.path == WS_PATH_PLAIN_FP32) {
     for (uint32_t i = 0; i < n && s == WS_OK; ++i) s = enqueue_steps(c, 1, c->stream);
-  } else if (use_tc_control(&c->cfg)) {
+  } else if (fused(c)) {
     cudaGraphExec_t g;
     s = graph_for(c, n, &g);
     if (s == WS_OK) s = cuda_check(c, cudaGraphLaunch(g, c->stream), "graph launch");
@@ -601,7 +714,8 @@ ws_status ws_fetch_async(ws_ctx *c, ws_field f, uint64_t t0, uint32_t n, void *d
   const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (f == WS_F_STATE || f == WS_F_PARAMS || f == WS_F_ENV_PARAMS || f == WS_F_LOGITS) {
     if (t0 != 0 || n != 0) return WS_ERR_INVALID;
-    if (f == WS_F_LOGITS && use_tc_control(&c->cfg)) return WS_ERR_UNSUPPORTED;
+    if (f == WS_F_LOGITS && (use_tc_control(&c->cfg) || (c->L.econ_fused && !c->d.dbg_logits)))
+      return WS_ERR_UNSUPPORTED;
     std::vector<Piece> v = state_pieces(c, f);
     if (v.empty()) return WS_ERR_INVALID;
     size_t tot = 0;

@@ -32,6 +32,7 @@ EXPORTED = ["ws_query_bytes", "ws_create", "ws_reset", "ws_step", "ws_rollout", 
             "ws_server_wait_chunk", "ws_server_fetch", "ws_server_ack", "ws_server_release",
             "ws_server_get_stats", "ws_server_destroy"]
 WS_REQ_CONSUME_ON_READY = 1
+WS_FLAG_DEBUG_LOGITS = 1
 
 
 class ws_config(C.Structure):
@@ -178,14 +179,14 @@ def ws_policy_forward_noalloc(obs_ptr, n_rows, params_ptr, in_dim, hidden0, hidd
 # --- convenience owner --------------------------------------------------------
 def make_config(env, path, n_envs, ring_steps, episode_limit, hidden0, hidden1, *,
                 chunk_steps=0, dim=0, n_gauss=0, noise_sigma=0.05, step_clip=0.1, gamma=0.99,
-                param_seed=1, agents_per_env=None):
+                param_seed=1, agents_per_env=None, flags=0):
     cfg = ws_config()
     cfg.struct_size = C.sizeof(ws_config)
     cfg.env, cfg.path, cfg.n_envs = env, path, n_envs
     cfg.ring_steps, cfg.episode_limit, cfg.chunk_steps = ring_steps, episode_limit, chunk_steps
     cfg.hidden0, cfg.hidden1, cfg.dim, cfg.n_gauss = hidden0, hidden1, dim, n_gauss
     cfg.noise_sigma, cfg.step_clip, cfg.gamma = noise_sigma, step_clip, gamma
-    cfg.flags, cfg.param_seed = 0, param_seed
+    cfg.flags, cfg.param_seed = flags, param_seed
     keep = None
     if agents_per_env is not None:
         keep = np.ascontiguousarray(agents_per_env, dtype=np.int32)

@@ -41,7 +41,8 @@ def test_econ_bf16_logits_actions_and_wealth(torch):
     pp = inputs.policy_params(g, PW, scale=3.0)
     w0, f0 = inputs.econ_state(g, counts)
     t0 = np.zeros(len(counts), np.int32)
-    r = W.Rollout(W.WS_ENV_ECONOMY, BF16, len(counts), 8, 540, 128, 128, agents_per_env=counts)
+    r = W.Rollout(W.WS_ENV_ECONOMY, BF16, len(counts), 8, 540, 128, 128, agents_per_env=counts,
+                  flags=W.WS_FLAG_DEBUG_LOGITS)
     r.load_raw(W.WS_F_PARAMS, np.concatenate([ap, pp]))
     k0 = 99
     r.load_raw(W.WS_F_STATE, H.pack_econ_state(w0, f0, t0), k=k0)
