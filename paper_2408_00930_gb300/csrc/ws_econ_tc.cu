@@ -75,7 +75,7 @@ struct EconTc {
   static constexpr int OFF_W2P = 32768;
   static constexpr int OFF_HS = 65536;             // [tile] 32 KB: h1 / h2, layer-1 A at its start
   static constexpr int OFF_HP = OFF_HS + AT * 32768;  // planner activations [128 env rows][128 k]
-  static constexpr int OFF_SFEAT = OFF_HP;            // aliases HP: f32 [16][ROWS]
+  static constexpr int OFF_SFEAT = OFF_HP;            // aliases HP: float4 [4][ROWS]
   static constexpr int OFF_SREW = OFF_HP + 16 * ROWS * 4;  // aliases HP: f32 [ROWS]
   static constexpr int OFF_W3A = OFF_HP + 32768;   // W3A | W3P | W1A | W1P | BIAS as packed
   static constexpr int OFF_W3P = OFF_W3A + 8192;
@@ -208,6 +208,24 @@ __device__ __forceinline__ long long seg_sum(long long v, int key, bool &tail) {
   return v;
 }
 
+// Sums of 16 per-lane values over a warp by recursive halving: at each level a
+// lane keeps half of its values and adds the partner's copy of that half (8, 4,
+// 2, 1 shuffles), then one exchange completes the sum.  Returns the total of
+// value (lane >> 1) & 15; 16 shuffles in place of 80 for 16 butterflies.
+__device__ __forceinline__ float warp_sum16(float (&v)[kEconF], int lane) {
+#pragma unroll
+  for (int w = 8, o = 16; w >= 1; w >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;  // keep the upper half of the w-pairs
+#pragma unroll
+    for (int i = 0; i < w; ++i) {
+      const float keep = up ? v[w + i] : v[i];
+      const float send = up ? v[i] : v[w + i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
 // Categorical draw by inverse CDF in FP32 (the arithmetic of the plain path's
 // sampler): a = min{i : u S < C_i}, C_i the running sum of exp(l - max), S the
 // total; logp = (l_a - max) - log S.
@@ -308,7 +326,7 @@ __global__ void __launch_bounds__((AT + 1) * 128, 1)
   long long *envT = (long long *)(sm + C::OFF_ENVT);
   long long *wsum = (long long *)(sm + C::OFF_WSUM);
   long long *income = (long long *)(sm + C::OFF_INC);
-  float *sfeat = (float *)(sm + C::OFF_SFEAT);
+  float4 *sfeat = (float4 *)(sm + C::OFF_SFEAT);
   float *srew = (float *)(sm + C::OFF_SREW);
 
   {
@@ -401,10 +419,10 @@ __global__ void __launch_bounds__((AT + 1) * 128, 1)
         if (valid) {
           float *ob = d.r_obs + rowR * kEconF * S + slot;
 #pragma unroll
-          for (int j = 0; j < kEconF; ++j) {
-            ob[(size_t)j * S] = f[j];
-            sfeat[j * C::ROWS + row] = f[j];
-          }
+          for (int j = 0; j < kEconF; ++j) ob[(size_t)j * S] = f[j];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            sfeat[q * C::ROWS + row] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
           d.r_wealth[rowR * S + slot] = w;
         }
         tc::sts128(a1_row, tc::pack_bf16x2(f[0], f[1]), tc::pack_bf16x2(f[2], f[3]),
@@ -416,8 +434,9 @@ __global__ void __launch_bounds__((AT + 1) * 128, 1)
           const long long ws = seg_sum(valid ? w : 0, e_loc, tail);
           if (tail && e_loc >= 0) atom_add_i64(sb + C::OFF_WSUM + 8u * (uint32_t)e_loc, ws);
         }
+        // (the named barrier orders these shared-memory writes before the
+        // planner's reads; the async-proxy fence covers the MMA's operand)
         tc::fence_async_smem();
-        __threadfence_block();
         bar_arrive_n(kBarObs, C::THREADS);
         // ---- agent policy on the tensor core
         float lg[kNA];
@@ -480,12 +499,14 @@ __global__ void __launch_bounds__((AT + 1) * 128, 1)
             tmem_ld16(tm + 16, z1);
             tc::tmem_wait_ld();
 #pragma unroll
-            for (int c = 0; c < 16; ++c)
-              lg[c] = __uint_as_float(z0[c]) + *(const float *)(sm + C::OFF_BIAS + (BO_B3A + c) * 4);
-#pragma unroll
-            for (int c = 16; c < kNA; ++c)
-              lg[c] = __uint_as_float(z1[c - 16]) +
-                      *(const float *)(sm + C::OFF_BIAS + (BO_B3A + c) * 4);
+            for (int q = 0; q < kNA / 4; ++q) {
+              const float4 b = lds128f(bias + (uint32_t)((BO_B3A + 4 * q) * 4));
+              const uint32_t *z = q < 4 ? z0 + 4 * q : z1 + 4 * (q - 4);
+              lg[4 * q] = __uint_as_float(z[0]) + b.x;
+              lg[4 * q + 1] = __uint_as_float(z[1]) + b.y;
+              lg[4 * q + 2] = __uint_as_float(z[2]) + b.z;
+              lg[4 * q + 3] = __uint_as_float(z[3]) + b.w;
+            }
           }
         }
         // ---- sample, transfer
@@ -527,10 +548,18 @@ __global__ void __launch_bounds__((AT + 1) * 128, 1)
         // ---- redistribution, features, reward, done, auto-reset
         if (valid) {
           const long long T = envT[e_loc];
-          long long share = T / n, rem = T % n;  // floor division for a pool of either sign
-          if (rem < 0) {
-            rem += n;
-            share -= 1;
+          long long share, rem;
+          if (T >= 0 && T <= 0x7fffffffLL) {  // the usual case, in 32-bit arithmetic
+            const uint32_t q = (uint32_t)T / (uint32_t)n;
+            share = q;
+            rem = (long long)((uint32_t)T - q * (uint32_t)n);
+          } else {  // floor division for a pool of either sign
+            share = T / n;
+            rem = T % n;
+            if (rem < 0) {
+              rem += n;
+              share -= 1;
+            }
           }
           const long long w2 = w_mid + share + ((long long)agent < rem ? 1 : 0);
           const float drive = ((float)a - 9.5f) / 9.5f;
@@ -553,10 +582,7 @@ __global__ void __launch_bounds__((AT + 1) * 128, 1)
           }
         }
       }
-      if (ok) {  // the planner's reward of the last step
-        __threadfence_block();
-        bar_arrive_n(kBarObs, C::THREADS);
-      }
+      if (ok) bar_arrive_n(kBarObs, C::THREADS);  // the planner's reward of the last step
       if (ok && valid) {
         d.wealth[slot] = w;
 #pragma unroll
@@ -615,19 +641,22 @@ __global__ void __launch_bounds__((AT + 1) * 128, 1)
           for (int j = 0; j < kEconF; ++j) acc[j] = 0.f;
           for (int i = lane; i < ei.y; i += 32) {
 #pragma unroll
-            for (int j = 0; j < kEconF; ++j) acc[j] += sfeat[j * C::ROWS + ei.x + i];
+            for (int q = 0; q < 4; ++q) {
+              const float4 v = sfeat[q * C::ROWS + ei.x + i];
+              acc[4 * q] += v.x;
+              acc[4 * q + 1] += v.y;
+              acc[4 * q + 2] += v.z;
+              acc[4 * q + 3] += v.w;
+            }
           }
-          float mine = 0.f;
-#pragma unroll
-          for (int j = 0; j < kEconF; ++j) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
-            if (lane == j) mine = acc[j];
-          }
-          if (lane < kEconF) {
-            const float mean = mine / (float)ei.y;
-            d.r_obs[(rowR * kEconF + (size_t)lane) * S + Sa + (uint32_t)ei.z] = mean;
-            *(uint16_t *)(sm + C::OFF_POBS + k16_off(e, lane)) = bf16_bits(mean);
+          // reduce-scatter over the warp (fixed order): after it, lanes 2j and
+          // 2j + 1 hold the total of feature j
+          const float tot = warp_sum16(acc, lane);
+          if ((lane & 1) == 0) {
+            const int j = lane >> 1;
+            const float mean = tot / (float)ei.y;
+            d.r_obs[(rowR * kEconF + (size_t)j) * S + Sa + (uint32_t)ei.z] = mean;
+            *(uint16_t *)(sm + C::OFF_POBS + k16_off(e, j)) = bf16_bits(mean);
           }
         }
         tc::fence_async_smem();
