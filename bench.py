@@ -232,6 +232,11 @@ def run_gpu(args, wl, world, rank, local):
         H = wl["horizon"]
         n_chunks = (H + CHUNK - 1) // CHUNK
         agent_steps = r.n_slots * H
+        launch = None
+        if measure_kernel:
+            # autotune the launch configuration (outside the timed region; the
+            # trials end with a reset) over one 50-step roll-out per candidate
+            launch, _ = r.tune(min(CHUNK, H))
 
         def bench_step(i, evs=None):
             r.reset(1000 + i)
@@ -271,7 +276,7 @@ def run_gpu(args, wl, world, rank, local):
         barrier(world)
         total_ms = max_over_ranks(sum(times), world)
         res = dict(agent_steps=agent_steps, total_ms=total_ms, times=times, chunk_ms=chunk_ms,
-                   roll_ms=roll_ms, clocks=clk, n_chunks=n_chunks, rollout=r)
+                   roll_ms=roll_ms, clocks=clk, n_chunks=n_chunks, rollout=r, launch=launch)
         return res
 
     main = one_path(path, args.steps, args.warmup, True)
@@ -486,10 +491,21 @@ def main():
         roofline["traffic"] = (3.461888 + 135.865344) * 1e6
         roofline["traffic_algorithmic"] = 29.0 * wl["n_envs"] * launch_steps
     lat = sorted(main_res["chunk_ms"])
-    # kernels of ours per bench step: reset, per chunk (fused kernel + counter
-    # advance) or per step the plain kernels, and the returns scan
-    plain_per_step = {0: 6, 1: 14, 2: 9}[wl["env"]]
-    per_launch = (1 + 2 * n_chunks + 1) if bf16 else (1 + plain_per_step * wl["horizon"] + n_chunks + 1)
+    # kernels of ours per bench step: the reset (plus the landscape's energy of
+    # the fresh state), per 50-step roll-out either the fused kernel and the
+    # counter advance per launch chunk (control, economy) or the per-step
+    # kernels (landscape: observe, three policy layers, sample, energy, step,
+    # reset energy, reset finish) and one advance per graph chunk, and the
+    # returns scan
+    launch = main_res["launch"] or {}
+    ch = int(launch.get("chunk_steps", CHUNK))
+    lens = [min(CHUNK, wl["horizon"] - c * CHUNK) for c in range(n_chunks)]
+    if bf16 and wl["env"] in (0, 1):
+        per_roll = sum(-(-n // ch) * 2 for n in lens)
+    else:
+        per_step = 9 if bf16 else {0: 6, 1: 14, 2: 9}[wl["env"]]
+        per_roll = sum(per_step * n + -(-n // ch) for n in lens)
+    per_launch = (3 if wl["env"] == 2 else 1) + per_roll + 1
     out = {
         "metric": METRIC, "value": value, "unit": "agent-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -500,6 +516,7 @@ def main():
                    "path": "batched_bf16" if bf16 else "batched_fp32",
                    "bench_step": f"ws_reset + ws_rollout x {n_chunks} chunks of {CHUNK} + ws_returns",
                    "l2": "flushed between timed steps (256 MiB write)",
+                   "launch": main_res["launch"],
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "latency": {"chunk_steps": CHUNK, "p50_ms": float(np.percentile(lat, 50)),
                     "p99_ms": float(np.percentile(lat, 99))},

@@ -195,6 +195,52 @@ const char *ws_last_error(const ws_ctx *ctx);
 void ws_destroy(ws_ctx *ctx);
 
 /* ------------------------------------------------------------------------
+ * Launch configuration and autotuning.  Every batched path has launch
+ * parameters that change speed, not results (the one exception is the
+ * landscape energy's Gaussian chunk count, which regroups an FP32 sum and so
+ * moves its last bits): the chunk of steps per
+ * persistent launch or captured graph, the persistent grid of the fused
+ * control kernel, the rows per work item ("envs per CTA") of the fused economy
+ * kernel and the order of its work queue, the Gaussian chunks per env tile of
+ * the BF16 landscape energy kernel, and the block size of the per-step
+ * kernels (envs per block).  A context starts with defaults; ws_tune times the
+ * candidates of its path on the device and keeps the fastest.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  uint32_t struct_size;    /* = sizeof(ws_launch)                                   */
+  uint32_t chunk_steps;    /* steps per persistent launch / captured graph (>= 1);
+                              a nonzero ws_config.chunk_steps fixes it              */
+  uint32_t grid;           /* fused control kernel: persistent CTAs, 0 = one per SM
+                              (at most one per tile)                                */
+  uint32_t econ_tiles;     /* fused economy kernel: 128-row agent tiles per work
+                              item (1..3; at least the largest env's agents / 128)  */
+  uint32_t econ_lpt;       /* fused economy kernel: 1 = queue the largest work items
+                              first, 0 = in env order                               */
+  uint32_t energy_chunks;  /* BF16 landscape: Gaussian chunks per env tile (1, 2, 4)*/
+  uint32_t env_threads;    /* per-step kernels: threads per block, 64..1024, a
+                              multiple of 32                                        */
+} ws_launch;
+
+/* The context's current launch configuration. */
+ws_status ws_get_launch(const ws_ctx *ctx, ws_launch *out);
+
+/* Replace the launch configuration (fields the context's path does not use
+ * are ignored but must be in range).  Cached graphs are rebuilt on the next
+ * roll-out; results are unchanged.  WS_ERR_INVALID for an out-of-range field. */
+ws_status ws_set_launch(ws_ctx *ctx, const ws_launch *l);
+
+/* Autotune: run each candidate launch configuration of the context's path for
+ * trial_steps steps (after one untimed run of the same length), timed with
+ * CUDA events on the context's stream, and keep the fastest.  The choice is
+ * cached per process for the configuration's shape (env, path, sizes, agent
+ * counts, device), so a later context of the same shape reuses it without
+ * timing.  The trials advance the envs, so the call ends with ws_reset under
+ * the context's current seed (step counter 0, ring contents overwritten).
+ * Synchronous.  chosen and ms_per_step (the winner's time per step; NULL
+ * allowed) report the result. */
+ws_status ws_tune(ws_ctx *ctx, uint32_t trial_steps, ws_launch *chosen, float *ms_per_step);
+
+/* ------------------------------------------------------------------------
  * Serving: a request loop with continuous batching over roll-out contexts.
  * Clients (trainers) submit roll-out requests of any env type and size.  A
  * request is admitted as soon as its device bytes (env state, parameters,

@@ -32,11 +32,12 @@ constexpr int kABytes = kKB * kRows * 128;
 constexpr int kBBytes = kKB * kBlockG * 128;
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr uint32_t kTmemCols = 512;
-// Gaussian chunks per env tile: each CTA sweeps Mp / kTcChunks Gaussians in
-// 256-wide blocks through its double-buffered pipeline (long enough to
-// amortise its set-up); partial sums land in the first kTcChunks of the
-// kEnergyChunks slots, whose others are kept at zero.
-constexpr int kTcChunks = 2;
+// Gaussian chunks per env tile (1, 2 or 4; a launch parameter the tuner
+// picks): each CTA sweeps Mp / chunks Gaussians in 256-wide blocks through its
+// double-buffered pipeline (long enough to amortise its set-up); partial sums
+// land in the first `chunks` of the kEnergyChunks slots, whose others are kept
+// at zero.  Mp is padded for the largest count, so one image serves all.
+constexpr int kMaxTcChunks = 4;
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
                                          uint64_t *bar) {
@@ -264,29 +265,36 @@ size_t smem_for(int per_chunk) {
 
 }  // namespace
 
-// Padded Gaussian count (a multiple of kEnergyChunks * 256) and its chunk size.
-void energy_tc_shape(int M, int *Mp, int *per_chunk) {
-  const int blk = kTcChunks * kBlockG;
+// Padded Gaussian count (a multiple of 4 * 256) and the chunk size for `chunks`.
+void energy_tc_shape(int M, int chunks, int *Mp, int *per_chunk) {
+  const int blk = kMaxTcChunks * kBlockG;
   *Mp = (M + blk - 1) / blk * blk;
-  *per_chunk = *Mp / kTcChunks;
+  *per_chunk = *Mp / chunks;
 }
 
 size_t energy_tc_bytes(int D, int M) {
   int Mp, pc;
-  energy_tc_shape(M, &Mp, &pc);
+  energy_tc_shape(M, kMaxTcChunks, &Mp, &pc);
   (void)D;
   return (size_t)Mp * kKB * 128 + (size_t)Mp * 16;
 }
 
 bool energy_tc_supported(int D, int M) {
   int Mp, pc;
-  energy_tc_shape(M, &Mp, &pc);
+  energy_tc_shape(M, kMaxTcChunks, &Mp, &pc);
   return D >= 1 && 3 * D <= kKB * 64 && D <= 40 && smem_for(pc) <= 232448;
+}
+
+bool energy_tc_chunks_ok(int M, int chunks) {
+  if (chunks != 1 && chunks != 2 && chunks != 4) return false;
+  int Mp, pc;
+  energy_tc_shape(M, chunks, &Mp, &pc);
+  return smem_for(pc) <= 232448;
 }
 
 void launch_energy_tc_pack(const Dev &d, void *buf, cudaStream_t st) {
   int Mp, pc;
-  energy_tc_shape((int)d.n_gauss, &Mp, &pc);
+  energy_tc_shape((int)d.n_gauss, kMaxTcChunks, &Mp, &pc);
   uint8_t *img = (uint8_t *)buf;
   float4 *tab = (float4 *)(img + (size_t)Mp * kKB * 128);
   k_energy_tc_pack<<<256, 256, 0, st>>>(d.centres, d.widths, d.amps, (int)d.dim, (int)d.n_gauss, Mp,
@@ -294,17 +302,22 @@ void launch_energy_tc_pack(const Dev &d, void *buf, cudaStream_t st) {
 }
 
 void energy_tc_init(int M) {
-  int Mp, pc;
-  energy_tc_shape(M, &Mp, &pc);
+  int Mp, pc = 0;
+  for (int c = 1; c <= kMaxTcChunks; c *= 2) {
+    if (!energy_tc_chunks_ok(M, c)) continue;
+    energy_tc_shape(M, c, &Mp, &pc);
+    break;  // the smallest supported count has the largest chunk
+  }
   cudaFuncSetAttribute(k_energy_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_for(pc));
 }
 
 void launch_energy_tc(const Dev &d, const void *buf, uint32_t off, int mode, cudaStream_t st) {
   int Mp, pc;
-  energy_tc_shape((int)d.n_gauss, &Mp, &pc);
+  const int chunks = d.energy_chunks > 0 ? d.energy_chunks : 2;
+  energy_tc_shape((int)d.n_gauss, chunks, &Mp, &pc);
   const uint8_t *img = (const uint8_t *)buf;
   const float4 *tab = (const float4 *)(img + (size_t)Mp * kKB * 128);
-  dim3 grid((d.n_envs + kRows - 1) / kRows, kTcChunks);
+  dim3 grid((d.n_envs + kRows - 1) / kRows, chunks);
   k_energy_tc<<<grid, kThreads, smem_for(pc), st>>>(d, off, mode, img, tab, Mp, pc);
 }
 

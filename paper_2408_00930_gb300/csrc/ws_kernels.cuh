@@ -44,6 +44,10 @@ struct Dev {
   uint32_t n_items;
   uint32_t *queue;
   int dbg_logits;           // fused kernels also write each step's logits to out / pout
+  // launch parameters (ws_launch): per-env kernels' block size, the BF16
+  // energy kernel's Gaussian chunks per env tile
+  int env_threads;
+  int energy_chunks;
   // ring
   float *r_obs;
   void *r_act;
@@ -121,6 +125,7 @@ bool energy_tc_supported(int D, int M);
 void launch_energy_tc_pack(const Dev &d, void *buf, cudaStream_t st);
 void launch_energy_tc(const Dev &d, const void *buf, uint32_t off, int mode, cudaStream_t st);
 void energy_tc_init(int M);
+bool energy_tc_chunks_ok(int M, int chunks);
 
 // Y[M][N] = act(X W + b) with the plain path's FP32 dense kernel (X row-major
 // when ldc == 1, or addressed X[r * ldr + c * ldc]).

@@ -694,11 +694,12 @@ void launch_reset(const Dev &d, cudaStream_t st) {
 }
 
 void launch_plain_step(const Dev &d, uint32_t off, cudaStream_t st, const Branch *br) {
+  const int T = d.env_threads > 0 ? d.env_threads : 256;  // per-env kernels' block size
   if (d.env == WS_ENV_CONTROL) {
-    k_store_obs<<<blocks(d.n_envs, 256), 256, 0, st>>>(d, off, d.s, 4, d.n_envs, d.n_envs, 0);
+    k_store_obs<<<blocks(d.n_envs, T), T, 0, st>>>(d, off, d.s, 4, d.n_envs, d.n_envs, 0);
     policy(d, d.s, 1, d.n_envs, d.params, d.pol, 0, d.h0, d.h1, d.out, (int)d.n_envs, st);
-    k_sample_cat<<<blocks(d.n_envs, 256), 256, 0, st>>>(d, off, d.out, 2, 0, d.n_envs, 0);
-    k_control_step<<<blocks(d.n_envs, 256), 256, 0, st>>>(d, off);
+    k_sample_cat<<<blocks(d.n_envs, T), T, 0, st>>>(d, off, d.out, 2, 0, d.n_envs, 0);
+    k_control_step<<<blocks(d.n_envs, T), T, 0, st>>>(d, off);
   } else if (d.env == WS_ENV_ECONOMY) {
     k_econ_observe<<<d.n_envs, kEconThreads, 0, st>>>(d, off);
     // the planner's policy and draw are independent of the agents': side branch
@@ -710,26 +711,26 @@ void launch_plain_step(const Dev &d, uint32_t off, cudaStream_t st, const Branch
     }
     policy(d, d.pobs, kEconF, 1, d.params_planner, d.pol_planner, 1, d.ph0, d.ph1, d.pout,
            (int)d.n_envs, ps);
-    k_sample_cat<<<blocks(d.n_envs, 256), 256, 0, ps>>>(d, off, d.pout, (int)d.n_out_planner, 2,
+    k_sample_cat<<<blocks(d.n_envs, T), T, 0, ps>>>(d, off, d.pout, (int)d.n_out_planner, 2,
                                                          d.n_envs, d.n_agent_slots);
     policy(d, d.feat, 1, d.n_agent_slots, d.params, d.pol, 0, d.h0, d.h1, d.out,
            (int)d.n_agent_slots, st);
-    k_sample_cat<<<blocks(d.n_agent_slots, 256), 256, 0, st>>>(d, off, d.out, (int)d.n_out, 1,
+    k_sample_cat<<<blocks(d.n_agent_slots, T), T, 0, st>>>(d, off, d.out, (int)d.n_out, 1,
                                                                 d.n_agent_slots, 0);
     if (br) {
       cudaEventRecord(br->join, br->aux);
       cudaStreamWaitEvent(st, br->join, 0);
     }
-    k_econ_transfer<<<blocks(d.n_agent_slots, 256), 256, 0, st>>>(d, off);
+    k_econ_transfer<<<blocks(d.n_agent_slots, T), T, 0, st>>>(d, off);
     k_econ_finish<<<d.n_envs, kEconThreads, 0, st>>>(d, off);
   } else {
-    k_store_obs<<<blocks(d.n_envs, 256), 256, 0, st>>>(d, off, d.s, (int)d.dim, d.n_envs, d.n_envs, 0);
+    k_store_obs<<<blocks(d.n_envs, T), T, 0, st>>>(d, off, d.s, (int)d.dim, d.n_envs, d.n_envs, 0);
     policy(d, d.s, 1, d.n_envs, d.params, d.pol, 0, d.h0, d.h1, d.out, (int)d.n_envs, st);
-    k_sample_gauss<<<blocks(d.n_envs, 128), 128, 0, st>>>(d, off);
+    k_sample_gauss<<<blocks(d.n_envs, T), T, 0, st>>>(d, off);
     landscape_energy(d, off, 0, st);
-    k_landscape_step<<<blocks(d.n_envs, 256), 256, 0, st>>>(d, off);
+    k_landscape_step<<<blocks(d.n_envs, T), T, 0, st>>>(d, off);
     landscape_energy(d, off, 1, st);
-    k_landscape_reset_finish<<<blocks(d.n_envs, 256), 256, 0, st>>>(d, off, 0);
+    k_landscape_reset_finish<<<blocks(d.n_envs, T), T, 0, st>>>(d, off, 0);
   }
 }
 

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -28,9 +29,8 @@ struct ws_ctx {
   uint64_t seed = 0;
   std::vector<int32_t> agents;      // economy agent counts (host copy)
   std::map<uint32_t, cudaGraphExec_t> graphs;
-  int tc_grid = 0;
-  int econ_tiles = 3;               // fused economy kernel: agent tiles per work item
-  int econ_lpt = 1;                 // work items queued largest first
+  int tc_grid = 0;                  // fused control kernel: default persistent grid
+  ws_launch lc{};                   // launch configuration (ws_get_launch / ws_tune)
   std::vector<int32_t> items;       // fused economy kernel: host copy of the work items
   ws_status err = WS_OK;
   std::string msg;
@@ -374,15 +374,36 @@ void drop_graphs(ws_ctx *c) {
 // Paths whose chunks run as one persistent kernel launch each.
 bool fused(const ws_ctx *c) { return use_tc_control(&c->cfg) || c->L.econ_fused; }
 
-uint32_t chunk_of(const ws_ctx *c) {
-  if (c->cfg.chunk_steps) return c->cfg.chunk_steps;
-  return fused(c) ? 100u : 25u;
-}
+uint32_t chunk_of(const ws_ctx *c) { return c->lc.chunk_steps; }
 
-int econ_grid(const ws_ctx *c) {
+int sm_count() {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+int max_agents(const ws_ctx *c) {
+  int m = 1;
+  for (int32_t a : c->agents) m = a > m ? a : m;
+  return m;
+}
+
+// Defaults of a fresh context.
+void default_launch(ws_ctx *c) {
+  ws_launch &l = c->lc;
+  l = ws_launch{};
+  l.struct_size = sizeof(ws_launch);
+  l.chunk_steps = c->cfg.chunk_steps ? c->cfg.chunk_steps : (fused(c) ? 100u : 25u);
+  l.grid = 0;
+  l.econ_tiles = 3;
+  l.econ_lpt = 1;
+  l.energy_chunks = 2;
+  l.env_threads = 256;
+}
+
+int econ_grid(const ws_ctx *c) {
+  const int sms = sm_count();
   const int n = (int)c->d.n_items;
   return n < sms ? n : sms;
 }
@@ -390,8 +411,8 @@ int econ_grid(const ws_ctx *c) {
 // (Re)build the fused economy kernel's work items for the context's tile count
 // and upload them (stream-ordered; the host copy lives in the context).
 ws_status set_econ_items(ws_ctx *c) {
-  c->items = econ_items(c->agents, c->econ_tiles * 128, econ_tc_max_envs_per_item(),
-                        c->econ_lpt != 0);
+  c->items = econ_items(c->agents, (int)c->lc.econ_tiles * 128, econ_tc_max_envs_per_item(),
+                        c->lc.econ_lpt != 0);
   c->d.n_items = (uint32_t)(c->items.size() / 4);
   cudaError_t e = cudaMemcpyAsync((void *)c->d.items, c->items.data(), c->items.size() * 4,
                                   cudaMemcpyHostToDevice, c->stream);
@@ -406,7 +427,8 @@ ws_status enqueue_steps(ws_ctx *c, uint32_t n, cudaStream_t st) {
     const uint32_t chunk = chunk_of(c);
     for (uint32_t done = 0; done < n;) {
       const uint32_t m = (n - done) < chunk ? (n - done) : chunk;
-      cudaError_t e = launch_control_tc(c->d, c->state + c->L.packed_off, m, c->tc_grid, st);
+      const int grid = c->lc.grid ? (int)c->lc.grid : c->tc_grid;
+      cudaError_t e = launch_control_tc(c->d, c->state + c->L.packed_off, m, grid, st);
       if (e != cudaSuccess) return cuda_check(c, e, "control_tc launch");
       launch_advance(c->d, m, st);
       done += m;
@@ -416,7 +438,8 @@ ws_status enqueue_steps(ws_ctx *c, uint32_t n, cudaStream_t st) {
     const int grid = econ_grid(c);
     for (uint32_t done = 0; done < n;) {
       const uint32_t m = (n - done) < chunk ? (n - done) : chunk;
-      cudaError_t e = launch_econ_tc(c->d, c->state + c->L.packed_off, m, c->econ_tiles, grid, st);
+      cudaError_t e =
+          launch_econ_tc(c->d, c->state + c->L.packed_off, m, (int)c->lc.econ_tiles, grid, st);
       if (e != cudaSuccess) return cuda_check(c, e, "econ_tc launch");
       launch_advance(c->d, m, st);
       done += m;
@@ -580,6 +603,9 @@ ws_status ws_create(const ws_config *cfg, void *state_buf, size_t state_bytes, v
   c->ring = (char *)ring_buf;
   c->seed = cfg->param_seed;
   make_dev(c);
+  default_launch(c);
+  c->d.env_threads = (int)c->lc.env_threads;
+  c->d.energy_chunks = (int)c->lc.energy_chunks;
   cudaError_t e = cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming);
   if (e == cudaSuccess && cfg->env == WS_ENV_ECONOMY) {
@@ -829,6 +855,170 @@ ws_status ws_sync(ws_ctx *c, uint32_t timeout_ms) {
 }
 
 const char *ws_last_error(const ws_ctx *c) { return c ? c->msg.c_str() : "null context"; }
+
+ws_status ws_get_launch(const ws_ctx *c, ws_launch *out) {
+  if (!c || !out) return WS_ERR_INVALID;
+  *out = c->lc;
+  return WS_OK;
+}
+
+ws_status ws_set_launch(ws_ctx *c, const ws_launch *l) {
+  if (!c || !l || l->struct_size != sizeof(ws_launch)) return WS_ERR_INVALID;
+  if (c->err != WS_OK) return c->err;
+  if (l->chunk_steps < 1 || (c->cfg.chunk_steps && l->chunk_steps != c->cfg.chunk_steps))
+    return WS_ERR_INVALID;
+  if (l->grid > 65535 || l->econ_tiles < 1 || l->econ_tiles > 3 || l->econ_lpt > 1)
+    return WS_ERR_INVALID;
+  if (c->L.econ_fused && (int)l->econ_tiles * 128 < max_agents(c)) return WS_ERR_INVALID;
+  if (l->energy_chunks != 1 && l->energy_chunks != 2 && l->energy_chunks != 4) return WS_ERR_INVALID;
+  if (c->d.eimg && !energy_tc_chunks_ok((int)c->cfg.n_gauss, (int)l->energy_chunks))
+    return WS_ERR_INVALID;
+  if (l->env_threads < 64 || l->env_threads > 1024 || l->env_threads % 32) return WS_ERR_INVALID;
+  const ws_launch old = c->lc;
+  c->lc = *l;
+  drop_graphs(c);  // graphs bake the launch parameters in
+  c->d.env_threads = (int)l->env_threads;
+  c->d.energy_chunks = (int)l->energy_chunks;
+  if (c->L.econ_fused && (old.econ_tiles != l->econ_tiles || old.econ_lpt != l->econ_lpt)) {
+    ws_status s = set_econ_items(c);
+    if (s != WS_OK) return s;
+  }
+  if (c->d.epart && old.energy_chunks != l->energy_chunks)  // unused partial slots read as zero
+    return cuda_check(c, cudaMemsetAsync(c->d.epart, 0, (size_t)kEnergyChunks * 2 * c->L.n_envs * 4,
+                                         c->stream), "launch change");
+  return WS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Process-wide cache of tuned launch configurations, keyed by the shape of the
+// configuration (everything that changes speed, nothing that changes results'
+// identity such as seeds).
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<ws_launch, float>> g_tune_cache;
+
+std::string tune_key(const ws_ctx *c) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  uint64_t h = 1469598103934665603ull;  // FNV-1a over the agent counts
+  for (int32_t a : c->agents) {
+    h ^= (uint32_t)a;
+    h *= 1099511628211ull;
+  }
+  char buf[256];
+  std::snprintf(buf, sizeof buf, "%d/%d/%u/%u/%u/%u/%u/%u/%u/%llx/%d/%d", c->cfg.env, c->cfg.path,
+                c->cfg.n_envs, c->cfg.hidden0, c->cfg.hidden1, c->cfg.dim, c->cfg.n_gauss,
+                c->cfg.chunk_steps, c->cfg.flags, (unsigned long long)h, dev, sm_count());
+  return buf;
+}
+
+// Candidate launch configurations of the context's path (cartesian product of
+// the knobs the path has; chunk lengths above the trial length are pointless).
+std::vector<ws_launch> tune_candidates(const ws_ctx *c, uint32_t trial) {
+  std::vector<uint32_t> chunks;
+  if (c->cfg.chunk_steps) {
+    chunks.push_back(c->cfg.chunk_steps);
+  } else if (c->cfg.path == WS_PATH_PLAIN_FP32) {
+    chunks.push_back(c->lc.chunk_steps);
+  } else {
+    const uint32_t opts_f[] = {25u, 50u, 100u, 200u}, opts_s[] = {10u, 25u, 50u};
+    const uint32_t *o = fused(c) ? opts_f : opts_s;
+    const int no = fused(c) ? 4 : 3;
+    for (int i = 0; i < no; ++i)
+      if (o[i] <= trial) chunks.push_back(o[i]);
+    if (chunks.empty()) chunks.push_back(trial);
+  }
+  std::vector<uint32_t> grids{0u}, tiles{c->lc.econ_tiles}, lpts{c->lc.econ_lpt},
+      echunks{c->lc.energy_chunks}, threads{c->lc.env_threads};
+  if (use_tc_control(&c->cfg)) {
+    const uint32_t n_tiles = (c->L.n_envs + 127) / 128, half = (n_tiles + 1) / 2;
+    if (half >= 1 && half < (uint32_t)c->tc_grid) grids.push_back(half);
+  }
+  if (c->L.econ_fused) {
+    tiles.clear();
+    for (uint32_t t = (uint32_t)((max_agents(c) + 127) / 128); t <= 3; ++t) tiles.push_back(t);
+    lpts = {1u, 0u};
+  }
+  if (c->d.eimg) {
+    echunks.clear();
+    for (uint32_t e : {1u, 2u, 4u})
+      if (energy_tc_chunks_ok((int)c->cfg.n_gauss, (int)e)) echunks.push_back(e);
+  }
+  if (!fused(c)) threads = {128u, 256u, 512u};
+  std::vector<ws_launch> v;
+  for (uint32_t ch : chunks)
+    for (uint32_t g : grids)
+      for (uint32_t t : tiles)
+        for (uint32_t lp : lpts)
+          for (uint32_t ec : echunks)
+            for (uint32_t th : threads) {
+              ws_launch l = c->lc;
+              l.chunk_steps = ch;
+              l.grid = g;
+              l.econ_tiles = t;
+              l.econ_lpt = lp;
+              l.energy_chunks = ec;
+              l.env_threads = th;
+              v.push_back(l);
+            }
+  return v;
+}
+
+}  // namespace
+
+extern "C" {
+
+ws_status ws_tune(ws_ctx *c, uint32_t trial_steps, ws_launch *chosen, float *ms_per_step) {
+  if (!c || trial_steps == 0) return WS_ERR_INVALID;
+  if (c->err != WS_OK) return c->err;
+  const std::string key = tune_key(c);
+  ws_launch best = c->lc;
+  float best_ms = -1.f;
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      best = it->second.first;
+      best_ms = it->second.second;
+    }
+  }
+  if (best_ms < 0.f) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ws_status s = cuda_check(c, cudaEventCreate(&e0), "tune event");
+    if (s == WS_OK) s = cuda_check(c, cudaEventCreate(&e1), "tune event");
+    for (const ws_launch &cand : tune_candidates(c, trial_steps)) {
+      if (s != WS_OK) break;
+      s = ws_set_launch(c, &cand);
+      if (s == WS_OK) s = ws_rollout(c, trial_steps);  // untimed: graph capture, warm caches
+      if (s == WS_OK) s = cuda_check(c, cudaEventRecord(e0, c->stream), "tune record");
+      if (s == WS_OK) s = ws_rollout(c, trial_steps);
+      if (s == WS_OK) s = cuda_check(c, cudaEventRecord(e1, c->stream), "tune record");
+      if (s == WS_OK) s = cuda_check(c, cudaEventSynchronize(e1), "tune sync");
+      if (s == WS_OK) s = ws_sync(c, 0);  // surfaces a device-side failure of the trial
+      float ms = 0.f;
+      if (s == WS_OK) s = cuda_check(c, cudaEventElapsedTime(&ms, e0, e1), "tune time");
+      if (s == WS_OK && (best_ms < 0.f || ms < best_ms)) {
+        best_ms = ms;
+        best = cand;
+      }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s != WS_OK) return s;
+    best_ms /= (float)trial_steps;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune_cache[key] = {best, best_ms};
+  }
+  ws_status s = ws_set_launch(c, &best);
+  if (s == WS_OK) s = ws_reset(c, c->seed);
+  if (s == WS_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream), "tune reset");
+  if (s != WS_OK) return s;
+  if (chosen) *chosen = best;
+  if (ms_per_step) *ms_per_step = best_ms;
+  return WS_OK;
+}
 
 void ws_destroy(ws_ctx *c) {
   if (!c) return;

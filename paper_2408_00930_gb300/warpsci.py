@@ -28,7 +28,8 @@ WS_PATH_PLAIN_FP32, WS_PATH_BATCHED_FP32, WS_PATH_BATCHED_BF16 = 0, 1, 2
 
 EXPORTED = ["ws_query_bytes", "ws_create", "ws_reset", "ws_step", "ws_rollout", "ws_returns",
             "ws_fetch", "ws_load", "ws_get_step", "ws_sync", "ws_last_error", "ws_destroy",
-            "ws_policy_forward_noalloc", "ws_server_create", "ws_server_submit",
+            "ws_policy_forward_noalloc", "ws_get_launch", "ws_set_launch", "ws_tune",
+            "ws_server_create", "ws_server_submit",
             "ws_server_wait_chunk", "ws_server_fetch", "ws_server_ack", "ws_server_release",
             "ws_server_get_stats", "ws_server_destroy"]
 WS_REQ_CONSUME_ON_READY = 1
@@ -43,6 +44,15 @@ class ws_config(C.Structure):
                 ("n_gauss", C.c_uint32), ("noise_sigma", C.c_float), ("step_clip", C.c_float),
                 ("gamma", C.c_float), ("flags", C.c_uint32), ("param_seed", C.c_uint64),
                 ("agents_per_env", C.POINTER(C.c_int32))]
+
+
+class ws_launch(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("chunk_steps", C.c_uint32), ("grid", C.c_uint32),
+                ("econ_tiles", C.c_uint32), ("econ_lpt", C.c_uint32),
+                ("energy_chunks", C.c_uint32), ("env_threads", C.c_uint32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "struct_size"}
 
 
 class ws_request(C.Structure):
@@ -98,6 +108,9 @@ def lib():
         L.ws_destroy.restype = None
         L.ws_policy_forward_noalloc.argtypes = [P, C.c_uint32, P, C.c_uint32, C.c_uint32,
                                                 C.c_uint32, C.c_uint32, P, P]
+        L.ws_get_launch.argtypes = [P, C.POINTER(ws_launch)]
+        L.ws_set_launch.argtypes = [P, C.POINTER(ws_launch)]
+        L.ws_tune.argtypes = [P, C.c_uint32, C.POINTER(ws_launch), C.POINTER(C.c_float)]
         L.ws_server_create.argtypes = [C.c_size_t, C.POINTER(P)]
         L.ws_server_submit.argtypes = [P, C.POINTER(ws_request), C.POINTER(C.c_uint64)]
         L.ws_server_wait_chunk.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint32]
@@ -160,6 +173,24 @@ def ws_get_step(ctx):
 
 def ws_sync(ctx, timeout_ms=0):
     return lib().ws_sync(ctx, timeout_ms)
+
+
+def ws_get_launch(ctx):
+    out = ws_launch()
+    out.struct_size = C.sizeof(ws_launch)
+    st = lib().ws_get_launch(ctx, C.byref(out))
+    return st, out
+
+
+def ws_set_launch(ctx, launch: ws_launch):
+    return lib().ws_set_launch(ctx, C.byref(launch))
+
+
+def ws_tune(ctx, trial_steps):
+    out = ws_launch()
+    ms = C.c_float()
+    st = lib().ws_tune(ctx, trial_steps, C.byref(out), C.byref(ms))
+    return st, out, ms.value
 
 
 def ws_last_error(ctx):
@@ -242,6 +273,23 @@ class Rollout:
 
     def sync(self, timeout_ms=0):
         self._ok(ws_sync(self.ctx, timeout_ms), "ws_sync")
+
+    def launch(self):
+        st, l = ws_get_launch(self.ctx)
+        self._ok(st, "ws_get_launch")
+        return l
+
+    def set_launch(self, **kw):
+        l = self.launch()
+        for k, v in kw.items():
+            setattr(l, k, v)
+        self._ok(ws_set_launch(self.ctx, l), "ws_set_launch")
+
+    def tune(self, trial_steps):
+        """Autotune the launch configuration (ends with a reset under the current seed)."""
+        st, l, ms = ws_tune(self.ctx, trial_steps)
+        self._ok(st, "ws_tune")
+        return l.as_dict(), ms
 
     @property
     def k(self):

@@ -32,7 +32,7 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(names) == set(W.EXPORTED) | set(n for n in names if n not in W.EXPORTED)
 
 
-@pytest.mark.parametrize("struct", ["ws_config", "ws_request", "ws_server_stats"])
+@pytest.mark.parametrize("struct", ["ws_config", "ws_request", "ws_server_stats", "ws_launch"])
 def test_struct_layout_matches_header(lib, tmp_path, struct):
     """Each ctypes mirror has the C compiler's size and field offsets."""
     import shutil
