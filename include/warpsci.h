@@ -61,9 +61,10 @@ typedef enum { WS_ENV_CONTROL = 0, WS_ENV_ECONOMY = 1, WS_ENV_LANDSCAPE = 2 } ws
  * host every step.  BATCHED_FP32: the same kernels, captured as a CUDA graph
  * per chunk of steps.  BATCHED_BF16: policy GEMMs (and the landscape
  * cross-term) on the tcgen05 tensor cores in BF16 with FP32 accumulation;
- * for the control env, and for the economy with 16-128-128-20 / -10 policies
- * and at most 384 agents per env, one persistent fused kernel runs a whole
- * chunk (the economy's over a device work queue of env groups). */
+ * for the control env, the economy with 16-128-128-20 / -10 policies and at
+ * most 384 agents per env, and the landscape with D in {8, 16, 24} and
+ * D-256-256-2D policies, one persistent fused kernel runs a whole chunk (the
+ * economy's over a device work queue of env groups). */
 typedef enum { WS_PATH_PLAIN_FP32 = 0, WS_PATH_BATCHED_FP32 = 1, WS_PATH_BATCHED_BF16 = 2 } ws_path;
 
 /* Fields of ws_fetch / ws_load.  Ring fields are time-major per step t:
@@ -202,8 +203,9 @@ void ws_destroy(ws_ctx *ctx);
  * persistent launch or captured graph, the persistent grid of the fused
  * control kernel, the rows per work item ("envs per CTA") of the fused economy
  * kernel and the order of its work queue, the Gaussian chunks per env tile of
- * the BF16 landscape energy kernel, and the block size of the per-step
- * kernels (envs per block).  A context starts with defaults; ws_tune times the
+ * the BF16 landscape energy kernel, the CTAs per env tile of the fused
+ * landscape kernel, and the block size of the per-step kernels (envs per
+ * block).  A context starts with defaults; ws_tune times the
  * candidates of its path on the device and keeps the fastest.
  * ------------------------------------------------------------------------ */
 typedef struct {
@@ -219,6 +221,8 @@ typedef struct {
   uint32_t energy_chunks;  /* BF16 landscape: Gaussian chunks per env tile (1, 2, 4)*/
   uint32_t env_threads;    /* per-step kernels: threads per block, 64..1024, a
                               multiple of 32                                        */
+  uint32_t tile_ctas;      /* fused landscape kernel: CTAs per 128-env tile, 1 or 2 (a
+                              cluster whose CTAs split the Gaussians)               */
 } ws_launch;
 
 /* The context's current launch configuration. */

@@ -121,6 +121,8 @@ struct Layout {
   size_t items_off;        // economy, fused kernel: work items [n_envs][4] i32
   size_t queue_off;        // economy, fused kernel: work-queue counters (2 x u32)
   int econ_fused;          // economy on the fused persistent kernel
+  int land_fused;          // landscape on the fused persistent kernel
+  size_t land_energy_off;  // landscape, fused kernel: its energy image (blocks of 64 Gaussians)
   size_t scratch_off;      // plain-path activations
   size_t scratch_h0_off, scratch_h1_off, scratch_out_off;
   size_t scratch_pobs_off, scratch_ph0_off, scratch_ph1_off, scratch_pout_off;

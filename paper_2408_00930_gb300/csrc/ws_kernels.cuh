@@ -119,6 +119,15 @@ void econ_tc_init();
 cudaError_t launch_econ_tc(const Dev &d, const void *packed, uint32_t n_steps, int tiles, int grid,
                            cudaStream_t st);
 
+// ---- fused persistent landscape kernel (ws_land_tc.cu) ----------------------------
+bool land_tc_supported(int D, int M, const PolicyShape &p);
+size_t land_tc_policy_bytes();
+size_t land_tc_energy_bytes(int M);
+void launch_land_tc_pack(const Dev &d, void *policy_img, void *energy_img, cudaStream_t st);
+void land_tc_init();
+cudaError_t launch_land_tc(const Dev &d, const void *policy_img, const void *energy_img,
+                           uint32_t n_steps, int tile_ctas, cudaStream_t st);
+
 // ---- BF16 tensor-core landscape energy (ws_energy_tc.cu) -------------------------
 size_t energy_tc_bytes(int D, int M);
 bool energy_tc_supported(int D, int M);

@@ -157,6 +157,15 @@ std::vector<int32_t> econ_items(const std::vector<int32_t> &agents, int cap_rows
   return out;
 }
 
+// Landscape on the BF16 path: the fused persistent kernel for the policy
+// shapes it holds (D in {8, 16, 24}, D-256-256-2D); the per-step tensor-core
+// kernels otherwise.  Resets still take the per-step energy kernel.
+bool use_land_fused(const ws_config *cfg, const PolicyShape &p) {
+  return cfg->env == WS_ENV_LANDSCAPE && cfg->path == WS_PATH_BATCHED_BF16 &&
+         land_tc_supported((int)cfg->dim, (int)cfg->n_gauss, p) &&
+         energy_tc_supported((int)cfg->dim, (int)cfg->n_gauss);
+}
+
 size_t tc_layers_bytes(const PolicyShape &p) {
   size_t n = 0;
   for (int l = 0; l < kMaxLayers; ++l) n += up(dense_tc_packed_bytes(p.w[l], p.w[l + 1]));
@@ -214,6 +223,8 @@ Layout make_layout(const ws_config *cfg, const std::vector<int32_t> &agents) {
   if (use_mlp3(cfg, L.pol, L.pol_planner))
     L.packed_bytes = up(mlp3_tc_packed_bytes(L.pol)) + up(mlp3_tc_packed_bytes(L.pol_planner));
   if (L.econ_fused) L.packed_bytes = econ_tc_packed_bytes();
+  L.land_fused = use_land_fused(cfg, L.pol) ? 1 : 0;
+  if (L.land_fused) L.packed_bytes = land_tc_policy_bytes();
   o += up(L.packed_bytes);
   L.env_params_off = o;
   if (cfg->env == WS_ENV_LANDSCAPE) o += up(M * D * 4) + up(M * 4) + up(M * 4);
@@ -222,6 +233,8 @@ Layout make_layout(const ws_config *cfg, const std::vector<int32_t> &agents) {
   L.env_derived_bytes = cfg->env == WS_ENV_LANDSCAPE ? up(M * 4) + up(M * 4) : 0;
   if (cfg->env == WS_ENV_LANDSCAPE && cfg->path == WS_PATH_BATCHED_BF16)
     L.env_derived_bytes += up(energy_tc_bytes((int)D, (int)M));
+  L.land_energy_off = L.env_derived_off + L.env_derived_bytes;
+  if (L.land_fused) L.env_derived_bytes += up(land_tc_energy_bytes((int)M));
   o += L.env_derived_bytes;
   L.state_off = o;
   if (cfg->env == WS_ENV_CONTROL) o += up(4 * N * 4);
@@ -327,6 +340,8 @@ void make_dev(ws_ctx *c) {
       d.out = (float *)(S + L.scratch_out_off);
       d.pout = (float *)(S + L.scratch_pout_off);
     }
+  } else if (L.land_fused) {
+    d.dbg_logits = (cfg.flags & WS_FLAG_DEBUG_LOGITS) ? 1 : 0;
   } else if (use_mlp3(&cfg, L.pol, L.pol_planner)) {
     d.tc_mlp = 1;
     d.mlp3 = 1;
@@ -372,7 +387,7 @@ void drop_graphs(ws_ctx *c) {
 }
 
 // Paths whose chunks run as one persistent kernel launch each.
-bool fused(const ws_ctx *c) { return use_tc_control(&c->cfg) || c->L.econ_fused; }
+bool fused(const ws_ctx *c) { return use_tc_control(&c->cfg) || c->L.econ_fused || c->L.land_fused; }
 
 uint32_t chunk_of(const ws_ctx *c) { return c->lc.chunk_steps; }
 
@@ -400,6 +415,9 @@ void default_launch(ws_ctx *c) {
   l.econ_lpt = 1;
   l.energy_chunks = 2;
   l.env_threads = 256;
+  // fused landscape: a CTA pair per tile while the pairs fit the SMs at once
+  const uint32_t tiles = (c->L.n_envs + 127) / 128;
+  l.tile_ctas = 2 * tiles <= (uint32_t)sm_count() ? 2u : 1u;
 }
 
 int econ_grid(const ws_ctx *c) {
@@ -430,6 +448,16 @@ ws_status enqueue_steps(ws_ctx *c, uint32_t n, cudaStream_t st) {
       const int grid = c->lc.grid ? (int)c->lc.grid : c->tc_grid;
       cudaError_t e = launch_control_tc(c->d, c->state + c->L.packed_off, m, grid, st);
       if (e != cudaSuccess) return cuda_check(c, e, "control_tc launch");
+      launch_advance(c->d, m, st);
+      done += m;
+    }
+  } else if (c->L.land_fused) {
+    const uint32_t chunk = chunk_of(c);
+    for (uint32_t done = 0; done < n;) {
+      const uint32_t m = (n - done) < chunk ? (n - done) : chunk;
+      cudaError_t e = launch_land_tc(c->d, c->state + c->L.packed_off, c->state + c->L.land_energy_off,
+                                     m, (int)c->lc.tile_ctas, st);
+      if (e != cudaSuccess) return cuda_check(c, e, "land_tc launch");
       launch_advance(c->d, m, st);
       done += m;
     }
@@ -528,7 +556,7 @@ std::vector<Piece> state_pieces(ws_ctx *c, ws_field f) {
     }
   } else if (f == WS_F_LOGITS) {
     if (L.env == WS_ENV_CONTROL && use_tc_control(&c->cfg)) return v;
-    if (L.econ_fused && !c->d.dbg_logits) return v;
+    if ((L.econ_fused || L.land_fused) && !c->d.dbg_logits) return v;
     v.push_back({S + L.scratch_out_off, (size_t)L.n_agent_slots * L.n_out * 4});
     if (L.env == WS_ENV_ECONOMY) v.push_back({S + L.scratch_pout_off, N * 10 * 4});
   }
@@ -541,6 +569,8 @@ ws_status after_params_changed(ws_ctx *c) {
   if (use_tc_control(&c->cfg)) launch_control_tc_pack(c->d, c->state + c->L.packed_off, c->stream);
   if (c->L.econ_fused) {
     launch_econ_tc_pack(c->d.params, c->d.params_planner, c->state + c->L.packed_off, c->stream);
+  } else if (c->L.land_fused) {
+    launch_land_tc_pack(c->d, c->state + c->L.packed_off, c->state + c->L.land_energy_off, c->stream);
   } else if (c->d.mlp3) {
     launch_mlp3_tc_pack(c->d.params, c->L.pol, (void *)c->d.pk[0][0], c->stream);
     launch_mlp3_tc_pack(c->d.params_planner, c->L.pol_planner, (void *)c->d.pk[1][0], c->stream);
@@ -655,6 +685,7 @@ ws_status ws_create(const ws_config *cfg, void *state_buf, size_t state_bytes, v
   if (use_tc_layers(cfg)) dense_tc_init();
   if (c->d.mlp3) mlp3_tc_init();
   if (use_tc_layers(cfg) && cfg->env == WS_ENV_LANDSCAPE) energy_tc_init((int)cfg->n_gauss);
+  if (c->L.land_fused) land_tc_init();
   s = after_params_changed(c);
   if (s == WS_OK) s = ws_reset(c, cfg->param_seed);
   if (s == WS_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream), "create sync");
@@ -740,7 +771,8 @@ ws_status ws_fetch_async(ws_ctx *c, ws_field f, uint64_t t0, uint32_t n, void *d
   const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (f == WS_F_STATE || f == WS_F_PARAMS || f == WS_F_ENV_PARAMS || f == WS_F_LOGITS) {
     if (t0 != 0 || n != 0) return WS_ERR_INVALID;
-    if (f == WS_F_LOGITS && (use_tc_control(&c->cfg) || (c->L.econ_fused && !c->d.dbg_logits)))
+    if (f == WS_F_LOGITS &&
+        (use_tc_control(&c->cfg) || ((c->L.econ_fused || c->L.land_fused) && !c->d.dbg_logits)))
       return WS_ERR_UNSUPPORTED;
     std::vector<Piece> v = state_pieces(c, f);
     if (v.empty()) return WS_ERR_INVALID;
@@ -874,6 +906,7 @@ ws_status ws_set_launch(ws_ctx *c, const ws_launch *l) {
   if (c->d.eimg && !energy_tc_chunks_ok((int)c->cfg.n_gauss, (int)l->energy_chunks))
     return WS_ERR_INVALID;
   if (l->env_threads < 64 || l->env_threads > 1024 || l->env_threads % 32) return WS_ERR_INVALID;
+  if (l->tile_ctas != 1 && l->tile_ctas != 2) return WS_ERR_INVALID;
   const ws_launch old = c->lc;
   c->lc = *l;
   drop_graphs(c);  // graphs bake the launch parameters in
@@ -931,7 +964,8 @@ std::vector<ws_launch> tune_candidates(const ws_ctx *c, uint32_t trial) {
     if (chunks.empty()) chunks.push_back(trial);
   }
   std::vector<uint32_t> grids{0u}, tiles{c->lc.econ_tiles}, lpts{c->lc.econ_lpt},
-      echunks{c->lc.energy_chunks}, threads{c->lc.env_threads};
+      echunks{c->lc.energy_chunks}, threads{c->lc.env_threads}, tctas{c->lc.tile_ctas};
+  if (c->L.land_fused) tctas = {1u, 2u};
   if (use_tc_control(&c->cfg)) {
     const uint32_t n_tiles = (c->L.n_envs + 127) / 128, half = (n_tiles + 1) / 2;
     if (half >= 1 && half < (uint32_t)c->tc_grid) grids.push_back(half);
@@ -941,7 +975,7 @@ std::vector<ws_launch> tune_candidates(const ws_ctx *c, uint32_t trial) {
     for (uint32_t t = (uint32_t)((max_agents(c) + 127) / 128); t <= 3; ++t) tiles.push_back(t);
     lpts = {1u, 0u};
   }
-  if (c->d.eimg) {
+  if (c->d.eimg && !c->L.land_fused) {
     echunks.clear();
     for (uint32_t e : {1u, 2u, 4u})
       if (energy_tc_chunks_ok((int)c->cfg.n_gauss, (int)e)) echunks.push_back(e);
@@ -953,8 +987,10 @@ std::vector<ws_launch> tune_candidates(const ws_ctx *c, uint32_t trial) {
       for (uint32_t t : tiles)
         for (uint32_t lp : lpts)
           for (uint32_t ec : echunks)
-            for (uint32_t th : threads) {
+            for (uint32_t th : threads)
+              for (uint32_t tcs : tctas) {
               ws_launch l = c->lc;
+              l.tile_ctas = tcs;
               l.chunk_steps = ch;
               l.grid = g;
               l.econ_tiles = t;

@@ -100,7 +100,8 @@ def test_landscape_bf16_outputs_and_step(torch):
     x0, eobs0, t0 = inputs.landscape_state(g, n, D)
     x0[:30] = (c[:30] + g.normal(0, 0.3, (30, D))).astype(np.float32)
     params = inputs.policy_params(g, [D, *h, 2 * D])
-    r = W.Rollout(W.WS_ENV_LANDSCAPE, BF16, n, 8, 1000, *h, dim=D, n_gauss=M)
+    r = W.Rollout(W.WS_ENV_LANDSCAPE, BF16, n, 8, 1000, *h, dim=D, n_gauss=M,
+                  flags=W.WS_FLAG_DEBUG_LOGITS)
     r.load_raw(W.WS_F_ENV_PARAMS, np.concatenate([c.astype(np.float32).ravel(),
                                                   wd.astype(np.float32), am.astype(np.float32)]))
     r.load_raw(W.WS_F_PARAMS, params)
