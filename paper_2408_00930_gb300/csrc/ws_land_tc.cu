@@ -19,11 +19,13 @@
 //   sample   diagonal Gaussian head: mean, log sigma clamped to [-5, 2],
 //            dx = clip(mean + sigma z) with Philox normals; log-probability of the
 //            unclipped sample
-//   energy   E(y) at y = x + dx: the cross-term y.c on tcgen05 as
-//            [y_hi, y_hi, y_lo] . [c_hi, c_lo, c_hi] (BF16 hi+lo, FP32 accumulate)
-//            in blocks of 64 Gaussians streamed by a producer warp (bulk copies
-//            into two buffers, MMAs into two TMEM accumulators), and the epilogue
-//            a_m 2^(q_m (|y|^2 + |c_m|^2 - 2 y.c_m)) summed per env
+//   energy   E(y) at y = x + dx, whole exponents on tcgen05: with q_m =
+//            -log2(e) / (2 w_m^2), q_m |y - c_m|^2 = -2 q_m y.c_m + q_m |c_m|^2 +
+//            q_m |y|^2 is one dot product of the operand row [y, 1, |y|^2] with the
+//            Gaussian row [-2 q c, q |c|^2, q], every product split BF16 hi+lo
+//            (FP32 accumulate), in blocks of 64 Gaussians streamed by a producer
+//            warp (bulk copies into three buffers, MMAs into three TMEM
+//            accumulators); the epilogue is a_m 2^(exponent) summed per env
 //   step     observed energy with Philox noise, reward Eobs(x) - Eobs(x'), done
 //            at the episode limit, reset to U(-3, 3)^D and a second sweep for the
 //            fresh state's energy when a tile has a reset
@@ -43,10 +45,10 @@ constexpr int kH = 256;                       // hidden width of both layers
 constexpr int kMaxD = 24;                     // coordinates (a multiple of 8, <= 24)
 constexpr int kN3 = 48;                       // layer-3 N (2 D, padded to 48)
 constexpr int kK1 = 32;                       // layer-1 K: D coordinates, 1, 1, zeros
-constexpr int kKE = 80;                       // energy K: 3 D <= 72, five K16 steps
+constexpr int kKE = 80;                       // energy K: 3 D + 5 <= 80, five K16 steps
 constexpr int kBlk = 64;                      // Gaussians per energy MMA block
 constexpr int kBlkImg = kBlk * kKE * 2;       // block image, K = 80 without swizzle
-constexpr int kBlkBytes = kBlkImg + kBlk * 16;  // + {|c|^2, q, a, 0} per Gaussian
+constexpr int kBlkBytes = kBlkImg + kBlk * 4;  // + the amplitudes a_m
 constexpr int kEpi = 256, kThreads = kEpi + 32;
 constexpr uint64_t kWaitNs = 2000000000ull;
 
@@ -61,12 +63,14 @@ constexpr int PK_B3 = PK_B2 + kH * 4;
 constexpr int POLICY = PK_B3 + 64 * 4;
 
 // shared memory
+constexpr int kNB = 3;                            // energy blocks in flight (buffers)
 constexpr int OFF_AE = POLICY;                    // energy A [128][80] (also the layer-1 A [128][32])
-constexpr int OFF_BE = OFF_AE + kRows * kKE * 2;  // two energy B blocks
-constexpr int OFF_XCH = OFF_BE + 2 * kBlkBytes;   // f32 [128] partial energies, [128] |y|^2
-constexpr int OFF_RECV = OFF_XCH + 2 * kRows * 4; // f32 [2][128] the cluster partner's partials
+constexpr int OFF_BE = OFF_AE + kRows * kKE * 2;  // kNB energy B blocks
+constexpr int OFF_XCH = OFF_BE + kNB * kBlkBytes; // f32 [128] each: partial energy, log-probability,
+                                                  // |y|^2 of half 0 and of half 1
+constexpr int OFF_RECV = OFF_XCH + 4 * kRows * 4; // f32 [2][128] the cluster partner's partials
 constexpr int OFF_BAR = OFF_RECV + 2 * kRows * 4;
-constexpr int N_BAR = 10;  // ae, b[2], mma[2], epi[2], pol, x, drain
+constexpr int N_BAR = 4 + 3 * kNB;  // ae, b[kNB], mma[kNB], epi[kNB], pol, x, drain
 constexpr int OFF_CMD = OFF_BAR + N_BAR * 8;
 constexpr int OFF_TM = OFF_CMD + 16;
 constexpr int SMEM = OFF_TM + 16 + 1024;
@@ -76,7 +80,9 @@ static_assert(PK_W3 % 1024 == 0 && (4 * kN3 * 128) % 1024 == 0 && (kN3 * 128) % 
 static_assert(OFF_AE % 128 == 0 && OFF_BE % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
 
 constexpr uint32_t TM_H = 256;   // TMEM columns of h1 / h2 (packed BF16 A operand)
-constexpr uint32_t TM_E = 384;   // TMEM columns of the two energy accumulators
+constexpr uint32_t TM_E = 256;   // TMEM columns of the energy accumulators (during a sweep the
+                                 // policy's columns are free)
+static_assert(TM_E + kNB * kBlk <= 512, "energy accumulators");
 
 __device__ __forceinline__ uint16_t bf16_bits(float f) {
   return (uint16_t)(tc::pack_bf16x2(f, 0.f) & 0xFFFFu);
@@ -116,9 +122,11 @@ __global__ void k_land_tc_pack_policy(const float *__restrict__ p, int D, uint8_
   for (int i = tid; i < 64; i += stride) ((float *)(out + PK_B3))[i] = i < 2 * D ? b3[i] : 0.f;
 }
 
-// Energy image: per block of 64 Gaussians, the B operand rows
-// [c_hi (D), c_lo (D), c_hi (D), 0...] (K = 80, no swizzle) followed by the
-// table {|c|^2, q = -log2(e) / (2 w^2), a, 0}; Gaussians beyond M have a = 0.
+// Energy image: per block of 64 Gaussians, the B operand rows (K = 80, no
+// swizzle) [v_hi (D) | v_lo (D) | v_hi (D) | s_hi, s_lo | q_hi, q_lo, q_hi | 0...]
+// with v = -2 q c, s = q |c|^2, q = -log2(e) / (2 w^2), against the operand row
+// [y_hi | y_hi | y_lo | 1, 1 | yy_hi, yy_hi, yy_lo | 0...] (yy = |y|^2), then the
+// amplitudes a_m; Gaussians beyond M have a = 0.
 __global__ void k_land_tc_pack_energy(const float *__restrict__ c, const float *__restrict__ w,
                                       const float *__restrict__ a, int D, int M, int Mp,
                                       uint8_t *__restrict__ img) {
@@ -126,25 +134,25 @@ __global__ void k_land_tc_pack_energy(const float *__restrict__ c, const float *
   for (int i = tid; i < Mp * kKE; i += stride) {
     const int m = i / kKE, k = i % kKE;
     float v = 0.f;
-    if (m < M && k < 3 * D) {
-      const float x = c[(size_t)m * D + (k % D)];
-      const float hi = bf16_val(x);
-      v = (k / D == 1) ? x - hi : x;
+    if (m < M && k < 3 * D + 5) {
+      const float q = -1.4426950408889634f / (2.0f * w[m] * w[m]);
+      if (k < 3 * D) {
+        const float x = -2.0f * q * c[(size_t)m * D + (k % D)];
+        v = (k / D == 1) ? x - bf16_val(x) : x;
+      } else if (k < 3 * D + 2) {
+        float s = 0.f;
+        for (int j = 0; j < D; ++j) s = fmaf(c[(size_t)m * D + j], c[(size_t)m * D + j], s);
+        const float x = q * s;
+        v = k == 3 * D ? x : x - bf16_val(x);
+      } else {
+        v = k == 3 * D + 3 ? q - bf16_val(q) : q;
+      }
     }
     const int blk = m / kBlk, n = m % kBlk;
     *(uint16_t *)(img + (size_t)blk * kBlkBytes + ns_off(n, k, kKE)) = bf16_bits(v);
   }
-  for (int m = tid; m < Mp; m += stride) {
-    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (m < M) {
-      float s = 0.f;
-      for (int j = 0; j < D; ++j) s = fmaf(c[(size_t)m * D + j], c[(size_t)m * D + j], s);
-      t.x = s;
-      t.y = -1.4426950408889634f / (2.0f * w[m] * w[m]);
-      t.z = a[m];
-    }
-    *(float4 *)(img + (size_t)(m / kBlk) * kBlkBytes + kBlkImg + (m % kBlk) * 16) = t;
-  }
+  for (int m = tid; m < Mp; m += stride)
+    *(float *)(img + (size_t)(m / kBlk) * kBlkBytes + kBlkImg + (m % kBlk) * 4) = m < M ? a[m] : 0.f;
 }
 
 // ---- helpers ---------------------------------------------------------------------
@@ -280,14 +288,15 @@ template <int D, int CL>
 __global__ void __launch_bounds__(kThreads, 1)
     k_land_tc(Dev d, const uint8_t *__restrict__ pol, const uint8_t *__restrict__ eimg, int n_blk,
               uint32_t n_steps) {
+  constexpr int DH = D / 2;  // coordinates per thread of a row (two threads per row)
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = tc::smem_u32(smem_raw);
   uint8_t *sm = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
   const uint32_t sb = tc::smem_u32(sm);
   const int tid = threadIdx.x, warp = tid >> 5;
   uint64_t *bars = (uint64_t *)(sm + OFF_BAR);
-  uint64_t *bar_ae = bars, *bar_b = bars + 1, *bar_mma = bars + 3, *bar_epi = bars + 5;
-  uint64_t *bar_pol = bars + 7, *bar_x = bars + 8, *bar_drain = bars + 9;
+  uint64_t *bar_ae = bars, *bar_b = bars + 1, *bar_mma = bar_b + kNB, *bar_epi = bar_mma + kNB;
+  uint64_t *bar_pol = bar_epi + kNB, *bar_x = bar_pol + 1, *bar_drain = bar_x + 1;
   volatile uint32_t *cmd = (volatile uint32_t *)(sm + OFF_CMD);
   uint32_t *tm_holder = (uint32_t *)(sm + OFF_TM);
   const uint32_t rank = CL > 1 ? cluster_rank() : 0u;
@@ -299,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (tid == 0) {
     tc::mbar_init(bar_ae, kEpi);
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kNB; ++i) {
       tc::mbar_init(bar_b + i, 1);
       tc::mbar_init(bar_mma + i, 1);
       tc::mbar_init(bar_epi + i, kEpi);
@@ -323,27 +332,36 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (tid >= kEpi) {
     // ===================== producer: energy blocks in, MMAs out =====================
+    // Block g of this CTA's sweep sequence sits in buffer g % kNB (shared memory
+    // and TMEM accumulator alike).  The load of block g + 2 is issued once block
+    // g - 1 is consumed, so two loads stay in flight ahead of the epilogue.
     if (tid == kEpi) {
       const uint8_t *src0 = eimg + (size_t)rank * n_blk * kBlkBytes;
       constexpr uint32_t idesc = tc::idesc_bf16_f32(128, kBlk);
-      uint32_t g = 0, pa = 0;
-      auto load = [&](uint32_t gg) -> bool {
-        const uint32_t b = gg & 1u;
-        if (gg >= 2 && !tc::mbar_wait(bar_epi + b, ((gg >> 1) - 1u) & 1u, kWaitNs)) return false;
+      uint32_t pa = 0, ph_b = 0, ph_e = 0;  // parities (one bit per buffer)
+      uint32_t g = 0, gl = 0;               // next block to MMA, next block to load
+      auto load = [&]() -> bool {
+        const uint32_t b = gl % kNB;
+        if (gl >= (uint32_t)kNB) {           // buffer b: block gl - kNB consumed
+          if (!tc::mbar_wait(bar_epi + b, (ph_e >> b) & 1u, kWaitNs)) return false;
+          ph_e ^= 1u << b;
+        }
         mbar_expect_tx(bar_b + b, kBlkBytes);
-        bulk_g2s(sb + OFF_BE + b * kBlkBytes, src0 + (size_t)(gg % (uint32_t)n_blk) * kBlkBytes,
+        bulk_g2s(sb + OFF_BE + b * kBlkBytes, src0 + (size_t)(gl % (uint32_t)n_blk) * kBlkBytes,
                  kBlkBytes, bar_b + b);
+        ++gl;
         return true;
       };
-      bool loaded = load(0);
-      fail = !loaded;
+      load();
+      load();
       while (!fail) {
         if (!tc::mbar_wait(bar_ae, pa, kWaitNs)) { fail = true; break; }
         pa ^= 1u;
         if (*cmd == 0u) break;
         for (int i = 0; i < n_blk && !fail; ++i, ++g) {
-          const uint32_t b = g & 1u;
-          if (!tc::mbar_wait(bar_b + b, (g >> 1) & 1u, kWaitNs)) { fail = true; loaded = false; break; }
+          const uint32_t b = g % kNB;
+          if (!tc::mbar_wait(bar_b + b, (ph_b >> b) & 1u, kWaitNs)) { fail = true; break; }
+          ph_b ^= 1u << b;
           tc::fence_after_sync();
 #pragma unroll
           for (int s = 0; s < kKE / 16; ++s) {
@@ -354,11 +372,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc::mma_bf16(tbase + TM_E + b * kBlk, da, db, idesc, s != 0);
           }
           tc::mma_commit(bar_mma + b);
-          if (!load(g + 1)) { fail = true; loaded = false; }
+          if (!load()) fail = true;
         }
       }
-      // the prefetched block g is in flight: wait for it before shared memory goes away
-      if (loaded) tc::mbar_wait(bar_b + (g & 1u), (g >> 1) & 1u, kWaitNs);
+      // blocks g .. gl - 1 were loaded ahead: their copies finish before shared
+      // memory goes away
+      if (!fail)
+        for (uint32_t q = g; q < gl; ++q) {
+          const uint32_t b = q % kNB;
+          tc::mbar_wait(bar_b + b, (ph_b >> b) & 1u, kWaitNs);
+          ph_b ^= 1u << b;
+        }
       tc::mma_commit(bar_drain);
       tc::mbar_wait(bar_drain, 0, kWaitNs);
       if (fail) {
@@ -368,11 +392,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ===================== epilogue: env rows =====================
+    // Row r is served by thread r (half 0: the env's record writer, its energy
+    // and observed energy) and thread r + 128 (half 1); each half holds and
+    // samples D / 2 of the row's coordinates and takes half of every tanh and
+    // exp epilogue.
     const int r = tid & 127, h = tid >> 7;
-    const bool own = h == 0;  // warps 0-3 hold the env state
+    const bool own = h == 0;
+    const int j0 = h * DH;
     const uint32_t lane_sel = (uint32_t)((warp & 3) * 32) << 16;
     const uint32_t pair = kBarPair0 + (uint32_t)(warp & 3);
-    float *xch_e = (float *)(sm + OFF_XCH), *xch_y = xch_e + kRows;
+    float *xch_e = (float *)(sm + OFF_XCH), *xch_lp = xch_e + kRows, *xch_yy = xch_lp + kRows;
     float *recv = (float *)(sm + OFF_RECV);
     const uint64_t seed = d.seed;
     const uint64_t k0 = d.k[0];
@@ -382,7 +411,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const float half_log_2pi = 0.91893853320467274f;
     constexpr uint32_t id_pol = tc::idesc_bf16_f32(128, kH);
     constexpr uint32_t id_out = tc::idesc_bf16_f32(128, kN3);
-    uint32_t pp = 0, ge = 0, px = 0, par = 0;
+    uint32_t pp = 0, ge = 0, px = 0, par = 0, ph_m = 0, ph_bt = 0;
     // After a wait has run out no other wait is attempted: the CTA runs on to the
     // vote at the next step boundary and leaves together.
     auto wait = [&](uint64_t *bar, uint32_t parity) {
@@ -391,30 +420,39 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t partner = rank ^ 1u;
     const uint32_t recv_remote = CL > 1 ? mapa(sb + OFF_RECV, partner) : 0u;
     const uint32_t barx_remote = CL > 1 ? mapa(tc::smem_u32(bar_x), partner) : 0u;
+    const uint32_t a1_row = sb + OFF_AE + (uint32_t)(r >> 3) * (kK1 * 16) + (uint32_t)(r & 7) * 16u;
+    const uint32_t ae_row = sb + OFF_AE + (uint32_t)(r >> 3) * (kKE * 16) + (uint32_t)(r & 7) * 16u;
+    // byte offset of element k within a row of a K-major operand without swizzle
+    auto kofs = [](int k) -> uint32_t { return (uint32_t)((k >> 3) * 128 + (k & 7) * 2); };
 
-    // One energy sweep over this CTA's Gaussians at the rows written to the
-    // energy operand; returns the whole-landscape energy on the owner threads.
-    auto sweep = [&](float yy) -> float {
+    // One energy sweep over this CTA's Gaussians at the rows of the energy
+    // operand; returns the whole-landscape energy on half 0.
+    auto sweep = [&]() -> float {
       if (tid == 0) *cmd = 1u;
       tc::fence_async_smem();
       mbar_arrive(bar_ae);
       float part = 0.f;
       for (int i = 0; i < n_blk; ++i, ++ge) {
-        const uint32_t b = ge & 1u;
-        wait(bar_mma + b, (ge >> 1) & 1u);
-        // the block's table arrived by bulk copy: observe its completion before
-        // reading it with ordinary loads (its phase is the one the MMA waited on)
-        wait(bar_b + b, (ge >> 1) & 1u);
+        const uint32_t b = ge % kNB;
+        wait(bar_mma + b, (ph_m >> b) & 1u);
+        ph_m ^= 1u << b;
+        // the block's amplitudes arrived by bulk copy: observe that copy's
+        // completion before reading them with ordinary loads (they cannot be
+        // overwritten before this thread marks the block consumed)
+        wait(bar_b + b, (ph_bt >> b) & 1u);
+        ph_bt ^= 1u << b;
         tc::fence_after_sync();
         uint32_t z[32];
         tc::tmem_ld32(tbase + lane_sel + TM_E + b * kBlk + (uint32_t)(32 * h), z);
         tc::tmem_wait_ld();
-        const uint32_t tab = sb + OFF_BE + b * kBlkBytes + kBlkImg + (uint32_t)(32 * h) * 16u;
+        const uint32_t amp = sb + OFF_BE + b * kBlkBytes + kBlkImg + (uint32_t)(32 * h) * 4u;
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          const float4 t = lds128f(tab + 16u * (uint32_t)c);
-          const float d2 = fmaf(-2.0f, __uint_as_float(z[c]), yy + t.x);
-          part = fmaf(t.z, ex2_fast(d2 * t.y), part);
+        for (int c = 0; c < 32; c += 4) {
+          const float4 a = lds128f(amp + 4u * (uint32_t)c);
+          part = fmaf(a.x, ex2_fast(__uint_as_float(z[c])), part);
+          part = fmaf(a.y, ex2_fast(__uint_as_float(z[c + 1])), part);
+          part = fmaf(a.z, ex2_fast(__uint_as_float(z[c + 2])), part);
+          part = fmaf(a.w, ex2_fast(__uint_as_float(z[c + 3])), part);
         }
         tc::fence_before_sync();
         mbar_arrive(bar_epi + b);
@@ -437,82 +475,75 @@ __global__ void __launch_bounds__(kThreads, 1)
       bar_sync_n(pair, 64);  // xch_e is free again
       return E;
     };
-    // Energy operand row [y_hi | y_hi | y_lo | 0] (K = 80) of the owner's row;
-    // |y|^2 (FP32) goes to both threads of the row.
-    auto write_ae = [&](const float (&y)[kMaxD]) -> float {
+    // The energy operand row [v_hi | v_hi | v_lo | 1, 1 | vv_hi, vv_hi, vv_lo | 0]
+    // (K = 80): each half writes its coordinates in pieces of four; after the
+    // two halves' sums of squares meet, half 1 writes the constant and |v|^2
+    // columns and the zero tail.  lp (half 1's log-probability part) rides along
+    // to half 0.
+    auto write_ae = [&](const float (&v)[DH], float lp_part) {
       float yy = 0.f;
-      if (own) {
-        uint32_t hi[kMaxD / 2], lo[kMaxD / 2];
 #pragma unroll
-        for (int j = 0; j < kMaxD; j += 2) {
-          const float a0 = j < D ? y[j] : 0.f, a1 = j + 1 < D ? y[j + 1] : 0.f;
-          yy = fmaf(a0, a0, yy);
-          yy = fmaf(a1, a1, yy);
-          const uint32_t hp = tc::pack_bf16x2(a0, a1);
-          hi[j / 2] = hp;
-          lo[j / 2] = tc::pack_bf16x2(a0 - tc::bf16_lo(hp), a1 - tc::bf16_hi(hp));
-        }
-        const uint32_t row = sb + OFF_AE + (uint32_t)(r >> 3) * (kKE * 16) + (uint32_t)(r & 7) * 16u;
-        constexpr int nc = D / 8;  // chunks of 8 per third
-#pragma unroll
-        for (int c = 0; c < kKE / 8; ++c) {
-          uint32_t q0 = 0u, q1 = 0u, q2 = 0u, q3 = 0u;
-          const int third = c / nc, cc = c % nc;
-          if (c < 3 * nc) {
-            // thirds 0 and 1: y_hi; third 2: y_lo
-#pragma unroll
-            for (int u = 0; u < kMaxD / 8; ++u) {
-              if (u == cc) {
-                const uint32_t *src = third == 2 ? lo : hi;
-                q0 = src[4 * u];
-                q1 = src[4 * u + 1];
-                q2 = src[4 * u + 2];
-                q3 = src[4 * u + 3];
-              }
-            }
-          }
-          tc::sts128(row + (uint32_t)c * 128u, q0, q1, q2, q3);
-        }
-        xch_y[r] = yy;
+      for (int q = 0; q < DH / 4; ++q) {
+        const float a0 = v[4 * q], a1 = v[4 * q + 1], a2 = v[4 * q + 2], a3 = v[4 * q + 3];
+        yy = fmaf(a0, a0, yy);
+        yy = fmaf(a1, a1, yy);
+        yy = fmaf(a2, a2, yy);
+        yy = fmaf(a3, a3, yy);
+        const uint32_t h01 = tc::pack_bf16x2(a0, a1), h23 = tc::pack_bf16x2(a2, a3);
+        const uint32_t l01 = tc::pack_bf16x2(a0 - tc::bf16_lo(h01), a1 - tc::bf16_hi(h01));
+        const uint32_t l23 = tc::pack_bf16x2(a2 - tc::bf16_lo(h23), a3 - tc::bf16_hi(h23));
+        const int j = j0 + 4 * q;
+        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(ae_row + kofs(j)), "r"(h01), "r"(h23) : "memory");
+        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(ae_row + kofs(D + j)), "r"(h01), "r"(h23) : "memory");
+        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(ae_row + kofs(2 * D + j)), "r"(l01), "r"(l23) : "memory");
       }
+      if (!own) xch_lp[r] = lp_part;
+      xch_yy[h * kRows + r] = yy;
       bar_sync_n(pair, 64);
-      if (!own) yy = xch_y[r];
-      return yy;
+      if (!own) {
+        const float vv = xch_yy[r] + xch_yy[kRows + r];
+        const uint32_t hv = tc::pack_bf16x2(vv, 0.f) & 0xFFFFu;
+        const uint32_t lv = tc::pack_bf16x2(vv - __uint_as_float(hv << 16), 0.f) & 0xFFFFu;
+#pragma unroll
+        for (int c = 3 * D / 8; c < kKE / 8; ++c) {
+          if (c == 3 * D / 8)  // [1, 1, vv_hi, vv_hi, vv_lo, 0, 0, 0]
+            tc::sts128(ae_row + (uint32_t)c * 128u, tc::pack_bf16x2(1.f, 1.f), hv | (hv << 16), lv, 0u);
+          else
+            tc::sts128(ae_row + (uint32_t)c * 128u, 0u, 0u, 0u, 0u);
+        }
+      }
     };
 
     for (int tile = cid; tile < n_tiles && !fail; tile += n_clus) {
       const uint32_t e = (uint32_t)tile * kRows + (uint32_t)r;
       const bool valid = e < N;
-      float x[kMaxD];
+      float x[DH];
       float eobs = 0.f;
       int t = 0;
 #pragma unroll
-      for (int j = 0; j < kMaxD; ++j) x[j] = (own && valid && j < D) ? d.s[(size_t)j * N + e] : 0.f;
-      if (own && valid) {
-        eobs = d.eobs[e];
+      for (int i = 0; i < DH; ++i) x[i] = valid ? d.s[(size_t)(j0 + i) * N + e] : 0.f;
+      if (valid) {
         t = d.t[e];
+        if (own) eobs = d.eobs[e];
       }
-      const bool rec = own && valid && rank == 0;
+      const bool rec = valid && rank == 0;  // this thread writes its part of the records
       for (uint32_t s = 0; s < n_steps; ++s) {
         const uint32_t k = (uint32_t)(k0 + s);
         const size_t rowR = (size_t)((k0 + s) % R);
         // ---- observation record and the layer-1 operand row [x, 1, 1, 0...]
-        if (own) {
-          if (rec)
-            for (int j = 0; j < D; ++j) d.r_obs[(rowR * D + (size_t)j) * S + e] = x[j];
-          const uint32_t row = sb + OFF_AE + (uint32_t)(r >> 3) * (kK1 * 16) + (uint32_t)(r & 7) * 16u;
+        if (rec)
 #pragma unroll
-          for (int c = 0; c < kK1 / 8; ++c) {
-            uint32_t q[4];
+          for (int i = 0; i < DH; ++i) d.r_obs[(rowR * D + (size_t)(j0 + i)) * S + e] = x[i];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int j = 8 * c + 2 * u;
-              const float a0 = j < D ? x[j < kMaxD ? j : 0] : (j == D ? 1.f : 0.f);
-              const float a1 = j + 1 < D ? x[j + 1 < kMaxD ? j + 1 : 0] : (j + 1 == D + 1 ? 1.f : 0.f);
-              q[u] = tc::pack_bf16x2(a0, a1);
-            }
-            tc::sts128(row + (uint32_t)c * 128u, q[0], q[1], q[2], q[3]);
-          }
+        for (int q = 0; q < DH / 4; ++q) {
+          const uint32_t a = tc::pack_bf16x2(x[4 * q], x[4 * q + 1]);
+          const uint32_t b = tc::pack_bf16x2(x[4 * q + 2], x[4 * q + 3]);
+          asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a1_row + kofs(j0 + 4 * q)), "r"(a), "r"(b) : "memory");
+        }
+        if (!own) {
+#pragma unroll
+          for (int c = D / 8; c < kK1 / 8; ++c)
+            tc::sts128(a1_row + (uint32_t)c * 128u, c == D / 8 ? tc::pack_bf16x2(1.f, 1.f) : 0u, 0u, 0u, 0u);
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
@@ -574,98 +605,107 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc::mma_commit(bar_pol);
           }
         }
-        // ---- sample the Gaussian head, candidate y = x + dx
-        float y[kMaxD];
-#pragma unroll
-        for (int j = 0; j < kMaxD; ++j) y[j] = x[j];
-        if (own) {
-          float out[kN3];
+        // ---- sample this half's coordinates of the Gaussian head, y = x + dx
+        float y[DH];
+        float lp = 0.f;
+        {
+          float out[2 * D];
 #pragma unroll
           for (int q = 0; q < kN3 / 16; ++q) {
             uint32_t z[16];
             tmem_ld16(tbase + lane_sel + (uint32_t)(16 * q), z);
             tc::tmem_wait_ld();
 #pragma unroll
-            for (int i = 0; i < 16; ++i)
-              out[16 * q + i] = __uint_as_float(z[i]) + *(const float *)(sm + PK_B3 + (16 * q + i) * 4);
-          }
-          float lp = 0.f;
-          float *act = (float *)d.r_act + rowR * (size_t)D * S + e;
-#pragma unroll
-          for (int j = 0; j < kMaxD; j += 4) {
-            if (j < D) {
-              const uint4 rw = draw(seed, k, e, 0, kTagAction, (uint32_t)(j >> 2));
-              const float2 p = box_muller(rw.x, rw.y), q2 = box_muller(rw.z, rw.w);
-              const float z4[4] = {p.x, p.y, q2.x, q2.y};
-#pragma unroll
-              for (int i = 0; i < 4; ++i) {
-                const float mu = out[j + i], lsr = out[D + j + i];
-                const float zz = z4[i];
-                const float ls = fminf(fmaxf(lsr, -5.0f), 2.0f);
-                const float smp = mu + expf(ls) * zz;
-                const float dx = fminf(fmaxf(smp, -clip), clip);
-                if (rec) act[(size_t)(j + i) * S] = dx;
-                lp += -0.5f * zz * zz - ls - half_log_2pi;
-                y[j + i] = x[j + i] + dx;
-              }
+            for (int i = 0; i < 16; ++i) {
+              const int c = 16 * q + i;
+              if (c < 2 * D) out[c] = __uint_as_float(z[i]) + *(const float *)(sm + PK_B3 + c * 4);
             }
           }
-          if (rec) d.r_logp[rowR * S + e] = lp;
-          if (rec && d.dbg_logits) {
+          if (rec && own && d.dbg_logits)
 #pragma unroll
-            for (int i = 0; i < 2 * D; ++i) d.out[(size_t)e * 2 * D + i] = out[i];
+            for (int c = 0; c < 2 * D; ++c) d.out[(size_t)e * 2 * D + c] = out[c];
+          float mu[DH], lsr[DH];
+#pragma unroll
+          for (int i = 0; i < DH; ++i) {
+            mu[i] = own ? out[i] : out[DH + i];
+            lsr[i] = own ? out[D + i] : out[D + DH + i];
+          }
+          float *act = (float *)d.r_act + rowR * (size_t)D * S + e;
+#pragma unroll
+          for (int q = 0; q < DH / 4; ++q) {
+            const int j = j0 + 4 * q;
+            const uint4 rw = draw(seed, k, e, 0, kTagAction, (uint32_t)(j >> 2));
+            const float2 p = box_muller(rw.x, rw.y), p2 = box_muller(rw.z, rw.w);
+            const float z4[4] = {p.x, p.y, p2.x, p2.y};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int u = 4 * q + i;
+              const float zz = z4[i];
+              const float ls = fminf(fmaxf(lsr[u], -5.0f), 2.0f);
+              const float smp = mu[u] + expf(ls) * zz;
+              const float dx = fminf(fmaxf(smp, -clip), clip);
+              if (rec) act[(size_t)(j + i) * S] = dx;
+              lp += -0.5f * zz * zz - ls - half_log_2pi;
+              y[u] = x[u] + dx;
+            }
           }
         }
-        const float yy = write_ae(y);
-        const float E2 = sweep(yy);
-        // ---- step: observed energy, reward, done, auto-reset
-        bool done = false;
-        if (own) {
-          const uint4 rn = draw(seed, k, e, 0, kTagNoise, 0);
-          const float eobs2 = E2 + sig_n * box_muller(rn.x, rn.y).x;
-          const int t2 = t + 1;
-          done = valid && t2 >= (int)d.episode_limit;
-          if (rec) {
-            const size_t o = rowR * S + e;
-            d.r_energy[o] = E2;
-            d.r_rew[o] = eobs - eobs2;
-            d.r_done[o] = (uint8_t)done;
+#pragma unroll
+        for (int i = 0; i < DH; ++i) x[i] = y[i];  // the candidate; the old state is recorded
+        // pass 0: energy of the candidate, the step; pass 1 (only when the tile has
+        // a reset; the same vote on every CTA of the cluster, whose states are
+        // identical): energy of the fresh states
+        const int t2 = t + 1;
+        const bool done = valid && t2 >= (int)d.episode_limit;
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+          write_ae(x, lp);
+          if (pass == 0 && own && rec) d.r_logp[rowR * S + e] = lp + xch_lp[r];
+          const float E = sweep();
+          if (pass == 1) {
+            if (own && done) {
+              const uint4 rn = draw(seed, k, e, 0, kTagNoise, 1);
+              eobs = E + sig_n * box_muller(rn.x, rn.y).x;
+            }
+            break;
+          }
+          // ---- step: observed energy, reward, done, auto-reset
+          if (own) {
+            const uint4 rn = draw(seed, k, e, 0, kTagNoise, 0);
+            const float eobs2 = E + sig_n * box_muller(rn.x, rn.y).x;
+            if (rec) {
+              const size_t o = rowR * S + e;
+              d.r_energy[o] = E;
+              d.r_rew[o] = eobs - eobs2;
+              d.r_done[o] = (uint8_t)done;
+            }
+            if (!done) eobs = eobs2;
           }
           if (done) {
 #pragma unroll
-            for (int j = 0; j < kMaxD; j += 4) {
-              if (j < D) {
-                const uint4 rr = draw(seed, k, e, 0, kTagReset, (uint32_t)(j >> 2));
-                x[j] = uniform(rr.x, -3.0f, 3.0f);
-                if (j + 1 < D) x[j + 1] = uniform(rr.y, -3.0f, 3.0f);
-                if (j + 2 < D) x[j + 2] = uniform(rr.z, -3.0f, 3.0f);
-                if (j + 3 < D) x[j + 3] = uniform(rr.w, -3.0f, 3.0f);
-              }
+            for (int q = 0; q < DH / 4; ++q) {
+              const uint4 rr = draw(seed, k, e, 0, kTagReset, (uint32_t)((j0 + 4 * q) >> 2));
+              x[4 * q] = uniform(rr.x, -3.0f, 3.0f);
+              x[4 * q + 1] = uniform(rr.y, -3.0f, 3.0f);
+              x[4 * q + 2] = uniform(rr.z, -3.0f, 3.0f);
+              x[4 * q + 3] = uniform(rr.w, -3.0f, 3.0f);
             }
             t = 0;
           } else {
-#pragma unroll
-            for (int j = 0; j < kMaxD; ++j) x[j] = y[j];
-            eobs = eobs2;
             t = t2;
           }
-        }
-        // a tile with a reset sweeps again at the fresh states (identical vote on
-        // every CTA of the cluster: they hold identical states)
-        if (bar_any_n(kBarEpi, kEpi, done)) {
-          const float xx = write_ae(x);
-          const float E0 = sweep(xx);
-          if (own && done) {
-            const uint4 rn = draw(seed, k, e, 0, kTagNoise, 1);
-            eobs = E0 + sig_n * box_muller(rn.x, rn.y).x;
-          }
+          lp = 0.f;
+          if (!bar_any_n(kBarEpi, kEpi, done)) break;
         }
       }
       if (rec && !fail) {
-        for (int j = 0; j < D; ++j) d.s[(size_t)j * N + e] = x[j];
-        d.eobs[e] = eobs;
-        d.t[e] = t;
-        d.needs_energy[e] = 0;
+#pragma unroll
+        for (int i = 0; i < DH; ++i) d.s[(size_t)(j0 + i) * N + e] = x[i];
+        if (own) {
+          d.eobs[e] = eobs;
+          d.t[e] = t;
+          d.needs_energy[e] = 0;
+        }
       }
     }
     // stop the producer
