@@ -47,9 +47,11 @@ constexpr int kN3 = 48;                       // layer-3 N (2 D, padded to 48)
 constexpr int kK1 = 32;                       // layer-1 K: D coordinates, 1, 1, zeros
 constexpr int kKE = 80;                       // energy K: 3 D + 5 <= 80, five K16 steps
 constexpr int kBlk = 64;                      // Gaussians per energy MMA block
-constexpr int kBlkImg = kBlk * kKE * 2;       // block image, K = 80 without swizzle
-constexpr int kBlkBytes = kBlkImg + kBlk * 4;  // + the amplitudes a_m
-constexpr int kEpi = 256, kThreads = kEpi + 32;
+constexpr int kBlkBytes = kBlk * kKE * 2;     // block image, K = 80 without swizzle
+constexpr int kNS = 3;                        // shared-memory block buffers
+constexpr int kNT = 8;                        // TMEM accumulators (all of TMEM during a sweep)
+constexpr int kHdr = 256;                     // energy image header: {blocks, positive blocks}
+constexpr int kEpi = 256, kThreads = kEpi + 64;  // + a loader warp and an MMA warp
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 // Packed policy image (copied verbatim to shared memory offset 0):
@@ -63,15 +65,14 @@ constexpr int PK_B3 = PK_B2 + kH * 4;
 constexpr int POLICY = PK_B3 + 64 * 4;
 
 // shared memory
-constexpr int kNB = 3;                            // energy blocks in flight (buffers)
 constexpr int OFF_AE = POLICY;                    // energy A [128][80] (also the layer-1 A [128][32])
-constexpr int OFF_BE = OFF_AE + kRows * kKE * 2;  // kNB energy B blocks
-constexpr int OFF_XCH = OFF_BE + kNB * kBlkBytes; // f32 [128] each: partial energy, log-probability,
+constexpr int OFF_BE = OFF_AE + kRows * kKE * 2;  // kNS energy B blocks
+constexpr int OFF_XCH = OFF_BE + kNS * kBlkBytes; // f32 [128] each: partial energy, log-probability,
                                                   // |y|^2 of half 0 and of half 1
 constexpr int OFF_RECV = OFF_XCH + 4 * kRows * 4; // f32 [2][128] the cluster partner's partials
 constexpr int OFF_BAR = OFF_RECV + 2 * kRows * 4;
-constexpr int N_BAR = 4 + 3 * kNB;  // ae, b[kNB], mma[kNB], epi[kNB], pol, x, drain
-constexpr int OFF_CMD = OFF_BAR + N_BAR * 8;
+constexpr int N_BAR = 4 + kNS + 2 * kNT;  // ae, b[kNS], mma[kNT], epi[kNT], pol, x, drain
+constexpr int OFF_CMD = OFF_BAR + N_BAR * 8;  // [0] sweep command, [1] end flag, [2] blocks loaded
 constexpr int OFF_TM = OFF_CMD + 16;
 constexpr int SMEM = OFF_TM + 16 + 1024;
 static_assert(SMEM <= 232448, "shared memory over the 227 KB per-CTA limit");
@@ -80,9 +81,9 @@ static_assert(PK_W3 % 1024 == 0 && (4 * kN3 * 128) % 1024 == 0 && (kN3 * 128) % 
 static_assert(OFF_AE % 128 == 0 && OFF_BE % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
 
 constexpr uint32_t TM_H = 256;   // TMEM columns of h1 / h2 (packed BF16 A operand)
-constexpr uint32_t TM_E = 256;   // TMEM columns of the energy accumulators (during a sweep the
+constexpr uint32_t TM_E = 0;     // TMEM columns of the energy accumulators (during a sweep the
                                  // policy's columns are free)
-static_assert(TM_E + kNB * kBlk <= 512, "energy accumulators");
+static_assert(TM_E + kNT * kBlk <= 512, "energy accumulators");
 
 __device__ __forceinline__ uint16_t bf16_bits(float f) {
   return (uint16_t)(tc::pack_bf16x2(f, 0.f) & 0xFFFFu);
@@ -122,19 +123,63 @@ __global__ void k_land_tc_pack_policy(const float *__restrict__ p, int D, uint8_
   for (int i = tid; i < 64; i += stride) ((float *)(out + PK_B3))[i] = i < 2 * D ? b3[i] : 0.f;
 }
 
-// Energy image: per block of 64 Gaussians, the B operand rows (K = 80, no
-// swizzle) [v_hi (D) | v_lo (D) | v_hi (D) | s_hi, s_lo | q_hi, q_lo, q_hi | 0...]
-// with v = -2 q c, s = q |c|^2, q = -log2(e) / (2 w^2), against the operand row
-// [y_hi | y_hi | y_lo | 1, 1 | yy_hi, yy_hi, yy_lo | 0...] (yy = |y|^2), then the
-// amplitudes a_m; Gaussians beyond M have a = 0.
+// Energy image: a header {block count (even), blocks of non-negative
+// amplitude}, the slot order (Gaussian index per slot, -1 for padding), then per
+// block of 64 slots the B operand rows (K = 80, no swizzle)
+//   [v_hi (D) | v_lo (D) | v_hi (D) | s_hi, s_lo | q_hi, q_lo, q_hi | 0...]
+// with v = -2 q c, q = -log2(e) / (2 w^2) and s = q |c|^2 + log2 |a|, against the
+// operand row [y_hi | y_hi | y_lo | 1, 1 | yy_hi, yy_hi, yy_lo | 0...] (yy = |y|^2):
+// the dot product is log2(|a_m| exp(-|y - c_m|^2 / (2 w_m^2))).  Gaussians with
+// a >= 0 fill the first blocks and those with a < 0 the rest (each group padded
+// to whole blocks), so that a block's sign is one flag; padding slots carry
+// s = -200 (2^-200 flushes to zero).
+inline int land_slots(int M) { return ((M + kBlk - 1) / kBlk + 3) * kBlk; }
+inline size_t land_order_off() { return (size_t)kHdr; }
+inline size_t land_blocks_off(int M) { return kHdr + ((size_t)land_slots(M) * 4 + 255) / 256 * 256; }
+
+__global__ void k_land_tc_order(const float *__restrict__ a, int M, int slots,
+                                int32_t *__restrict__ hdr, int32_t *__restrict__ order) {
+  __shared__ int cnt[1024], base_p[1024], base_n[1024];
+  const int t = threadIdx.x, T = blockDim.x;
+  const int per = (M + T - 1) / T, lo = t * per, hi = min(M, lo + per);
+  int np = 0;
+  for (int m = lo; m < hi; ++m) np += a[m] >= 0.f;
+  cnt[t] = np;
+  for (int s = t; s < slots; s += T) order[s] = -1;
+  __syncthreads();
+  if (t == 0) {  // exclusive scans of the group counts, in thread order (stable)
+    int p = 0, n = 0;
+    for (int i = 0; i < T; ++i) {
+      const int li = min(M, i * per), hi_i = min(M, li + per), len = max(0, hi_i - li);
+      base_p[i] = p;
+      base_n[i] = n;
+      p += cnt[i];
+      n += len - cnt[i];
+    }
+    const int pb = (p + kBlk - 1) / kBlk, nb = (n + kBlk - 1) / kBlk;
+    hdr[0] = (pb + nb + 1) / 2 * 2;
+    hdr[1] = pb;
+    cnt[0] = pb * kBlk;  // first slot of the negative group
+  }
+  __syncthreads();
+  const int neg0 = cnt[0];
+  int ip = base_p[t], in = base_n[t];
+  for (int m = lo; m < hi; ++m) {
+    if (a[m] >= 0.f) order[ip++] = m;
+    else order[neg0 + in++] = m;
+  }
+}
+
 __global__ void k_land_tc_pack_energy(const float *__restrict__ c, const float *__restrict__ w,
-                                      const float *__restrict__ a, int D, int M, int Mp,
-                                      uint8_t *__restrict__ img) {
+                                      const float *__restrict__ a, int D, int slots,
+                                      const int32_t *__restrict__ order, uint8_t *__restrict__ img) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-  for (int i = tid; i < Mp * kKE; i += stride) {
-    const int m = i / kKE, k = i % kKE;
+  for (int i = tid; i < slots * kKE; i += stride) {
+    const int sl = i / kKE, k = i % kKE, m = order[sl];
     float v = 0.f;
-    if (m < M && k < 3 * D + 5) {
+    if (m < 0) {
+      if (k == 3 * D) v = -200.f;
+    } else if (k < 3 * D + 5) {
       const float q = -1.4426950408889634f / (2.0f * w[m] * w[m]);
       if (k < 3 * D) {
         const float x = -2.0f * q * c[(size_t)m * D + (k % D)];
@@ -142,17 +187,14 @@ __global__ void k_land_tc_pack_energy(const float *__restrict__ c, const float *
       } else if (k < 3 * D + 2) {
         float s = 0.f;
         for (int j = 0; j < D; ++j) s = fmaf(c[(size_t)m * D + j], c[(size_t)m * D + j], s);
-        const float x = q * s;
+        const float x = fmaf(q, s, fmaxf(log2f(fabsf(a[m])), -200.f));
         v = k == 3 * D ? x : x - bf16_val(x);
       } else {
         v = k == 3 * D + 3 ? q - bf16_val(q) : q;
       }
     }
-    const int blk = m / kBlk, n = m % kBlk;
-    *(uint16_t *)(img + (size_t)blk * kBlkBytes + ns_off(n, k, kKE)) = bf16_bits(v);
+    *(uint16_t *)(img + (size_t)(sl / kBlk) * kBlkBytes + ns_off(sl % kBlk, k, kKE)) = bf16_bits(v);
   }
-  for (int m = tid; m < Mp; m += stride)
-    *(float *)(img + (size_t)(m / kBlk) * kBlkBytes + kBlkImg + (m % kBlk) * 4) = m < M ? a[m] : 0.f;
 }
 
 // ---- helpers ---------------------------------------------------------------------
@@ -281,13 +323,14 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t *bar, uint32_t parity
   }
 }
 
-// Barrier ids: 1 the 256 epilogue threads; 2 + w the two warps (w, w + 4) of rows 32w..
-constexpr uint32_t kBarEpi = 1, kBarPair0 = 2;
+// Barrier ids: 1 the 256 epilogue threads; 2 + w the two warps (w, w + 4) of rows
+// 32w..; 6 the two producer warps.
+constexpr uint32_t kBarEpi = 1, kBarPair0 = 2, kBarProd = 6;
 
 template <int D, int CL>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_land_tc(Dev d, const uint8_t *__restrict__ pol, const uint8_t *__restrict__ eimg, int n_blk,
-              uint32_t n_steps) {
+    k_land_tc(Dev d, const uint8_t *__restrict__ pol, const uint8_t *__restrict__ eimg,
+              const uint8_t *__restrict__ blocks, uint32_t n_steps) {
   constexpr int DH = D / 2;  // coordinates per thread of a row (two threads per row)
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = tc::smem_u32(smem_raw);
@@ -295,8 +338,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t sb = tc::smem_u32(sm);
   const int tid = threadIdx.x, warp = tid >> 5;
   uint64_t *bars = (uint64_t *)(sm + OFF_BAR);
-  uint64_t *bar_ae = bars, *bar_b = bars + 1, *bar_mma = bar_b + kNB, *bar_epi = bar_mma + kNB;
-  uint64_t *bar_pol = bar_epi + kNB, *bar_x = bar_pol + 1, *bar_drain = bar_x + 1;
+  uint64_t *bar_ae = bars, *bar_b = bars + 1, *bar_mma = bar_b + kNS, *bar_epi = bar_mma + kNT;
+  uint64_t *bar_pol = bar_epi + kNT, *bar_x = bar_pol + 1, *bar_drain = bar_x + 1;
   volatile uint32_t *cmd = (volatile uint32_t *)(sm + OFF_CMD);
   uint32_t *tm_holder = (uint32_t *)(sm + OFF_TM);
   const uint32_t rank = CL > 1 ? cluster_rank() : 0u;
@@ -308,14 +351,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (tid == 0) {
     tc::mbar_init(bar_ae, kEpi);
-    for (int i = 0; i < kNB; ++i) {
-      tc::mbar_init(bar_b + i, 1);
+    for (int i = 0; i < kNS; ++i) tc::mbar_init(bar_b + i, 1);
+    for (int i = 0; i < kNT; ++i) {
       tc::mbar_init(bar_mma + i, 1);
-      tc::mbar_init(bar_epi + i, kEpi);
+      tc::mbar_init(bar_epi + i, kRows);  // the half that evaluates the block
     }
     tc::mbar_init(bar_pol, 1);
     tc::mbar_init(bar_x, kRows);
     tc::mbar_init(bar_drain, 1);
+    cmd[0] = 0u;
+    cmd[1] = 0u;
+    cmd[2] = 0u;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tc::tmem_alloc(tm_holder, 512);
@@ -328,67 +374,93 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t N = d.n_envs;
   const int n_tiles = (int)((N + kRows - 1) / kRows);
   const int n_clus = (int)gridDim.x / CL, cid = (int)blockIdx.x / CL;
+  const int n_blk = ((const int32_t *)eimg)[0] / CL;  // this CTA's blocks per sweep
+  const int nb_pos = ((const int32_t *)eimg)[1];       // blocks before the first a < 0 block
+  const int blk0 = (int)rank * n_blk;                  // this CTA's first block
   bool fail = false;
 
   if (tid >= kEpi) {
-    // ===================== producer: energy blocks in, MMAs out =====================
-    // Block g of this CTA's sweep sequence sits in buffer g % kNB (shared memory
-    // and TMEM accumulator alike).  The load of block g + 2 is issued once block
-    // g - 1 is consumed, so two loads stay in flight ahead of the epilogue.
-    if (tid == kEpi) {
-      const uint8_t *src0 = eimg + (size_t)rank * n_blk * kBlkBytes;
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(128, kBlk);
-      uint32_t pa = 0, ph_b = 0, ph_e = 0;  // parities (one bit per buffer)
-      uint32_t g = 0, gl = 0;               // next block to MMA, next block to load
-      auto load = [&]() -> bool {
-        const uint32_t b = gl % kNB;
-        if (gl >= (uint32_t)kNB) {           // buffer b: block gl - kNB consumed
-          if (!tc::mbar_wait(bar_epi + b, (ph_e >> b) & 1u, kWaitNs)) return false;
-          ph_e ^= 1u << b;
-        }
-        mbar_expect_tx(bar_b + b, kBlkBytes);
-        bulk_g2s(sb + OFF_BE + b * kBlkBytes, src0 + (size_t)(gl % (uint32_t)n_blk) * kBlkBytes,
-                 kBlkBytes, bar_b + b);
-        ++gl;
-        return true;
-      };
-      load();
-      load();
-      while (!fail) {
-        if (!tc::mbar_wait(bar_ae, pa, kWaitNs)) { fail = true; break; }
-        pa ^= 1u;
-        if (*cmd == 0u) break;
-        for (int i = 0; i < n_blk && !fail; ++i, ++g) {
-          const uint32_t b = g % kNB;
-          if (!tc::mbar_wait(bar_b + b, (ph_b >> b) & 1u, kWaitNs)) { fail = true; break; }
-          ph_b ^= 1u << b;
-          tc::fence_after_sync();
-#pragma unroll
-          for (int s = 0; s < kKE / 16; ++s) {
-            const uint64_t da = tc::smem_desc(sb + OFF_AE + (uint32_t)s * 256u, 128, kKE * 16,
-                                              tc::kSwizzleNone);
-            const uint64_t db = tc::smem_desc(sb + OFF_BE + b * kBlkBytes + (uint32_t)s * 256u, 128,
-                                              kKE * 16, tc::kSwizzleNone);
-            tc::mma_bf16(tbase + TM_E + b * kBlk, da, db, idesc, s != 0);
+    // ===================== producer warps =====================
+    // Block g of this CTA's sweep sequence lands in shared-memory buffer g % kNS
+    // and accumulates in TMEM buffer g % kNT.  The loader (warp 8) refills a
+    // shared-memory buffer as soon as the MMA that read it has completed, ahead of
+    // the sweeps (blocks do not depend on the env rows); the MMA warp (warp 9)
+    // issues block g once its bytes have landed, its accumulator has been read
+    // out, and the sweep's operand rows are ready.  The epilogue thus finds up to
+    // kNT blocks already multiplied.  A block's phase on one of these barriers is
+    // (g / buffers) & 1: no later phase can complete before the waiter acts.
+    volatile uint32_t *endf = cmd + 1, *s_gl = cmd + 2;
+    const int lane = tid & 31;
+    if (warp == kEpi / 32) {
+      if (lane == 0) {
+        const uint8_t *src0 = blocks + (size_t)blk0 * kBlkBytes;
+        uint32_t gl = 0;
+        for (;;) {
+          if (gl >= (uint32_t)kNS) {  // the MMA of block gl - kNS has read its buffer, or the end
+            const uint32_t gp = gl - kNS;
+            bool got = false;
+            uint64_t t0 = 0;
+            for (int it = 0;; ++it) {
+              if (tc::mbar_try_wait(bar_mma + gp % kNT, (gp / kNT) & 1u)) { got = true; break; }
+              if (*endf) break;
+              if (it == 0) t0 = tc::global_ns();
+              else if ((it & 255) == 0 && tc::global_ns() - t0 > kWaitNs) { fail = true; break; }
+            }
+            if (!got) break;
           }
-          tc::mma_commit(bar_mma + b);
-          if (!load()) fail = true;
+          const uint32_t sbuf = gl % kNS;
+          mbar_expect_tx(bar_b + sbuf, kBlkBytes);
+          bulk_g2s(sb + OFF_BE + sbuf * kBlkBytes, src0 + (size_t)(gl % (uint32_t)n_blk) * kBlkBytes,
+                   kBlkBytes, bar_b + sbuf);
+          ++gl;
+        }
+        *s_gl = gl;
+      }
+      __syncwarp();
+      bar_sync_n(kBarProd, 64);
+    } else {
+      uint32_t g = 0;
+      if (lane == 0) {
+        constexpr uint32_t idesc = tc::idesc_bf16_f32(128, kBlk);
+        uint32_t pa = 0;
+        while (!fail) {
+          if (!tc::mbar_wait(bar_ae, pa, kWaitNs)) { fail = true; break; }
+          pa ^= 1u;
+          if (*cmd == 0u) break;
+          for (int i = 0; i < n_blk && !fail; ++i, ++g) {
+            const uint32_t sbuf = g % kNS, t = g % kNT;
+            if (!tc::mbar_wait(bar_b + sbuf, (g / kNS) & 1u, kWaitNs)) { fail = true; break; }
+            if (g >= (uint32_t)kNT &&
+                !tc::mbar_wait(bar_epi + t, ((g - kNT) / kNT) & 1u, kWaitNs)) { fail = true; break; }
+            tc::fence_after_sync();
+#pragma unroll
+            for (int s = 0; s < kKE / 16; ++s) {
+              const uint64_t da = tc::smem_desc(sb + OFF_AE + (uint32_t)s * 256u, 128, kKE * 16,
+                                                tc::kSwizzleNone);
+              const uint64_t db = tc::smem_desc(sb + OFF_BE + sbuf * kBlkBytes + (uint32_t)s * 256u,
+                                                128, kKE * 16, tc::kSwizzleNone);
+              tc::mma_bf16(tbase + TM_E + t * kBlk, da, db, idesc, s != 0);
+            }
+            tc::mma_commit(bar_mma + t);
+          }
         }
       }
-      // blocks g .. gl - 1 were loaded ahead: their copies finish before shared
-      // memory goes away
-      if (!fail)
-        for (uint32_t q = g; q < gl; ++q) {
-          const uint32_t b = q % kNB;
-          tc::mbar_wait(bar_b + b, (ph_b >> b) & 1u, kWaitNs);
-          ph_b ^= 1u << b;
+      __syncwarp();
+      bar_sync_n(kBarProd, 64);
+      if (lane == 0) {
+        // blocks g .. gl - 1 were loaded ahead: their copies finish before shared
+        // memory goes away
+        if (!fail) {
+          const uint32_t gl = *s_gl;
+          for (uint32_t q = g; q < gl; ++q) tc::mbar_wait(bar_b + q % kNS, (q / kNS) & 1u, kWaitNs);
         }
-      tc::mma_commit(bar_drain);
-      tc::mbar_wait(bar_drain, 0, kWaitNs);
-      if (fail) {
-        atomicExch(d.err, 1u);
-        atomicExch(d.err + 1, 500u);
+        tc::mma_commit(bar_drain);
+        tc::mbar_wait(bar_drain, 0, kWaitNs);
       }
+    }
+    if (fail && (tid & 31) == 0) {
+      atomicExch(d.err, 1u);
+      atomicExch(d.err + 1, 500u);
     }
   } else {
     // ===================== epilogue: env rows =====================
@@ -411,7 +483,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const float half_log_2pi = 0.91893853320467274f;
     constexpr uint32_t id_pol = tc::idesc_bf16_f32(128, kH);
     constexpr uint32_t id_out = tc::idesc_bf16_f32(128, kN3);
-    uint32_t pp = 0, ge = 0, px = 0, par = 0, ph_m = 0, ph_bt = 0;
+    uint32_t pp = 0, ge = 0, px = 0, par = 0;
     // After a wait has run out no other wait is attempted: the CTA runs on to the
     // vote at the next step boundary and leaves together.
     auto wait = [&](uint64_t *bar, uint32_t parity) {
@@ -431,32 +503,42 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (tid == 0) *cmd = 1u;
       tc::fence_async_smem();
       mbar_arrive(bar_ae);
-      float part = 0.f;
-      for (int i = 0; i < n_blk; ++i, ++ge) {
-        const uint32_t b = ge % kNB;
-        wait(bar_mma + b, (ph_m >> b) & 1u);
-        ph_m ^= 1u << b;
-        // the block's amplitudes arrived by bulk copy: observe that copy's
-        // completion before reading them with ordinary loads (they cannot be
-        // overwritten before this thread marks the block consumed)
-        wait(bar_b + b, (ph_bt >> b) & 1u);
-        ph_bt ^= 1u << b;
+      // Half h evaluates the blocks of parity h, all 64 columns of each, so that
+      // the two warps of an SMSP work on different blocks (one's TMEM load and
+      // waits overlap the other's exponentials).  A block holds Gaussians of one
+      // sign; the two signs are summed apart.
+      float ap = 0.f, an = 0.f;
+      for (int i = h; i < n_blk; i += 2) {
+        const uint32_t gb = ge + (uint32_t)i, t = gb % kNT;
+        wait(bar_mma + t, (gb / kNT) & 1u);
         tc::fence_after_sync();
-        uint32_t z[32];
-        tc::tmem_ld32(tbase + lane_sel + TM_E + b * kBlk + (uint32_t)(32 * h), z);
+        uint32_t z0[32], z1[32];
+        tc::tmem_ld32(tbase + lane_sel + TM_E + t * kBlk, z0);
+        tc::tmem_ld32(tbase + lane_sel + TM_E + t * kBlk + 32u, z1);
         tc::tmem_wait_ld();
-        const uint32_t amp = sb + OFF_BE + b * kBlkBytes + kBlkImg + (uint32_t)(32 * h) * 4u;
+        tc::fence_before_sync();
+        mbar_arrive(bar_epi + t);
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
         for (int c = 0; c < 32; c += 4) {
-          const float4 a = lds128f(amp + 4u * (uint32_t)c);
-          part = fmaf(a.x, ex2_fast(__uint_as_float(z[c])), part);
-          part = fmaf(a.y, ex2_fast(__uint_as_float(z[c + 1])), part);
-          part = fmaf(a.z, ex2_fast(__uint_as_float(z[c + 2])), part);
-          part = fmaf(a.w, ex2_fast(__uint_as_float(z[c + 3])), part);
+          s0 += ex2_fast(__uint_as_float(z0[c]));
+          s1 += ex2_fast(__uint_as_float(z0[c + 1]));
+          s2 += ex2_fast(__uint_as_float(z0[c + 2]));
+          s3 += ex2_fast(__uint_as_float(z0[c + 3]));
         }
-        tc::fence_before_sync();
-        mbar_arrive(bar_epi + b);
+#pragma unroll
+        for (int c = 0; c < 32; c += 4) {
+          s0 += ex2_fast(__uint_as_float(z1[c]));
+          s1 += ex2_fast(__uint_as_float(z1[c + 1]));
+          s2 += ex2_fast(__uint_as_float(z1[c + 2]));
+          s3 += ex2_fast(__uint_as_float(z1[c + 3]));
+        }
+        const float bs = (s0 + s1) + (s2 + s3);
+        if (blk0 + i < nb_pos) ap += bs;
+        else an += bs;
       }
+      ge += (uint32_t)n_blk;
+      const float part = ap - an;
       if (!own) xch_e[r] = part;
       bar_sync_n(pair, 64);
       float E = 0.f;
@@ -708,9 +790,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-    // stop the producer
+    // stop the producer warps
     bar_sync_n(kBarEpi, kEpi);
-    if (tid == 0) *cmd = 0u;
+    if (tid == 0) {
+      *cmd = 0u;
+      cmd[1] = 1u;  // the loader stops waiting
+    }
     mbar_arrive(bar_ae);
     if (fail && tid == 0) {
       // a policy MMA may still be in flight after a wait that ran out
@@ -736,14 +821,18 @@ bool land_tc_supported(int D, int M, const PolicyShape &p) {
          p.w[2] == kH && p.w[3] == 2 * D;
 }
 size_t land_tc_policy_bytes() { return (size_t)POLICY; }
-int land_tc_padded_gauss(int M) { return (M + 2 * kBlk - 1) / (2 * kBlk) * (2 * kBlk); }
-size_t land_tc_energy_bytes(int M) { return (size_t)(land_tc_padded_gauss(M) / kBlk) * kBlkBytes; }
+size_t land_tc_energy_bytes(int M) {
+  return land_blocks_off(M) + (size_t)(land_slots(M) / kBlk) * kBlkBytes;
+}
 
 void launch_land_tc_pack(const Dev &d, void *policy_img, void *energy_img, cudaStream_t st) {
+  const int M = (int)d.n_gauss, slots = land_slots(M);
+  uint8_t *img = (uint8_t *)energy_img;
+  int32_t *order = (int32_t *)(img + land_order_off());
   k_land_tc_pack_policy<<<64, 256, 0, st>>>(d.params, (int)d.dim, (uint8_t *)policy_img);
-  k_land_tc_pack_energy<<<128, 256, 0, st>>>(d.centres, d.widths, d.amps, (int)d.dim, (int)d.n_gauss,
-                                             land_tc_padded_gauss((int)d.n_gauss),
-                                             (uint8_t *)energy_img);
+  k_land_tc_order<<<1, 1024, 0, st>>>(d.amps, M, slots, (int32_t *)img, order);
+  k_land_tc_pack_energy<<<128, 256, 0, st>>>(d.centres, d.widths, d.amps, (int)d.dim, slots, order,
+                                             img + land_blocks_off(M));
 }
 
 template <int D>
@@ -765,10 +854,10 @@ cudaError_t launch_land_d(const Dev &d, const uint8_t *pol, const uint8_t *eimg,
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int n_tiles = (int)((d.n_envs + kRows - 1) / kRows);
-  const int Mp = land_tc_padded_gauss((int)d.n_gauss);
+  const uint8_t *blocks = eimg + land_blocks_off((int)d.n_gauss);
   if (tile_ctas == 1) {
     const int grid = n_tiles < sms ? n_tiles : sms;
-    k_land_tc<D, 1><<<grid, kThreads, SMEM, st>>>(d, pol, eimg, Mp / kBlk, n_steps);
+    k_land_tc<D, 1><<<grid, kThreads, SMEM, st>>>(d, pol, eimg, blocks, n_steps);
     return cudaGetLastError();
   }
   if (tile_ctas != 2) return cudaErrorInvalidValue;
@@ -785,7 +874,7 @@ cudaError_t launch_land_d(const Dev &d, const uint8_t *pol, const uint8_t *eimg,
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_land_tc<D, 2>, d, pol, eimg, Mp / kBlk / 2, n_steps);
+  return cudaLaunchKernelEx(&cfg, k_land_tc<D, 2>, d, pol, eimg, blocks, n_steps);
 }
 
 // tile_ctas = CTAs per 128-env tile (1, or 2 as a cluster splitting the Gaussians).
