@@ -233,10 +233,12 @@ def run_gpu(args, wl, world, rank, local):
         n_chunks = (H + CHUNK - 1) // CHUNK
         agent_steps = r.n_slots * H
         launch = None
-        if measure_kernel:
+        if measure_kernel and not args.no_tune:
             # autotune the launch configuration (outside the timed region; the
             # trials end with a reset) over one 50-step roll-out per candidate
             launch, _ = r.tune(min(CHUNK, H))
+        elif measure_kernel:
+            launch = r.launch().as_dict()
 
         def bench_step(i, evs=None):
             r.reset(1000 + i)
@@ -376,9 +378,9 @@ def run_serving(args, world, rank, local):
             "config": {"workload": "serving mix: Poisson 200 req/s across control / economy / "
                                    "landscape, 256-65,536 envs, horizons 100-1,000, chunks of 50, "
                                    f"{args.serve_budget_gb:g} GB admission budget",
-                       "paths": "served: BF16 tensor-core paths (control fused kernel; economy and "
-                                "landscape per-layer policy GEMMs + hi/lo energy cross-term); "
-                                "plain_fp32: one launch per sub-step per step"},
+                       "paths": "served: BF16 tensor-core paths (one fused persistent kernel per "
+                                "chunk for each env type); plain_fp32: one launch per sub-step "
+                                "per step"},
             "latency": {"chunk_steps": CHUNK, "p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"]},
             "serving": out}), flush=True)
 
@@ -406,6 +408,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default launch configuration (profiling captures)")
     ap.add_argument("--horizon", type=int, default=0,
                     help="override the horizon (smaller cases for profiling captures)")
     ap.add_argument("--n-envs", type=int, default=0, help="override the env count")
@@ -462,29 +466,45 @@ def main():
               "peak_source": f"{peak_src} bf16 sustained" if bf16 else
               f"{peak_src} bf16 sustained / 4 (fp32 SIMT)"}
     tensor["frac"] = tensor["achieved"] / tensor["peak"]
-    if bf16 and wl["env"] == 0:
-        # The fused control kernel is bound by the SFU: every agent-step takes
-        # H0 + H1 tanh, and an SM retires 16 SFU results per clock (measured 15.2
-        # for tanh.approx in any of f32 / bf16x2 / f16x2 form).
+    if bf16:
+        # The fused kernels are bound by the SFU (tanh, exp2): an SM retires 16
+        # SFU results per clock (measured 15.2 for tanh.approx in any of f32 /
+        # bf16x2 / f16x2 form).  SFU results per agent-step, counted from the
+        # kernels' arithmetic:
+        #   control    H0 + H1 tanh (+ one exp for the two-way softmax)
+        #   economy    agent: H0 + H1 tanh, 20 exp, 1 log; planner: H0 + H1
+        #              tanh, 10 exp
+        #   landscape  H0 + H1 tanh, M exp2 (one per Gaussian), D exp (sigma),
+        #              2 D for the Box-Muller normals (log, sqrt, sin, cos per
+        #              pair) and 4 for the noise draw
         import torch
         n_sms = torch.cuda.get_device_properties(local).multi_processor_count
         clk = main_res["clocks"] or {}
         sm_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
-        tanh_launch = sum(wl["h"]) * (main_res["agent_steps"] / wl["horizon"]) * launch_steps
-        roofline = {"bound": "alu", "op": "tanh on the SFU",
-                    "achieved": tanh_launch / (launch_ms * 1e-3) / 1e12,
+        n_slots = main_res["agent_steps"] / wl["horizon"]
+        H = sum(wl["h"])
+        if wl["env"] == 0:
+            per_step, op, kern = n_slots * (H + 1), "tanh (and exp) on the SFU", "ws_control_tc"
+        elif wl["env"] == 1:
+            n_pl = wl["n_envs"]
+            per_step = (n_slots - n_pl) * (H + 21) + n_pl * (H + 10)
+            op, kern = "tanh and exp on the SFU", "ws_econ_tc (work queue of env groups)"
+        else:
+            per_step = n_slots * (H + wl["n_gauss"] + 3 * wl["dim"] + 4)
+            op, kern = "exp2 (energy) and tanh on the SFU", "ws_land_tc (CTA-pair clusters)"
+        sfu_launch = per_step * launch_steps
+        roofline = {"bound": "alu", "op": op,
+                    "achieved": sfu_launch / (launch_ms * 1e-3) / 1e12,
                     "peak": 16 * n_sms * sm_mhz * 1e6 / 1e12, "unit": "Top/s", "frac": None,
                     "traffic": None,
-                    "kernel": "ws_control_tc (fused persistent, one launch per 50-step chunk)",
+                    "kernel": kern + " (fused persistent, one launch per 50-step chunk)",
                     "peak_source": f"16 SFU results / clock / SM x {n_sms} SMs x {sm_mhz:.0f} MHz "
                                    "(median sampled SM clock)",
                     "tensor": {k: tensor[k] for k in ("achieved", "peak", "unit", "frac",
                                                       "peak_source")}}
         roofline["frac"] = roofline["achieved"] / roofline["peak"]
     else:
-        roofline = dict(tensor, traffic=None,
-                        kernel="per-step graph of tensor-core layers" if bf16
-                        else "plain per-step kernels")
+        roofline = dict(tensor, traffic=None, kernel="plain per-step kernels")
     if bf16 and args.workload == "control_scale" and not args.horizon and not args.n_envs:
         # DRAM bytes (read + write) of one 50-step launch of this kernel, from the
         # ncu capture summarised in profiles/control_tc_ncu_full_control_50steps.md
@@ -493,17 +513,15 @@ def main():
     lat = sorted(main_res["chunk_ms"])
     # kernels of ours per bench step: the reset (plus the landscape's energy of
     # the fresh state), per 50-step roll-out either the fused kernel and the
-    # counter advance per launch chunk (control, economy) or the per-step
-    # kernels (landscape: observe, three policy layers, sample, energy, step,
-    # reset energy, reset finish) and one advance per graph chunk, and the
-    # returns scan
+    # counter advance per launch chunk (BF16 paths) or the per-step kernels
+    # and one advance per graph chunk (plain path), and the returns scan
     launch = main_res["launch"] or {}
     ch = int(launch.get("chunk_steps", CHUNK))
     lens = [min(CHUNK, wl["horizon"] - c * CHUNK) for c in range(n_chunks)]
-    if bf16 and wl["env"] in (0, 1):
+    if bf16:
         per_roll = sum(-(-n // ch) * 2 for n in lens)
     else:
-        per_step = 9 if bf16 else {0: 6, 1: 14, 2: 9}[wl["env"]]
+        per_step = {0: 6, 1: 14, 2: 9}[wl["env"]]
         per_roll = sum(per_step * n + -(-n // ch) for n in lens)
     per_launch = (3 if wl["env"] == 2 else 1) + per_roll + 1
     out = {
