@@ -505,11 +505,19 @@ def main():
         roofline["frac"] = roofline["achieved"] / roofline["peak"]
     else:
         roofline = dict(tensor, traffic=None, kernel="plain per-step kernels")
-    if bf16 and args.workload == "control_scale" and not args.horizon and not args.n_envs:
-        # DRAM bytes (read + write) of one 50-step launch of this kernel, from the
-        # ncu capture summarised in profiles/control_tc_ncu_full_control_50steps.md
-        roofline["traffic"] = (3.461888 + 135.865344) * 1e6
-        roofline["traffic_algorithmic"] = 29.0 * wl["n_envs"] * launch_steps
+    if bf16 and not args.horizon and not args.n_envs:
+        # DRAM bytes (read + write) of one 50-step launch of the fused kernel, from
+        # the ncu captures summarised under profiles/ (*_ncu_full_*.md), beside the
+        # algorithmic record bytes of the launch (control 29 B, economy 85 B,
+        # landscape 205 B per agent-step)
+        ncu_bytes = {"control_scale": (3.461888 + 135.865344) * 1e6,
+                     "economy": 92.359424e6 + 1.189169e9,
+                     "landscape": (1.788928 + 24.135424) * 1e6}
+        rec_bytes = {0: 29.0, 1: 85.0, 2: 205.0}[wl["env"]]
+        if args.workload in ncu_bytes:
+            roofline["traffic"] = ncu_bytes[args.workload]
+            roofline["traffic_algorithmic"] = (rec_bytes * main_res["agent_steps"] / wl["horizon"]
+                                               * launch_steps)
     lat = sorted(main_res["chunk_ms"])
     # kernels of ours per bench step: the reset (plus the landscape's energy of
     # the fresh state), per 50-step roll-out either the fused kernel and the
