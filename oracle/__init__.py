@@ -80,6 +80,14 @@ def _declare(L):
     L.or_control_reset_draw.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, _P]
     L.or_control_rollout.argtypes = ([_P, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32,
                                       _P, C.c_int, _P, _P, C.c_int, C.c_int] + [_P] * 10)
+    L.or_acrobot_deriv.argtypes = [_P, C.c_double, _P]
+    L.or_acrobot_step.argtypes = [_P, C.c_int, C.c_double, _P, _P]
+    L.or_acrobot_obs.argtypes = [_P, _P]
+    L.or_acrobot_terminal.argtypes = [_P, _P]
+    L.or_acrobot_terminal.restype = C.c_int
+    L.or_acrobot_reset_draw.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, _P]
+    L.or_acrobot_rollout.argtypes = ([_P, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32,
+                                      _P, C.c_int, _P, _P, C.c_int, C.c_int] + [_P] * 11)
     L.or_econ_agent_count.argtypes = [C.c_uint64, C.c_uint32]
     L.or_econ_agent_count.restype = C.c_uint32
     L.or_econ_reset_agent.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, _P, _P]
@@ -97,7 +105,8 @@ def _declare(L):
     L.or_landscape_reset_draw.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, _P]
     L.or_landscape_rollout.argtypes = ([C.c_int, C.c_int, _P, _P, _P, _P, C.c_int, C.c_int,
                                         C.c_uint32, C.c_double, C.c_double, C.c_uint64,
-                                        C.c_uint32, _P, C.c_int, _P, _P, _P, C.c_int, C.c_int]
+                                        C.c_uint32, _P, C.c_int, _P, _P, _P, C.c_int, C.c_int,
+                                        C.c_double]
                                        + [_P] * 10)
     L.or_returns.argtypes = [C.c_int, C.c_long, _P, _P, C.c_double, _P]
 
@@ -247,6 +256,63 @@ def control_rollout(params, hidden0, hidden1, seed, env_ids, n_steps, episode_li
 
 
 # --------------------------------------------------------------------------
+# acrobot (App. C classic control; the Sutton & Barto two-link acrobot)
+# --------------------------------------------------------------------------
+def acrobot_deriv(s, tau):
+    out = np.empty(4)
+    lib().or_acrobot_deriv(_ptr(_arr(s, np.float64)), float(tau), _ptr(out))
+    return out
+
+
+def acrobot_step(s, action, dt=0.2):
+    """One RK4 step with the torque of ``action``; returns (wrapped and clipped
+    state, raw RK4 state)."""
+    out, raw = np.empty(4), np.empty(4)
+    lib().or_acrobot_step(_ptr(_arr(s, np.float64)), int(action), float(dt), _ptr(out), _ptr(raw))
+    return out, raw
+
+
+def acrobot_obs(s):
+    o = np.empty(6)
+    lib().or_acrobot_obs(_ptr(_arr(s, np.float64)), _ptr(o))
+    return o
+
+
+def acrobot_terminal(s):
+    mg = C.c_double()
+    t = lib().or_acrobot_terminal(_ptr(_arr(s, np.float64)), C.byref(mg))
+    return bool(t), mg.value
+
+
+def acrobot_reset_draw(seed, k, env):
+    out = np.empty(4)
+    lib().or_acrobot_reset_draw(seed, k & 0xFFFFFFFF, env, _ptr(out))
+    return out
+
+
+def acrobot_rollout(params, hidden0, hidden1, seed, env_ids, n_steps, episode_limit,
+                    k0=0, state0=None, t0=None, bf16_layers=0):
+    """Roll out the acrobot for envs ``env_ids``; arrays are [n_steps][n_envs]."""
+    ids = _arr(env_ids, np.uint32)
+    n = len(ids)
+    out = dict(
+        obs=np.empty((n_steps, n, 6)), state=np.empty((n_steps, n, 4)),
+        action=np.empty((n_steps, n), np.int32), logp=np.empty((n_steps, n)),
+        reward=np.empty((n_steps, n)), done=np.empty((n_steps, n), np.uint8),
+        logits=np.empty((n_steps, n, 3)), act_margin=np.empty((n_steps, n)),
+        done_margin=np.empty((n_steps, n)), state_out=np.empty((n, 4)),
+        t=np.empty(n, np.int32))
+    lib().or_acrobot_rollout(
+        _ptr(_arr(params, np.float32)), hidden0, hidden1, bf16_layers, seed, k0 & 0xFFFFFFFF,
+        _ptr(ids), n, _ptr(_arr(state0, np.float64)), _ptr(_arr(t0, np.int32)), n_steps,
+        episode_limit, _ptr(out["obs"]), _ptr(out["state"]), _ptr(out["action"]),
+        _ptr(out["logp"]), _ptr(out["reward"]), _ptr(out["done"]), _ptr(out["logits"]),
+        _ptr(out["act_margin"]), _ptr(out["done_margin"]), _ptr(out["state_out"]),
+        _ptr(out["t"]))
+    return out
+
+
+# --------------------------------------------------------------------------
 # economy
 # --------------------------------------------------------------------------
 def econ_agent_count(param_seed, env):
@@ -335,7 +401,10 @@ def landscape_reset_draw(seed, k, env, D):
 
 def landscape_rollout(c, w, a, params, hidden0, hidden1, seed, env_ids, n_steps, episode_limit,
                       noise_sigma=0.05, step_clip=0.1, k0=0, x0=None, eobs0=None, t0=None,
-                      bf16_layers=0):
+                      bf16_layers=0, energy_target=None):
+    """Landscape roll-out (App. C stand-in).  An episode ends at the step limit
+    or, with energy_target set, when the pure energy of the post-step state
+    falls below it."""
     c = _arr(c, np.float64); w = _arr(w, np.float64); a = _arr(a, np.float64)
     M, D = c.shape
     ids = _arr(env_ids, np.uint32)
@@ -350,7 +419,7 @@ def landscape_rollout(c, w, a, params, hidden0, hidden1, seed, env_ids, n_steps,
         D, M, _ptr(c), _ptr(w), _ptr(a), _ptr(_arr(params, np.float32)), hidden0, hidden1,
         bf16_layers, noise_sigma, step_clip, seed, k0 & 0xFFFFFFFF, _ptr(ids), n,
         _ptr(_arr(x0, np.float64)), _ptr(_arr(eobs0, np.float64)), _ptr(_arr(t0, np.int32)),
-        n_steps, episode_limit,
+        n_steps, episode_limit, -np.inf if energy_target is None else float(energy_target),
         _ptr(out["obs"]), _ptr(out["act"]), _ptr(out["logp"]), _ptr(out["reward"]),
         _ptr(out["done"]), _ptr(out["energy"]), _ptr(out["energy_scale"]), _ptr(out["x"]),
         _ptr(out["eobs"]), _ptr(out["t"]))

@@ -345,6 +345,157 @@ void or_control_rollout(const float *params, int hidden0, int hidden1, uint32_t 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Acrobot (App. C "Classic Control": the gym Acrobot-v1 benchmark).  Two    */
+/* links hang from a pivot; only the joint between them is actuated.  The     */
+/* physics is the two-link acrobot of Sutton & Barto (1998, Sec. 11.3) in     */
+/* its book form: m1 = m2 = 1, l1 = 1, lc1 = lc2 = 0.5 (centres of mass),     */
+/* I1 = I2 = 1, g = 9.8, angles from hanging straight down.  With            */
+/*   d1 = m1 lc1^2 + m2 (l1^2 + lc2^2 + 2 l1 lc2 cos th2) + I1 + I2          */
+/*   d2 = m2 (lc2^2 + l1 lc2 cos th2) + I2                                   */
+/*   phi2 = m2 lc2 g sin(th1 + th2)                                          */
+/*   phi1 = -m2 l1 lc2 w2^2 sin th2 - 2 m2 l1 lc2 w2 w1 sin th2              */
+/*          + (m1 lc1 + m2 l1) g sin th1 + phi2                              */
+/* the accelerations are                                                     */
+/*   th2'' = (tau + d2/d1 phi1 - m2 l1 lc2 w1^2 sin th2 - phi2)              */
+/*           / (m2 lc2^2 + I2 - d2^2 / d1)                                   */
+/*   th1'' = -(d2 th2'' + phi1) / d1.                                        */
+/* Readings: action a in {0, 1, 2} applies torque tau = a - 1; one classic  */
+/* Runge-Kutta (RK4) step of dt = 0.2 with tau held; then both angles are    */
+/* wrapped into [-pi, pi] and the velocities clipped to |w1| <= 4 pi,        */
+/* |w2| <= 9 pi.  Terminal when the tip is more than one link above the     */
+/* pivot, -cos th1 - cos(th1 + th2) > 1.  Reward -1 per step, 0 on the      */
+/* terminal step.  Observation (cos th1, sin th1, cos th2, sin th2, w1, w2); */
+/* a reset draws the state (th1, th2, w1, w2) from U(-0.1, 0.1)^4.          */
+/* ------------------------------------------------------------------------ */
+void or_acrobot_deriv(const double s[4], double tau, double ds[4]) {
+  const double m1 = 1.0, m2 = 1.0, l1 = 1.0, lc1 = 0.5, lc2 = 0.5, I1 = 1.0, I2 = 1.0, g = 9.8;
+  double th1 = s[0], th2 = s[1], w1 = s[2], w2 = s[3];
+  double d1 = m1 * lc1 * lc1 + m2 * (l1 * l1 + lc2 * lc2 + 2.0 * l1 * lc2 * cos(th2)) + I1 + I2;
+  double d2 = m2 * (lc2 * lc2 + l1 * lc2 * cos(th2)) + I2;
+  double phi2 = m2 * lc2 * g * sin(th1 + th2);
+  double phi1 = -m2 * l1 * lc2 * w2 * w2 * sin(th2) - 2.0 * m2 * l1 * lc2 * w2 * w1 * sin(th2) +
+                (m1 * lc1 + m2 * l1) * g * sin(th1) + phi2;
+  double acc2 = (tau + d2 / d1 * phi1 - m2 * l1 * lc2 * w1 * w1 * sin(th2) - phi2) /
+                (m2 * lc2 * lc2 + I2 - d2 * d2 / d1);
+  double acc1 = -(d2 * acc2 + phi1) / d1;
+  ds[0] = w1;
+  ds[1] = w2;
+  ds[2] = acc1;
+  ds[3] = acc2;
+}
+
+static double or_wrap_pi(double x) {
+  while (x > M_PI) x -= 2.0 * M_PI;
+  while (x < -M_PI) x += 2.0 * M_PI;
+  return x;
+}
+
+/* One step: RK4 over dt, then wrap and clip.  raw (may be NULL) receives the
+ * RK4 result before wrapping and clipping. */
+void or_acrobot_step(const double s[4], int action, double dt, double out[4], double raw[4]) {
+  double tau = (double)action - 1.0;
+  double k1[4], k2[4], k3[4], k4[4], y[4];
+  or_acrobot_deriv(s, tau, k1);
+  for (int i = 0; i < 4; ++i) y[i] = s[i] + 0.5 * dt * k1[i];
+  or_acrobot_deriv(y, tau, k2);
+  for (int i = 0; i < 4; ++i) y[i] = s[i] + 0.5 * dt * k2[i];
+  or_acrobot_deriv(y, tau, k3);
+  for (int i = 0; i < 4; ++i) y[i] = s[i] + dt * k3[i];
+  or_acrobot_deriv(y, tau, k4);
+  for (int i = 0; i < 4; ++i) y[i] = s[i] + dt / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+  if (raw)
+    for (int i = 0; i < 4; ++i) raw[i] = y[i];
+  const double v1 = 4.0 * M_PI, v2 = 9.0 * M_PI;
+  out[0] = or_wrap_pi(y[0]);
+  out[1] = or_wrap_pi(y[1]);
+  out[2] = y[2] < -v1 ? -v1 : (y[2] > v1 ? v1 : y[2]);
+  out[3] = y[3] < -v2 ? -v2 : (y[3] > v2 ? v2 : y[3]);
+}
+
+void or_acrobot_obs(const double s[4], double o[6]) {
+  o[0] = cos(s[0]);
+  o[1] = sin(s[0]);
+  o[2] = cos(s[1]);
+  o[3] = sin(s[1]);
+  o[4] = s[2];
+  o[5] = s[3];
+}
+
+/* Tip height above the pivot in link lengths: -cos th1 - cos(th1 + th2);
+ * terminal when it exceeds 1.  margin = |height - 1|. */
+int or_acrobot_terminal(const double s[4], double *margin) {
+  double h = -cos(s[0]) - cos(s[0] + s[1]);
+  if (margin) *margin = fabs(h - 1.0);
+  return h > 1.0;
+}
+
+void or_acrobot_reset_draw(uint64_t seed, uint32_t k, uint32_t env, double s[4]) {
+  uint32_t w[4];
+  or_draw(seed, k, env, 0, OR_TAG_RESET, 0, w);
+  for (int d = 0; d < 4; ++d) s[d] = (double)or_uniform_f32(w[d], -0.1f, 0.1f);
+}
+
+/* Roll out envs env_ids[] for n_steps from step counter k0 (as the control
+ * roll-out): policy 6 -> hidden0 -> hidden1 -> 3 on the observation, action
+ * drawn from ACTION(k, env) word 0, done on the terminal height or at the
+ * episode limit, reset in place.  obs [n_steps][n_envs][6] is the pre-step
+ * observation, state_rec [n_steps][n_envs][4] the pre-step state; margins
+ * are the sampler's distance to its tie band and the height's distance to 1. */
+void or_acrobot_rollout(const float *params, int hidden0, int hidden1, uint32_t bf16_layers,
+                        uint64_t seed, uint32_t k0, const uint32_t *env_ids, int n_envs,
+                        const double *state0, const int32_t *t0, int n_steps, int episode_limit,
+                        double *obs, double *state_rec, int32_t *action, double *logp,
+                        double *reward, uint8_t *done, double *logits, double *act_margin,
+                        double *done_margin, double *state_out, int32_t *t_out) {
+  int32_t widths[4] = {6, hidden0, hidden1, 3};
+  for (int e = 0; e < n_envs; ++e) {
+    uint32_t env = env_ids[e];
+    double s[4];
+    int t = t0 ? t0[e] : 0;
+    if (state0)
+      for (int d = 0; d < 4; ++d) s[d] = state0[(long)e * 4 + d];
+    else
+      or_acrobot_reset_draw(seed, OR_STEP_INIT, env, s);
+    for (int i = 0; i < n_steps; ++i) {
+      uint32_t k = k0 + (uint32_t)i;
+      long r = (long)i * n_envs + e;
+      double o[6], lg[3], lp, mg;
+      or_acrobot_obs(s, o);
+      or_mlp_forward(3, widths, params, bf16_layers, o, lg);
+      uint32_t w[4];
+      or_draw(seed, k, env, 0, OR_TAG_ACTION, 0, w);
+      int a = or_sample_categorical(3, lg, or_u01(w[0]), &lp, &mg);
+      double s2[4], dm;
+      or_acrobot_step(s, a, 0.2, s2, NULL);
+      int term = or_acrobot_terminal(s2, &dm);
+      int dn = term || (t + 1 >= episode_limit);
+      if (obs)
+        for (int d = 0; d < 6; ++d) obs[r * 6 + d] = o[d];
+      if (state_rec)
+        for (int d = 0; d < 4; ++d) state_rec[r * 4 + d] = s[d];
+      if (action) action[r] = a;
+      if (logp) logp[r] = lp;
+      if (reward) reward[r] = term ? 0.0 : -1.0;
+      if (done) done[r] = (uint8_t)dn;
+      if (logits)
+        for (int c = 0; c < 3; ++c) logits[r * 3 + c] = lg[c];
+      if (act_margin) act_margin[r] = mg;
+      if (done_margin) done_margin[r] = dm;
+      if (dn) {
+        or_acrobot_reset_draw(seed, k, env, s);
+        t = 0;
+      } else {
+        for (int d = 0; d < 4; ++d) s[d] = s2[d];
+        t = t + 1;
+      }
+    }
+    if (state_out)
+      for (int d = 0; d < 4; ++d) state_out[(long)e * 4 + d] = s[d];
+    if (t_out) t_out[e] = t;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Multi-agent economy (stand-in for the two-level economic simulation of   */
 /* App. C "Multi-Agent Economics": many agents plus one planner per env,    */
 /* agent interactions across threads).  Whole definition is a reading:     */
@@ -640,13 +791,17 @@ void or_landscape_reset_draw(uint64_t seed, uint32_t k, uint32_t env, int D, dou
 
 /* Roll out envs env_ids[] for n_steps.  Policy D -> h0 -> h1 -> 2D.  Outputs
  * [n_steps][n_envs] (obs and act [n_steps][n_envs][D]); energy is the pure
- * E of the post-step (pre-reset) state and energy_scale its error scale. */
+ * E of the post-step (pre-reset) state and energy_scale its error scale.
+ * An episode ends at the step limit or, when the pure energy of the post-step
+ * state falls below energy_target, on reaching the low-energy (product) basin
+ * (App. C: an episode runs from the initial to the terminal state of the
+ * reaction; -INFINITY turns the energy condition off). */
 void or_landscape_rollout(int D, int M, const double *c, const double *wd, const double *am,
                           const float *params, int hidden0, int hidden1, uint32_t bf16_layers,
                           double noise_sigma, double step_clip, uint64_t seed, uint32_t k0,
                           const uint32_t *env_ids, int n_envs, const double *x0,
                           const double *eobs0, const int32_t *t0, int n_steps, int episode_limit,
-                          double *obs, double *act, double *logp, double *reward, uint8_t *done,
+                          double energy_target, double *obs, double *act, double *logp, double *reward, uint8_t *done,
                           double *energy, double *energy_scale, double *x_out, double *eobs_out,
                           int32_t *t_out) {
   int32_t widths[4] = {D, hidden0, hidden1, 2 * D};
@@ -686,7 +841,7 @@ void or_landscape_rollout(int D, int M, const double *c, const double *wd, const
       if (energy) energy[r] = E2;
       if (energy_scale) energy_scale[r] = or_landscape_energy_scale(D, M, c, wd, am, x2);
       t = t + 1;
-      int dn = t >= episode_limit;
+      int dn = t >= episode_limit || E2 < energy_target;
       if (done) done[r] = (uint8_t)dn;
       if (dn) {
         or_landscape_reset_draw(seed, k, env, D, x);

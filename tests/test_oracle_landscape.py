@@ -130,3 +130,48 @@ def test_returns_done_cuts_bootstrap(orc):
     G = orc.returns(r, d, 0.5)
     # t=3: 8; t=2: 4 + 0.5*8 = 8; t=1 (done): 2; t=0: 1 + 0.5*2 = 2
     np.testing.assert_allclose(G[:, 0], [2.0, 2.0, 8.0, 8.0])
+
+
+def test_landscape_energy_target_terminal(orc):
+    """Energy-target terminal condition (App. C: an episode runs until the
+    reaction's terminal state): done when the pure energy of the post-step
+    state falls below the target, checked against the closed form of a single
+    Gaussian well E(x) = -exp(-|x|^2 / 2) on the recorded positions."""
+    g = inputs.rng(5)
+    D = 2
+    c, w, a = np.zeros((1, D)), np.ones(1), -np.ones(1)
+    widths = [D, 8, 8, 2 * D]
+    p = inputs.policy_params(g, widths)
+    n, T = 40, 30
+    x0 = g.uniform(-1.5, 1.5, (n, D))
+    eobs0 = np.zeros(n)
+    t0 = np.zeros(n, np.int32)
+    kw = dict(seed=3, env_ids=np.arange(n), n_steps=T, episode_limit=25, noise_sigma=0.0,
+              step_clip=0.1, x0=x0, eobs0=eobs0, t0=t0)
+    target = -0.6
+    r = orc.landscape_rollout(c, w, a, p, 8, 8, energy_target=target, **kw)
+    n_target = 0
+    for e in range(n):
+        t = 0
+        for s in range(T):
+            y = r["obs"][s, e] + r["act"][s, e]
+            E = -np.exp(-(y * y).sum() / 2)
+            assert r["energy"][s, e] == pytest.approx(E, rel=1e-14)
+            t += 1
+            want = E < target or t >= 25
+            assert r["done"][s, e] == want, (e, s)
+            n_target += int(E < target)
+            if want:
+                t = 0
+                if s + 1 < T:
+                    np.testing.assert_array_equal(r["obs"][s + 1, e],
+                                                  orc.landscape_reset_draw(3, s, e, D))
+    assert 0 < n_target < n * T
+    # +inf ends every episode after one step; -inf is the plain step limit
+    r_all = orc.landscape_rollout(c, w, a, p, 8, 8, energy_target=np.inf, **kw)
+    assert r_all["done"].all()
+    r_off = orc.landscape_rollout(c, w, a, p, 8, 8, energy_target=-np.inf, **kw)
+    r_none = orc.landscape_rollout(c, w, a, p, 8, 8, **kw)
+    for f in ("obs", "act", "done", "energy", "reward"):
+        np.testing.assert_array_equal(r_off[f], r_none[f])
+    assert r_none["done"].sum() == n
