@@ -32,6 +32,10 @@ if ROOT not in sys.path:
 
 METRIC = "agent-steps/sec on 1 GB300, served BF16 vs plain FP32; p50/p99 rollout latency"
 CHUNK = 50
+# DRAM bytes (read + write) per slot-step of the returns scan, from an ncu
+# capture of k_returns on the control workload (summarised under profiles/);
+# the traffic scales with the slot-steps scanned
+RETURNS_NCU_BYTES_PER_SLOT_STEP = None
 
 WORKLOADS = {
     "control_scale": dict(env=0, n_envs=131072, horizon=500, limit=200, h=(256, 256),
@@ -217,7 +221,8 @@ def run_gpu(args, wl, world, rank, local):
     stream = torch.cuda.Stream(device=dev)
     kw = dict(chunk_steps=CHUNK, param_seed=1 + rank)
     if wl["env"] == 2:
-        kw.update(dim=wl["dim"], n_gauss=wl["n_gauss"])
+        # the FORCE field only adds ring memory; the roll-out kernels ignore it
+        kw.update(dim=wl["dim"], n_gauss=wl["n_gauss"], flags=W.WS_FLAG_FORCE)
     path = W.WS_PATH_BATCHED_BF16
     cfg, _ = W.make_config(wl["env"], path, wl["n_envs"], wl["horizon"], wl["limit"], *wl["h"],
                            **kw)
@@ -277,8 +282,25 @@ def run_gpu(args, wl, world, rank, local):
         clk = clocks.stop()
         barrier(world)
         total_ms = max_over_ranks(sum(times), world)
+        ret_ms = [t - rm for t, rm in zip(times, roll_ms)]
+        force_ms = None
+        if wl["env"] == 2 and measure_kernel:
+            # ws_forces over the last 50-step chunk (outside the timed step; the
+            # force is an optional output), L2 flushed before each launch
+            force_ms = []
+            for _ in range(3):
+                flush.zero_()
+                torch.cuda.synchronize(dev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r.forces(min(CHUNK, H))
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                force_ms.append(e0.elapsed_time(e1))
         res = dict(agent_steps=agent_steps, total_ms=total_ms, times=times, chunk_ms=chunk_ms,
-                   roll_ms=roll_ms, clocks=clk, n_chunks=n_chunks, rollout=r, launch=launch)
+                   force_ms=force_ms,
+                   roll_ms=roll_ms, ret_ms=ret_ms, clocks=clk, n_chunks=n_chunks, rollout=r,
+                   launch=launch)
         return res
 
     main = one_path(path, args.steps, args.warmup, True)
@@ -518,6 +540,39 @@ def main():
             roofline["traffic"] = ncu_bytes[args.workload]
             roofline["traffic_algorithmic"] = (rec_bytes * main_res["agent_steps"] / wl["horizon"]
                                                * launch_steps)
+    # S7 returns scan (k_returns, one launch per bench step over the whole
+    # horizon): HBM-bound at 9 B per slot-step (reward and done read, return
+    # written); its time is the gap between the roll-out's last event and the
+    # step's end event, on the same stream
+    ret_ms = statistics.mean(main_res["ret_ms"])
+    ret_bytes = 9.0 * main_res["agent_steps"]
+    returns_roofline = {"bound": "hbm", "kernel": "k_returns",
+                        "achieved": ret_bytes / (ret_ms * 1e-3) / 1e9, "peak": hbm,
+                        "unit": "GB/s", "frac": None, "ms": ret_ms,
+                        "algorithmic_bytes": ret_bytes,
+                        "traffic": RETURNS_NCU_BYTES_PER_SLOT_STEP * main_res["agent_steps"]
+                        if RETURNS_NCU_BYTES_PER_SLOT_STEP and args.workload == "control_scale"
+                        else None,
+                        "peak_source": f"{peak_src} hbm_gbs"}
+    returns_roofline["frac"] = returns_roofline["achieved"] / hbm
+    force_roofline = None
+    if main_res.get("force_ms"):
+        # k_force_f32 (FP32 SIMT, direct difference form): per (row, Gaussian)
+        # pair D subtractions, D FMAs for |y - c|^2 and D FMAs for the force
+        # sum on the FP32 pipe (128 lanes / SM / clock), one exp on the SFU
+        import torch
+        n_sms = torch.cuda.get_device_properties(local).multi_processor_count
+        clk = (main_res["clocks"] or {}).get("sm_mhz") or 2070.0
+        f_ms = statistics.median(main_res["force_ms"])
+        pairs = wl["n_envs"] * min(CHUNK, wl["horizon"]) * wl["n_gauss"]
+        force_roofline = {"bound": "alu", "kernel": "k_force_f32 (ws_forces, 50 steps)",
+                          "op": "FP32 instructions (3 D per env-Gaussian pair)",
+                          "achieved": 3 * wl["dim"] * pairs / (f_ms * 1e-3) / 1e12,
+                          "peak": 128 * n_sms * clk * 1e6 / 1e12, "unit": "Tinst/s",
+                          "frac": None, "ms": f_ms,
+                          "peak_source": f"128 FP32 lanes / clock / SM x {n_sms} SMs x "
+                                         f"{clk:.0f} MHz"}
+        force_roofline["frac"] = force_roofline["achieved"] / force_roofline["peak"]
     lat = sorted(main_res["chunk_ms"])
     # kernels of ours per bench step: the reset (plus the landscape's energy of
     # the fresh state), per 50-step roll-out either the fused kernel and the
@@ -547,6 +602,8 @@ def main():
         "latency": {"chunk_steps": CHUNK, "p50_ms": float(np.percentile(lat, 50)),
                     "p99_ms": float(np.percentile(lat, 99))},
         "roofline": roofline,
+        "roofline_returns": returns_roofline,
+        "roofline_force": force_roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "plain_fp32": plain,

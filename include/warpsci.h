@@ -77,6 +77,8 @@ typedef enum { WS_PATH_PLAIN_FP32 = 0, WS_PATH_BATCHED_FP32 = 1, WS_PATH_BATCHED
  *   WEALTH  i64 [t][n_slots]            economy: pre-step agent wealth;
  *                                       planner slot: total wealth of its env
  *   ENERGY  f32 [t][n_slots]            landscape: E of the post-step state
+ *   FORCE   f32 [t][dim][n_slots]       landscape with WS_FLAG_FORCE: -grad E
+ *                                       of the post-step state (ws_forces)
  * State fields (no step range; t0 and n_steps must be 0):
  *   STATE   control:   f32 s[4][n_envs] (x, v, th, w), i32 t[n_envs]
  *           economy:   i64 wealth[n_agents], f32 feat[16][n_agents], i32 t[n_envs]
@@ -100,13 +102,23 @@ typedef enum {
   WS_F_STATE = 8,
   WS_F_PARAMS = 9,
   WS_F_ENV_PARAMS = 10,
-  WS_F_LOGITS = 11
+  WS_F_LOGITS = 11,
+  WS_F_FORCE = 12
 } ws_field;
 
 /* ws_config.flags: the fused kernels (economy on the BF16 path) also write each
  * step's policy outputs to the LOGITS field (costs HBM bandwidth; for tests
  * and debugging).  The per-step paths always keep them. */
 #define WS_FLAG_DEBUG_LOGITS 1u
+/* ws_config.flags: landscape episodes also end when the pure energy E(x') of
+ * the post-step state falls below ws_config.energy_target (the low-energy
+ * product basin is the reaction's terminal state, paper App. C); the env then
+ * resets like at the step limit.  On the BF16 paths E is the tensor-core
+ * estimate, so a decision within its error of the target can go either way. */
+#define WS_FLAG_ENERGY_TARGET 2u
+/* ws_config.flags: the ring also holds the landscape FORCE field (D floats
+ * per slot-step), written by ws_forces.  Landscape only. */
+#define WS_FLAG_FORCE 4u
 
 /* Roll-out configuration.  Slots: control and landscape have one agent per
  * env (n_slots = n_envs); the economy has agents_per_env[e] agents in env e,
@@ -130,6 +142,8 @@ typedef struct {
   uint64_t param_seed;    /* Philox key of policy / landscape / agent counts  */
   const int32_t *agents_per_env; /* economy, host, n_envs entries in 2..1024;
                                     NULL = draw U{8..256} from param_seed      */
+  float energy_target;    /* landscape, with WS_FLAG_ENERGY_TARGET: done when
+                             E(x') < energy_target (finite); else ignored    */
 } ws_config;
 
 /* Bytes of the two caller-owned device buffers a configuration needs:
@@ -166,6 +180,15 @@ ws_status ws_rollout(ws_ctx *ctx, uint32_t n_steps);
  * G_t = r_t + gamma (1 - done_t) G_{t+1}, with G = 0 after the window, in
  * compensated (float-float) FP32.  n_steps <= min(k, ring_steps). */
 ws_status ws_returns(ws_ctx *ctx, uint32_t n_steps);
+
+/* Landscape force over the last n_steps ring rows (steps k-n..k-1), written to
+ * the FORCE field: F = -grad E(x') = sum_m a_m e_m (x' - c_m) / w_m^2 at the
+ * post-step state x' = x + dx recorded in OBS and ACTION (paper App. C: the
+ * landscape is the potential energy of the atomic positions, the force its
+ * negative gradient).  Asynchronous.  WS_ERR_STATE without WS_FLAG_FORCE;
+ * n_steps <= min(k, ring_steps) (WS_ERR_RANGE).  A step that ended an episode
+ * still has its pre-reset x' recorded, so its force is that of x'. */
+ws_status ws_forces(ws_ctx *ctx, uint32_t n_steps);
 
 /* Copy a field (see ws_field) for absolute steps [t0, t0 + n_steps) into
  * dst (device memory if dst_on_device, else host memory; a host copy is

@@ -130,6 +130,7 @@ struct Layout {
   size_t state_bytes;
   // ring buffer: per field, [ring_steps][...]
   size_t ring_obs, ring_act, ring_logp, ring_rew, ring_done, ring_ret, ring_wealth, ring_energy;
+  size_t ring_force;  // landscape with WS_FLAG_FORCE
   size_t ring_bytes;
 };
 

@@ -12,6 +12,7 @@ struct Dev {
   uint32_t n_envs, n_slots, n_agent_slots, ring_steps, episode_limit, dim, n_gauss;
   uint32_t n_out, n_out_planner;
   float noise_sigma, step_clip, gamma;
+  float energy_target;  // landscape: done when E(x') < energy_target (-inf: off)
   uint64_t seed;        // key of the per-step draws (set by ws_reset)
   uint64_t *k;          // device step counter
   uint32_t *err;        // [0] error flag, [1] where
@@ -52,6 +53,7 @@ struct Dev {
   float *r_obs;
   void *r_act;
   float *r_logp, *r_rew, *r_ret, *r_energy;
+  float *r_force;  // landscape FORCE field [t][D][slot] (WS_FLAG_FORCE), else null
   uint8_t *r_done;
   int64_t *r_wealth;
 };
@@ -79,6 +81,8 @@ void launch_advance(const Dev &d, uint32_t n, cudaStream_t st);
 
 // ---- S7: discounted returns ----------------------------------------------
 void launch_returns(const Dev &d, uint32_t n_steps, cudaStream_t st);
+// Landscape force -grad E(x') of the last n_steps ring rows (ws_force.cu).
+void launch_forces(const Dev &d, uint32_t n_steps, cudaStream_t st);
 
 // ---- BF16 tensor-core control path -----------------------------------------
 size_t control_tc_packed_bytes(const PolicyShape &shape);

@@ -20,19 +20,24 @@
 //            dx = clip(mean + sigma z) with Philox normals; log-probability of the
 //            unclipped sample
 //   energy   E(y) at y = x + dx, whole exponents on tcgen05: with q_m =
-//            -log2(e) / (2 w_m^2), q_m |y - c_m|^2 = -2 q_m y.c_m + q_m |c_m|^2 +
-//            q_m |y|^2 is one dot product of the operand row [y, 1, |y|^2] with the
-//            Gaussian row [-2 q c, q |c|^2, q], every product split BF16 hi+lo
-//            (FP32 accumulate), in blocks of 64 Gaussians streamed by a producer
-//            warp (bulk copies into three buffers, MMAs into three TMEM
-//            accumulators); the epilogue is a_m 2^(exponent) summed per env
+//            -log2(e) / (2 w_m^2), q_m |y - c_m|^2 + log2|a_m| = -2 q_m y.c_m +
+//            (q_m |c_m|^2 + log2|a_m|) + q_m |y|^2 is one dot product of the
+//            operand row [y, 1, |y|^2] with the Gaussian row [-2 q c,
+//            q |c|^2 + log2|a|, q], every product split BF16 hi+lo (FP32
+//            accumulate).  The Gaussians are grouped by the sign of a_m, so the
+//            epilogue is one ex2 per pair summed into a positive and a negative
+//            part.  Blocks of 64 Gaussians stream through three shared-memory
+//            buffers (a loader warp) into eight TMEM accumulators (an MMA warp);
+//            the two threads of a row take the blocks of even and odd index.
 //   step     observed energy with Philox noise, reward Eobs(x) - Eobs(x'), done
-//            at the episode limit, reset to U(-3, 3)^D and a second sweep for the
-//            fresh state's energy when a tile has a reset
+//            at the episode limit or when E(y) falls below the energy target
+//            (the product basin of App. C), reset to U(-3, 3)^D and a second
+//            sweep for the fresh state's energy when a tile has a reset
 // Threads: warps 0-3 own the env rows (state, sampling, records); warps 4-7
-// take the other half of every tanh and exp epilogue; warp 8 is the producer.
-// Every wait is bounded; a wait that runs out sets the error flag and the CTA
-// leaves its loops at the next step boundary.
+// take the other half of every tanh and exp epilogue; warp 8 loads the energy
+// blocks, warp 9 issues the energy MMAs.  Every wait is bounded; a wait that
+// runs out sets the error flag and the CTA leaves its loops at the next step
+// boundary.
 #include "ws_kernels.cuh"
 #include "ws_tc.cuh"
 
@@ -498,7 +503,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     auto kofs = [](int k) -> uint32_t { return (uint32_t)((k >> 3) * 128 + (k & 7) * 2); };
 
     // One energy sweep over this CTA's Gaussians at the rows of the energy
-    // operand; returns the whole-landscape energy on half 0.
+    // operand; returns the whole-landscape energy (the same bits on both halves
+    // and on both CTAs of a pair).
     auto sweep = [&]() -> float {
       if (tid == 0) *cmd = 1u;
       tc::fence_async_smem();
@@ -551,10 +557,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           const float other = recv[par * kRows + r];
           E = rank == 0 ? E + other : other + E;
         }
+        xch_e[r] = E;
       }
       px ^= 1u;
       par ^= 1u;
-      bar_sync_n(pair, 64);  // xch_e is free again
+      bar_sync_n(pair, 64);
+      if (!own) E = xch_e[r];  // half 1 writes xch_e next only after this read
       return E;
     };
     // The energy operand row [v_hi | v_hi | v_lo | 1, 1 | vv_hi, vv_hi, vv_lo | 0]
@@ -738,12 +746,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         // a reset; the same vote on every CTA of the cluster, whose states are
         // identical): energy of the fresh states
         const int t2 = t + 1;
-        const bool done = valid && t2 >= (int)d.episode_limit;
+        bool done = false;
 #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
           write_ae(x, lp);
           if (pass == 0 && own && rec) d.r_logp[rowR * S + e] = lp + xch_lp[r];
           const float E = sweep();
+          // the step limit, or the product basin reached (both halves and both
+          // CTAs of a pair hold the same E, so they take the same decision)
+          if (pass == 0) done = valid && (t2 >= (int)d.episode_limit || E < d.energy_target);
           if (pass == 1) {
             if (own && done) {
               const uint4 rn = draw(seed, k, e, 0, kTagNoise, 1);

@@ -570,7 +570,9 @@ __device__ float energy_combine(const Dev &d, uint32_t e) {
 }
 
 // x' = x + dx; E' and observed E' = E' + sigma N(0,1) (NOISE, sub 0); reward
-// = Eobs(x) - Eobs(x'); done at the episode limit; reset redraws x (RESET).
+// = Eobs(x) - Eobs(x'); done at the episode limit or when E' falls below the
+// energy target (App. C: the episode ends in the product basin); reset
+// redraws x (RESET).
 __global__ void k_landscape_step(Dev d, uint32_t off) {
   const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= d.n_envs) return;
@@ -585,7 +587,7 @@ __global__ void k_landscape_step(Dev d, uint32_t off) {
   d.r_energy[o] = E2;
   d.r_rew[o] = d.eobs[e] - eobs2;
   const int t2 = d.t[e] + 1;
-  const bool done = t2 >= (int)d.episode_limit;
+  const bool done = t2 >= (int)d.episode_limit || E2 < d.energy_target;
   d.r_done[o] = (uint8_t)done;
   if (done) {
     landscape_reset_env(d, (uint32_t)k, e);
@@ -633,30 +635,137 @@ __global__ void k_advance(Dev d, uint32_t n) {
 
 // S7: G_t = r_t + gamma (1 - d_t) G_{t+1} over the last n rows, carried as a
 // float-float pair (error-free TwoProduct / TwoSum with explicit roundings).
-__global__ void k_returns(Dev d, uint32_t n) {
-  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= d.n_slots) return;
-  const uint64_t k = d.k[0];
-  const float g = d.gamma;
-  float hi = 0.f, lo = 0.f;
-  for (uint32_t i = 0; i < n; ++i) {
-    const uint64_t t = k - 1 - i;
-    const size_t o = (size_t)(t % d.ring_steps) * d.n_slots + s;
-    const float r = d.r_rew[o];
-    if (d.r_done[o]) {
-      hi = r;
-      lo = 0.f;
-    } else {
-      const float p_hi = __fmul_rn(g, hi);
-      const float p_lo = __fadd_rn(__fmaf_rn(g, hi, -p_hi), __fmul_rn(g, lo));
-      const float s_hi = __fadd_rn(r, p_hi);
-      const float bb = __fsub_rn(s_hi, r);
-      const float s_lo = __fadd_rn(__fsub_rn(r, __fsub_rn(s_hi, bb)), __fsub_rn(p_hi, bb));
-      const float t_lo = __fadd_rn(s_lo, p_lo);
-      hi = __fadd_rn(s_hi, t_lo);
-      lo = __fsub_rn(t_lo, __fsub_rn(hi, s_hi));
+//
+// The scan is HBM-bound (9 B per slot-step: reward and done read, return
+// written) and each slot's steps are serial, so the bandwidth comes from the
+// loads in flight: a thread owns V consecutive slots (V = 4 when the slot count
+// keeps every ring row 16-byte aligned: one float4 of rewards and one word of
+// four done flags per step) and loads the rewards and done flags of its next
+// kRetU steps into registers before it scans the current kRetU.
+constexpr int kRetU = 16;
+
+// Branch-free (the done flag selects), so that a thread's V chains interleave.
+__device__ __forceinline__ float ret_update(float r, bool dn, float g, float &hi, float &lo) {
+  const float p_hi = __fmul_rn(g, hi);
+  const float p_lo = __fadd_rn(__fmaf_rn(g, hi, -p_hi), __fmul_rn(g, lo));
+  const float s_hi = __fadd_rn(r, p_hi);
+  const float bb = __fsub_rn(s_hi, r);
+  const float s_lo = __fadd_rn(__fsub_rn(r, __fsub_rn(s_hi, bb)), __fsub_rn(p_hi, bb));
+  const float t_lo = __fadd_rn(s_lo, p_lo);
+  const float n_hi = __fadd_rn(s_hi, t_lo);
+  const float n_lo = __fsub_rn(t_lo, __fsub_rn(n_hi, s_hi));
+  hi = dn ? r : n_hi;
+  lo = dn ? 0.f : n_lo;
+  return hi;
+}
+
+template <int V>
+struct RetVec;
+template <>
+struct RetVec<1> {
+  float r;
+  uint32_t d;
+  __device__ __forceinline__ void load(const float *rew, const uint8_t *done, size_t o) {
+    r = __ldcs(rew + o);
+    d = __ldcs(done + o);
+  }
+  __device__ __forceinline__ float at(int) const { return r; }
+  __device__ __forceinline__ bool dn(int) const { return d != 0; }
+  __device__ __forceinline__ static void store(float *ret, size_t o, const float (&g)[1]) {
+    __stcs(ret + o, g[0]);
+  }
+};
+template <>
+struct RetVec<4> {
+  float4 r;
+  uint32_t d;  // the four done bytes
+  __device__ __forceinline__ void load(const float *rew, const uint8_t *done, size_t o) {
+    r = __ldcs((const float4 *)(rew + o));
+    d = __ldcs((const unsigned int *)(done + o));
+  }
+  __device__ __forceinline__ float at(int v) const {
+    return v == 0 ? r.x : v == 1 ? r.y : v == 2 ? r.z : r.w;
+  }
+  __device__ __forceinline__ bool dn(int v) const { return ((d >> (8 * v)) & 0xFFu) != 0; }
+  __device__ __forceinline__ static void store(float *ret, size_t o, const float (&g)[4]) {
+    __stcs((float4 *)(ret + o), make_float4(g[0], g[1], g[2], g[3]));
+  }
+};
+
+template <int V>
+__device__ __forceinline__ void ret_load(const float *__restrict__ rew,
+                                         const uint8_t *__restrict__ done, size_t S, uint32_t R,
+                                         size_t s, uint32_t row, uint32_t left,
+                                         RetVec<V> (&b)[kRetU]) {
+#pragma unroll
+  for (int j = 0; j < kRetU; ++j) {
+    if ((uint32_t)j < left) b[j].load(rew, done, (size_t)row * S + s);
+    row = row == 0 ? R - 1 : row - 1;
+  }
+}
+
+// Scans the kRetU steps held in b (the first `left` of them), newest first.
+template <int V, bool FULL>
+__device__ __forceinline__ void ret_scan_n(const RetVec<V> (&b)[kRetU], uint32_t left, float g,
+                                           float (&hi)[V], float (&lo)[V],
+                                           float *__restrict__ ret, size_t S, uint32_t R,
+                                           size_t s, uint32_t &row) {
+#pragma unroll
+  for (int j = 0; j < kRetU; ++j) {
+    if (FULL || (uint32_t)j < left) {
+      float G[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) G[v] = ret_update(b[j].at(v), b[j].dn(v), g, hi[v], lo[v]);
+      RetVec<V>::store(ret, (size_t)row * S + s, G);
     }
-    d.r_ret[o] = hi;
+    row = row == 0 ? R - 1 : row - 1;
+  }
+}
+
+template <int V>
+__device__ __forceinline__ void ret_scan(const RetVec<V> (&b)[kRetU], uint32_t left, float g,
+                                         float (&hi)[V], float (&lo)[V], float *__restrict__ ret,
+                                         size_t S, uint32_t R, size_t s, uint32_t &row) {
+  if (left >= (uint32_t)kRetU)
+    ret_scan_n<V, true>(b, left, g, hi, lo, ret, S, R, s, row);
+  else
+    ret_scan_n<V, false>(b, left, g, hi, lo, ret, S, R, s, row);
+}
+
+// Two register buffers alternate without copies: the loads of one are in
+// flight while the other is scanned.
+template <int V, int T, int MINB>
+__global__ __launch_bounds__(T, MINB) void k_returns(Dev d, uint32_t n) {
+  const size_t s = ((size_t)blockIdx.x * T + threadIdx.x) * V;
+  if (s >= d.n_slots) return;
+  const float *__restrict__ rew = d.r_rew;
+  const uint8_t *__restrict__ done = d.r_done;
+  float *__restrict__ ret = d.r_ret;
+  const size_t S = d.n_slots;
+  const uint32_t R = d.ring_steps;
+  const float g = d.gamma;
+  uint32_t row = (uint32_t)((d.k[0] - 1) % R);  // ring row of step k-1 (scan cursor)
+  uint32_t lrow = row;                          // ring row of the next load
+  auto back = [&](uint32_t r0) {
+#pragma unroll
+    for (int j = 0; j < kRetU; ++j) r0 = r0 == 0 ? R - 1 : r0 - 1;
+    return r0;
+  };
+  RetVec<V> bufA[kRetU], bufB[kRetU];
+  float hi[V], lo[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) hi[v] = lo[v] = 0.f;
+  ret_load<V>(rew, done, S, R, s, lrow, n, bufA);
+  lrow = back(lrow);
+  for (uint32_t i = 0; i < n; i += 2 * kRetU) {
+    const uint32_t left = n - i;
+    if (left > (uint32_t)kRetU) ret_load<V>(rew, done, S, R, s, lrow, left - kRetU, bufB);
+    lrow = back(lrow);
+    ret_scan<V>(bufA, left, g, hi, lo, ret, S, R, s, row);
+    if (left <= (uint32_t)kRetU) break;
+    if (left > (uint32_t)(2 * kRetU)) ret_load<V>(rew, done, S, R, s, lrow, left - 2 * kRetU, bufA);
+    lrow = back(lrow);
+    ret_scan<V>(bufB, left - kRetU, g, hi, lo, ret, S, R, s, row);
   }
 }
 
@@ -737,7 +846,10 @@ void launch_plain_step(const Dev &d, uint32_t off, cudaStream_t st, const Branch
 void launch_advance(const Dev &d, uint32_t n, cudaStream_t st) { k_advance<<<1, 32, 0, st>>>(d, n); }
 
 void launch_returns(const Dev &d, uint32_t n_steps, cudaStream_t st) {
-  k_returns<<<blocks(d.n_slots, 256), 256, 0, st>>>(d, n_steps);
+  if (d.n_slots % 4 == 0)  // every ring row starts on a 16-byte boundary
+    k_returns<4, 32, 8><<<blocks(d.n_slots / 4, 32), 32, 0, st>>>(d, n_steps);
+  else
+    k_returns<1, 128, 5><<<blocks(d.n_slots, 128), 128, 0, st>>>(d, n_steps);
 }
 
 }  // namespace ws

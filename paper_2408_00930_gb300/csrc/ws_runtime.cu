@@ -3,6 +3,7 @@
 // CUDA-graph capture of the horizon loop, fetch/load, host-side waits.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -62,7 +63,12 @@ ws_status validate(const ws_config *cfg) {
   if (cfg->ring_steps < 1 || cfg->episode_limit < 1) return WS_ERR_INVALID;
   if (cfg->hidden0 < 1 || cfg->hidden0 > 4096 || cfg->hidden1 < 1 || cfg->hidden1 > 4096)
     return WS_ERR_INVALID;
-  if (cfg->flags & ~WS_FLAG_DEBUG_LOGITS) return WS_ERR_INVALID;
+  if (cfg->flags & ~(WS_FLAG_DEBUG_LOGITS | WS_FLAG_ENERGY_TARGET | WS_FLAG_FORCE))
+    return WS_ERR_INVALID;
+  if ((cfg->flags & WS_FLAG_FORCE) && cfg->env != WS_ENV_LANDSCAPE) return WS_ERR_INVALID;
+  if ((cfg->flags & WS_FLAG_ENERGY_TARGET) &&
+      (cfg->env != WS_ENV_LANDSCAPE || !std::isfinite(cfg->energy_target)))
+    return WS_ERR_INVALID;
   if (!(cfg->gamma >= 0.f && cfg->gamma <= 1.f)) return WS_ERR_INVALID;
   if (cfg->env == WS_ENV_LANDSCAPE) {
     if (cfg->dim < 1 || cfg->dim > 64 || cfg->n_gauss < 1 || cfg->n_gauss > (1u << 22))
@@ -280,6 +286,9 @@ Layout make_layout(const ws_config *cfg, const std::vector<int32_t> &agents) {
   if (cfg->env == WS_ENV_ECONOMY) r += up(R * S * 8);
   L.ring_energy = r;
   if (cfg->env == WS_ENV_LANDSCAPE) r += up(R * S * 4);
+  L.ring_force = r;
+  if (cfg->env == WS_ENV_LANDSCAPE && (cfg->flags & WS_FLAG_FORCE))
+    r += up(R * (size_t)cfg->dim * S * 4);
   L.ring_bytes = r;
   return L;
 }
@@ -301,6 +310,7 @@ void make_dev(ws_ctx *c) {
   d.n_out = L.n_out;
   d.n_out_planner = L.n_out_planner;
   d.noise_sigma = cfg.noise_sigma;
+  d.energy_target = (cfg.flags & WS_FLAG_ENERGY_TARGET) ? cfg.energy_target : -INFINITY;
   d.step_clip = cfg.step_clip;
   d.gamma = cfg.gamma;
   d.seed = c->seed;
@@ -379,6 +389,7 @@ void make_dev(ws_ctx *c) {
   d.r_ret = (float *)(R + L.ring_ret);
   d.r_wealth = cfg.env == WS_ENV_ECONOMY ? (int64_t *)(R + L.ring_wealth) : nullptr;
   d.r_energy = cfg.env == WS_ENV_LANDSCAPE ? (float *)(R + L.ring_energy) : nullptr;
+  d.r_force = (cfg.flags & WS_FLAG_FORCE) ? (float *)(R + L.ring_force) : nullptr;
 }
 
 void drop_graphs(ws_ctx *c) {
@@ -521,6 +532,9 @@ size_t ring_field_step_bytes(const ws_ctx *c, ws_field f, size_t *field_off) {
     case WS_F_ENERGY:
       if (L.env != WS_ENV_LANDSCAPE) return 0;
       *field_off = L.ring_energy; return S * 4;
+    case WS_F_FORCE:
+      if (!(c->cfg.flags & WS_FLAG_FORCE)) return 0;
+      *field_off = L.ring_force; return (size_t)c->cfg.dim * S * 4;
     default: return 0;
   }
 }
@@ -758,6 +772,15 @@ ws_status ws_returns(ws_ctx *c, uint32_t n) {
   if (n == 0 || n > c->k_host || n > c->L.ring_steps) return WS_ERR_RANGE;
   launch_returns(c->d, n, c->stream);
   return cuda_check(c, cudaGetLastError(), "returns");
+}
+
+ws_status ws_forces(ws_ctx *c, uint32_t n) {
+  if (!c) return WS_ERR_INVALID;
+  if (c->err != WS_OK) return c->err;
+  if (!(c->cfg.flags & WS_FLAG_FORCE)) return WS_ERR_STATE;
+  if (n == 0 || n > c->k_host || n > c->L.ring_steps) return WS_ERR_RANGE;
+  launch_forces(c->d, n, c->stream);
+  return cuda_check(c, cudaGetLastError(), "forces");
 }
 
 }  // extern "C"

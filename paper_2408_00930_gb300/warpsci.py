@@ -24,9 +24,10 @@ STATUS_NAMES = {0: "WS_OK", 1: "WS_ERR_INVALID", 2: "WS_ERR_NOMEM", 3: "WS_ERR_C
 WS_ENV_CONTROL, WS_ENV_ECONOMY, WS_ENV_LANDSCAPE = 0, 1, 2
 WS_PATH_PLAIN_FP32, WS_PATH_BATCHED_FP32, WS_PATH_BATCHED_BF16 = 0, 1, 2
 (WS_F_OBS, WS_F_ACTION, WS_F_LOGP, WS_F_REWARD, WS_F_DONE, WS_F_RETURN, WS_F_WEALTH, WS_F_ENERGY,
- WS_F_STATE, WS_F_PARAMS, WS_F_ENV_PARAMS, WS_F_LOGITS) = range(12)
+ WS_F_STATE, WS_F_PARAMS, WS_F_ENV_PARAMS, WS_F_LOGITS, WS_F_FORCE) = range(13)
 
 EXPORTED = ["ws_query_bytes", "ws_create", "ws_reset", "ws_step", "ws_rollout", "ws_returns",
+            "ws_forces",
             "ws_fetch", "ws_load", "ws_get_step", "ws_sync", "ws_last_error", "ws_destroy",
             "ws_policy_forward_noalloc", "ws_get_launch", "ws_set_launch", "ws_tune",
             "ws_server_create", "ws_server_submit",
@@ -34,6 +35,8 @@ EXPORTED = ["ws_query_bytes", "ws_create", "ws_reset", "ws_step", "ws_rollout", 
             "ws_server_get_stats", "ws_server_destroy"]
 WS_REQ_CONSUME_ON_READY = 1
 WS_FLAG_DEBUG_LOGITS = 1
+WS_FLAG_ENERGY_TARGET = 2
+WS_FLAG_FORCE = 4
 
 
 class ws_config(C.Structure):
@@ -43,7 +46,7 @@ class ws_config(C.Structure):
                 ("hidden0", C.c_uint32), ("hidden1", C.c_uint32), ("dim", C.c_uint32),
                 ("n_gauss", C.c_uint32), ("noise_sigma", C.c_float), ("step_clip", C.c_float),
                 ("gamma", C.c_float), ("flags", C.c_uint32), ("param_seed", C.c_uint64),
-                ("agents_per_env", C.POINTER(C.c_int32))]
+                ("agents_per_env", C.POINTER(C.c_int32)), ("energy_target", C.c_float)]
 
 
 class ws_launch(C.Structure):
@@ -99,6 +102,7 @@ def lib():
         L.ws_step.argtypes = [P]
         L.ws_rollout.argtypes = [P, C.c_uint32]
         L.ws_returns.argtypes = [P, C.c_uint32]
+        L.ws_forces.argtypes = [P, C.c_uint32]
         L.ws_fetch.argtypes = [P, C.c_int, C.c_uint64, C.c_uint32, P, C.c_size_t, C.c_int]
         L.ws_load.argtypes = [P, C.c_int, P, C.c_size_t, C.c_int, C.c_uint64]
         L.ws_get_step.argtypes = [P, C.POINTER(C.c_uint64)]
@@ -158,6 +162,10 @@ def ws_returns(ctx, n_steps):
     return lib().ws_returns(ctx, n_steps)
 
 
+def ws_forces(ctx, n_steps):
+    return lib().ws_forces(ctx, n_steps)
+
+
 def ws_fetch(ctx, field, t0, n_steps, dst_ptr, dst_bytes, dst_on_device):
     return lib().ws_fetch(ctx, field, t0, n_steps, dst_ptr, dst_bytes, int(dst_on_device))
 
@@ -211,7 +219,7 @@ def ws_policy_forward_noalloc(obs_ptr, n_rows, params_ptr, in_dim, hidden0, hidd
 # --- convenience owner --------------------------------------------------------
 def make_config(env, path, n_envs, ring_steps, episode_limit, hidden0, hidden1, *,
                 chunk_steps=0, dim=0, n_gauss=0, noise_sigma=0.05, step_clip=0.1, gamma=0.99,
-                param_seed=1, agents_per_env=None, flags=0):
+                param_seed=1, agents_per_env=None, flags=0, energy_target=None):
     cfg = ws_config()
     cfg.struct_size = C.sizeof(ws_config)
     cfg.env, cfg.path, cfg.n_envs = env, path, n_envs
@@ -219,6 +227,9 @@ def make_config(env, path, n_envs, ring_steps, episode_limit, hidden0, hidden1, 
     cfg.hidden0, cfg.hidden1, cfg.dim, cfg.n_gauss = hidden0, hidden1, dim, n_gauss
     cfg.noise_sigma, cfg.step_clip, cfg.gamma = noise_sigma, step_clip, gamma
     cfg.flags, cfg.param_seed = flags, param_seed
+    if energy_target is not None:  # landscape: done when E(x') < energy_target
+        cfg.flags |= WS_FLAG_ENERGY_TARGET
+        cfg.energy_target = energy_target
     keep = None
     if agents_per_env is not None:
         keep = np.ascontiguousarray(agents_per_env, dtype=np.int32)
@@ -272,6 +283,9 @@ class Rollout:
     def returns(self, n):
         self._ok(ws_returns(self.ctx, n), "ws_returns")
 
+    def forces(self, n):
+        self._ok(ws_forces(self.ctx, n), "ws_forces")
+
     def sync(self, timeout_ms=0):
         self._ok(ws_sync(self.ctx, timeout_ms), "ws_sync")
 
@@ -315,6 +329,8 @@ class Rollout:
             return np.uint8, (S,)
         if field == WS_F_WEALTH:
             return np.int64, (S,)
+        if field == WS_F_FORCE:
+            return np.float32, (self.dim, S)
         raise ValueError(field)
 
     def fetch(self, field, t0, n):

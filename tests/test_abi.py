@@ -66,6 +66,17 @@ def test_query_bytes_validation(lib):
     assert W.ws_query_bytes(bad)[0] == W.WS_ERR_INVALID
     cfg.struct_size = 8
     assert W.ws_query_bytes(cfg)[0] == W.WS_ERR_INVALID
+    # the energy target is a landscape option and must be finite
+    ok, _ = W.make_config(W.WS_ENV_LANDSCAPE, W.WS_PATH_PLAIN_FP32, 8, 10, 10, 16, 16, dim=4,
+                          n_gauss=4, energy_target=-0.5)
+    assert ok.flags & W.WS_FLAG_ENERGY_TARGET and W.ws_query_bytes(ok)[0] == W.WS_OK
+    ok.energy_target = float("nan")
+    assert W.ws_query_bytes(ok)[0] == W.WS_ERR_INVALID
+    bad, _ = W.make_config(W.WS_ENV_CONTROL, W.WS_PATH_PLAIN_FP32, 8, 10, 10, 16, 16,
+                           energy_target=-0.5)
+    assert W.ws_query_bytes(bad)[0] == W.WS_ERR_INVALID
+    bad.flags = 4
+    assert W.ws_query_bytes(bad)[0] == W.WS_ERR_INVALID
 
 
 def test_economy_slot_count_uses_agent_counts(lib):

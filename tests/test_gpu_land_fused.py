@@ -183,3 +183,25 @@ def test_fused_bench_launch_shape(torch):
     assert rec[W.WS_F_DONE].sum() == 0
     assert np.all(np.abs(rec[W.WS_F_ACTION]) <= np.float32(0.1))
     _teacher_forced(rec, init, par, cwa, [0, 4097, 8191], T, 1000, 11)
+
+
+@pytest.mark.parametrize("tile_ctas", [1, 2])
+def test_fused_energy_target_terminal(torch, tile_ctas):
+    """Episodes end on reaching the energy target (the product basin) as well
+    as at the step limit: every done flag against the FP64 energy of the
+    recorded post-step state (decisions within the BF16 energy error of the
+    target may go either way), every reset against its Philox draw."""
+    n, T, limit, target = 256, 24, 1000, -0.005
+    r = land(n, T, limit, seed=3, chunk_steps=10, energy_target=target)
+    r.set_launch(tile_ctas=tile_ctas)
+    r.reset(4)
+    r.rollout(T)
+    r.sync()
+    obs, act, dn = (r.fetch(f, 0, T) for f in (W.WS_F_OBS, W.WS_F_ACTION, W.WS_F_DONE))
+    envp = r.fetch_raw(W.WS_F_ENV_PARAMS, 4 * (M * D + 2 * M)).view(np.float32)
+    c = envp[:M * D].reshape(M, D).astype(np.float64)
+    w, a = envp[M * D:M * D + M].astype(np.float64), envp[M * D + M:].astype(np.float64)
+    r.close()
+    n_target, n_band = H.check_landscape_dones(obs, act, dn, (c, w, a), limit, target, 4,
+                                               ENERGY_TOL)
+    assert n_target >= 20 and n_band <= 0.05 * n * T, (n_target, n_band)

@@ -120,3 +120,25 @@ def test_graph_path_bytes_equal_plain_path(torch):
                                                           W.WS_F_OBS, W.WS_F_REWARD)])
         r.close()
     assert out[0] == out[1]
+
+
+@pytest.mark.parametrize("path", [W.WS_PATH_PLAIN_FP32, W.WS_PATH_BATCHED_FP32])
+def test_energy_target_terminal(torch, path):
+    """Episodes end at the step limit or on reaching the energy target (the
+    product basin); every done flag against the FP64 energy of the recorded
+    post-step state, every reset against its Philox draw."""
+    D, M, n, h, T, limit = 8, 64, 120, (32, 32), 40, 30
+    r = land(path, n, D=D, M=M, ring=T, limit=limit, seed=6, h=h, chunk_steps=7,
+             energy_target=-0.01)
+    r.reset(13)
+    r.rollout(T)
+    r.sync()
+    obs, act, dn = (r.fetch(f, 0, T) for f in (W.WS_F_OBS, W.WS_F_ACTION, W.WS_F_DONE))
+    raw = r.fetch_raw(W.WS_F_ENV_PARAMS, 4 * (M * D + 2 * M))
+    c = raw[:4 * M * D].view(np.float32).reshape(M, D).astype(np.float64)
+    wd = raw[4 * M * D:4 * M * D + 4 * M].view(np.float32).astype(np.float64)
+    am = raw[4 * M * D + 4 * M:].view(np.float32).astype(np.float64)
+    n_target, n_band = H.check_landscape_dones(obs, act, dn, (c, wd, am), limit, -0.01, 13,
+                                               TOL_F32)
+    assert n_target >= 5 and n_band <= 2, (n_target, n_band)
+    r.close()

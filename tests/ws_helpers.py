@@ -61,3 +61,35 @@ def first_divergence(ambiguous):
 def valid_mask(first, T):
     """[T][n] True for steps strictly before each env's first ambiguous step."""
     return np.arange(T)[:, None] < first[None, :]
+
+
+def check_landscape_dones(obs, act, done, cwa, limit, target, seed, tol):
+    """Done flags of a landscape roll-out recorded from a reset at step 0 (obs
+    and act [T][D][n]): done at the step limit or when the FP64 energy of the
+    recorded post-step state x + dx is below the target.  A decision whose FP64
+    energy lies within tol * max(scale, 1e-3) of the target may go either way
+    (the GPU decides on its own FP32 or BF16 estimate).  The state after a done
+    is the Philox reset draw.  Returns (energy-target dones, borderline cases)."""
+    import oracle
+    c, w, a = cwa
+    T, D, n = obs.shape
+    n_target = n_band = 0
+    for e in range(n):
+        t = 0
+        for s in range(T):
+            y = (obs[s][:, e] + act[s][:, e]).astype(np.float32).astype(np.float64)
+            E = oracle.landscape_energy(c, w, a, y)
+            t += 1
+            if abs(E - target) <= tol * max(oracle.landscape_energy_scale(c, w, a, y), 1e-3):
+                n_band += 1
+            else:
+                assert bool(done[s][e]) == (t >= limit or E < target), (s, e, E, target)
+            if done[s][e]:
+                n_target += int(t < limit)
+                t = 0
+                if s + 1 < T:
+                    np.testing.assert_array_equal(
+                        obs[s + 1][:, e], oracle.landscape_reset_draw(seed, s, e, D).astype(np.float32))
+            elif s + 1 < T:
+                np.testing.assert_array_equal(obs[s + 1][:, e], y.astype(np.float32))
+    return n_target, n_band
