@@ -51,6 +51,9 @@ WORKLOADS = {
                       n_gauss=4096,
                       desc="landscape, 8,192 envs x 1 agent, D=24, M=4,096 Gaussians, "
                            "horizon 1,000, policy 24-256-256-48"),
+    "acrobot": dict(env=3, n_envs=10000, horizon=500, limit=500, h=(64, 64),
+                    desc="acrobot, 10,000 envs x 1 agent, horizon 500, policy 6-64-64-3, "
+                         "episode limit 500"),
 }
 
 
@@ -59,6 +62,8 @@ def flops_per_agent_step(wl):
         w = [4, *wl["h"], 2]
     elif wl["env"] == 1:
         w = [16, *wl["h"], 20]
+    elif wl["env"] == 3:
+        w = [6, *wl["h"], 3]
     else:
         w = [wl["dim"], *wl["h"], 2 * wl["dim"]]
     return 2 * sum(a * b for a, b in zip(w[:-1], w[1:]))
@@ -175,6 +180,11 @@ def _oracle_shard(args):
         oracle.econ_rollout(ap, pp, seed=1, env_ids=env_ids, n_agents=na, n_steps=steps,
                             episode_limit=wl["limit"])
         agent_steps = (sum(na) + len(env_ids)) * steps
+    elif wl["env"] == 3:
+        p = oracle.policy_init(1, 0, [6, *wl["h"], 3])
+        oracle.acrobot_rollout(p, *wl["h"], seed=1, env_ids=env_ids, n_steps=steps,
+                               episode_limit=wl["limit"])
+        agent_steps = len(env_ids) * steps
     else:
         c, w, a = oracle.landscape_init(1, wl["dim"], wl["n_gauss"])
         p = oracle.policy_init(1, 0, [wl["dim"], *wl["h"], 2 * wl["dim"]])
@@ -415,6 +425,9 @@ def _param_bytes(wl):
         w = [16, *wl["h"], 20]
         pw = [16, *wl["h"], 10]
         extra = sum(a * b + b for a, b in zip(pw[:-1], pw[1:]))
+    elif wl["env"] == 3:
+        w = [6, *wl["h"], 3]
+        extra = 0
     else:
         w = [wl["dim"], *wl["h"], 2 * wl["dim"]]
         extra = 0
@@ -488,7 +501,12 @@ def main():
               "peak_source": f"{peak_src} bf16 sustained" if bf16 else
               f"{peak_src} bf16 sustained / 4 (fp32 SIMT)"}
     tensor["frac"] = tensor["achieved"] / tensor["peak"]
-    if bf16:
+    if bf16 and wl["env"] == 3:
+        # acrobot BF16: per-step kernels (observe, three tcgen05 layers, sample,
+        # RK4 step) captured in CUDA graphs; no fused kernel
+        roofline = dict(tensor, traffic=None,
+                        kernel="per-step kernels, tcgen05 policy layers, CUDA graphs")
+    elif bf16:
         # The fused kernels are bound by the SFU (tanh, exp2): an SM retires 16
         # SFU results per clock (measured 15.2 for tanh.approx in any of f32 /
         # bf16x2 / f16x2 form).  SFU results per agent-step, counted from the
@@ -535,7 +553,7 @@ def main():
         ncu_bytes = {"control_scale": (3.461888 + 135.865344) * 1e6,
                      "economy": 92.359424e6 + 1.189169e9,
                      "landscape": (1.788928 + 24.135424) * 1e6}
-        rec_bytes = {0: 29.0, 1: 85.0, 2: 205.0}[wl["env"]]
+        rec_bytes = {0: 29.0, 1: 85.0, 2: 205.0, 3: 37.0}[wl["env"]]
         if args.workload in ncu_bytes:
             roofline["traffic"] = ncu_bytes[args.workload]
             roofline["traffic_algorithmic"] = (rec_bytes * main_res["agent_steps"] / wl["horizon"]
@@ -557,22 +575,30 @@ def main():
     returns_roofline["frac"] = returns_roofline["achieved"] / hbm
     force_roofline = None
     if main_res.get("force_ms"):
-        # k_force_f32 (FP32 SIMT, direct difference form): per (row, Gaussian)
-        # pair D subtractions, D FMAs for |y - c|^2 and D FMAs for the force
-        # sum on the FP32 pipe (128 lanes / SM / clock), one exp on the SFU
         import torch
         n_sms = torch.cuda.get_device_properties(local).multi_processor_count
         clk = (main_res["clocks"] or {}).get("sm_mhz") or 2070.0
         f_ms = statistics.median(main_res["force_ms"])
         pairs = wl["n_envs"] * min(CHUNK, wl["horizon"]) * wl["n_gauss"]
-        force_roofline = {"bound": "alu", "kernel": "k_force_f32 (ws_forces, 50 steps)",
-                          "op": "FP32 instructions (3 D per env-Gaussian pair)",
-                          "achieved": 3 * wl["dim"] * pairs / (f_ms * 1e-3) / 1e12,
-                          "peak": 128 * n_sms * clk * 1e6 / 1e12, "unit": "Tinst/s",
-                          "frac": None, "ms": f_ms,
-                          "peak_source": f"128 FP32 lanes / clock / SM x {n_sms} SMs x "
-                                         f"{clk:.0f} MHz"}
-        force_roofline["frac"] = force_roofline["achieved"] / force_roofline["peak"]
+        if bf16:
+            # k_force_tc: exponents and the force sums on tcgen05; the epilogue's
+            # one ex2 per (row, Gaussian) pair on the SFU (16 / clock / SM) binds
+            force_roofline = {"bound": "alu", "kernel": "k_force_tc (ws_forces, 50 steps)",
+                              "op": "ex2 on the SFU (one per env-Gaussian pair)",
+                              "achieved": pairs / (f_ms * 1e-3) / 1e12,
+                              "peak": 16 * n_sms * clk * 1e6 / 1e12, "unit": "Top/s"}
+            src = f"16 SFU results / clock / SM x {n_sms} SMs x {clk:.0f} MHz"
+        else:
+            # k_force_f32 (FP32 SIMT, direct difference form): per pair D
+            # subtractions, D FMAs for |y - c|^2 and D FMAs for the force sum on
+            # the FP32 pipe (128 lanes / SM / clock), one exp
+            force_roofline = {"bound": "alu", "kernel": "k_force_f32 (ws_forces, 50 steps)",
+                              "op": "FP32 instructions (3 D per env-Gaussian pair)",
+                              "achieved": 3 * wl["dim"] * pairs / (f_ms * 1e-3) / 1e12,
+                              "peak": 128 * n_sms * clk * 1e6 / 1e12, "unit": "Tinst/s"}
+            src = f"128 FP32 lanes / clock / SM x {n_sms} SMs x {clk:.0f} MHz"
+        force_roofline.update(ms=f_ms, peak_source=src,
+                              frac=force_roofline["achieved"] / force_roofline["peak"])
     lat = sorted(main_res["chunk_ms"])
     # kernels of ours per bench step: the reset (plus the landscape's energy of
     # the fresh state), per 50-step roll-out either the fused kernel and the
@@ -581,10 +607,10 @@ def main():
     launch = main_res["launch"] or {}
     ch = int(launch.get("chunk_steps", CHUNK))
     lens = [min(CHUNK, wl["horizon"] - c * CHUNK) for c in range(n_chunks)]
-    if bf16:
+    if bf16 and wl["env"] != 3:
         per_roll = sum(-(-n // ch) * 2 for n in lens)
     else:
-        per_step = {0: 6, 1: 14, 2: 9}[wl["env"]]
+        per_step = {0: 6, 1: 14, 2: 9, 3: 6}[wl["env"]]
         per_roll = sum(per_step * n + -(-n // ch) for n in lens)
     per_launch = (3 if wl["env"] == 2 else 1) + per_roll + 1
     out = {

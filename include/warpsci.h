@@ -53,8 +53,17 @@ typedef enum {
 } ws_status;
 
 /* Environment families (paper App. C: classic control, multi-agent
- * economics, catalytic reaction paths on an energy landscape). */
-typedef enum { WS_ENV_CONTROL = 0, WS_ENV_ECONOMY = 1, WS_ENV_LANDSCAPE = 2 } ws_env;
+ * economics, catalytic reaction paths on an energy landscape).  ACROBOT is the
+ * second classic-control benchmark: the two-link acrobot of Sutton & Barto
+ * (book dynamics, one RK4 step of 0.2 s per env step, torque a - 1 for action
+ * a in {0, 1, 2}, done when the tip rises more than one link above the pivot
+ * or at the episode limit, reward -1 per step and 0 on the terminal step). */
+typedef enum {
+  WS_ENV_CONTROL = 0,
+  WS_ENV_ECONOMY = 1,
+  WS_ENV_LANDSCAPE = 2,
+  WS_ENV_ACROBOT = 3
+} ws_env;
 
 /* Execution paths.  PLAIN_FP32: one kernel launch per sub-step (observe,
  * each policy layer, sample, env step) per step, FP32 SIMT, launched from the
@@ -68,7 +77,9 @@ typedef enum { WS_ENV_CONTROL = 0, WS_ENV_ECONOMY = 1, WS_ENV_LANDSCAPE = 2 } ws
 typedef enum { WS_PATH_PLAIN_FP32 = 0, WS_PATH_BATCHED_FP32 = 1, WS_PATH_BATCHED_BF16 = 2 } ws_path;
 
 /* Fields of ws_fetch / ws_load.  Ring fields are time-major per step t:
- *   OBS     f32 [t][obs_dim][n_slots]   pre-step observation
+ *   OBS     f32 [t][obs_dim][n_slots]   pre-step observation (acrobot:
+ *                                       cos th1, sin th1, cos th2, sin th2,
+ *                                       w1, w2)
  *   ACTION  i32 [t][n_slots]            (landscape: f32 [t][dim][n_slots] step dx)
  *   LOGP    f32 [t][n_slots]            log-probability of the sampled action
  *   REWARD  f32 [t][n_slots]
@@ -81,6 +92,7 @@ typedef enum { WS_PATH_PLAIN_FP32 = 0, WS_PATH_BATCHED_FP32 = 1, WS_PATH_BATCHED
  *                                       of the post-step state (ws_forces)
  * State fields (no step range; t0 and n_steps must be 0):
  *   STATE   control:   f32 s[4][n_envs] (x, v, th, w), i32 t[n_envs]
+ *           acrobot:   f32 s[4][n_envs] (th1, th2, w1, w2), i32 t[n_envs]
  *           economy:   i64 wealth[n_agents], f32 feat[16][n_agents], i32 t[n_envs]
  *           landscape: f32 x[dim][n_envs], f32 eobs[n_envs], i32 t[n_envs]
  *   PARAMS  f32 policy parameters, per layer W[n_in][n_out] row-major then b;

@@ -85,6 +85,7 @@ WS_HD uint32_t bounded(uint32_t w, uint32_t n) { return mul_hi32(w, n); }
 // Context layout: byte offsets into the caller's state and ring buffers.
 // ------------------------------------------------------------------------
 constexpr int kEconF = 16;
+constexpr int kAcroObs = 6;  // acrobot observation: cos/sin of both angles, both velocities
 constexpr int kMaxLayers = 3;
 
 struct PolicyShape {
@@ -122,7 +123,8 @@ struct Layout {
   size_t queue_off;        // economy, fused kernel: work-queue counters (2 x u32)
   int econ_fused;          // economy on the fused persistent kernel
   int land_fused;          // landscape on the fused persistent kernel
-  size_t land_energy_off;  // landscape, fused kernel: its energy image (blocks of 64 Gaussians)
+  size_t land_energy_off;
+  size_t force_img_off;    // landscape, fused kernel with WS_FLAG_FORCE: the force image  // landscape, fused kernel: its energy image (blocks of 64 Gaussians)
   size_t scratch_off;      // plain-path activations
   size_t scratch_h0_off, scratch_h1_off, scratch_out_off;
   size_t scratch_pobs_off, scratch_ph0_off, scratch_ph1_off, scratch_pout_off;

@@ -12,7 +12,8 @@
 // kernels are unchanged and pay nothing when forces are not asked for.
 //
 // This file holds the FP32 kernel (plain and batched-FP32 paths, and the BF16
-// path where the tensor-core kernel does not apply): one thread per (step,
+// path where the tensor-core kernel of ws_land_tc.cu does not apply, i.e.
+// without the fused roll-out kernel's energy image): one thread per (step,
 // env) row, the direct difference form in registers, Gaussians staged through
 // shared memory 64 at a time; each tile's partial sums are added to the running
 // sum once per tile (pairwise-style grouping keeps the FP32 error near 64 + M/64
@@ -98,6 +99,10 @@ void launch_f32(const Dev &d, uint32_t n, cudaStream_t st) {
 
 void launch_forces(const Dev &d, uint32_t n_steps, cudaStream_t st) {
   if (n_steps == 0) return;
+  if (d.fimg) {  // BF16 path with the fused kernel's energy image: tensor cores
+    launch_force_tc(d, d.limg, d.fimg, n_steps, st);
+    return;
+  }
   if (d.dim <= 8)
     launch_f32<8>(d, n_steps, st);
   else if (d.dim <= 16)

@@ -38,6 +38,8 @@ struct Dev {
   int tc_mlp;
   const uint8_t *pk[2][3];  // [agent, planner][layer]
   const uint8_t *eimg;      // landscape: packed hi/lo centre image + table (BF16 energy)
+  const uint8_t *limg;      // landscape, fused kernel: its energy image (blocks of 64 Gaussians)
+  const uint8_t *fimg;      // landscape, fused kernel with WS_FLAG_FORCE: the force image
   int mlp3;                 // economy: whole-MLP tensor-core kernel (images in pk[pid][0])
   // economy on the fused persistent kernel: work items {first agent slot, rows,
   // first env, envs} and the work-queue counters {next item, CTAs finished}
@@ -129,6 +131,12 @@ size_t land_tc_policy_bytes();
 size_t land_tc_energy_bytes(int M);
 void launch_land_tc_pack(const Dev &d, void *policy_img, void *energy_img, cudaStream_t st);
 void land_tc_init();
+// Force of recorded transitions on the tensor cores over the fused kernel's
+// energy image and a force image packed beside it (ws_land_tc.cu).
+size_t force_tc_bytes(int M);
+void launch_force_tc_pack(const Dev &d, const void *energy_img, void *force_img, cudaStream_t st);
+cudaError_t launch_force_tc(const Dev &d, const void *energy_img, const void *force_img,
+                            uint32_t n_steps, cudaStream_t st);
 cudaError_t launch_land_tc(const Dev &d, const void *policy_img, const void *energy_img,
                            uint32_t n_steps, int tile_ctas, cudaStream_t st);
 

@@ -825,6 +825,332 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// =====================================================================
+// Force of recorded transitions on the tensor cores (ws_forces, BF16 path).
+// F(y) = -grad E(y) = sum_m s_m P_m (y - c_m) / w_m^2 with P_m = |a_m| e_m and
+// s_m the sign of a_m:
+//   F_j = y_j * sum_m P_m f_m  -  sum_m P_m f_m c_mj,   f_m = s_m / w_m^2.
+// Per 128-row tile of (step, env) rows: each 64-Gaussian block's whole
+// exponents log2 P_m come from the energy image exactly as in the roll-out
+// sweep (one MMA, K = 80, into one of four TMEM accumulators); the epilogue
+// turns them into P = 2^z (one ex2 per pair) and writes P as BF16 hi + lo into
+// a shared-memory A operand [128 rows][64 Gaussians]; a second MMA multiplies
+// it with the block's force image [32 columns][64 Gaussians] = (f c_m, f, 0...)
+// (hi + lo; three products hi.hi + lo.hi + hi.lo) into one FP32 accumulator of
+// 32 columns per row.  The sign and 1 / w^2 ride in the force image, so the
+// epilogue is the exponential and the split alone.
+constexpr int kFN = 32;                          // force columns: D coordinates, the sum, zeros
+constexpr int kFImgBytes = kFN * kBlk * 2;       // one plane of a block's force image
+constexpr int kFBlkBytes = 2 * kFImgBytes;       // hi plane | lo plane
+constexpr int kFS = 4;                           // shared-memory stages (energy + force block)
+constexpr int kFStage = kBlkBytes + kFBlkBytes;
+constexpr int kFZ = 4;                           // TMEM exponent accumulators
+constexpr int kFP = 3;                           // P operand buffers
+constexpr int kPPlane = kRows * kBlk * 2;        // one plane of P [128][64]
+constexpr uint32_t TM_F = kFZ * kBlk;            // TMEM columns of the force accumulator
+constexpr int FOFF_AE = 0;
+constexpr int FOFF_ST = FOFF_AE + kRows * kKE * 2;
+constexpr int FOFF_P = FOFF_ST + kFS * kFStage;
+constexpr int FOFF_BAR = FOFF_P + kFP * 2 * kPPlane;
+constexpr int F_NBAR = 1 + 2 * kFS + 2 * kFZ + 2 * kFP + 2;  // ae, b, sf, z, zf, p, pf, f, drain
+constexpr int FOFF_CMD = FOFF_BAR + F_NBAR * 8;
+constexpr int FOFF_TM = FOFF_CMD + 16;
+constexpr int FSMEM = FOFF_TM + 16 + 1024;
+static_assert(FSMEM <= 232448, "force kernel shared memory");
+static_assert(FOFF_ST % 16 == 0 && FOFF_P % 16 == 0 && FOFF_BAR % 8 == 0, "alignment");
+static_assert(TM_F + kFN <= 512, "force accumulator");
+
+inline size_t force_img_bytes(int M) { return (size_t)(land_slots(M) / kBlk) * kFBlkBytes; }
+
+// Block b's force image: planes hi and lo of [32 n][64 k] (K-major, no swizzle),
+// n < D: f_m c_mn, n = D: f_m, else 0; padding slots all 0.
+__global__ void k_force_tc_pack(const float *__restrict__ c, const float *__restrict__ w,
+                                const float *__restrict__ a, int D, int slots,
+                                const int32_t *__restrict__ order, uint8_t *__restrict__ img) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  for (int i = tid; i < slots * kFN; i += stride) {
+    const int sl = i / kFN, n = i % kFN, m = order[sl];
+    float v = 0.f;
+    if (m >= 0 && n <= D) {
+      const float f = (a[m] >= 0.f ? 1.0f : -1.0f) / (w[m] * w[m]);
+      v = n < D ? f * c[(size_t)m * D + n] : f;
+    }
+    uint8_t *blk = img + (size_t)(sl / kBlk) * kFBlkBytes;
+    const int off = ns_off(n, sl % kBlk, kBlk);
+    *(uint16_t *)(blk + off) = bf16_bits(v);
+    *(uint16_t *)(blk + kFImgBytes + off) = bf16_bits(v - bf16_val(v));
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_force_tc(Dev d, const uint8_t *__restrict__ eimg, const uint8_t *__restrict__ eblocks,
+               const uint8_t *__restrict__ fblocks, uint32_t n) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = tc::smem_u32(smem_raw);
+  uint8_t *sm = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+  const uint32_t sb = tc::smem_u32(sm);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  uint64_t *bars = (uint64_t *)(sm + FOFF_BAR);
+  uint64_t *bar_ae = bars, *bar_b = bar_ae + 1, *bar_sf = bar_b + kFS, *bar_z = bar_sf + kFS;
+  uint64_t *bar_zf = bar_z + kFZ, *bar_p = bar_zf + kFZ, *bar_pf = bar_p + kFP;
+  uint64_t *bar_f = bar_pf + kFP, *bar_drain = bar_f + 1;
+  volatile uint32_t *cmd = (volatile uint32_t *)(sm + FOFF_CMD);
+  uint32_t *tm_holder = (uint32_t *)(sm + FOFF_TM);
+  if (tid == 0) {
+    tc::mbar_init(bar_ae, kRows);  // half 0 writes the operand rows
+    for (int i = 0; i < kFS; ++i) {
+      tc::mbar_init(bar_b + i, 1);
+      tc::mbar_init(bar_sf + i, 1);
+    }
+    for (int i = 0; i < kFZ; ++i) {
+      tc::mbar_init(bar_z + i, 1);
+      tc::mbar_init(bar_zf + i, kEpi);
+    }
+    for (int i = 0; i < kFP; ++i) {
+      tc::mbar_init(bar_p + i, kEpi);
+      tc::mbar_init(bar_pf + i, 1);
+    }
+    tc::mbar_init(bar_f, 1);
+    tc::mbar_init(bar_drain, 1);
+    cmd[0] = 0u;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tc::tmem_alloc(tm_holder, 512);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tm_holder;
+  const size_t N = d.n_envs, S = d.n_slots, rows = (size_t)n * N;
+  const int n_tiles = (int)((rows + kRows - 1) / kRows);
+  const int nb = ((const int32_t *)eimg)[0];  // blocks per tile (all Gaussians)
+  int my_tiles = 0;
+  for (int t = (int)blockIdx.x; t < n_tiles; t += (int)gridDim.x) ++my_tiles;
+  const uint32_t total = (uint32_t)my_tiles * (uint32_t)nb;
+  bool fail = false;
+
+  if (tid >= kEpi) {
+    // ===================== producer warps =====================
+    // Block g (counted over this CTA's tiles) sits in stage g % kFS, its
+    // exponents in TMEM accumulator g % kFZ, its P in buffer g % kFP.  The MMA
+    // warp issues the exponent MMA of block g, then the force MMA of block g - 1,
+    // so the tensor core works on g while the epilogue exponentiates g - 1.
+    const int lane = tid & 31;
+    if (warp == kEpi / 32) {
+      if (lane == 0) {
+        uint32_t gl = 0;
+        for (; gl < total && !fail; ++gl) {
+          const uint32_t st = gl % kFS;
+          if (gl >= (uint32_t)kFS &&
+              !tc::mbar_wait(bar_sf + st, ((gl - kFS) / kFS) & 1u, kWaitNs)) { fail = true; break; }
+          const uint32_t b = gl % (uint32_t)nb;
+          mbar_expect_tx(bar_b + st, kFStage);
+          bulk_g2s(sb + FOFF_ST + st * kFStage, eblocks + (size_t)b * kBlkBytes, kBlkBytes, bar_b + st);
+          bulk_g2s(sb + FOFF_ST + st * kFStage + kBlkBytes, fblocks + (size_t)b * kFBlkBytes,
+                   kFBlkBytes, bar_b + st);
+        }
+        cmd[0] = gl;
+      }
+      __syncwarp();
+      bar_sync_n(kBarProd, 64);
+    } else {
+      uint32_t g = 0;
+      if (lane == 0) {
+        constexpr uint32_t id_e = tc::idesc_bf16_f32(128, kBlk), id_f = tc::idesc_bf16_f32(128, kFN);
+        // force MMA of block q: three products of P (hi, lo) and the image (hi, lo)
+        auto force_mma = [&](uint32_t q, bool first) -> bool {
+          const uint32_t pb = q % kFP, st = q % kFS;
+          if (!tc::mbar_wait(bar_p + pb, (q / kFP) & 1u, kWaitNs)) return false;
+          tc::fence_after_sync();
+          const uint32_t pa = sb + FOFF_P + pb * 2u * kPPlane;
+          const uint32_t fb = sb + FOFF_ST + st * kFStage + kBlkBytes;
+#pragma unroll
+          for (int prod = 0; prod < 3; ++prod) {
+            const uint32_t a0 = pa + (prod == 1 ? (uint32_t)kPPlane : 0u);
+            const uint32_t b0 = fb + (prod == 2 ? (uint32_t)kFImgBytes : 0u);
+#pragma unroll
+            for (int s = 0; s < kBlk / 16; ++s) {
+              const uint64_t da = tc::smem_desc(a0 + (uint32_t)s * 256u, 128, kBlk * 16, tc::kSwizzleNone);
+              const uint64_t db = tc::smem_desc(b0 + (uint32_t)s * 256u, 128, kBlk * 16, tc::kSwizzleNone);
+              tc::mma_bf16(tbase + TM_F, da, db, id_f, !(first && prod == 0 && s == 0));
+            }
+          }
+          tc::mma_commit(bar_pf + pb);
+          tc::mma_commit(bar_sf + st);
+          return true;
+        };
+        uint32_t pa = 0;
+        for (int t = 0; t < my_tiles && !fail; ++t) {
+          if (!tc::mbar_wait(bar_ae, pa, kWaitNs)) { fail = true; break; }
+          pa ^= 1u;
+          for (int i = 0; i < nb; ++i, ++g) {
+            const uint32_t st = g % kFS, z = g % kFZ;
+            if (!tc::mbar_wait(bar_b + st, (g / kFS) & 1u, kWaitNs)) { fail = true; break; }
+            if (g >= (uint32_t)kFZ &&
+                !tc::mbar_wait(bar_zf + z, ((g - kFZ) / kFZ) & 1u, kWaitNs)) { fail = true; break; }
+            tc::fence_after_sync();
+#pragma unroll
+            for (int s = 0; s < kKE / 16; ++s) {
+              const uint64_t da = tc::smem_desc(sb + FOFF_AE + (uint32_t)s * 256u, 128, kKE * 16,
+                                                tc::kSwizzleNone);
+              const uint64_t db = tc::smem_desc(sb + FOFF_ST + st * kFStage + (uint32_t)s * 256u, 128,
+                                                kKE * 16, tc::kSwizzleNone);
+              tc::mma_bf16(tbase + z * kBlk, da, db, id_e, s != 0);
+            }
+            tc::mma_commit(bar_z + z);
+            if (i > 0 && !force_mma(g - 1, i == 1)) { fail = true; break; }
+          }
+          if (fail) break;
+          if (!force_mma(g - 1, nb == 1)) { fail = true; break; }
+          tc::mma_commit(bar_f);
+        }
+      }
+      __syncwarp();
+      bar_sync_n(kBarProd, 64);
+      if (lane == 0) {
+        // copies issued ahead of a wait that ran out land before shared memory goes away
+        if (fail) {
+          const uint32_t gl = cmd[0];
+          for (uint32_t q = g; q < gl; ++q) tc::mbar_wait(bar_b + q % kFS, (q / kFS) & 1u, kWaitNs);
+        }
+        tc::mma_commit(bar_drain);
+        tc::mbar_wait(bar_drain, 0, kWaitNs);
+      }
+    }
+    if (fail && (tid & 31) == 0) {
+      atomicExch(d.err, 1u);
+      atomicExch(d.err + 1, 510u);
+    }
+  } else {
+    // ===================== epilogue =====================
+    // Row r of a tile: thread r (half 0) holds y, writes the operand row and the
+    // force; threads r and r + 128 exponentiate columns [32 h, 32 h + 32) of
+    // every block.
+    const int r = tid & 127, h = tid >> 7;
+    const uint32_t lane_sel = (uint32_t)((warp & 3) * 32) << 16;
+    const uint32_t ae_row = sb + FOFF_AE + (uint32_t)(r >> 3) * (kKE * 16) + (uint32_t)(r & 7) * 16u;
+    auto kofs = [](int k) -> uint32_t { return (uint32_t)((k >> 3) * 128 + (k & 7) * 2); };
+    const uint64_t k_end = d.k[0];
+    uint32_t g = 0, pf = 0;
+    for (int tile = (int)blockIdx.x; tile < n_tiles && !fail; tile += (int)gridDim.x) {
+      const size_t q = (size_t)tile * kRows + (size_t)r;
+      const bool valid = q < rows;
+      const uint32_t i = valid ? (uint32_t)(q / N) : 0u, e = valid ? (uint32_t)(q % N) : 0u;
+      const size_t rowR = (size_t)((k_end - n + i) % d.ring_steps);
+      float y[D];
+      if (h == 0) {
+        const float *obs = d.r_obs + rowR * D * S + e;
+        const float *act = (const float *)d.r_act + rowR * D * S + e;
+        float yy = 0.f;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          y[j] = valid ? obs[(size_t)j * S] + act[(size_t)j * S] : 0.f;
+          yy = fmaf(y[j], y[j], yy);
+        }
+        // [y_hi | y_hi | y_lo | 1, 1 | yy_hi, yy_hi, yy_lo | 0...]
+#pragma unroll
+        for (int q4 = 0; q4 < D / 4; ++q4) {
+          const float a0 = y[4 * q4], a1 = y[4 * q4 + 1], a2 = y[4 * q4 + 2], a3 = y[4 * q4 + 3];
+          const uint32_t h01 = tc::pack_bf16x2(a0, a1), h23 = tc::pack_bf16x2(a2, a3);
+          const uint32_t l01 = tc::pack_bf16x2(a0 - tc::bf16_lo(h01), a1 - tc::bf16_hi(h01));
+          const uint32_t l23 = tc::pack_bf16x2(a2 - tc::bf16_lo(h23), a3 - tc::bf16_hi(h23));
+          const int j = 4 * q4;
+          asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(ae_row + kofs(j)), "r"(h01), "r"(h23) : "memory");
+          asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(ae_row + kofs(D + j)), "r"(h01), "r"(h23) : "memory");
+          asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(ae_row + kofs(2 * D + j)), "r"(l01), "r"(l23) : "memory");
+        }
+        const uint32_t hv = tc::pack_bf16x2(yy, 0.f) & 0xFFFFu;
+        const uint32_t lv = tc::pack_bf16x2(yy - __uint_as_float(hv << 16), 0.f) & 0xFFFFu;
+#pragma unroll
+        for (int c = 3 * D / 8; c < kKE / 8; ++c) {
+          if (c == 3 * D / 8)
+            tc::sts128(ae_row + (uint32_t)c * 128u, tc::pack_bf16x2(1.f, 1.f), hv | (hv << 16), lv, 0u);
+          else
+            tc::sts128(ae_row + (uint32_t)c * 128u, 0u, 0u, 0u, 0u);
+        }
+        tc::fence_async_smem();
+        mbar_arrive(bar_ae);
+      }
+      // ---- the blocks: P = 2^z as BF16 hi + lo into the A operand of the force MMA
+      const uint32_t p_row = (uint32_t)(r >> 3) * (kBlk * 16) + (uint32_t)(r & 7) * 16u;
+      for (int b = 0; b < nb; ++b, ++g) {
+        const uint32_t z = g % kFZ, pb = g % kFP;
+        if (!tc::mbar_wait(bar_z + z, (g / kFZ) & 1u, kWaitNs)) { fail = true; break; }
+        tc::fence_after_sync();
+        uint32_t v[32];
+        tc::tmem_ld32(tbase + lane_sel + z * kBlk + (uint32_t)(32 * h), v);
+        tc::tmem_wait_ld();
+        tc::fence_before_sync();
+        mbar_arrive(bar_zf + z);
+        if (g >= (uint32_t)kFP &&
+            !tc::mbar_wait(bar_pf + pb, ((g - kFP) / kFP) & 1u, kWaitNs)) { fail = true; break; }
+        const uint32_t pbase = sb + FOFF_P + pb * 2u * kPPlane + p_row;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          uint32_t hi[4], lo[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float p0 = ex2_fast(__uint_as_float(v[8 * c + 2 * u]));
+            const float p1 = ex2_fast(__uint_as_float(v[8 * c + 2 * u + 1]));
+            hi[u] = tc::pack_bf16x2(p0, p1);
+            lo[u] = tc::pack_bf16x2(p0 - tc::bf16_lo(hi[u]), p1 - tc::bf16_hi(hi[u]));
+          }
+          const uint32_t off = (uint32_t)((4 * h + c) * 128);
+          tc::sts128(pbase + off, hi[0], hi[1], hi[2], hi[3]);
+          tc::sts128(pbase + kPPlane + off, lo[0], lo[1], lo[2], lo[3]);
+        }
+        tc::fence_async_smem();
+        mbar_arrive(bar_p + pb);
+      }
+      if (fail) break;
+      // ---- the tile's force: F_j = y_j * acc[D] - acc[j]
+      if (h == 0) {
+        if (!tc::mbar_wait(bar_f, pf, kWaitNs)) { fail = true; break; }
+        tc::fence_after_sync();
+        uint32_t acc[32];
+        tc::tmem_ld32(tbase + lane_sel + TM_F, acc);
+        tc::tmem_wait_ld();
+        tc::fence_before_sync();
+        if (valid) {
+          const float sp = __uint_as_float(acc[D]);
+          float *out = d.r_force + rowR * D * S + e;
+#pragma unroll
+          for (int j = 0; j < D; ++j) out[(size_t)j * S] = fmaf(y[j], sp, -__uint_as_float(acc[j]));
+        }
+      }
+      pf ^= 1u;
+    }
+    if (fail && tid == 0) {
+      atomicExch(d.err, 1u);
+      atomicExch(d.err + 1, 511u);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tbase, 512);
+  }
+}
+
+template <int D>
+cudaError_t launch_force_d(const Dev &d, const uint8_t *eimg, const uint8_t *fimg, uint32_t n,
+                           cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_force_tc<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, FSMEM);
+    attr = true;
+  }
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t rows = (size_t)n * d.n_envs;
+  const int n_tiles = (int)((rows + kRows - 1) / kRows);
+  const int grid = n_tiles < sms ? n_tiles : sms;
+  k_force_tc<D><<<grid, kThreads, FSMEM, st>>>(d, eimg, eimg + land_blocks_off((int)d.n_gauss), fimg, n);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 bool land_tc_supported(int D, int M, const PolicyShape &p) {
@@ -834,6 +1160,25 @@ bool land_tc_supported(int D, int M, const PolicyShape &p) {
 size_t land_tc_policy_bytes() { return (size_t)POLICY; }
 size_t land_tc_energy_bytes(int M) {
   return land_blocks_off(M) + (size_t)(land_slots(M) / kBlk) * kBlkBytes;
+}
+size_t force_tc_bytes(int M) { return force_img_bytes(M); }
+
+// Needs the energy image packed first (its slot order).
+void launch_force_tc_pack(const Dev &d, const void *energy_img, void *force_img, cudaStream_t st) {
+  const int M = (int)d.n_gauss, slots = land_slots(M);
+  const int32_t *order = (const int32_t *)((const uint8_t *)energy_img + land_order_off());
+  k_force_tc_pack<<<128, 256, 0, st>>>(d.centres, d.widths, d.amps, (int)d.dim, slots, order,
+                                       (uint8_t *)force_img);
+}
+
+cudaError_t launch_force_tc(const Dev &d, const void *energy_img, const void *force_img,
+                            uint32_t n_steps, cudaStream_t st) {
+  const uint8_t *e = (const uint8_t *)energy_img, *f = (const uint8_t *)force_img;
+  if (n_steps == 0) return cudaSuccess;
+  if (d.dim == 8) return launch_force_d<8>(d, e, f, n_steps, st);
+  if (d.dim == 16) return launch_force_d<16>(d, e, f, n_steps, st);
+  if (d.dim == 24) return launch_force_d<24>(d, e, f, n_steps, st);
+  return cudaErrorInvalidValue;
 }
 
 void launch_land_tc_pack(const Dev &d, void *policy_img, void *energy_img, cudaStream_t st) {

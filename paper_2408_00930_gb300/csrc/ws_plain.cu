@@ -82,6 +82,15 @@ __device__ void control_reset_env(const Dev &d, uint32_t k, uint32_t e) {
   d.s[3 * d.n_envs + e] = uniform(r.w, -0.05f, 0.05f);
 }
 
+// Acrobot: (th1, th2, w1, w2) from the four words of RESET(k, env), U(-0.1, 0.1).
+__device__ void acrobot_reset_env(const Dev &d, uint32_t k, uint32_t e) {
+  const uint4 r = draw(d.seed, k, e, 0, kTagReset, 0);
+  d.s[0 * d.n_envs + e] = uniform(r.x, -0.1f, 0.1f);
+  d.s[1 * d.n_envs + e] = uniform(r.y, -0.1f, 0.1f);
+  d.s[2 * d.n_envs + e] = uniform(r.z, -0.1f, 0.1f);
+  d.s[3 * d.n_envs + e] = uniform(r.w, -0.1f, 0.1f);
+}
+
 // Economy agent redraw: wealth 1e4 + (64-bit word) mod 990001, features N(0,1).
 __device__ void econ_reset_agent(const Dev &d, uint32_t k, uint32_t env, uint32_t agent,
                                  uint32_t slot) {
@@ -112,6 +121,11 @@ __global__ void k_reset(Dev d) {
   if (d.env == WS_ENV_CONTROL) {
     if (i < d.n_envs) {
       control_reset_env(d, kStepInit, i);
+      d.t[i] = 0;
+    }
+  } else if (d.env == WS_ENV_ACROBOT) {
+    if (i < d.n_envs) {
+      acrobot_reset_env(d, kStepInit, i);
       d.t[i] = 0;
     }
   } else if (d.env == WS_ENV_ECONOMY) {
@@ -343,6 +357,99 @@ __global__ void k_control_step(Dev d, uint32_t off) {
     d.s[d.n_envs + e] = v2;
     d.s[2 * d.n_envs + e] = th2;
     d.s[3 * d.n_envs + e] = w2;
+    d.t[e] = t2;
+  }
+}
+
+// ----------------------------------------------------- acrobot (S1, S4/S5)
+// Two-link acrobot of Sutton & Barto (paper App. C, classic control), book
+// dynamics: m1 = m2 = l1 = I1 = I2 = 1, lc1 = lc2 = 0.5, g = 9.8, angles from
+// hanging down, torque tau on the second joint.
+__device__ __forceinline__ void acro_accel(float th1, float th2, float w1, float w2, float tau,
+                                           float &acc1, float &acc2) {
+  const float m1 = 1.f, m2 = 1.f, l1 = 1.f, lc1 = 0.5f, lc2 = 0.5f, I1 = 1.f, I2 = 1.f, g = 9.8f;
+  float s2, c2;
+  sincosf(th2, &s2, &c2);
+  const float d1 = m1 * lc1 * lc1 + m2 * (l1 * l1 + lc2 * lc2 + 2.f * l1 * lc2 * c2) + I1 + I2;
+  const float d2 = m2 * (lc2 * lc2 + l1 * lc2 * c2) + I2;
+  const float phi2 = m2 * lc2 * g * sinf(th1 + th2);
+  const float phi1 = -m2 * l1 * lc2 * w2 * w2 * s2 - 2.f * m2 * l1 * lc2 * w2 * w1 * s2 +
+                     (m1 * lc1 + m2 * l1) * g * sinf(th1) + phi2;
+  acc2 = (tau + d2 / d1 * phi1 - m2 * l1 * lc2 * w1 * w1 * s2 - phi2) /
+         (m2 * lc2 * lc2 + I2 - d2 * d2 / d1);
+  acc1 = -(d2 * acc2 + phi1) / d1;
+}
+
+// One classic RK4 step of dt with tau held; angles wrapped into [-pi, pi],
+// velocities clipped to |w1| <= 4 pi, |w2| <= 9 pi.
+__device__ __forceinline__ void acro_step(float (&s)[4], float tau, float dt) {
+  float k[4][4];
+  float y[4] = {s[0], s[1], s[2], s[3]};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    k[q][0] = y[2];
+    k[q][1] = y[3];
+    acro_accel(y[0], y[1], y[2], y[3], tau, k[q][2], k[q][3]);
+    if (q < 3) {
+      const float h = q < 2 ? 0.5f * dt : dt;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) y[i] = s[i] + h * k[q][i];
+    }
+  }
+  const float kPi = 3.14159265358979f, k2Pi = 6.28318530717959f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    s[i] = s[i] + dt / 6.f * (k[0][i] + 2.f * k[1][i] + 2.f * k[2][i] + k[3][i]);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    for (int it = 0; it < 64 && s[i] > kPi; ++it) s[i] -= k2Pi;
+    for (int it = 0; it < 64 && s[i] < -kPi; ++it) s[i] += k2Pi;
+  }
+  s[2] = fminf(fmaxf(s[2], -4.f * kPi), 4.f * kPi);
+  s[3] = fminf(fmaxf(s[3], -9.f * kPi), 9.f * kPi);
+}
+
+// Observation (cos th1, sin th1, cos th2, sin th2, w1, w2): into the policy's
+// input [6][N] and the ring.
+__global__ void k_acrobot_observe(Dev d, uint32_t off) {
+  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.n_envs) return;
+  const size_t N = d.n_envs;
+  const float th1 = d.s[e], th2 = d.s[N + e];
+  float o[kAcroObs];
+  sincosf(th1, &o[1], &o[0]);
+  sincosf(th2, &o[3], &o[2]);
+  o[4] = d.s[2 * N + e];
+  o[5] = d.s[3 * N + e];
+  const uint32_t row = ring_row(d, step_k(d, off));
+  float *dst = d.r_obs + (size_t)row * kAcroObs * d.n_slots + e;
+#pragma unroll
+  for (int j = 0; j < kAcroObs; ++j) {
+    d.pobs[(size_t)j * N + e] = o[j];
+    dst[(size_t)j * d.n_slots] = o[j];
+  }
+}
+
+__global__ void k_acrobot_step(Dev d, uint32_t off) {
+  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.n_envs) return;
+  const uint64_t k = step_k(d, off);
+  const uint32_t row = ring_row(d, k);
+  const size_t o = (size_t)row * d.n_slots + e, N = d.n_envs;
+  const int a = ((const int32_t *)d.r_act)[o];
+  float s[4] = {d.s[e], d.s[N + e], d.s[2 * N + e], d.s[3 * N + e]};
+  acro_step(s, (float)(a - 1), 0.2f);
+  const bool term = -cosf(s[0]) - cosf(s[0] + s[1]) > 1.0f;
+  const int t2 = d.t[e] + 1;
+  const bool done = term || t2 >= (int)d.episode_limit;
+  d.r_rew[o] = term ? 0.0f : -1.0f;
+  d.r_done[o] = (uint8_t)done;
+  if (done) {
+    acrobot_reset_env(d, (uint32_t)k, e);
+    d.t[e] = 0;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) d.s[i * N + e] = s[i];
     d.t[e] = t2;
   }
 }
@@ -809,6 +916,11 @@ void launch_plain_step(const Dev &d, uint32_t off, cudaStream_t st, const Branch
     policy(d, d.s, 1, d.n_envs, d.params, d.pol, 0, d.h0, d.h1, d.out, (int)d.n_envs, st);
     k_sample_cat<<<blocks(d.n_envs, T), T, 0, st>>>(d, off, d.out, 2, 0, d.n_envs, 0);
     k_control_step<<<blocks(d.n_envs, T), T, 0, st>>>(d, off);
+  } else if (d.env == WS_ENV_ACROBOT) {
+    k_acrobot_observe<<<blocks(d.n_envs, T), T, 0, st>>>(d, off);
+    policy(d, d.pobs, 1, d.n_envs, d.params, d.pol, 0, d.h0, d.h1, d.out, (int)d.n_envs, st);
+    k_sample_cat<<<blocks(d.n_envs, T), T, 0, st>>>(d, off, d.out, 3, 0, d.n_envs, 0);
+    k_acrobot_step<<<blocks(d.n_envs, T), T, 0, st>>>(d, off);
   } else if (d.env == WS_ENV_ECONOMY) {
     k_econ_observe<<<d.n_envs, kEconThreads, 0, st>>>(d, off);
     // the planner's policy and draw are independent of the agents': side branch

@@ -57,7 +57,7 @@ ws_status cuda_check(ws_ctx *c, cudaError_t e, const char *where) {
 
 ws_status validate(const ws_config *cfg) {
   if (!cfg || cfg->struct_size != sizeof(ws_config)) return WS_ERR_INVALID;
-  if (cfg->env < WS_ENV_CONTROL || cfg->env > WS_ENV_LANDSCAPE) return WS_ERR_INVALID;
+  if (cfg->env < WS_ENV_CONTROL || cfg->env > WS_ENV_ACROBOT) return WS_ERR_INVALID;
   if (cfg->path < WS_PATH_PLAIN_FP32 || cfg->path > WS_PATH_BATCHED_BF16) return WS_ERR_INVALID;
   if (cfg->n_envs < 1 || cfg->n_envs > (1u << 26)) return WS_ERR_INVALID;
   if (cfg->ring_steps < 1 || cfg->episode_limit < 1) return WS_ERR_INVALID;
@@ -203,6 +203,14 @@ Layout make_layout(const ws_config *cfg, const std::vector<int32_t> &agents) {
     L.n_out = 2;
     L.pol = PolicyShape{{4, (int)cfg->hidden0, (int)cfg->hidden1, 2}};
     L.pol_planner = PolicyShape{{0, 0, 0, 0}};
+  } else if (cfg->env == WS_ENV_ACROBOT) {
+    L.n_agent_slots = cfg->n_envs;
+    L.n_slots = cfg->n_envs;
+    L.obs_dim = kAcroObs;
+    L.act_dim = 1;
+    L.n_out = 3;
+    L.pol = PolicyShape{{kAcroObs, (int)cfg->hidden0, (int)cfg->hidden1, 3}};
+    L.pol_planner = PolicyShape{{0, 0, 0, 0}};
   } else {
     L.n_agent_slots = cfg->n_envs;
     L.n_slots = cfg->n_envs;
@@ -241,9 +249,11 @@ Layout make_layout(const ws_config *cfg, const std::vector<int32_t> &agents) {
     L.env_derived_bytes += up(energy_tc_bytes((int)D, (int)M));
   L.land_energy_off = L.env_derived_off + L.env_derived_bytes;
   if (L.land_fused) L.env_derived_bytes += up(land_tc_energy_bytes((int)M));
+  L.force_img_off = L.env_derived_off + L.env_derived_bytes;
+  if (L.land_fused && (cfg->flags & WS_FLAG_FORCE)) L.env_derived_bytes += up(force_tc_bytes((int)M));
   o += L.env_derived_bytes;
   L.state_off = o;
-  if (cfg->env == WS_ENV_CONTROL) o += up(4 * N * 4);
+  if (cfg->env == WS_ENV_CONTROL || cfg->env == WS_ENV_ACROBOT) o += up(4 * N * 4);
   if (cfg->env == WS_ENV_ECONOMY) o += up(Sa * 8) + up(kEconF * Sa * 4);
   if (cfg->env == WS_ENV_LANDSCAPE) o += up(D * N * 4) + up(N * 4) + up(N);
   L.t_off = o; o += up(N * 4);
@@ -272,6 +282,9 @@ Layout make_layout(const ws_config *cfg, const std::vector<int32_t> &agents) {
     }
     if (cfg->env == WS_ENV_LANDSCAPE) {
       L.scratch_income_off = o; o += up((size_t)kEnergyChunks * 2 * N * 4);  // energy partials
+    }
+    if (cfg->env == WS_ENV_ACROBOT) {
+      L.scratch_pobs_off = o; o += up((size_t)kAcroObs * N * 4);  // the policy's input
     }
   }
   L.state_bytes = o;
@@ -334,6 +347,9 @@ void make_dev(ws_ctx *c) {
     d.needs_energy = (uint8_t *)(S + L.state_off + up(D * N * 4) + up(N * 4));
   } else if (cfg.env == WS_ENV_CONTROL) {
     d.s = (float *)(S + L.state_off);
+  } else if (cfg.env == WS_ENV_ACROBOT) {
+    d.s = (float *)(S + L.state_off);
+    d.pobs = (float *)(S + L.scratch_pobs_off);
   } else {
     d.wealth = (int64_t *)(S + L.state_off);
     d.feat = (float *)(S + L.state_off + up(Sa * 8));
@@ -352,6 +368,8 @@ void make_dev(ws_ctx *c) {
     }
   } else if (L.land_fused) {
     d.dbg_logits = (cfg.flags & WS_FLAG_DEBUG_LOGITS) ? 1 : 0;
+    d.limg = (const uint8_t *)(S + L.land_energy_off);
+    if (cfg.flags & WS_FLAG_FORCE) d.fimg = (const uint8_t *)(S + L.force_img_off);
   } else if (use_mlp3(&cfg, L.pol, L.pol_planner)) {
     d.tc_mlp = 1;
     d.mlp3 = 1;
@@ -547,7 +565,7 @@ std::vector<Piece> state_pieces(ws_ctx *c, ws_field f) {
   char *S = c->state;
   std::vector<Piece> v;
   if (f == WS_F_STATE) {
-    if (L.env == WS_ENV_CONTROL) {
+    if (L.env == WS_ENV_CONTROL || L.env == WS_ENV_ACROBOT) {
       v.push_back({S + L.state_off, 4 * N * 4});
     } else if (L.env == WS_ENV_ECONOMY) {
       v.push_back({S + L.state_off, Sa * 8});
@@ -585,6 +603,7 @@ ws_status after_params_changed(ws_ctx *c) {
     launch_econ_tc_pack(c->d.params, c->d.params_planner, c->state + c->L.packed_off, c->stream);
   } else if (c->L.land_fused) {
     launch_land_tc_pack(c->d, c->state + c->L.packed_off, c->state + c->L.land_energy_off, c->stream);
+    if (c->d.fimg) launch_force_tc_pack(c->d, c->d.limg, (void *)c->d.fimg, c->stream);
   } else if (c->d.mlp3) {
     launch_mlp3_tc_pack(c->d.params, c->L.pol, (void *)c->d.pk[0][0], c->stream);
     launch_mlp3_tc_pack(c->d.params_planner, c->L.pol_planner, (void *)c->d.pk[1][0], c->stream);

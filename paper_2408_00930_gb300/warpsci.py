@@ -21,7 +21,7 @@ WS_ERR_TIMEOUT, WS_ERR_STATE, WS_ERR_RANGE, WS_ERR_UNSUPPORTED = 4, 5, 6, 7
 STATUS_NAMES = {0: "WS_OK", 1: "WS_ERR_INVALID", 2: "WS_ERR_NOMEM", 3: "WS_ERR_CUDA",
                 4: "WS_ERR_TIMEOUT", 5: "WS_ERR_STATE", 6: "WS_ERR_RANGE", 7: "WS_ERR_UNSUPPORTED"}
 
-WS_ENV_CONTROL, WS_ENV_ECONOMY, WS_ENV_LANDSCAPE = 0, 1, 2
+WS_ENV_CONTROL, WS_ENV_ECONOMY, WS_ENV_LANDSCAPE, WS_ENV_ACROBOT = 0, 1, 2, 3
 WS_PATH_PLAIN_FP32, WS_PATH_BATCHED_FP32, WS_PATH_BATCHED_BF16 = 0, 1, 2
 (WS_F_OBS, WS_F_ACTION, WS_F_LOGP, WS_F_REWARD, WS_F_DONE, WS_F_RETURN, WS_F_WEALTH, WS_F_ENERGY,
  WS_F_STATE, WS_F_PARAMS, WS_F_ENV_PARAMS, WS_F_LOGITS, WS_F_FORCE) = range(13)
@@ -314,7 +314,8 @@ class Rollout:
 
     # layouts ---------------------------------------------------------------
     def obs_dim(self):
-        return {WS_ENV_CONTROL: 4, WS_ENV_ECONOMY: 16, WS_ENV_LANDSCAPE: self.dim}[self.env]
+        return {WS_ENV_CONTROL: 4, WS_ENV_ECONOMY: 16, WS_ENV_LANDSCAPE: self.dim,
+                WS_ENV_ACROBOT: 6}[self.env]
 
     def _ring_spec(self, field):
         S = self.n_slots

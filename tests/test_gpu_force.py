@@ -11,6 +11,11 @@ from tests.gpu_common import need_gpu
 pytestmark = pytest.mark.gpu
 # FP32 sums over M Gaussians, tile partials added once per 64 Gaussians
 TOL_FORCE_F32 = 2e-5
+# BF16 tensor-core path: the exponents carry the energy sweep's hi+lo error
+# (~5e-3 of a term, as the energy), P and the force image are split hi + lo,
+# and the force is formed as y sum(p) - sum(p c): the error is measured against
+# sum_m |a_m| e_m (|y_j| + |c_mj|) / w_m^2, the size of the terms of that form
+TOL_FORCE_BF16 = 5e-3
 
 
 @pytest.fixture(scope="module")
@@ -18,12 +23,14 @@ def torch():
     return need_gpu()
 
 
-def force_scale(c, w, a, y):
-    """sum_m |a_m| e_m |y_j - c_mj| / w_m^2 per coordinate: the size of the
-    terms the force sums, against which its error is measured."""
+def force_scale(c, w, a, y, split=False):
+    """sum_m |a_m| e_m |y_j - c_mj| / w_m^2 per coordinate (the size of the
+    terms of the direct form), or with split sum_m |a_m| e_m (|y_j| + |c_mj|) /
+    w_m^2 (the terms of y sum(p) - sum(p c))."""
     d = y[None, :] - c
     e = np.exp(-(d * d).sum(1) / (2 * w * w))
-    return ((np.abs(a) * e / (w * w))[:, None] * np.abs(d)).sum(0)
+    size = np.abs(y[None, :]) + np.abs(c) if split else np.abs(d)
+    return ((np.abs(a) * e / (w * w))[:, None] * size).sum(0)
 
 
 def env_params(r, M, D):
@@ -32,14 +39,14 @@ def env_params(r, M, D):
     return c, envp[M * D:M * D + M].astype(np.float64), envp[M * D + M:].astype(np.float64)
 
 
-def check_forces(r, T, M, D, rows, tol):
+def check_forces(r, T, M, D, rows, tol, split=False):
     obs, act, F = (r.fetch(f, 0, T) for f in (W.WS_F_OBS, W.WS_F_ACTION, W.WS_F_FORCE))
     c, w, a = env_params(r, M, D)
     worst = 0.0
     for t, e in rows:
         y = (obs[t][:, e] + act[t][:, e]).astype(np.float32).astype(np.float64)
         ref = -oracle.landscape_grad(c, w, a, y)
-        sc = np.maximum(force_scale(c, w, a, y), 1e-3)
+        sc = np.maximum(force_scale(c, w, a, y, split), 1e-3)
         err = np.abs(F[t][:, e] - ref) / sc
         worst = max(worst, err.max())
         assert err.max() <= tol, (t, e, err.max())
@@ -59,8 +66,33 @@ def test_forces_match_oracle_gradient(torch, path):
     g = np.random.default_rng(0)
     rows = [(t, int(e)) for t in range(T) for e in g.choice(n, 6, replace=False)]
     rows += [(6, 0), (6, n - 1)]          # steps that end an episode: the pre-reset x'
-    check_forces(r, T, M, D, rows, TOL_FORCE_F32)
+    bf16 = path == W.WS_PATH_BATCHED_BF16
+    worst = check_forces(r, T, M, D, rows, TOL_FORCE_BF16 if bf16 else TOL_FORCE_F32, split=bf16)
     r.close()
+    if bf16:
+        assert worst > 1e-7          # the tensor-core kernel ran (not the FP32 one)
+
+
+def test_forces_tc_near_centres_and_all_rows(torch):
+    """BF16 tensor-core force: states placed near Gaussian centres (large,
+    cancelling terms), several 128-row tiles with a ragged tail, D = 8 and 16
+    as well as 24, every row compared."""
+    for D, n, T in ((24, 200, 3), (16, 130, 2), (8, 70, 4)):
+        M = 1000
+        g = np.random.default_rng(D)
+        r = W.Rollout(W.WS_ENV_LANDSCAPE, W.WS_PATH_BATCHED_BF16, n, T, 1000, 256, 256, dim=D,
+                      n_gauss=M, param_seed=7, flags=W.WS_FLAG_FORCE)
+        c, w, a = env_params(r, M, D)
+        x0 = (c[g.integers(0, M, n)] + g.normal(0, 0.3, (n, D))).astype(np.float32)
+        r.load_raw(W.WS_F_STATE, np.concatenate([np.ascontiguousarray(x0.T).view(np.uint8).ravel(),
+                                                 np.zeros(n, np.float32).view(np.uint8),
+                                                 np.zeros(n, np.int32).view(np.uint8)]), k=0)
+        r.rollout(T)
+        r.forces(T)
+        r.sync()
+        rows = [(t, e) for t in range(T) for e in range(n)]
+        check_forces(r, T, M, D, rows, TOL_FORCE_BF16, split=True)
+        r.close()
 
 
 def test_forces_window_ring_wrap_and_small_dims(torch):
