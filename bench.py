@@ -35,7 +35,7 @@ CHUNK = 50
 # DRAM bytes (read + write) per slot-step of the returns scan, from an ncu
 # capture of k_returns on the control workload (summarised under profiles/);
 # the traffic scales with the slot-steps scanned
-RETURNS_NCU_BYTES_PER_SLOT_STEP = None
+RETURNS_NCU_BYTES_PER_SLOT_STEP = 7.1
 
 WORKLOADS = {
     "control_scale": dict(env=0, n_envs=131072, horizon=500, limit=200, h=(256, 256),
@@ -501,17 +501,14 @@ def main():
               "peak_source": f"{peak_src} bf16 sustained" if bf16 else
               f"{peak_src} bf16 sustained / 4 (fp32 SIMT)"}
     tensor["frac"] = tensor["achieved"] / tensor["peak"]
-    if bf16 and wl["env"] == 3:
-        # acrobot BF16: per-step kernels (observe, three tcgen05 layers, sample,
-        # RK4 step) captured in CUDA graphs; no fused kernel
-        roofline = dict(tensor, traffic=None,
-                        kernel="per-step kernels, tcgen05 policy layers, CUDA graphs")
-    elif bf16:
+    if bf16:
         # The fused kernels are bound by the SFU (tanh, exp2): an SM retires 16
         # SFU results per clock (measured 15.2 for tanh.approx in any of f32 /
         # bf16x2 / f16x2 form).  SFU results per agent-step, counted from the
         # kernels' arithmetic:
         #   control    H0 + H1 tanh (+ one exp for the two-way softmax)
+        #   acrobot    H0 + H1 tanh, 3 exp and 1 log (the RK4's sin / cos are
+        #              CUDA's accurate software functions, on the FMA pipe)
         #   economy    agent: H0 + H1 tanh, 20 exp, 1 log; planner: H0 + H1
         #              tanh, 10 exp
         #   landscape  H0 + H1 tanh, M exp2 (one per Gaussian), D exp (sigma),
@@ -525,6 +522,9 @@ def main():
         H = sum(wl["h"])
         if wl["env"] == 0:
             per_step, op, kern = n_slots * (H + 1), "tanh (and exp) on the SFU", "ws_control_tc"
+        elif wl["env"] == 3:
+            per_step, op, kern = n_slots * (H + 4), "tanh, exp, log on the SFU", \
+                "ws_control_tc (acrobot)"
         elif wl["env"] == 1:
             n_pl = wl["n_envs"]
             per_step = (n_slots - n_pl) * (H + 21) + n_pl * (H + 10)
@@ -607,7 +607,7 @@ def main():
     launch = main_res["launch"] or {}
     ch = int(launch.get("chunk_steps", CHUNK))
     lens = [min(CHUNK, wl["horizon"] - c * CHUNK) for c in range(n_chunks)]
-    if bf16 and wl["env"] != 3:
+    if bf16:
         per_roll = sum(-(-n // ch) * 2 for n in lens)
     else:
         per_step = {0: 6, 1: 14, 2: 9, 3: 6}[wl["env"]]

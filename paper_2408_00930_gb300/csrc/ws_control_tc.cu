@@ -1,34 +1,40 @@
 // ws_control_tc.cu -- fused persistent BF16 tensor-core roll-out kernel of the
-// control env: one launch runs a whole chunk of steps for every env, with the
-// env state held in registers and nothing but the transition records leaving
-// the SM (paper Sec. 2 / App. B: roll-out, inference, reset and the in-place
-// store all on the GPU; envs independent, policy referenced from GPU memory).
+// classic-control envs (the cart-pole-like control env and the acrobot, paper
+// App. C): one launch runs a whole chunk of steps for every env, with the env
+// state held in registers and nothing but the transition records leaving the SM
+// (paper Sec. 2 / App. B: roll-out, inference, reset and the in-place store all
+// on the GPU; envs independent, policy referenced from GPU memory).  The two
+// envs differ in the observation (4 state values; the acrobot's cos / sin of
+// both angles and both velocities), the action count (2; 3) and the step
+// (explicit Euler; RK4 of the two-link dynamics).
 //
 // Work split: a CTA holds two groups of 256 threads; each group owns a tile of
 // 128 envs and 256 of the CTA's 512 TMEM columns.  Env row r of a tile is served
 // by two threads ("halves" h = 0, 1; both in warps that may reach TMEM lane r),
 // which split the row's hidden units by 64-unit blocks.  Per step and tile:
-//   layer 1  z1 = s W1 + b1 on the tensor core, K = 16: the operand row
-//            [s_hi, s_lo, s_hi, 1, 1, 0, 0] against [W1_hi; W1_hi; W1_lo; b1_hi;
-//            b1_lo] keeps FP32-level accuracy (missing term s_lo W1_lo ~ 2^-16);
-//            z1 lands in TMEM columns [0, H0)
+//   layer 1  z1 = o W1 + b1 on the tensor core, K = 16 (acrobot 32): the
+//            operand row [o_hi, o_lo, o_hi, 1, 1, 0...] against [W1_hi; W1_hi;
+//            W1_lo; b1_hi; b1_lo] keeps FP32-level accuracy (missing term
+//            o_lo W1_lo ~ 2^-16); z1 lands in TMEM columns [0, H0)
 //   act 1    h1 = tanh(z1) as packed bf16x2, written back into TMEM columns
 //            [128, 128 + H0/2): the A operand of layer 2 stays in tensor memory
 //            (two bf16 per 32-bit column), so it never touches shared memory
 //   layer 2  z2 = h1 W2 + b2 in passes of up to 128 output units into TMEM
-//            columns [0, 128): b2 by one K = 16 MMA of the operand row's constant
-//            columns against [0 x 12, b2_hi, b2_lo, 0, 0], then H0 / 16 MMAs with
-//            A read from tensor memory and W2^T resident in shared memory
+//            columns [0, 128): b2 by one K = 16 MMA of the K-chunk of the operand
+//            row that holds its constant columns against [.., b2_hi, b2_lo, ..],
+//            then H0 / 16 MMAs with A read from tensor memory and W2^T resident
+//            in shared memory
 //   layer 3  logits = tanh(z2) W3 + b3 on the CUDA cores after each pass: each
 //            half reads its block of z2, applies tanh (FP32, SFU) and accumulates
 //            its partial dot products with W3 (FP32, packed f32x2 FMAs, W3 read as
 //            shared-memory broadcasts); half 1 hands its partial to half 0
-//   then     half 0: categorical sample (Philox), Euler step, reward, done,
+//   then     half 0: categorical sample (Philox), env step, reward, done,
 //            auto-reset, the time-major record write and the next operand row.
 // Two threads per row give 16 warps per SM, so that one warp's MUFU/TMEM
 // latency overlaps another's work, and the two groups' tensor and tanh phases
 // interleave.  Tiles go to CTAs round-robin, group 0's turn first, so that
 // every SM receives either floor or ceil of tiles / SMs.
+#include "ws_acrobot.cuh"
 #include "ws_kernels.cuh"
 #include "ws_tc.cuh"
 
@@ -43,7 +49,15 @@ constexpr int kThreads = kGroups * kGroupThreads;
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s, far above any MMA completion time
 constexpr uint32_t kTmemCols = 512;
 
-template <int H0, int H1>
+// The two envs: observation width, actions, layer-1 K.
+struct EnvCart {
+  static constexpr int OBS = 4, NA = 2, K1 = 16;
+};
+struct EnvAcro {
+  static constexpr int OBS = 6, NA = 3, K1 = 32;
+};
+
+template <typename E, int H0, int H1>
 struct CtrlTc {
   static_assert(H0 == 64 || H0 == 128 || H0 == 256, "layer-2 K must be 64, 128 or 256");
   static_assert(H1 == 64 || H1 == 128 || H1 == 256, "layer-3 K (= H1) must be 64, 128 or 256");
@@ -52,10 +66,13 @@ struct CtrlTc {
   static constexpr int NPW = H1 / NP;               // output units per pass (64 or 128)
   static constexpr int KBP = NPW / 64;              // 64-unit blocks per pass (1 or 2)
   static constexpr uint32_t A_COL = 128;            // TMEM column of the layer-2 A operand
+  static constexpr int K1 = E::K1;                  // layer-1 K (operand row length)
+  static constexpr int KC = 3 * E::OBS;             // the operand row's first constant column
   static constexpr int W2_BYTES = KB * H1 * 128;    // B of layer 2, SW128, K-blocks of 64
-  static constexpr int B1_BYTES = H0 * 32;          // B of layer 1, no swizzle, K = 16
+  static constexpr int B1_BYTES = H0 * K1 * 2;      // B of layer 1, no swizzle
   static constexpr int BB_BYTES = H1 * 32;          // B of the b2 MMA, no swizzle, K = 16
-  static constexpr int W3_BYTES = H1 * 8;           // W3 as float4 per unit pair (FP32)
+  static constexpr int W3P = E::NA == 2 ? 16 : 32;  // W3 bytes per unit pair (FP32 float4s)
+  static constexpr int W3_BYTES = H1 / 2 * W3P;
   static constexpr int B3V_BYTES = 16;              // b3
   // packed global image: [W2 | B1 | BB | W3 | b3]
   static constexpr int PK_W2 = 0;
@@ -66,13 +83,13 @@ struct CtrlTc {
   static constexpr int PACKED = PK_B3V + B3V_BYTES;
   // shared memory (from a 1024-aligned base)
   static constexpr int OFF_W2 = 0;
-  static constexpr int OFF_A1 = OFF_W2 + W2_BYTES;  // [group] layer-1 operand, 4 KB each
-  static constexpr int OFF_B1 = OFF_A1 + kGroups * 128 * 32;
+  static constexpr int OFF_A1 = OFF_W2 + W2_BYTES;  // [group] layer-1 operand [128][K1]
+  static constexpr int OFF_B1 = OFF_A1 + kGroups * 128 * K1 * 2;
   static constexpr int OFF_BB = OFF_B1 + B1_BYTES;  // B1, BB, W3, b3 contiguous as packed
   static constexpr int OFF_W3 = OFF_BB + BB_BYTES;
   static constexpr int OFF_B3V = OFF_W3 + W3_BYTES;
-  // [group][row] from half 1 to half 0: two logit partials, the action uniform
-  // and the four reset words (8 words, 32 B)
+  // [group][row] from half 1 to half 0: two logit partials, the action uniform,
+  // the third logit partial (acrobot) and the four reset words (8 words, 32 B)
   static constexpr int OFF_XCH = OFF_B3V + B3V_BYTES;
   static constexpr int OFF_BAR = OFF_XCH + kGroups * 128 * 32;
   static constexpr int N_BAR = 3;  // per group: layer 1, layer-2 pass, error drain
@@ -99,62 +116,66 @@ __device__ __forceinline__ int sw128_off(int n, int k, int rows) {
   const int kb = k >> 6, kk = k & 63;
   return kb * (rows * 128) + n * 128 + (((kk >> 3) ^ (n & 7)) << 4) + (kk & 7) * 2;
 }
-// Byte offset of element (row n, q) in a K = 16 operand without swizzle
-// (8-row core matrices of 16 B rows; K-adjacent core matrices 128 B apart).
-__device__ __forceinline__ int k16_off(int n, int q) {
-  return (n >> 3) * 256 + (q >> 3) * 128 + (n & 7) * 16 + (q & 7) * 2;
+// Byte offset of element (row n, q) in an operand of K elements per row without
+// swizzle (8-row core matrices of 16 B rows; K-adjacent core matrices 128 B apart).
+__device__ __forceinline__ int kns_off(int n, int q, int K) {
+  return (n >> 3) * (K * 16) + (q >> 3) * 128 + (n & 7) * 16 + (q & 7) * 2;
 }
 
 // Pack the FP32 policy into the byte images the kernel copies verbatim.
-template <int H0, int H1>
+template <typename E, int H0, int H1>
 __global__ void k_ctrl_tc_pack(const float *__restrict__ params, uint8_t *__restrict__ packed) {
-  using C = CtrlTc<H0, H1>;
-  const float *W1 = params;        // [4][H0]
-  const float *b1 = W1 + 4 * H0;   // [H0]
-  const float *W2 = b1 + H0;       // [H0][H1]
-  const float *b2 = W2 + H0 * H1;  // [H1]
-  const float *W3 = b2 + H1;       // [H1][2]
-  const float *b3 = W3 + 2 * H1;   // [2]
+  using C = CtrlTc<E, H0, H1>;
+  constexpr int OBS = E::OBS, NA = E::NA;
+  const float *W1 = params;          // [OBS][H0]
+  const float *b1 = W1 + OBS * H0;   // [H0]
+  const float *W2 = b1 + H0;         // [H0][H1]
+  const float *b2 = W2 + H0 * H1;    // [H1]
+  const float *W3 = b2 + H1;         // [H1][NA]
+  const float *b3 = W3 + NA * H1;    // [NA]
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
   // layer 2: B row n (output unit), K = input unit
   for (int i = tid; i < H0 * H1; i += stride) {
     const int n = i / H0, k = i % H0;
     *(uint16_t *)(packed + C::PK_W2 + sw128_off(n, k, H1)) = bf16_bits(W2[(size_t)k * H1 + n]);
   }
-  // layer 3: float4 {W3[2i][0], W3[2i+1][0], W3[2i][1], W3[2i+1][1]} per unit pair i
+  // layer 3 per unit pair i (k = 2i): float4 {W3[k][0], W3[k+1][0], W3[k][1],
+  // W3[k+1][1]}, and for three actions float4 {W3[k][2], W3[k+1][2], 0, 0}
   for (int i = tid; i < H1 / 2; i += stride) {
-    float4 q;
-    q.x = W3[2 * (2 * i) + 0];
-    q.y = W3[2 * (2 * i + 1) + 0];
-    q.z = W3[2 * (2 * i) + 1];
-    q.w = W3[2 * (2 * i + 1) + 1];
-    *(float4 *)(packed + C::PK_W3 + 16 * i) = q;
+    const int k = 2 * i;
+    *(float4 *)(packed + C::PK_W3 + C::W3P * i) =
+        make_float4(W3[k * NA + 0], W3[(k + 1) * NA + 0], W3[k * NA + 1], W3[(k + 1) * NA + 1]);
+    if (NA == 3)
+      *(float4 *)(packed + C::PK_W3 + C::W3P * i + 16) =
+          make_float4(W3[k * NA + 2], W3[(k + 1) * NA + 2], 0.f, 0.f);
   }
-  // layer 1 row n: [W1_hi[0..3][n], W1_hi[0..3][n], W1_lo[0..3][n], b1_hi, b1_lo, 0, 0]
-  for (int i = tid; i < H0 * 16; i += stride) {
-    const int n = i / 16, q = i % 16;
+  // layer 1 row n: [W1_hi[.][n] | W1_hi[.][n] | W1_lo[.][n] | b1_hi, b1_lo | 0...]
+  for (int i = tid; i < H0 * C::K1; i += stride) {
+    const int n = i / C::K1, q = i % C::K1;
     float v = 0.f;
-    if (q < 8) {
-      v = bf16_val(W1[(q & 3) * H0 + n]);
-    } else if (q < 12) {
-      const float w = W1[(q - 8) * H0 + n];
+    if (q < 2 * OBS) {
+      v = bf16_val(W1[(q % OBS) * H0 + n]);
+    } else if (q < 3 * OBS) {
+      const float w = W1[(q - 2 * OBS) * H0 + n];
       v = bf16_val(w - bf16_val(w));
-    } else if (q == 12) {
+    } else if (q == 3 * OBS) {
       v = bf16_val(b1[n]);
-    } else if (q == 13) {
+    } else if (q == 3 * OBS + 1) {
       v = bf16_val(b1[n] - bf16_val(b1[n]));
     }
-    *(uint16_t *)(packed + C::PK_B1 + k16_off(n, q)) = bf16_bits(v);
+    *(uint16_t *)(packed + C::PK_B1 + kns_off(n, q, C::K1)) = bf16_bits(v);
   }
-  // b2 row n: [0 x 12, b2_hi, b2_lo, 0, 0]
+  // b2 row n (K = 16, the chunk of the operand row with its constant columns):
+  // b2_hi, b2_lo at the constant columns, 0 elsewhere
   for (int i = tid; i < H1 * 16; i += stride) {
     const int n = i / 16, q = i % 16;
     float v = 0.f;
-    if (q == 12) v = bf16_val(b2[n]);
-    if (q == 13) v = bf16_val(b2[n] - bf16_val(b2[n]));
-    *(uint16_t *)(packed + C::PK_BB + k16_off(n, q)) = bf16_bits(v);
+    if (q == C::KC % 16) v = bf16_val(b2[n]);
+    if (q == C::KC % 16 + 1) v = bf16_val(b2[n] - bf16_val(b2[n]));
+    *(uint16_t *)(packed + C::PK_BB + kns_off(n, q, 16)) = bf16_bits(v);
   }
-  if (tid == 0) *(float4 *)(packed + C::PK_B3V) = make_float4(b3[0], b3[1], 0.f, 0.f);
+  if (tid == 0)
+    *(float4 *)(packed + C::PK_B3V) = make_float4(b3[0], b3[1], NA == 3 ? b3[2] : 0.f, 0.f);
 }
 
 // 32 consecutive 32-bit TMEM columns of this thread's lane from registers.
@@ -224,11 +245,14 @@ __device__ __forceinline__ float4 lds128f(uint32_t addr) {
 
 // Layer 3 over one 64-unit block: tanh of the block's z2 columns (FP32 SFU
 // tanh; the same SFU rate per value as the packed bf16x2 form, and no packing)
-// against W3 in FP32.  acc0 / acc1 hold (even-unit, odd-unit) partial sums of
-// logit 0 / logit 1; w3 is the block's 32 float4 {W3[k][0], W3[k+1][0],
-// W3[k][1], W3[k+1][1]} (k even).
+// against W3 in FP32.  acc0 / acc1 / acc2 hold (even-unit, odd-unit) partial
+// sums of logits 0 / 1 / 2; w3 holds the block's unit pairs (W3P bytes each:
+// float4 {W3[k][0], W3[k+1][0], W3[k][1], W3[k+1][1]}, k even, then for three
+// actions float4 {W3[k][2], W3[k+1][2], 0, 0}).
+template <int NA>
 __device__ __forceinline__ void layer3_block(uint32_t taddr, uint32_t w3, uint64_t &acc0,
-                                             uint64_t &acc1) {
+                                             uint64_t &acc1, uint64_t &acc2) {
+  constexpr uint32_t W3P = NA == 2 ? 16u : 32u;
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
     uint32_t z[32];
@@ -236,11 +260,16 @@ __device__ __forceinline__ void layer3_block(uint32_t taddr, uint32_t w3, uint64
     tc::tmem_wait_ld();
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-      const float4 q = lds128f(w3 + 16u * (uint32_t)(half * 16 + j));
+      const uint32_t wa = w3 + W3P * (uint32_t)(half * 16 + j);
+      const float4 q = lds128f(wa);
       const uint64_t hv = f2(tc::tanh_fast(__uint_as_float(z[2 * j])),
                              tc::tanh_fast(__uint_as_float(z[2 * j + 1])));
       acc0 = fma2(hv, f2(q.x, q.y), acc0);
       acc1 = fma2(hv, f2(q.z, q.w), acc1);
+      if (NA == 3) {
+        const float4 q2 = lds128f(wa + 16u);
+        acc2 = fma2(hv, f2(q2.x, q2.y), acc2);
+      }
     }
   }
 }
@@ -305,10 +334,11 @@ __device__ __forceinline__ bool grp_all(uint32_t id, bool v) {
   return r != 0;
 }
 
-template <int H0, int H1>
+template <typename E, int H0, int H1>
 __global__ void __launch_bounds__(kThreads, 1)
     k_ctrl_tc(Dev d, const uint8_t *__restrict__ packed, uint32_t n_steps) {
-  using C = CtrlTc<H0, H1>;
+  using C = CtrlTc<E, H0, H1>;
+  constexpr bool ACRO = E::NA == 3;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = tc::smem_u32(smem_raw);
   uint8_t *sm = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
@@ -349,12 +379,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t lane = (uint32_t)((warp & 3) * 32) << 16;
   const uint32_t bar_id = 1u + (uint32_t)g;
   const uint32_t pair_id = 3u + 4u * (uint32_t)g + (uint32_t)(warp & 3);
-  const uint32_t a1 = sb + C::OFF_A1 + (uint32_t)g * 128 * 32;
-  const uint32_t a1_row = a1 + (uint32_t)(r >> 3) * 256u + (uint32_t)(r & 7) * 16u;
+  const uint32_t a1 = sb + C::OFF_A1 + (uint32_t)g * 128 * (C::K1 * 2);
+  const uint32_t a1_row = a1 + (uint32_t)(r >> 3) * (C::K1 * 16) + (uint32_t)(r & 7) * 16u;
   const uint32_t w3s = sb + C::OFF_W3;
   const uint32_t xch = sb + C::OFF_XCH + (uint32_t)g * 128 * 32 + (uint32_t)r * 32;
-  const uint64_t desc_a1 = tc::smem_desc(a1, 128, 256, tc::kSwizzleNone);
-  const uint64_t desc_b1 = tc::smem_desc(sb + C::OFF_B1, 128, 256, tc::kSwizzleNone);
+  const uint64_t desc_a1 = tc::smem_desc(a1, 128, C::K1 * 16, tc::kSwizzleNone);
+  const uint64_t desc_b1 = tc::smem_desc(sb + C::OFF_B1, 128, C::K1 * 16, tc::kSwizzleNone);
+  // the K = 16 chunk of the operand row that holds its constant columns (b2 MMA)
+  const uint64_t desc_ac = tc::smem_desc(a1 + (uint32_t)(C::KC / 16) * 256u, 128, C::K1 * 16,
+                                         tc::kSwizzleNone);
   const uint64_t desc_bb0 = tc::smem_desc(sb + C::OFF_BB, 128, 256, tc::kSwizzleNone);
   const uint64_t desc_w20 = tc::smem_desc(sb + C::OFF_W2, 16, 1024, tc::kSwizzle128B);
   constexpr uint32_t idesc1 = tc::idesc_bf16_f32(128, H0);
@@ -396,13 +429,38 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t row = row0;
     for (uint32_t j = 0; j < n_steps; ++j) {
       const uint32_t k = (uint32_t)(k0 + j);
-      // ---- layer 1 operand row [s_hi | s_lo | s_hi | 1 1 0 0] (half 0 holds the state)
+      // ---- layer 1 operand row [o_hi | o_lo | o_hi | 1 1 0...] (half 0 holds the state)
+      float ob[E::OBS];  // this step's observation (the record)
       if (h == 0) {
-        const float xh = bf16_val(x), vh = bf16_val(v), thh = bf16_val(th), wh = bf16_val(w);
-        const uint32_t hi01 = tc::pack_bf16x2(xh, vh), hi23 = tc::pack_bf16x2(thh, wh);
-        tc::sts128(a1_row, hi01, hi23, tc::pack_bf16x2(x - xh, v - vh),
-                   tc::pack_bf16x2(th - thh, w - wh));
-        tc::sts128(a1_row + 128, hi01, hi23, tc::pack_bf16x2(1.f, 1.f), 0u);
+        if constexpr (ACRO) {
+          sincosf(x, &ob[1], &ob[0]);  // (th1, th2, w1, w2) in (x, v, th, w)
+          sincosf(v, &ob[3], &ob[2]);
+          ob[4] = th;
+          ob[5] = w;
+          float oh[6];
+#pragma unroll
+          for (int i = 0; i < 6; ++i) oh[i] = bf16_val(ob[i]);
+          const uint32_t h01 = tc::pack_bf16x2(oh[0], oh[1]), h23 = tc::pack_bf16x2(oh[2], oh[3]),
+                         h45 = tc::pack_bf16x2(oh[4], oh[5]);
+          const uint32_t l01 = tc::pack_bf16x2(ob[0] - oh[0], ob[1] - oh[1]);
+          const uint32_t l23 = tc::pack_bf16x2(ob[2] - oh[2], ob[3] - oh[3]);
+          const uint32_t l45 = tc::pack_bf16x2(ob[4] - oh[4], ob[5] - oh[5]);
+          // K 0-7: h h h l | 8-15: l l h h | 16-23: h 1 0 0 | 24-31: 0
+          tc::sts128(a1_row, h01, h23, h45, l01);
+          tc::sts128(a1_row + 128, l23, l45, h01, h23);
+          tc::sts128(a1_row + 256, h45, tc::pack_bf16x2(1.f, 1.f), 0u, 0u);
+          tc::sts128(a1_row + 384, 0u, 0u, 0u, 0u);
+        } else {
+          ob[0] = x;
+          ob[1] = v;
+          ob[2] = th;
+          ob[3] = w;
+          const float xh = bf16_val(x), vh = bf16_val(v), thh = bf16_val(th), wh = bf16_val(w);
+          const uint32_t hi01 = tc::pack_bf16x2(xh, vh), hi23 = tc::pack_bf16x2(thh, wh);
+          tc::sts128(a1_row, hi01, hi23, tc::pack_bf16x2(x - xh, v - vh),
+                     tc::pack_bf16x2(th - thh, w - wh));
+          tc::sts128(a1_row + 128, hi01, hi23, tc::pack_bf16x2(1.f, 1.f), 0u);
+        }
       }
       tc::fence_async_smem();
       tc::fence_before_sync();  // (also orders the last step's TMEM reads before the MMA)
@@ -410,7 +468,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) { fail_site = fsite ? fsite : 9u; break; }
       if (issuer) {
         tc::fence_after_sync();
-        tc::mma_bf16(tmem, desc_a1, desc_b1, idesc1, false);
+#pragma unroll
+        for (int q = 0; q < C::K1 / 16; ++q)
+          tc::mma_bf16(tmem, desc_a1 + (uint64_t)(16 * q), desc_b1 + (uint64_t)(16 * q), idesc1,
+                       q != 0);
         tc::mma_commit(bar_l1);
       }
       if (!tc::mbar_wait(bar_l1, ph_l1, kWaitNs) && !wfail) { wfail = true; fsite = 1; }
@@ -432,7 +493,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tmem_wait_st();
       // ---- layer 2 in passes of NPW output units; layer 3 after each pass
-      uint64_t acc0 = 0ull, acc1 = 0ull;  // (+0.f, +0.f) pairs
+      uint64_t acc0 = 0ull, acc1 = 0ull, acc2 = 0ull;  // (+0.f, +0.f) pairs
       float sin_th = 0.f, cos_th = 0.f;
 #pragma unroll
       for (int p = 0; p < C::NP; ++p) {
@@ -445,7 +506,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           // in registers across the step loop
           uint64_t dbb = desc_bb0, dw2 = desc_w20;
           asm volatile("" : "+l"(dbb), "+l"(dw2));
-          tc::mma_bf16(tmem, desc_a1, dbb + (uint64_t)((p * C::NPW * 32) >> 4), idesc2,
+          tc::mma_bf16(tmem, desc_ac, dbb + (uint64_t)((p * C::NPW * 32) >> 4), idesc2,
                        false);  // b2
 #pragma unroll
           for (int kb = 0; kb < C::KB; ++kb) {
@@ -467,7 +528,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                          "r"(rr.y), "r"(rr.z), "r"(rr.w)
                          : "memory");
             asm volatile("st.shared.f32 [%0], %1;" ::"r"(xch + 8), "f"(ud) : "memory");
-          } else {
+          } else if constexpr (!ACRO) {
             sin_th = sinf(th);
             cos_th = cosf(th);
           }
@@ -477,43 +538,78 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc::fence_after_sync();
         tok_take(tok, kWaitNs);
         if (h < C::KBP)
-          layer3_block(tmem + lane + (uint32_t)(h * 64),
-                       w3s + (uint32_t)((p * C::NPW + h * 64) * 8), acc0, acc1);
+          layer3_block<E::NA>(tmem + lane + (uint32_t)(h * 64),
+                              w3s + (uint32_t)((p * C::NPW + h * 64) / 2 * C::W3P), acc0, acc1,
+                              acc2);
         tok_give(tok);
       }
-      const float2 pa = unf2(acc0), pb = unf2(acc1);
-      const float p0 = pa.x + pa.y, p1 = pb.x + pb.y;
-      if (h == 1) asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(xch), "f"(p0), "f"(p1) : "memory");
+      const float2 pa = unf2(acc0), pb = unf2(acc1), pc = unf2(acc2);
+      const float p0 = pa.x + pa.y, p1 = pb.x + pb.y, p2 = pc.x + pc.y;
+      if (h == 1) {
+        asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(xch), "f"(p0), "f"(p1) : "memory");
+        if (ACRO) asm volatile("st.shared.f32 [%0], %1;" ::"r"(xch + 12), "f"(p2) : "memory");
+      }
       pair_sync(pair_id);
       if (h == 0) {
-        float q0, q1, u;
+        float q0, q1, q2 = 0.f, u;
         asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(q0), "=f"(q1) : "r"(xch) : "memory");
         asm volatile("ld.shared.f32 %0, [%1];" : "=f"(u) : "r"(xch + 8) : "memory");
-        const float l0 = (p0 + q0) + b3.x, l1v = (p1 + q1) + b3.y;
-        // ---- sample: a = 0 iff u S < exp(l0 - m)
-        const float m = fmaxf(l0, l1v);
-        const float e0 = expf(l0 - m), e1 = expf(l1v - m);
-        const float Ssum = e0 + e1;
-        const int a = (u * Ssum < e0) ? 0 : 1;
-        // ---- env step (explicit Euler, dt = 0.02), reward, done, auto-reset
-        const float uf = a ? 10.0f : -10.0f;
-        const float xacc = uf - 0.5f * x - 0.1f * v;
-        const float thacc = 9.8f * sin_th - 0.3f * cos_th * uf;
-        const float x2 = x + 0.02f * v, v2 = v + 0.02f * xacc;
-        const float th2 = th + 0.02f * w, w2 = w + 0.02f * thacc;
+        if (ACRO) asm volatile("ld.shared.f32 %0, [%1];" : "=f"(q2) : "r"(xch + 12) : "memory");
+        const float l0 = (p0 + q0) + b3.x, l1v = (p1 + q1) + b3.y, l2 = (p2 + q2) + b3.z;
+        // ---- sample by inverse CDF: a = min{ i : u S < C_i } (C_i running sums
+        // of exp(l - max), S the total), as the per-step sampler
+        int a;
+        float m, Ssum, la;
+        if constexpr (ACRO) {
+          m = fmaxf(fmaxf(l0, l1v), l2);
+          const float e0 = expf(l0 - m), e1 = expf(l1v - m), e2 = expf(l2 - m);
+          Ssum = (e0 + e1) + e2;
+          const float thr = u * Ssum;
+          a = thr < e0 ? 0 : (thr < e0 + e1 ? 1 : 2);
+          la = a == 0 ? l0 : (a == 1 ? l1v : l2);
+        } else {
+          m = fmaxf(l0, l1v);
+          const float e0 = expf(l0 - m), e1 = expf(l1v - m);
+          Ssum = e0 + e1;
+          a = (u * Ssum < e0) ? 0 : 1;
+          la = a ? l1v : l0;
+        }
+        // ---- env step, reward, done, auto-reset
+        float ns[4];
+        float rew;
+        bool done;
         const int t2 = tep + 1;
-        const bool done = fabsf(x2) > 2.4f || fabsf(th2) > 0.21f || t2 >= (int)d.episode_limit;
+        if constexpr (ACRO) {
+          // RK4 of the two-link dynamics, dt = 0.2, torque a - 1
+          ns[0] = x;
+          ns[1] = v;
+          ns[2] = th;
+          ns[3] = w;
+          acro_step(ns, (float)(a - 1), 0.2f);
+          const bool term = acro_terminal(ns);
+          rew = term ? 0.0f : -1.0f;
+          done = term || t2 >= (int)d.episode_limit;
+        } else {
+          // explicit Euler, dt = 0.02
+          const float uf = a ? 10.0f : -10.0f;
+          const float xacc = uf - 0.5f * x - 0.1f * v;
+          const float thacc = 9.8f * sin_th - 0.3f * cos_th * uf;
+          ns[0] = x + 0.02f * v;
+          ns[1] = v + 0.02f * xacc;
+          ns[2] = th + 0.02f * w;
+          ns[3] = w + 0.02f * thacc;
+          rew = 1.0f;
+          done = fabsf(ns[0]) > 2.4f || fabsf(ns[2]) > 0.21f || t2 >= (int)d.episode_limit;
+        }
         if (valid) {
-          const float lp = ((a ? l1v : l0) - m) - logf(Ssum);
+          const float lp = (la - m) - logf(Ssum);
           const size_t o = (size_t)row * S + e;
-          float *ob = d.r_obs + (size_t)row * 4 * S + e;
-          ob[0] = x;
-          ob[S] = v;
-          ob[2 * (size_t)S] = th;
-          ob[3 * (size_t)S] = w;
+          float *obr = d.r_obs + (size_t)row * E::OBS * S + e;
+#pragma unroll
+          for (int i = 0; i < E::OBS; ++i) obr[(size_t)i * S] = ob[i];
           ((int32_t *)d.r_act)[o] = a;
           d.r_logp[o] = lp;
-          d.r_rew[o] = 1.0f;
+          d.r_rew[o] = rew;
           d.r_done[o] = (uint8_t)done;
         }
         if (done) {
@@ -522,16 +618,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                        : "=r"(rr.x), "=r"(rr.y), "=r"(rr.z), "=r"(rr.w)
                        : "r"(xch + 16)
                        : "memory");
-          x = uniform(rr.x, -0.05f, 0.05f);
-          v = uniform(rr.y, -0.05f, 0.05f);
-          th = uniform(rr.z, -0.05f, 0.05f);
-          w = uniform(rr.w, -0.05f, 0.05f);
+          const float lim = ACRO ? 0.1f : 0.05f;
+          x = uniform(rr.x, -lim, lim);
+          v = uniform(rr.y, -lim, lim);
+          th = uniform(rr.z, -lim, lim);
+          w = uniform(rr.w, -lim, lim);
           tep = 0;
         } else {
-          x = x2;
-          v = v2;
-          th = th2;
-          w = w2;
+          x = ns[0];
+          v = ns[1];
+          th = ns[2];
+          w = ns[3];
           tep = t2;
         }
       }
@@ -572,28 +669,37 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-template <int H0, int H1>
+template <typename E, int H0, int H1>
 struct Shape {
-  static constexpr size_t packed_bytes = CtrlTc<H0, H1>::PACKED;
+  using C = CtrlTc<E, H0, H1>;
+  static constexpr size_t packed_bytes = C::PACKED;
   static void pack(const Dev &d, void *packed, cudaStream_t st) {
-    k_ctrl_tc_pack<H0, H1><<<64, 256, 0, st>>>(d.params, (uint8_t *)packed);
+    k_ctrl_tc_pack<E, H0, H1><<<64, 256, 0, st>>>(d.params, (uint8_t *)packed);
   }
   static cudaError_t run(const Dev &d, const void *packed, uint32_t n, int grid, cudaStream_t st) {
-    k_ctrl_tc<H0, H1><<<grid, kThreads, CtrlTc<H0, H1>::SMEM, st>>>(d, (const uint8_t *)packed, n);
+    k_ctrl_tc<E, H0, H1><<<grid, kThreads, C::SMEM, st>>>(d, (const uint8_t *)packed, n);
     return cudaGetLastError();
   }
   static cudaError_t attr() {
-    return cudaFuncSetAttribute(k_ctrl_tc<H0, H1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                CtrlTc<H0, H1>::SMEM);
+    return cudaFuncSetAttribute(k_ctrl_tc<E, H0, H1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                C::SMEM);
   }
 };
 
+template <typename E, typename F>
+bool dispatch_env(const PolicyShape &sh, F &&f) {
+  if (sh.w[1] == 256 && sh.w[2] == 256) return f(Shape<E, 256, 256>()), true;
+  if (sh.w[1] == 128 && sh.w[2] == 128) return f(Shape<E, 128, 128>()), true;
+  if (sh.w[1] == 64 && sh.w[2] == 64) return f(Shape<E, 64, 64>()), true;
+  return false;
+}
+
+// The policy's input and output widths name the env: 4 -> 2 the control env,
+// 6 -> 3 the acrobot.
 template <typename F>
 bool dispatch(const PolicyShape &sh, F &&f) {
-  if (sh.w[0] != 4 || sh.w[3] != 2) return false;
-  if (sh.w[1] == 256 && sh.w[2] == 256) return f(Shape<256, 256>()), true;
-  if (sh.w[1] == 128 && sh.w[2] == 128) return f(Shape<128, 128>()), true;
-  if (sh.w[1] == 64 && sh.w[2] == 64) return f(Shape<64, 64>()), true;
+  if (sh.w[0] == EnvCart::OBS && sh.w[3] == EnvCart::NA) return dispatch_env<EnvCart>(sh, f);
+  if (sh.w[0] == EnvAcro::OBS && sh.w[3] == EnvAcro::NA) return dispatch_env<EnvAcro>(sh, f);
   return false;
 }
 

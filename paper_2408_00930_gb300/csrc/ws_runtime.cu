@@ -96,13 +96,16 @@ void agent_counts(const ws_config *cfg, std::vector<int32_t> &out) {
   }
 }
 
+// The classic-control envs (control, acrobot) on BF16: the fused kernel of
+// ws_control_tc.cu.
 bool use_tc_control(const ws_config *cfg) {
-  return cfg->env == WS_ENV_CONTROL && cfg->path == WS_PATH_BATCHED_BF16;
+  return (cfg->env == WS_ENV_CONTROL || cfg->env == WS_ENV_ACROBOT) &&
+         cfg->path == WS_PATH_BATCHED_BF16;
 }
 
 // Economy / landscape on the BF16 path: per-layer tensor-core policy kernels.
 bool use_tc_layers(const ws_config *cfg) {
-  return cfg->env != WS_ENV_CONTROL && cfg->path == WS_PATH_BATCHED_BF16;
+  return !use_tc_control(cfg) && cfg->path == WS_PATH_BATCHED_BF16;
 }
 
 bool tc_layers_supported(const PolicyShape &p) {
@@ -349,7 +352,7 @@ void make_dev(ws_ctx *c) {
     d.s = (float *)(S + L.state_off);
   } else if (cfg.env == WS_ENV_ACROBOT) {
     d.s = (float *)(S + L.state_off);
-    d.pobs = (float *)(S + L.scratch_pobs_off);
+    if (!use_tc_control(&cfg)) d.pobs = (float *)(S + L.scratch_pobs_off);
   } else {
     d.wealth = (int64_t *)(S + L.state_off);
     d.feat = (float *)(S + L.state_off + up(Sa * 8));
@@ -587,7 +590,7 @@ std::vector<Piece> state_pieces(ws_ctx *c, ws_field f) {
       v.push_back({S + L.env_params_off, N * 4});
     }
   } else if (f == WS_F_LOGITS) {
-    if (L.env == WS_ENV_CONTROL && use_tc_control(&c->cfg)) return v;
+    if (use_tc_control(&c->cfg)) return v;
     if ((L.econ_fused || L.land_fused) && !c->d.dbg_logits) return v;
     v.push_back({S + L.scratch_out_off, (size_t)L.n_agent_slots * L.n_out * 4});
     if (L.env == WS_ENV_ECONOMY) v.push_back({S + L.scratch_pout_off, N * 10 * 4});

@@ -2,7 +2,9 @@
 the FP64 oracle: parameter and reset draws bit-exact, one-step replays of
 seeded states, and long roll-outs checked step by step against oracle steps
 taken from the GPU's own recorded states (teacher forcing: the dynamics are
-chaotic, so free-running FP32 and FP64 trajectories part after a while)."""
+chaotic, so free-running FP32 and FP64 trajectories part after a while).  The
+BF16 path is the fused classic-control kernel (layer 2 in BF16, layers 1 and 3
+at FP32 accuracy), compared with the oracle in that operand mode."""
 import numpy as np
 import pytest
 
@@ -10,7 +12,7 @@ import oracle
 from paper_2408_00930_gb300 import inputs
 from paper_2408_00930_gb300 import warpsci as W
 from tests import ws_helpers as H
-from tests.gpu_common import TIE_F32, TOL_BF16, TOL_F32, need_gpu
+from tests.gpu_common import TIE_BF16, TIE_F32, TOL_BF16, TOL_F32, need_gpu
 
 pytestmark = pytest.mark.gpu
 PATHS = [W.WS_PATH_PLAIN_FP32, W.WS_PATH_BATCHED_FP32, W.WS_PATH_BATCHED_BF16]
@@ -18,10 +20,10 @@ PATHS = [W.WS_PATH_PLAIN_FP32, W.WS_PATH_BATCHED_FP32, W.WS_PATH_BATCHED_BF16]
 # to the largest magnitude the step passes through (the unclipped RK4 result;
 # at |w| ~ 40 rad/s the w^2 terms put FP32 rounding near 1e-5 of it)
 TOL_STEP = 3e-5
-# the tip-height threshold of the terminal condition, and the categorical tie
-# band when the logits carry BF16 operand rounding
+# the tip-height threshold of the terminal condition
 HEIGHT_BAND = 1e-4
-TIE_BF16 = 5e-3
+# the fused kernel's precision: layer 2 with BF16 operands (and BF16 tanh of h1)
+ORACLE_BF16_LAYERS = 0b010
 
 
 @pytest.fixture(scope="module")
@@ -51,10 +53,6 @@ def state_from_obs(o):
     return np.array([np.arctan2(o[1], o[0]), np.arctan2(o[3], o[2]), o[4], o[5]])
 
 
-def rel(a, b):
-    return np.abs(a - b).max() / max(np.abs(b).max(), 1.0)
-
-
 @pytest.mark.parametrize("path", PATHS)
 def test_one_step_replay_seeded_states(torch, path):
     n, h = 1500, 64
@@ -66,7 +64,7 @@ def test_one_step_replay_seeded_states(torch, path):
     s0[20:40, 0] = np.float32(2.9)                  # near upright: terminal heights
     t0 = g.integers(0, 400, n).astype(np.int32)
     t0[40:60] = 499                                 # the episode limit
-    r = acro(path, n, 8, 500, h=h, flags=W.WS_FLAG_DEBUG_LOGITS)
+    r = acro(path, n, 8, 500, h=h)
     r.load_raw(W.WS_F_PARAMS, params)
     k0 = 77
     r.load_raw(W.WS_F_STATE, H.pack_control_state(s0, t0), k=k0)
@@ -77,25 +75,17 @@ def test_one_step_replay_seeded_states(torch, path):
                                                        W.WS_F_REWARD, W.WS_F_DONE))
     s1, t1 = H.unpack_control_state(r.fetch_raw(W.WS_F_STATE, 20 * n), n)
     bf16 = path == W.WS_PATH_BATCHED_BF16
-    if bf16:
-        lg = r.fetch_raw(W.WS_F_LOGITS, 4 * 3 * n).view(np.float32).reshape(n, 3)
+    tie = TIE_BF16 if bf16 else TIE_F32
     s0d = s0.astype(np.float64)
     n_amb = 0
     for e in range(n):
         o_ref = oracle.acrobot_obs(s0d[e])
         np.testing.assert_allclose(obs[:, e], o_ref, rtol=0, atol=2e-6)
-        if bf16:
-            # the BF16 layers' logits against the oracle in BF16-operand mode;
-            # the draw then follows the GPU's own logits
-            o_l = oracle.mlp_forward([6, h, h, 3], params, obs[:, e].astype(np.float64),
-                                     bf16_layers=0b111)
-            assert rel(lg[e], o_l) <= TOL_BF16, e
-            logits = lg[e].astype(np.float64)
-        else:
-            logits = oracle.mlp_forward([6, h, h, 3], params, obs[:, e].astype(np.float64))
+        logits = oracle.mlp_forward([6, h, h, 3], params, obs[:, e].astype(np.float64),
+                                    bf16_layers=ORACLE_BF16_LAYERS if bf16 else 0)
         u = oracle.u01(int(oracle.draw(1, k0, e, 0, oracle.TAG_ACTION, 0)[0]))
         a_o, lp_o, mg = oracle.sample_categorical(logits, u)
-        if mg < TIE_F32:
+        if mg < tie:
             n_amb += 1
             continue
         assert act[e] == a_o, e
@@ -115,7 +105,7 @@ def test_one_step_replay_seeded_states(torch, path):
             d[:2] = (d[:2] + np.pi) % (2 * np.pi) - np.pi      # angles modulo 2 pi
             assert np.abs(d).max() <= TOL_STEP * max(1.0, np.abs(raw).max()), (e, d)
             assert t1[e] == t0[e] + 1
-    assert n_amb <= 10 and dn[20:40].sum() > 0 and dn[40:60].all()
+    assert n_amb <= (0.12 * n if bf16 else 10) and dn[20:40].sum() > 0 and dn[40:60].all()
     r.close()
 
 
@@ -142,7 +132,7 @@ def test_long_rollout_teacher_forced(torch, path):
                 np.testing.assert_allclose(st, oracle.acrobot_reset_draw(8, oracle.STEP_INIT, e),
                                            rtol=0, atol=1e-6)
             logits = oracle.mlp_forward([6, h, h, 3], params, obs[s][:, e].astype(np.float64),
-                                        bf16_layers=0b111 if bf16 else 0)
+                                        bf16_layers=ORACLE_BF16_LAYERS if bf16 else 0)
             u = oracle.u01(int(oracle.draw(8, s, e, 0, oracle.TAG_ACTION, 0)[0]))
             a_o, _, mg = oracle.sample_categorical(logits, u)
             a = int(act[s][e])
@@ -168,7 +158,8 @@ def test_long_rollout_teacher_forced(torch, path):
                 o_ref = oracle.acrobot_obs(nxt)
                 assert np.abs(o_next - o_ref).max() <= TOL_STEP * max(1.0, np.abs(raw).max()), \
                     (s, e, o_next, o_ref)
-    assert n_amb <= 0.05 * 5 * T             # draws inside the tie band: ~2 x 2 x tie per draw
+    # draws inside the tie band: ~2 boundaries x 2 tie per draw
+    assert n_amb <= (0.12 if bf16 else 0.05) * 5 * T
     assert dn.sum() >= n                      # every env ends at least one episode
     r.close()
 
@@ -182,3 +173,16 @@ def test_graph_path_bytes_equal_plain_path(torch):
                                                           W.WS_F_REWARD, W.WS_F_DONE)])
         r.close()
     assert out[0] == out[1]
+
+
+def test_bf16_fused_deterministic_and_chunk_invariant(torch):
+    out = []
+    for ch in (40, 7, 40):
+        r = acro(W.WS_PATH_BATCHED_BF16, 700, 90, 60, h=128, seed=5, chunk_steps=ch)
+        r.reset(2)
+        r.rollout(90)
+        r.sync()
+        out.append([r.fetch(f, 0, 90).tobytes() for f in (W.WS_F_OBS, W.WS_F_ACTION, W.WS_F_LOGP,
+                                                          W.WS_F_REWARD, W.WS_F_DONE)])
+        r.close()
+    assert out[0] == out[1] == out[2]
