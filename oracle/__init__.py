@@ -109,6 +109,8 @@ def _declare(L):
                                         C.c_double]
                                        + [_P] * 10)
     L.or_returns.argtypes = [C.c_int, C.c_long, _P, _P, C.c_double, _P]
+    L.or_a2c.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P, _P,
+                         C.c_double, C.c_double, _P, _P, _P]
 
 
 def _ptr(a):
@@ -437,3 +439,23 @@ def returns(reward, done, gamma):
     G = np.empty_like(r)
     lib().or_returns(T, ns, _ptr(r), _ptr(d), float(gamma), _ptr(G))
     return G
+
+
+# --------------------------------------------------------------------------
+# actor-critic update (A2C with Monte-Carlo returns)
+# --------------------------------------------------------------------------
+def a2c(actor, critic, obs, act, ret, h0, h1, n_act, c_v=0.5, c_e=0.0, adv=None, grads=True):
+    """Loss terms {policy, value, entropy} (means over the rows) and, with
+    grads, dL/d(actor params) and dL/d(critic params) in FP64.  obs [R][obs_dim],
+    act [R], ret [R]; adv (the actor's advantage) defaults to G - V."""
+    o = _arr(obs, np.float64)
+    R, od = o.shape
+    na = policy_param_count([od, h0, h1, n_act])
+    nc = policy_param_count([od, h0, h1, 1])
+    ga = np.empty(na) if grads else None
+    gc = np.empty(nc) if grads else None
+    st = np.empty(3)
+    lib().or_a2c(R, od, n_act, h0, h1, _ptr(_arr(actor, np.float32)), _ptr(_arr(critic, np.float32)),
+                 _ptr(o), _ptr(_arr(act, np.int32)), _ptr(_arr(ret, np.float64)),
+                 _ptr(_arr(adv, np.float64)), float(c_v), float(c_e), _ptr(ga), _ptr(gc), _ptr(st))
+    return st, ga, gc

@@ -865,6 +865,152 @@ void or_landscape_rollout(int D, int M, const double *c, const double *wd, const
 }
 
 /* ------------------------------------------------------------------------ */
+/* Actor-critic update on recorded transitions (paper Sec. 2 and App. B: the */
+/* roll-out store feeds training on the GPU).  Advantage actor-critic with   */
+/* Monte-Carlo returns [reading]: the actor is the roll-out policy          */
+/* (categorical head), the critic an MLP of the same widths with one output. */
+/* Over the R recorded rows (obs s_i, action a_i, return G_i):               */
+/*   A_i = G_i - V(s_i)              (a constant in the actor's loss)        */
+/*   L   = (1/R) sum_i [ -A_i log pi(a_i | s_i) - c_e H(pi(. | s_i))         */
+/*                       + c_v (G_i - V(s_i))^2 ]                            */
+/* Gradients by the chain rule through the tanh layers, in FP64.            */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  double *a[4];  /* activations per layer (a[0] = input) */
+  double *z[4];  /* pre-activations */
+} or_trace;
+
+static void or_trace_alloc(or_trace *t, const int32_t *w) {
+  for (int l = 0; l < 4; ++l) {
+    t->a[l] = (double *)malloc(sizeof(double) * w[l]);
+    t->z[l] = (double *)malloc(sizeof(double) * w[l]);
+  }
+}
+static void or_trace_free(or_trace *t) {
+  for (int l = 0; l < 4; ++l) {
+    free(t->a[l]);
+    free(t->z[l]);
+  }
+}
+
+/* Forward with every activation kept (three layers, tanh hidden, linear out). */
+static void or_mlp_trace(const int32_t *w, const float *params, const double *x, or_trace *t) {
+  for (int i = 0; i < w[0]; ++i) t->a[0][i] = x[i];
+  long off = 0;
+  for (int l = 0; l < 3; ++l) {
+    const float *W = params + off, *b = W + (long)w[l] * w[l + 1];
+    for (int j = 0; j < w[l + 1]; ++j) {
+      double s = (double)b[j];
+      for (int i = 0; i < w[l]; ++i) s += t->a[l][i] * (double)W[(long)i * w[l + 1] + j];
+      t->z[l + 1][j] = s;
+      t->a[l + 1][j] = l == 2 ? s : tanh(s);
+    }
+    off += (long)w[l] * w[l + 1] + w[l + 1];
+  }
+}
+
+/* Accumulate into grad the gradient of (dy . output) through the traced pass. */
+static void or_mlp_backward(const int32_t *w, const float *params, const or_trace *t,
+                            const double *dy, double *grad) {
+  int maxw = 0;
+  for (int l = 0; l < 4; ++l)
+    if (w[l] > maxw) maxw = w[l];
+  double *d = (double *)malloc(sizeof(double) * maxw);
+  double *dn = (double *)malloc(sizeof(double) * maxw);
+  long offs[3], off = 0;
+  for (int l = 0; l < 3; ++l) {
+    offs[l] = off;
+    off += (long)w[l] * w[l + 1] + w[l + 1];
+  }
+  for (int j = 0; j < w[3]; ++j) d[j] = dy[j];  /* d of layer 3's pre-activation */
+  for (int l = 2; l >= 0; --l) {
+    const float *W = params + offs[l];
+    double *gW = grad + offs[l], *gb = gW + (long)w[l] * w[l + 1];
+    for (int j = 0; j < w[l + 1]; ++j) {
+      gb[j] += d[j];
+      for (int i = 0; i < w[l]; ++i) gW[(long)i * w[l + 1] + j] += t->a[l][i] * d[j];
+    }
+    if (l > 0) {
+      for (int i = 0; i < w[l]; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < w[l + 1]; ++j) s += (double)W[(long)i * w[l + 1] + j] * d[j];
+        dn[i] = s * (1.0 - t->a[l][i] * t->a[l][i]);  /* tanh' = 1 - tanh^2 */
+      }
+      for (int i = 0; i < w[l]; ++i) d[i] = dn[i];
+    }
+  }
+  free(d);
+  free(dn);
+}
+
+/* Loss terms and (optionally) gradients.  obs [R][obs_dim], act [R], ret [R];
+ * adv [R] may be NULL (then A = G - V from the critic).  grad_actor /
+ * grad_critic may be NULL; else they receive dL/dparams (zeroed first).
+ * stats: {mean -A log pi, mean (G - V)^2, mean entropy}. */
+void or_a2c(int R, int obs_dim, int n_act, int h0, int h1, const float *actor, const float *critic,
+            const double *obs, const int32_t *act, const double *ret, const double *adv,
+            double c_v, double c_e, double *grad_actor, double *grad_critic, double stats[3]) {
+  int32_t wa[4] = {obs_dim, h0, h1, n_act}, wc[4] = {obs_dim, h0, h1, 1};
+  long na = 0, nc = 0;
+  for (int l = 0; l < 3; ++l) {
+    na += (long)wa[l] * wa[l + 1] + wa[l + 1];
+    nc += (long)wc[l] * wc[l + 1] + wc[l + 1];
+  }
+  if (grad_actor) memset(grad_actor, 0, sizeof(double) * na);
+  if (grad_critic) memset(grad_critic, 0, sizeof(double) * nc);
+  or_trace ta, tc;
+  or_trace_alloc(&ta, wa);
+  or_trace_alloc(&tc, wc);
+  double *p = (double *)malloc(sizeof(double) * n_act);
+  double *dl = (double *)malloc(sizeof(double) * n_act);
+  double s_pg = 0.0, s_v = 0.0, s_h = 0.0;
+  for (int i = 0; i < R; ++i) {
+    const double *x = obs + (long)i * obs_dim;
+    or_mlp_trace(wa, actor, x, &ta);
+    or_mlp_trace(wc, critic, x, &tc);
+    const double *lg = ta.a[3];
+    double m = lg[0];
+    for (int k = 1; k < n_act; ++k)
+      if (lg[k] > m) m = lg[k];
+    double S = 0.0;
+    for (int k = 0; k < n_act; ++k) S += exp(lg[k] - m);
+    double H = 0.0;
+    for (int k = 0; k < n_act; ++k) {
+      p[k] = exp(lg[k] - m) / S;
+      H -= p[k] * ((lg[k] - m) - log(S));
+    }
+    const double V = tc.a[3][0];
+    const double A = adv ? adv[i] : ret[i] - V;
+    const double logp = (lg[act[i]] - m) - log(S);
+    s_pg += -A * logp;
+    s_v += (ret[i] - V) * (ret[i] - V);
+    s_h += H;
+    if (grad_actor) {
+      /* d(-A log p_a)/dl_k = A (p_k - [k = a]);
+       * d(-c_e H)/dl_k = c_e p_k (log p_k + H) */
+      for (int k = 0; k < n_act; ++k) {
+        const double lpk = (lg[k] - m) - log(S);
+        dl[k] = (A * (p[k] - (k == act[i] ? 1.0 : 0.0)) + c_e * p[k] * (lpk + H)) / R;
+      }
+      or_mlp_backward(wa, actor, &ta, dl, grad_actor);
+    }
+    if (grad_critic) {
+      double dv = 2.0 * c_v * (V - ret[i]) / R;
+      or_mlp_backward(wc, critic, &tc, &dv, grad_critic);
+    }
+  }
+  if (stats) {
+    stats[0] = s_pg / R;
+    stats[1] = s_v / R;
+    stats[2] = s_h / R;
+  }
+  free(p);
+  free(dl);
+  or_trace_free(&ta);
+  or_trace_free(&tc);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Discounted returns over a window of n_steps records ([n_steps][n_slots]):*/
 /*   G_t = r_t + gamma (1 - d_t) G_{t+1},  G_{n_steps} = 0.                 */
 /* ------------------------------------------------------------------------ */
