@@ -352,6 +352,54 @@ def run_gpu(args, wl, world, rank, local):
     return path, value, main, plain, e2e
 
 
+def run_a2c(wl, local):
+    """One actor-critic update (ws_a2c_update) over the last 50 steps of a
+    roll-out of the workload, timed with CUDA events on the context's stream
+    (L2 flushed before each of three launches).  FP32 SIMT GEMMs: algorithmic
+    flops per row = forward of policy and critic, their weight gradients
+    (same count) and the data gradients of the two hidden layers."""
+    import torch
+    from paper_2408_00930_gb300 import warpsci as W
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    T = min(CHUNK, wl["horizon"])
+    with torch.cuda.stream(stream):
+        r = W.Rollout(wl["env"], W.WS_PATH_BATCHED_BF16, wl["n_envs"], T, wl["limit"], *wl["h"],
+                      device=dev, stream=stream, chunk_steps=CHUNK, flags=W.WS_FLAG_TRAIN)
+    od, na = (4, 2) if wl["env"] == 0 else (6, 3)
+    h0, h1 = wl["h"]
+    fwd = lambda n_out: 2 * (od * h0 + h0 * h1 + h1 * n_out)
+    flops_row = 2 * (fwd(na) + fwd(1)) + 2 * 2 * (h1 * na + h0 * h1 + h1 + h0 * h1)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ms = []
+    for i in range(4):
+        r.reset(77 + i)
+        r.rollout(T)
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        W.ws_a2c_update(r.ctx, T, 1e-3, 0.5, 0.01, None)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if i:
+            ms.append(e0.elapsed_time(e1))
+    r.close()
+    rows = T * wl["n_envs"]
+    t = statistics.median(ms)
+    hbm, bf16_burst, bf16_sus, peak_src = load_peaks()
+    n_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = 2 * 128 * n_sms * 2070e6 / 1e12   # FP32 FMA: 128 lanes / SM / clock
+    achieved = flops_row * rows / (t * 1e-3) / 1e12
+    return {"rows": rows, "ms": t, "rows_per_s": rows / (t * 1e-3), "unit": "rows/s",
+            "roofline": {"bound": "fp32", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak,
+                         "peak_source": f"128 FP32 lanes x 2 flops / clock / SM x {n_sms} SMs x "
+                                        "2070 MHz"},
+            "kernels": "k_a2c_gather, k_dense_fp32 (forward), k_a2c_head, k_wgrad + "
+                       "k_reduce_slices, k_bwd_data, k_sgd; FP32 SIMT"}
+
+
 def run_serving(args, world, rank, local):
     """Serving mix: Poisson arrivals (200 req/s) of requests across the three env
     types, admitted under a 150 GB budget, delivered in chunks of 50 steps."""
@@ -443,6 +491,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--a2c", action="store_true",
+                    help="also time one actor-critic update (ws_a2c_update) over 50 steps "
+                         "(control and acrobot workloads)")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch configuration (profiling captures)")
     ap.add_argument("--horizon", type=int, default=0,
@@ -486,6 +537,7 @@ def main():
         cpu = {"value": v, "unit": "agent-steps/s", "cores": cores, "kind": "oracle",
                "sample": sample}
     path, value, main_res, plain, e2e = run_gpu(args, wl, world, rank, local)
+    a2c = run_a2c(wl, local) if args.a2c and wl["env"] in (0, 3) and rank == 0 else None
     if rank != 0:
         return
     from paper_2408_00930_gb300 import warpsci as W
@@ -635,6 +687,7 @@ def main():
         "plain_fp32": plain,
         "gpu_launches": per_launch * args.steps,
         "clocks": main_res["clocks"],
+        "a2c_update": a2c,
     }
     print(json.dumps(out), flush=True)
 

@@ -99,6 +99,7 @@ typedef enum { WS_PATH_PLAIN_FP32 = 0, WS_PATH_BATCHED_FP32 = 1, WS_PATH_BATCHED
  *           economy: agent policy then planner policy
  *   ENV_PARAMS  landscape: f32 centres[M][dim], f32 widths[M], f32 amps[M];
  *               economy:   i32 agents_per_env[n_envs]
+ *   CRITIC  f32 critic parameters (WS_FLAG_TRAIN), laid out as PARAMS
  *   LOGITS  f32 [n_slots][n_out] policy outputs of the last step (plain and
  *           batched-FP32 paths, the economy's per-layer BF16 path, and its
  *           fused kernel with WS_FLAG_DEBUG_LOGITS)                         */
@@ -115,7 +116,8 @@ typedef enum {
   WS_F_PARAMS = 9,
   WS_F_ENV_PARAMS = 10,
   WS_F_LOGITS = 11,
-  WS_F_FORCE = 12
+  WS_F_FORCE = 12,
+  WS_F_CRITIC = 13
 } ws_field;
 
 /* ws_config.flags: the fused kernels (economy on the BF16 path) also write each
@@ -131,6 +133,10 @@ typedef enum {
 /* ws_config.flags: the ring also holds the landscape FORCE field (D floats
  * per slot-step), written by ws_forces.  Landscape only. */
 #define WS_FLAG_FORCE 4u
+/* ws_config.flags: the context also holds a critic (an MLP obs -> hidden0 ->
+ * hidden1 -> 1, drawn from param_seed like the policy) and the scratch of
+ * ws_a2c_update.  Control and acrobot envs (one categorical policy). */
+#define WS_FLAG_TRAIN 8u
 
 /* Roll-out configuration.  Slots: control and landscape have one agent per
  * env (n_slots = n_envs); the economy has agents_per_env[e] agents in env e,
@@ -192,6 +198,19 @@ ws_status ws_rollout(ws_ctx *ctx, uint32_t n_steps);
  * G_t = r_t + gamma (1 - done_t) G_{t+1}, with G = 0 after the window, in
  * compensated (float-float) FP32.  n_steps <= min(k, ring_steps). */
 ws_status ws_returns(ws_ctx *ctx, uint32_t n_steps);
+
+/* Actor-critic update on the last n_steps ring rows (steps k-n..k-1), in place
+ * (paper Sec. 2 / App. B: the roll-out store feeds training on the GPU).
+ * Advantage actor-critic with Monte-Carlo returns: the returns scan runs first
+ * (into RETURN), then over the R = n_steps x n_slots rows (obs s, action a,
+ * return G), with A = G - V(s) held constant in the policy's loss,
+ *   L = (1/R) sum [ -A log pi(a|s) - c_e H(pi(.|s)) + c_v (G - V(s))^2 ],
+ * and one SGD step of rate lr on the policy and the critic (FP32; the BF16
+ * operand images are repacked).  stats (host, may be NULL; the call then
+ * waits for the stream): the means of -A log pi, (G - V)^2 and H.  Needs
+ * WS_FLAG_TRAIN (WS_ERR_STATE); n_steps <= min(k, ring_steps) (WS_ERR_RANGE). */
+ws_status ws_a2c_update(ws_ctx *ctx, uint32_t n_steps, float lr, float c_v, float c_e,
+                        double *stats);
 
 /* Landscape force over the last n_steps ring rows (steps k-n..k-1), written to
  * the FORCE field: F = -grad E(x') = sum_m a_m e_m (x' - c_m) / w_m^2 at the

@@ -124,7 +124,8 @@ struct Layout {
   int econ_fused;          // economy on the fused persistent kernel
   int land_fused;          // landscape on the fused persistent kernel
   size_t land_energy_off;
-  size_t force_img_off;    // landscape, fused kernel with WS_FLAG_FORCE: the force image  // landscape, fused kernel: its energy image (blocks of 64 Gaussians)
+  size_t force_img_off;
+  size_t critic_off, train_off;  // WS_FLAG_TRAIN: critic parameters, update scratch    // landscape, fused kernel with WS_FLAG_FORCE: the force image  // landscape, fused kernel: its energy image (blocks of 64 Gaussians)
   size_t scratch_off;      // plain-path activations
   size_t scratch_h0_off, scratch_h1_off, scratch_out_off;
   size_t scratch_pobs_off, scratch_ph0_off, scratch_ph1_off, scratch_pout_off;

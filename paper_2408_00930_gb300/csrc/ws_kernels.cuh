@@ -83,6 +83,25 @@ void launch_advance(const Dev &d, uint32_t n, cudaStream_t st);
 
 // ---- S7: discounted returns ----------------------------------------------
 void launch_returns(const Dev &d, uint32_t n_steps, cudaStream_t st);
+// Three-layer FP32 MLP (tanh, tanh, linear) on row-major or SoA inputs.
+void launch_mlp3_f32(const float *X, long ldr, long ldc, const float *params,
+                     const PolicyShape &sh, float *h0, float *h1, float *out, int M,
+                     cudaStream_t st);
+
+// ---- actor-critic update (ws_train.cu) ----------------------------------------
+constexpr int kTrainChunk = 8192;  // rows per chunk of the update
+struct TrainBufs {                 // per-chunk scratch in the state buffer
+  float *x, *ret;
+  int32_t *act;
+  float *h1, *h2, *out, *c1, *c2, *vout, *d1, *d2, *part;
+  double *stats;                   // policy loss, value loss, entropy (sums)
+  float *grad;                     // actor gradient, then the critic's
+};
+size_t train_scratch_bytes(const PolicyShape &pol, const PolicyShape &crit);
+TrainBufs train_bufs(uint8_t *base, const PolicyShape &pol, const PolicyShape &crit);
+void launch_a2c_update(const Dev &d, const TrainBufs &tb, float *critic, const PolicyShape &crit,
+                       uint32_t n, float lr, float c_v, float c_e, cudaStream_t st);
+
 // Landscape force -grad E(x') of the last n_steps ring rows (ws_force.cu).
 void launch_forces(const Dev &d, uint32_t n_steps, cudaStream_t st);
 

@@ -42,6 +42,9 @@ namespace {
 constexpr size_t kAlign = 256;
 inline size_t up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
+// The critic of WS_FLAG_TRAIN: the policy's widths with one output.
+PolicyShape critic_shape(const PolicyShape &p) { return PolicyShape{{p.w[0], p.w[1], p.w[2], 1}}; }
+
 ws_status fail(ws_ctx *c, ws_status s, const std::string &m) {
   if (c && c->err == WS_OK) {
     c->err = s;
@@ -63,7 +66,9 @@ ws_status validate(const ws_config *cfg) {
   if (cfg->ring_steps < 1 || cfg->episode_limit < 1) return WS_ERR_INVALID;
   if (cfg->hidden0 < 1 || cfg->hidden0 > 4096 || cfg->hidden1 < 1 || cfg->hidden1 > 4096)
     return WS_ERR_INVALID;
-  if (cfg->flags & ~(WS_FLAG_DEBUG_LOGITS | WS_FLAG_ENERGY_TARGET | WS_FLAG_FORCE))
+  if (cfg->flags & ~(WS_FLAG_DEBUG_LOGITS | WS_FLAG_ENERGY_TARGET | WS_FLAG_FORCE | WS_FLAG_TRAIN))
+    return WS_ERR_INVALID;
+  if ((cfg->flags & WS_FLAG_TRAIN) && cfg->env != WS_ENV_CONTROL && cfg->env != WS_ENV_ACROBOT)
     return WS_ERR_INVALID;
   if ((cfg->flags & WS_FLAG_FORCE) && cfg->env != WS_ENV_LANDSCAPE) return WS_ERR_INVALID;
   if ((cfg->flags & WS_FLAG_ENERGY_TARGET) &&
@@ -289,6 +294,12 @@ Layout make_layout(const ws_config *cfg, const std::vector<int32_t> &agents) {
     if (cfg->env == WS_ENV_ACROBOT) {
       L.scratch_pobs_off = o; o += up((size_t)kAcroObs * N * 4);  // the policy's input
     }
+  }
+  L.critic_off = L.train_off = o;
+  if (cfg->flags & WS_FLAG_TRAIN) {
+    const PolicyShape crit = critic_shape(L.pol);
+    L.critic_off = o; o += up(crit.count() * 4);
+    L.train_off = o; o += up(train_scratch_bytes(L.pol, crit));
   }
   L.state_bytes = o;
   size_t r = 0;
@@ -578,6 +589,8 @@ std::vector<Piece> state_pieces(ws_ctx *c, ws_field f) {
       v.push_back({S + L.state_off + up(D * N * 4), N * 4});
     }
     v.push_back({S + L.t_off, N * 4});
+  } else if (f == WS_F_CRITIC) {
+    if (c->cfg.flags & WS_FLAG_TRAIN) v.push_back({S + L.critic_off, critic_shape(L.pol).count() * 4});
   } else if (f == WS_F_PARAMS) {
     v.push_back({S + L.params_off, L.pol.count() * 4});
     if (L.env == WS_ENV_ECONOMY) v.push_back({S + L.params_planner_off, L.pol_planner.count() * 4});
@@ -714,6 +727,9 @@ ws_status ws_create(const ws_config *cfg, void *state_buf, size_t state_bytes, v
     }
   }
   launch_init_policy((float *)c->d.params, c->L.pol, cfg->param_seed, 0, c->stream);
+  if (cfg->flags & WS_FLAG_TRAIN)  // the critic: policy id 2
+    launch_init_policy((float *)(c->state + c->L.critic_off), critic_shape(c->L.pol),
+                       cfg->param_seed, 2, c->stream);
   if (cfg->env == WS_ENV_ECONOMY)
     launch_init_policy((float *)c->d.params_planner, c->L.pol_planner, cfg->param_seed, 1, c->stream);
   if (cfg->env == WS_ENV_LANDSCAPE) launch_init_landscape(c->d, cfg->param_seed, c->stream);
@@ -796,6 +812,31 @@ ws_status ws_returns(ws_ctx *c, uint32_t n) {
   return cuda_check(c, cudaGetLastError(), "returns");
 }
 
+ws_status ws_a2c_update(ws_ctx *c, uint32_t n, float lr, float c_v, float c_e, double *stats) {
+  if (!c) return WS_ERR_INVALID;
+  if (c->err != WS_OK) return c->err;
+  if (!(c->cfg.flags & WS_FLAG_TRAIN)) return WS_ERR_STATE;
+  if (n == 0 || n > c->k_host || n > c->L.ring_steps) return WS_ERR_RANGE;
+  if (!std::isfinite(lr) || !std::isfinite(c_v) || !std::isfinite(c_e)) return WS_ERR_INVALID;
+  const PolicyShape crit = critic_shape(c->L.pol);
+  const TrainBufs tb = train_bufs((uint8_t *)c->state + c->L.train_off, c->L.pol, crit);
+  launch_returns(c->d, n, c->stream);
+  launch_a2c_update(c->d, tb, (float *)(c->state + c->L.critic_off), crit, n, lr, c_v, c_e,
+                    c->stream);
+  ws_status s = cuda_check(c, cudaGetLastError(), "a2c update");
+  if (s == WS_OK) s = after_params_changed(c);
+  if (s == WS_OK && stats) {
+    double h[3];
+    s = cuda_check(c, cudaMemcpyAsync(h, tb.stats, sizeof(h), cudaMemcpyDeviceToHost, c->stream),
+                   "a2c stats");
+    if (s == WS_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream), "a2c stats sync");
+    const double R = (double)n * c->L.n_slots;
+    if (s == WS_OK)
+      for (int i = 0; i < 3; ++i) stats[i] = h[i] / R;
+  }
+  return s;
+}
+
 ws_status ws_forces(ws_ctx *c, uint32_t n) {
   if (!c) return WS_ERR_INVALID;
   if (c->err != WS_OK) return c->err;
@@ -814,7 +855,8 @@ ws_status ws_fetch_async(ws_ctx *c, ws_field f, uint64_t t0, uint32_t n, void *d
   if (!c || (!dst && dst_bytes)) return WS_ERR_INVALID;
   if (c->err != WS_OK) return c->err;
   const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  if (f == WS_F_STATE || f == WS_F_PARAMS || f == WS_F_ENV_PARAMS || f == WS_F_LOGITS) {
+  if (f == WS_F_STATE || f == WS_F_PARAMS || f == WS_F_ENV_PARAMS || f == WS_F_LOGITS ||
+      f == WS_F_CRITIC) {
     if (t0 != 0 || n != 0) return WS_ERR_INVALID;
     if (f == WS_F_LOGITS &&
         (use_tc_control(&c->cfg) || ((c->L.econ_fused || c->L.land_fused) && !c->d.dbg_logits)))
@@ -870,8 +912,10 @@ ws_status ws_fetch(ws_ctx *c, ws_field f, uint64_t t0, uint32_t n, void *dst, si
 ws_status ws_load(ws_ctx *c, ws_field f, const void *src, size_t src_bytes, int on_dev, uint64_t k) {
   if (!c || !src) return WS_ERR_INVALID;
   if (c->err != WS_OK) return c->err;
-  if (f != WS_F_STATE && f != WS_F_PARAMS && f != WS_F_ENV_PARAMS) return WS_ERR_INVALID;
+  if (f != WS_F_STATE && f != WS_F_PARAMS && f != WS_F_ENV_PARAMS && f != WS_F_CRITIC)
+    return WS_ERR_INVALID;
   if (f == WS_F_ENV_PARAMS && c->cfg.env != WS_ENV_LANDSCAPE) return WS_ERR_INVALID;
+  if (f == WS_F_CRITIC && !(c->cfg.flags & WS_FLAG_TRAIN)) return WS_ERR_INVALID;
   if (f == WS_F_STATE && k == UINT64_MAX) return WS_ERR_INVALID;
   std::vector<Piece> v = state_pieces(c, f);
   size_t tot = 0;

@@ -1,0 +1,102 @@
+"""GPU parity of the actor-critic update (ws_a2c_update) against the oracle's
+FP64 loss and gradients (pinned to finite differences and autograd): the
+update's parameter change over lr is the gradient of the mean loss over the
+ring's recorded rows, for the control env and the acrobot, on the FP32 and the
+BF16 paths; a roll-out after the update runs on the new parameters."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2408_00930_gb300 import warpsci as W
+from tests.gpu_common import TIE_BF16, need_gpu
+
+pytestmark = pytest.mark.gpu
+F32, BF16 = W.WS_PATH_BATCHED_FP32, W.WS_PATH_BATCHED_BF16
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return need_gpu()
+
+
+def run_update(env, path, n, T, h, lr, c_v, c_e, seed=3):
+    od, na = (4, 2) if env == W.WS_ENV_CONTROL else (6, 3)
+    r = W.Rollout(env, path, n, T, 25, h, h, param_seed=seed, flags=W.WS_FLAG_TRAIN, chunk_steps=10)
+    r.reset(seed + 1)
+    r.rollout(T)
+    pa = r.fetch_raw(W.WS_F_PARAMS, 4 * oracle.policy_param_count([od, h, h, na])).view(np.float32).copy()
+    pc = r.fetch_raw(W.WS_F_CRITIC, 4 * oracle.policy_param_count([od, h, h, 1])).view(np.float32).copy()
+    obs = r.fetch(W.WS_F_OBS, 0, T)                      # [T][od][n]
+    act = r.fetch(W.WS_F_ACTION, 0, T)
+    rew, done = r.fetch(W.WS_F_REWARD, 0, T), r.fetch(W.WS_F_DONE, 0, T)
+    stats = r.a2c_update(T, lr, c_v, c_e)
+    ret = r.fetch(W.WS_F_RETURN, 0, T)
+    pa2 = r.fetch_raw(W.WS_F_PARAMS, pa.nbytes).view(np.float32).copy()
+    pc2 = r.fetch_raw(W.WS_F_CRITIC, pc.nbytes).view(np.float32).copy()
+    rows = dict(obs=obs.transpose(0, 2, 1).reshape(-1, od).astype(np.float64),
+                act=act.reshape(-1), ret=ret.reshape(-1).astype(np.float64))
+    # the update's own returns scan (pinned elsewhere) against the oracle's
+    Go = oracle.returns(rew, done, float(np.float32(0.99)))
+    assert np.abs(ret - Go).max() <= 1e-6 * max(1.0, np.abs(Go).max())
+    return r, (pa, pc, pa2, pc2), rows, stats, (od, na)
+
+
+def check_grads(params, rows, stats, shape, h, lr, c_v, c_e):
+    pa, pc, pa2, pc2 = params
+    od, na = shape
+    st, ga, gc = oracle.a2c(pa, pc, rows["obs"], rows["act"], rows["ret"], h, h, na, c_v=c_v, c_e=c_e)
+    np.testing.assert_allclose(stats, st, rtol=1e-4, atol=1e-7)
+    for before, after, g in ((pa, pa2, ga), (pc, pc2, gc)):
+        step = (before.astype(np.float64) - after.astype(np.float64)) / lr
+        # after = fl(before - lr g): the subtraction loses up to half an ulp of the parameter
+        tol = 1e-4 * np.abs(g).max() + 0.6 * np.spacing(np.abs(before)).astype(np.float64) / lr
+        assert np.all(np.abs(step - g) <= tol), np.abs(step - g).max()
+        assert np.abs(g).max() > 0
+
+
+@pytest.mark.parametrize("env", [W.WS_ENV_CONTROL, W.WS_ENV_ACROBOT])
+def test_a2c_update_matches_oracle_fp32(torch, env):
+    n, T, h, lr, c_v, c_e = 300, 30, 64, 1.0, 0.5, 0.01   # 9,000 rows: two update chunks
+    r, params, rows, stats, shape = run_update(env, F32, n, T, h, lr, c_v, c_e)
+    check_grads(params, rows, stats, shape, h, lr, c_v, c_e)
+    r.close()
+
+
+def test_a2c_update_bf16_acrobot_and_next_rollout(torch):
+    n, T, h, lr, c_v, c_e = 257, 20, 64, 0.5, 0.5, 0.0
+    r, params, rows, stats, shape = run_update(W.WS_ENV_ACROBOT, BF16, n, T, h, lr, c_v, c_e, seed=8)
+    check_grads(params, rows, stats, shape, h, lr, c_v, c_e)
+    # the next step's draws follow the updated policy (BF16 images repacked)
+    k = r.k
+    r.step()
+    r.sync()
+    obs = r.fetch(W.WS_F_OBS, k, 1)[0].T.astype(np.float64)
+    act = r.fetch(W.WS_F_ACTION, k, 1)[0]
+    pa2 = params[2]
+    n_ok = 0
+    for e in range(n):
+        lg = oracle.mlp_forward([6, h, h, 3], pa2, obs[e], bf16_layers=0b010)
+        u = oracle.u01(int(oracle.draw(9, k, e, 0, oracle.TAG_ACTION, 0)[0]))
+        a_o, _, mg = oracle.sample_categorical(lg, u)
+        if mg >= TIE_BF16:
+            assert act[e] == a_o, e
+            n_ok += 1
+    assert n_ok > 0.8 * n
+    r.close()
+
+
+def test_a2c_errors(torch):
+    r = W.Rollout(W.WS_ENV_CONTROL, F32, 16, 4, 100, 16, 16)
+    r.rollout(2)
+    assert W.ws_a2c_update(r.ctx, 2, 0.1, 0.5, 0.0) == W.WS_ERR_STATE      # no WS_FLAG_TRAIN
+    r.close()
+    r = W.Rollout(W.WS_ENV_CONTROL, F32, 16, 4, 100, 16, 16, flags=W.WS_FLAG_TRAIN)
+    r.rollout(2)
+    assert W.ws_a2c_update(r.ctx, 3, 0.1, 0.5, 0.0) == W.WS_ERR_RANGE
+    assert W.ws_a2c_update(r.ctx, 2, float("nan"), 0.5, 0.0) == W.WS_ERR_INVALID
+    assert W.ws_a2c_update(r.ctx, 2, 0.1, 0.5, 0.0) == W.WS_OK
+    r.sync()
+    r.close()
+    cfg, _ = W.make_config(W.WS_ENV_LANDSCAPE, F32, 8, 4, 10, 16, 16, dim=8, n_gauss=16,
+                           flags=W.WS_FLAG_TRAIN)
+    assert W.ws_query_bytes(cfg)[0] == W.WS_ERR_INVALID                    # categorical envs only
