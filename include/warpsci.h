@@ -135,7 +135,7 @@ typedef enum {
 #define WS_FLAG_FORCE 4u
 /* ws_config.flags: the context also holds a critic (an MLP obs -> hidden0 ->
  * hidden1 -> 1, drawn from param_seed like the policy) and the scratch of
- * ws_a2c_update.  Control and acrobot envs (one categorical policy). */
+ * ws_a2c_update.  Control, acrobot and landscape envs (one policy each). */
 #define WS_FLAG_TRAIN 8u
 
 /* Roll-out configuration.  Slots: control and landscape have one agent per
@@ -201,7 +201,8 @@ ws_status ws_returns(ws_ctx *ctx, uint32_t n_steps);
 
 /* Actor-critic update on the last n_steps ring rows (steps k-n..k-1), in place
  * (paper Sec. 2 / App. B: the roll-out store feeds training on the GPU).
- * Advantage actor-critic with Monte-Carlo returns: the returns scan runs first
+ * Advantage actor-critic with Monte-Carlo returns (on policy: the ring's steps
+ * were sampled by the current parameters): the returns scan runs first
  * (into RETURN), then over the R = n_steps x n_slots rows (obs s, action a,
  * return G), with A = G - V(s) held constant in the policy's loss,
  *   L = (1/R) sum [ -A log pi(a|s) - c_e H(pi(.|s)) + c_v (G - V(s))^2 ],

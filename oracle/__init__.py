@@ -111,6 +111,8 @@ def _declare(L):
     L.or_returns.argtypes = [C.c_int, C.c_long, _P, _P, C.c_double, _P]
     L.or_a2c.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P, _P,
                          C.c_double, C.c_double, _P, _P, _P]
+    L.or_a2c_gauss.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P, _P,
+                               C.c_double, C.c_double, _P, _P, _P]
 
 
 def _ptr(a):
@@ -458,4 +460,21 @@ def a2c(actor, critic, obs, act, ret, h0, h1, n_act, c_v=0.5, c_e=0.0, adv=None,
     lib().or_a2c(R, od, n_act, h0, h1, _ptr(_arr(actor, np.float32)), _ptr(_arr(critic, np.float32)),
                  _ptr(o), _ptr(_arr(act, np.int32)), _ptr(_arr(ret, np.float64)),
                  _ptr(_arr(adv, np.float64)), float(c_v), float(c_e), _ptr(ga), _ptr(gc), _ptr(st))
+    return st, ga, gc
+
+
+def a2c_gauss(actor, critic, obs, z, ret, h0, h1, c_v=0.5, c_e=0.0, adv=None, grads=True):
+    """The actor-critic update for the diagonal Gaussian head (landscape): obs
+    and z (the normals the recorded samples used) [R][D]."""
+    o = _arr(obs, np.float64)
+    R, D = o.shape
+    na = policy_param_count([D, h0, h1, 2 * D])
+    nc = policy_param_count([D, h0, h1, 1])
+    ga = np.empty(na) if grads else None
+    gc = np.empty(nc) if grads else None
+    st = np.empty(3)
+    lib().or_a2c_gauss(R, D, h0, h1, _ptr(_arr(actor, np.float32)), _ptr(_arr(critic, np.float32)),
+                       _ptr(o), _ptr(_arr(z, np.float64)), _ptr(_arr(ret, np.float64)),
+                       _ptr(_arr(adv, np.float64)), float(c_v), float(c_e), _ptr(ga), _ptr(gc),
+                       _ptr(st))
     return st, ga, gc

@@ -1010,6 +1010,67 @@ void or_a2c(int R, int obs_dim, int n_act, int h0, int h1, const float *actor, c
   or_trace_free(&tc);
 }
 
+/* The same update for the diagonal Gaussian head (landscape): out = (mean,
+ * raw log sigma), log sigma = clamp(raw, -5, 2).  On policy, the recorded
+ * sample is x = mean + sigma z with the row's normals z [R][D], so at the
+ * current parameters log pi(x) = sum_j (-z_j^2 / 2 - log sigma_j - log(2 pi)/2),
+ * d log pi / d mean_j = z_j / sigma_j, d log pi / d raw_j = z_j^2 - 1 and
+ * H = sum_j (log sigma_j + (1 + log 2 pi) / 2), d H / d raw_j = 1 (both 0 where
+ * the clamp holds raw outside (-5, 2)). */
+void or_a2c_gauss(int R, int D, int h0, int h1, const float *actor, const float *critic,
+                  const double *obs, const double *z, const double *ret, const double *adv,
+                  double c_v, double c_e, double *grad_actor, double *grad_critic,
+                  double stats[3]) {
+  int32_t wa[4] = {D, h0, h1, 2 * D}, wc[4] = {D, h0, h1, 1};
+  long na = 0, nc = 0;
+  for (int l = 0; l < 3; ++l) {
+    na += (long)wa[l] * wa[l + 1] + wa[l + 1];
+    nc += (long)wc[l] * wc[l + 1] + wc[l + 1];
+  }
+  if (grad_actor) memset(grad_actor, 0, sizeof(double) * na);
+  if (grad_critic) memset(grad_critic, 0, sizeof(double) * nc);
+  or_trace ta, tc;
+  or_trace_alloc(&ta, wa);
+  or_trace_alloc(&tc, wc);
+  double *dl = (double *)malloc(sizeof(double) * 2 * D);
+  const double half_log_2pi = 0.5 * log(2.0 * M_PI);
+  double s_pg = 0.0, s_v = 0.0, s_h = 0.0;
+  for (int i = 0; i < R; ++i) {
+    or_mlp_trace(wa, actor, obs + (long)i * D, &ta);
+    or_mlp_trace(wc, critic, obs + (long)i * D, &tc);
+    const double *out = ta.a[3], *zi = z + (long)i * D;
+    const double V = tc.a[3][0];
+    const double A = adv ? adv[i] : ret[i] - V;
+    double logp = 0.0, H = 0.0;
+    for (int j = 0; j < D; ++j) {
+      const double raw = out[D + j];
+      const double ls = raw < -5.0 ? -5.0 : (raw > 2.0 ? 2.0 : raw);
+      const double sig = exp(ls);
+      const int free_ls = raw > -5.0 && raw < 2.0;
+      logp += -0.5 * zi[j] * zi[j] - ls - half_log_2pi;
+      H += ls + 0.5 + half_log_2pi;
+      dl[j] = -A * zi[j] / sig / R;
+      dl[D + j] = free_ls ? (-A * (zi[j] * zi[j] - 1.0) - c_e) / R : 0.0;
+    }
+    s_pg += -A * logp;
+    s_v += (ret[i] - V) * (ret[i] - V);
+    s_h += H;
+    if (grad_actor) or_mlp_backward(wa, actor, &ta, dl, grad_actor);
+    if (grad_critic) {
+      double dv = 2.0 * c_v * (V - ret[i]) / R;
+      or_mlp_backward(wc, critic, &tc, &dv, grad_critic);
+    }
+  }
+  if (stats) {
+    stats[0] = s_pg / R;
+    stats[1] = s_v / R;
+    stats[2] = s_h / R;
+  }
+  free(dl);
+  or_trace_free(&ta);
+  or_trace_free(&tc);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Discounted returns over a window of n_steps records ([n_steps][n_slots]):*/
 /*   G_t = r_t + gamma (1 - d_t) G_{t+1},  G_{n_steps} = 0.                 */

@@ -83,13 +83,8 @@ void launch_advance(const Dev &d, uint32_t n, cudaStream_t st);
 
 // ---- S7: discounted returns ----------------------------------------------
 void launch_returns(const Dev &d, uint32_t n_steps, cudaStream_t st);
-// Three-layer FP32 MLP (tanh, tanh, linear) on row-major or SoA inputs.
-void launch_mlp3_f32(const float *X, long ldr, long ldc, const float *params,
-                     const PolicyShape &sh, float *h0, float *h1, float *out, int M,
-                     cudaStream_t st);
-
 // ---- actor-critic update (ws_train.cu) ----------------------------------------
-constexpr int kTrainChunk = 8192;  // rows per chunk of the update
+constexpr int kTrainChunk = 65536;  // rows per chunk of the update
 struct TrainBufs {                 // per-chunk scratch in the state buffer
   float *x, *ret;
   int32_t *act;

@@ -912,12 +912,6 @@ void launch_plain_step(const Dev &d, uint32_t off, cudaStream_t st, const Branch
 
 void launch_advance(const Dev &d, uint32_t n, cudaStream_t st) { k_advance<<<1, 32, 0, st>>>(d, n); }
 
-void launch_mlp3_f32(const float *X, long ldr, long ldc, const float *params,
-                     const PolicyShape &sh, float *h0, float *h1, float *out, int M,
-                     cudaStream_t st) {
-  mlp3(X, ldr, ldc, params, sh, h0, h1, out, M, st);
-}
-
 void launch_returns(const Dev &d, uint32_t n_steps, cudaStream_t st) {
   if (d.n_slots % 4 == 0)  // every ring row starts on a 16-byte boundary
     k_returns<4, 32, 8><<<blocks(d.n_slots / 4, 32), 32, 0, st>>>(d, n_steps);

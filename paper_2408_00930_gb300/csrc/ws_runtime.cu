@@ -68,8 +68,7 @@ ws_status validate(const ws_config *cfg) {
     return WS_ERR_INVALID;
   if (cfg->flags & ~(WS_FLAG_DEBUG_LOGITS | WS_FLAG_ENERGY_TARGET | WS_FLAG_FORCE | WS_FLAG_TRAIN))
     return WS_ERR_INVALID;
-  if ((cfg->flags & WS_FLAG_TRAIN) && cfg->env != WS_ENV_CONTROL && cfg->env != WS_ENV_ACROBOT)
-    return WS_ERR_INVALID;
+  if ((cfg->flags & WS_FLAG_TRAIN) && cfg->env == WS_ENV_ECONOMY) return WS_ERR_INVALID;
   if ((cfg->flags & WS_FLAG_FORCE) && cfg->env != WS_ENV_LANDSCAPE) return WS_ERR_INVALID;
   if ((cfg->flags & WS_FLAG_ENERGY_TARGET) &&
       (cfg->env != WS_ENV_LANDSCAPE || !std::isfinite(cfg->energy_target)))

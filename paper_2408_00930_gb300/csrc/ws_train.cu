@@ -4,15 +4,15 @@
 // Paper grounding: Sec. 2 and App. B keep roll-out and training on the GPU,
 // the roll-out store feeding the trainer with no host round trip.  The update
 // is advantage actor-critic with Monte-Carlo returns: the actor is the roll-out
-// policy (categorical head), the critic an MLP of the same hidden widths with
-// one output, held in the context.  Over the R = n_steps x n_slots recorded
+// policy (categorical head, or the landscape's diagonal Gaussian head), the
+// critic an MLP of the same hidden widths with one output, held in the context.  Over the R = n_steps x n_slots recorded
 // rows (observation s, action a, return G from the returns scan):
 //   A = G - V(s) (a constant of the actor's loss),
 //   L = (1/R) sum [ -A log pi(a|s) - c_e H(pi(.|s)) + c_v (G - V(s))^2 ],
 // then one SGD step on both networks.
 //
 // FP32 SIMT throughout, in chunks of kTrainChunk rows: gather the chunk's rows from
-// the ring, forward both MLPs (the per-step path's dense kernel), the loss head
+// the ring, forward both MLPs keeping the activations, the loss head
 // (softmax, advantage, dL/dlogits, dL/dV), then the backward pass per layer:
 // weight gradients as row-sliced partial products summed in a fixed order
 // (deterministic), data gradients through W^T and tanh' = 1 - tanh^2.
@@ -22,8 +22,6 @@ namespace ws {
 
 namespace {
 
-constexpr int kTB = 64, kTK = 16;  // GEMM tiles: 64 x 64 outputs, K staged 16 at a time
-constexpr int kTT = 256;           // threads per GEMM block (4 x 4 outputs each)
 constexpr int kSliceRows = 512;    // rows per weight-gradient partial
 
 // Row i of the chunk starting at global row q0: (step index t, slot s) with
@@ -37,15 +35,49 @@ __global__ void k_a2c_gather(Dev d, uint32_t n, size_t q0, uint32_t rows, TrainB
   const int od = d.pol.w[0];
   for (int j = 0; j < od; ++j) tb.x[(size_t)i * od + j] = d.r_obs[(rowR * od + j) * S + s];
   tb.ret[i] = d.r_ret[rowR * S + s];
-  tb.act[i] = ((const int32_t *)d.r_act)[rowR * S + s];
+  if (d.env != WS_ENV_LANDSCAPE) tb.act[i] = ((const int32_t *)d.r_act)[rowR * S + s];
 }
 
-// Per row: softmax of the logits, the advantage, dL/dlogits and dL/dV (the
-// 1/R of the mean folded in), and the three loss terms (double atomics; they
-// are statistics only).
-__global__ void k_a2c_head(Dev d, uint32_t rows, double inv_r, float c_v, float c_e, TrainBufs tb) {
+// Per row: the advantage, dL/d(policy outputs) and dL/dV (the 1/R of the mean
+// folded in), and the three loss terms (double atomics; they are statistics
+// only).  Categorical head: softmax of the logits.  Diagonal Gaussian head
+// (landscape): outputs (mean, raw log sigma), log sigma = clamp(raw, -5, 2);
+// on policy the recorded sample is mean + sigma z with the row's Philox
+// normals z (redrawn here as the sampler drew them), so d log pi / d mean =
+// z / sigma and d log pi / d raw = z^2 - 1, and dH / d raw = 1, where the
+// clamp does not hold raw.
+__global__ void k_a2c_head(Dev d, uint32_t n, size_t q0, uint32_t rows, double inv_r, float c_v,
+                           float c_e, TrainBufs tb) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
+  if (d.env == WS_ENV_LANDSCAPE) {
+    const int D = (int)d.dim;
+    const size_t q = q0 + i, S = d.n_slots;
+    const uint32_t k = (uint32_t)(d.k[0] - n + q / S), e = (uint32_t)(q % S);
+    float *o = tb.out + (size_t)i * 2 * D;
+    const float V = tb.vout[i], G = tb.ret[i], A = G - V;
+    const float half_log_2pi = 0.91893853320467274f;
+    float logp = 0.f, H = 0.f;
+    for (int j = 0; j < D; j += 4) {
+      const uint4 r = draw(d.seed, k, e, 0, kTagAction, (uint32_t)(j >> 2));
+      const float2 p = box_muller(r.x, r.y), p2 = box_muller(r.z, r.w);
+      const float z4[4] = {p.x, p.y, p2.x, p2.y};
+      for (int u = 0; u < 4 && j + u < D; ++u) {
+        const float z = z4[u], raw = o[D + j + u];
+        const float ls = fminf(fmaxf(raw, -5.0f), 2.0f);
+        const bool free_ls = raw > -5.0f && raw < 2.0f;
+        logp += -0.5f * z * z - ls - half_log_2pi;
+        H += ls + 0.5f + half_log_2pi;
+        o[j + u] = (float)(-A * z / expf(ls) * inv_r);
+        o[D + j + u] = free_ls ? (float)((-A * (z * z - 1.f) - c_e) * inv_r) : 0.f;
+      }
+    }
+    tb.vout[i] = (float)(2.0 * c_v * (V - G) * inv_r);
+    atomicAdd(tb.stats + 0, -(double)A * logp);
+    atomicAdd(tb.stats + 1, (double)(G - V) * (G - V));
+    atomicAdd(tb.stats + 2, (double)H);
+    return;
+  }
   const int na = d.pol.w[3];
   float *lg = tb.out + (size_t)i * na;
   float m = lg[0];
@@ -71,100 +103,119 @@ __global__ void k_a2c_head(Dev d, uint32_t rows, double inv_r, float c_v, float 
   atomicAdd(tb.stats + 2, (double)H);
 }
 
-// Y[r][n] = (sum_k Dout[r][k] W[n][k]) * (1 - H[r][n]^2): the gradient at the
-// pre-activation of a tanh layer, W stored [n_in = N][n_out = K] row-major.
-__global__ __launch_bounds__(kTT) void k_bwd_data(const float *__restrict__ Dout,
-                                                   const float *__restrict__ W,
-                                                   const float *__restrict__ Hact,
-                                                   float *__restrict__ Y, int rows, int K, int N) {
-  __shared__ float As[kTK][kTB + 4];
-  __shared__ float Bs[kTK][kTB + 4];
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const long r0 = (long)blockIdx.x * kTB;
-  const int n0 = blockIdx.y * kTB;
-  float acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += kTK) {
-    for (int idx = tid; idx < kTB * kTK; idx += kTT) {
-      const int kk = idx % kTK, m = idx / kTK;
-      const long r = r0 + m;
-      As[kk][m] = (r < rows && k0 + kk < K) ? Dout[r * K + k0 + kk] : 0.f;
-      const int nn = n0 + m;
-      Bs[kk][m] = (nn < N && k0 + kk < K) ? W[(long)nn * K + k0 + kk] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < kTK; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
+// FP32 GEMM C[M][N] = sum_k A(m, k) B(k, n) over k in [k_lo, k_hi), with
+// A(m, k) = TA ? A[k lda + m] : A[m lda + k] and B(k, n) = TB ? B[n ldb + k] :
+// B[k ldb + n].  128 x 128 tiles, 8 x 8 outputs per thread (rows ty*4 + {0..3}
+// and 64 + ty*4 + {0..3}, columns likewise), K staged 8 at a time through two
+// shared-memory buffers.  Epilogues: the forward layer (+ bias, tanh or not),
+// the data gradient of a tanh layer (* (1 - H^2)), or none (a partial product
+// of row slice z, written at C + z slice_stride).
+enum { kEpiBiasTanh = 0, kEpiBias = 1, kEpiDTanh = 2, kEpiNone = 3 };
+constexpr int kGM = 128, kGN = 128, kGK = 8, kGT = 256;
+
+template <bool TA, bool TB, int EPI>
+__global__ __launch_bounds__(kGT) void k_sgemm(const float *__restrict__ A, int lda,
+                                                const float *__restrict__ B, int ldb,
+                                                float *__restrict__ C, int M, int N, int k_lo,
+                                                int k_hi, int k_slice, size_t slice_stride,
+                                                const float *__restrict__ aux) {
+  __shared__ __align__(16) float As[2][kGK][kGM];
+  __shared__ __align__(16) float Bs[2][kGK][kGN];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.x * kGM, n0 = blockIdx.y * kGN;
+  int kb = k_lo, ke = k_hi;
+  if (k_slice > 0) {  // weight gradients: block z takes rows [k_lo + z k_slice, +k_slice)
+    kb = k_lo + (int)blockIdx.z * k_slice;
+    ke = min(k_hi, kb + k_slice);
   }
+  // staging: 1,024 elements of each operand per K step, 4 per thread
+  float ra[4], rb[4];
+  auto load = [&](int k0) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const long r = r0 + ty * 4 + i;
-    if (r >= rows) continue;
+    for (int i = 0; i < 4; ++i) {
+      const int e = tid + i * kGT;
+      // A: m fastest when TA (m contiguous in memory), else k fastest
+      const int am = TA ? (e & (kGM - 1)) : (e >> 3), ak = TA ? (e >> 7) : (e & 7);
+      const int gm = m0 + am, gk = k0 + ak;
+      ra[i] = (gm < M && gk < ke) ? (TA ? A[(long)gk * lda + gm] : A[(long)gm * lda + gk]) : 0.f;
+      const int bn = TB ? (e >> 3) : (e & (kGN - 1)), bk = TB ? (e & 7) : (e >> 7);
+      const int gn = n0 + bn, gk2 = k0 + bk;
+      rb[i] = (gn < N && gk2 < ke) ? (TB ? B[(long)gn * ldb + gk2] : B[(long)gk2 * ldb + gn]) : 0.f;
+    }
+  };
+  auto store = [&](int buf) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = n0 + tx * 4 + j;
-      if (c >= N) continue;
-      const float h = Hact[r * N + c];
-      Y[r * N + c] = acc[i][j] * (1.f - h * h);
+    for (int i = 0; i < 4; ++i) {
+      const int e = tid + i * kGT;
+      const int am = TA ? (e & (kGM - 1)) : (e >> 3), ak = TA ? (e >> 7) : (e & 7);
+      As[buf][ak][am] = ra[i];
+      const int bn = TB ? (e >> 3) : (e & (kGN - 1)), bk = TB ? (e & 7) : (e >> 7);
+      Bs[buf][bk][bn] = rb[i];
+    }
+  };
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  int buf = 0;
+  if (kb < ke) {
+    load(kb);
+    store(0);
+  }
+  __syncthreads();
+  for (int k0 = kb; k0 < ke; k0 += kGK) {
+    const bool more = k0 + kGK < ke;
+    if (more) load(k0 + kGK);  // next tile's loads in flight during this tile's FMAs
+#pragma unroll
+    for (int kk = 0; kk < kGK; ++kk) {
+      const float4 a0 = *(const float4 *)&As[buf][kk][ty * 4];
+      const float4 a1 = *(const float4 *)&As[buf][kk][64 + ty * 4];
+      const float4 b0 = *(const float4 *)&Bs[buf][kk][tx * 4];
+      const float4 b1 = *(const float4 *)&Bs[buf][kk][64 + tx * 4];
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    if (more) {
+      store(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+  float *Cz = C + (k_slice > 0 ? (size_t)blockIdx.z * slice_stride : 0);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+      if (n >= N) continue;
+      float v = acc[i][j];
+      if (EPI == kEpiBiasTanh) v = tanhf(v + aux[n]);
+      if (EPI == kEpiBias) v = v + aux[n];
+      if (EPI == kEpiDTanh) {
+        const float h = aux[(size_t)m * N + n];
+        v = v * (1.f - h * h);
+      }
+      Cz[(size_t)m * N + n] = v;
     }
   }
 }
 
-// Partial weight gradient of slice z: P[z][m][n] = sum over the slice's rows r
-// of Ain[r][m] * Dout[r][n], with row m = M standing for the bias (Ain = 1).
-// The layer's parameters are laid out exactly so: W [M][N] then b [N].
-__global__ __launch_bounds__(kTT) void k_wgrad(const float *__restrict__ Ain,
-                                                const float *__restrict__ Dout,
-                                                float *__restrict__ P, int rows, int M, int N) {
-  __shared__ float As[kTK][kTB + 4];
-  __shared__ float Bs[kTK][kTB + 4];
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const int m0 = blockIdx.x * kTB, n0 = blockIdx.y * kTB;
-  const int rb = blockIdx.z * kSliceRows, re = min(rows, rb + kSliceRows);
-  float acc[4][4] = {};
-  for (int k0 = rb; k0 < re; k0 += kTK) {
-    for (int idx = tid; idx < kTB * kTK; idx += kTT) {
-      const int mm = idx % kTB, kk = idx / kTB;
-      const int r = k0 + kk, m = m0 + mm, nn = n0 + mm;
-      As[kk][mm] = (r < re && m <= M) ? (m == M ? 1.f : Ain[(long)r * M + m]) : 0.f;
-      Bs[kk][mm] = (r < re && nn < N) ? Dout[(long)r * N + nn] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < kTK; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-  float *out = P + (size_t)blockIdx.z * (M + 1) * N;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int m = m0 + ty * 4 + i;
-    if (m > M) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = n0 + tx * 4 + j;
-      if (c < N) out[(size_t)m * N + c] = acc[i][j];
-    }
-  }
+// Bias-gradient row of slice z: P[z][M][n] = sum over the slice's rows of D[r][n].
+__global__ void k_colsum_slices(const float *__restrict__ D, float *__restrict__ P, int rows, int M,
+                                int N) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x, z = blockIdx.y;
+  if (n >= N) return;
+  const int rb = z * kSliceRows, re = min(rows, rb + kSliceRows);
+  float s = 0.f;
+  for (int r = rb; r < re; ++r) s += D[(size_t)r * N + n];
+  P[((size_t)z * (M + 1) + M) * N + n] = s;
 }
 
 // grad[i] += sum_z P[z][i], the slices in order.
@@ -183,27 +234,53 @@ __global__ void k_sgd(float *p, const float *g, size_t n, float lr) {
 
 inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+inline dim3 ggrid(int M, int N, int z = 1) {
+  return dim3((unsigned)((M + kGM - 1) / kGM), (unsigned)((N + kGN - 1) / kGN), (unsigned)z);
+}
+
+// Forward of one three-layer MLP for a chunk (rows x w0 row-major input),
+// keeping the tanh activations h1, h2.
+void mlp_forward(const PolicyShape &sh, const float *params, const float *X, float *h1, float *h2,
+                 float *out, int rows, cudaStream_t st) {
+  const float *in[3] = {X, h1, h2};
+  float *o[3] = {h1, h2, out};
+  for (int l = 0; l < 3; ++l) {
+    const int K = sh.w[l], N = sh.w[l + 1];
+    const float *W = params + sh.layer_offset(l), *b = W + (size_t)K * N;
+    if (l < 2)
+      k_sgemm<false, false, kEpiBiasTanh><<<ggrid(rows, N), kGT, 0, st>>>(in[l], K, W, N, o[l], rows, N,
+                                                                          0, K, 0, 0, b);
+    else
+      k_sgemm<false, false, kEpiBias><<<ggrid(rows, N), kGT, 0, st>>>(in[l], K, W, N, o[l], rows, N, 0,
+                                                                      K, 0, 0, b);
+  }
+}
+
 // Backward through one three-layer MLP for a chunk: X [rows][w0], h1, h2 the
-// tanh activations, dout [rows][w3] the gradient at the output.
+// tanh activations, dout [rows][w3] the gradient at the output.  Per layer the
+// weight gradient as 512-row slice partials (and the bias row), summed into
+// grad in slice order, then the data gradient into the layer below.
 void mlp_backward(const PolicyShape &sh, const float *params, const float *X, const float *h1,
                   const float *h2, const float *dout, float *grad, float *d1, float *d2,
                   float *part, int rows, cudaStream_t st) {
   const int nz = (rows + kSliceRows - 1) / kSliceRows;
   const float *ain[3] = {X, h1, h2};
-  const float *dl[3] = {nullptr, d1, d2};
-  // layer 3, then the data gradient into layer 2, and so on
+  float *dl[3] = {nullptr, d1, d2};
   for (int l = 2; l >= 0; --l) {
     const int M = sh.w[l], N = sh.w[l + 1];
     const float *D = l == 2 ? dout : dl[l + 1];
-    dim3 g((unsigned)((M + 1 + kTB - 1) / kTB), (unsigned)((N + kTB - 1) / kTB), (unsigned)nz);
-    k_wgrad<<<g, kTT, 0, st>>>(ain[l], D, part, rows, M, N);
+    // P[z][m][n] = sum over slice z of Ain[r][m] D[r][n]; the partials of one
+    // slice are (M + 1) x N apart so that the bias row fits after them
     const size_t len = (size_t)(M + 1) * N;
+    k_sgemm<true, false, kEpiNone><<<ggrid(M, N, nz), kGT, 0, st>>>(ain[l], M, D, N, part, M, N, 0,
+                                                                    rows, kSliceRows, len, nullptr);
+    k_colsum_slices<<<dim3((unsigned)((N + 127) / 128), (unsigned)nz), 128, 0, st>>>(D, part, rows, M,
+                                                                                    N);
     k_reduce_slices<<<nblk(len, 256), 256, 0, st>>>(part, nz, len, grad + sh.layer_offset(l));
     if (l > 0) {
       // gradient at layer l's input pre-activation: (D W_l^T) * (1 - a_l^2)
-      dim3 gb((unsigned)((rows + kTB - 1) / kTB), (unsigned)((M + kTB - 1) / kTB));
-      k_bwd_data<<<gb, kTT, 0, st>>>(D, params + sh.layer_offset(l), ain[l], (float *)dl[l], rows, N,
-                                     M);
+      k_sgemm<false, true, kEpiDTanh><<<ggrid(rows, M), kGT, 0, st>>>(
+          D, N, params + sh.layer_offset(l), N, dl[l], rows, M, 0, N, 0, 0, ain[l]);
     }
   }
 }
@@ -284,9 +361,9 @@ void launch_a2c_update(const Dev &d, const TrainBufs &tb, float *critic, const P
     const int rows = (int)((R - q0) < (size_t)kTrainChunk ? (R - q0) : (size_t)kTrainChunk);
     k_a2c_gather<<<nblk(rows, 256), 256, 0, st>>>(d, n, q0, (uint32_t)rows, tb);
     // forward: actor and critic
-    launch_mlp3_f32(tb.x, pol.w[0], 1, d.params, pol, tb.h1, tb.h2, tb.out, rows, st);
-    launch_mlp3_f32(tb.x, pol.w[0], 1, critic, crit, tb.c1, tb.c2, tb.vout, rows, st);
-    k_a2c_head<<<nblk(rows, 256), 256, 0, st>>>(d, (uint32_t)rows, inv_r, c_v, c_e, tb);
+    mlp_forward(pol, d.params, tb.x, tb.h1, tb.h2, tb.out, rows, st);
+    mlp_forward(crit, critic, tb.x, tb.c1, tb.c2, tb.vout, rows, st);
+    k_a2c_head<<<nblk(rows, 256), 256, 0, st>>>(d, n, q0, (uint32_t)rows, inv_r, c_v, c_e, tb);
     mlp_backward(pol, d.params, tb.x, tb.h1, tb.h2, tb.out, ga, tb.d1, tb.d2, tb.part, rows, st);
     mlp_backward(crit, critic, tb.x, tb.c1, tb.c2, tb.vout, gc, tb.d1, tb.d2, tb.part, rows, st);
   }

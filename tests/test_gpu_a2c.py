@@ -1,8 +1,9 @@
 """GPU parity of the actor-critic update (ws_a2c_update) against the oracle's
 FP64 loss and gradients (pinned to finite differences and autograd): the
 update's parameter change over lr is the gradient of the mean loss over the
-ring's recorded rows, for the control env and the acrobot, on the FP32 and the
-BF16 paths; a roll-out after the update runs on the new parameters."""
+ring's recorded rows, for the control env, the acrobot (categorical heads) and
+the landscape (diagonal Gaussian head), on the FP32 and the BF16 paths; a
+roll-out after the update runs on the new parameters."""
 import numpy as np
 import pytest
 
@@ -56,7 +57,7 @@ def check_grads(params, rows, stats, shape, h, lr, c_v, c_e):
 
 @pytest.mark.parametrize("env", [W.WS_ENV_CONTROL, W.WS_ENV_ACROBOT])
 def test_a2c_update_matches_oracle_fp32(torch, env):
-    n, T, h, lr, c_v, c_e = 300, 30, 64, 1.0, 0.5, 0.01   # 9,000 rows: two update chunks
+    n, T, h, lr, c_v, c_e = 3000, 30, 64, 1.0, 0.5, 0.01  # 90,000 rows: two update chunks
     r, params, rows, stats, shape = run_update(env, F32, n, T, h, lr, c_v, c_e)
     check_grads(params, rows, stats, shape, h, lr, c_v, c_e)
     r.close()
@@ -97,6 +98,38 @@ def test_a2c_errors(torch):
     assert W.ws_a2c_update(r.ctx, 2, 0.1, 0.5, 0.0) == W.WS_OK
     r.sync()
     r.close()
-    cfg, _ = W.make_config(W.WS_ENV_LANDSCAPE, F32, 8, 4, 10, 16, 16, dim=8, n_gauss=16,
-                           flags=W.WS_FLAG_TRAIN)
-    assert W.ws_query_bytes(cfg)[0] == W.WS_ERR_INVALID                    # categorical envs only
+    cfg, _ = W.make_config(W.WS_ENV_ECONOMY, F32, 8, 4, 10, 16, 16, flags=W.WS_FLAG_TRAIN)
+    assert W.ws_query_bytes(cfg)[0] == W.WS_ERR_INVALID                    # one-policy envs only
+
+
+@pytest.mark.parametrize("path", [F32, BF16])
+def test_a2c_update_landscape_gaussian_head(torch, path):
+    D, M, n, T, h, lr, c_v, c_e = 8, 64, 200, 12, 256, 1.0, 0.5, 0.01
+    if path == F32:
+        h = 32
+    r = W.Rollout(W.WS_ENV_LANDSCAPE, path, n, T, 7, h, h, dim=D, n_gauss=M, param_seed=4,
+                  flags=W.WS_FLAG_TRAIN, chunk_steps=5)
+    r.reset(6)
+    r.rollout(T)
+    na = oracle.policy_param_count([D, h, h, 2 * D])
+    nc = oracle.policy_param_count([D, h, h, 1])
+    pa = r.fetch_raw(W.WS_F_PARAMS, 4 * na).view(np.float32).copy()
+    pc = r.fetch_raw(W.WS_F_CRITIC, 4 * nc).view(np.float32).copy()
+    obs = r.fetch(W.WS_F_OBS, 0, T)
+    stats = r.a2c_update(T, lr, c_v, c_e)
+    ret = r.fetch(W.WS_F_RETURN, 0, T)
+    pa2 = r.fetch_raw(W.WS_F_PARAMS, 4 * na).view(np.float32).copy()
+    pc2 = r.fetch_raw(W.WS_F_CRITIC, 4 * nc).view(np.float32).copy()
+    X = obs.transpose(0, 2, 1).reshape(-1, D).astype(np.float64)
+    Z = np.array([oracle.landscape_action_normals(6, t, e, D) for t in range(T) for e in range(n)])
+    st, ga, gc = oracle.a2c_gauss(pa, pc, X, Z, ret.reshape(-1).astype(np.float64), h, h,
+                                  c_v=c_v, c_e=c_e)
+    np.testing.assert_allclose(stats, st, rtol=1e-4, atol=1e-7)
+    for before, after, g in ((pa, pa2, ga), (pc, pc2, gc)):
+        step = (before.astype(np.float64) - after.astype(np.float64)) / lr
+        tol = 1e-4 * np.abs(g).max() + 0.6 * np.spacing(np.abs(before)).astype(np.float64) / lr
+        assert np.all(np.abs(step - g) <= tol), np.abs(step - g).max()
+    # the next roll-out runs on the updated policy
+    r.rollout(2)
+    r.sync()
+    r.close()

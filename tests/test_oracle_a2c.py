@@ -104,3 +104,55 @@ def test_a2c_zero_gradient_cases(orc):
     # c_v = 0: the critic gets no gradient whatever the returns
     _, _, gc = orc.a2c(actor, critic, obs, act, ret, h, h, na, c_v=0.0)
     assert np.all(gc == 0)
+
+
+def test_a2c_gauss_matches_torch_autograd(orc):
+    """Gaussian head: the loss written with torch.distributions at the sample
+    x = mean + sigma z (the clamp of log sigma included), autograd float64."""
+    torch = pytest.importorskip("torch")
+    g = inputs.rng(7)
+    D, h, R = 3, 8, 50
+    actor = inputs.policy_params(g, [D, h, h, 2 * D], scale=3.0)
+    critic = inputs.policy_params(g, [D, h, h, 1], scale=2.0)
+    obs, z, ret = g.normal(size=(R, D)), g.normal(size=(R, D)), g.normal(size=R)
+    c_v, c_e = 0.3, 0.02
+    st, ga, gc = orc.a2c_gauss(actor, critic, obs, z, ret, h, h, c_v=c_v, c_e=c_e)
+
+    def layers(p, w):
+        out, off = [], 0
+        for a, b in zip(w[:-1], w[1:]):
+            out.append(torch.tensor(p[off:off + a * b].reshape(a, b), dtype=torch.float64,
+                                    requires_grad=True))
+            out.append(torch.tensor(p[off + a * b:off + a * b + b], dtype=torch.float64,
+                                    requires_grad=True))
+            off += a * b + b
+        return out
+
+    def mlp(ps, x):
+        for i in range(3):
+            x = x @ ps[2 * i] + ps[2 * i + 1]
+            if i < 2:
+                x = torch.tanh(x)
+        return x
+
+    pa, pc = layers(actor, [D, h, h, 2 * D]), layers(critic, [D, h, h, 1])
+    x = torch.tensor(obs)
+    out, v = mlp(pa, x), mlp(pc, x)[:, 0]
+    mu, ls = out[:, :D], torch.clamp(out[:, D:], -5.0, 2.0)
+    sample = (mu + ls.exp() * torch.tensor(z)).detach()     # the recorded sample
+    dist = torch.distributions.Normal(mu, ls.exp())
+    logp = dist.log_prob(sample).sum(1)
+    ent = dist.entropy().sum(1)
+    G = torch.tensor(ret)
+    A = (G - v).detach()
+    loss = (-A * logp).mean() + c_v * ((G - v) ** 2).mean() - c_e * ent.mean()
+    loss.backward()
+    ref_a = np.concatenate([t.grad.numpy().ravel() for t in pa])
+    ref_c = np.concatenate([t.grad.numpy().ravel() for t in pc])
+    np.testing.assert_allclose(ga, ref_a, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(gc, ref_c, rtol=1e-9, atol=1e-12)
+    assert st[0] == pytest.approx(float((-A * logp).mean().detach()), rel=1e-12)
+    assert st[2] == pytest.approx(float(ent.mean().detach()), rel=1e-12)
+    # the clamp really binds somewhere in this draw
+    raw = out[:, D:].detach().numpy()
+    assert ((raw < -5) | (raw > 2)).any()
