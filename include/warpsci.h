@@ -100,6 +100,7 @@ typedef enum { WS_PATH_PLAIN_FP32 = 0, WS_PATH_BATCHED_FP32 = 1, WS_PATH_BATCHED
  *   ENV_PARAMS  landscape: f32 centres[M][dim], f32 widths[M], f32 amps[M];
  *               economy:   i32 agents_per_env[n_envs]
  *   CRITIC  f32 critic parameters (WS_FLAG_TRAIN), laid out as PARAMS
+ *           (economy: the agents' critic then the planner's)
  *   LOGITS  f32 [n_slots][n_out] policy outputs of the last step (plain and
  *           batched-FP32 paths, the economy's per-layer BF16 path, and its
  *           fused kernel with WS_FLAG_DEBUG_LOGITS)                         */
@@ -133,9 +134,10 @@ typedef enum {
 /* ws_config.flags: the ring also holds the landscape FORCE field (D floats
  * per slot-step), written by ws_forces.  Landscape only. */
 #define WS_FLAG_FORCE 4u
-/* ws_config.flags: the context also holds a critic (an MLP obs -> hidden0 ->
- * hidden1 -> 1, drawn from param_seed like the policy) and the scratch of
- * ws_a2c_update.  Control, acrobot and landscape envs (one policy each). */
+/* ws_config.flags: the context also holds a critic per policy (an MLP obs ->
+ * hidden0 -> hidden1 -> 1, drawn from param_seed like the policies; the
+ * economy's agents and planners have one each) and the scratch of
+ * ws_a2c_update. */
 #define WS_FLAG_TRAIN 8u
 
 /* Roll-out configuration.  Slots: control and landscape have one agent per
@@ -207,8 +209,10 @@ ws_status ws_returns(ws_ctx *ctx, uint32_t n_steps);
  * return G), with A = G - V(s) held constant in the policy's loss,
  *   L = (1/R) sum [ -A log pi(a|s) - c_e H(pi(.|s)) + c_v (G - V(s))^2 ],
  * and one SGD step of rate lr on the policy and the critic (FP32; the BF16
- * operand images are repacked).  stats (host, may be NULL; the call then
- * waits for the stream): the means of -A log pi, (G - V)^2 and H.  Needs
+ * operand images are repacked).  The economy's agents (slots of agents) and
+ * planner (planner slots) are two such updates, each the mean over its own
+ * rows.  stats (host, may be NULL; the call then waits for the stream): the
+ * means over all rows of -A log pi, (G - V)^2 and H.  Needs
  * WS_FLAG_TRAIN (WS_ERR_STATE); n_steps <= min(k, ring_steps) (WS_ERR_RANGE). */
 ws_status ws_a2c_update(ws_ctx *ctx, uint32_t n_steps, float lr, float c_v, float c_e,
                         double *stats);

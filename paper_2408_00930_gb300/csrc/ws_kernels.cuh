@@ -92,9 +92,15 @@ struct TrainBufs {                 // per-chunk scratch in the state buffer
   double *stats;                   // policy loss, value loss, entropy (sums)
   float *grad;                     // actor gradient, then the critic's
 };
-size_t train_scratch_bytes(const PolicyShape &pol, const PolicyShape &crit);
-TrainBufs train_bufs(uint8_t *base, const PolicyShape &pol, const PolicyShape &crit);
-void launch_a2c_update(const Dev &d, const TrainBufs &tb, float *critic, const PolicyShape &crit,
+struct TrainGroup {  // one policy and its critic, on slots [slot0, slot0 + n_slots) of every step
+  float *params, *critic;
+  PolicyShape pol, crit;
+  uint32_t slot0, n_slots;
+};
+// Scratch sized for the widest policy of the context (and its critic).
+size_t train_scratch_bytes(const PolicyShape &pol);
+TrainBufs train_bufs(uint8_t *base, const PolicyShape &pol);
+void launch_a2c_update(const Dev &d, const TrainBufs &tb, const TrainGroup *groups, int n_groups,
                        uint32_t n, float lr, float c_v, float c_e, cudaStream_t st);
 
 // Landscape force -grad E(x') of the last n_steps ring rows (ws_force.cu).

@@ -68,7 +68,6 @@ ws_status validate(const ws_config *cfg) {
     return WS_ERR_INVALID;
   if (cfg->flags & ~(WS_FLAG_DEBUG_LOGITS | WS_FLAG_ENERGY_TARGET | WS_FLAG_FORCE | WS_FLAG_TRAIN))
     return WS_ERR_INVALID;
-  if ((cfg->flags & WS_FLAG_TRAIN) && cfg->env == WS_ENV_ECONOMY) return WS_ERR_INVALID;
   if ((cfg->flags & WS_FLAG_FORCE) && cfg->env != WS_ENV_LANDSCAPE) return WS_ERR_INVALID;
   if ((cfg->flags & WS_FLAG_ENERGY_TARGET) &&
       (cfg->env != WS_ENV_LANDSCAPE || !std::isfinite(cfg->energy_target)))
@@ -296,9 +295,11 @@ Layout make_layout(const ws_config *cfg, const std::vector<int32_t> &agents) {
   }
   L.critic_off = L.train_off = o;
   if (cfg->flags & WS_FLAG_TRAIN) {
-    const PolicyShape crit = critic_shape(L.pol);
-    L.critic_off = o; o += up(crit.count() * 4);
-    L.train_off = o; o += up(train_scratch_bytes(L.pol, crit));
+    // critics: the policy's (agents'), then the planner's
+    L.critic_off = o;
+    o += up(critic_shape(L.pol).count() * 4);
+    if (cfg->env == WS_ENV_ECONOMY) o += up(critic_shape(L.pol_planner).count() * 4);
+    L.train_off = o; o += up(train_scratch_bytes(L.pol));
   }
   L.state_bytes = o;
   size_t r = 0;
@@ -589,7 +590,12 @@ std::vector<Piece> state_pieces(ws_ctx *c, ws_field f) {
     }
     v.push_back({S + L.t_off, N * 4});
   } else if (f == WS_F_CRITIC) {
-    if (c->cfg.flags & WS_FLAG_TRAIN) v.push_back({S + L.critic_off, critic_shape(L.pol).count() * 4});
+    if (c->cfg.flags & WS_FLAG_TRAIN) {
+      v.push_back({S + L.critic_off, critic_shape(L.pol).count() * 4});
+      if (L.env == WS_ENV_ECONOMY)
+        v.push_back({S + L.critic_off + up(critic_shape(L.pol).count() * 4),
+                     critic_shape(L.pol_planner).count() * 4});
+    }
   } else if (f == WS_F_PARAMS) {
     v.push_back({S + L.params_off, L.pol.count() * 4});
     if (L.env == WS_ENV_ECONOMY) v.push_back({S + L.params_planner_off, L.pol_planner.count() * 4});
@@ -726,9 +732,13 @@ ws_status ws_create(const ws_config *cfg, void *state_buf, size_t state_bytes, v
     }
   }
   launch_init_policy((float *)c->d.params, c->L.pol, cfg->param_seed, 0, c->stream);
-  if (cfg->flags & WS_FLAG_TRAIN)  // the critic: policy id 2
+  if (cfg->flags & WS_FLAG_TRAIN) {  // the critics: policy ids 2 (and 3, the planner's)
     launch_init_policy((float *)(c->state + c->L.critic_off), critic_shape(c->L.pol),
                        cfg->param_seed, 2, c->stream);
+    if (cfg->env == WS_ENV_ECONOMY)
+      launch_init_policy((float *)(c->state + c->L.critic_off + up(critic_shape(c->L.pol).count() * 4)),
+                         critic_shape(c->L.pol_planner), cfg->param_seed, 3, c->stream);
+  }
   if (cfg->env == WS_ENV_ECONOMY)
     launch_init_policy((float *)c->d.params_planner, c->L.pol_planner, cfg->param_seed, 1, c->stream);
   if (cfg->env == WS_ENV_LANDSCAPE) launch_init_landscape(c->d, cfg->param_seed, c->stream);
@@ -817,11 +827,20 @@ ws_status ws_a2c_update(ws_ctx *c, uint32_t n, float lr, float c_v, float c_e, d
   if (!(c->cfg.flags & WS_FLAG_TRAIN)) return WS_ERR_STATE;
   if (n == 0 || n > c->k_host || n > c->L.ring_steps) return WS_ERR_RANGE;
   if (!std::isfinite(lr) || !std::isfinite(c_v) || !std::isfinite(c_e)) return WS_ERR_INVALID;
-  const PolicyShape crit = critic_shape(c->L.pol);
-  const TrainBufs tb = train_bufs((uint8_t *)c->state + c->L.train_off, c->L.pol, crit);
+  const Layout &L = c->L;
+  const TrainBufs tb = train_bufs((uint8_t *)c->state + L.train_off, L.pol);
+  float *crit0 = (float *)(c->state + L.critic_off);
+  TrainGroup g[2];
+  int ng = 1;
+  g[0] = TrainGroup{(float *)c->d.params, crit0, L.pol, critic_shape(L.pol), 0u, L.n_agent_slots};
+  if (L.env == WS_ENV_ECONOMY) {  // agents on slots [0, Sa), planners on [Sa, S)
+    g[1] = TrainGroup{(float *)c->d.params_planner,
+                      (float *)(c->state + L.critic_off + up(critic_shape(L.pol).count() * 4)),
+                      L.pol_planner, critic_shape(L.pol_planner), L.n_agent_slots, L.n_envs};
+    ng = 2;
+  }
   launch_returns(c->d, n, c->stream);
-  launch_a2c_update(c->d, tb, (float *)(c->state + c->L.critic_off), crit, n, lr, c_v, c_e,
-                    c->stream);
+  launch_a2c_update(c->d, tb, g, ng, n, lr, c_v, c_e, c->stream);
   ws_status s = cuda_check(c, cudaGetLastError(), "a2c update");
   if (s == WS_OK) s = after_params_changed(c);
   if (s == WS_OK && stats) {

@@ -5,7 +5,8 @@
 // the roll-out store feeding the trainer with no host round trip.  The update
 // is advantage actor-critic with Monte-Carlo returns: the actor is the roll-out
 // policy (categorical head, or the landscape's diagonal Gaussian head), the
-// critic an MLP of the same hidden widths with one output, held in the context.  Over the R = n_steps x n_slots recorded
+// critic an MLP of the same hidden widths with one output, held in the context;
+// the economy's agents and planners are two such pairs, each on its own slots.  Over the R = n_steps x n_slots recorded
 // rows (observation s, action a, return G from the returns scan):
 //   A = G - V(s) (a constant of the actor's loss),
 //   L = (1/R) sum [ -A log pi(a|s) - c_e H(pi(.|s)) + c_v (G - V(s))^2 ],
@@ -24,15 +25,15 @@ namespace {
 
 constexpr int kSliceRows = 512;    // rows per weight-gradient partial
 
-// Row i of the chunk starting at global row q0: (step index t, slot s) with
-// q = t * S + s over the last n steps.
-__global__ void k_a2c_gather(Dev d, uint32_t n, size_t q0, uint32_t rows, TrainBufs tb) {
+// Row i of the chunk starting at global row q0 of a group: (step index t,
+// slot slot0 + s) with q = t * ns + s over the last n steps.
+__global__ void k_a2c_gather(Dev d, uint32_t n, size_t q0, uint32_t rows, uint32_t slot0,
+                             uint32_t ns, int od, TrainBufs tb) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
   const size_t q = q0 + i, S = d.n_slots;
-  const uint64_t k = d.k[0] - n + q / S;
-  const size_t rowR = (size_t)(k % d.ring_steps), s = q % S;
-  const int od = d.pol.w[0];
+  const uint64_t k = d.k[0] - n + q / ns;
+  const size_t rowR = (size_t)(k % d.ring_steps), s = slot0 + q % ns;
   for (int j = 0; j < od; ++j) tb.x[(size_t)i * od + j] = d.r_obs[(rowR * od + j) * S + s];
   tb.ret[i] = d.r_ret[rowR * S + s];
   if (d.env != WS_ENV_LANDSCAPE) tb.act[i] = ((const int32_t *)d.r_act)[rowR * S + s];
@@ -46,14 +47,14 @@ __global__ void k_a2c_gather(Dev d, uint32_t n, size_t q0, uint32_t rows, TrainB
 // normals z (redrawn here as the sampler drew them), so d log pi / d mean =
 // z / sigma and d log pi / d raw = z^2 - 1, and dH / d raw = 1, where the
 // clamp does not hold raw.
-__global__ void k_a2c_head(Dev d, uint32_t n, size_t q0, uint32_t rows, double inv_r, float c_v,
-                           float c_e, TrainBufs tb) {
+__global__ void k_a2c_head(Dev d, uint32_t n, size_t q0, uint32_t rows, uint32_t ns, int na,
+                           double inv_r, float c_v, float c_e, TrainBufs tb) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
-  if (d.env == WS_ENV_LANDSCAPE) {
+  if (d.env == WS_ENV_LANDSCAPE) {  // one group: every slot
     const int D = (int)d.dim;
-    const size_t q = q0 + i, S = d.n_slots;
-    const uint32_t k = (uint32_t)(d.k[0] - n + q / S), e = (uint32_t)(q % S);
+    const size_t q = q0 + i;
+    const uint32_t k = (uint32_t)(d.k[0] - n + q / ns), e = (uint32_t)(q % ns);
     float *o = tb.out + (size_t)i * 2 * D;
     const float V = tb.vout[i], G = tb.ret[i], A = G - V;
     const float half_log_2pi = 0.91893853320467274f;
@@ -78,7 +79,6 @@ __global__ void k_a2c_head(Dev d, uint32_t n, size_t q0, uint32_t rows, double i
     atomicAdd(tb.stats + 2, (double)H);
     return;
   }
-  const int na = d.pol.w[3];
   float *lg = tb.out + (size_t)i * na;
   float m = lg[0];
   for (int c = 1; c < na; ++c) m = fmaxf(m, lg[c]);
@@ -287,7 +287,8 @@ void mlp_backward(const PolicyShape &sh, const float *params, const float *X, co
 
 }  // namespace
 
-size_t train_scratch_bytes(const PolicyShape &pol, const PolicyShape &crit) {
+size_t train_scratch_bytes(const PolicyShape &pol) {
+  const PolicyShape crit{{pol.w[0], pol.w[1], pol.w[2], 1}};
   const size_t CH = kTrainChunk, w0 = pol.w[0], H0 = pol.w[1], H1 = pol.w[2], NA = pol.w[3];
   const size_t hmax = H0 > H1 ? H0 : H1;
   const size_t nz = (CH + kSliceRows - 1) / kSliceRows;
@@ -315,7 +316,8 @@ size_t train_scratch_bytes(const PolicyShape &pol, const PolicyShape &crit) {
   return b;
 }
 
-TrainBufs train_bufs(uint8_t *base, const PolicyShape &pol, const PolicyShape &crit) {
+TrainBufs train_bufs(uint8_t *base, const PolicyShape &pol) {
+  const PolicyShape crit{{pol.w[0], pol.w[1], pol.w[2], 1}};
   const size_t CH = kTrainChunk, w0 = pol.w[0], H0 = pol.w[1], H1 = pol.w[2], NA = pol.w[3];
   const size_t hmax = H0 > H1 ? H0 : H1;
   const size_t nz = (CH + kSliceRows - 1) / kSliceRows;
@@ -348,27 +350,33 @@ TrainBufs train_bufs(uint8_t *base, const PolicyShape &pol, const PolicyShape &c
   return t;
 }
 
-void launch_a2c_update(const Dev &d, const TrainBufs &tb, float *critic, const PolicyShape &crit,
+// Per group (the economy: agents, then planners; else one group of all
+// slots): gradients over the group's rows in chunks, then the SGD step.
+void launch_a2c_update(const Dev &d, const TrainBufs &tb, const TrainGroup *groups, int n_groups,
                        uint32_t n, float lr, float c_v, float c_e, cudaStream_t st) {
-  const PolicyShape &pol = d.pol;
-  const size_t R = (size_t)n * d.n_slots;
-  const size_t na = pol.count(), nc = crit.count();
-  float *ga = tb.grad, *gc = tb.grad + na;
-  cudaMemsetAsync(tb.grad, 0, (na + nc) * 4, st);
   cudaMemsetAsync(tb.stats, 0, 3 * 8, st);
-  const double inv_r = 1.0 / (double)R;
-  for (size_t q0 = 0; q0 < R; q0 += kTrainChunk) {
-    const int rows = (int)((R - q0) < (size_t)kTrainChunk ? (R - q0) : (size_t)kTrainChunk);
-    k_a2c_gather<<<nblk(rows, 256), 256, 0, st>>>(d, n, q0, (uint32_t)rows, tb);
-    // forward: actor and critic
-    mlp_forward(pol, d.params, tb.x, tb.h1, tb.h2, tb.out, rows, st);
-    mlp_forward(crit, critic, tb.x, tb.c1, tb.c2, tb.vout, rows, st);
-    k_a2c_head<<<nblk(rows, 256), 256, 0, st>>>(d, n, q0, (uint32_t)rows, inv_r, c_v, c_e, tb);
-    mlp_backward(pol, d.params, tb.x, tb.h1, tb.h2, tb.out, ga, tb.d1, tb.d2, tb.part, rows, st);
-    mlp_backward(crit, critic, tb.x, tb.c1, tb.c2, tb.vout, gc, tb.d1, tb.d2, tb.part, rows, st);
+  for (int gi = 0; gi < n_groups; ++gi) {
+    const TrainGroup &G = groups[gi];
+    const size_t R = (size_t)n * G.n_slots;
+    const size_t na = G.pol.count(), nc = G.crit.count();
+    float *ga = tb.grad, *gc = tb.grad + na;
+    cudaMemsetAsync(tb.grad, 0, (na + nc) * 4, st);
+    const double inv_r = 1.0 / (double)R;
+    for (size_t q0 = 0; q0 < R; q0 += kTrainChunk) {
+      const int rows = (int)((R - q0) < (size_t)kTrainChunk ? (R - q0) : (size_t)kTrainChunk);
+      k_a2c_gather<<<nblk(rows, 256), 256, 0, st>>>(d, n, q0, (uint32_t)rows, G.slot0, G.n_slots,
+                                                    G.pol.w[0], tb);
+      mlp_forward(G.pol, G.params, tb.x, tb.h1, tb.h2, tb.out, rows, st);
+      mlp_forward(G.crit, G.critic, tb.x, tb.c1, tb.c2, tb.vout, rows, st);
+      k_a2c_head<<<nblk(rows, 256), 256, 0, st>>>(d, n, q0, (uint32_t)rows, G.n_slots, G.pol.w[3],
+                                                  inv_r, c_v, c_e, tb);
+      mlp_backward(G.pol, G.params, tb.x, tb.h1, tb.h2, tb.out, ga, tb.d1, tb.d2, tb.part, rows, st);
+      mlp_backward(G.crit, G.critic, tb.x, tb.c1, tb.c2, tb.vout, gc, tb.d1, tb.d2, tb.part, rows,
+                   st);
+    }
+    k_sgd<<<nblk(na, 256), 256, 0, st>>>(G.params, ga, na, lr);
+    k_sgd<<<nblk(nc, 256), 256, 0, st>>>(G.critic, gc, nc, lr);
   }
-  k_sgd<<<nblk(na, 256), 256, 0, st>>>((float *)d.params, ga, na, lr);
-  k_sgd<<<nblk(nc, 256), 256, 0, st>>>(critic, gc, nc, lr);
 }
 
 }  // namespace ws

@@ -98,8 +98,8 @@ def test_a2c_errors(torch):
     assert W.ws_a2c_update(r.ctx, 2, 0.1, 0.5, 0.0) == W.WS_OK
     r.sync()
     r.close()
-    cfg, _ = W.make_config(W.WS_ENV_ECONOMY, F32, 8, 4, 10, 16, 16, flags=W.WS_FLAG_TRAIN)
-    assert W.ws_query_bytes(cfg)[0] == W.WS_ERR_INVALID                    # one-policy envs only
+    cfg, _ = W.make_config(W.WS_ENV_CONTROL, F32, 8, 4, 10, 16, 16, flags=W.WS_FLAG_TRAIN | 64)
+    assert W.ws_query_bytes(cfg)[0] == W.WS_ERR_INVALID                    # unknown flag
 
 
 @pytest.mark.parametrize("path", [F32, BF16])
@@ -133,3 +133,42 @@ def test_a2c_update_landscape_gaussian_head(torch, path):
     r.rollout(2)
     r.sync()
     r.close()
+
+
+@pytest.mark.parametrize("path", [F32, BF16])
+def test_a2c_update_economy_agents_and_planner(torch, path):
+    """Two updates in one call: the agents' policy and critic on the agent
+    slots, the planner's on the planner slots, each the mean over its rows."""
+    n_env, T, lr, c_v, c_e = 40, 12, 1.0, 0.5, 0.01
+    counts = [oracle.econ_agent_count(5, e) for e in range(n_env)]
+    Sa = sum(counts)
+    r = W.Rollout(W.WS_ENV_ECONOMY, path, n_env, T, 540, 128, 128, param_seed=5,
+                  flags=W.WS_FLAG_TRAIN, chunk_steps=6)
+    r.reset(2)
+    r.rollout(T)
+    AW, PW = [16, 128, 128, 20], [16, 128, 128, 10]
+    na, npl = oracle.policy_param_count(AW), oracle.policy_param_count(PW)
+    nca, ncp = oracle.policy_param_count([16, 128, 128, 1]), oracle.policy_param_count([16, 128, 128, 1])
+    par = r.fetch_raw(W.WS_F_PARAMS, 4 * (na + npl)).view(np.float32).copy()
+    cri = r.fetch_raw(W.WS_F_CRITIC, 4 * (nca + ncp)).view(np.float32).copy()
+    obs, act = r.fetch(W.WS_F_OBS, 0, T), r.fetch(W.WS_F_ACTION, 0, T)
+    stats = r.a2c_update(T, lr, c_v, c_e)
+    ret = r.fetch(W.WS_F_RETURN, 0, T)
+    par2 = r.fetch_raw(W.WS_F_PARAMS, par.nbytes).view(np.float32).copy()
+    cri2 = r.fetch_raw(W.WS_F_CRITIC, cri.nbytes).view(np.float32).copy()
+    r.close()
+    tot = np.zeros(3)
+    for sl, pw, p0, c0, nap, ncr in ((slice(0, Sa), AW, 0, 0, na, nca),
+                                     (slice(Sa, Sa + n_env), PW, na, nca, npl, ncp)):
+        X = obs[:, :, sl].transpose(0, 2, 1).reshape(-1, 16).astype(np.float64)
+        A = act[:, sl].reshape(-1)
+        G = ret[:, sl].reshape(-1).astype(np.float64)
+        st, ga, gc = oracle.a2c(par[p0:p0 + nap], cri[c0:c0 + ncr], X, A, G, 128, 128, pw[3],
+                                c_v=c_v, c_e=c_e)
+        tot += st * len(G)
+        for before, after, g in ((par[p0:p0 + nap], par2[p0:p0 + nap], ga),
+                                 (cri[c0:c0 + ncr], cri2[c0:c0 + ncr], gc)):
+            step = (before.astype(np.float64) - after.astype(np.float64)) / lr
+            tol = 1e-4 * np.abs(g).max() + 0.6 * np.spacing(np.abs(before)).astype(np.float64) / lr
+            assert np.all(np.abs(step - g) <= tol), np.abs(step - g).max()
+    np.testing.assert_allclose(stats, tot / (T * (Sa + n_env)), rtol=1e-4, atol=1e-7)
