@@ -559,8 +559,9 @@ def main():
         # bf16x2 / f16x2 form).  SFU results per agent-step, counted from the
         # kernels' arithmetic:
         #   control    H0 + H1 tanh (+ one exp for the two-way softmax)
-        #   acrobot    H0 + H1 tanh, 3 exp and 1 log (the RK4's sin / cos are
-        #              CUDA's accurate software functions, on the FMA pipe)
+        #   acrobot    H0 + H1 tanh, 3 exp and 1 log, and 22 sin / cos (the
+        #              observation's two pairs, four RK4 stages of one pair and
+        #              two sines, the terminal height's two cosines)
         #   economy    agent: H0 + H1 tanh, 20 exp, 1 log; planner: H0 + H1
         #              tanh, 10 exp
         #   landscape  H0 + H1 tanh, M exp2 (one per Gaussian), D exp (sigma),
@@ -575,7 +576,7 @@ def main():
         if wl["env"] == 0:
             per_step, op, kern = n_slots * (H + 1), "tanh (and exp) on the SFU", "ws_control_tc"
         elif wl["env"] == 3:
-            per_step, op, kern = n_slots * (H + 4), "tanh, exp, log on the SFU", \
+            per_step, op, kern = n_slots * (H + 26), "tanh, exp, log, sin, cos on the SFU", \
                 "ws_control_tc (acrobot)"
         elif wl["env"] == 1:
             n_pl = wl["n_envs"]

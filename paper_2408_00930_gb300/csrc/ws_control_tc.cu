@@ -433,8 +433,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       float ob[E::OBS];  // this step's observation (the record)
       if (h == 0) {
         if constexpr (ACRO) {
-          sincosf(x, &ob[1], &ob[0]);  // (th1, th2, w1, w2) in (x, v, th, w)
-          sincosf(v, &ob[3], &ob[2]);
+          acro_sincos<true>(x, &ob[1], &ob[0]);  // (th1, th2, w1, w2) in (x, v, th, w)
+          acro_sincos<true>(v, &ob[3], &ob[2]);
           ob[4] = th;
           ob[5] = w;
           float oh[6];
@@ -585,8 +585,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           ns[1] = v;
           ns[2] = th;
           ns[3] = w;
-          acro_step(ns, (float)(a - 1), 0.2f);
-          const bool term = acro_terminal(ns);
+          acro_step<true>(ns, (float)(a - 1), 0.2f);
+          const bool term = acro_terminal<true>(ns);
           rew = term ? 0.0f : -1.0f;
           done = term || t2 >= (int)d.episode_limit;
         } else {

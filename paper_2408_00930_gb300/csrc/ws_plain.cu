@@ -393,8 +393,8 @@ __global__ void k_acrobot_step(Dev d, uint32_t off) {
   const size_t o = (size_t)row * d.n_slots + e, N = d.n_envs;
   const int a = ((const int32_t *)d.r_act)[o];
   float s[4] = {d.s[e], d.s[N + e], d.s[2 * N + e], d.s[3 * N + e]};
-  acro_step(s, (float)(a - 1), 0.2f);
-  const bool term = acro_terminal(s);
+  acro_step<false>(s, (float)(a - 1), 0.2f);
+  const bool term = acro_terminal<false>(s);
   const int t2 = d.t[e] + 1;
   const bool done = term || t2 >= (int)d.episode_limit;
   d.r_rew[o] = term ? 0.0f : -1.0f;
