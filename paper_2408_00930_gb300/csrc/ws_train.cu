@@ -39,6 +39,22 @@ __global__ void k_a2c_gather(Dev d, uint32_t n, size_t q0, uint32_t rows, uint32
   if (d.env != WS_ENV_LANDSCAPE) tb.act[i] = ((const int32_t *)d.r_act)[rowR * S + s];
 }
 
+// The three loss sums: reduced over the warp first, one atomic per warp (every
+// thread of the warp calls it, rows past the end with zeros).
+__device__ __forceinline__ void add_stats(const TrainBufs &tb, double a, double b, double c) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(tb.stats + 0, a);
+    atomicAdd(tb.stats + 1, b);
+    atomicAdd(tb.stats + 2, c);
+  }
+}
+
 // Per row: the advantage, dL/d(policy outputs) and dL/dV (the 1/R of the mean
 // folded in), and the three loss terms (double atomics; they are statistics
 // only).  Categorical head: softmax of the logits.  Diagonal Gaussian head
@@ -50,8 +66,8 @@ __global__ void k_a2c_gather(Dev d, uint32_t n, size_t q0, uint32_t rows, uint32
 __global__ void k_a2c_head(Dev d, uint32_t n, size_t q0, uint32_t rows, uint32_t ns, int na,
                            double inv_r, float c_v, float c_e, TrainBufs tb) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= rows) return;
-  if (d.env == WS_ENV_LANDSCAPE) {  // one group: every slot
+  double s_pg = 0.0, s_v = 0.0, s_h = 0.0;  // rows past the end add zeros
+  if (i < rows && d.env == WS_ENV_LANDSCAPE) {  // one group: every slot
     const int D = (int)d.dim;
     const size_t q = q0 + i;
     const uint32_t k = (uint32_t)(d.k[0] - n + q / ns), e = (uint32_t)(q % ns);
@@ -74,33 +90,34 @@ __global__ void k_a2c_head(Dev d, uint32_t n, size_t q0, uint32_t rows, uint32_t
       }
     }
     tb.vout[i] = (float)(2.0 * c_v * (V - G) * inv_r);
-    atomicAdd(tb.stats + 0, -(double)A * logp);
-    atomicAdd(tb.stats + 1, (double)(G - V) * (G - V));
-    atomicAdd(tb.stats + 2, (double)H);
-    return;
+    s_pg = -(double)A * logp;
+    s_v = (double)(G - V) * (G - V);
+    s_h = H;
+  } else if (i < rows) {
+    float *lg = tb.out + (size_t)i * na;
+    float m = lg[0];
+    for (int c = 1; c < na; ++c) m = fmaxf(m, lg[c]);
+    float S = 0.f;
+    for (int c = 0; c < na; ++c) S += expf(lg[c] - m);
+    const float lS = logf(S);
+    float H = 0.f;
+    for (int c = 0; c < na; ++c) {
+      const float lp = (lg[c] - m) - lS;
+      H -= expf(lp) * lp;
+    }
+    const float V = tb.vout[i], G = tb.ret[i], A = G - V;
+    const int a = tb.act[i];
+    const float lpa = (lg[a] - m) - lS;
+    for (int c = 0; c < na; ++c) {
+      const float lp = (lg[c] - m) - lS, p = expf(lp);
+      lg[c] = (float)((A * (p - (c == a ? 1.f : 0.f)) + c_e * p * (lp + H)) * inv_r);
+    }
+    tb.vout[i] = (float)(2.0 * c_v * (V - G) * inv_r);
+    s_pg = -(double)A * lpa;
+    s_v = (double)(G - V) * (G - V);
+    s_h = H;
   }
-  float *lg = tb.out + (size_t)i * na;
-  float m = lg[0];
-  for (int c = 1; c < na; ++c) m = fmaxf(m, lg[c]);
-  float S = 0.f;
-  for (int c = 0; c < na; ++c) S += expf(lg[c] - m);
-  const float lS = logf(S);
-  float H = 0.f;
-  for (int c = 0; c < na; ++c) {
-    const float lp = (lg[c] - m) - lS;
-    H -= expf(lp) * lp;
-  }
-  const float V = tb.vout[i], G = tb.ret[i], A = G - V;
-  const int a = tb.act[i];
-  const float lpa = (lg[a] - m) - lS;
-  for (int c = 0; c < na; ++c) {
-    const float lp = (lg[c] - m) - lS, p = expf(lp);
-    lg[c] = (float)((A * (p - (c == a ? 1.f : 0.f)) + c_e * p * (lp + H)) * inv_r);
-  }
-  tb.vout[i] = (float)(2.0 * c_v * (V - G) * inv_r);
-  atomicAdd(tb.stats + 0, -(double)A * lpa);
-  atomicAdd(tb.stats + 1, (double)(G - V) * (G - V));
-  atomicAdd(tb.stats + 2, (double)H);
+  add_stats(tb, s_pg, s_v, s_h);
 }
 
 // FP32 GEMM C[M][N] = sum_k A(m, k) B(k, n) over k in [k_lo, k_hi), with
@@ -207,15 +224,120 @@ __global__ __launch_bounds__(kGT) void k_sgemm(const float *__restrict__ A, int 
   }
 }
 
-// Bias-gradient row of slice z: P[z][M][n] = sum over the slice's rows of D[r][n].
+// Bias-gradient row of slice z: P[z][M][n] = sum over the slice's rows of
+// D[r][n]; a warp per (z, n), the lanes over rows, a fixed-order reduction.
 __global__ void k_colsum_slices(const float *__restrict__ D, float *__restrict__ P, int rows, int M,
                                 int N) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x, z = blockIdx.y;
-  if (n >= N) return;
+  const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  const int z = blockIdx.y;
+  if (w >= N) return;  // whole warps leave together
   const int rb = z * kSliceRows, re = min(rows, rb + kSliceRows);
   float s = 0.f;
-  for (int r = rb; r < re; ++r) s += D[(size_t)r * N + n];
-  P[((size_t)z * (M + 1) + M) * N + n] = s;
+  for (int r = rb + lane; r < re; r += 32) s += D[(size_t)r * N + w];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) P[((size_t)z * (M + 1) + M) * N + w] = s;
+}
+
+// Thin layers (32 or fewer outputs, or 32 or fewer inputs) would leave most of
+// a 128 x 128 tile idle; they get their own kernels.
+constexpr int kThin = 32;
+
+// Forward of a layer with N <= 32 outputs: a warp per row, the lanes over the
+// inputs, a fixed-order warp reduction per output.
+template <bool TANH>
+__global__ void k_fwd_thin(const float *__restrict__ X, const float *__restrict__ W,
+                           const float *__restrict__ b, float *__restrict__ Y, int rows, int K,
+                           int N) {
+  const int r = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (r >= rows) return;  // whole warps leave together
+  float acc[kThin];
+#pragma unroll
+  for (int n = 0; n < kThin; ++n) acc[n] = 0.f;
+  for (int k = lane; k < K; k += 32) {
+    const float x = X[(size_t)r * K + k];
+#pragma unroll
+    for (int n = 0; n < kThin; ++n)
+      if (n < N) acc[n] = fmaf(x, W[(size_t)k * N + n], acc[n]);
+  }
+#pragma unroll
+  for (int n = 0; n < kThin; ++n) {
+    if (n >= N) break;
+    float v = acc[n];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) Y[(size_t)r * N + n] = TANH ? tanhf(v + b[n]) : v + b[n];
+  }
+}
+
+// Weight gradient of a layer with N <= 32 outputs, slice z: P[z][m][n] for every
+// input m (and the bias row m = M): a thread per m, the slice's D rows staged
+// through shared memory 64 at a time.
+__global__ __launch_bounds__(256) void k_wgrad_thin_n(const float *__restrict__ Ain,
+                                                      const float *__restrict__ D,
+                                                      float *__restrict__ P, int rows, int M,
+                                                      int N) {
+  __shared__ float Ds[64][kThin];
+  const int m = blockIdx.x * blockDim.x + threadIdx.x, z = blockIdx.y;
+  const int rb = z * kSliceRows, re = min(rows, rb + kSliceRows);
+  float acc[kThin];
+#pragma unroll
+  for (int n = 0; n < kThin; ++n) acc[n] = 0.f;
+  for (int r0 = rb; r0 < re; r0 += 64) {
+    const int nr = min(64, re - r0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 64 * kThin; idx += blockDim.x) {
+      const int rr = idx / kThin, n = idx % kThin;
+      Ds[rr][n] = (rr < nr && n < N) ? D[(size_t)(r0 + rr) * N + n] : 0.f;
+    }
+    __syncthreads();
+    if (m <= M)
+      for (int rr = 0; rr < nr; ++rr) {
+        const float a = m == M ? 1.f : Ain[(size_t)(r0 + rr) * M + m];
+#pragma unroll
+        for (int n = 0; n < kThin; ++n) acc[n] = fmaf(a, Ds[rr][n], acc[n]);
+      }
+  }
+  if (m > M) return;
+  float *out = P + (size_t)z * (M + 1) * N + (size_t)m * N;
+#pragma unroll
+  for (int n = 0; n < kThin; ++n)
+    if (n < N) out[n] = acc[n];
+}
+
+// Weight gradient of a layer with M <= 32 inputs, slice z: P[z][m][n] for every
+// output n, all m (and the bias row): a thread per n, the slice's input rows
+// staged through shared memory 64 at a time.
+__global__ __launch_bounds__(256) void k_wgrad_thin_m(const float *__restrict__ Ain,
+                                                      const float *__restrict__ D,
+                                                      float *__restrict__ P, int rows, int M,
+                                                      int N) {
+  __shared__ float As[64][kThin + 1];
+  const int n = blockIdx.x * blockDim.x + threadIdx.x, z = blockIdx.y;
+  const int rb = z * kSliceRows, re = min(rows, rb + kSliceRows);
+  float acc[kThin + 1];
+#pragma unroll
+  for (int m = 0; m <= kThin; ++m) acc[m] = 0.f;
+  for (int r0 = rb; r0 < re; r0 += 64) {
+    const int nr = min(64, re - r0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 64 * (kThin + 1); idx += blockDim.x) {
+      const int rr = idx / (kThin + 1), m = idx % (kThin + 1);
+      As[rr][m] = (rr < nr && m < M) ? Ain[(size_t)(r0 + rr) * M + m] : (rr < nr && m == M ? 1.f : 0.f);
+    }
+    __syncthreads();
+    if (n < N)
+      for (int rr = 0; rr < nr; ++rr) {
+        const float dv = D[(size_t)(r0 + rr) * N + n];
+#pragma unroll
+        for (int m = 0; m <= kThin; ++m) acc[m] = fmaf(As[rr][m], dv, acc[m]);
+      }
+  }
+  if (n >= N) return;
+  float *out = P + (size_t)z * (M + 1) * N + n;
+#pragma unroll
+  for (int m = 0; m <= kThin; ++m)
+    if (m <= M) out[(size_t)m * N] = acc[m];
 }
 
 // grad[i] += sum_z P[z][i], the slices in order.
@@ -247,12 +369,19 @@ void mlp_forward(const PolicyShape &sh, const float *params, const float *X, flo
   for (int l = 0; l < 3; ++l) {
     const int K = sh.w[l], N = sh.w[l + 1];
     const float *W = params + sh.layer_offset(l), *b = W + (size_t)K * N;
-    if (l < 2)
+    if (N <= kThin) {
+      const unsigned g = nblk((size_t)rows * 32, 256);
+      if (l < 2)
+        k_fwd_thin<true><<<g, 256, 0, st>>>(in[l], W, b, o[l], rows, K, N);
+      else
+        k_fwd_thin<false><<<g, 256, 0, st>>>(in[l], W, b, o[l], rows, K, N);
+    } else if (l < 2) {
       k_sgemm<false, false, kEpiBiasTanh><<<ggrid(rows, N), kGT, 0, st>>>(in[l], K, W, N, o[l], rows, N,
                                                                           0, K, 0, 0, b);
-    else
+    } else {
       k_sgemm<false, false, kEpiBias><<<ggrid(rows, N), kGT, 0, st>>>(in[l], K, W, N, o[l], rows, N, 0,
                                                                       K, 0, 0, b);
+    }
   }
 }
 
@@ -272,10 +401,16 @@ void mlp_backward(const PolicyShape &sh, const float *params, const float *X, co
     // P[z][m][n] = sum over slice z of Ain[r][m] D[r][n]; the partials of one
     // slice are (M + 1) x N apart so that the bias row fits after them
     const size_t len = (size_t)(M + 1) * N;
-    k_sgemm<true, false, kEpiNone><<<ggrid(M, N, nz), kGT, 0, st>>>(ain[l], M, D, N, part, M, N, 0,
-                                                                    rows, kSliceRows, len, nullptr);
-    k_colsum_slices<<<dim3((unsigned)((N + 127) / 128), (unsigned)nz), 128, 0, st>>>(D, part, rows, M,
-                                                                                    N);
+    if (N <= kThin) {
+      k_wgrad_thin_n<<<dim3(nblk(M + 1, 256), (unsigned)nz), 256, 0, st>>>(ain[l], D, part, rows, M, N);
+    } else if (M <= kThin) {
+      k_wgrad_thin_m<<<dim3(nblk(N, 256), (unsigned)nz), 256, 0, st>>>(ain[l], D, part, rows, M, N);
+    } else {
+      k_sgemm<true, false, kEpiNone><<<ggrid(M, N, nz), kGT, 0, st>>>(ain[l], M, D, N, part, M, N, 0,
+                                                                      rows, kSliceRows, len, nullptr);
+      k_colsum_slices<<<dim3(nblk((size_t)N * 32, 256), (unsigned)nz), 256, 0, st>>>(D, part, rows,
+                                                                                     M, N);
+    }
     k_reduce_slices<<<nblk(len, 256), 256, 0, st>>>(part, nz, len, grad + sh.layer_offset(l));
     if (l > 0) {
       // gradient at layer l's input pre-activation: (D W_l^T) * (1 - a_l^2)
