@@ -217,9 +217,12 @@ def oracle_throughput(wl_name, target_s=20.0):
         res = pool.map(_oracle_shard, shards)
     wall = time.perf_counter() - t0
     total = sum(r[0] for r in res)
+    # one process alone: the mean of the processes' own rates
+    single = float(np.mean([r[0] / r[1] for r in res]))
     sample = (f"{cores} processes x {envs_per_core} envs x {steps} steps of the workload "
-              f"({total} agent-steps, FP64 C oracle, {wall:.1f} s wall)")
-    return total / wall, cores, sample, wall
+              f"({total} agent-steps, FP64 C oracle, {wall:.1f} s wall; "
+              f"{single:.0f} agent-steps/s per process)")
+    return total / wall, cores, sample, wall, single
 
 
 # ----------------------------------------------------------------- GPU leg
@@ -323,8 +326,18 @@ def run_gpu(args, wl, world, rank, local):
         pk = one_path(W.WS_PATH_PLAIN_FP32, max(1, min(args.steps, 2)), 1, False)
         plain = dict(value=pk["agent_steps"] * len(pk["times"]) * world / (pk["total_ms"] / 1e3),
                      unit="agent-steps/s", ms_per_step=pk["total_ms"] / len(pk["times"]),
-                     path="plain_fp32 (one launch per sub-step per step, FP32 SIMT)")
+                     path="plain_fp32 (one launch per sub-step per step, FP32 SIMT)",
+                     us_per_env_step=pk["total_ms"] / len(pk["times"]) * 1e3 / wl["horizon"])
         pk["rollout"].close()
+        if wl["n_envs"] <= 10000:
+            # small configs are launch-bound: the same FP32 kernels captured in
+            # CUDA graphs (the batched FP32 path) beside the per-step launches
+            gk = one_path(W.WS_PATH_BATCHED_FP32, max(1, min(args.steps, 5)), 1, False)
+            plain["batched_fp32_graphs"] = dict(
+                value=gk["agent_steps"] * len(gk["times"]) * world / (gk["total_ms"] / 1e3),
+                unit="agent-steps/s",
+                us_per_env_step=gk["total_ms"] / len(gk["times"]) * 1e3 / wl["horizon"])
+            gk["rollout"].close()
     # end to end through the C ABI with host buffers: policy weights H2D from
     # pinned host memory, the roll-out, returns, and the per-env return at t=0 D2H.
     par_bytes = r.fetch_raw(W.WS_F_PARAMS, _param_bytes(wl)).copy()
@@ -517,7 +530,7 @@ def main():
     world, rank, local = dist_init()
     if args.impl == "reference":
         if rank == 0:
-            v, cores, sample, wall = oracle_throughput(args.workload)
+            v, cores, sample, wall, single = oracle_throughput(args.workload)
             steps_ms = wall * 1e3
             print(json.dumps({
                 "impl": "reference", "metric": METRIC, "value": v, "unit": "agent-steps/s",
@@ -526,16 +539,16 @@ def main():
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": wl["desc"], "arm": "FP64 C oracle on host cores"},
                 "cpu_baseline": {"value": v, "unit": "agent-steps/s", "cores": cores,
-                                 "kind": "oracle", "sample": sample},
+                                 "kind": "oracle", "sample": sample, "single_core_value": single},
                 "e2e": {"value": v, "unit": "agent-steps/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}), flush=True)
         return
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         # before the first GPU call: the pool is spawned, never forked after CUDA init
-        v, cores, sample, _ = oracle_throughput(args.workload)
+        v, cores, sample, _, single = oracle_throughput(args.workload)
         cpu = {"value": v, "unit": "agent-steps/s", "cores": cores, "kind": "oracle",
-               "sample": sample}
+               "sample": sample, "single_core_value": single}
     path, value, main_res, plain, e2e = run_gpu(args, wl, world, rank, local)
     a2c = run_a2c(wl, local) if args.a2c and wl["env"] in (0, 3) and rank == 0 else None
     if rank != 0:

@@ -24,6 +24,9 @@ def req(env, n, horizon, seed, path=None, flags=0):
     if env == W.WS_ENV_ECONOMY:
         return W.make_request(env, path if path is not None else W.WS_PATH_BATCHED_FP32, n, horizon,
                               50, 540, 128, 128, seed=seed, flags=flags)
+    if env == W.WS_ENV_ACROBOT:
+        return W.make_request(env, path if path is not None else W.WS_PATH_BATCHED_BF16, n, horizon,
+                              50, 500, 64, 64, seed=seed, flags=flags)
     return W.make_request(env, path if path is not None else W.WS_PATH_BATCHED_FP32, n, horizon, 50,
                           1000, 64, 64, dim=24, n_gauss=512, seed=seed, flags=flags)
 
@@ -55,8 +58,10 @@ def slots_of(q):
 
 def test_results_identical_alone_and_in_mix(torch):
     specs = [(W.WS_ENV_CONTROL, 5000, 150, 11), (W.WS_ENV_ECONOMY, 40, 100, 12),
-             (W.WS_ENV_LANDSCAPE, 700, 100, 13), (W.WS_ENV_CONTROL, 70000, 200, 14)]
-    dims = {W.WS_ENV_CONTROL: (4, 1), W.WS_ENV_ECONOMY: (16, 1), W.WS_ENV_LANDSCAPE: (24, 24)}
+             (W.WS_ENV_LANDSCAPE, 700, 100, 13), (W.WS_ENV_CONTROL, 70000, 200, 14),
+             (W.WS_ENV_ACROBOT, 3000, 100, 15)]
+    dims = {W.WS_ENV_CONTROL: (4, 1), W.WS_ENV_ECONOMY: (16, 1), W.WS_ENV_LANDSCAPE: (24, 24),
+            W.WS_ENV_ACROBOT: (6, 1)}
     alone = []
     srv = W.Server(8 * GB)
     for env, n, h, seed in specs:
@@ -66,7 +71,7 @@ def test_results_identical_alone_and_in_mix(torch):
         alone.append(collect(srv, rid, slots_of(q), *dims[env], h // 50))
         srv.release(rid)
     srv.close()
-    # all four at once: their chunks run concurrently on separate streams
+    # all at once: their chunks run concurrently on separate streams
     srv = W.Server(8 * GB)
     ids = []
     for env, n, h, seed in specs:
@@ -79,7 +84,7 @@ def test_results_identical_alone_and_in_mix(torch):
     srv.close()
     for a, b in zip(alone, mixed):
         assert a == b
-    assert stats["completed"] == 4 and stats["chunks"] == sum(h // 50 for _, _, h, _ in specs)
+    assert stats["completed"] == len(specs) and stats["chunks"] == sum(h // 50 for _, _, h, _ in specs)
     assert stats["p99_ms"] >= stats["p50_ms"] > 0
 
 
