@@ -409,8 +409,9 @@ def run_a2c(wl, local):
                          "frac": achieved / peak,
                          "peak_source": f"128 FP32 lanes x 2 flops / clock / SM x {n_sms} SMs x "
                                         "2070 MHz"},
-            "kernels": "k_a2c_gather, k_dense_fp32 (forward), k_a2c_head, k_wgrad + "
-                       "k_reduce_slices, k_bwd_data, k_sgd; FP32 SIMT"}
+            "kernels": "k_a2c_gather, k_sgemm (forward, weight and data gradients), k_fwd_thin, "
+                       "k_wgrad_thin_n/_m, k_colsum_slices, k_reduce_slices, k_a2c_head, k_sgd; "
+                       "FP32 SIMT"}
 
 
 def run_serving(args, world, rank, local):
