@@ -131,13 +131,15 @@ enum { kEpiBiasTanh = 0, kEpiBias = 1, kEpiDTanh = 2, kEpiNone = 3 };
 constexpr int kGM = 128, kGN = 128, kGK = 8, kGT = 256;
 
 template <bool TA, bool TB, int EPI>
-__global__ __launch_bounds__(kGT) void k_sgemm(const float *__restrict__ A, int lda,
+__global__ __launch_bounds__(kGT, 2) void k_sgemm(const float *__restrict__ A, int lda,
                                                 const float *__restrict__ B, int ldb,
                                                 float *__restrict__ C, int M, int N, int k_lo,
                                                 int k_hi, int k_slice, size_t slice_stride,
                                                 const float *__restrict__ aux) {
-  __shared__ __align__(16) float As[2][kGK][kGM];
-  __shared__ __align__(16) float Bs[2][kGK][kGN];
+  // rows padded by 4 floats: the transposing stores of k-contiguous operands
+  // (8 k of 4 rows per warp) then fall in 32 distinct banks
+  __shared__ __align__(16) float As[2][kGK][kGM + 4];
+  __shared__ __align__(16) float Bs[2][kGK][kGN + 4];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.x * kGM, n0 = blockIdx.y * kGN;
   int kb = k_lo, ke = k_hi;
