@@ -23,7 +23,8 @@ namespace ws {
 
 namespace {
 
-constexpr int kSliceRows = 512;    // rows per weight-gradient partial
+constexpr int kSliceRows = 512;    // rows per weight-gradient partial (128 x 128 GEMM)
+constexpr int kThinSlice = 128;    // rows per partial of the thin kernels (more blocks)
 
 // Row i of the chunk starting at global row q0 of a group: (step index t,
 // slot slot0 + s) with q = t * ns + s over the last n steps.
@@ -281,7 +282,7 @@ __global__ __launch_bounds__(256) void k_wgrad_thin_n(const float *__restrict__ 
                                                       int N) {
   __shared__ float Ds[64][kThin];
   const int m = blockIdx.x * blockDim.x + threadIdx.x, z = blockIdx.y;
-  const int rb = z * kSliceRows, re = min(rows, rb + kSliceRows);
+  const int rb = z * kThinSlice, re = min(rows, rb + kThinSlice);
   float acc[kThin];
 #pragma unroll
   for (int n = 0; n < kThin; ++n) acc[n] = 0.f;
@@ -316,7 +317,7 @@ __global__ __launch_bounds__(256) void k_wgrad_thin_m(const float *__restrict__ 
                                                       int N) {
   __shared__ float As[64][kThin + 1];
   const int n = blockIdx.x * blockDim.x + threadIdx.x, z = blockIdx.y;
-  const int rb = z * kSliceRows, re = min(rows, rb + kSliceRows);
+  const int rb = z * kThinSlice, re = min(rows, rb + kThinSlice);
   float acc[kThin + 1];
 #pragma unroll
   for (int m = 0; m <= kThin; ++m) acc[m] = 0.f;
@@ -358,6 +359,11 @@ __global__ void k_sgd(float *p, const float *g, size_t n, float lr) {
 
 inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// A layer's weight gradient goes to the thin kernels when it has 32 or fewer
+// outputs or inputs; their row slices are shorter.
+inline bool thin_layer(int M, int N) { return N <= kThin || M <= kThin; }
+inline int slice_rows(int M, int N) { return thin_layer(M, N) ? kThinSlice : kSliceRows; }
+
 inline dim3 ggrid(int M, int N, int z = 1) {
   return dim3((unsigned)((M + kGM - 1) / kGM), (unsigned)((N + kGN - 1) / kGN), (unsigned)z);
 }
@@ -394,11 +400,11 @@ void mlp_forward(const PolicyShape &sh, const float *params, const float *X, flo
 void mlp_backward(const PolicyShape &sh, const float *params, const float *X, const float *h1,
                   const float *h2, const float *dout, float *grad, float *d1, float *d2,
                   float *part, int rows, cudaStream_t st) {
-  const int nz = (rows + kSliceRows - 1) / kSliceRows;
   const float *ain[3] = {X, h1, h2};
   float *dl[3] = {nullptr, d1, d2};
   for (int l = 2; l >= 0; --l) {
     const int M = sh.w[l], N = sh.w[l + 1];
+    const int sr = slice_rows(M, N), nz = (rows + sr - 1) / sr;
     const float *D = l == 2 ? dout : dl[l + 1];
     // P[z][m][n] = sum over slice z of Ain[r][m] D[r][n]; the partials of one
     // slice are (M + 1) x N apart so that the bias row fits after them
@@ -428,11 +434,16 @@ size_t train_scratch_bytes(const PolicyShape &pol) {
   const PolicyShape crit{{pol.w[0], pol.w[1], pol.w[2], 1}};
   const size_t CH = kTrainChunk, w0 = pol.w[0], H0 = pol.w[1], H1 = pol.w[2], NA = pol.w[3];
   const size_t hmax = H0 > H1 ? H0 : H1;
-  const size_t nz = (CH + kSliceRows - 1) / kSliceRows;
-  size_t maxlen = 0;
+  size_t part_len = 0;  // the largest slice-partial set over the layers of both networks
   for (int l = 0; l < kMaxLayers; ++l) {
     const size_t len = (size_t)(pol.w[l] + 1) * pol.w[l + 1];
-    if (len > maxlen) maxlen = len;
+    const size_t sr = (size_t)slice_rows(pol.w[l], pol.w[l + 1]);
+    const size_t v = (CH + sr - 1) / sr * len;
+    if (v > part_len) part_len = v;
+    const size_t lenc = (size_t)(crit.w[l] + 1) * crit.w[l + 1];
+    const size_t src = (size_t)slice_rows(crit.w[l], crit.w[l + 1]);
+    const size_t vc = (CH + src - 1) / src * lenc;
+    if (vc > part_len) part_len = vc;
   }
   size_t b = 0;
   auto add = [&](size_t n) { b += (n + 63) / 64 * 64; };
@@ -447,7 +458,7 @@ size_t train_scratch_bytes(const PolicyShape &pol) {
   add(CH * 4);                   // v / dv
   add(CH * hmax * 4);            // d1
   add(CH * hmax * 4);            // d2
-  add(nz * maxlen * 4);          // weight-gradient partials
+  add(part_len * 4);             // weight-gradient partials
   add(3 * 8);                    // stats
   add((pol.count() + crit.count()) * 4);  // gradients
   return b;
@@ -457,11 +468,16 @@ TrainBufs train_bufs(uint8_t *base, const PolicyShape &pol) {
   const PolicyShape crit{{pol.w[0], pol.w[1], pol.w[2], 1}};
   const size_t CH = kTrainChunk, w0 = pol.w[0], H0 = pol.w[1], H1 = pol.w[2], NA = pol.w[3];
   const size_t hmax = H0 > H1 ? H0 : H1;
-  const size_t nz = (CH + kSliceRows - 1) / kSliceRows;
-  size_t maxlen = 0;
+  size_t part_len = 0;  // the largest slice-partial set over the layers of both networks
   for (int l = 0; l < kMaxLayers; ++l) {
     const size_t len = (size_t)(pol.w[l] + 1) * pol.w[l + 1];
-    if (len > maxlen) maxlen = len;
+    const size_t sr = (size_t)slice_rows(pol.w[l], pol.w[l + 1]);
+    const size_t v = (CH + sr - 1) / sr * len;
+    if (v > part_len) part_len = v;
+    const size_t lenc = (size_t)(crit.w[l] + 1) * crit.w[l + 1];
+    const size_t src = (size_t)slice_rows(crit.w[l], crit.w[l + 1]);
+    const size_t vc = (CH + src - 1) / src * lenc;
+    if (vc > part_len) part_len = vc;
   }
   TrainBufs t{};
   size_t o = 0;
@@ -481,7 +497,7 @@ TrainBufs train_bufs(uint8_t *base, const PolicyShape &pol) {
   t.vout = (float *)take(CH * 4);
   t.d1 = (float *)take(CH * hmax * 4);
   t.d2 = (float *)take(CH * hmax * 4);
-  t.part = (float *)take(nz * maxlen * 4);
+  t.part = (float *)take(part_len * 4);
   t.stats = (double *)take(3 * 8);
   t.grad = (float *)take((pol.count() + crit.count()) * 4);
   return t;
