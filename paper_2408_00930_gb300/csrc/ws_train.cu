@@ -131,7 +131,26 @@ __global__ void k_a2c_head(Dev d, uint32_t n, size_t q0, uint32_t rows, uint32_t
 enum { kEpiBiasTanh = 0, kEpiBias = 1, kEpiDTanh = 2, kEpiNone = 3 };
 constexpr int kGM = 128, kGN = 128, kGK = 8, kGT = 256;
 
-template <bool TA, bool TB, int EPI>
+// Loads one 4-element vector of an operand tile: along the contiguous dimension
+// from (row r, column c) of a matrix with leading dimension ld, valid up to
+// r < rmax and c + i < cmax; VEC: one 16-byte load when all four are in range.
+template <bool VEC>
+__device__ __forceinline__ void ld4(const float *__restrict__ X, long ld, int r, int c, int rmax,
+                                    int cmax, float (&v)[4]) {
+  const float *p = X + (long)r * ld + c;
+  if (VEC && r < rmax && c + 3 < cmax) {
+    const float4 q = __ldg((const float4 *)p);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = (r < rmax && c + i < cmax) ? p[i] : 0.f;
+  }
+}
+
+template <bool TA, bool TB, int EPI, bool VEC>
 __global__ __launch_bounds__(kGT, 2) void k_sgemm(const float *__restrict__ A, int lda,
                                                 const float *__restrict__ B, int ldb,
                                                 float *__restrict__ C, int M, int N, int k_lo,
@@ -148,29 +167,32 @@ __global__ __launch_bounds__(kGT, 2) void k_sgemm(const float *__restrict__ A, i
     kb = k_lo + (int)blockIdx.z * k_slice;
     ke = min(k_hi, kb + k_slice);
   }
-  // staging: 1,024 elements of each operand per K step, 4 per thread
+  // staging: 1,024 elements of each operand per K step, 4 consecutive ones (in
+  // memory order) per thread: a k-contiguous operand tile is 128 rows of two
+  // 4-vectors, an m- (n-) contiguous one 8 rows of 32 4-vectors
   float ra[4], rb[4];
   auto load = [&](int k0) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int e = tid + i * kGT;
-      // A: m fastest when TA (m contiguous in memory), else k fastest
-      const int am = TA ? (e & (kGM - 1)) : (e >> 3), ak = TA ? (e >> 7) : (e & 7);
-      const int gm = m0 + am, gk = k0 + ak;
-      ra[i] = (gm < M && gk < ke) ? (TA ? A[(long)gk * lda + gm] : A[(long)gm * lda + gk]) : 0.f;
-      const int bn = TB ? (e >> 3) : (e & (kGN - 1)), bk = TB ? (e & 7) : (e >> 7);
-      const int gn = n0 + bn, gk2 = k0 + bk;
-      rb[i] = (gn < N && gk2 < ke) ? (TB ? B[(long)gn * ldb + gk2] : B[(long)gk2 * ldb + gn]) : 0.f;
-    }
+    if (TA)  // A(m, k) = A[k lda + m]
+      ld4<VEC>(A, lda, k0 + (tid >> 5), m0 + (tid & 31) * 4, ke, M, ra);
+    else     // A(m, k) = A[m lda + k]
+      ld4<VEC>(A, lda, m0 + (tid >> 1), k0 + (tid & 1) * 4, M, ke, ra);
+    if (TB)  // B(k, n) = B[n ldb + k]
+      ld4<VEC>(B, ldb, n0 + (tid >> 1), k0 + (tid & 1) * 4, N, ke, rb);
+    else     // B(k, n) = B[k ldb + n]
+      ld4<VEC>(B, ldb, k0 + (tid >> 5), n0 + (tid & 31) * 4, ke, N, rb);
   };
   auto store = [&](int buf) {
+    if (TA) {
+      *(float4 *)&As[buf][tid >> 5][(tid & 31) * 4] = make_float4(ra[0], ra[1], ra[2], ra[3]);
+    } else {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int e = tid + i * kGT;
-      const int am = TA ? (e & (kGM - 1)) : (e >> 3), ak = TA ? (e >> 7) : (e & 7);
-      As[buf][ak][am] = ra[i];
-      const int bn = TB ? (e >> 3) : (e & (kGN - 1)), bk = TB ? (e & 7) : (e >> 7);
-      Bs[buf][bk][bn] = rb[i];
+      for (int i = 0; i < 4; ++i) As[buf][(tid & 1) * 4 + i][tid >> 1] = ra[i];
+    }
+    if (TB) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) Bs[buf][(tid & 1) * 4 + i][tid >> 1] = rb[i];
+    } else {
+      *(float4 *)&Bs[buf][tid >> 5][(tid & 31) * 4] = make_float4(rb[0], rb[1], rb[2], rb[3]);
     }
   };
   float acc[8][8];
@@ -364,6 +386,23 @@ inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 inline bool thin_layer(int M, int N) { return N <= kThin || M <= kThin; }
 inline int slice_rows(int M, int N) { return thin_layer(M, N) ? kThinSlice : kSliceRows; }
 
+// 16-byte loads when both operands' rows start on 16-byte boundaries.
+inline bool vec_ok(const void *A, int lda, const void *B, int ldb) {
+  return lda % 4 == 0 && ldb % 4 == 0 && ((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0;
+}
+
+// Launch k_sgemm with the 16-byte-load variant when the operands allow it.
+template <bool TA, bool TB, int EPI>
+void sgemm(dim3 g, cudaStream_t st, const float *A, int lda, const float *B, int ldb, float *C,
+           int M, int N, int k_lo, int k_hi, int k_slice, size_t slice_stride, const float *aux) {
+  if (vec_ok(A, lda, B, ldb))
+    k_sgemm<TA, TB, EPI, true><<<g, kGT, 0, st>>>(A, lda, B, ldb, C, M, N, k_lo, k_hi, k_slice,
+                                                  slice_stride, aux);
+  else
+    k_sgemm<TA, TB, EPI, false><<<g, kGT, 0, st>>>(A, lda, B, ldb, C, M, N, k_lo, k_hi, k_slice,
+                                                   slice_stride, aux);
+}
+
 inline dim3 ggrid(int M, int N, int z = 1) {
   return dim3((unsigned)((M + kGM - 1) / kGM), (unsigned)((N + kGN - 1) / kGN), (unsigned)z);
 }
@@ -384,11 +423,10 @@ void mlp_forward(const PolicyShape &sh, const float *params, const float *X, flo
       else
         k_fwd_thin<false><<<g, 256, 0, st>>>(in[l], W, b, o[l], rows, K, N);
     } else if (l < 2) {
-      k_sgemm<false, false, kEpiBiasTanh><<<ggrid(rows, N), kGT, 0, st>>>(in[l], K, W, N, o[l], rows, N,
-                                                                          0, K, 0, 0, b);
+      sgemm<false, false, kEpiBiasTanh>(ggrid(rows, N), st, in[l], K, W, N, o[l], rows, N, 0, K, 0, 0,
+                                        b);
     } else {
-      k_sgemm<false, false, kEpiBias><<<ggrid(rows, N), kGT, 0, st>>>(in[l], K, W, N, o[l], rows, N, 0,
-                                                                      K, 0, 0, b);
+      sgemm<false, false, kEpiBias>(ggrid(rows, N), st, in[l], K, W, N, o[l], rows, N, 0, K, 0, 0, b);
     }
   }
 }
@@ -414,16 +452,16 @@ void mlp_backward(const PolicyShape &sh, const float *params, const float *X, co
     } else if (M <= kThin) {
       k_wgrad_thin_m<<<dim3(nblk(N, 256), (unsigned)nz), 256, 0, st>>>(ain[l], D, part, rows, M, N);
     } else {
-      k_sgemm<true, false, kEpiNone><<<ggrid(M, N, nz), kGT, 0, st>>>(ain[l], M, D, N, part, M, N, 0,
-                                                                      rows, kSliceRows, len, nullptr);
+      sgemm<true, false, kEpiNone>(ggrid(M, N, nz), st, ain[l], M, D, N, part, M, N, 0, rows,
+                                   kSliceRows, len, nullptr);
       k_colsum_slices<<<dim3(nblk((size_t)N * 32, 256), (unsigned)nz), 256, 0, st>>>(D, part, rows,
                                                                                      M, N);
     }
     k_reduce_slices<<<nblk(len, 256), 256, 0, st>>>(part, nz, len, grad + sh.layer_offset(l));
     if (l > 0) {
       // gradient at layer l's input pre-activation: (D W_l^T) * (1 - a_l^2)
-      k_sgemm<false, true, kEpiDTanh><<<ggrid(rows, M), kGT, 0, st>>>(
-          D, N, params + sh.layer_offset(l), N, dl[l], rows, M, 0, N, 0, 0, ain[l]);
+      sgemm<false, true, kEpiDTanh>(ggrid(rows, M), st, D, N, params + sh.layer_offset(l), N, dl[l],
+                                    rows, M, 0, N, 0, 0, ain[l]);
     }
   }
 }
