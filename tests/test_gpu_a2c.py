@@ -172,3 +172,27 @@ def test_a2c_update_economy_agents_and_planner(torch, path):
             tol = 1e-4 * np.abs(g).max() + 0.6 * np.spacing(np.abs(before)).astype(np.float64) / lr
             assert np.all(np.abs(step - g) <= tol), np.abs(step - g).max()
     np.testing.assert_allclose(stats, tot / (T * (Sa + n_env)), rtol=1e-4, atol=1e-7)
+
+
+def test_a2c_update_window_over_wrapped_ring(torch):
+    """The update's window is the last n steps of a ring that has wrapped: rows
+    gathered modulo the ring, returns scanned over the same window."""
+    n_env, R, T, n, h, lr, c_v, c_e = 500, 20, 33, 14, 32, 1.0, 0.5, 0.0
+    r = W.Rollout(W.WS_ENV_CONTROL, F32, n_env, R, 25, h, h, param_seed=6, flags=W.WS_FLAG_TRAIN,
+                  chunk_steps=7)
+    r.reset(3)
+    r.rollout(T)
+    pa = r.fetch_raw(W.WS_F_PARAMS, 4 * oracle.policy_param_count([4, h, h, 2])).view(np.float32).copy()
+    pc = r.fetch_raw(W.WS_F_CRITIC, 4 * oracle.policy_param_count([4, h, h, 1])).view(np.float32).copy()
+    obs, act = r.fetch(W.WS_F_OBS, T - n, n), r.fetch(W.WS_F_ACTION, T - n, n)
+    rew, done = r.fetch(W.WS_F_REWARD, T - n, n), r.fetch(W.WS_F_DONE, T - n, n)
+    stats = r.a2c_update(n, lr, c_v, c_e)
+    ret = r.fetch(W.WS_F_RETURN, T - n, n)
+    pa2 = r.fetch_raw(W.WS_F_PARAMS, pa.nbytes).view(np.float32).copy()
+    pc2 = r.fetch_raw(W.WS_F_CRITIC, pc.nbytes).view(np.float32).copy()
+    r.close()
+    Go = oracle.returns(rew, done, float(np.float32(0.99)))
+    assert np.abs(ret - Go).max() <= 1e-6 * max(1.0, np.abs(Go).max())
+    rows = dict(obs=obs.transpose(0, 2, 1).reshape(-1, 4).astype(np.float64), act=act.reshape(-1),
+                ret=ret.reshape(-1).astype(np.float64))
+    check_grads((pa, pc, pa2, pc2), rows, stats, (4, 2), h, lr, c_v, c_e)
