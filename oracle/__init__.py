@@ -113,6 +113,8 @@ def _declare(L):
                          C.c_double, C.c_double, _P, _P, _P]
     L.or_a2c_gauss.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P, _P,
                                C.c_double, C.c_double, _P, _P, _P]
+    L.or_ppo.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P, _P, _P,
+                         C.c_double, C.c_double, C.c_double, _P, _P, _P]
 
 
 def _ptr(a):
@@ -460,6 +462,26 @@ def a2c(actor, critic, obs, act, ret, h0, h1, n_act, c_v=0.5, c_e=0.0, adv=None,
     lib().or_a2c(R, od, n_act, h0, h1, _ptr(_arr(actor, np.float32)), _ptr(_arr(critic, np.float32)),
                  _ptr(o), _ptr(_arr(act, np.int32)), _ptr(_arr(ret, np.float64)),
                  _ptr(_arr(adv, np.float64)), float(c_v), float(c_e), _ptr(ga), _ptr(gc), _ptr(st))
+    return st, ga, gc
+
+
+def ppo(actor, critic, obs, act, ret, adv, logp_old, h0, h1, n_act, eps, c_v=0.5, c_e=0.0,
+        grads=True):
+    """PPO clipped-surrogate loss terms {surrogate, value, entropy, clip
+    fraction} and, with grads, dL/d(actor) and dL/d(critic) in FP64
+    (or_ppo).  adv is the advantage held from before the update, logp_old
+    the behaviour policy's log-probability of each row's action."""
+    o = _arr(obs, np.float64)
+    R, od = o.shape
+    na = policy_param_count([od, h0, h1, n_act])
+    nc = policy_param_count([od, h0, h1, 1])
+    ga = np.empty(na) if grads else None
+    gc = np.empty(nc) if grads else None
+    st = np.empty(4)
+    lib().or_ppo(R, od, n_act, h0, h1, _ptr(_arr(actor, np.float32)), _ptr(_arr(critic, np.float32)),
+                 _ptr(o), _ptr(_arr(act, np.int32)), _ptr(_arr(ret, np.float64)),
+                 _ptr(_arr(adv, np.float64)), _ptr(_arr(logp_old, np.float64)), float(eps),
+                 float(c_v), float(c_e), _ptr(ga), _ptr(gc), _ptr(st))
     return st, ga, gc
 
 

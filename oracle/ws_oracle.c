@@ -1072,6 +1072,88 @@ void or_a2c_gauss(int R, int D, int h0, int h1, const float *actor, const float 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Proximal policy optimisation, clipped surrogate [reading]: the same      */
+/* actor and critic as or_a2c; the advantage A_i is held from before the    */
+/* update (G_i - V(s_i) under the critic as it was), and the roll-out's     */
+/* recorded log-probability logp_old_i of its action is the behaviour       */
+/* policy.  With rho_i = exp(log pi(a_i | s_i) - logp_old_i):               */
+/*   L = (1/R) sum_i [ -min(rho_i A_i, clip(rho_i, 1 - eps, 1 + eps) A_i)   */
+/*                     - c_e H(pi(. | s_i)) + c_v (G_i - V(s_i))^2 ]         */
+/* The min takes the clipped (constant) term, and rho gets no gradient,     */
+/* exactly where A > 0 and rho > 1 + eps or A < 0 and rho < 1 - eps; inside */
+/* [1 - eps, 1 + eps] both terms agree and the gradient is d(rho A).        */
+/* stats: {mean -min(..), mean (G - V)^2, mean entropy, fraction of rows    */
+/*         with |rho - 1| > eps}.                                           */
+/* ------------------------------------------------------------------------ */
+void or_ppo(int R, int obs_dim, int n_act, int h0, int h1, const float *actor, const float *critic,
+            const double *obs, const int32_t *act, const double *ret, const double *adv,
+            const double *logp_old, double eps, double c_v, double c_e, double *grad_actor,
+            double *grad_critic, double stats[4]) {
+  int32_t wa[4] = {obs_dim, h0, h1, n_act}, wc[4] = {obs_dim, h0, h1, 1};
+  long na = 0, nc = 0;
+  for (int l = 0; l < 3; ++l) {
+    na += (long)wa[l] * wa[l + 1] + wa[l + 1];
+    nc += (long)wc[l] * wc[l + 1] + wc[l + 1];
+  }
+  if (grad_actor) memset(grad_actor, 0, sizeof(double) * na);
+  if (grad_critic) memset(grad_critic, 0, sizeof(double) * nc);
+  or_trace ta, tc;
+  or_trace_alloc(&ta, wa);
+  or_trace_alloc(&tc, wc);
+  double *lp = (double *)malloc(sizeof(double) * n_act);
+  double *dl = (double *)malloc(sizeof(double) * n_act);
+  double s_pg = 0.0, s_v = 0.0, s_h = 0.0, s_clip = 0.0;
+  for (int i = 0; i < R; ++i) {
+    const double *x = obs + (long)i * obs_dim;
+    or_mlp_trace(wa, actor, x, &ta);
+    or_mlp_trace(wc, critic, x, &tc);
+    const double *lg = ta.a[3];
+    double m = lg[0];
+    for (int k = 1; k < n_act; ++k)
+      if (lg[k] > m) m = lg[k];
+    double S = 0.0;
+    for (int k = 0; k < n_act; ++k) S += exp(lg[k] - m);
+    double H = 0.0;
+    for (int k = 0; k < n_act; ++k) {
+      lp[k] = (lg[k] - m) - log(S);
+      H -= exp(lp[k]) * lp[k];
+    }
+    const double A = adv[i], V = tc.a[3][0];
+    const double rho = exp(lp[act[i]] - logp_old[i]);
+    const double rc = rho < 1.0 - eps ? 1.0 - eps : (rho > 1.0 + eps ? 1.0 + eps : rho);
+    const double surr = rho * A < rc * A ? rho * A : rc * A;
+    const int held = (A > 0.0 && rho > 1.0 + eps) || (A < 0.0 && rho < 1.0 - eps);
+    s_pg += -surr;
+    s_v += (ret[i] - V) * (ret[i] - V);
+    s_h += H;
+    s_clip += fabs(rho - 1.0) > eps ? 1.0 : 0.0;
+    if (grad_actor) {
+      /* d(-rho A)/dl_k = A rho (p_k - [k = a]);  d(-c_e H)/dl_k = c_e p_k (log p_k + H) */
+      for (int k = 0; k < n_act; ++k) {
+        const double pk = exp(lp[k]);
+        const double g_pg = held ? 0.0 : A * rho * (pk - (k == act[i] ? 1.0 : 0.0));
+        dl[k] = (g_pg + c_e * pk * (lp[k] + H)) / R;
+      }
+      or_mlp_backward(wa, actor, &ta, dl, grad_actor);
+    }
+    if (grad_critic) {
+      double dv = 2.0 * c_v * (V - ret[i]) / R;
+      or_mlp_backward(wc, critic, &tc, &dv, grad_critic);
+    }
+  }
+  if (stats) {
+    stats[0] = s_pg / R;
+    stats[1] = s_v / R;
+    stats[2] = s_h / R;
+    stats[3] = s_clip / R;
+  }
+  free(lp);
+  free(dl);
+  or_trace_free(&ta);
+  or_trace_free(&tc);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Discounted returns over a window of n_steps records ([n_steps][n_slots]):*/
 /*   G_t = r_t + gamma (1 - d_t) G_{t+1},  G_{n_steps} = 0.                 */
 /* ------------------------------------------------------------------------ */
