@@ -367,10 +367,13 @@ def run_gpu(args, wl, world, rank, local):
 
 def run_a2c(wl, local):
     """One actor-critic update (ws_a2c_update) over the last 50 steps of a
-    roll-out of the workload, timed with CUDA events on the context's stream
-    (L2 flushed before each of three launches).  FP32 SIMT GEMMs: algorithmic
-    flops per row = forward of policy and critic, their weight gradients
-    (same count) and the data gradients of the two hidden layers."""
+    roll-out of the workload, then the PPO advantages (ws_advantages) and one
+    PPO epoch (ws_ppo_update) over the same rows, each timed with CUDA events
+    on the context's stream (L2 flushed before each; three measured rounds
+    after one untimed).  FP32 SIMT GEMMs: algorithmic flops per row of an
+    update = forward of policy and critic, their weight gradients (same count)
+    and the data gradients of the two hidden layers; of the advantages, the
+    critic's forward."""
     import torch
     from paper_2408_00930_gb300 import warpsci as W
     dev = torch.device("cuda", local)
@@ -384,19 +387,29 @@ def run_a2c(wl, local):
     fwd = lambda n_out: 2 * (od * h0 + h0 * h1 + h1 * n_out)
     flops_row = 2 * (fwd(na) + fwd(1)) + 2 * 2 * (h1 * na + h0 * h1 + h1 + h0 * h1)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    ms = []
-    for i in range(4):
-        r.reset(77 + i)
-        r.rollout(T)
+
+    def timed(fn):
         flush.zero_()
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        W.ws_a2c_update(r.ctx, T, 1e-3, 0.5, 0.01, None)
+        st = fn()
         e1.record(stream)
         torch.cuda.synchronize(dev)
+        assert st == W.WS_OK, st
+        return e0.elapsed_time(e1)
+
+    ms, ms_adv, ms_ppo = [], [], []
+    for i in range(4):
+        r.reset(77 + i)
+        r.rollout(T)
+        t_a2c = timed(lambda: W.ws_a2c_update(r.ctx, T, 1e-3, 0.5, 0.01, None))
+        t_adv = timed(lambda: W.ws_advantages(r.ctx, T))
+        t_ppo = timed(lambda: W.ws_ppo_update(r.ctx, T, 1e-3, 0.2, 0.5, 0.01, None))
         if i:
-            ms.append(e0.elapsed_time(e1))
+            ms.append(t_a2c)
+            ms_adv.append(t_adv)
+            ms_ppo.append(t_ppo)
     r.close()
     rows = T * wl["n_envs"]
     t = statistics.median(ms)
@@ -411,7 +424,15 @@ def run_a2c(wl, local):
                                         "2070 MHz"},
             "kernels": "k_a2c_gather, k_sgemm (forward, weight and data gradients), k_fwd_thin, "
                        "k_wgrad_thin_n/_m, k_colsum_slices, k_reduce_slices, k_a2c_head, k_sgd; "
-                       "FP32 SIMT"}
+                       "FP32 SIMT",
+            "ppo": {"advantages_ms": statistics.median(ms_adv),
+                    "epoch_ms": statistics.median(ms_ppo),
+                    "epoch_rows_per_s": rows / (statistics.median(ms_ppo) * 1e-3),
+                    "epoch_frac_fp32": flops_row * rows / (statistics.median(ms_ppo) * 1e-3) / 1e12
+                    / peak,
+                    "advantages_tflops": fwd(1) * rows / (statistics.median(ms_adv) * 1e-3) / 1e12,
+                    "kernels": "ws_advantages: k_a2c_gather, the critic's forward, k_adv_store; "
+                               "ws_ppo_update: as the A2C update with k_ppo_head"}}
 
 
 def run_serving(args, world, rank, local):
@@ -506,7 +527,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--a2c", action="store_true",
-                    help="also time one actor-critic update (ws_a2c_update) over 50 steps "
+                    help="also time one actor-critic update (ws_a2c_update), the PPO advantages "
+                         "and one PPO epoch over 50 steps "
                          "(control and acrobot workloads)")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch configuration (profiling captures)")

@@ -124,8 +124,8 @@ struct Layout {
   int econ_fused;          // economy on the fused persistent kernel
   int land_fused;          // landscape on the fused persistent kernel
   size_t land_energy_off;
-  size_t force_img_off;
-  size_t critic_off, train_off;  // WS_FLAG_TRAIN: critic parameters, update scratch    // landscape, fused kernel with WS_FLAG_FORCE: the force image  // landscape, fused kernel: its energy image (blocks of 64 Gaussians)
+  size_t force_img_off;     // landscape, fused kernel with WS_FLAG_FORCE: the force image
+  size_t critic_off, train_off;  // WS_FLAG_TRAIN: critic parameters, update scratch
   size_t scratch_off;      // plain-path activations
   size_t scratch_h0_off, scratch_h1_off, scratch_out_off;
   size_t scratch_pobs_off, scratch_ph0_off, scratch_ph1_off, scratch_pout_off;
@@ -134,6 +134,7 @@ struct Layout {
   // ring buffer: per field, [ring_steps][...]
   size_t ring_obs, ring_act, ring_logp, ring_rew, ring_done, ring_ret, ring_wealth, ring_energy;
   size_t ring_force;  // landscape with WS_FLAG_FORCE
+  size_t ring_adv;    // WS_FLAG_TRAIN: advantages of ws_advantages
   size_t ring_bytes;
 };
 

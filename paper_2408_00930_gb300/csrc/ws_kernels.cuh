@@ -56,6 +56,7 @@ struct Dev {
   void *r_act;
   float *r_logp, *r_rew, *r_ret, *r_energy;
   float *r_force;  // landscape FORCE field [t][D][slot] (WS_FLAG_FORCE), else null
+  float *r_adv;    // ADVANTAGE field [t][slot] (WS_FLAG_TRAIN), else null
   uint8_t *r_done;
   int64_t *r_wealth;
 };
@@ -83,13 +84,14 @@ void launch_advance(const Dev &d, uint32_t n, cudaStream_t st);
 
 // ---- S7: discounted returns ----------------------------------------------
 void launch_returns(const Dev &d, uint32_t n_steps, cudaStream_t st);
-// ---- actor-critic update (ws_train.cu) ----------------------------------------
+// ---- actor-critic updates (ws_train.cu) ---------------------------------------
 constexpr int kTrainChunk = 65536;  // rows per chunk of the update
 struct TrainBufs {                 // per-chunk scratch in the state buffer
   float *x, *ret;
   int32_t *act;
+  float *adv, *lpo;                // PPO: held advantage, behaviour log-probability
   float *h1, *h2, *out, *c1, *c2, *vout, *d1, *d2, *part;
-  double *stats;                   // policy loss, value loss, entropy (sums)
+  double *stats;                   // policy loss, value loss, entropy, clipped rows (sums)
   float *grad;                     // actor gradient, then the critic's
 };
 struct TrainGroup {  // one policy and its critic, on slots [slot0, slot0 + n_slots) of every step
@@ -102,6 +104,12 @@ size_t train_scratch_bytes(const PolicyShape &pol);
 TrainBufs train_bufs(uint8_t *base, const PolicyShape &pol);
 void launch_a2c_update(const Dev &d, const TrainBufs &tb, const TrainGroup *groups, int n_groups,
                        uint32_t n, float lr, float c_v, float c_e, cudaStream_t st);
+// A = G - V(s) of the last n steps into the ADVANTAGE field (returns computed).
+void launch_advantages(const Dev &d, const TrainBufs &tb, const TrainGroup *groups, int n_groups,
+                       uint32_t n, cudaStream_t st);
+// One PPO epoch (categorical heads) over the last n steps.
+void launch_ppo_update(const Dev &d, const TrainBufs &tb, const TrainGroup *groups, int n_groups,
+                       uint32_t n, float lr, float eps, float c_v, float c_e, cudaStream_t st);
 
 // Landscape force -grad E(x') of the last n_steps ring rows (ws_force.cu).
 void launch_forces(const Dev &d, uint32_t n_steps, cudaStream_t st);

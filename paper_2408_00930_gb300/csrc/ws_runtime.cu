@@ -27,6 +27,9 @@ struct ws_ctx {
   char *state = nullptr;
   char *ring = nullptr;
   uint64_t k_host = 0;
+  uint64_t ring_gen = 0;            // bumped whenever k moves (steps, reset, step load)
+  uint64_t adv_gen = ~0ull;         // ring_gen when ws_advantages last ran
+  uint32_t adv_n = 0;               // ... over this many last steps
   uint64_t seed = 0;
   std::vector<int32_t> agents;      // economy agent counts (host copy)
   std::map<uint32_t, cudaGraphExec_t> graphs;
@@ -316,6 +319,8 @@ Layout make_layout(const ws_config *cfg, const std::vector<int32_t> &agents) {
   L.ring_force = r;
   if (cfg->env == WS_ENV_LANDSCAPE && (cfg->flags & WS_FLAG_FORCE))
     r += up(R * (size_t)cfg->dim * S * 4);
+  L.ring_adv = r;
+  if (cfg->flags & WS_FLAG_TRAIN) r += up(R * S * 4);
   L.ring_bytes = r;
   return L;
 }
@@ -422,6 +427,7 @@ void make_dev(ws_ctx *c) {
   d.r_wealth = cfg.env == WS_ENV_ECONOMY ? (int64_t *)(R + L.ring_wealth) : nullptr;
   d.r_energy = cfg.env == WS_ENV_LANDSCAPE ? (float *)(R + L.ring_energy) : nullptr;
   d.r_force = (cfg.flags & WS_FLAG_FORCE) ? (float *)(R + L.ring_force) : nullptr;
+  d.r_adv = (cfg.flags & WS_FLAG_TRAIN) ? (float *)(R + L.ring_adv) : nullptr;
 }
 
 void drop_graphs(ws_ctx *c) {
@@ -567,6 +573,9 @@ size_t ring_field_step_bytes(const ws_ctx *c, ws_field f, size_t *field_off) {
     case WS_F_FORCE:
       if (!(c->cfg.flags & WS_FLAG_FORCE)) return 0;
       *field_off = L.ring_force; return (size_t)c->cfg.dim * S * 4;
+    case WS_F_ADVANTAGE:
+      if (!(c->cfg.flags & WS_FLAG_TRAIN)) return 0;
+      *field_off = L.ring_adv; return S * 4;
     default: return 0;
   }
 }
@@ -640,6 +649,37 @@ ws_status after_params_changed(ws_ctx *c) {
     }
   }
   return cuda_check(c, cudaGetLastError(), "param derive");
+}
+
+// The update's policy / critic pairs: one over every slot, or the economy's
+// agents on slots [0, Sa) and planners on [Sa, S).
+int train_groups(const ws_ctx *c, TrainGroup (&g)[2]) {
+  const Layout &L = c->L;
+  float *crit0 = (float *)(c->state + L.critic_off);
+  g[0] = TrainGroup{(float *)c->d.params, crit0, L.pol, critic_shape(L.pol), 0u, L.n_agent_slots};
+  if (L.env != WS_ENV_ECONOMY) return 1;
+  g[1] = TrainGroup{(float *)c->d.params_planner,
+                    (float *)(c->state + L.critic_off + up(critic_shape(L.pol).count() * 4)),
+                    L.pol_planner, critic_shape(L.pol_planner), L.n_agent_slots, L.n_envs};
+  return 2;
+}
+
+// After an update: repack the BF16 images, then (stats != NULL) wait and
+// return the loss sums as means over the n x n_slots rows.
+ws_status finish_update(ws_ctx *c, const TrainBufs &tb, uint32_t n, double *stats, int n_stats,
+                        const char *what) {
+  ws_status s = cuda_check(c, cudaGetLastError(), what);
+  if (s == WS_OK) s = after_params_changed(c);
+  if (s == WS_OK && stats) {
+    double h[4];
+    s = cuda_check(c, cudaMemcpyAsync(h, tb.stats, 8 * n_stats, cudaMemcpyDeviceToHost, c->stream),
+                   "update stats");
+    if (s == WS_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream), "update stats sync");
+    const double R = (double)n * c->L.n_slots;
+    if (s == WS_OK)
+      for (int i = 0; i < n_stats; ++i) stats[i] = h[i] / R;
+  }
+  return s;
 }
 
 }  // namespace
@@ -773,6 +813,7 @@ ws_status ws_reset(ws_ctx *c, uint64_t seed) {
     cudaMemsetAsync(c->d.epart, 0, (size_t)kEnergyChunks * 2 * c->L.n_envs * 4, c->stream);
   launch_reset(c->d, c->stream);
   c->k_host = 0;
+  c->ring_gen += 1;
   return cuda_check(c, cudaGetLastError(), "reset");
 }
 
@@ -780,6 +821,7 @@ ws_status ws_step(ws_ctx *c) {
   if (!c) return WS_ERR_INVALID;
   if (c->err != WS_OK) return c->err;
   ws_status s = enqueue_steps(c, 1, c->stream);
+  c->ring_gen += 1;
   if (s == WS_OK) c->k_host += 1;
   return s;
 }
@@ -809,6 +851,7 @@ ws_status ws_rollout(ws_ctx *c, uint32_t n) {
       if (s == WS_OK) s = cuda_check(c, cudaGraphLaunch(g, c->stream), "graph launch");
     }
   }
+  c->ring_gen += 1;
   if (s == WS_OK) c->k_host += n;
   return s;
 }
@@ -827,32 +870,48 @@ ws_status ws_a2c_update(ws_ctx *c, uint32_t n, float lr, float c_v, float c_e, d
   if (!(c->cfg.flags & WS_FLAG_TRAIN)) return WS_ERR_STATE;
   if (n == 0 || n > c->k_host || n > c->L.ring_steps) return WS_ERR_RANGE;
   if (!std::isfinite(lr) || !std::isfinite(c_v) || !std::isfinite(c_e)) return WS_ERR_INVALID;
-  const Layout &L = c->L;
-  const TrainBufs tb = train_bufs((uint8_t *)c->state + L.train_off, L.pol);
-  float *crit0 = (float *)(c->state + L.critic_off);
+  const TrainBufs tb = train_bufs((uint8_t *)c->state + c->L.train_off, c->L.pol);
   TrainGroup g[2];
-  int ng = 1;
-  g[0] = TrainGroup{(float *)c->d.params, crit0, L.pol, critic_shape(L.pol), 0u, L.n_agent_slots};
-  if (L.env == WS_ENV_ECONOMY) {  // agents on slots [0, Sa), planners on [Sa, S)
-    g[1] = TrainGroup{(float *)c->d.params_planner,
-                      (float *)(c->state + L.critic_off + up(critic_shape(L.pol).count() * 4)),
-                      L.pol_planner, critic_shape(L.pol_planner), L.n_agent_slots, L.n_envs};
-    ng = 2;
-  }
+  const int ng = train_groups(c, g);
   launch_returns(c->d, n, c->stream);
   launch_a2c_update(c->d, tb, g, ng, n, lr, c_v, c_e, c->stream);
-  ws_status s = cuda_check(c, cudaGetLastError(), "a2c update");
-  if (s == WS_OK) s = after_params_changed(c);
-  if (s == WS_OK && stats) {
-    double h[3];
-    s = cuda_check(c, cudaMemcpyAsync(h, tb.stats, sizeof(h), cudaMemcpyDeviceToHost, c->stream),
-                   "a2c stats");
-    if (s == WS_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream), "a2c stats sync");
-    const double R = (double)n * c->L.n_slots;
-    if (s == WS_OK)
-      for (int i = 0; i < 3; ++i) stats[i] = h[i] / R;
+  return finish_update(c, tb, n, stats, 3, "a2c update");
+}
+
+ws_status ws_advantages(ws_ctx *c, uint32_t n) {
+  if (!c) return WS_ERR_INVALID;
+  if (c->err != WS_OK) return c->err;
+  if (!(c->cfg.flags & WS_FLAG_TRAIN)) return WS_ERR_STATE;
+  if (n == 0 || n > c->k_host || n > c->L.ring_steps) return WS_ERR_RANGE;
+  const TrainBufs tb = train_bufs((uint8_t *)c->state + c->L.train_off, c->L.pol);
+  TrainGroup g[2];
+  const int ng = train_groups(c, g);
+  launch_returns(c->d, n, c->stream);
+  launch_advantages(c->d, tb, g, ng, n, c->stream);
+  ws_status s = cuda_check(c, cudaGetLastError(), "advantages");
+  if (s == WS_OK) {
+    c->adv_gen = c->ring_gen;
+    c->adv_n = n;
   }
   return s;
+}
+
+ws_status ws_ppo_update(ws_ctx *c, uint32_t n, float lr, float eps, float c_v, float c_e,
+                        double *stats) {
+  if (!c) return WS_ERR_INVALID;
+  if (c->err != WS_OK) return c->err;
+  if (!(c->cfg.flags & WS_FLAG_TRAIN)) return WS_ERR_STATE;
+  if (c->L.env == WS_ENV_LANDSCAPE) return WS_ERR_INVALID;
+  if (!std::isfinite(lr) || !std::isfinite(c_v) || !std::isfinite(c_e) || !std::isfinite(eps) ||
+      !(eps > 0.f))
+    return WS_ERR_INVALID;
+  if (n == 0 || n > c->k_host || n > c->L.ring_steps) return WS_ERR_RANGE;
+  if (c->adv_gen != c->ring_gen || n > c->adv_n) return WS_ERR_STATE;
+  const TrainBufs tb = train_bufs((uint8_t *)c->state + c->L.train_off, c->L.pol);
+  TrainGroup g[2];
+  const int ng = train_groups(c, g);
+  launch_ppo_update(c->d, tb, g, ng, n, lr, eps, c_v, c_e, c->stream);
+  return finish_update(c, tb, n, stats, 4, "ppo update");
 }
 
 ws_status ws_forces(ws_ctx *c, uint32_t n) {
@@ -957,6 +1016,7 @@ ws_status ws_load(ws_ctx *c, ws_field f, const void *src, size_t src_bytes, int 
                              "load step");
     if (s != WS_OK) return s;
     c->k_host = k;
+    c->ring_gen += 1;
   }
   // pageable host sources are consumed before return
   if (!on_dev || k != UINT64_MAX) return cuda_check(c, cudaStreamSynchronize(c->stream), "load sync");

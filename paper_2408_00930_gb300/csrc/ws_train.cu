@@ -1,5 +1,5 @@
 // ws_train.cu -- actor-critic update consuming the trajectory ring in place
-// (ws_a2c_update).
+// (ws_a2c_update, ws_advantages, ws_ppo_update).
 //
 // Paper grounding: Sec. 2 and App. B keep roll-out and training on the GPU,
 // the roll-out store feeding the trainer with no host round trip.  The update
@@ -10,7 +10,11 @@
 // rows (observation s, action a, return G from the returns scan):
 //   A = G - V(s) (a constant of the actor's loss),
 //   L = (1/R) sum [ -A log pi(a|s) - c_e H(pi(.|s)) + c_v (G - V(s))^2 ],
-// then one SGD step on both networks.
+// then one SGD step on both networks.  PPO (clipped surrogate): the advantage
+// A = G - V(s) is computed once (ws_advantages, into the ring's ADVANTAGE
+// field) and held; each epoch replaces -A log pi with -min(rho A,
+// clip(rho, 1 - eps, 1 + eps) A), rho = pi(a|s) / exp(recorded logp), whose
+// gradient is A rho d log pi except where the min holds the clipped constant.
 //
 // FP32 SIMT throughout, in chunks of kTrainChunk rows: gather the chunk's rows from
 // the ring, forward both MLPs keeping the activations, the loss head
@@ -26,33 +30,61 @@ namespace {
 constexpr int kSliceRows = 512;    // rows per weight-gradient partial (128 x 128 GEMM)
 constexpr int kThinSlice = 128;    // rows per partial of the thin kernels (more blocks)
 
-// Row i of the chunk starting at global row q0 of a group: (step index t,
-// slot slot0 + s) with q = t * ns + s over the last n steps.
+// Ring offset (row of step, slot) of row i of the chunk starting at global
+// row q0 of a group: step index t and slot slot0 + s with q = t * ns + s over
+// the last n steps.
+__device__ __forceinline__ size_t ring_pos(const Dev &d, uint32_t n, size_t q0, uint32_t i,
+                                           uint32_t slot0, uint32_t ns, size_t *rowR) {
+  const size_t q = q0 + i;
+  const uint64_t k = d.k[0] - n + q / ns;
+  *rowR = (size_t)(k % d.ring_steps);
+  return slot0 + q % ns;
+}
+
+// The chunk's rows from the ring: obs, return, action (categorical), and for
+// PPO the held advantage and the recorded log-probability.
 __global__ void k_a2c_gather(Dev d, uint32_t n, size_t q0, uint32_t rows, uint32_t slot0,
-                             uint32_t ns, int od, TrainBufs tb) {
+                             uint32_t ns, int od, int ppo, TrainBufs tb) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
-  const size_t q = q0 + i, S = d.n_slots;
-  const uint64_t k = d.k[0] - n + q / ns;
-  const size_t rowR = (size_t)(k % d.ring_steps), s = slot0 + q % ns;
+  const size_t S = d.n_slots;
+  size_t rowR;
+  const size_t s = ring_pos(d, n, q0, i, slot0, ns, &rowR);
   for (int j = 0; j < od; ++j) tb.x[(size_t)i * od + j] = d.r_obs[(rowR * od + j) * S + s];
   tb.ret[i] = d.r_ret[rowR * S + s];
   if (d.env != WS_ENV_LANDSCAPE) tb.act[i] = ((const int32_t *)d.r_act)[rowR * S + s];
+  if (ppo) {
+    tb.adv[i] = d.r_adv[rowR * S + s];
+    tb.lpo[i] = d.r_logp[rowR * S + s];
+  }
 }
 
-// The three loss sums: reduced over the warp first, one atomic per warp (every
+// A = G - V(s) of the chunk's rows into the ADVANTAGE field.
+__global__ void k_adv_store(Dev d, uint32_t n, size_t q0, uint32_t rows, uint32_t slot0,
+                            uint32_t ns, TrainBufs tb) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  size_t rowR;
+  const size_t s = ring_pos(d, n, q0, i, slot0, ns, &rowR);
+  d.r_adv[rowR * d.n_slots + s] = tb.ret[i] - tb.vout[i];
+}
+
+// The loss sums: reduced over the warp first, one atomic per warp (every
 // thread of the warp calls it, rows past the end with zeros).
-__device__ __forceinline__ void add_stats(const TrainBufs &tb, double a, double b, double c) {
+__device__ __forceinline__ void add_stats(const TrainBufs &tb, double a, double b, double c,
+                                          double e) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_xor_sync(0xffffffffu, a, o);
     b += __shfl_xor_sync(0xffffffffu, b, o);
     c += __shfl_xor_sync(0xffffffffu, c, o);
+    e += __shfl_xor_sync(0xffffffffu, e, o);
   }
   if ((threadIdx.x & 31) == 0) {
     atomicAdd(tb.stats + 0, a);
     atomicAdd(tb.stats + 1, b);
     atomicAdd(tb.stats + 2, c);
+    atomicAdd(tb.stats + 3, e);
   }
 }
 
@@ -118,7 +150,47 @@ __global__ void k_a2c_head(Dev d, uint32_t n, size_t q0, uint32_t rows, uint32_t
     s_v = (double)(G - V) * (G - V);
     s_h = H;
   }
-  add_stats(tb, s_pg, s_v, s_h);
+  add_stats(tb, s_pg, s_v, s_h, 0.0);
+}
+
+// PPO head (categorical): per row rho = exp(log pi(a|s) - logp_old), the
+// surrogate min(rho A, clip(rho) A) and dL/dlogits = A rho (p - onehot(a))
+// (zero where A > 0 and rho > 1 + eps or A < 0 and rho < 1 - eps: the min then
+// holds the clipped constant) plus the entropy term, dL/dV as the A2C head;
+// the sums of -surrogate, (G - V)^2, H and the rows with |rho - 1| > eps.
+__global__ void k_ppo_head(uint32_t rows, int na, double inv_r, float eps, float c_v, float c_e,
+                           TrainBufs tb) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  double s_pg = 0.0, s_v = 0.0, s_h = 0.0, s_c = 0.0;
+  if (i < rows) {
+    float *lg = tb.out + (size_t)i * na;
+    float m = lg[0];
+    for (int c = 1; c < na; ++c) m = fmaxf(m, lg[c]);
+    float S = 0.f;
+    for (int c = 0; c < na; ++c) S += expf(lg[c] - m);
+    const float lS = logf(S);
+    float H = 0.f;
+    for (int c = 0; c < na; ++c) {
+      const float lp = (lg[c] - m) - lS;
+      H -= expf(lp) * lp;
+    }
+    const float V = tb.vout[i], G = tb.ret[i], A = tb.adv[i];
+    const int a = tb.act[i];
+    const float rho = expf(((lg[a] - m) - lS) - tb.lpo[i]);
+    const float rc = fminf(fmaxf(rho, 1.f - eps), 1.f + eps);
+    const bool held = (A > 0.f && rho > 1.f + eps) || (A < 0.f && rho < 1.f - eps);
+    const float gA = held ? 0.f : A * rho;
+    for (int c = 0; c < na; ++c) {
+      const float lp = (lg[c] - m) - lS, p = expf(lp);
+      lg[c] = (float)((gA * (p - (c == a ? 1.f : 0.f)) + c_e * p * (lp + H)) * inv_r);
+    }
+    tb.vout[i] = (float)(2.0 * c_v * (V - G) * inv_r);
+    s_pg = -(double)fminf(rho * A, rc * A);
+    s_v = (double)(G - V) * (G - V);
+    s_h = H;
+    s_c = fabsf(rho - 1.f) > eps ? 1.0 : 0.0;
+  }
+  add_stats(tb, s_pg, s_v, s_h, s_c);
 }
 
 // FP32 GEMM C[M][N] = sum_k A(m, k) B(k, n) over k in [k_lo, k_hi), with
@@ -466,9 +538,9 @@ void mlp_backward(const PolicyShape &sh, const float *params, const float *X, co
   }
 }
 
-}  // namespace
-
-size_t train_scratch_bytes(const PolicyShape &pol) {
+// The scratch of one update chunk, carved from base (or, with base null, only
+// measured): returns its size in bytes.
+size_t train_layout(uint8_t *base, const PolicyShape &pol, TrainBufs *t) {
   const PolicyShape crit{{pol.w[0], pol.w[1], pol.w[2], 1}};
   const size_t CH = kTrainChunk, w0 = pol.w[0], H0 = pol.w[1], H1 = pol.w[2], NA = pol.w[3];
   const size_t hmax = H0 > H1 ? H0 : H1;
@@ -483,69 +555,51 @@ size_t train_scratch_bytes(const PolicyShape &pol) {
     const size_t vc = (CH + src - 1) / src * lenc;
     if (vc > part_len) part_len = vc;
   }
-  size_t b = 0;
-  auto add = [&](size_t n) { b += (n + 63) / 64 * 64; };
-  add(CH * w0 * 4);              // x
-  add(CH * 4);                   // ret
-  add(CH * 4);                   // act
-  add(CH * H0 * 4);              // actor h1
-  add(CH * H1 * 4);              // actor h2
-  add(CH * NA * 4);              // logits / dlogits
-  add(CH * H0 * 4);              // critic h1
-  add(CH * H1 * 4);              // critic h2
-  add(CH * 4);                   // v / dv
-  add(CH * hmax * 4);            // d1
-  add(CH * hmax * 4);            // d2
-  add(part_len * 4);             // weight-gradient partials
-  add(3 * 8);                    // stats
-  add((pol.count() + crit.count()) * 4);  // gradients
-  return b;
-}
-
-TrainBufs train_bufs(uint8_t *base, const PolicyShape &pol) {
-  const PolicyShape crit{{pol.w[0], pol.w[1], pol.w[2], 1}};
-  const size_t CH = kTrainChunk, w0 = pol.w[0], H0 = pol.w[1], H1 = pol.w[2], NA = pol.w[3];
-  const size_t hmax = H0 > H1 ? H0 : H1;
-  size_t part_len = 0;  // the largest slice-partial set over the layers of both networks
-  for (int l = 0; l < kMaxLayers; ++l) {
-    const size_t len = (size_t)(pol.w[l] + 1) * pol.w[l + 1];
-    const size_t sr = (size_t)slice_rows(pol.w[l], pol.w[l + 1]);
-    const size_t v = (CH + sr - 1) / sr * len;
-    if (v > part_len) part_len = v;
-    const size_t lenc = (size_t)(crit.w[l] + 1) * crit.w[l + 1];
-    const size_t src = (size_t)slice_rows(crit.w[l], crit.w[l + 1]);
-    const size_t vc = (CH + src - 1) / src * lenc;
-    if (vc > part_len) part_len = vc;
-  }
-  TrainBufs t{};
   size_t o = 0;
   auto take = [&](size_t n) {
-    uint8_t *p = base + o;
+    uint8_t *p = base ? base + o : nullptr;
     o += (n + 63) / 64 * 64;
     return p;
   };
-  t.x = (float *)take(CH * w0 * 4);
-  t.ret = (float *)take(CH * 4);
-  t.act = (int32_t *)take(CH * 4);
-  t.h1 = (float *)take(CH * H0 * 4);
-  t.h2 = (float *)take(CH * H1 * 4);
-  t.out = (float *)take(CH * NA * 4);
-  t.c1 = (float *)take(CH * H0 * 4);
-  t.c2 = (float *)take(CH * H1 * 4);
-  t.vout = (float *)take(CH * 4);
-  t.d1 = (float *)take(CH * hmax * 4);
-  t.d2 = (float *)take(CH * hmax * 4);
-  t.part = (float *)take(part_len * 4);
-  t.stats = (double *)take(3 * 8);
-  t.grad = (float *)take((pol.count() + crit.count()) * 4);
+  TrainBufs b{};
+  b.x = (float *)take(CH * w0 * 4);
+  b.ret = (float *)take(CH * 4);
+  b.act = (int32_t *)take(CH * 4);
+  b.adv = (float *)take(CH * 4);
+  b.lpo = (float *)take(CH * 4);
+  b.h1 = (float *)take(CH * H0 * 4);    // actor activations
+  b.h2 = (float *)take(CH * H1 * 4);
+  b.out = (float *)take(CH * NA * 4);   // logits, then dL/dlogits
+  b.c1 = (float *)take(CH * H0 * 4);    // critic activations
+  b.c2 = (float *)take(CH * H1 * 4);
+  b.vout = (float *)take(CH * 4);       // V, then dL/dV
+  b.d1 = (float *)take(CH * hmax * 4);  // data gradients
+  b.d2 = (float *)take(CH * hmax * 4);
+  b.part = (float *)take(part_len * 4); // weight-gradient partials
+  b.stats = (double *)take(4 * 8);
+  b.grad = (float *)take((pol.count() + crit.count()) * 4);
+  if (t) *t = b;
+  return o;
+}
+
+}  // namespace
+
+size_t train_scratch_bytes(const PolicyShape &pol) { return train_layout(nullptr, pol, nullptr); }
+
+TrainBufs train_bufs(uint8_t *base, const PolicyShape &pol) {
+  TrainBufs t;
+  train_layout(base, pol, &t);
   return t;
 }
 
+namespace {
+
 // Per group (the economy: agents, then planners; else one group of all
-// slots): gradients over the group's rows in chunks, then the SGD step.
-void launch_a2c_update(const Dev &d, const TrainBufs &tb, const TrainGroup *groups, int n_groups,
-                       uint32_t n, float lr, float c_v, float c_e, cudaStream_t st) {
-  cudaMemsetAsync(tb.stats, 0, 3 * 8, st);
+// slots): gradients over the group's rows in chunks, then the SGD step.  ppo
+// selects the clipped-surrogate head (eps) over the A2C head.
+void run_update(const Dev &d, const TrainBufs &tb, const TrainGroup *groups, int n_groups,
+                uint32_t n, float lr, float c_v, float c_e, bool ppo, float eps, cudaStream_t st) {
+  cudaMemsetAsync(tb.stats, 0, 4 * 8, st);
   for (int gi = 0; gi < n_groups; ++gi) {
     const TrainGroup &G = groups[gi];
     const size_t R = (size_t)n * G.n_slots;
@@ -556,17 +610,50 @@ void launch_a2c_update(const Dev &d, const TrainBufs &tb, const TrainGroup *grou
     for (size_t q0 = 0; q0 < R; q0 += kTrainChunk) {
       const int rows = (int)((R - q0) < (size_t)kTrainChunk ? (R - q0) : (size_t)kTrainChunk);
       k_a2c_gather<<<nblk(rows, 256), 256, 0, st>>>(d, n, q0, (uint32_t)rows, G.slot0, G.n_slots,
-                                                    G.pol.w[0], tb);
+                                                    G.pol.w[0], ppo ? 1 : 0, tb);
       mlp_forward(G.pol, G.params, tb.x, tb.h1, tb.h2, tb.out, rows, st);
       mlp_forward(G.crit, G.critic, tb.x, tb.c1, tb.c2, tb.vout, rows, st);
-      k_a2c_head<<<nblk(rows, 256), 256, 0, st>>>(d, n, q0, (uint32_t)rows, G.n_slots, G.pol.w[3],
-                                                  inv_r, c_v, c_e, tb);
+      if (ppo)
+        k_ppo_head<<<nblk(rows, 256), 256, 0, st>>>((uint32_t)rows, G.pol.w[3], inv_r, eps, c_v,
+                                                    c_e, tb);
+      else
+        k_a2c_head<<<nblk(rows, 256), 256, 0, st>>>(d, n, q0, (uint32_t)rows, G.n_slots,
+                                                    G.pol.w[3], inv_r, c_v, c_e, tb);
       mlp_backward(G.pol, G.params, tb.x, tb.h1, tb.h2, tb.out, ga, tb.d1, tb.d2, tb.part, rows, st);
       mlp_backward(G.crit, G.critic, tb.x, tb.c1, tb.c2, tb.vout, gc, tb.d1, tb.d2, tb.part, rows,
                    st);
     }
     k_sgd<<<nblk(na, 256), 256, 0, st>>>(G.params, ga, na, lr);
     k_sgd<<<nblk(nc, 256), 256, 0, st>>>(G.critic, gc, nc, lr);
+  }
+}
+
+}  // namespace
+
+void launch_a2c_update(const Dev &d, const TrainBufs &tb, const TrainGroup *groups, int n_groups,
+                       uint32_t n, float lr, float c_v, float c_e, cudaStream_t st) {
+  run_update(d, tb, groups, n_groups, n, lr, c_v, c_e, false, 0.f, st);
+}
+
+void launch_ppo_update(const Dev &d, const TrainBufs &tb, const TrainGroup *groups, int n_groups,
+                       uint32_t n, float lr, float eps, float c_v, float c_e, cudaStream_t st) {
+  run_update(d, tb, groups, n_groups, n, lr, c_v, c_e, true, eps, st);
+}
+
+// Per group and chunk: gather, the critic's forward, A = G - V into the ring.
+void launch_advantages(const Dev &d, const TrainBufs &tb, const TrainGroup *groups, int n_groups,
+                       uint32_t n, cudaStream_t st) {
+  for (int gi = 0; gi < n_groups; ++gi) {
+    const TrainGroup &G = groups[gi];
+    const size_t R = (size_t)n * G.n_slots;
+    for (size_t q0 = 0; q0 < R; q0 += kTrainChunk) {
+      const int rows = (int)((R - q0) < (size_t)kTrainChunk ? (R - q0) : (size_t)kTrainChunk);
+      k_a2c_gather<<<nblk(rows, 256), 256, 0, st>>>(d, n, q0, (uint32_t)rows, G.slot0, G.n_slots,
+                                                    G.pol.w[0], 0, tb);
+      mlp_forward(G.crit, G.critic, tb.x, tb.c1, tb.c2, tb.vout, rows, st);
+      k_adv_store<<<nblk(rows, 256), 256, 0, st>>>(d, n, q0, (uint32_t)rows, G.slot0, G.n_slots,
+                                                   tb);
+    }
   }
 }
 

@@ -24,10 +24,11 @@ STATUS_NAMES = {0: "WS_OK", 1: "WS_ERR_INVALID", 2: "WS_ERR_NOMEM", 3: "WS_ERR_C
 WS_ENV_CONTROL, WS_ENV_ECONOMY, WS_ENV_LANDSCAPE, WS_ENV_ACROBOT = 0, 1, 2, 3
 WS_PATH_PLAIN_FP32, WS_PATH_BATCHED_FP32, WS_PATH_BATCHED_BF16 = 0, 1, 2
 (WS_F_OBS, WS_F_ACTION, WS_F_LOGP, WS_F_REWARD, WS_F_DONE, WS_F_RETURN, WS_F_WEALTH, WS_F_ENERGY,
- WS_F_STATE, WS_F_PARAMS, WS_F_ENV_PARAMS, WS_F_LOGITS, WS_F_FORCE, WS_F_CRITIC) = range(14)
+ WS_F_STATE, WS_F_PARAMS, WS_F_ENV_PARAMS, WS_F_LOGITS, WS_F_FORCE, WS_F_CRITIC,
+ WS_F_ADVANTAGE) = range(15)
 
 EXPORTED = ["ws_query_bytes", "ws_create", "ws_reset", "ws_step", "ws_rollout", "ws_returns",
-            "ws_forces", "ws_a2c_update",
+            "ws_forces", "ws_a2c_update", "ws_advantages", "ws_ppo_update",
             "ws_fetch", "ws_load", "ws_get_step", "ws_sync", "ws_last_error", "ws_destroy",
             "ws_policy_forward_noalloc", "ws_get_launch", "ws_set_launch", "ws_tune",
             "ws_server_create", "ws_server_submit",
@@ -106,6 +107,9 @@ def lib():
         L.ws_forces.argtypes = [P, C.c_uint32]
         L.ws_a2c_update.argtypes = [P, C.c_uint32, C.c_float, C.c_float, C.c_float,
                                     C.POINTER(C.c_double)]
+        L.ws_advantages.argtypes = [P, C.c_uint32]
+        L.ws_ppo_update.argtypes = [P, C.c_uint32, C.c_float, C.c_float, C.c_float, C.c_float,
+                                    C.POINTER(C.c_double)]
         L.ws_fetch.argtypes = [P, C.c_int, C.c_uint64, C.c_uint32, P, C.c_size_t, C.c_int]
         L.ws_load.argtypes = [P, C.c_int, P, C.c_size_t, C.c_int, C.c_uint64]
         L.ws_get_step.argtypes = [P, C.POINTER(C.c_uint64)]
@@ -172,6 +176,15 @@ def ws_forces(ctx, n_steps):
 def ws_a2c_update(ctx, n_steps, lr, c_v, c_e, stats=None):
     """stats: a ctypes c_double * 3 (or None)."""
     return lib().ws_a2c_update(ctx, n_steps, lr, c_v, c_e, stats)
+
+
+def ws_advantages(ctx, n_steps):
+    return lib().ws_advantages(ctx, n_steps)
+
+
+def ws_ppo_update(ctx, n_steps, lr, clip_eps, c_v, c_e, stats=None):
+    """stats: a ctypes c_double * 4 (or None)."""
+    return lib().ws_ppo_update(ctx, n_steps, lr, clip_eps, c_v, c_e, stats)
 
 
 def ws_fetch(ctx, field, t0, n_steps, dst_ptr, dst_bytes, dst_on_device):
@@ -301,6 +314,17 @@ class Rollout:
         self._ok(ws_a2c_update(self.ctx, n, lr, c_v, c_e, st), "ws_a2c_update")
         return np.array(st[:])
 
+    def advantages(self, n):
+        """Returns, then A = G - V(s) of the last n steps into ADVANTAGE."""
+        self._ok(ws_advantages(self.ctx, n), "ws_advantages")
+
+    def ppo_update(self, n, lr, clip_eps=0.2, c_v=0.5, c_e=0.0):
+        """One PPO epoch on the last n steps (after advantages(n)); returns the
+        means of -surrogate, (G - V)^2, the entropy and the clipped fraction."""
+        st = (C.c_double * 4)()
+        self._ok(ws_ppo_update(self.ctx, n, lr, clip_eps, c_v, c_e, st), "ws_ppo_update")
+        return np.array(st[:])
+
     def sync(self, timeout_ms=0):
         self._ok(ws_sync(self.ctx, timeout_ms), "ws_sync")
 
@@ -339,7 +363,7 @@ class Rollout:
         if field == WS_F_ACTION:
             return ((np.float32, (self.dim, S)) if self.env == WS_ENV_LANDSCAPE
                     else (np.int32, (S,)))
-        if field in (WS_F_LOGP, WS_F_REWARD, WS_F_RETURN, WS_F_ENERGY):
+        if field in (WS_F_LOGP, WS_F_REWARD, WS_F_RETURN, WS_F_ENERGY, WS_F_ADVANTAGE):
             return np.float32, (S,)
         if field == WS_F_DONE:
             return np.uint8, (S,)
