@@ -115,6 +115,8 @@ def _declare(L):
                                C.c_double, C.c_double, _P, _P, _P]
     L.or_ppo.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P, _P, _P,
                          C.c_double, C.c_double, C.c_double, _P, _P, _P]
+    L.or_ppo_gauss.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P, _P, _P,
+                               C.c_double, C.c_double, C.c_double, _P, _P, _P]
 
 
 def _ptr(a):
@@ -482,6 +484,24 @@ def ppo(actor, critic, obs, act, ret, adv, logp_old, h0, h1, n_act, eps, c_v=0.5
                  _ptr(o), _ptr(_arr(act, np.int32)), _ptr(_arr(ret, np.float64)),
                  _ptr(_arr(adv, np.float64)), _ptr(_arr(logp_old, np.float64)), float(eps),
                  float(c_v), float(c_e), _ptr(ga), _ptr(gc), _ptr(st))
+    return st, ga, gc
+
+
+def ppo_gauss(actor, critic, obs, u, ret, adv, logp_old, h0, h1, eps, c_v=0.5, c_e=0.0,
+              grads=True):
+    """PPO for the diagonal Gaussian head (or_ppo_gauss): u [R][D] the
+    behaviour samples (unclipped), logp_old their recorded log-densities."""
+    o = _arr(obs, np.float64)
+    R, D = o.shape
+    na = policy_param_count([D, h0, h1, 2 * D])
+    nc = policy_param_count([D, h0, h1, 1])
+    ga = np.empty(na) if grads else None
+    gc = np.empty(nc) if grads else None
+    st = np.empty(4)
+    lib().or_ppo_gauss(R, D, h0, h1, _ptr(_arr(actor, np.float32)), _ptr(_arr(critic, np.float32)),
+                       _ptr(o), _ptr(_arr(u, np.float64)), _ptr(_arr(ret, np.float64)),
+                       _ptr(_arr(adv, np.float64)), _ptr(_arr(logp_old, np.float64)), float(eps),
+                       float(c_v), float(c_e), _ptr(ga), _ptr(gc), _ptr(st))
     return st, ga, gc
 
 

@@ -1153,6 +1153,84 @@ void or_ppo(int R, int obs_dim, int n_act, int h0, int h1, const float *actor, c
   or_trace_free(&tc);
 }
 
+/* PPO for the diagonal Gaussian head (landscape) [reading]: the behaviour */
+/* sample u [R][D] is the unclipped mean + sigma z of the policy held at   */
+/* the advantage pass, logp_old its recorded log-density; at the current   */
+/* parameters y_j = (u_j - mean_j) / sigma_j and                            */
+/*   log pi(u) = sum_j (-y_j^2 / 2 - log sigma_j - log(2 pi) / 2),          */
+/*   d log pi / d mean_j = y_j / sigma_j, d log pi / d raw_j = y_j^2 - 1,   */
+/* with H and the clamp of log sigma as in or_a2c_gauss; the surrogate, the */
+/* held side of the clip and the stats as in or_ppo.                        */
+void or_ppo_gauss(int R, int D, int h0, int h1, const float *actor, const float *critic,
+                  const double *obs, const double *u, const double *ret, const double *adv,
+                  const double *logp_old, double eps, double c_v, double c_e, double *grad_actor,
+                  double *grad_critic, double stats[4]) {
+  int32_t wa[4] = {D, h0, h1, 2 * D}, wc[4] = {D, h0, h1, 1};
+  long na = 0, nc = 0;
+  for (int l = 0; l < 3; ++l) {
+    na += (long)wa[l] * wa[l + 1] + wa[l + 1];
+    nc += (long)wc[l] * wc[l + 1] + wc[l + 1];
+  }
+  if (grad_actor) memset(grad_actor, 0, sizeof(double) * na);
+  if (grad_critic) memset(grad_critic, 0, sizeof(double) * nc);
+  or_trace ta, tc;
+  or_trace_alloc(&ta, wa);
+  or_trace_alloc(&tc, wc);
+  double *y = (double *)malloc(sizeof(double) * D);
+  double *sg = (double *)malloc(sizeof(double) * D);
+  double *dl = (double *)malloc(sizeof(double) * 2 * D);
+  const double half_log_2pi = 0.5 * log(2.0 * M_PI);
+  double s_pg = 0.0, s_v = 0.0, s_h = 0.0, s_clip = 0.0;
+  for (int i = 0; i < R; ++i) {
+    or_mlp_trace(wa, actor, obs + (long)i * D, &ta);
+    or_mlp_trace(wc, critic, obs + (long)i * D, &tc);
+    const double *out = ta.a[3], *ui = u + (long)i * D;
+    double logp = 0.0, H = 0.0;
+    for (int j = 0; j < D; ++j) {
+      const double raw = out[D + j];
+      const double ls = raw < -5.0 ? -5.0 : (raw > 2.0 ? 2.0 : raw);
+      sg[j] = exp(ls);
+      y[j] = (ui[j] - out[j]) / sg[j];
+      logp += -0.5 * y[j] * y[j] - ls - half_log_2pi;
+      H += ls + 0.5 + half_log_2pi;
+    }
+    const double A = adv[i], V = tc.a[3][0];
+    const double rho = exp(logp - logp_old[i]);
+    const double rc = rho < 1.0 - eps ? 1.0 - eps : (rho > 1.0 + eps ? 1.0 + eps : rho);
+    const double surr = rho * A < rc * A ? rho * A : rc * A;
+    const int held = (A > 0.0 && rho > 1.0 + eps) || (A < 0.0 && rho < 1.0 - eps);
+    const double gA = held ? 0.0 : A * rho;  /* d(-surrogate)/d log pi = -gA */
+    s_pg += -surr;
+    s_v += (ret[i] - V) * (ret[i] - V);
+    s_h += H;
+    s_clip += fabs(rho - 1.0) > eps ? 1.0 : 0.0;
+    if (grad_actor) {
+      for (int j = 0; j < D; ++j) {
+        const double raw = out[D + j];
+        const int free_ls = raw > -5.0 && raw < 2.0;
+        dl[j] = -gA * y[j] / sg[j] / R;
+        dl[D + j] = free_ls ? (-gA * (y[j] * y[j] - 1.0) - c_e) / R : 0.0;
+      }
+      or_mlp_backward(wa, actor, &ta, dl, grad_actor);
+    }
+    if (grad_critic) {
+      double dv = 2.0 * c_v * (V - ret[i]) / R;
+      or_mlp_backward(wc, critic, &tc, &dv, grad_critic);
+    }
+  }
+  if (stats) {
+    stats[0] = s_pg / R;
+    stats[1] = s_v / R;
+    stats[2] = s_h / R;
+    stats[3] = s_clip / R;
+  }
+  free(y);
+  free(sg);
+  free(dl);
+  or_trace_free(&ta);
+  or_trace_free(&tc);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Discounted returns over a window of n_steps records ([n_steps][n_slots]):*/
 /*   G_t = r_t + gamma (1 - d_t) G_{t+1},  G_{n_steps} = 0.                 */

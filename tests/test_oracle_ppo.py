@@ -3,7 +3,10 @@ finite differences of the loss with rows in all three regimes of the clip
 (below, inside and above [1 - eps, 1 + eps]), PyTorch autograd (float64) on the
 loss written with torch.minimum / torch.clamp, the reduction to the actor-critic
 gradient when the behaviour policy is the current one and eps is unbounded,
-and the fully clipped case, where the surrogate passes no gradient."""
+and the fully clipped case, where the surrogate passes no gradient; for the
+categorical head and for the diagonal Gaussian head (behaviour samples scored
+under the current mean and sigma, the clamp of log sigma binding on some
+outputs; on policy it reduces to the Gaussian actor-critic gradient)."""
 import numpy as np
 import pytest
 
@@ -148,3 +151,101 @@ def test_ppo_fully_clipped_passes_no_policy_gradient(orc):
     st, ga, _ = orc.ppo(actor, critic, obs, act, ret, adv, lp + np.sign(adv) * 0.5, h, h, na, eps,
                         0.5, 0.0)
     assert np.abs(ga).max() > 1e-3 and st[3] == 1.0
+
+
+def gauss_setup(seed=0, R=48, D=3, h=8, spread=0.6):
+    """Gaussian head: samples u = mean + sigma z of the actor itself, the
+    behaviour log-densities moved by up to +-spread (rows in all clip regimes);
+    the actor's scale makes the clamp of log sigma bind on some outputs."""
+    from oracle import mlp_forward
+    g = inputs.rng(seed)
+    actor = inputs.policy_params(g, [D, h, h, 2 * D], scale=3.0)
+    critic = inputs.policy_params(g, [D, h, h, 1], scale=2.0)
+    obs, z = g.normal(size=(R, D)), g.normal(size=(R, D))
+    out = np.asarray(mlp_forward([D, h, h, 2 * D], actor, obs))
+    ls = np.clip(out[:, D:], -5.0, 2.0)
+    u = out[:, :D] + np.exp(ls) * z
+    lp = (-0.5 * z * z - ls - 0.5 * np.log(2 * np.pi)).sum(1)
+    ret, adv = g.normal(size=R) * 3, g.normal(size=R) * 2
+    return actor, critic, obs, z, u, lp, lp + g.uniform(-spread, spread, R), ret, adv, h, out
+
+
+def test_ppo_gauss_gradient_matches_finite_differences(orc):
+    eps, c_v, c_e = 0.2, 0.5, 0.01
+    actor, critic, obs, _, u, lp, lpo, ret, adv, h, out = gauss_setup()
+    D = obs.shape[1]
+    rho = np.exp(lp - lpo)
+    assert (rho < 1 - eps).sum() >= 5 and (rho > 1 + eps).sum() >= 5
+    assert (np.abs(rho - 1) < eps).sum() >= 5
+    assert np.abs(np.abs(rho - 1) - eps).min() > 1e-3
+    raw = out[:, D:]
+    assert (raw < -5).any() or (raw > 2).any()          # the clamp binds somewhere
+    st, ga, gc = orc.ppo_gauss(actor, critic, obs, u, ret, adv, lpo, h, h, eps, c_v, c_e)
+    assert st[3] == pytest.approx(np.mean(np.abs(rho - 1) > eps), abs=0)
+    g = np.random.default_rng(3)
+    for idx in g.choice(len(actor), 30, replace=False):
+        up, dn = actor.copy(), actor.copy()
+        up[idx] += np.float32(2.0 ** -16)
+        dn[idx] -= np.float32(2.0 ** -16)
+        lu = total(orc.ppo_gauss(up, critic, obs, u, ret, adv, lpo, h, h, eps, c_v, c_e,
+                                 grads=False)[0], 0.0, c_e)
+        ld = total(orc.ppo_gauss(dn, critic, obs, u, ret, adv, lpo, h, h, eps, c_v, c_e,
+                                 grads=False)[0], 0.0, c_e)
+        fd = (lu - ld) / (float(up[idx]) - float(dn[idx]))
+        assert fd == pytest.approx(ga[idx], rel=2e-6, abs=1e-10), idx
+
+
+def test_ppo_gauss_matches_torch_autograd(orc):
+    torch = pytest.importorskip("torch")
+    eps, c_v, c_e = 0.15, 0.3, 0.02
+    actor, critic, obs, _, u, _, lpo, ret, adv, h, _ = gauss_setup(seed=5, R=64, D=4)
+    D = obs.shape[1]
+    st, ga, gc = orc.ppo_gauss(actor, critic, obs, u, ret, adv, lpo, h, h, eps, c_v, c_e)
+
+    def layers(p, w):
+        out, off = [], 0
+        for a, b in zip(w[:-1], w[1:]):
+            out.append(torch.tensor(p[off:off + a * b].reshape(a, b), dtype=torch.float64,
+                                    requires_grad=True))
+            out.append(torch.tensor(p[off + a * b:off + a * b + b], dtype=torch.float64,
+                                    requires_grad=True))
+            off += a * b + b
+        return out
+
+    def mlp(ps, x):
+        for i in range(3):
+            x = x @ ps[2 * i] + ps[2 * i + 1]
+            if i < 2:
+                x = torch.tanh(x)
+        return x
+
+    pa, pc = layers(actor, [D, h, h, 2 * D]), layers(critic, [D, h, h, 1])
+    x = torch.tensor(obs)
+    out, v = mlp(pa, x), mlp(pc, x)[:, 0]
+    mean, ls = out[:, :D], torch.clamp(out[:, D:], -5.0, 2.0)
+    dist = torch.distributions.Normal(mean, torch.exp(ls))
+    logp = dist.log_prob(torch.tensor(u)).sum(1)
+    A, G = torch.tensor(adv), torch.tensor(ret)
+    rho = torch.exp(logp - torch.tensor(lpo))
+    surr = torch.minimum(rho * A, torch.clamp(rho, 1 - eps, 1 + eps) * A)
+    ent = dist.entropy().sum(1)
+    loss = -surr.mean() + c_v * ((G - v) ** 2).mean() - c_e * ent.mean()
+    loss.backward()
+    ref_a = np.concatenate([t.grad.numpy().ravel() for t in pa])
+    ref_c = np.concatenate([t.grad.numpy().ravel() for t in pc])
+    np.testing.assert_allclose(ga, ref_a, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(gc, ref_c, rtol=1e-9, atol=1e-12)
+    assert st[0] == pytest.approx(float(-surr.mean().detach()), rel=1e-12)
+    assert st[2] == pytest.approx(float(ent.mean().detach()), rel=1e-12)
+    assert 0 < st[3] < 1
+
+
+def test_ppo_gauss_reduces_to_actor_critic_on_policy(orc):
+    """u = mean + sigma z of the current actor, logp_old its own density and
+    eps unbounded: the gradient of or_a2c_gauss with the same normals z."""
+    actor, critic, obs, z, u, lp, _, ret, adv, h, _ = gauss_setup(seed=8)
+    st, ga, gc = orc.ppo_gauss(actor, critic, obs, u, ret, adv, lp, h, h, 1e9, 0.5, 0.02)
+    st2, ga2, gc2 = orc.a2c_gauss(actor, critic, obs, z, ret, h, h, c_v=0.5, c_e=0.02, adv=adv)
+    np.testing.assert_allclose(ga, ga2, rtol=1e-9, atol=1e-13)
+    np.testing.assert_allclose(gc, gc2, rtol=1e-12, atol=1e-15)
+    assert st[1:3] == pytest.approx(st2[1:3], rel=1e-12) and st[3] == 0
