@@ -91,6 +91,9 @@ typedef enum { WS_PATH_PLAIN_FP32 = 0, WS_PATH_BATCHED_FP32 = 1, WS_PATH_BATCHED
  *   FORCE   f32 [t][dim][n_slots]       landscape with WS_FLAG_FORCE: -grad E
  *                                       of the post-step state (ws_forces)
  *   ADVANTAGE f32 [t][n_slots]          WS_FLAG_TRAIN: G - V(s) (ws_advantages)
+ *   SAMPLE  f32 [t][dim][n_slots]       landscape with WS_FLAG_TRAIN: the
+ *                                       unclipped Gaussian sample mean + sigma z
+ *                                       of each step (ws_advantages)
  * State fields (no step range; t0 and n_steps must be 0):
  *   STATE   control:   f32 s[4][n_envs] (x, v, th, w), i32 t[n_envs]
  *           acrobot:   f32 s[4][n_envs] (th1, th2, w1, w2), i32 t[n_envs]
@@ -120,7 +123,8 @@ typedef enum {
   WS_F_LOGITS = 11,
   WS_F_FORCE = 12,
   WS_F_CRITIC = 13,
-  WS_F_ADVANTAGE = 14
+  WS_F_ADVANTAGE = 14,
+  WS_F_SAMPLE = 15
 } ws_field;
 
 /* ws_config.flags: the fused kernels (economy on the BF16 path) also write each
@@ -139,7 +143,8 @@ typedef enum {
 /* ws_config.flags: the context also holds a critic per policy (an MLP obs ->
  * hidden0 -> hidden1 -> 1, drawn from param_seed like the policies; the
  * economy's agents and planners have one each), the scratch of
- * ws_a2c_update and ws_ppo_update, and the ring's ADVANTAGE field. */
+ * ws_a2c_update and ws_ppo_update, and the ring's ADVANTAGE (and, for the
+ * landscape, SAMPLE) field. */
 #define WS_FLAG_TRAIN 8u
 
 /* Roll-out configuration.  Slots: control and landscape have one agent per
@@ -222,27 +227,31 @@ ws_status ws_a2c_update(ws_ctx *ctx, uint32_t n_steps, float lr, float c_v, floa
 /* Advantages for a PPO update over the last n_steps ring rows (steps
  * k-n..k-1): the returns scan (into RETURN), then A = G - V(s) under the
  * critic as it is now, written to the ADVANTAGE field, where it stays fixed
- * for the epochs of ws_ppo_update that follow.  Asynchronous.  Needs
+ * for the epochs of ws_ppo_update that follow.  Landscape: also each row's
+ * behaviour sample u = mean + sigma z (before the step clip) under the policy
+ * as it is now, with the row's Philox normals z as the sampler drew them, into
+ * the SAMPLE field (the ring keeps only the clipped step).  Asynchronous.  Needs
  * WS_FLAG_TRAIN (WS_ERR_STATE); n_steps <= min(k, ring_steps) (WS_ERR_RANGE). */
 ws_status ws_advantages(ws_ctx *ctx, uint32_t n_steps);
 
 /* One epoch of proximal policy optimisation (clipped surrogate) on the last
  * n_steps ring rows, in place (paper Sec. 2: the roll-out store feeds the
- * actor-critic trainer on the GPU).  Per row (obs s, action a, recorded
- * log-probability logp_old of the behaviour policy, return G, advantage A
- * from ws_advantages): rho = exp(log pi(a|s) - logp_old) and
+ * actor-critic trainer on the GPU; Sec. 3: actor-critic for discrete and
+ * continuous actions).  Per row (obs s, action a, recorded log-probability
+ * logp_old of the behaviour policy, return G, advantage A from
+ * ws_advantages): rho = exp(log pi(a|s) - logp_old) and
  *   L = (1/R) sum [ -min(rho A, clip(rho, 1 - clip_eps, 1 + clip_eps) A)
  *                   - c_e H(pi(.|s)) + c_v (G - V(s))^2 ],
  * then one SGD step of rate lr on the policy and the critic (FP32; the BF16
- * operand images are repacked).  The economy's agents and planners are two
- * such updates, each over its own rows.  Call it once per epoch: A stays
+ * operand images are repacked).  The landscape's diagonal Gaussian head scores
+ * the SAMPLE field's u as its action.  The economy's agents and planners are
+ * two such updates, each over its own rows.  Call it once per epoch: A stays
  * fixed, rho moves with the policy.  stats (host, may be NULL; the call then
  * waits for the stream): the means over all rows of -min(..), (G - V)^2, H,
  * and the fraction of rows with |rho - 1| > clip_eps.
  * Errors: WS_ERR_STATE without WS_FLAG_TRAIN, or unless ws_advantages covered
  * these n_steps rows since the last step, roll-out, reset or step-counter load;
- * WS_ERR_INVALID for the landscape (its ring keeps the clipped step, not the
- * Gaussian sample whose probability the ratio needs) or clip_eps not > 0. */
+ * WS_ERR_INVALID for clip_eps not > 0 or a non-finite argument. */
 ws_status ws_ppo_update(ws_ctx *ctx, uint32_t n_steps, float lr, float clip_eps, float c_v,
                         float c_e, double *stats);
 

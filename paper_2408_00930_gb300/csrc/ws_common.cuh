@@ -135,6 +135,7 @@ struct Layout {
   size_t ring_obs, ring_act, ring_logp, ring_rew, ring_done, ring_ret, ring_wealth, ring_energy;
   size_t ring_force;  // landscape with WS_FLAG_FORCE
   size_t ring_adv;    // WS_FLAG_TRAIN: advantages of ws_advantages
+  size_t ring_sample; // landscape with WS_FLAG_TRAIN: behaviour samples of ws_advantages
   size_t ring_bytes;
 };
 

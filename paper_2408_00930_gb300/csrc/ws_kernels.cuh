@@ -57,6 +57,7 @@ struct Dev {
   float *r_logp, *r_rew, *r_ret, *r_energy;
   float *r_force;  // landscape FORCE field [t][D][slot] (WS_FLAG_FORCE), else null
   float *r_adv;    // ADVANTAGE field [t][slot] (WS_FLAG_TRAIN), else null
+  float *r_sample; // landscape SAMPLE field [t][D][slot] (WS_FLAG_TRAIN), else null
   uint8_t *r_done;
   int64_t *r_wealth;
 };
@@ -104,10 +105,11 @@ size_t train_scratch_bytes(const PolicyShape &pol);
 TrainBufs train_bufs(uint8_t *base, const PolicyShape &pol);
 void launch_a2c_update(const Dev &d, const TrainBufs &tb, const TrainGroup *groups, int n_groups,
                        uint32_t n, float lr, float c_v, float c_e, cudaStream_t st);
-// A = G - V(s) of the last n steps into the ADVANTAGE field (returns computed).
+// A = G - V(s) of the last n steps into the ADVANTAGE field (returns computed);
+// landscape: also the behaviour samples into SAMPLE.
 void launch_advantages(const Dev &d, const TrainBufs &tb, const TrainGroup *groups, int n_groups,
                        uint32_t n, cudaStream_t st);
-// One PPO epoch (categorical heads) over the last n steps.
+// One PPO epoch over the last n steps.
 void launch_ppo_update(const Dev &d, const TrainBufs &tb, const TrainGroup *groups, int n_groups,
                        uint32_t n, float lr, float eps, float c_v, float c_e, cudaStream_t st);
 

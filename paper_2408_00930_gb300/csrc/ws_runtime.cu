@@ -321,6 +321,9 @@ Layout make_layout(const ws_config *cfg, const std::vector<int32_t> &agents) {
     r += up(R * (size_t)cfg->dim * S * 4);
   L.ring_adv = r;
   if (cfg->flags & WS_FLAG_TRAIN) r += up(R * S * 4);
+  L.ring_sample = r;
+  if (cfg->env == WS_ENV_LANDSCAPE && (cfg->flags & WS_FLAG_TRAIN))
+    r += up(R * (size_t)cfg->dim * S * 4);
   L.ring_bytes = r;
   return L;
 }
@@ -428,6 +431,9 @@ void make_dev(ws_ctx *c) {
   d.r_energy = cfg.env == WS_ENV_LANDSCAPE ? (float *)(R + L.ring_energy) : nullptr;
   d.r_force = (cfg.flags & WS_FLAG_FORCE) ? (float *)(R + L.ring_force) : nullptr;
   d.r_adv = (cfg.flags & WS_FLAG_TRAIN) ? (float *)(R + L.ring_adv) : nullptr;
+  d.r_sample = (cfg.env == WS_ENV_LANDSCAPE && (cfg.flags & WS_FLAG_TRAIN))
+                   ? (float *)(R + L.ring_sample)
+                   : nullptr;
 }
 
 void drop_graphs(ws_ctx *c) {
@@ -576,6 +582,9 @@ size_t ring_field_step_bytes(const ws_ctx *c, ws_field f, size_t *field_off) {
     case WS_F_ADVANTAGE:
       if (!(c->cfg.flags & WS_FLAG_TRAIN)) return 0;
       *field_off = L.ring_adv; return S * 4;
+    case WS_F_SAMPLE:
+      if (L.env != WS_ENV_LANDSCAPE || !(c->cfg.flags & WS_FLAG_TRAIN)) return 0;
+      *field_off = L.ring_sample; return (size_t)c->cfg.dim * S * 4;
     default: return 0;
   }
 }
@@ -901,7 +910,6 @@ ws_status ws_ppo_update(ws_ctx *c, uint32_t n, float lr, float eps, float c_v, f
   if (!c) return WS_ERR_INVALID;
   if (c->err != WS_OK) return c->err;
   if (!(c->cfg.flags & WS_FLAG_TRAIN)) return WS_ERR_STATE;
-  if (c->L.env == WS_ENV_LANDSCAPE) return WS_ERR_INVALID;
   if (!std::isfinite(lr) || !std::isfinite(c_v) || !std::isfinite(c_e) || !std::isfinite(eps) ||
       !(eps > 0.f))
     return WS_ERR_INVALID;

@@ -14,7 +14,9 @@
 // A = G - V(s) is computed once (ws_advantages, into the ring's ADVANTAGE
 // field) and held; each epoch replaces -A log pi with -min(rho A,
 // clip(rho, 1 - eps, 1 + eps) A), rho = pi(a|s) / exp(recorded logp), whose
-// gradient is A rho d log pi except where the min holds the clipped constant.
+// gradient is A rho d log pi except where the min holds the clipped constant;
+// the Gaussian head's action is the unclipped sample mean + sigma z rebuilt by
+// ws_advantages (the SAMPLE field), scored under the current mean and sigma.
 //
 // FP32 SIMT throughout, in chunks of kTrainChunk rows: gather the chunk's rows from
 // the ring, forward both MLPs keeping the activations, the loss head
@@ -69,6 +71,40 @@ __global__ void k_adv_store(Dev d, uint32_t n, size_t q0, uint32_t rows, uint32_
   d.r_adv[rowR * d.n_slots + s] = tb.ret[i] - tb.vout[i];
 }
 
+// The Philox normals z[j..j+3] of the Gaussian head's sample of (step k,
+// env e), as the sampler drew them: one draw per four coordinates.
+__device__ __forceinline__ void action_normals4(const Dev &d, uint32_t k, uint32_t e, int j,
+                                                float (&z)[4]) {
+  const uint4 r = draw(d.seed, k, e, 0, kTagAction, (uint32_t)(j >> 2));
+  const float2 p = box_muller(r.x, r.y), p2 = box_muller(r.z, r.w);
+  z[0] = p.x;
+  z[1] = p.y;
+  z[2] = p2.x;
+  z[3] = p2.y;
+}
+
+// Landscape: the chunk's behaviour samples u = mean + sigma z (unclipped)
+// from the actor's outputs into the SAMPLE field.
+__global__ void k_sample_store(Dev d, uint32_t n, size_t q0, uint32_t rows, uint32_t ns,
+                               TrainBufs tb) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  const int D = (int)d.dim;
+  size_t rowR;
+  const size_t s = ring_pos(d, n, q0, i, 0, ns, &rowR);
+  const size_t q = q0 + i;
+  const uint32_t k = (uint32_t)(d.k[0] - n + q / ns), e = (uint32_t)(q % ns);
+  const float *o = tb.out + (size_t)i * 2 * D;
+  for (int j = 0; j < D; j += 4) {
+    float z[4];
+    action_normals4(d, k, e, j, z);
+    for (int u = 0; u < 4 && j + u < D; ++u) {
+      const float ls = fminf(fmaxf(o[D + j + u], -5.0f), 2.0f);
+      d.r_sample[(rowR * D + j + u) * d.n_slots + s] = o[j + u] + expf(ls) * z[u];
+    }
+  }
+}
+
 // The loss sums: reduced over the warp first, one atomic per warp (every
 // thread of the warp calls it, rows past the end with zeros).
 __device__ __forceinline__ void add_stats(const TrainBufs &tb, double a, double b, double c,
@@ -109,9 +145,8 @@ __global__ void k_a2c_head(Dev d, uint32_t n, size_t q0, uint32_t rows, uint32_t
     const float half_log_2pi = 0.91893853320467274f;
     float logp = 0.f, H = 0.f;
     for (int j = 0; j < D; j += 4) {
-      const uint4 r = draw(d.seed, k, e, 0, kTagAction, (uint32_t)(j >> 2));
-      const float2 p = box_muller(r.x, r.y), p2 = box_muller(r.z, r.w);
-      const float z4[4] = {p.x, p.y, p2.x, p2.y};
+      float z4[4];
+      action_normals4(d, k, e, j, z4);
       for (int u = 0; u < 4 && j + u < D; ++u) {
         const float z = z4[u], raw = o[D + j + u];
         const float ls = fminf(fmaxf(raw, -5.0f), 2.0f);
@@ -153,16 +188,57 @@ __global__ void k_a2c_head(Dev d, uint32_t n, size_t q0, uint32_t rows, uint32_t
   add_stats(tb, s_pg, s_v, s_h, 0.0);
 }
 
-// PPO head (categorical): per row rho = exp(log pi(a|s) - logp_old), the
-// surrogate min(rho A, clip(rho) A) and dL/dlogits = A rho (p - onehot(a))
-// (zero where A > 0 and rho > 1 + eps or A < 0 and rho < 1 - eps: the min then
-// holds the clipped constant) plus the entropy term, dL/dV as the A2C head;
-// the sums of -surrogate, (G - V)^2, H and the rows with |rho - 1| > eps.
-__global__ void k_ppo_head(uint32_t rows, int na, double inv_r, float eps, float c_v, float c_e,
-                           TrainBufs tb) {
+// PPO heads.  Per row rho = exp(log pi(a|s) - logp_old), the surrogate
+// min(rho A, clip(rho) A), and dL/d(outputs) = -g d log pi / d(outputs) with
+// g = A rho, or 0 where A > 0 and rho > 1 + eps or A < 0 and rho < 1 - eps
+// (the min then holds the clipped constant), plus the entropy term; dL/dV as
+// the A2C head; the sums of -surrogate, (G - V)^2, H and the rows with
+// |rho - 1| > eps.  Categorical: d log pi / d logits = onehot(a) - p.
+// Diagonal Gaussian (landscape): the action is the SAMPLE field's u, y =
+// (u - mean) / sigma, d log pi / d mean = y / sigma, d log pi / d raw = y^2 - 1
+// and dH / d raw = 1 where the clamp of log sigma to [-5, 2] does not hold.
+__device__ __forceinline__ void ppo_ratio(float lp, float lpo, float A, float eps, float &rho,
+                                          float &g, double &s_pg, double &s_c) {
+  rho = expf(lp - lpo);
+  const float rc = fminf(fmaxf(rho, 1.f - eps), 1.f + eps);
+  const bool held = (A > 0.f && rho > 1.f + eps) || (A < 0.f && rho < 1.f - eps);
+  g = held ? 0.f : A * rho;
+  s_pg = -(double)fminf(rho * A, rc * A);
+  s_c = fabsf(rho - 1.f) > eps ? 1.0 : 0.0;
+}
+
+__global__ void k_ppo_head(Dev d, uint32_t n, size_t q0, uint32_t rows, uint32_t ns, int na,
+                           double inv_r, float eps, float c_v, float c_e, TrainBufs tb) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   double s_pg = 0.0, s_v = 0.0, s_h = 0.0, s_c = 0.0;
-  if (i < rows) {
+  if (i < rows && d.env == WS_ENV_LANDSCAPE) {  // one group: every slot
+    const int D = (int)d.dim;
+    size_t rowR;
+    const size_t s = ring_pos(d, n, q0, i, 0, ns, &rowR);
+    float *o = tb.out + (size_t)i * 2 * D;
+    const float half_log_2pi = 0.91893853320467274f;
+    float lp = 0.f, H = 0.f;
+    for (int j = 0; j < D; ++j) {
+      const float ls = fminf(fmaxf(o[D + j], -5.0f), 2.0f);
+      const float y = (d.r_sample[(rowR * D + j) * d.n_slots + s] - o[j]) / expf(ls);
+      lp += -0.5f * y * y - ls - half_log_2pi;
+      H += ls + 0.5f + half_log_2pi;
+    }
+    const float V = tb.vout[i], G = tb.ret[i], A = tb.adv[i];
+    float rho, g;
+    ppo_ratio(lp, tb.lpo[i], A, eps, rho, g, s_pg, s_c);
+    for (int j = 0; j < D; ++j) {
+      const float raw = o[D + j];
+      const float ls = fminf(fmaxf(raw, -5.0f), 2.0f), sig = expf(ls);
+      const float y = (d.r_sample[(rowR * D + j) * d.n_slots + s] - o[j]) / sig;
+      const bool free_ls = raw > -5.0f && raw < 2.0f;
+      o[j] = (float)(-g * y / sig * inv_r);
+      o[D + j] = free_ls ? (float)((-g * (y * y - 1.f) - c_e) * inv_r) : 0.f;
+    }
+    tb.vout[i] = (float)(2.0 * c_v * (V - G) * inv_r);
+    s_v = (double)(G - V) * (G - V);
+    s_h = H;
+  } else if (i < rows) {
     float *lg = tb.out + (size_t)i * na;
     float m = lg[0];
     for (int c = 1; c < na; ++c) m = fmaxf(m, lg[c]);
@@ -176,19 +252,15 @@ __global__ void k_ppo_head(uint32_t rows, int na, double inv_r, float eps, float
     }
     const float V = tb.vout[i], G = tb.ret[i], A = tb.adv[i];
     const int a = tb.act[i];
-    const float rho = expf(((lg[a] - m) - lS) - tb.lpo[i]);
-    const float rc = fminf(fmaxf(rho, 1.f - eps), 1.f + eps);
-    const bool held = (A > 0.f && rho > 1.f + eps) || (A < 0.f && rho < 1.f - eps);
-    const float gA = held ? 0.f : A * rho;
+    float rho, g;
+    ppo_ratio((lg[a] - m) - lS, tb.lpo[i], A, eps, rho, g, s_pg, s_c);
     for (int c = 0; c < na; ++c) {
       const float lp = (lg[c] - m) - lS, p = expf(lp);
-      lg[c] = (float)((gA * (p - (c == a ? 1.f : 0.f)) + c_e * p * (lp + H)) * inv_r);
+      lg[c] = (float)((g * (p - (c == a ? 1.f : 0.f)) + c_e * p * (lp + H)) * inv_r);
     }
     tb.vout[i] = (float)(2.0 * c_v * (V - G) * inv_r);
-    s_pg = -(double)fminf(rho * A, rc * A);
     s_v = (double)(G - V) * (G - V);
     s_h = H;
-    s_c = fabsf(rho - 1.f) > eps ? 1.0 : 0.0;
   }
   add_stats(tb, s_pg, s_v, s_h, s_c);
 }
@@ -614,8 +686,8 @@ void run_update(const Dev &d, const TrainBufs &tb, const TrainGroup *groups, int
       mlp_forward(G.pol, G.params, tb.x, tb.h1, tb.h2, tb.out, rows, st);
       mlp_forward(G.crit, G.critic, tb.x, tb.c1, tb.c2, tb.vout, rows, st);
       if (ppo)
-        k_ppo_head<<<nblk(rows, 256), 256, 0, st>>>((uint32_t)rows, G.pol.w[3], inv_r, eps, c_v,
-                                                    c_e, tb);
+        k_ppo_head<<<nblk(rows, 256), 256, 0, st>>>(d, n, q0, (uint32_t)rows, G.n_slots,
+                                                    G.pol.w[3], inv_r, eps, c_v, c_e, tb);
       else
         k_a2c_head<<<nblk(rows, 256), 256, 0, st>>>(d, n, q0, (uint32_t)rows, G.n_slots,
                                                     G.pol.w[3], inv_r, c_v, c_e, tb);
@@ -640,7 +712,8 @@ void launch_ppo_update(const Dev &d, const TrainBufs &tb, const TrainGroup *grou
   run_update(d, tb, groups, n_groups, n, lr, c_v, c_e, true, eps, st);
 }
 
-// Per group and chunk: gather, the critic's forward, A = G - V into the ring.
+// Per group and chunk: gather, the critic's forward, A = G - V into the ring;
+// landscape: the actor's forward and the behaviour samples.
 void launch_advantages(const Dev &d, const TrainBufs &tb, const TrainGroup *groups, int n_groups,
                        uint32_t n, cudaStream_t st) {
   for (int gi = 0; gi < n_groups; ++gi) {
@@ -653,6 +726,10 @@ void launch_advantages(const Dev &d, const TrainBufs &tb, const TrainGroup *grou
       mlp_forward(G.crit, G.critic, tb.x, tb.c1, tb.c2, tb.vout, rows, st);
       k_adv_store<<<nblk(rows, 256), 256, 0, st>>>(d, n, q0, (uint32_t)rows, G.slot0, G.n_slots,
                                                    tb);
+      if (d.env == WS_ENV_LANDSCAPE) {  // one group: every slot
+        mlp_forward(G.pol, G.params, tb.x, tb.h1, tb.h2, tb.out, rows, st);
+        k_sample_store<<<nblk(rows, 256), 256, 0, st>>>(d, n, q0, (uint32_t)rows, G.n_slots, tb);
+      }
     }
   }
 }

@@ -25,7 +25,7 @@ WS_ENV_CONTROL, WS_ENV_ECONOMY, WS_ENV_LANDSCAPE, WS_ENV_ACROBOT = 0, 1, 2, 3
 WS_PATH_PLAIN_FP32, WS_PATH_BATCHED_FP32, WS_PATH_BATCHED_BF16 = 0, 1, 2
 (WS_F_OBS, WS_F_ACTION, WS_F_LOGP, WS_F_REWARD, WS_F_DONE, WS_F_RETURN, WS_F_WEALTH, WS_F_ENERGY,
  WS_F_STATE, WS_F_PARAMS, WS_F_ENV_PARAMS, WS_F_LOGITS, WS_F_FORCE, WS_F_CRITIC,
- WS_F_ADVANTAGE) = range(15)
+ WS_F_ADVANTAGE, WS_F_SAMPLE) = range(16)
 
 EXPORTED = ["ws_query_bytes", "ws_create", "ws_reset", "ws_step", "ws_rollout", "ws_returns",
             "ws_forces", "ws_a2c_update", "ws_advantages", "ws_ppo_update",
@@ -369,7 +369,7 @@ class Rollout:
             return np.uint8, (S,)
         if field == WS_F_WEALTH:
             return np.int64, (S,)
-        if field == WS_F_FORCE:
+        if field in (WS_F_FORCE, WS_F_SAMPLE):
             return np.float32, (self.dim, S)
         raise ValueError(field)
 

@@ -4,8 +4,10 @@ differences and autograd): the ADVANTAGE field is G - V(s) under the critic
 before the update; each epoch's parameter change over lr is the gradient of
 the mean loss at the parameters that epoch started from, with the advantage
 held and the ring's recorded log-probabilities as the behaviour policy; for
-the control env, the acrobot and the economy's agents and planners, on the
-FP32 and the BF16 roll-out paths.  The actor is perturbed after the roll-out
+the control env, the acrobot and the economy's agents and planners
+(categorical heads) and the landscape (diagonal Gaussian head, its behaviour
+samples rebuilt into the SAMPLE field), on the FP32 and the BF16 roll-out
+paths.  The actor is perturbed after the roll-out
 (output layer) so that rows fall on both sides of the clip range."""
 import numpy as np
 import pytest
@@ -216,10 +218,72 @@ def test_ppo_errors(torch):
     assert W.ws_ppo_update(r.ctx, 1, 0.1, 0.2, 0.5, 0.0) in (W.WS_ERR_STATE, W.WS_ERR_RANGE)
     r.sync()
     r.close()
-    r = W.Rollout(W.WS_ENV_LANDSCAPE, F32, 16, 4, 100, 16, 16, dim=8, n_gauss=16,
-                  flags=W.WS_FLAG_TRAIN)
+    r = W.Rollout(W.WS_ENV_LANDSCAPE, F32, 16, 4, 100, 16, 16, dim=8, n_gauss=16)
     r.rollout(2)
-    assert W.ws_advantages(r.ctx, 2) == W.WS_OK                               # A = G - V is defined
-    assert W.ws_ppo_update(r.ctx, 2, 0.1, 0.2, 0.5, 0.0) == W.WS_ERR_INVALID # Gaussian head
-    r.sync()
+    dst = np.empty((2, 8, 16), np.float32)
+    assert W.ws_fetch(r.ctx, W.WS_F_SAMPLE, 0, 2, dst.ctypes.data, dst.nbytes, 0) != W.WS_OK
+    r.close()
+
+
+@pytest.mark.parametrize("path,h", [(F32, 32), (BF16, 256)])
+def test_ppo_landscape_gaussian_head(torch, path, h):
+    """ws_advantages rebuilds each row's unclipped sample u = mean + sigma z
+    (checked against the oracle's forward and normals, and on the FP32 path
+    against the step the env took); two epochs score u under the perturbed
+    and then updated Gaussian."""
+    D, M, n, T, lr, eps, c_v, c_e = 8, 64, 200, 12, 0.5, 0.15, 0.5, 0.01
+    widths = [D, h, h, 2 * D]
+    r = W.Rollout(W.WS_ENV_LANDSCAPE, path, n, T, 7, h, h, dim=D, n_gauss=M, param_seed=4,
+                  flags=W.WS_FLAG_TRAIN, chunk_steps=5)
+    r.reset(6)
+    r.rollout(T)
+    pa = r.fetch_raw(W.WS_F_PARAMS, 4 * oracle.policy_param_count(widths)).view(np.float32).copy()
+    pc = r.fetch_raw(W.WS_F_CRITIC, 4 * oracle.policy_param_count([D, h, h, 1])).view(np.float32).copy()
+    r.advantages(T)
+    obs, dx, smp = (r.fetch(f, 0, T) for f in (W.WS_F_OBS, W.WS_F_ACTION, W.WS_F_SAMPLE))
+    lpo = r.fetch(W.WS_F_LOGP, 0, T).reshape(-1).astype(np.float64)
+    G = r.fetch(W.WS_F_RETURN, 0, T).reshape(-1).astype(np.float64)
+    adv_gpu = r.fetch(W.WS_F_ADVANTAGE, 0, T).reshape(-1)
+    X = obs.transpose(0, 2, 1).reshape(-1, D).astype(np.float64)
+    U_gpu = smp.transpose(0, 2, 1).reshape(-1, D).astype(np.float64)
+    Z = np.array([oracle.landscape_action_normals(6, t, e, D) for t in range(T) for e in range(n)])
+    out0 = oracle.mlp_forward(widths, pa, X)
+    sig0 = np.exp(np.clip(out0[:, D:], -5.0, 2.0))
+    U = out0[:, :D] + sig0 * Z
+    assert np.all(np.abs(U_gpu - U) <= 1e-5 * (1 + np.abs(out0[:, :D]) + sig0 * np.abs(Z)))
+    if path == F32:      # the env took the clipped sample
+        step = dx.transpose(0, 2, 1).reshape(-1, D).astype(np.float64)
+        assert np.abs(np.clip(U_gpu, -0.1, 0.1) - step).max() <= 1e-6
+    V = oracle.mlp_forward([D, h, h, 1], pc, X)[:, 0]
+    adv = G - V
+    assert np.all(np.abs(adv_gpu - adv) <= 1e-5 * (1 + np.abs(G) + np.abs(V)))
+    pa = perturb_output_layer(pa, widths, 0.2, seed=15)
+    r.load_raw(W.WS_F_PARAMS, pa)
+    fracs = []
+    for _ in range(2):
+        stats = r.ppo_update(T, lr, eps, c_v, c_e)
+        pa2 = r.fetch_raw(W.WS_F_PARAMS, pa.nbytes).view(np.float32).copy()
+        pc2 = r.fetch_raw(W.WS_F_CRITIC, pc.nbytes).view(np.float32).copy()
+        st, ga, gc = oracle.ppo_gauss(pa, pc, X, U, G, adv, lpo, h, h, eps, c_v, c_e)
+        # rows within FP32 reach of a clip boundary: their policy term is in the tolerance
+        o = oracle.mlp_forward(widths, pa, X)
+        ls = np.clip(o[:, D:], -5.0, 2.0)
+        y = (U - o[:, :D]) / np.exp(ls)
+        rho = np.exp((-0.5 * y * y - ls - 0.5 * np.log(2 * np.pi)).sum(1) - lpo)
+        amb = (np.abs(rho - (1 + eps)) < AMBIG * rho) | (np.abs(rho - (1 - eps)) < AMBIG * rho)
+        extra = np.zeros_like(ga)
+        if amb.any():
+            _, g_amb, _ = oracle.ppo_gauss(pa, pc, X[amb], U[amb], G[amb], adv[amb], lpo[amb], h,
+                                           h, 1e30, 0.0, 0.0)
+            extra = np.abs(g_amb) * amb.sum() / len(G)
+        np.testing.assert_allclose(stats[1:3], st[1:3], rtol=1e-4, atol=1e-7)
+        assert abs(stats[3] - st[3]) <= amb.sum() / len(G) + 1e-12
+        for before, after, g, ex in ((pa, pa2, ga, extra), (pc, pc2, gc, 0.0)):
+            dstep = (before.astype(np.float64) - after.astype(np.float64)) / lr
+            tol = (1e-4 * np.abs(g).max() + ex +
+                   0.6 * np.spacing(np.abs(before)).astype(np.float64) / lr)
+            assert np.all(np.abs(dstep - g) <= tol), np.abs(dstep - g).max()
+        fracs.append(st[3])
+        pa, pc = pa2, pc2
+    assert 0.02 < fracs[0] < 0.98, fracs
     r.close()
