@@ -269,7 +269,10 @@ __global__ void k_ppo_head(Dev d, uint32_t n, size_t q0, uint32_t rows, uint32_t
 // A(m, k) = TA ? A[k lda + m] : A[m lda + k] and B(k, n) = TB ? B[n ldb + k] :
 // B[k ldb + n].  128 x 128 tiles, 8 x 8 outputs per thread (rows ty*4 + {0..3}
 // and 64 + ty*4 + {0..3}, columns likewise), K staged 8 at a time through two
-// shared-memory buffers.  Epilogues: the forward layer (+ bias, tanh or not),
+// shared-memory buffers.  The FMAs are packed (fma.rn.f32x2: two columns of a
+// row per instruction, each lane rounded as a scalar fmaf, in the same k
+// order): the A tile is staged as duplicated pairs {a, a}, so one 16-byte
+// shared load gives the broadcast operands of two rows.  Epilogues: the forward layer (+ bias, tanh or not),
 // the data gradient of a tanh layer (* (1 - H^2)), or none (a partial product
 // of row slice z, written at C + z slice_stride).
 enum { kEpiBiasTanh = 0, kEpiBias = 1, kEpiDTanh = 2, kEpiNone = 3 };
@@ -294,15 +297,27 @@ __device__ __forceinline__ void ld4(const float *__restrict__ X, long ld, int r,
   }
 }
 
+__device__ __forceinline__ uint64_t fma_f32x2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ float2 unpack_f32x2(uint64_t v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+
 template <bool TA, bool TB, int EPI, bool VEC>
 __global__ __launch_bounds__(kGT, 2) void k_sgemm(const float *__restrict__ A, int lda,
                                                 const float *__restrict__ B, int ldb,
                                                 float *__restrict__ C, int M, int N, int k_lo,
                                                 int k_hi, int k_slice, size_t slice_stride,
                                                 const float *__restrict__ aux) {
-  // rows padded by 4 floats: the transposing stores of k-contiguous operands
-  // (8 k of 4 rows per warp) then fall in 32 distinct banks
-  __shared__ __align__(16) float As[2][kGK][kGM + 4];
+  // As holds A(m, k) twice at [k][2m] and [k][2m + 1]; rows padded by 8 (4)
+  // floats: the transposing stores of k-contiguous operands (8 k of 4 rows
+  // per warp) then fall in distinct banks
+  __shared__ __align__(16) float As[2][kGK][2 * kGM + 8];
   __shared__ __align__(16) float Bs[2][kGK][kGN + 4];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.x * kGM, n0 = blockIdx.y * kGN;
@@ -327,10 +342,13 @@ __global__ __launch_bounds__(kGT, 2) void k_sgemm(const float *__restrict__ A, i
   };
   auto store = [&](int buf) {
     if (TA) {
-      *(float4 *)&As[buf][tid >> 5][(tid & 31) * 4] = make_float4(ra[0], ra[1], ra[2], ra[3]);
+      float *d = &As[buf][tid >> 5][(tid & 31) * 8];
+      *(float4 *)d = make_float4(ra[0], ra[0], ra[1], ra[1]);
+      *(float4 *)(d + 4) = make_float4(ra[2], ra[2], ra[3], ra[3]);
     } else {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) As[buf][(tid & 1) * 4 + i][tid >> 1] = ra[i];
+      for (int i = 0; i < 4; ++i)
+        *(float2 *)&As[buf][(tid & 1) * 4 + i][(tid >> 1) * 2] = make_float2(ra[i], ra[i]);
     }
     if (TB) {
 #pragma unroll
@@ -339,11 +357,12 @@ __global__ __launch_bounds__(kGT, 2) void k_sgemm(const float *__restrict__ A, i
       *(float4 *)&Bs[buf][tid >> 5][(tid & 31) * 4] = make_float4(rb[0], rb[1], rb[2], rb[3]);
     }
   };
-  float acc[8][8];
+  // acc[i][p]: row i, columns 2p and 2p + 1 of the thread's eight
+  uint64_t acc[8][4];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    for (int p = 0; p < 4; ++p) acc[i][p] = 0ull;
   int buf = 0;
   if (kb < ke) {
     load(kb);
@@ -355,16 +374,19 @@ __global__ __launch_bounds__(kGT, 2) void k_sgemm(const float *__restrict__ A, i
     if (more) load(k0 + kGK);  // next tile's loads in flight during this tile's FMAs
 #pragma unroll
     for (int kk = 0; kk < kGK; ++kk) {
-      const float4 a0 = *(const float4 *)&As[buf][kk][ty * 4];
-      const float4 a1 = *(const float4 *)&As[buf][kk][64 + ty * 4];
-      const float4 b0 = *(const float4 *)&Bs[buf][kk][tx * 4];
-      const float4 b1 = *(const float4 *)&Bs[buf][kk][64 + tx * 4];
-      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+      const ulonglong2 b0 = *(const ulonglong2 *)&Bs[buf][kk][tx * 4];
+      const ulonglong2 b1 = *(const ulonglong2 *)&Bs[buf][kk][64 + tx * 4];
+      const uint64_t bv[4] = {b0.x, b0.y, b1.x, b1.y};
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+      for (int h = 0; h < 4; ++h) {  // rows 2h, 2h + 1 of the eight: one shared load
+        const int r = (h < 2 ? ty * 4 : 64 + ty * 4) + (h & 1) * 2;
+        const ulonglong2 a = *(const ulonglong2 *)&As[buf][kk][2 * r];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        for (int p = 0; p < 4; ++p) {
+          acc[2 * h][p] = fma_f32x2(a.x, bv[p], acc[2 * h][p]);
+          acc[2 * h + 1][p] = fma_f32x2(a.y, bv[p], acc[2 * h + 1][p]);
+        }
+      }
     }
     if (more) {
       store(buf ^ 1);
@@ -381,7 +403,8 @@ __global__ __launch_bounds__(kGT, 2) void k_sgemm(const float *__restrict__ A, i
     for (int j = 0; j < 8; ++j) {
       const int n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
       if (n >= N) continue;
-      float v = acc[i][j];
+      const float2 pr = unpack_f32x2(acc[i][j >> 1]);
+      float v = (j & 1) ? pr.y : pr.x;
       if (EPI == kEpiBiasTanh) v = tanhf(v + aux[n]);
       if (EPI == kEpiBias) v = v + aux[n];
       if (EPI == kEpiDTanh) {
@@ -412,25 +435,30 @@ __global__ void k_colsum_slices(const float *__restrict__ D, float *__restrict__
 // a 128 x 128 tile idle; they get their own kernels.
 constexpr int kThin = 32;
 
-// Forward of a layer with N <= 32 outputs: a warp per row, the lanes over the
+// The thin kernels are instantiated for the narrow width rounded up to a power
+// of two (NT or MT >= the true width), so that their per-row work is that of
+// the layer, not of the widest thin layer.
+inline int thin_width(int v) { return v <= 1 ? 1 : v <= 2 ? 2 : v <= 4 ? 4 : v <= 8 ? 8 : v <= 16 ? 16 : 32; }
+
+// Forward of a layer with N <= NT outputs: a warp per row, the lanes over the
 // inputs, a fixed-order warp reduction per output.
-template <bool TANH>
+template <bool TANH, int NT>
 __global__ void k_fwd_thin(const float *__restrict__ X, const float *__restrict__ W,
                            const float *__restrict__ b, float *__restrict__ Y, int rows, int K,
                            int N) {
   const int r = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (r >= rows) return;  // whole warps leave together
-  float acc[kThin];
+  float acc[NT];
 #pragma unroll
-  for (int n = 0; n < kThin; ++n) acc[n] = 0.f;
+  for (int n = 0; n < NT; ++n) acc[n] = 0.f;
   for (int k = lane; k < K; k += 32) {
     const float x = X[(size_t)r * K + k];
 #pragma unroll
-    for (int n = 0; n < kThin; ++n)
+    for (int n = 0; n < NT; ++n)
       if (n < N) acc[n] = fmaf(x, W[(size_t)k * N + n], acc[n]);
   }
 #pragma unroll
-  for (int n = 0; n < kThin; ++n) {
+  for (int n = 0; n < NT; ++n) {
     if (n >= N) break;
     float v = acc[n];
 #pragma unroll
@@ -439,24 +467,25 @@ __global__ void k_fwd_thin(const float *__restrict__ X, const float *__restrict_
   }
 }
 
-// Weight gradient of a layer with N <= 32 outputs, slice z: P[z][m][n] for every
-// input m (and the bias row m = M): a thread per m, the slice's D rows staged
-// through shared memory 64 at a time.
+// Weight gradient of a layer with N <= NT outputs, slice z: P[z][m][n] for
+// every input m (and the bias row m = M): a thread per m, the slice's D rows
+// staged through shared memory 64 at a time.
+template <int NT>
 __global__ __launch_bounds__(256) void k_wgrad_thin_n(const float *__restrict__ Ain,
                                                       const float *__restrict__ D,
                                                       float *__restrict__ P, int rows, int M,
                                                       int N) {
-  __shared__ float Ds[64][kThin];
+  __shared__ float Ds[64][NT];
   const int m = blockIdx.x * blockDim.x + threadIdx.x, z = blockIdx.y;
   const int rb = z * kThinSlice, re = min(rows, rb + kThinSlice);
-  float acc[kThin];
+  float acc[NT];
 #pragma unroll
-  for (int n = 0; n < kThin; ++n) acc[n] = 0.f;
+  for (int n = 0; n < NT; ++n) acc[n] = 0.f;
   for (int r0 = rb; r0 < re; r0 += 64) {
     const int nr = min(64, re - r0);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < 64 * kThin; idx += blockDim.x) {
-      const int rr = idx / kThin, n = idx % kThin;
+    for (int idx = threadIdx.x; idx < 64 * NT; idx += blockDim.x) {
+      const int rr = idx / NT, n = idx % NT;
       Ds[rr][n] = (rr < nr && n < N) ? D[(size_t)(r0 + rr) * N + n] : 0.f;
     }
     __syncthreads();
@@ -464,34 +493,35 @@ __global__ __launch_bounds__(256) void k_wgrad_thin_n(const float *__restrict__ 
       for (int rr = 0; rr < nr; ++rr) {
         const float a = m == M ? 1.f : Ain[(size_t)(r0 + rr) * M + m];
 #pragma unroll
-        for (int n = 0; n < kThin; ++n) acc[n] = fmaf(a, Ds[rr][n], acc[n]);
+        for (int n = 0; n < NT; ++n) acc[n] = fmaf(a, Ds[rr][n], acc[n]);
       }
   }
   if (m > M) return;
   float *out = P + (size_t)z * (M + 1) * N + (size_t)m * N;
 #pragma unroll
-  for (int n = 0; n < kThin; ++n)
+  for (int n = 0; n < NT; ++n)
     if (n < N) out[n] = acc[n];
 }
 
-// Weight gradient of a layer with M <= 32 inputs, slice z: P[z][m][n] for every
+// Weight gradient of a layer with M <= MT inputs, slice z: P[z][m][n] for every
 // output n, all m (and the bias row): a thread per n, the slice's input rows
 // staged through shared memory 64 at a time.
+template <int MT>
 __global__ __launch_bounds__(256) void k_wgrad_thin_m(const float *__restrict__ Ain,
                                                       const float *__restrict__ D,
                                                       float *__restrict__ P, int rows, int M,
                                                       int N) {
-  __shared__ float As[64][kThin + 1];
+  __shared__ float As[64][MT + 1];
   const int n = blockIdx.x * blockDim.x + threadIdx.x, z = blockIdx.y;
   const int rb = z * kThinSlice, re = min(rows, rb + kThinSlice);
-  float acc[kThin + 1];
+  float acc[MT + 1];
 #pragma unroll
-  for (int m = 0; m <= kThin; ++m) acc[m] = 0.f;
+  for (int m = 0; m <= MT; ++m) acc[m] = 0.f;
   for (int r0 = rb; r0 < re; r0 += 64) {
     const int nr = min(64, re - r0);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < 64 * (kThin + 1); idx += blockDim.x) {
-      const int rr = idx / (kThin + 1), m = idx % (kThin + 1);
+    for (int idx = threadIdx.x; idx < 64 * (MT + 1); idx += blockDim.x) {
+      const int rr = idx / (MT + 1), m = idx % (MT + 1);
       As[rr][m] = (rr < nr && m < M) ? Ain[(size_t)(r0 + rr) * M + m] : (rr < nr && m == M ? 1.f : 0.f);
     }
     __syncthreads();
@@ -499,15 +529,26 @@ __global__ __launch_bounds__(256) void k_wgrad_thin_m(const float *__restrict__ 
       for (int rr = 0; rr < nr; ++rr) {
         const float dv = D[(size_t)(r0 + rr) * N + n];
 #pragma unroll
-        for (int m = 0; m <= kThin; ++m) acc[m] = fmaf(As[rr][m], dv, acc[m]);
+        for (int m = 0; m <= MT; ++m) acc[m] = fmaf(As[rr][m], dv, acc[m]);
       }
   }
   if (n >= N) return;
   float *out = P + (size_t)z * (M + 1) * N + n;
 #pragma unroll
-  for (int m = 0; m <= kThin; ++m)
+  for (int m = 0; m <= MT; ++m)
     if (m <= M) out[(size_t)m * N] = acc[m];
 }
+
+// Launch a thin kernel instantiated for thin_width(w).
+#define WS_THIN_DISPATCH(w, LAUNCH) \
+  switch (thin_width(w)) {          \
+    case 1: LAUNCH(1); break;       \
+    case 2: LAUNCH(2); break;       \
+    case 4: LAUNCH(4); break;       \
+    case 8: LAUNCH(8); break;       \
+    case 16: LAUNCH(16); break;     \
+    default: LAUNCH(32); break;     \
+  }
 
 // grad[i] += sum_z P[z][i], the slices in order.
 __global__ void k_reduce_slices(const float *__restrict__ P, int nz, size_t len, float *grad) {
@@ -562,10 +603,15 @@ void mlp_forward(const PolicyShape &sh, const float *params, const float *X, flo
     const float *W = params + sh.layer_offset(l), *b = W + (size_t)K * N;
     if (N <= kThin) {
       const unsigned g = nblk((size_t)rows * 32, 256);
-      if (l < 2)
-        k_fwd_thin<true><<<g, 256, 0, st>>>(in[l], W, b, o[l], rows, K, N);
-      else
-        k_fwd_thin<false><<<g, 256, 0, st>>>(in[l], W, b, o[l], rows, K, N);
+#define WS_FWD_TANH(NT) k_fwd_thin<true, NT><<<g, 256, 0, st>>>(in[l], W, b, o[l], rows, K, N)
+#define WS_FWD_LIN(NT) k_fwd_thin<false, NT><<<g, 256, 0, st>>>(in[l], W, b, o[l], rows, K, N)
+      if (l < 2) {
+        WS_THIN_DISPATCH(N, WS_FWD_TANH)
+      } else {
+        WS_THIN_DISPATCH(N, WS_FWD_LIN)
+      }
+#undef WS_FWD_TANH
+#undef WS_FWD_LIN
     } else if (l < 2) {
       sgemm<false, false, kEpiBiasTanh>(ggrid(rows, N), st, in[l], K, W, N, o[l], rows, N, 0, K, 0, 0,
                                         b);
@@ -592,9 +638,15 @@ void mlp_backward(const PolicyShape &sh, const float *params, const float *X, co
     // slice are (M + 1) x N apart so that the bias row fits after them
     const size_t len = (size_t)(M + 1) * N;
     if (N <= kThin) {
-      k_wgrad_thin_n<<<dim3(nblk(M + 1, 256), (unsigned)nz), 256, 0, st>>>(ain[l], D, part, rows, M, N);
+      const dim3 g(nblk(M + 1, 256), (unsigned)nz);
+#define WS_WG_N(NT) k_wgrad_thin_n<NT><<<g, 256, 0, st>>>(ain[l], D, part, rows, M, N)
+      WS_THIN_DISPATCH(N, WS_WG_N)
+#undef WS_WG_N
     } else if (M <= kThin) {
-      k_wgrad_thin_m<<<dim3(nblk(N, 256), (unsigned)nz), 256, 0, st>>>(ain[l], D, part, rows, M, N);
+      const dim3 g(nblk(N, 256), (unsigned)nz);
+#define WS_WG_M(MT) k_wgrad_thin_m<MT><<<g, 256, 0, st>>>(ain[l], D, part, rows, M, N)
+      WS_THIN_DISPATCH(M, WS_WG_M)
+#undef WS_WG_M
     } else {
       sgemm<true, false, kEpiNone>(ggrid(M, N, nz), st, ain[l], M, D, N, part, M, N, 0, rows,
                                    kSliceRows, len, nullptr);
