@@ -417,18 +417,29 @@ __global__ __launch_bounds__(kGT, 2) void k_sgemm(const float *__restrict__ A, i
 }
 
 // Bias-gradient row of slice z: P[z][M][n] = sum over the slice's rows of
-// D[r][n]; a warp per (z, n), the lanes over rows, a fixed-order reduction.
-__global__ void k_colsum_slices(const float *__restrict__ D, float *__restrict__ P, int rows, int M,
-                                int N) {
-  const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  const int z = blockIdx.y;
-  if (w >= N) return;  // whole warps leave together
+// D[r][n].  A block per (32 columns, slice): the lanes over the columns (each
+// row's 32 columns are one coalesced load), warp w over rows rb + w, rb + w +
+// 8, ... in order; the eight warp sums are added in warp order.
+__global__ __launch_bounds__(256) void k_colsum_slices(const float *__restrict__ D,
+                                                       float *__restrict__ P, int rows, int M,
+                                                       int N) {
+  __shared__ float part[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int n = blockIdx.x * 32 + lane, z = blockIdx.y;
   const int rb = z * kSliceRows, re = min(rows, rb + kSliceRows);
   float s = 0.f;
-  for (int r = rb + lane; r < re; r += 32) s += D[(size_t)r * N + w];
+  if (n < N) {
+#pragma unroll 8
+    for (int r = rb + w; r < re; r += 8) s += D[(size_t)r * N + n];
+  }
+  part[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && n < N) {
+    float t = part[0][lane];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) P[((size_t)z * (M + 1) + M) * N + w] = s;
+    for (int q = 1; q < 8; ++q) t += part[q][lane];
+    P[((size_t)z * (M + 1) + M) * N + n] = t;
+  }
 }
 
 // Thin layers (32 or fewer outputs, or 32 or fewer inputs) would leave most of
@@ -550,13 +561,27 @@ __global__ __launch_bounds__(256) void k_wgrad_thin_m(const float *__restrict__ 
     default: LAUNCH(32); break;     \
   }
 
-// grad[i] += sum_z P[z][i], the slices in order.
-__global__ void k_reduce_slices(const float *__restrict__ P, int nz, size_t len, float *grad) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= len) return;
-  float s = grad[i];
-  for (int z = 0; z < nz; ++z) s += P[(size_t)z * len + i];
-  grad[i] = s;
+// grad[i] += sum_z P[z][i] in a fixed order: a block per 32 consecutive i (the
+// lanes), warp w summing slices z = w, w + 8, ... in order, then the eight
+// warp sums added to grad[i] in warp order.
+__global__ __launch_bounds__(256) void k_reduce_slices(const float *__restrict__ P, int nz,
+                                                       size_t len, float *grad) {
+  __shared__ float part[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const size_t i = (size_t)blockIdx.x * 32 + lane;
+  float s = 0.f;
+  if (i < len) {
+#pragma unroll 8
+    for (int z = w; z < nz; z += 8) s += P[(size_t)z * len + i];
+  }
+  part[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && i < len) {
+    float t = grad[i];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += part[q][lane];
+    grad[i] = t;
+  }
 }
 
 __global__ void k_sgd(float *p, const float *g, size_t n, float lr) {
@@ -650,10 +675,9 @@ void mlp_backward(const PolicyShape &sh, const float *params, const float *X, co
     } else {
       sgemm<true, false, kEpiNone>(ggrid(M, N, nz), st, ain[l], M, D, N, part, M, N, 0, rows,
                                    kSliceRows, len, nullptr);
-      k_colsum_slices<<<dim3(nblk((size_t)N * 32, 256), (unsigned)nz), 256, 0, st>>>(D, part, rows,
-                                                                                     M, N);
+      k_colsum_slices<<<dim3(nblk(N, 32), (unsigned)nz), 256, 0, st>>>(D, part, rows, M, N);
     }
-    k_reduce_slices<<<nblk(len, 256), 256, 0, st>>>(part, nz, len, grad + sh.layer_offset(l));
+    k_reduce_slices<<<nblk(len, 32), 256, 0, st>>>(part, nz, len, grad + sh.layer_offset(l));
     if (l > 0) {
       // gradient at layer l's input pre-activation: (D W_l^T) * (1 - a_l^2)
       sgemm<false, true, kEpiDTanh>(ggrid(rows, M), st, D, N, params + sh.layer_offset(l), N, dl[l],
