@@ -478,6 +478,71 @@ __global__ void k_fwd_thin(const float *__restrict__ X, const float *__restrict_
   }
 }
 
+// Forward of a layer with K <= KT inputs and a wide output: a thread per
+// output column n (its K weights and bias in registers), kFwdRows rows per
+// block with their inputs staged in shared memory; the sum runs over k in
+// order from 0 and then adds the bias, as the GEMM's epilogue does.
+constexpr int kFwdRows = 32;
+template <bool TANH, int KT>
+__global__ __launch_bounds__(256) void k_fwd_thin_k(const float *__restrict__ X,
+                                                    const float *__restrict__ W,
+                                                    const float *__restrict__ b,
+                                                    float *__restrict__ Y, int rows, int K, int N) {
+  __shared__ float Xs[kFwdRows][KT];
+  const int n = blockIdx.x * blockDim.x + threadIdx.x, r0 = blockIdx.y * kFwdRows;
+  for (int idx = threadIdx.x; idx < kFwdRows * KT; idx += blockDim.x) {
+    const int rr = idx / KT, k = idx % KT;
+    Xs[rr][k] = (r0 + rr < rows && k < K) ? X[(size_t)(r0 + rr) * K + k] : 0.f;
+  }
+  __syncthreads();
+  if (n >= N) return;
+  float w[KT];
+#pragma unroll
+  for (int k = 0; k < KT; ++k) w[k] = k < K ? W[(size_t)k * N + n] : 0.f;
+  const float bn = b[n];
+  const int nr = min(kFwdRows, rows - r0);
+  for (int rr = 0; rr < nr; ++rr) {
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < KT; ++k)
+      if (k < K) acc = fmaf(Xs[rr][k], w[k], acc);
+    Y[(size_t)(r0 + rr) * N + n] = TANH ? tanhf(acc + bn) : acc + bn;
+  }
+}
+
+// Data gradient through a layer with K <= KT outputs into its M inputs:
+// out[r][m] = (sum_k D[r][k] W[m][k]) (1 - H[r][m]^2), a thread per input m
+// (its K weights in registers), kFwdRows rows per block with their D rows
+// staged in shared memory; the sum over k in order from 0, as the GEMM's.
+template <int KT>
+__global__ __launch_bounds__(256) void k_dgrad_thin_k(const float *__restrict__ D,
+                                                      const float *__restrict__ W,
+                                                      const float *__restrict__ H,
+                                                      float *__restrict__ out, int rows, int K,
+                                                      int M) {
+  __shared__ float Ds[kFwdRows][KT];
+  const int m = blockIdx.x * blockDim.x + threadIdx.x, r0 = blockIdx.y * kFwdRows;
+  for (int idx = threadIdx.x; idx < kFwdRows * KT; idx += blockDim.x) {
+    const int rr = idx / KT, k = idx % KT;
+    Ds[rr][k] = (r0 + rr < rows && k < K) ? D[(size_t)(r0 + rr) * K + k] : 0.f;
+  }
+  __syncthreads();
+  if (m >= M) return;
+  float w[KT];
+#pragma unroll
+  for (int k = 0; k < KT; ++k) w[k] = k < K ? W[(size_t)m * K + k] : 0.f;
+  const int nr = min(kFwdRows, rows - r0);
+  for (int rr = 0; rr < nr; ++rr) {
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < KT; ++k)
+      if (k < K) acc = fmaf(Ds[rr][k], w[k], acc);
+    const size_t o = (size_t)(r0 + rr) * M + m;
+    const float h = H[o];
+    out[o] = acc * (1.f - h * h);
+  }
+}
+
 // Weight gradient of a layer with N <= NT outputs, slice z: P[z][m][n] for
 // every input m (and the bias row m = M): a thread per m, the slice's D rows
 // staged through shared memory 64 at a time.
@@ -637,6 +702,17 @@ void mlp_forward(const PolicyShape &sh, const float *params, const float *X, flo
       }
 #undef WS_FWD_TANH
 #undef WS_FWD_LIN
+    } else if (K <= kThin) {
+      const dim3 g(nblk(N, 256), nblk(rows, kFwdRows));
+#define WS_FWDK_TANH(KT) k_fwd_thin_k<true, KT><<<g, 256, 0, st>>>(in[l], W, b, o[l], rows, K, N)
+#define WS_FWDK_LIN(KT) k_fwd_thin_k<false, KT><<<g, 256, 0, st>>>(in[l], W, b, o[l], rows, K, N)
+      if (l < 2) {
+        WS_THIN_DISPATCH(K, WS_FWDK_TANH)
+      } else {
+        WS_THIN_DISPATCH(K, WS_FWDK_LIN)
+      }
+#undef WS_FWDK_TANH
+#undef WS_FWDK_LIN
     } else if (l < 2) {
       sgemm<false, false, kEpiBiasTanh>(ggrid(rows, N), st, in[l], K, W, N, o[l], rows, N, 0, K, 0, 0,
                                         b);
@@ -678,8 +754,14 @@ void mlp_backward(const PolicyShape &sh, const float *params, const float *X, co
       k_colsum_slices<<<dim3(nblk(N, 32), (unsigned)nz), 256, 0, st>>>(D, part, rows, M, N);
     }
     k_reduce_slices<<<nblk(len, 32), 256, 0, st>>>(part, nz, len, grad + sh.layer_offset(l));
-    if (l > 0) {
+    if (l > 0 && N <= kThin) {
       // gradient at layer l's input pre-activation: (D W_l^T) * (1 - a_l^2)
+      const dim3 g(nblk(M, 256), nblk(rows, kFwdRows));
+#define WS_DG(KT) k_dgrad_thin_k<KT><<<g, 256, 0, st>>>(D, params + sh.layer_offset(l), ain[l], \
+                                                        dl[l], rows, N, M)
+      WS_THIN_DISPATCH(N, WS_DG)
+#undef WS_DG
+    } else if (l > 0) {
       sgemm<false, true, kEpiDTanh>(ggrid(rows, M), st, D, N, params + sh.layer_offset(l), N, dl[l],
                                     rows, M, 0, N, 0, 0, ain[l]);
     }
