@@ -422,7 +422,8 @@ def run_a2c(wl, local):
                          "frac": achieved / peak,
                          "peak_source": f"128 FP32 lanes x 2 flops / clock / SM x {n_sms} SMs x "
                                         "2070 MHz"},
-            "kernels": "k_a2c_gather, k_sgemm (forward, weight and data gradients), k_fwd_thin, "
+            "kernels": "k_a2c_gather, k_sgemm (forward, weight and data gradients of the "
+                       "wide layers; packed f32x2 FMAs), k_fwd_thin, k_fwd_thin_k, k_dgrad_thin_k, "
                        "k_wgrad_thin_n/_m, k_colsum_slices, k_reduce_slices, k_a2c_head, k_sgd; "
                        "FP32 SIMT",
             "ppo": {"advantages_ms": statistics.median(ms_adv),
