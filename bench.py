@@ -717,6 +717,14 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "latency": {"chunk_steps": CHUNK, "p50_ms": float(np.percentile(lat, 50)),
                     "p99_ms": float(np.percentile(lat, 99))},
+        # every timed step resets the envs under its own seed (1000 + warm-up
+        # + step index): the spread of the step time over those seeds
+        "seeds": {"reset_seeds": [1000 + args.warmup + i for i in range(args.steps)],
+                  "ms_min": float(min(main_res["times"])),
+                  "ms_median": float(statistics.median(main_res["times"])),
+                  "ms_max": float(max(main_res["times"])),
+                  "rel_spread": float((max(main_res["times"]) - min(main_res["times"]))
+                                      / statistics.median(main_res["times"]))},
         "roofline": roofline,
         "roofline_returns": returns_roofline,
         "roofline_force": force_roofline,
