@@ -146,6 +146,12 @@ typedef enum {
  * ws_a2c_update and ws_ppo_update, and the ring's ADVANTAGE (and, for the
  * landscape, SAMPLE) field. */
 #define WS_FLAG_TRAIN 8u
+/* ws_config.flags: bounds check for debugging.  The state and the ring buffer
+ * each end in a 256-byte canary (counted by ws_query_bytes) that ws_create
+ * fills with 0xA5; ws_sync checks both after its wait and fails with
+ * WS_ERR_CUDA ("canary overwritten", sticky) if a kernel wrote past the end of
+ * either buffer's used part. */
+#define WS_FLAG_BOUNDS_CHECK 16u
 
 /* Roll-out configuration.  Slots: control and landscape have one agent per
  * env (n_slots = n_envs); the economy has agents_per_env[e] agents in env e,

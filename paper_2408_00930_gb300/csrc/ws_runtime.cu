@@ -43,6 +43,8 @@ struct ws_ctx {
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr size_t kCanary = 256;            // WS_FLAG_BOUNDS_CHECK tail per buffer
+constexpr unsigned char kCanaryByte = 0xA5;
 inline size_t up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 // The critic of WS_FLAG_TRAIN: the policy's widths with one output.
@@ -69,7 +71,8 @@ ws_status validate(const ws_config *cfg) {
   if (cfg->ring_steps < 1 || cfg->episode_limit < 1) return WS_ERR_INVALID;
   if (cfg->hidden0 < 1 || cfg->hidden0 > 4096 || cfg->hidden1 < 1 || cfg->hidden1 > 4096)
     return WS_ERR_INVALID;
-  if (cfg->flags & ~(WS_FLAG_DEBUG_LOGITS | WS_FLAG_ENERGY_TARGET | WS_FLAG_FORCE | WS_FLAG_TRAIN))
+  if (cfg->flags & ~(WS_FLAG_DEBUG_LOGITS | WS_FLAG_ENERGY_TARGET | WS_FLAG_FORCE | WS_FLAG_TRAIN |
+                     WS_FLAG_BOUNDS_CHECK))
     return WS_ERR_INVALID;
   if ((cfg->flags & WS_FLAG_FORCE) && cfg->env != WS_ENV_LANDSCAPE) return WS_ERR_INVALID;
   if ((cfg->flags & WS_FLAG_ENERGY_TARGET) &&
@@ -304,6 +307,8 @@ Layout make_layout(const ws_config *cfg, const std::vector<int32_t> &agents) {
     if (cfg->env == WS_ENV_ECONOMY) o += up(critic_shape(L.pol_planner).count() * 4);
     L.train_off = o; o += up(train_scratch_bytes(L.pol));
   }
+  L.state_canary_off = o;
+  if (cfg->flags & WS_FLAG_BOUNDS_CHECK) o += kCanary;
   L.state_bytes = o;
   size_t r = 0;
   L.ring_obs = r; r += up(R * L.obs_dim * S * 4);
@@ -324,6 +329,8 @@ Layout make_layout(const ws_config *cfg, const std::vector<int32_t> &agents) {
   L.ring_sample = r;
   if (cfg->env == WS_ENV_LANDSCAPE && (cfg->flags & WS_FLAG_TRAIN))
     r += up(R * (size_t)cfg->dim * S * 4);
+  L.ring_canary_off = r;
+  if (cfg->flags & WS_FLAG_BOUNDS_CHECK) r += kCanary;
   L.ring_bytes = r;
   return L;
 }
@@ -746,6 +753,11 @@ ws_status ws_create(const ws_config *cfg, void *state_buf, size_t state_bytes, v
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->br.fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->br.join, cudaEventDisableTiming);
   }
+  if (e == cudaSuccess && (cfg->flags & WS_FLAG_BOUNDS_CHECK)) {
+    e = cudaMemsetAsync(c->state + c->L.state_canary_off, kCanaryByte, kCanary, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(c->ring + c->L.ring_canary_off, kCanaryByte, kCanary, c->stream);
+  }
   if (e != cudaSuccess) {
     cuda_check(c, e, "stream/event create");
     ws_status r = c->err;
@@ -1057,6 +1069,23 @@ ws_status ws_sync(ws_ctx *c, uint32_t timeout_ms) {
     char buf[96];
     std::snprintf(buf, sizeof buf, "device wait ran out (site %u)", flag[1]);
     return fail(c, WS_ERR_TIMEOUT, buf);
+  }
+  if (c->cfg.flags & WS_FLAG_BOUNDS_CHECK) {
+    unsigned char tail[2][kCanary];
+    s = cuda_check(c, cudaMemcpy(tail[0], c->state + c->L.state_canary_off, kCanary,
+                                 cudaMemcpyDeviceToHost), "canary");
+    if (s == WS_OK)
+      s = cuda_check(c, cudaMemcpy(tail[1], c->ring + c->L.ring_canary_off, kCanary,
+                                   cudaMemcpyDeviceToHost), "canary");
+    if (s != WS_OK) return s;
+    for (int b = 0; b < 2; ++b)
+      for (size_t i = 0; i < kCanary; ++i)
+        if (tail[b][i] != kCanaryByte) {
+          char buf[96];
+          std::snprintf(buf, sizeof buf, "canary overwritten (%s buffer, byte %zu)",
+                        b ? "ring" : "state", i);
+          return fail(c, WS_ERR_CUDA, buf);
+        }
   }
   return WS_OK;
 }

@@ -39,6 +39,7 @@ WS_FLAG_DEBUG_LOGITS = 1
 WS_FLAG_ENERGY_TARGET = 2
 WS_FLAG_FORCE = 4
 WS_FLAG_TRAIN = 8
+WS_FLAG_BOUNDS_CHECK = 16
 
 
 class ws_config(C.Structure):
