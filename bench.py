@@ -222,7 +222,7 @@ def oracle_throughput(wl_name, target_s=20.0):
     sample = (f"{cores} processes x {envs_per_core} envs x {steps} steps of the workload "
               f"({total} agent-steps, FP64 C oracle, {wall:.1f} s wall; "
               f"{single:.0f} agent-steps/s per process)")
-    return total / wall, cores, sample, wall, single
+    return total / wall, cores, sample, wall, single, steps
 
 
 # ----------------------------------------------------------------- GPU leg
@@ -554,12 +554,13 @@ def main():
     world, rank, local = dist_init()
     if args.impl == "reference":
         if rank == 0:
-            v, cores, sample, wall, single = oracle_throughput(args.workload)
-            steps_ms = wall * 1e3
+            # one timed sample: every process rolls its envs over `steps` env
+            # steps; the line reports those steps and the wall time per step
+            v, cores, sample, wall, single, steps = oracle_throughput(args.workload)
             print(json.dumps({
                 "impl": "reference", "metric": METRIC, "value": v, "unit": "agent-steps/s",
-                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": steps_ms, "higher_is_better": True, "scaling": "weak",
+                "n_gpus": args.gpus, "steps": steps, "warmup": 0,
+                "ms_per_step": wall * 1e3 / steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": wl["desc"], "arm": "FP64 C oracle on host cores"},
                 "cpu_baseline": {"value": v, "unit": "agent-steps/s", "cores": cores,
@@ -570,7 +571,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         # before the first GPU call: the pool is spawned, never forked after CUDA init
-        v, cores, sample, _, single = oracle_throughput(args.workload)
+        v, cores, sample, _, single, _ = oracle_throughput(args.workload)
         cpu = {"value": v, "unit": "agent-steps/s", "cores": cores, "kind": "oracle",
                "sample": sample, "single_core_value": single}
     path, value, main_res, plain, e2e = run_gpu(args, wl, world, rank, local)

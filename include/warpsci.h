@@ -45,7 +45,8 @@ typedef enum {
   WS_OK = 0,
   WS_ERR_INVALID = 1,     /* bad argument or configuration                  */
   WS_ERR_NOMEM = 2,       /* a buffer is smaller than ws_query_bytes asks   */
-  WS_ERR_CUDA = 3,        /* a CUDA call or a kernel failed                 */
+  WS_ERR_CUDA = 3,        /* a CUDA call or a kernel failed, or a bounds-
+                             check canary was overwritten (ws_sync)         */
   WS_ERR_TIMEOUT = 4,     /* ws_sync gave up, or a device wait ran out      */
   WS_ERR_STATE = 5,       /* call not valid in the context's current state  */
   WS_ERR_RANGE = 6,       /* requested steps are not (or no longer) in ring */
@@ -94,6 +95,13 @@ typedef enum { WS_PATH_PLAIN_FP32 = 0, WS_PATH_BATCHED_FP32 = 1, WS_PATH_BATCHED
  *   SAMPLE  f32 [t][dim][n_slots]       landscape with WS_FLAG_TRAIN: the
  *                                       unclipped Gaussian sample mean + sigma z
  *                                       of each step (ws_advantages)
+ *   POLICY_OUT f32 [t][n_out][n_slots]  WS_FLAG_DEBUG_LOGITS: the policy outputs
+ *                                       each step's sampler used, in FP32 (the
+ *                                       logits; landscape: mean, then the raw
+ *                                       log sigma before its clamp), written by
+ *                                       every path; n_out is the agents' width
+ *                                       (economy 20) and a planner slot holds
+ *                                       its 10 logits in rows 0..9, zeros after
  * State fields (no step range; t0 and n_steps must be 0):
  *   STATE   control:   f32 s[4][n_envs] (x, v, th, w), i32 t[n_envs]
  *           acrobot:   f32 s[4][n_envs] (th1, th2, w1, w2), i32 t[n_envs]
@@ -124,12 +132,15 @@ typedef enum {
   WS_F_FORCE = 12,
   WS_F_CRITIC = 13,
   WS_F_ADVANTAGE = 14,
-  WS_F_SAMPLE = 15
+  WS_F_SAMPLE = 15,
+  WS_F_POLICY_OUT = 16
 } ws_field;
 
-/* ws_config.flags: the fused kernels (economy on the BF16 path) also write each
- * step's policy outputs to the LOGITS field (costs HBM bandwidth; for tests
- * and debugging).  The per-step paths always keep them. */
+/* ws_config.flags: every path also records each step's policy outputs in the
+ * ring's POLICY_OUT field, and the fused economy and landscape kernels also
+ * keep the last step's in the LOGITS field (costs HBM bandwidth; for tests and
+ * debugging: the sampled actions can then be checked against the very logits
+ * the sampler read).  The per-step paths always keep LOGITS. */
 #define WS_FLAG_DEBUG_LOGITS 1u
 /* ws_config.flags: landscape episodes also end when the pure energy E(x') of
  * the post-step state falls below ws_config.energy_target (the low-energy
@@ -287,8 +298,12 @@ ws_status ws_load(ws_ctx *ctx, ws_field field, const void *src, size_t src_bytes
 ws_status ws_get_step(const ws_ctx *ctx, uint64_t *k);
 
 /* Block the host until the context's stream is idle, or return
- * WS_ERR_TIMEOUT after timeout_ms milliseconds (0 = wait forever).  Reads the
- * device error flag of the fused kernels; a set flag -> WS_ERR_TIMEOUT. */
+ * WS_ERR_TIMEOUT after timeout_ms milliseconds (0 = wait forever; this one is
+ * not sticky).  Then reads the device error flag of the tensor-core kernels: a
+ * set flag (a bounded device wait ran out) is a sticky WS_ERR_TIMEOUT, and
+ * ws_last_error names the wait's site.  With WS_FLAG_BOUNDS_CHECK it also
+ * checks the canaries: an overwritten one is a sticky WS_ERR_CUDA, and
+ * ws_last_error names the buffer, the field the canary guards and the byte. */
 ws_status ws_sync(ws_ctx *ctx, uint32_t timeout_ms);
 
 /* One-line description of the sticky error, or "" if none.  Never NULL. */

@@ -130,14 +130,13 @@ struct Layout {
   size_t scratch_h0_off, scratch_h1_off, scratch_out_off;
   size_t scratch_pobs_off, scratch_ph0_off, scratch_ph1_off, scratch_pout_off;
   size_t scratch_income_off;
-  size_t state_canary_off;  // WS_FLAG_BOUNDS_CHECK: the state's 256-byte canary
   size_t state_bytes;
   // ring buffer: per field, [ring_steps][...]
   size_t ring_obs, ring_act, ring_logp, ring_rew, ring_done, ring_ret, ring_wealth, ring_energy;
   size_t ring_force;  // landscape with WS_FLAG_FORCE
   size_t ring_adv;    // WS_FLAG_TRAIN: advantages of ws_advantages
   size_t ring_sample; // landscape with WS_FLAG_TRAIN: behaviour samples of ws_advantages
-  size_t ring_canary_off;   // WS_FLAG_BOUNDS_CHECK: the ring's 256-byte canary
+  size_t ring_pout;   // WS_FLAG_DEBUG_LOGITS: every step's policy outputs
   size_t ring_bytes;
 };
 

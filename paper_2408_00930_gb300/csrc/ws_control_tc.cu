@@ -611,6 +611,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           d.r_logp[o] = lp;
           d.r_rew[o] = rew;
           d.r_done[o] = (uint8_t)done;
+          if (d.r_pout) {  // the FP32 logits the draw read
+            float *po = d.r_pout + (size_t)row * E::NA * S + e;
+            po[0] = l0;
+            po[S] = l1v;
+            if (ACRO) po[2 * (size_t)S] = l2;
+          }
         }
         if (done) {
           uint4 rr;

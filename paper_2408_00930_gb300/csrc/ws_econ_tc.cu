@@ -522,6 +522,8 @@ __global__ void __launch_bounds__((AT + 1) * 128, 1)
           if (d.dbg_logits) {
 #pragma unroll
             for (int c = 0; c < kNA; ++c) d.out[(size_t)slot * kNA + c] = lg[c];
+#pragma unroll
+            for (int c = 0; c < kNA; ++c) d.r_pout[(rowR * kNA + c) * S + slot] = lg[c];
           }
           const uint32_t rp = draw(seed, k, env, agent, kTagPartner, 0).x;
           const uint32_t p = (agent + 1u + bounded(rp, (uint32_t)(n - 1))) % (uint32_t)n;
@@ -735,6 +737,9 @@ __global__ void __launch_bounds__((AT + 1) * 128, 1)
             if (d.dbg_logits) {
 #pragma unroll
               for (int c = 0; c < kNP; ++c) d.pout[(size_t)penv * kNP + c] = lg[c];
+#pragma unroll
+              for (int c = 0; c < kNA; ++c)
+                d.r_pout[(rowR * kNA + c) * S + ps] = c < kNP ? lg[c] : 0.f;
             }
             envi[pt].w = tau;
             const int t2 = t + 1;

@@ -58,6 +58,7 @@ struct Dev {
   float *r_force;  // landscape FORCE field [t][D][slot] (WS_FLAG_FORCE), else null
   float *r_adv;    // ADVANTAGE field [t][slot] (WS_FLAG_TRAIN), else null
   float *r_sample; // landscape SAMPLE field [t][D][slot] (WS_FLAG_TRAIN), else null
+  float *r_pout;   // POLICY_OUT field [t][n_out][slot] (WS_FLAG_DEBUG_LOGITS), else null
   uint8_t *r_done;
   int64_t *r_wealth;
 };

@@ -711,9 +711,12 @@ __global__ void __launch_bounds__(kThreads, 1)
               if (c < 2 * D) out[c] = __uint_as_float(z[i]) + *(const float *)(sm + PK_B3 + c * 4);
             }
           }
-          if (rec && own && d.dbg_logits)
+          if (rec && own && d.dbg_logits) {
 #pragma unroll
             for (int c = 0; c < 2 * D; ++c) d.out[(size_t)e * 2 * D + c] = out[c];
+#pragma unroll
+            for (int c = 0; c < 2 * D; ++c) d.r_pout[(rowR * 2 * D + c) * S + e] = out[c];
+          }
           float mu[DH], lsr[DH];
 #pragma unroll
           for (int i = 0; i < DH; ++i) {

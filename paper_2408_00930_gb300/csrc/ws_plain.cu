@@ -302,6 +302,10 @@ __global__ void k_sample_cat(Dev d, uint32_t off, const float *logits, int n_cls
   const size_t o = (size_t)row * d.n_slots + slot_base + i;
   ((int32_t *)d.r_act)[o] = a;
   d.r_logp[o] = (l[a] - m) - logf(S);
+  if (d.r_pout) {  // the logits this draw read (a planner's rows past its 10 are zero)
+    float *po = d.r_pout + (size_t)row * d.n_out * d.n_slots + slot_base + i;
+    for (int c = 0; c < (int)d.n_out; ++c) po[(size_t)c * d.n_slots] = c < n_cls ? l[c] : 0.f;
+  }
 }
 
 // Diagonal Gaussian head: mean out[0:D], log sigma clamp(out[D:2D], -5, 2);
@@ -329,6 +333,10 @@ __global__ void k_sample_gauss(Dev d, uint32_t off) {
     }
   }
   d.r_logp[(size_t)row * d.n_slots + e] = lp;
+  if (d.r_pout) {
+    float *po = d.r_pout + (size_t)row * 2 * D * d.n_slots + e;
+    for (int c = 0; c < 2 * D; ++c) po[(size_t)c * d.n_slots] = o[c];
+  }
 }
 
 // ----------------------------------------------------- S4/S5 control env

@@ -16,6 +16,13 @@
 
 using namespace ws;
 
+// A WS_FLAG_BOUNDS_CHECK canary: its byte offset in the state or ring buffer
+// and the region it follows.
+struct Canary {
+  size_t off;
+  const char *after;
+};
+
 struct ws_ctx {
   ws_config cfg;
   Layout L;
@@ -36,6 +43,7 @@ struct ws_ctx {
   int tc_grid = 0;                  // fused control kernel: default persistent grid
   ws_launch lc{};                   // launch configuration (ws_get_launch / ws_tune)
   std::vector<int32_t> items;       // fused economy kernel: host copy of the work items
+  std::vector<Canary> state_spots, ring_spots;  // WS_FLAG_BOUNDS_CHECK canaries
   ws_status err = WS_OK;
   std::string msg;
 };
@@ -43,7 +51,7 @@ struct ws_ctx {
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr size_t kCanary = 256;            // WS_FLAG_BOUNDS_CHECK tail per buffer
+constexpr size_t kCanary = 256;            // WS_FLAG_BOUNDS_CHECK canary after each region
 constexpr unsigned char kCanaryByte = 0xA5;
 inline size_t up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
@@ -190,7 +198,9 @@ size_t tc_layers_bytes(const PolicyShape &p) {
   return n;
 }
 
-Layout make_layout(const ws_config *cfg, const std::vector<int32_t> &agents) {
+Layout make_layout(const ws_config *cfg, const std::vector<int32_t> &agents,
+                   std::vector<Canary> *state_spots = nullptr,
+                   std::vector<Canary> *ring_spots = nullptr) {
   Layout L{};
   L.env = cfg->env;
   L.path = cfg->path;
@@ -234,14 +244,30 @@ Layout make_layout(const ws_config *cfg, const std::vector<int32_t> &agents) {
   }
   const size_t N = cfg->n_envs, S = L.n_slots, Sa = L.n_agent_slots, M = cfg->n_gauss,
                D = cfg->dim, R = cfg->ring_steps;
+  // Regions are carved in order, each 256-byte aligned.  With
+  // WS_FLAG_BOUNDS_CHECK each one is followed right at its end by a 256-byte
+  // canary (recorded with the region's name), so that a kernel writing past one
+  // field hits the canary before the next field.
+  const bool check = (cfg->flags & WS_FLAG_BOUNDS_CHECK) != 0;
+  auto carve = [&](size_t &o, size_t bytes, const char *name, std::vector<Canary> *spots) {
+    const size_t at = o;
+    o = at + bytes;
+    if (check && bytes) {
+      if (spots) spots->push_back(Canary{o, name});
+      o += kCanary;
+    }
+    o = up(o);
+    return at;
+  };
+  auto st = [&](size_t &o, size_t bytes, const char *name) { return carve(o, bytes, name, state_spots); };
+  auto rg = [&](size_t &o, size_t bytes, const char *name) { return carve(o, bytes, name, ring_spots); };
   size_t o = 0;
-  L.k_off = o; o += up(8);
-  L.err_off = o; o += up(8);
-  L.params_off = o; o += up(L.pol.count() * 4);
-  L.params_planner_off = o;
-  if (cfg->env == WS_ENV_ECONOMY) o += up(L.pol_planner.count() * 4);
+  L.k_off = st(o, 8, "step counter");
+  L.err_off = st(o, 8, "error flag");
+  L.params_off = st(o, L.pol.count() * 4, "PARAMS");
+  L.params_planner_off =
+      st(o, cfg->env == WS_ENV_ECONOMY ? L.pol_planner.count() * 4 : 0, "planner PARAMS");
   L.econ_fused = use_econ_fused(cfg, L.pol, L.pol_planner, agents) ? 1 : 0;
-  L.packed_off = o;
   L.packed_bytes = use_tc_control(cfg) ? control_tc_packed_bytes(L.pol) : 0;
   if (use_tc_layers(cfg))
     L.packed_bytes = tc_layers_bytes(L.pol) +
@@ -251,86 +277,80 @@ Layout make_layout(const ws_config *cfg, const std::vector<int32_t> &agents) {
   if (L.econ_fused) L.packed_bytes = econ_tc_packed_bytes();
   L.land_fused = use_land_fused(cfg, L.pol) ? 1 : 0;
   if (L.land_fused) L.packed_bytes = land_tc_policy_bytes();
-  o += up(L.packed_bytes);
-  L.env_params_off = o;
-  if (cfg->env == WS_ENV_LANDSCAPE) o += up(M * D * 4) + up(M * 4) + up(M * 4);
-  if (cfg->env == WS_ENV_ECONOMY) o += up(N * 4);
-  L.env_derived_off = o;
+  L.packed_off = st(o, L.packed_bytes, "BF16 operand images");
+  size_t env_params = 0;
+  if (cfg->env == WS_ENV_LANDSCAPE) env_params = up(M * D * 4) + up(M * 4) + up(M * 4);
+  if (cfg->env == WS_ENV_ECONOMY) env_params = up(N * 4);
+  L.env_params_off = st(o, env_params, "ENV_PARAMS");
+  // landscape tables: |c|^2 and the exponent coefficients, the BF16 centre
+  // image, the fused kernel's energy image and its force image
   L.env_derived_bytes = cfg->env == WS_ENV_LANDSCAPE ? up(M * 4) + up(M * 4) : 0;
   if (cfg->env == WS_ENV_LANDSCAPE && cfg->path == WS_PATH_BATCHED_BF16)
     L.env_derived_bytes += up(energy_tc_bytes((int)D, (int)M));
-  L.land_energy_off = L.env_derived_off + L.env_derived_bytes;
+  const size_t land_energy_rel = L.env_derived_bytes;
   if (L.land_fused) L.env_derived_bytes += up(land_tc_energy_bytes((int)M));
-  L.force_img_off = L.env_derived_off + L.env_derived_bytes;
+  const size_t force_img_rel = L.env_derived_bytes;
   if (L.land_fused && (cfg->flags & WS_FLAG_FORCE)) L.env_derived_bytes += up(force_tc_bytes((int)M));
-  o += L.env_derived_bytes;
-  L.state_off = o;
-  if (cfg->env == WS_ENV_CONTROL || cfg->env == WS_ENV_ACROBOT) o += up(4 * N * 4);
-  if (cfg->env == WS_ENV_ECONOMY) o += up(Sa * 8) + up(kEconF * Sa * 4);
-  if (cfg->env == WS_ENV_LANDSCAPE) o += up(D * N * 4) + up(N * 4) + up(N);
-  L.t_off = o; o += up(N * 4);
-  L.aux_off = o;
-  if (cfg->env == WS_ENV_ECONOMY) o += up((N + 1) * 4) + up(Sa * 4);
-  L.items_off = o;
-  if (L.econ_fused) o += up(N * 16);
-  L.queue_off = o;
-  if (L.econ_fused) o += up(8);
+  L.env_derived_off = st(o, L.env_derived_bytes, "landscape tables");
+  L.land_energy_off = L.env_derived_off + land_energy_rel;
+  L.force_img_off = L.env_derived_off + force_img_rel;
+  size_t state = 0;
+  if (cfg->env == WS_ENV_CONTROL || cfg->env == WS_ENV_ACROBOT) state = up(4 * N * 4);
+  if (cfg->env == WS_ENV_ECONOMY) state = up(Sa * 8) + up(kEconF * Sa * 4);
+  if (cfg->env == WS_ENV_LANDSCAPE) state = up(D * N * 4) + up(N * 4) + up(N);
+  L.state_off = st(o, state, "STATE");
+  L.t_off = st(o, N * 4, "episode counters");
+  L.aux_off = st(o, cfg->env == WS_ENV_ECONOMY ? up((N + 1) * 4) + up(Sa * 4) : 0,
+                 "agent offsets");
+  L.items_off = st(o, L.econ_fused ? N * 16 : 0, "work items");
+  L.queue_off = st(o, L.econ_fused ? 8 : 0, "work queue");
   L.scratch_off = o;
   const bool plain_scratch = !use_tc_control(cfg) && !L.econ_fused;
   if (L.econ_fused && (cfg->flags & WS_FLAG_DEBUG_LOGITS)) {
-    L.scratch_out_off = o; o += up(Sa * L.n_out * 4);
-    L.scratch_pout_off = o; o += up(N * 10 * 4);
+    L.scratch_out_off = st(o, Sa * L.n_out * 4, "LOGITS");
+    L.scratch_pout_off = st(o, N * 10 * 4, "planner LOGITS");
   }
   if (plain_scratch) {
-    L.scratch_h0_off = o; o += up(S * cfg->hidden0 * 4);
-    L.scratch_h1_off = o; o += up(S * cfg->hidden1 * 4);
-    L.scratch_out_off = o; o += up(S * L.n_out * 4);
+    L.scratch_h0_off = st(o, S * cfg->hidden0 * 4, "hidden 0");
+    L.scratch_h1_off = st(o, S * cfg->hidden1 * 4, "hidden 1");
+    L.scratch_out_off = st(o, S * L.n_out * 4, "LOGITS");
     if (cfg->env == WS_ENV_ECONOMY) {
-      L.scratch_pobs_off = o; o += up(N * kEconF * 4);
-      L.scratch_ph0_off = o; o += up(N * cfg->hidden0 * 4);
-      L.scratch_ph1_off = o; o += up(N * cfg->hidden1 * 4);
-      L.scratch_pout_off = o; o += up(N * 10 * 4);
-      L.scratch_income_off = o; o += up(Sa * 8);
+      L.scratch_pobs_off = st(o, N * kEconF * 4, "planner observation");
+      L.scratch_ph0_off = st(o, N * cfg->hidden0 * 4, "planner hidden 0");
+      L.scratch_ph1_off = st(o, N * cfg->hidden1 * 4, "planner hidden 1");
+      L.scratch_pout_off = st(o, N * 10 * 4, "planner LOGITS");
+      L.scratch_income_off = st(o, Sa * 8, "income");
     }
-    if (cfg->env == WS_ENV_LANDSCAPE) {
-      L.scratch_income_off = o; o += up((size_t)kEnergyChunks * 2 * N * 4);  // energy partials
-    }
-    if (cfg->env == WS_ENV_ACROBOT) {
-      L.scratch_pobs_off = o; o += up((size_t)kAcroObs * N * 4);  // the policy's input
-    }
+    if (cfg->env == WS_ENV_LANDSCAPE)  // energy partials
+      L.scratch_income_off = st(o, (size_t)kEnergyChunks * 2 * N * 4, "energy partials");
+    if (cfg->env == WS_ENV_ACROBOT)    // the policy's input
+      L.scratch_pobs_off = st(o, (size_t)kAcroObs * N * 4, "acrobot observation");
   }
   L.critic_off = L.train_off = o;
   if (cfg->flags & WS_FLAG_TRAIN) {
     // critics: the policy's (agents'), then the planner's
-    L.critic_off = o;
-    o += up(critic_shape(L.pol).count() * 4);
-    if (cfg->env == WS_ENV_ECONOMY) o += up(critic_shape(L.pol_planner).count() * 4);
-    L.train_off = o; o += up(train_scratch_bytes(L.pol));
+    size_t cb = up(critic_shape(L.pol).count() * 4);
+    if (cfg->env == WS_ENV_ECONOMY) cb += up(critic_shape(L.pol_planner).count() * 4);
+    L.critic_off = st(o, cb, "CRITIC");
+    L.train_off = st(o, train_scratch_bytes(L.pol), "update scratch");
   }
-  L.state_canary_off = o;
-  if (cfg->flags & WS_FLAG_BOUNDS_CHECK) o += kCanary;
   L.state_bytes = o;
   size_t r = 0;
-  L.ring_obs = r; r += up(R * L.obs_dim * S * 4);
-  L.ring_act = r; r += up(R * L.act_dim * S * 4);
-  L.ring_logp = r; r += up(R * S * 4);
-  L.ring_rew = r; r += up(R * S * 4);
-  L.ring_done = r; r += up(R * S);
-  L.ring_ret = r; r += up(R * S * 4);
-  L.ring_wealth = r;
-  if (cfg->env == WS_ENV_ECONOMY) r += up(R * S * 8);
-  L.ring_energy = r;
-  if (cfg->env == WS_ENV_LANDSCAPE) r += up(R * S * 4);
-  L.ring_force = r;
-  if (cfg->env == WS_ENV_LANDSCAPE && (cfg->flags & WS_FLAG_FORCE))
-    r += up(R * (size_t)cfg->dim * S * 4);
-  L.ring_adv = r;
-  if (cfg->flags & WS_FLAG_TRAIN) r += up(R * S * 4);
-  L.ring_sample = r;
-  if (cfg->env == WS_ENV_LANDSCAPE && (cfg->flags & WS_FLAG_TRAIN))
-    r += up(R * (size_t)cfg->dim * S * 4);
-  L.ring_canary_off = r;
-  if (cfg->flags & WS_FLAG_BOUNDS_CHECK) r += kCanary;
+  L.ring_obs = rg(r, R * L.obs_dim * S * 4, "OBS");
+  L.ring_act = rg(r, R * L.act_dim * S * 4, "ACTION");
+  L.ring_logp = rg(r, R * S * 4, "LOGP");
+  L.ring_rew = rg(r, R * S * 4, "REWARD");
+  L.ring_done = rg(r, R * S, "DONE");
+  L.ring_ret = rg(r, R * S * 4, "RETURN");
+  L.ring_wealth = rg(r, cfg->env == WS_ENV_ECONOMY ? R * S * 8 : 0, "WEALTH");
+  L.ring_energy = rg(r, cfg->env == WS_ENV_LANDSCAPE ? R * S * 4 : 0, "ENERGY");
+  L.ring_force = rg(r, cfg->env == WS_ENV_LANDSCAPE && (cfg->flags & WS_FLAG_FORCE)
+                           ? R * (size_t)cfg->dim * S * 4 : 0, "FORCE");
+  L.ring_adv = rg(r, (cfg->flags & WS_FLAG_TRAIN) ? R * S * 4 : 0, "ADVANTAGE");
+  L.ring_sample = rg(r, cfg->env == WS_ENV_LANDSCAPE && (cfg->flags & WS_FLAG_TRAIN)
+                            ? R * (size_t)cfg->dim * S * 4 : 0, "SAMPLE");
+  L.ring_pout = rg(r, (cfg->flags & WS_FLAG_DEBUG_LOGITS) ? R * (size_t)L.n_out * S * 4 : 0,
+                   "POLICY_OUT");
   L.ring_bytes = r;
   return L;
 }
@@ -441,6 +461,7 @@ void make_dev(ws_ctx *c) {
   d.r_sample = (cfg.env == WS_ENV_LANDSCAPE && (cfg.flags & WS_FLAG_TRAIN))
                    ? (float *)(R + L.ring_sample)
                    : nullptr;
+  d.r_pout = (cfg.flags & WS_FLAG_DEBUG_LOGITS) ? (float *)(R + L.ring_pout) : nullptr;
 }
 
 void drop_graphs(ws_ctx *c) {
@@ -592,6 +613,9 @@ size_t ring_field_step_bytes(const ws_ctx *c, ws_field f, size_t *field_off) {
     case WS_F_SAMPLE:
       if (L.env != WS_ENV_LANDSCAPE || !(c->cfg.flags & WS_FLAG_TRAIN)) return 0;
       *field_off = L.ring_sample; return (size_t)c->cfg.dim * S * 4;
+    case WS_F_POLICY_OUT:
+      if (!(c->cfg.flags & WS_FLAG_DEBUG_LOGITS)) return 0;
+      *field_off = L.ring_pout; return (size_t)L.n_out * S * 4;
     default: return 0;
   }
 }
@@ -737,7 +761,7 @@ ws_status ws_create(const ws_config *cfg, void *state_buf, size_t state_bytes, v
   c->cfg = *cfg;
   c->cfg.agents_per_env = nullptr;  // host array is copied, never kept
   agent_counts(cfg, c->agents);
-  c->L = make_layout(cfg, c->agents);
+  c->L = make_layout(cfg, c->agents, &c->state_spots, &c->ring_spots);
   c->stream = (cudaStream_t)cuda_stream;
   c->state = (char *)state_buf;
   c->ring = (char *)ring_buf;
@@ -753,11 +777,10 @@ ws_status ws_create(const ws_config *cfg, void *state_buf, size_t state_bytes, v
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->br.fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->br.join, cudaEventDisableTiming);
   }
-  if (e == cudaSuccess && (cfg->flags & WS_FLAG_BOUNDS_CHECK)) {
-    e = cudaMemsetAsync(c->state + c->L.state_canary_off, kCanaryByte, kCanary, c->stream);
-    if (e == cudaSuccess)
-      e = cudaMemsetAsync(c->ring + c->L.ring_canary_off, kCanaryByte, kCanary, c->stream);
-  }
+  for (const Canary &k : c->state_spots)
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->state + k.off, kCanaryByte, kCanary, c->stream);
+  for (const Canary &k : c->ring_spots)
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ring + k.off, kCanaryByte, kCanary, c->stream);
   if (e != cudaSuccess) {
     cuda_check(c, e, "stream/event create");
     ws_status r = c->err;
@@ -1070,22 +1093,23 @@ ws_status ws_sync(ws_ctx *c, uint32_t timeout_ms) {
     std::snprintf(buf, sizeof buf, "device wait ran out (site %u)", flag[1]);
     return fail(c, WS_ERR_TIMEOUT, buf);
   }
-  if (c->cfg.flags & WS_FLAG_BOUNDS_CHECK) {
-    unsigned char tail[2][kCanary];
-    s = cuda_check(c, cudaMemcpy(tail[0], c->state + c->L.state_canary_off, kCanary,
-                                 cudaMemcpyDeviceToHost), "canary");
-    if (s == WS_OK)
-      s = cuda_check(c, cudaMemcpy(tail[1], c->ring + c->L.ring_canary_off, kCanary,
-                                   cudaMemcpyDeviceToHost), "canary");
-    if (s != WS_OK) return s;
-    for (int b = 0; b < 2; ++b)
+  // WS_FLAG_BOUNDS_CHECK: every region's canary must still hold its fill byte
+  for (int b = 0; b < 2; ++b) {
+    const std::vector<Canary> &spots = b ? c->ring_spots : c->state_spots;
+    const char *base = b ? c->ring : c->state;
+    for (const Canary &k : spots) {
+      unsigned char tail[kCanary];
+      s = cuda_check(c, cudaMemcpy(tail, base + k.off, kCanary, cudaMemcpyDeviceToHost), "canary");
+      if (s != WS_OK) return s;
       for (size_t i = 0; i < kCanary; ++i)
-        if (tail[b][i] != kCanaryByte) {
-          char buf[96];
-          std::snprintf(buf, sizeof buf, "canary overwritten (%s buffer, byte %zu)",
-                        b ? "ring" : "state", i);
+        if (tail[i] != kCanaryByte) {
+          char buf[160];
+          std::snprintf(buf, sizeof buf,
+                        "canary overwritten (%s buffer, canary after %s at byte %zu, offset %zu)",
+                        b ? "ring" : "state", k.after, k.off + i, i);
           return fail(c, WS_ERR_CUDA, buf);
         }
+    }
   }
   return WS_OK;
 }

@@ -25,7 +25,7 @@ WS_ENV_CONTROL, WS_ENV_ECONOMY, WS_ENV_LANDSCAPE, WS_ENV_ACROBOT = 0, 1, 2, 3
 WS_PATH_PLAIN_FP32, WS_PATH_BATCHED_FP32, WS_PATH_BATCHED_BF16 = 0, 1, 2
 (WS_F_OBS, WS_F_ACTION, WS_F_LOGP, WS_F_REWARD, WS_F_DONE, WS_F_RETURN, WS_F_WEALTH, WS_F_ENERGY,
  WS_F_STATE, WS_F_PARAMS, WS_F_ENV_PARAMS, WS_F_LOGITS, WS_F_FORCE, WS_F_CRITIC,
- WS_F_ADVANTAGE, WS_F_SAMPLE) = range(16)
+ WS_F_ADVANTAGE, WS_F_SAMPLE, WS_F_POLICY_OUT) = range(17)
 
 EXPORTED = ["ws_query_bytes", "ws_create", "ws_reset", "ws_step", "ws_rollout", "ws_returns",
             "ws_forces", "ws_a2c_update", "ws_advantages", "ws_ppo_update",
@@ -357,6 +357,10 @@ class Rollout:
         return {WS_ENV_CONTROL: 4, WS_ENV_ECONOMY: 16, WS_ENV_LANDSCAPE: self.dim,
                 WS_ENV_ACROBOT: 6}[self.env]
 
+    def n_out(self):
+        return {WS_ENV_CONTROL: 2, WS_ENV_ECONOMY: 20, WS_ENV_LANDSCAPE: 2 * self.dim,
+                WS_ENV_ACROBOT: 3}[self.env]
+
     def _ring_spec(self, field):
         S = self.n_slots
         if field == WS_F_OBS:
@@ -372,6 +376,8 @@ class Rollout:
             return np.int64, (S,)
         if field in (WS_F_FORCE, WS_F_SAMPLE):
             return np.float32, (self.dim, S)
+        if field == WS_F_POLICY_OUT:
+            return np.float32, (self.n_out(), S)
         raise ValueError(field)
 
     def fetch(self, field, t0, n):

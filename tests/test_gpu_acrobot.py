@@ -11,6 +11,7 @@ import pytest
 import oracle
 from paper_2408_00930_gb300 import inputs
 from paper_2408_00930_gb300 import warpsci as W
+from tests import classic_replay as CR
 from tests import ws_helpers as H
 from tests.gpu_common import TIE_BF16, TIE_F32, TOL_BF16, TOL_F32, need_gpu
 
@@ -46,11 +47,6 @@ def test_param_init_and_reset_bit_exact(torch):
     np.testing.assert_array_equal(s, exp)
     assert np.all(t == 0)
     r.close()
-
-
-def state_from_obs(o):
-    """(th1, th2, w1, w2) from a recorded observation (cos, sin, cos, sin, w1, w2)."""
-    return np.array([np.arctan2(o[1], o[0]), np.arctan2(o[3], o[2]), o[4], o[5]])
 
 
 @pytest.mark.parametrize("path", PATHS)
@@ -111,56 +107,52 @@ def test_one_step_replay_seeded_states(torch, path):
 
 @pytest.mark.parametrize("path", PATHS)
 def test_long_rollout_teacher_forced(torch, path):
-    """2,000 envs x 300 steps from a reset: every transition of sampled envs
-    against the oracle's step from the recorded pre-step state."""
+    """2,000 envs x 300 steps from a reset, episodes ending inside and across
+    chunks: every transition of sampled envs against the oracle's step from the
+    recorded pre-step state, the draw against the path's own recorded logits."""
     n, T, limit, h = 2000, 300, 200, 64
-    r = acro(path, n, T, limit, h=h, seed=3, chunk_steps=40)
+    r = acro(path, n, T, limit, h=h, seed=3, chunk_steps=40, flags=W.WS_FLAG_DEBUG_LOGITS)
     r.reset(8)
     r.rollout(T)
     r.sync()
-    obs, act, rew, dn = (r.fetch(f, 0, T) for f in (W.WS_F_OBS, W.WS_F_ACTION, W.WS_F_REWARD,
-                                                   W.WS_F_DONE))
-    params = oracle.policy_init(3, 0, [6, h, h, 3])
+    ids = np.array([0, 1, 2, 127, 128, 999, 1920, 1998, 1999])
+    rec = CR.records(r, 0, T, ids)
+    s_all, t_all = H.unpack_control_state(r.fetch_raw(W.WS_F_STATE, 20 * n), n)
+    np.testing.assert_allclose(
+        [CR.acrobot_state_from_obs(rec["obs"][0][:, i].astype(np.float64)) for i in range(len(ids))],
+        [oracle.acrobot_reset_draw(8, oracle.STEP_INIT, e) for e in ids], rtol=0, atol=2e-6)
     bf16 = path == W.WS_PATH_BATCHED_BF16
-    tie = TIE_BF16 if bf16 else TIE_F32
-    n_amb = n_term = 0
-    for e in (0, 1, 999, 1998, 1999):
-        t = 0
-        for s in range(T):
-            st = state_from_obs(obs[s][:, e].astype(np.float64))
-            if s == 0:
-                np.testing.assert_allclose(st, oracle.acrobot_reset_draw(8, oracle.STEP_INIT, e),
-                                           rtol=0, atol=1e-6)
-            logits = oracle.mlp_forward([6, h, h, 3], params, obs[s][:, e].astype(np.float64),
-                                        bf16_layers=ORACLE_BF16_LAYERS if bf16 else 0)
-            u = oracle.u01(int(oracle.draw(8, s, e, 0, oracle.TAG_ACTION, 0)[0]))
-            a_o, _, mg = oracle.sample_categorical(logits, u)
-            a = int(act[s][e])
-            if mg < tie:
-                n_amb += 1
-            else:
-                assert a == a_o, (s, e)
-            nxt, raw = oracle.acrobot_step(st, a)      # the GPU's action
-            term, hm = oracle.acrobot_terminal(nxt)
-            t += 1
-            if hm >= HEIGHT_BAND:
-                assert dn[s][e] == (term or t >= limit), (s, e)
-                assert rew[s][e] == (0.0 if term else -1.0)
-            n_term += int(dn[s][e] and t < limit)
-            if dn[s][e]:
-                t = 0
-                if s + 1 < T:
-                    np.testing.assert_allclose(
-                        state_from_obs(obs[s + 1][:, e].astype(np.float64)),
-                        oracle.acrobot_reset_draw(8, s, e), rtol=0, atol=1e-6)
-            elif s + 1 < T:
-                o_next = obs[s + 1][:, e].astype(np.float64)
-                o_ref = oracle.acrobot_obs(nxt)
-                assert np.abs(o_next - o_ref).max() <= TOL_STEP * max(1.0, np.abs(raw).max()), \
-                    (s, e, o_next, o_ref)
-    # draws inside the tie band: ~2 boundaries x 2 tie per draw
-    assert n_amb <= (0.12 if bf16 else 0.05) * 5 * T
-    assert dn.sum() >= n                      # every env ends at least one episode
+    c = CR.replay("acrobot", rec, ids, oracle.policy_init(3, 0, [6, h, h, 3]), [6, h, h, 3], 8,
+                  limit, ORACLE_BF16_LAYERS if bf16 else 0, TOL_BF16 if bf16 else TOL_F32,
+                  s_all[ids], t_all[ids], tol_state=TOL_STEP, height_band=HEIGHT_BAND)
+    print("replay", c)
+    assert c["steps"] == len(ids) * T and c["dones"] >= len(ids)
+    assert c["tie"] <= 2 and c["done_band"] <= 2, c
+    r.close()
+
+
+def test_bf16_bench_workload_teacher_forced(torch):
+    """The acrobot bench workload on the fused kernel: 10,000 envs x 500 steps,
+    6-64-64-3, chunks of 50.  256 envs (random ones, the ragged last tile,
+    env n - 1) replayed by the oracle at every step from the recorded state."""
+    n, T, limit, h = 10000, 500, 500, 64
+    r = acro(W.WS_PATH_BATCHED_BF16, n, T, limit, h=h, seed=1, chunk_steps=50,
+             flags=W.WS_FLAG_DEBUG_LOGITS)
+    r.reset(1000)
+    for _ in range(T // 50):
+        r.rollout(50)
+    r.sync()
+    g = np.random.default_rng(1)
+    ids = np.unique(np.concatenate([g.choice(9984, 240, replace=False), np.arange(9984, n)]))
+    assert len(ids) == 256 and ids[-1] == n - 1
+    rec = CR.records(r, 0, T, ids)
+    s_all, t_all = H.unpack_control_state(r.fetch_raw(W.WS_F_STATE, 20 * n), n)
+    c = CR.replay("acrobot", rec, ids, oracle.policy_init(1, 0, [6, h, h, 3]), [6, h, h, 3], 1000,
+                  limit, ORACLE_BF16_LAYERS, TOL_BF16, s_all[ids], t_all[ids], tol_state=TOL_STEP,
+                  height_band=HEIGHT_BAND)
+    print("replay", c)
+    assert c["steps"] == len(ids) * T
+    assert c["tie"] <= 2e-4 * len(ids) * T and c["done_band"] <= 1e-3 * len(ids) * T, c
     r.close()
 
 

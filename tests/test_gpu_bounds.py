@@ -1,9 +1,12 @@
-"""WS_FLAG_BOUNDS_CHECK: the state and ring buffers end in 256-byte canaries
-that ws_sync verifies.  Every env on its batched paths (the fused BF16 kernels
-included) runs roll-outs, returns and, where the flags add them, the force
-pass and both training updates with the canaries intact; an overwrite planted
-from the host (a byte of the ring's canary set through torch) makes ws_sync
-fail with WS_ERR_CUDA and a message naming the buffer, and the error sticks."""
+"""WS_FLAG_BOUNDS_CHECK: every region of the state and ring buffers (each
+parameter block, the env state, each scratch array, each ring field) is
+followed right at its end by a 256-byte canary that ws_sync verifies.  Every
+env on its batched paths (the fused BF16 kernels included) runs roll-outs,
+returns and, where the flags add them, the force pass and both training
+updates with all canaries intact; a one-byte overrun planted from the host just
+past the end of a field (the ring's OBS field, the state's step counter) makes
+ws_sync fail with WS_ERR_CUDA and a message naming the buffer and that field,
+and the error sticks."""
 import pytest
 
 from paper_2408_00930_gb300 import warpsci as W
@@ -33,7 +36,8 @@ CASES = [
 @pytest.mark.parametrize("env,path,n,h,kw,extra", CASES)
 def test_canaries_intact(torch, env, path, n, h, kw, extra):
     T = 12
-    r = W.Rollout(env, path, n, T, 7, h, h, flags=BC | extra, chunk_steps=5, **kw)
+    r = W.Rollout(env, path, n, T, 7, h, h, flags=BC | W.WS_FLAG_DEBUG_LOGITS | extra,
+                  chunk_steps=5, **kw)
     r.reset(3)
     r.rollout(T)
     r.returns(T)
@@ -47,20 +51,31 @@ def test_canaries_intact(torch, env, path, n, h, kw, extra):
     r.close()
 
 
-def test_canary_overwrite_detected(torch):
-    r = W.Rollout(W.WS_ENV_CONTROL, F32, 64, 8, 100, 16, 16, flags=BC)
+@pytest.mark.parametrize("where", ["ring", "state"])
+def test_overrun_past_a_field_detected(torch, where):
+    n, R = 64, 8
+    r = W.Rollout(W.WS_ENV_CONTROL, F32, n, R, 100, 16, 16, flags=BC)
     r.rollout(4)
     r.sync()
-    n = r.ring_buf.numel()            # the canary is the ring's last 256 bytes
-    r.ring_buf[n - 256 + 7].fill_(0)
+    if where == "ring":
+        # OBS is the ring's first field: [R][4][n] f32 from byte 0; one byte past it
+        r.ring_buf[R * 4 * n * 4 + 3].fill_(0)
+        field = "OBS"
+    else:
+        # the step counter is the state's first region (8 bytes)
+        r.state_buf[8].fill_(0x5A)
+        field = "step counter"
     torch.cuda.synchronize()
     assert W.ws_sync(r.ctx, 0) == W.WS_ERR_CUDA
     msg = W.ws_last_error(r.ctx)
-    assert "canary" in msg and "ring" in msg, msg
+    assert "canary" in msg and where in msg and field in msg, msg
     assert W.ws_rollout(r.ctx, 1) == W.WS_ERR_CUDA      # sticky
     r.close()
-    # without the flag the buffers carry no canary
+
+
+def test_no_canaries_without_the_flag(torch):
     cfg, _ = W.make_config(W.WS_ENV_CONTROL, F32, 64, 8, 100, 16, 16)
     cfg_b, _ = W.make_config(W.WS_ENV_CONTROL, F32, 64, 8, 100, 16, 16, flags=BC)
     s0, s1 = W.ws_query_bytes(cfg), W.ws_query_bytes(cfg_b)
-    assert s1[1] == s0[1] + 256 and s1[2] == s0[2] + 256
+    # the ring's six fields (OBS, ACTION, LOGP, REWARD, DONE, RETURN) each gain one
+    assert s1[2] >= s0[2] + 6 * 256 and s1[1] > s0[1]

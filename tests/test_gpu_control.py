@@ -5,6 +5,7 @@ import pytest
 import oracle
 from paper_2408_00930_gb300 import inputs
 from paper_2408_00930_gb300 import warpsci as W
+from tests import classic_replay as CR
 from tests import ws_helpers as H
 from tests.gpu_common import (DONE_BAND_BF16, DONE_BAND_F32, TIE_BF16, TIE_F32, TOL_BF16, TOL_F32,
                               TOL_F32_FREE, control_rollout, need_gpu)
@@ -231,23 +232,28 @@ def test_bf16_one_step_replay_seeded_states(torch, h):
     r.close()
 
 
-def test_bf16_small_config_rollout(torch):
-    """1,000 envs x 200 steps, 4-64-64-2 on the tensor-core path, vs the oracle in
-    BF16-operand mode, compared up to each env's first tie-band draw."""
+def test_bf16_small_config_teacher_forced(torch):
+    """1,000 envs x 200 steps, 4-64-64-2, chunks of 50 on the fused tensor-core
+    kernel: every step of every env replayed by the oracle from the recorded
+    state, actions checked against the kernel's own recorded FP32 logits."""
     n, T, h = 1000, 200, 64
-    r = control_rollout(BF16, n, T, 200, h, h, seed=7, chunk_steps=50)
+    r = control_rollout(BF16, n, T, 200, h, h, seed=7, chunk_steps=50,
+                        flags=W.WS_FLAG_DEBUG_LOGITS)
     r.reset(42)
     r.rollout(T)
     r.sync()
-    g = {f: r.fetch(fid, 0, T) for f, fid in [("obs", W.WS_F_OBS), ("action", W.WS_F_ACTION),
-                                              ("logp", W.WS_F_LOGP), ("reward", W.WS_F_REWARD),
-                                              ("done", W.WS_F_DONE)]}
+    ids = np.arange(n)
+    rec = CR.records(r, 0, T, ids)
+    s_fin, t_fin = H.unpack_control_state(r.fetch_raw(W.WS_F_STATE, 20 * n), n)
+    np.testing.assert_array_equal(
+        rec["obs"][0].T, np.array([oracle.control_reset_draw(42, oracle.STEP_INIT, e)
+                                   for e in ids]).astype(np.float32))
     params = oracle.policy_init(7, 0, [4, h, h, 2])
-    o = oracle.control_rollout(params, h, h, seed=42, env_ids=np.arange(n), n_steps=T,
-                               episode_limit=200, bf16_layers=ORACLE_BF16_LAYERS)
-    first = _check_rollout(g, o, T, n, TIE_BF16, DONE_BAND_F32, TOL_BF16)
-    assert first.mean() > 10
-    np.testing.assert_array_equal(g["obs"][0].T, o["obs"][0].astype(np.float32))
+    c = CR.replay("control", rec, ids, params, [4, h, h, 2], 42, 200, ORACLE_BF16_LAYERS,
+                  TOL_BF16, s_fin, t_fin)
+    print("replay", c)
+    assert c["steps"] == n * T and c["dones"] > n
+    assert c["tie"] <= 2e-4 * n * T and c["done_band"] <= 1e-3 * n * T, c
     r.close()
 
 
@@ -267,43 +273,36 @@ def test_bf16_graph_is_deterministic_and_chunk_invariant(torch):
     a.close(); b.close(); c.close()
 
 
-def test_bf16_scale_config_sampled(torch):
-    """131,072 envs x 500 steps, 4-256-256-2, chunks of 50 (the launch shape the bench
-    times): initial draws exact for every env, sampled envs against the oracle."""
+def test_bf16_scale_config_teacher_forced(torch):
+    """131,072 envs x 500 steps, 4-256-256-2, chunks of 50: the launch shape the
+    bench times.  Initial draws exact for every 97th env; 256 envs (random ones,
+    the whole last tile, env n - 1) replayed by the oracle at every step from the
+    recorded state: logits, the draw from the kernel's own FP32 logits, done,
+    reset draw, next state, and the final state and episode counters."""
     n, T, h = 131072, 500, 256
-    r = control_rollout(BF16, n, T, 200, h, h, seed=1, chunk_steps=50)
+    r = control_rollout(BF16, n, T, 200, h, h, seed=1, chunk_steps=50,
+                        flags=W.WS_FLAG_DEBUG_LOGITS)
     r.reset(1000)
     for _ in range(T // 50):
         r.rollout(50)
     r.sync()
-    act = r.fetch(W.WS_F_ACTION, 0, T)
-    dn = r.fetch(W.WS_F_DONE, 0, T)
-    obs0 = r.fetch(W.WS_F_OBS, 0, 1)[0]
-    g_rng = np.random.default_rng(0)
-    ids = np.sort(g_rng.choice(n, 48, replace=False))
-    ids[-1] = n - 1
+    obs0 = CR.fetch_cols(r, W.WS_F_OBS, 0, 1, np.arange(0, n, 97))[0]
     exp0 = np.array([oracle.control_reset_draw(1000, oracle.STEP_INIT, e) for e in range(0, n, 97)])
-    np.testing.assert_array_equal(obs0[:, ::97].T, exp0.astype(np.float32))
-    obs = r.fetch(W.WS_F_OBS, 0, T)[:, :, ids]
-    lp = r.fetch(W.WS_F_LOGP, 0, T)[:, ids]
+    np.testing.assert_array_equal(obs0.T, exp0.astype(np.float32))
+    g_rng = np.random.default_rng(0)
+    ids = np.unique(np.concatenate([g_rng.choice(n - 128, 224, replace=False),
+                                    np.arange(n - 32, n)]))
+    assert len(ids) == 256 and ids[-1] == n - 1
+    rec = CR.records(r, 0, T, ids)
+    s_all, t_all = H.unpack_control_state(r.fetch_raw(W.WS_F_STATE, 20 * n), n)
     params = oracle.policy_init(1, 0, [4, h, h, 2])
-    o = oracle.control_rollout(params, h, h, seed=1000, env_ids=ids, n_steps=T, episode_limit=200,
-                               bf16_layers=ORACLE_BF16_LAYERS)
-    g = dict(obs=obs, action=act[:, ids], logp=lp, reward=np.ones((T, len(ids)), np.float32),
-             done=dn[:, ids])
-    first = _check_rollout(g, o, T, len(ids), TIE_BF16, DONE_BAND_F32, TOL_BF16)
-    assert first.mean() > 10
-    # every done leads to the Philox reset draw (checked on a sample of done events)
-    tt, ee = np.nonzero(dn[:-1])
-    pick = g_rng.choice(len(tt), min(300, len(tt)), replace=False)
-    nxt = r.fetch(W.WS_F_OBS, 0, T)
-    for i in pick:
-        t, e = int(tt[i]), int(ee[i])
-        np.testing.assert_array_equal(nxt[t + 1, :, e],
-                                      oracle.control_reset_draw(1000, t, e).astype(np.float32))
+    c = CR.replay("control", rec, ids, params, [4, h, h, 2], 1000, 200, ORACLE_BF16_LAYERS,
+                  TOL_BF16, s_all[ids], t_all[ids])
+    print("replay", c)
+    assert c["steps"] == len(ids) * T and c["dones"] > len(ids)
+    assert c["tie"] <= 2e-4 * len(ids) * T and c["done_band"] <= 1e-3 * len(ids) * T, c
     # episode statistics of the random policy: dones happen, actions are balanced
-    assert 0.2 < act.mean() < 0.8
-    assert dn.mean() > 0.01
+    assert 0.2 < rec["action"].mean() < 0.8
     r.close()
 
 
