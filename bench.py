@@ -10,9 +10,11 @@ path (the FP32 one-launch-per-step path is timed beside it).
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
                     [--impl ours|reference]
 
-Under torchrun each rank runs an independent replica of the workload on its
-own GPU (envs are independent; no collective on the data path) and rank 0
-prints one JSON line with the whole-job throughput.
+Under torchrun each rank runs one shard of a workload N times the size: rank r
+holds the workload's env count at global env ids [r n, (r + 1) n) under the
+same parameters (envs are independent and share only read-only parameters, so
+there is no collective on the data path) and rank 0 prints one JSON line with
+the whole-job throughput.
 """
 from __future__ import annotations
 
@@ -145,6 +147,13 @@ def barrier(world):
         dist.barrier()
 
 
+def shard_of(n_envs, world, rank):
+    """(env_base, n_envs) of a rank: weak scaling, every rank holds the
+    workload's env count at its own range of global env ids."""
+    assert 0 <= rank < world
+    return rank * n_envs, n_envs
+
+
 def job_throughput(units_per_rank_step, steps, world, max_ms):
     """Whole-job rate: the units all ranks processed over the slowest rank's time."""
     return units_per_rank_step * steps * world / (max_ms / 1e3)
@@ -232,7 +241,8 @@ def run_gpu(args, wl, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    kw = dict(chunk_steps=CHUNK, param_seed=1 + rank)
+    env_base, _ = shard_of(wl["n_envs"], world, rank)
+    kw = dict(chunk_steps=CHUNK, param_seed=1, env_base=env_base)
     if wl["env"] == 2:
         # the FORCE field only adds ring memory; the roll-out kernels ignore it
         kw.update(dim=wl["dim"], n_gauss=wl["n_gauss"], flags=W.WS_FLAG_FORCE)
@@ -715,7 +725,9 @@ def main():
                    "bench_step": f"ws_reset + ws_rollout x {n_chunks} chunks of {CHUNK} + ws_returns",
                    "l2": "flushed between timed steps (256 MiB write)",
                    "launch": main_res["launch"],
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": f"{world} env shards (rank r: global env ids "
+                                  f"[r n, (r + 1) n), n = {wl['n_envs']})" if world > 1
+                                  else "single GPU"},
         "latency": {"chunk_steps": CHUNK, "p50_ms": float(np.percentile(lat, 50)),
                     "p99_ms": float(np.percentile(lat, 99))},
         # every timed step resets the envs under its own seed (1000 + warm-up

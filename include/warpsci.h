@@ -188,6 +188,16 @@ typedef struct {
                                     NULL = draw U{8..256} from param_seed      */
   float energy_target;    /* landscape, with WS_FLAG_ENERGY_TARGET: done when
                              E(x') < energy_target (finite); else ignored    */
+  uint32_t env_base;      /* global id of this context's env 0 (env_base +
+                             n_envs <= 2^32 - 1).  Every per-env Philox
+                             counter (action, reset, partner, noise draws,
+                             the economy's drawn agent counts) carries the
+                             global id env_base + e, while parameters depend
+                             on param_seed alone: contexts over disjoint
+                             ranges [b, b + n) of one workload (one per GPU)
+                             record exactly what one context over the union
+                             records for those envs (paper Sec. 2: one
+                             workflow on one or several GPUs).            */
 } ws_config;
 
 /* Bytes of the two caller-owned device buffers a configuration needs:

@@ -522,8 +522,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           // while the pass runs: half 1 draws this step's action uniform and reset
           // words for half 0; half 0 takes sin / cos of the pole angle
           if (h == 1) {
-            const float ud = u01(draw(d.seed, k, e, 0, kTagAction, 0).x);
-            const uint4 rr = draw(d.seed, k, e, 0, kTagReset, 0);
+            const float ud = u01(draw(d.seed, k, d.env_base + e, 0, kTagAction, 0).x);
+            const uint4 rr = draw(d.seed, k, d.env_base + e, 0, kTagReset, 0);
             asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(xch + 16), "r"(rr.x),
                          "r"(rr.y), "r"(rr.z), "r"(rr.w)
                          : "memory");

@@ -513,7 +513,7 @@ __global__ void __launch_bounds__((AT + 1) * 128, 1)
         int a = 0;
         long long w_after = w;
         if (valid) {
-          const float u = u01(draw(seed, k, env, agent, kTagAction, 0).x);
+          const float u = u01(draw(seed, k, d.env_base + env, agent, kTagAction, 0).x);
           float lp;
           a = sample_cat<kNA>(lg, u, lp);
           const size_t o = rowR * S + slot;
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__((AT + 1) * 128, 1)
 #pragma unroll
             for (int c = 0; c < kNA; ++c) d.r_pout[(rowR * kNA + c) * S + slot] = lg[c];
           }
-          const uint32_t rp = draw(seed, k, env, agent, kTagPartner, 0).x;
+          const uint32_t rp = draw(seed, k, d.env_base + env, agent, kTagPartner, 0).x;
           const uint32_t p = (agent + 1u + bounded(rp, (uint32_t)(n - 1))) % (uint32_t)n;
           const long long amt = (w * (long long)a) / 400;
           w_after = w - amt;
@@ -576,7 +576,7 @@ __global__ void __launch_bounds__((AT + 1) * 128, 1)
           d.r_done[o] = (uint8_t)done;
           srew[row] = rew;
           if (done) {
-            reset_agent(seed, k, env, agent, w, f);
+            reset_agent(seed, k, d.env_base + env, agent, w, f);
             t = 0;
           } else {
             w = w2;
@@ -729,7 +729,7 @@ __global__ void __launch_bounds__((AT + 1) * 128, 1)
 #pragma unroll
             for (int c = 0; c < kNP; ++c)
               lg[c] = __uint_as_float(z[c]) + *(const float *)(sm + C::OFF_BIAS + (BO_B3P + c) * 4);
-            const float u = u01(draw(seed, k, penv, kPlannerId, kTagAction, 0).x);
+            const float u = u01(draw(seed, k, d.env_base + penv, kPlannerId, kTagAction, 0).x);
             float lp;
             const int tau = sample_cat<kNP>(lg, u, lp);
             ((int32_t *)d.r_act)[rowR * S + ps] = tau;

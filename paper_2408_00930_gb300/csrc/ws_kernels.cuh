@@ -14,6 +14,7 @@ struct Dev {
   float noise_sigma, step_clip, gamma;
   float energy_target;  // landscape: done when E(x') < energy_target (-inf: off)
   uint64_t seed;        // key of the per-step draws (set by ws_reset)
+  uint32_t env_base;    // global id of env 0 (the env word of every per-env draw)
   uint64_t *k;          // device step counter
   uint32_t *err;        // [0] error flag, [1] where
   const float *params, *params_planner;

@@ -727,7 +727,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int q = 0; q < DH / 4; ++q) {
             const int j = j0 + 4 * q;
-            const uint4 rw = draw(seed, k, e, 0, kTagAction, (uint32_t)(j >> 2));
+            const uint4 rw = draw(seed, k, d.env_base + e, 0, kTagAction, (uint32_t)(j >> 2));
             const float2 p = box_muller(rw.x, rw.y), p2 = box_muller(rw.z, rw.w);
             const float z4[4] = {p.x, p.y, p2.x, p2.y};
 #pragma unroll
@@ -760,14 +760,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (pass == 0) done = valid && (t2 >= (int)d.episode_limit || E < d.energy_target);
           if (pass == 1) {
             if (own && done) {
-              const uint4 rn = draw(seed, k, e, 0, kTagNoise, 1);
+              const uint4 rn = draw(seed, k, d.env_base + e, 0, kTagNoise, 1);
               eobs = E + sig_n * box_muller(rn.x, rn.y).x;
             }
             break;
           }
           // ---- step: observed energy, reward, done, auto-reset
           if (own) {
-            const uint4 rn = draw(seed, k, e, 0, kTagNoise, 0);
+            const uint4 rn = draw(seed, k, d.env_base + e, 0, kTagNoise, 0);
             const float eobs2 = E + sig_n * box_muller(rn.x, rn.y).x;
             if (rec) {
               const size_t o = rowR * S + e;
@@ -780,7 +780,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (done) {
 #pragma unroll
             for (int q = 0; q < DH / 4; ++q) {
-              const uint4 rr = draw(seed, k, e, 0, kTagReset, (uint32_t)((j0 + 4 * q) >> 2));
+              const uint4 rr = draw(seed, k, d.env_base + e, 0, kTagReset, (uint32_t)((j0 + 4 * q) >> 2));
               x[4 * q] = uniform(rr.x, -3.0f, 3.0f);
               x[4 * q + 1] = uniform(rr.y, -3.0f, 3.0f);
               x[4 * q + 2] = uniform(rr.z, -3.0f, 3.0f);

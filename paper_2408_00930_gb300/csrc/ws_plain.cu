@@ -76,7 +76,7 @@ __global__ void k_landscape_derive(Dev d) {
 
 // ---------------------------------------------------------------- resets
 __device__ void control_reset_env(const Dev &d, uint32_t k, uint32_t e) {
-  const uint4 r = draw(d.seed, k, e, 0, kTagReset, 0);
+  const uint4 r = draw(d.seed, k, d.env_base + e, 0, kTagReset, 0);
   d.s[0 * d.n_envs + e] = uniform(r.x, -0.05f, 0.05f);
   d.s[1 * d.n_envs + e] = uniform(r.y, -0.05f, 0.05f);
   d.s[2 * d.n_envs + e] = uniform(r.z, -0.05f, 0.05f);
@@ -85,7 +85,7 @@ __device__ void control_reset_env(const Dev &d, uint32_t k, uint32_t e) {
 
 // Acrobot: (th1, th2, w1, w2) from the four words of RESET(k, env), U(-0.1, 0.1).
 __device__ void acrobot_reset_env(const Dev &d, uint32_t k, uint32_t e) {
-  const uint4 r = draw(d.seed, k, e, 0, kTagReset, 0);
+  const uint4 r = draw(d.seed, k, d.env_base + e, 0, kTagReset, 0);
   d.s[0 * d.n_envs + e] = uniform(r.x, -0.1f, 0.1f);
   d.s[1 * d.n_envs + e] = uniform(r.y, -0.1f, 0.1f);
   d.s[2 * d.n_envs + e] = uniform(r.z, -0.1f, 0.1f);
@@ -95,11 +95,11 @@ __device__ void acrobot_reset_env(const Dev &d, uint32_t k, uint32_t e) {
 // Economy agent redraw: wealth 1e4 + (64-bit word) mod 990001, features N(0,1).
 __device__ void econ_reset_agent(const Dev &d, uint32_t k, uint32_t env, uint32_t agent,
                                  uint32_t slot) {
-  uint4 r = draw(d.seed, k, env, agent, kTagReset, 0);
+  uint4 r = draw(d.seed, k, d.env_base + env, agent, kTagReset, 0);
   const uint64_t big = ((uint64_t)r.y << 32) | (uint64_t)r.x;
   d.wealth[slot] = 10000 + (int64_t)(big % 990001ull);
   for (int j = 0; j < 4; ++j) {
-    r = draw(d.seed, k, env, agent, kTagReset, 1 + j);
+    r = draw(d.seed, k, d.env_base + env, agent, kTagReset, 1 + j);
     const float2 a = box_muller(r.x, r.y), b = box_muller(r.z, r.w);
     d.feat[(size_t)(4 * j + 0) * d.n_agent_slots + slot] = a.x;
     d.feat[(size_t)(4 * j + 1) * d.n_agent_slots + slot] = a.y;
@@ -110,7 +110,7 @@ __device__ void econ_reset_agent(const Dev &d, uint32_t k, uint32_t env, uint32_
 
 __device__ void landscape_reset_env(const Dev &d, uint32_t k, uint32_t e) {
   for (int j = 0; j < (int)d.dim; j += 4) {
-    const uint4 r = draw(d.seed, k, e, 0, kTagReset, (uint32_t)(j >> 2));
+    const uint4 r = draw(d.seed, k, d.env_base + e, 0, kTagReset, (uint32_t)(j >> 2));
     for (int i = 0; i < 4 && j + i < (int)d.dim; ++i)
       d.s[(size_t)(j + i) * d.n_envs + e] = uniform(word(r, i), -3.0f, 3.0f);
   }
@@ -282,7 +282,7 @@ __global__ void k_sample_cat(Dev d, uint32_t off, const float *logits, int n_cls
   } else if (mode == 2) {
     agent = kPlannerId;
   }
-  const float u = u01(draw(d.seed, (uint32_t)k, env, agent, kTagAction, 0).x);
+  const float u = u01(draw(d.seed, (uint32_t)k, d.env_base + env, agent, kTagAction, 0).x);
   const float *l = logits + (size_t)i * n_cls;
   float m = l[0];
   for (int c = 1; c < n_cls; ++c) m = fmaxf(m, l[c]);
@@ -321,7 +321,7 @@ __global__ void k_sample_gauss(Dev d, uint32_t off) {
   float lp = 0.f;
   const float half_log_2pi = 0.91893853320467274f;
   for (int j = 0; j < D; j += 4) {
-    const uint4 r = draw(d.seed, (uint32_t)k, e, 0, kTagAction, (uint32_t)(j >> 2));
+    const uint4 r = draw(d.seed, (uint32_t)k, d.env_base + e, 0, kTagAction, (uint32_t)(j >> 2));
     const float2 p = box_muller(r.x, r.y), q = box_muller(r.z, r.w);
     const float z4[4] = {p.x, p.y, q.x, q.y};
     for (int i = 0; i < 4 && j + i < D; ++i) {
@@ -503,7 +503,7 @@ __global__ void k_econ_transfer(Dev d, uint32_t off) {
   const uint32_t ai = i - (uint32_t)a0;
   const int64_t act = ((const int32_t *)d.r_act)[(size_t)row * d.n_slots + i];
   const int64_t w0 = d.r_wealth[(size_t)row * d.n_slots + i];
-  const uint32_t r = draw(d.seed, (uint32_t)k, env, ai, kTagPartner, 0).x;
+  const uint32_t r = draw(d.seed, (uint32_t)k, d.env_base + env, ai, kTagPartner, 0).x;
   const uint32_t p = (ai + 1u + bounded(r, (uint32_t)(n - 1))) % (uint32_t)n;
   const int64_t amt = (w0 * act) / 400;
   atomicAdd((unsigned long long *)&d.wealth[i], (unsigned long long)(-amt));
@@ -652,7 +652,7 @@ __global__ void k_landscape_step(Dev d, uint32_t off) {
   const int D = (int)d.dim;
   const float *act = (const float *)d.r_act + (size_t)row * D * d.n_slots;
   const float E2 = energy_combine(d, e);
-  const uint4 rn = draw(d.seed, (uint32_t)k, e, 0, kTagNoise, 0);
+  const uint4 rn = draw(d.seed, (uint32_t)k, d.env_base + e, 0, kTagNoise, 0);
   const float eobs2 = E2 + d.noise_sigma * box_muller(rn.x, rn.y).x;
   d.r_energy[o] = E2;
   d.r_rew[o] = d.eobs[e] - eobs2;
@@ -680,7 +680,7 @@ __global__ void k_landscape_reset_finish(Dev d, uint32_t off, int full_reset) {
   if (e >= d.n_envs || !d.needs_energy[e]) return;
   const uint32_t kk = full_reset ? kStepInit : (uint32_t)step_k(d, off);
   const float E = energy_combine(d, e);
-  const uint4 rn = draw(d.seed, kk, e, 0, kTagNoise, 1);
+  const uint4 rn = draw(d.seed, kk, d.env_base + e, 0, kTagNoise, 1);
   d.eobs[e] = E + d.noise_sigma * box_muller(rn.x, rn.y).x;
   d.needs_energy[e] = 0;
 }

@@ -76,6 +76,7 @@ ws_status validate(const ws_config *cfg) {
   if (cfg->env < WS_ENV_CONTROL || cfg->env > WS_ENV_ACROBOT) return WS_ERR_INVALID;
   if (cfg->path < WS_PATH_PLAIN_FP32 || cfg->path > WS_PATH_BATCHED_BF16) return WS_ERR_INVALID;
   if (cfg->n_envs < 1 || cfg->n_envs > (1u << 26)) return WS_ERR_INVALID;
+  if ((uint64_t)cfg->env_base + cfg->n_envs > 0xFFFFFFFFull) return WS_ERR_INVALID;
   if (cfg->ring_steps < 1 || cfg->episode_limit < 1) return WS_ERR_INVALID;
   if (cfg->hidden0 < 1 || cfg->hidden0 > 4096 || cfg->hidden1 < 1 || cfg->hidden1 > 4096)
     return WS_ERR_INVALID;
@@ -107,7 +108,7 @@ void agent_counts(const ws_config *cfg, std::vector<int32_t> &out) {
     if (cfg->agents_per_env) {
       out[e] = cfg->agents_per_env[e];
     } else {
-      const uint4 r = draw(cfg->param_seed, 0, e, 0, kTagEconInit, 0);
+      const uint4 r = draw(cfg->param_seed, 0, cfg->env_base + e, 0, kTagEconInit, 0);
       out[e] = 8 + (int32_t)bounded(r.x, 249u);
     }
   }
@@ -376,6 +377,7 @@ void make_dev(ws_ctx *c) {
   d.step_clip = cfg.step_clip;
   d.gamma = cfg.gamma;
   d.seed = c->seed;
+  d.env_base = cfg.env_base;
   d.k = (uint64_t *)(S + L.k_off);
   d.err = (uint32_t *)(S + L.err_off);
   d.params = (const float *)(S + L.params_off);

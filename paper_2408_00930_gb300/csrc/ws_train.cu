@@ -75,7 +75,7 @@ __global__ void k_adv_store(Dev d, uint32_t n, size_t q0, uint32_t rows, uint32_
 // env e), as the sampler drew them: one draw per four coordinates.
 __device__ __forceinline__ void action_normals4(const Dev &d, uint32_t k, uint32_t e, int j,
                                                 float (&z)[4]) {
-  const uint4 r = draw(d.seed, k, e, 0, kTagAction, (uint32_t)(j >> 2));
+  const uint4 r = draw(d.seed, k, d.env_base + e, 0, kTagAction, (uint32_t)(j >> 2));
   const float2 p = box_muller(r.x, r.y), p2 = box_muller(r.z, r.w);
   z[0] = p.x;
   z[1] = p.y;

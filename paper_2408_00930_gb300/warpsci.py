@@ -49,7 +49,8 @@ class ws_config(C.Structure):
                 ("hidden0", C.c_uint32), ("hidden1", C.c_uint32), ("dim", C.c_uint32),
                 ("n_gauss", C.c_uint32), ("noise_sigma", C.c_float), ("step_clip", C.c_float),
                 ("gamma", C.c_float), ("flags", C.c_uint32), ("param_seed", C.c_uint64),
-                ("agents_per_env", C.POINTER(C.c_int32)), ("energy_target", C.c_float)]
+                ("agents_per_env", C.POINTER(C.c_int32)), ("energy_target", C.c_float),
+                ("env_base", C.c_uint32)]
 
 
 class ws_launch(C.Structure):
@@ -241,14 +242,14 @@ def ws_policy_forward_noalloc(obs_ptr, n_rows, params_ptr, in_dim, hidden0, hidd
 # --- convenience owner --------------------------------------------------------
 def make_config(env, path, n_envs, ring_steps, episode_limit, hidden0, hidden1, *,
                 chunk_steps=0, dim=0, n_gauss=0, noise_sigma=0.05, step_clip=0.1, gamma=0.99,
-                param_seed=1, agents_per_env=None, flags=0, energy_target=None):
+                param_seed=1, agents_per_env=None, flags=0, energy_target=None, env_base=0):
     cfg = ws_config()
     cfg.struct_size = C.sizeof(ws_config)
     cfg.env, cfg.path, cfg.n_envs = env, path, n_envs
     cfg.ring_steps, cfg.episode_limit, cfg.chunk_steps = ring_steps, episode_limit, chunk_steps
     cfg.hidden0, cfg.hidden1, cfg.dim, cfg.n_gauss = hidden0, hidden1, dim, n_gauss
     cfg.noise_sigma, cfg.step_clip, cfg.gamma = noise_sigma, step_clip, gamma
-    cfg.flags, cfg.param_seed = flags, param_seed
+    cfg.flags, cfg.param_seed, cfg.env_base = flags, param_seed, env_base
     if energy_target is not None:  # landscape: done when E(x') < energy_target
         cfg.flags |= WS_FLAG_ENERGY_TARGET
         cfg.energy_target = energy_target
