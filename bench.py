@@ -446,15 +446,16 @@ def run_a2c(wl, local):
                                "ws_ppo_update: as the A2C update with k_ppo_head"}}
 
 
-def run_serving(args, world, rank, local):
+def serve_mix(args, n_requests, rank, local):
     """Serving mix: Poisson arrivals (200 req/s) of requests across the three env
-    types, admitted under a 150 GB budget, delivered in chunks of 50 steps."""
+    types, admitted under a 150 GB budget, delivered in chunks of 50 steps; once
+    on the BF16 paths (served) and once on the plain FP32 path."""
     import torch
     from paper_2408_00930_gb300 import serving_mix
     from paper_2408_00930_gb300 import warpsci as W
     torch.cuda.set_device(local)
     budget = int(args.serve_budget_gb * (1 << 30))
-    stream = list(serving_mix.request_stream(1234 + rank, args.serve_requests, rate=200.0))
+    stream = list(serving_mix.request_stream(1234 + rank, n_requests, rate=200.0))
     out = {}
     for label, bf16 in (("served", True), ("plain_fp32", False)):
         if not bf16 and args.no_plain:
@@ -494,6 +495,11 @@ def run_serving(args, world, rank, local):
                       "requests": len(stream), "rejected": rejected, "failed": s_["failed"],
                       "completed": s_["completed"], "chunks": s_["chunks"],
                       "peak_bytes": s_["peak_bytes"], "agent_steps": s_["agent_steps"]}
+    return out
+
+
+def run_serving(args, world, rank, local):
+    out = serve_mix(args, args.serve_requests, rank, local)
     if rank == 0:
         sv = out["served"]
         print(json.dumps({
@@ -549,6 +555,9 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-timeout-s", type=float, default=600.0)
+    ap.add_argument("--serve-sub-requests", type=int, default=12,
+                    help="requests of the serving mix timed after the main workload and "
+                         "reported in its line's serving object (0: skip)")
     args = ap.parse_args()
     if args.workload == "serving":
         world, rank, local = dist_init()
@@ -586,6 +595,13 @@ def main():
                "sample": sample, "single_core_value": single}
     path, value, main_res, plain, e2e = run_gpu(args, wl, world, rank, local)
     a2c = run_a2c(wl, local) if args.a2c and wl["env"] in (0, 3) and rank == 0 else None
+    serving = None
+    if args.serve_sub_requests > 0 and world == 1:
+        sv = serve_mix(args, args.serve_sub_requests, rank, local)
+        serving = {"workload": f"{args.serve_sub_requests} requests of the serving mix (Poisson "
+                               "200 req/s across control / economy / landscape, 256-65,536 envs, "
+                               "horizons 100-1,000, chunks of 50, "
+                               f"{args.serve_budget_gb:g} GB admission budget)", **sv}
     if rank != 0:
         return
     from paper_2408_00930_gb300 import warpsci as W
@@ -747,6 +763,7 @@ def main():
         "gpu_launches": per_launch * args.steps,
         "clocks": main_res["clocks"],
         "a2c_update": a2c,
+        "serving": serving,
     }
     print(json.dumps(out), flush=True)
 

@@ -118,14 +118,15 @@ def _run(counts, T, chunk, limit, seed, reset_seed):
     return out, init, fin, par
 
 
-def _replay_records(out, t_init, counts, envs, par, T, limit, seed):
+def _replay_records(out, t_init, counts, envs, par, T, limit, seed, k0=0):
     """Teacher-forced one-step replays along the kernel's own trajectory: the
     ring holds every step's pre-step state (features as the observation, wealth),
     so for each step t the oracle steps the listed envs from the recorded state
     and must reproduce the recorded draws, rewards and dones and the state
     recorded at t + 1.  A draw may differ from the oracle's only inside the tie
     band (its CDF margin below TIE); an env with such a draw is skipped at that
-    step only.  Returns the number of env-steps compared in full."""
+    step only.  The records start at step k0.  Returns the number of env-steps
+    compared in full."""
     off = np.r_[0, np.cumsum(counts)]
     sa = int(off[-1])
     na = counts[envs]
@@ -138,7 +139,7 @@ def _replay_records(out, t_init, counts, envs, par, T, limit, seed):
         w0 = out["wealth"][t][sl_a]
         f0 = out["obs"][t][:, sl_a].T.astype(np.float64)
         o = oracle.econ_rollout(par[:NA], par[NA:], seed=seed, env_ids=envs, n_agents=na,
-                                n_steps=1, episode_limit=limit, k0=t, wealth0=w0, feat0=f0,
+                                n_steps=1, episode_limit=limit, k0=k0 + t, wealth0=w0, feat0=f0,
                                 t0=t_env, bf16_layers=ALL_BF16)
         for i, e in enumerate(envs):
             g_a, o_a = np.arange(off[e], off[e + 1]), np.arange(ooff[i], ooff[i + 1])

@@ -124,33 +124,37 @@ def test_fused_chunks_tile_ctas_determinism(torch):
     assert a[W.WS_F_DONE].sum(1).tolist() == [n if t in (11, 23) else 0 for t in range(T)]
 
 
-def _teacher_forced(rec, init, par, cwa, envs, T, limit, rs):
+def _teacher_forced(rec, init, par, cwa, envs, T, limit, rs, k0=0):
     """Each step of the listed envs from the recorded pre-step state: the
     oracle's BF16-operand policy and head give the action, the FP64 energy at the
     kernel's own x + dx bounds its energy, and the recorded next state is x + dx
-    or the Philox reset draw."""
+    or the Philox reset draw.  The records start at step k0 from the state
+    ``init`` (x, observed energy, episode counters)."""
     c, w, a = cwa
     x_t = rec[W.WS_F_OBS]                      # [T][D][n]
     eobs = init[1].copy()
-    for t in range(T):
+    t_ep = np.asarray(init[2], np.int64).copy()
+    for s in range(T):
+        t = k0 + s
         for e in envs:
-            x = x_t[t][:, e].astype(np.float64)
+            x = x_t[s][:, e].astype(np.float64)
             out = oracle.mlp_forward(PW, par, x, bf16_layers=ALL_BF16)
             z = oracle.landscape_action_normals(rs, t, e, D)
             dx_o, lp_o = oracle.gaussian_action(out, z, 0.1)
-            dx = rec[W.WS_F_ACTION][t][:, e].astype(np.float64)
+            dx = rec[W.WS_F_ACTION][s][:, e].astype(np.float64)
             assert np.abs(dx - dx_o).max() <= 2e-2, (t, e)       # BF16 logits through the head
-            assert abs(rec[W.WS_F_LOGP][t][e] - lp_o) <= 0.5, (t, e)
-            x2 = (x_t[t][:, e] + rec[W.WS_F_ACTION][t][:, e]).astype(np.float32)
-            E = rec[W.WS_F_ENERGY][t][e]
+            assert abs(rec[W.WS_F_LOGP][s][e] - lp_o) <= 0.5, (t, e)
+            x2 = (x_t[s][:, e] + rec[W.WS_F_ACTION][s][:, e]).astype(np.float32)
+            E = rec[W.WS_F_ENERGY][s][e]
             ok, info = energy_close(E, c, w, a, x2)
             assert ok, (t, e, info)
             eobs2 = E + 0.05 * oracle.landscape_noise(rs, t, e, 0)
-            assert abs(rec[W.WS_F_REWARD][t][e] - (eobs[e] - eobs2)) <= 2e-5 * max(1.0, abs(eobs2))
-            done = (t + 1) % limit == 0
-            assert rec[W.WS_F_DONE][t][e] == done
-            if t + 1 < T:
-                nxt = x_t[t + 1][:, e]
+            assert abs(rec[W.WS_F_REWARD][s][e] - (eobs[e] - eobs2)) <= 2e-5 * max(1.0, abs(eobs2))
+            done = t_ep[e] + 1 >= limit
+            t_ep[e] = 0 if done else t_ep[e] + 1
+            assert rec[W.WS_F_DONE][s][e] == done
+            if s + 1 < T:
+                nxt = x_t[s + 1][:, e]
                 if done:
                     xr = oracle.landscape_reset_draw(rs, t, e, D)
                     np.testing.assert_array_equal(nxt, xr.astype(np.float32))

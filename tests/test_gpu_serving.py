@@ -17,7 +17,17 @@ def torch():
     return need_gpu()
 
 
-def req(env, n, horizon, seed, path=None, flags=0):
+def req(env, n, horizon, seed, path=None, flags=0, fused=False):
+    """A request of the env's test shape; fused=True asks for the configured
+    shape that the BF16 path runs on its fused persistent kernel (economy
+    16-128-128-20 with drawn U{8..256} agents, landscape D=24, M=4,096,
+    24-256-256-48)."""
+    if fused and env == W.WS_ENV_ECONOMY:
+        return W.make_request(env, W.WS_PATH_BATCHED_BF16, n, horizon, 50, 540, 128, 128,
+                              seed=seed, flags=flags)
+    if fused and env == W.WS_ENV_LANDSCAPE:
+        return W.make_request(env, W.WS_PATH_BATCHED_BF16, n, horizon, 50, 1000, 256, 256,
+                              dim=24, n_gauss=4096, seed=seed, flags=flags)
     if env == W.WS_ENV_CONTROL:
         return W.make_request(env, path if path is not None else W.WS_PATH_BATCHED_BF16, n, horizon,
                               50, 200, 256, 256, seed=seed, flags=flags)
@@ -57,15 +67,20 @@ def slots_of(q):
 
 
 def test_results_identical_alone_and_in_mix(torch):
-    specs = [(W.WS_ENV_CONTROL, 5000, 150, 11), (W.WS_ENV_ECONOMY, 40, 100, 12),
-             (W.WS_ENV_LANDSCAPE, 700, 100, 13), (W.WS_ENV_CONTROL, 70000, 200, 14),
-             (W.WS_ENV_ACROBOT, 3000, 100, 15)]
+    """Every request's records are the same served alone and in a concurrent
+    mix of all env types, the configured BF16 shapes on their fused kernels
+    included (the economy's work queue with drawn agent counts, the landscape's
+    CTA-pair clusters over 4,096 Gaussians, the control and acrobot kernels)."""
+    specs = [(W.WS_ENV_CONTROL, 5000, 150, 11, False), (W.WS_ENV_ECONOMY, 40, 100, 12, False),
+             (W.WS_ENV_LANDSCAPE, 700, 100, 13, False), (W.WS_ENV_CONTROL, 70000, 200, 14, False),
+             (W.WS_ENV_ACROBOT, 3000, 100, 15, False), (W.WS_ENV_ECONOMY, 300, 150, 16, True),
+             (W.WS_ENV_LANDSCAPE, 1000, 100, 17, True)]
     dims = {W.WS_ENV_CONTROL: (4, 1), W.WS_ENV_ECONOMY: (16, 1), W.WS_ENV_LANDSCAPE: (24, 24),
             W.WS_ENV_ACROBOT: (6, 1)}
     alone = []
     srv = W.Server(8 * GB)
-    for env, n, h, seed in specs:
-        q, keep = req(env, n, h, seed)
+    for env, n, h, seed, fz in specs:
+        q, keep = req(env, n, h, seed, fused=fz)
         st, rid = srv.submit(q)
         assert st == W.WS_OK
         alone.append(collect(srv, rid, slots_of(q), *dims[env], h // 50))
@@ -74,17 +89,18 @@ def test_results_identical_alone_and_in_mix(torch):
     # all at once: their chunks run concurrently on separate streams
     srv = W.Server(8 * GB)
     ids = []
-    for env, n, h, seed in specs:
-        q, keep = req(env, n, h, seed)
+    for env, n, h, seed, fz in specs:
+        q, keep = req(env, n, h, seed, fused=fz)
         st, rid = srv.submit(q)
         assert st == W.WS_OK
         ids.append((rid, q))
     mixed = [collect(srv, rid, slots_of(q), *dims[q.env], q.horizon // 50) for rid, q in ids]
     stats = srv.stats()
     srv.close()
-    for a, b in zip(alone, mixed):
-        assert a == b
-    assert stats["completed"] == len(specs) and stats["chunks"] == sum(h // 50 for _, _, h, _ in specs)
+    for (env, n, h, seed, fz), a, b in zip(specs, alone, mixed):
+        assert a == b, (env, n, fz)
+    assert stats["completed"] == len(specs)
+    assert stats["chunks"] == sum(h // 50 for _, _, h, _, _ in specs)
     assert stats["p99_ms"] >= stats["p50_ms"] > 0
 
 

@@ -5,13 +5,16 @@ hosts whose allocator forbids foreign allocations, fixed-memory embedded
 runtimes) use this entry point: it keeps its hidden activations in a
 library-owned static device array.  Its output must equal the logits the
 regular plain-FP32 step computes with its own scratch (ws_step, then ws_fetch
-of LOGITS), call after call, even though every call reuses the same array.
+of LOGITS), call after call, even though every call reuses the same array:
+bit for bit (both run the same FP32 layer kernel in the same summation order),
+and within the FP32 tolerance of the oracle's FP64 forward pass.
 This file is collected last so that a run stopping at the first failure has
 already run every other test.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_2408_00930_gb300 import inputs
 from paper_2408_00930_gb300 import warpsci as W
 from tests import ws_helpers as H
@@ -55,6 +58,9 @@ def test_noalloc_forward_matches_step_logits_twice():
         err = np.abs(got - ref) / np.maximum(np.abs(ref), 1.0)
         assert np.all(np.isfinite(got))
         assert err.max() <= TOL_F32, err.max()
+        assert np.array_equal(got, ref)
+        o = oracle.mlp_forward([4, h, h, 2], params, s0.astype(np.float32).astype(np.float64))
+        assert H.rel_err_rows(got, o).max() <= TOL_F32
 
 
 def test_noalloc_rejects_requests_beyond_the_static_array():
