@@ -326,7 +326,13 @@ def run_gpu(args, wl, world, rank, local):
                    launch=launch)
         return res
 
+    sfu_rates = None
+    if path == W.WS_PATH_BATCHED_BF16:
+        sfu_rates = probe_rates(local, ops=("tanh.approx.f32", "ex2.approx.ftz.f32",
+                                            "sin.approx.ftz.f32", "lg2.approx.ftz.f32",
+                                            "rsqrt.approx.ftz.f32"))
     main = one_path(path, args.steps, args.warmup, True)
+    main["sfu_rates"] = sfu_rates
     r = main["rollout"]
     n_steps_total = args.steps
     value = job_throughput(main["agent_steps"], n_steps_total, world, main["total_ms"])
@@ -498,6 +504,40 @@ def serve_mix(args, n_requests, rank, local):
     return out
 
 
+def probe_rates(local, iters=2048, ops=None):
+    """Results per clock per SM of the probed operations (ws_probe_rate), each
+    the best of three launches."""
+    import torch
+    from paper_2408_00930_gb300 import warpsci as W
+    dev = torch.device("cuda", local)
+    n_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    buf = torch.empty(n_sms * 4 * 16, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for op, name in enumerate(W.PROBE_OPS):
+        if ops is not None and name not in ops:
+            continue
+        best = 0.0
+        for _ in range(3):
+            st, v = W.ws_probe_rate(op, iters, buf.data_ptr(), buf.numel(), stream.cuda_stream)
+            assert st == W.WS_OK, st
+            best = max(best, v)
+        out[name] = best
+    return out
+
+
+def run_peaks(args, local):
+    """Measured rates of the SFU operations and the FMA pipe that the rooflines
+    divide by (results per SM clock; x SMs x clock = the chip's rate)."""
+    import torch
+    torch.cuda.set_device(local)
+    rates = probe_rates(local)
+    n_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    print(json.dumps({"peaks": "results per clock per SM (4 blocks x 256 threads x 8 chains per SM, "
+                               "clock64 spans, best of 3)", "n_sms": n_sms,
+                      "gpu": torch.cuda.get_device_name(local), "rates": rates}), flush=True)
+
+
 def run_serving(args, world, rank, local):
     out = serve_mix(args, args.serve_requests, rank, local)
     if rank == 0:
@@ -555,10 +595,16 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-timeout-s", type=float, default=600.0)
+    ap.add_argument("--peaks", action="store_true",
+                    help="measure the SFU and FMA-pipe rates (ws_probe_rate) and exit")
     ap.add_argument("--serve-sub-requests", type=int, default=12,
                     help="requests of the serving mix timed after the main workload and "
                          "reported in its line's serving object (0: skip)")
     args = ap.parse_args()
+    if args.peaks:
+        _, _, local = dist_init()
+        run_peaks(args, local)
+        return
     if args.workload == "serving":
         world, rank, local = dist_init()
         run_serving(args, world, rank, local)
@@ -618,45 +664,65 @@ def main():
               f"{peak_src} bf16 sustained / 4 (fp32 SIMT)"}
     tensor["frac"] = tensor["achieved"] / tensor["peak"]
     if bf16:
-        # The fused kernels are bound by the SFU (tanh, exp2): an SM retires 16
-        # SFU results per clock (measured 15.2 for tanh.approx in any of f32 /
-        # bf16x2 / f16x2 form).  SFU results per agent-step, counted from the
-        # kernels' arithmetic:
-        #   control    H0 + H1 tanh (+ one exp for the two-way softmax)
-        #   acrobot    H0 + H1 tanh, 3 exp and 1 log, and 22 sin / cos (the
+        # The fused kernels are bound by the SFU.  Its rates differ per
+        # operation (ws_probe_rate, measured here before the timed region:
+        # tanh, sin, lg2 ~16 results / clock / SM; ex2 ~32), so the work is
+        # counted in tanh-equivalents: each operation weighted by
+        # rate(tanh) / rate(op).  SFU operations per agent-step, from the
+        # kernels' arithmetic (expf / logf each take one ex2 / lg2):
+        #   control    H0 + H1 tanh; 2 ex2 and 1 lg2 (the two-way softmax)
+        #   acrobot    H0 + H1 tanh; 3 ex2, 1 lg2; 22 sin / cos (the
         #              observation's two pairs, four RK4 stages of one pair and
         #              two sines, the terminal height's two cosines)
-        #   economy    agent: H0 + H1 tanh, 20 exp, 1 log; planner: H0 + H1
-        #              tanh, 10 exp
-        #   landscape  H0 + H1 tanh, M exp2 (one per Gaussian), D exp (sigma),
-        #              2 D for the Box-Muller normals (log, sqrt, sin, cos per
-        #              pair) and 4 for the noise draw
+        #   economy    agent: H0 + H1 tanh, 20 ex2, 2 lg2 (log-probability and
+        #              the wealth feature); planner: H0 + H1 tanh, 10 ex2, 1 lg2
+        #   landscape  H0 + H1 tanh; M ex2 (one per Gaussian) + D ex2 (sigma);
+        #              per coordinate half a Box-Muller pair (lg2, rsqrt, sin,
+        #              cos) and one pair for the noise draw
         import torch
         n_sms = torch.cuda.get_device_properties(local).multi_processor_count
         clk = main_res["clocks"] or {}
         sm_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
         n_slots = main_res["agent_steps"] / wl["horizon"]
         H = sum(wl["h"])
+        rates = main_res.get("sfu_rates") or {}
+        r_t = rates.get("tanh.approx.f32", 16.0)
+        w = {"tanh": 1.0, "ex2": r_t / rates.get("ex2.approx.ftz.f32", 16.0),
+             "sin": r_t / rates.get("sin.approx.ftz.f32", 16.0),
+             "lg2": r_t / rates.get("lg2.approx.ftz.f32", 16.0),
+             "rsqrt": r_t / rates.get("rsqrt.approx.ftz.f32", 16.0)}
+
+        def teq(**ops):
+            return sum(n * w[k] for k, n in ops.items())
         if wl["env"] == 0:
-            per_step, op, kern = n_slots * (H + 1), "tanh (and exp) on the SFU", "ws_control_tc"
+            per_step = n_slots * teq(tanh=H, ex2=2, lg2=1)
+            op, kern = "tanh (and the softmax's ex2, lg2) on the SFU", "ws_control_tc"
         elif wl["env"] == 3:
-            per_step, op, kern = n_slots * (H + 26), "tanh, exp, log, sin, cos on the SFU", \
-                "ws_control_tc (acrobot)"
+            per_step = n_slots * teq(tanh=H, ex2=3, lg2=1, sin=22)
+            op, kern = "tanh, ex2, lg2, sin, cos on the SFU", "ws_control_tc (acrobot)"
         elif wl["env"] == 1:
             n_pl = wl["n_envs"]
-            per_step = (n_slots - n_pl) * (H + 21) + n_pl * (H + 10)
-            op, kern = "tanh and exp on the SFU", "ws_econ_tc (work queue of env groups)"
+            per_step = ((n_slots - n_pl) * teq(tanh=H, ex2=20, lg2=2)
+                        + n_pl * teq(tanh=H, ex2=10, lg2=1))
+            op, kern = "tanh, ex2, lg2 on the SFU", "ws_econ_tc (work queue of env groups)"
         else:
-            per_step = n_slots * (H + wl["n_gauss"] + 3 * wl["dim"] + 4)
-            op, kern = "exp2 (energy) and tanh on the SFU", "ws_land_tc (CTA-pair clusters)"
+            D = wl["dim"]
+            per_step = n_slots * teq(tanh=H, ex2=wl["n_gauss"] + D, lg2=D / 2 + 1,
+                                     rsqrt=D / 2 + 1, sin=D + 2)
+            op, kern = "ex2 (energy), tanh and the normals' lg2 / rsqrt / sin / cos on the SFU", \
+                "ws_land_tc (CTA-pair clusters)"
         sfu_launch = per_step * launch_steps
+        src = ("measured by ws_probe_rate before the timed region" if rates else
+               "nominal 16 / clock / SM for every SFU operation (probe unavailable)")
         roofline = {"bound": "alu", "op": op,
                     "achieved": sfu_launch / (launch_ms * 1e-3) / 1e12,
-                    "peak": 16 * n_sms * sm_mhz * 1e6 / 1e12, "unit": "Top/s", "frac": None,
+                    "peak": r_t * n_sms * sm_mhz * 1e6 / 1e12,
+                    "unit": "T tanh-equivalent SFU results/s", "frac": None,
                     "traffic": None,
                     "kernel": kern + " (fused persistent, one launch per 50-step chunk)",
-                    "peak_source": f"16 SFU results / clock / SM x {n_sms} SMs x {sm_mhz:.0f} MHz "
-                                   "(median sampled SM clock)",
+                    "peak_source": f"tanh.approx {r_t:.2f} results / clock / SM x {n_sms} SMs x "
+                                   f"{sm_mhz:.0f} MHz (median sampled SM clock); rates {src}",
+                    "sfu_rates_per_clk_per_sm": rates or None,
                     "tensor": {k: tensor[k] for k in ("achieved", "peak", "unit", "frac",
                                                       "peak_source")}}
         roofline["frac"] = roofline["achieved"] / roofline["peak"]
@@ -699,12 +765,13 @@ def main():
         pairs = wl["n_envs"] * min(CHUNK, wl["horizon"]) * wl["n_gauss"]
         if bf16:
             # k_force_tc: exponents and the force sums on tcgen05; the epilogue's
-            # one ex2 per (row, Gaussian) pair on the SFU (16 / clock / SM) binds
+            # one ex2 per (row, Gaussian) pair on the SFU (measured rate) binds
+            r_e = (main_res.get("sfu_rates") or {}).get("ex2.approx.ftz.f32", 16.0)
             force_roofline = {"bound": "alu", "kernel": "k_force_tc (ws_forces, 50 steps)",
                               "op": "ex2 on the SFU (one per env-Gaussian pair)",
                               "achieved": pairs / (f_ms * 1e-3) / 1e12,
-                              "peak": 16 * n_sms * clk * 1e6 / 1e12, "unit": "Top/s"}
-            src = f"16 SFU results / clock / SM x {n_sms} SMs x {clk:.0f} MHz"
+                              "peak": r_e * n_sms * clk * 1e6 / 1e12, "unit": "Top/s"}
+            src = f"ex2.approx {r_e:.2f} results / clock / SM x {n_sms} SMs x {clk:.0f} MHz"
         else:
             # k_force_f32 (FP32 SIMT, direct difference form): per pair D
             # subtractions, D FMAs for |y - c|^2 and D FMAs for the force sum on

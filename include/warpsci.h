@@ -351,6 +351,14 @@ typedef struct {
                               multiple of 32                                        */
   uint32_t tile_ctas;      /* fused landscape kernel: CTAs per 128-env tile, 1 or 2 (a
                               cluster whose CTAs split the Gaussians)               */
+  uint32_t wait_ns;        /* limit of every device wait of the fused control,
+                              acrobot, economy and landscape kernels (an MMA's
+                              completion, the SFU token, a block load, the cluster
+                              partner), in ns; 0 = 2 s.  A wait that runs out makes
+                              the kernel drain its own MMAs and copies, free its
+                              tensor memory and leave, and ws_sync reports a
+                              sticky WS_ERR_TIMEOUT naming the wait's site.  For
+                              tests of that path; results do not depend on it    */
 } ws_launch;
 
 /* The context's current launch configuration. */
@@ -462,6 +470,35 @@ void ws_server_destroy(ws_server *s);
 ws_status ws_policy_forward_noalloc(const float *obs, uint32_t n_rows, const float *params,
                                     uint32_t in_dim, uint32_t hidden0, uint32_t hidden1,
                                     uint32_t out_dim, float *out, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Throughput probes (the paper has no counterpart: these measure the peak
+ * rates the roofline fractions of the fused kernels divide by).  One launch of
+ * a probe kernel on the current device: 4 blocks of 256 threads per SM, each
+ * thread running 8 independent chains of the operation for `iters` rounds;
+ * *per_clk_per_sm = results per SM clock (packed forms count two results per
+ * lane), from clock64 spans.  dev_buf: caller-owned device memory of at least
+ * 16 bytes per block (4 x SMs blocks).  Synchronous on cuda_stream.
+ * WS_ERR_INVALID for an unknown op or iters == 0, WS_ERR_NOMEM for a small
+ * buffer.
+ * ------------------------------------------------------------------------ */
+typedef enum {
+  WS_PROBE_TANH_F32 = 0,     /* tanh.approx.f32                               */
+  WS_PROBE_TANH_BF16X2 = 1,  /* tanh.approx.bf16x2 (two results)              */
+  WS_PROBE_EX2_F32 = 2,      /* ex2.approx.ftz.f32                            */
+  WS_PROBE_EX2_BF16X2 = 3,   /* ex2.approx.ftz.bf16x2 (two results)           */
+  WS_PROBE_EX2_F16X2 = 4,    /* ex2.approx.f16x2 (two results)                */
+  WS_PROBE_RCP_F32 = 5,      /* rcp.approx.ftz.f32 (with one FP32 add)        */
+  WS_PROBE_SIN_F32 = 6,      /* sin.approx.ftz.f32                            */
+  WS_PROBE_FMA_F32 = 7,      /* fma.rn.f32                                    */
+  WS_PROBE_FMA_F32X2 = 8,    /* fma.rn.f32x2 (two results)                    */
+  WS_PROBE_LG2_F32 = 9,      /* lg2.approx.ftz.f32 (with one FP32 FMA)        */
+  WS_PROBE_RSQRT_F32 = 10,   /* rsqrt.approx.ftz.f32 (with one FP32 add)      */
+  WS_PROBE_COUNT = 11
+} ws_probe_op;
+
+ws_status ws_probe_rate(int op, uint32_t iters, void *dev_buf, size_t buf_bytes,
+                        double *per_clk_per_sm, void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -46,7 +46,6 @@ constexpr int kTile = 128;
 constexpr int kGroups = 2;
 constexpr int kGroupThreads = 2 * kTile;
 constexpr int kThreads = kGroups * kGroupThreads;
-constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s, far above any MMA completion time
 constexpr uint32_t kTmemCols = 512;
 
 // The two envs: observation width, actions, layer-1 K.
@@ -408,6 +407,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   bool wfail = false;
   uint32_t fsite = 0;
   const uint64_t k0 = d.k[0];
+  const uint64_t wlim = d.wait_ns;
   const uint32_t R = d.ring_steps;
   const uint32_t row0 = (uint32_t)(k0 % R);
   const uint32_t N = d.n_envs, S = d.n_slots;
@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                        q != 0);
         tc::mma_commit(bar_l1);
       }
-      if (!tc::mbar_wait(bar_l1, ph_l1, kWaitNs) && !wfail) { wfail = true; fsite = 1; }
+      if (!tc::mbar_wait(bar_l1, ph_l1, wlim) && !wfail) { wfail = true; fsite = 1; }
       ph_l1 ^= 1u;
       tc::fence_after_sync();
       // ---- act 1: h1 block kb -> TMEM columns A_COL + 32 kb.  With H0 = 256, z1
@@ -533,10 +533,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             cos_th = cosf(th);
           }
         }
-        if (!tc::mbar_wait(bar_l2, ph_l2, kWaitNs) && !wfail) { wfail = true; fsite = 2 + (uint32_t)p; }
+        if (!tc::mbar_wait(bar_l2, ph_l2, wlim) && !wfail) { wfail = true; fsite = 2 + (uint32_t)p; }
         ph_l2 ^= 1u;
         tc::fence_after_sync();
-        tok_take(tok, kWaitNs);
+        tok_take(tok, wlim);
         if (h < C::KBP)
           layer3_block<E::NA>(tmem + lane + (uint32_t)(h * 64),
                               w3s + (uint32_t)((p * C::NPW + h * 64) / 2 * C::W3P), acc0, acc1,
@@ -663,7 +663,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (!ok && issuer) {
     // let any MMA still in flight finish before the columns are released
     tc::mma_commit(bar_drain);
-    tc::mbar_wait(bar_drain, 0, kWaitNs);
+    tc::mbar_wait(bar_drain, 0, tc::kDrainNs);
     atomicExch(d.err, 1u);
     atomicExch(d.err + 1, 100u + fail_site);
   }

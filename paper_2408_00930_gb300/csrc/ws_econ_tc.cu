@@ -44,7 +44,6 @@ constexpr int kH = 128;                 // hidden width of both policies
 constexpr int kNA = 20, kNAp = 32;      // agent classes, padded layer-3 N
 constexpr int kNP = 10, kNPp = 16;      // planner classes, padded layer-3 N
 constexpr int kMaxEnvs = 64;            // envs per work item (planner MMA N <= 64)
-constexpr uint64_t kWaitNs = 2000000000ull;
 
 // Packed global image (the kernel copies it verbatim into shared memory):
 //   W2A  agent W2^T, B operand, SW128 K-major [128 n][128 k]
@@ -450,7 +449,7 @@ __global__ void __launch_bounds__((AT + 1) * 128, 1)
             tc::mma_bf16(tcol, da1, db1, id12, false);
             tc::mma_commit(bar);
           }
-          if (!tc::mbar_wait(bar, ph, kWaitNs) && !wfail) { wfail = true; fsite = 1; }
+          if (!tc::mbar_wait(bar, ph, d.wait_ns) && !wfail) { wfail = true; fsite = 1; }
           ph ^= 1u;
           tc::fence_after_sync();
 #pragma unroll 1
@@ -489,7 +488,7 @@ __global__ void __launch_bounds__((AT + 1) * 128, 1)
               }
               tc::mma_commit(bar);
             }
-            if (!tc::mbar_wait(bar, ph, kWaitNs) && !wfail) { wfail = true; fsite = 2 + (uint32_t)l; }
+            if (!tc::mbar_wait(bar, ph, d.wait_ns) && !wfail) { wfail = true; fsite = 2 + (uint32_t)l; }
             ph ^= 1u;
             tc::fence_after_sync();
           }
@@ -669,7 +668,7 @@ __global__ void __launch_bounds__((AT + 1) * 128, 1)
           tc::mma_bf16(tcol, dw1, dpo, idn, false);
           tc::mma_commit(bar);
         }
-        if (!tc::mbar_wait(bar, ph, kWaitNs) && !wfail) { wfail = true; fsite = 5; }
+        if (!tc::mbar_wait(bar, ph, d.wait_ns) && !wfail) { wfail = true; fsite = 5; }
         ph ^= 1u;
         tc::fence_after_sync();
 #pragma unroll 1
@@ -716,7 +715,7 @@ __global__ void __launch_bounds__((AT + 1) * 128, 1)
             }
             tc::mma_commit(bar);
           }
-          if (!tc::mbar_wait(bar, ph, kWaitNs) && !wfail) { wfail = true; fsite = 6 + (uint32_t)l; }
+          if (!tc::mbar_wait(bar, ph, d.wait_ns) && !wfail) { wfail = true; fsite = 6 + (uint32_t)l; }
           ph ^= 1u;
           tc::fence_after_sync();
         }
@@ -762,7 +761,7 @@ __global__ void __launch_bounds__((AT + 1) * 128, 1)
     if (r == 0 && (planner || tid < C::ROWS)) {
       // let any MMA still in flight finish before the columns are released
       tc::mma_commit(bars + AT + 1);
-      tc::mbar_wait(bars + AT + 1, 0, kWaitNs);
+      tc::mbar_wait(bars + AT + 1, 0, tc::kDrainNs);
     }
     if (tid == 0) {
       atomicExch(d.err, 1u);

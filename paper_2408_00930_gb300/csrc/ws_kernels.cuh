@@ -52,6 +52,10 @@ struct Dev {
   // energy kernel's Gaussian chunks per env tile
   int env_threads;
   int energy_chunks;
+  // limit of the fused kernels' device waits (MMA completions, the SFU token,
+  // block loads, the cluster partner), in ns: a wait that runs out sets the
+  // error flag (ws_sync reports it) and the kernel leaves after draining
+  uint64_t wait_ns;
   // ring
   float *r_obs;
   void *r_act;

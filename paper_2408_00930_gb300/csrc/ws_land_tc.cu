@@ -76,7 +76,7 @@ constexpr int OFF_XCH = OFF_BE + kNS * kBlkBytes; // f32 [128] each: partial ene
                                                   // |y|^2 of half 0 and of half 1
 constexpr int OFF_RECV = OFF_XCH + 4 * kRows * 4; // f32 [2][128] the cluster partner's partials
 constexpr int OFF_BAR = OFF_RECV + 2 * kRows * 4;
-constexpr int N_BAR = 4 + kNS + 2 * kNT;  // ae, b[kNS], mma[kNT], epi[kNT], pol, x, drain
+constexpr int N_BAR = 5 + kNS + 2 * kNT;  // ae, b[kNS], mma[kNT], epi[kNT], pol, x, drain, drain_pol
 constexpr int OFF_CMD = OFF_BAR + N_BAR * 8;  // [0] sweep command, [1] end flag, [2] blocks loaded
 constexpr int OFF_TM = OFF_CMD + 16;
 constexpr int SMEM = OFF_TM + 16 + 1024;
@@ -249,6 +249,24 @@ __device__ __forceinline__ float ex2_fast(float x) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+// Exponentials of 32 accumulator columns summed into s[0..3] (by column mod 4).
+__device__ __forceinline__ void ex2_sum32(const uint32_t (&z)[32], float (&s)[4]) {
+#pragma unroll
+  for (int c = 0; c < 32; ++c) s[c & 3] += ex2_fast(__uint_as_float(z[c]));
+}
+// tcgen05.wait::ld with the loaded registers as operands, so that no use of
+// them can be scheduled before the wait.
+__device__ __forceinline__ void tmem_wait_ld_regs(uint32_t (&z)[32]) {
+  asm volatile(
+      "tcgen05.wait::ld.sync.aligned;"
+      : "+r"(z[0]), "+r"(z[1]), "+r"(z[2]), "+r"(z[3]), "+r"(z[4]), "+r"(z[5]), "+r"(z[6]),
+        "+r"(z[7]), "+r"(z[8]), "+r"(z[9]), "+r"(z[10]), "+r"(z[11]), "+r"(z[12]), "+r"(z[13]),
+        "+r"(z[14]), "+r"(z[15]), "+r"(z[16]), "+r"(z[17]), "+r"(z[18]), "+r"(z[19]), "+r"(z[20]),
+        "+r"(z[21]), "+r"(z[22]), "+r"(z[23]), "+r"(z[24]), "+r"(z[25]), "+r"(z[26]), "+r"(z[27]),
+        "+r"(z[28]), "+r"(z[29]), "+r"(z[30]), "+r"(z[31])
+      :
+      : "memory");
+}
 __device__ __forceinline__ float4 lds128f(uint32_t addr) {
   float4 v;
   asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
@@ -310,21 +328,37 @@ __device__ __forceinline__ void arrive_remote(uint32_t addr) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
 }
 // Bounded wait with cluster-scope acquire (for arrivals from the partner CTA).
-__device__ __forceinline__ bool mbar_wait_cluster(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
   const uint32_t a = tc::smem_u32(bar);
+  const bool short_lim = limit_ns < tc::kShortWaitNs;
   uint64_t t0 = 0;
   for (int it = 0;; ++it) {
     uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
+    if (short_lim)  // a poll that never suspends (see tc::mbar_test_wait)
+      asm volatile(
+          "{\n\t.reg .pred p;\n\t"
+          "mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(ok)
+          : "r"(a), "r"(parity)
+          : "memory");
+    else
+      asm volatile(
+          "{\n\t.reg .pred p;\n\t"
+          "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(ok)
+          : "r"(a), "r"(parity)
+          : "memory");
     if (ok) return true;
-    if (it == 0) t0 = tc::global_ns();
-    else if ((it & 255) == 0 && tc::global_ns() - t0 > kWaitNs) return false;
+    if (short_lim) {  // the SM clock, 2 cycles per ns
+      if (it == 0) t0 = tc::sm_clock();
+      else if (tc::sm_clock() - t0 > 2 * limit_ns) return false;
+    } else if (it == 0) {
+      t0 = tc::global_ns();
+    } else if ((it & 255) == 0 && tc::global_ns() - t0 > limit_ns) {
+      return false;
+    }
   }
 }
 
@@ -345,6 +379,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t *bars = (uint64_t *)(sm + OFF_BAR);
   uint64_t *bar_ae = bars, *bar_b = bars + 1, *bar_mma = bar_b + kNS, *bar_epi = bar_mma + kNT;
   uint64_t *bar_pol = bar_epi + kNT, *bar_x = bar_pol + 1, *bar_drain = bar_x + 1;
+  uint64_t *bar_drain_pol = bar_drain + 1;
   volatile uint32_t *cmd = (volatile uint32_t *)(sm + OFF_CMD);
   uint32_t *tm_holder = (uint32_t *)(sm + OFF_TM);
   const uint32_t rank = CL > 1 ? cluster_rank() : 0u;
@@ -364,6 +399,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::mbar_init(bar_pol, 1);
     tc::mbar_init(bar_x, kRows);
     tc::mbar_init(bar_drain, 1);
+    tc::mbar_init(bar_drain_pol, 1);
     cmd[0] = 0u;
     cmd[1] = 0u;
     cmd[2] = 0u;
@@ -382,6 +418,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int n_blk = ((const int32_t *)eimg)[0] / CL;  // this CTA's blocks per sweep
   const int nb_pos = ((const int32_t *)eimg)[1];       // blocks before the first a < 0 block
   const int blk0 = (int)rank * n_blk;                  // this CTA's first block
+  const uint64_t wlim = d.wait_ns;
   bool fail = false;
 
   if (tid >= kEpi) {
@@ -406,10 +443,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool got = false;
             uint64_t t0 = 0;
             for (int it = 0;; ++it) {
-              if (tc::mbar_try_wait(bar_mma + gp % kNT, (gp / kNT) & 1u)) { got = true; break; }
+              if (tc::mbar_try_wait_lim(bar_mma + gp % kNT, (gp / kNT) & 1u, wlim)) { got = true; break; }
               if (*endf) break;
-              if (it == 0) t0 = tc::global_ns();
-              else if ((it & 255) == 0 && tc::global_ns() - t0 > kWaitNs) { fail = true; break; }
+              if (wlim < tc::kShortWaitNs) {  // short limits: the SM clock, 2 cycles per ns
+                if (it == 0) t0 = tc::sm_clock();
+                else if (tc::sm_clock() - t0 > 2 * wlim) { fail = true; break; }
+              } else if (it == 0) {
+                t0 = tc::global_ns();
+              } else if ((it & 255) == 0 && tc::global_ns() - t0 > wlim) {
+                fail = true;
+                break;
+              }
             }
             if (!got) break;
           }
@@ -429,14 +473,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         constexpr uint32_t idesc = tc::idesc_bf16_f32(128, kBlk);
         uint32_t pa = 0;
         while (!fail) {
-          if (!tc::mbar_wait(bar_ae, pa, kWaitNs)) { fail = true; break; }
+          if (!tc::mbar_wait(bar_ae, pa, wlim)) { fail = true; break; }
           pa ^= 1u;
           if (*cmd == 0u) break;
           for (int i = 0; i < n_blk && !fail; ++i, ++g) {
             const uint32_t sbuf = g % kNS, t = g % kNT;
-            if (!tc::mbar_wait(bar_b + sbuf, (g / kNS) & 1u, kWaitNs)) { fail = true; break; }
+            if (!tc::mbar_wait(bar_b + sbuf, (g / kNS) & 1u, wlim)) { fail = true; break; }
             if (g >= (uint32_t)kNT &&
-                !tc::mbar_wait(bar_epi + t, ((g - kNT) / kNT) & 1u, kWaitNs)) { fail = true; break; }
+                !tc::mbar_wait(bar_epi + t, ((g - kNT) / kNT) & 1u, wlim)) { fail = true; break; }
             tc::fence_after_sync();
 #pragma unroll
             for (int s = 0; s < kKE / 16; ++s) {
@@ -453,14 +497,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncwarp();
       bar_sync_n(kBarProd, 64);
       if (lane == 0) {
-        // blocks g .. gl - 1 were loaded ahead: their copies finish before shared
-        // memory goes away
-        if (!fail) {
-          const uint32_t gl = *s_gl;
-          for (uint32_t q = g; q < gl; ++q) tc::mbar_wait(bar_b + q % kNS, (q / kNS) & 1u, kWaitNs);
-        }
+        // blocks g .. gl - 1 were loaded ahead (or their MMA was never issued
+        // after a wait ran out): their copies finish before shared memory goes
+        // away, on every path
+        const uint32_t gl = *s_gl;
+        for (uint32_t q = g; q < gl; ++q) tc::mbar_wait(bar_b + q % kNS, (q / kNS) & 1u, tc::kDrainNs);
         tc::mma_commit(bar_drain);
-        tc::mbar_wait(bar_drain, 0, kWaitNs);
+        tc::mbar_wait(bar_drain, 0, tc::kDrainNs);
       }
     }
     if (fail && (tid & 31) == 0) {
@@ -492,7 +535,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // After a wait has run out no other wait is attempted: the CTA runs on to the
     // vote at the next step boundary and leaves together.
     auto wait = [&](uint64_t *bar, uint32_t parity) {
-      if (!fail && !tc::mbar_wait(bar, parity, kWaitNs)) fail = true;
+      if (!fail && !tc::mbar_wait(bar, parity, wlim)) fail = true;
     };
     const uint32_t partner = rank ^ 1u;
     const uint32_t recv_remote = CL > 1 ? mapa(sb + OFF_RECV, partner) : 0u;
@@ -513,33 +556,36 @@ __global__ void __launch_bounds__(kThreads, 1)
       // the two warps of an SMSP work on different blocks (one's TMEM load and
       // waits overlap the other's exponentials).  A block holds Gaussians of one
       // sign; the two signs are summed apart.
+      // The loads are pipelined: a block's second 32 columns load while its
+      // first 32 are exponentiated, and the next block's first 32 while its
+      // second 32 are (two 32-register buffers).
       float ap = 0.f, an = 0.f;
-      for (int i = h; i < n_blk; i += 2) {
-        const uint32_t gb = ge + (uint32_t)i, t = gb % kNT;
+      uint32_t za[32], zb[32];
+      if (h < n_blk) {
+        const uint32_t gb = ge + (uint32_t)h, t = gb % kNT;
         wait(bar_mma + t, (gb / kNT) & 1u);
         tc::fence_after_sync();
-        uint32_t z0[32], z1[32];
-        tc::tmem_ld32(tbase + lane_sel + TM_E + t * kBlk, z0);
-        tc::tmem_ld32(tbase + lane_sel + TM_E + t * kBlk + 32u, z1);
-        tc::tmem_wait_ld();
+        tc::tmem_ld32(tbase + lane_sel + TM_E + t * kBlk, za);
+        tmem_wait_ld_regs(za);
+      }
+      for (int i = h; i < n_blk; i += 2) {
+        const uint32_t gb = ge + (uint32_t)i, t = gb % kNT;
+        tc::tmem_ld32(tbase + lane_sel + TM_E + t * kBlk + 32u, zb);
+        float sv[4] = {0.f, 0.f, 0.f, 0.f};
+        ex2_sum32(za, sv);
+        tmem_wait_ld_regs(zb);
         tc::fence_before_sync();
         mbar_arrive(bar_epi + t);
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-#pragma unroll
-        for (int c = 0; c < 32; c += 4) {
-          s0 += ex2_fast(__uint_as_float(z0[c]));
-          s1 += ex2_fast(__uint_as_float(z0[c + 1]));
-          s2 += ex2_fast(__uint_as_float(z0[c + 2]));
-          s3 += ex2_fast(__uint_as_float(z0[c + 3]));
+        const int in = i + 2;
+        if (in < n_blk) {
+          const uint32_t gn = ge + (uint32_t)in, tn = gn % kNT;
+          wait(bar_mma + tn, (gn / kNT) & 1u);
+          tc::fence_after_sync();
+          tc::tmem_ld32(tbase + lane_sel + TM_E + tn * kBlk, za);
         }
-#pragma unroll
-        for (int c = 0; c < 32; c += 4) {
-          s0 += ex2_fast(__uint_as_float(z1[c]));
-          s1 += ex2_fast(__uint_as_float(z1[c + 1]));
-          s2 += ex2_fast(__uint_as_float(z1[c + 2]));
-          s3 += ex2_fast(__uint_as_float(z1[c + 3]));
-        }
-        const float bs = (s0 + s1) + (s2 + s3);
+        ex2_sum32(zb, sv);
+        if (in < n_blk) tmem_wait_ld_regs(za);
+        const float bs = (sv[0] + sv[1]) + (sv[2] + sv[3]);
         if (blk0 + i < nb_pos) ap += bs;
         else an += bs;
       }
@@ -553,7 +599,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (CL > 1) {
           st_cluster_f32(recv_remote + (par * kRows + (uint32_t)r) * 4u, E);
           arrive_remote(barx_remote);
-          if (!fail && !mbar_wait_cluster(bar_x, px)) fail = true;
+          if (!fail && !mbar_wait_cluster(bar_x, px, wlim)) fail = true;
           const float other = recv[par * kRows + r];
           E = rank == 0 ? E + other : other + E;
         }
@@ -804,17 +850,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-    // stop the producer warps
-    bar_sync_n(kBarEpi, kEpi);
+    // stop the producer warps (a wait of the last step that ran out on any
+    // epilogue thread counts: the vote makes every thread see it)
+    fail = !bar_all_n(kBarEpi, kEpi, !fail);
     if (tid == 0) {
       *cmd = 0u;
       cmd[1] = 1u;  // the loader stops waiting
     }
     mbar_arrive(bar_ae);
     if (fail && tid == 0) {
-      // a policy MMA may still be in flight after a wait that ran out
-      tc::mma_commit(bar_pol);
-      tc::mbar_wait(bar_pol, pp, kWaitNs);
+      // a policy MMA may still be in flight after a wait that ran out: the
+      // commit on a barrier not used before completes once all of them have
+      tc::mma_commit(bar_drain_pol);
+      tc::mbar_wait(bar_drain_pol, 0, tc::kDrainNs);
       atomicExch(d.err, 1u);
       atomicExch(d.err + 1, 501u);
     }

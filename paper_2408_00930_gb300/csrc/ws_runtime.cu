@@ -505,6 +505,9 @@ void default_launch(ws_ctx *c) {
   l.tile_ctas = 2 * tiles <= (uint32_t)sm_count() ? 2u : 1u;
 }
 
+// The fused kernels' device-wait limit of a launch configuration (0 = 2 s).
+uint64_t device_wait_ns(const ws_launch &l) { return l.wait_ns ? l.wait_ns : 2000000000ull; }
+
 int econ_grid(const ws_ctx *c) {
   const int sms = sm_count();
   const int n = (int)c->d.n_items;
@@ -772,6 +775,7 @@ ws_status ws_create(const ws_config *cfg, void *state_buf, size_t state_bytes, v
   default_launch(c);
   c->d.env_threads = (int)c->lc.env_threads;
   c->d.energy_chunks = (int)c->lc.energy_chunks;
+  c->d.wait_ns = device_wait_ns(c->lc);
   cudaError_t e = cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming);
   if (e == cudaSuccess && cfg->env == WS_ENV_ECONOMY) {
@@ -1142,6 +1146,7 @@ ws_status ws_set_launch(ws_ctx *c, const ws_launch *l) {
   drop_graphs(c);  // graphs bake the launch parameters in
   c->d.env_threads = (int)l->env_threads;
   c->d.energy_chunks = (int)l->energy_chunks;
+  c->d.wait_ns = device_wait_ns(*l);
   if (c->L.econ_fused && (old.econ_tiles != l->econ_tiles || old.econ_lpt != l->econ_lpt)) {
     ws_status s = set_econ_items(c);
     if (s != WS_OK) return s;

@@ -29,15 +29,57 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
+// test_wait never suspends the thread (try_wait may stay suspended until the
+// phase completes, which would hide a short wait limit).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Limits below this are taken as short: the phase is polled with test_wait,
+// and the elapsed time is read from the SM clock (2 cycles per ns), since
+// %globaltimer may tick more coarsely than such a limit.
+constexpr uint64_t kShortWaitNs = 1000000ull;
+
+__device__ __forceinline__ uint64_t sm_clock() {
+  uint64_t c;
+  asm volatile("mov.u64 %0, %clock64;" : "=l"(c));
+  return c;
+}
+
+__device__ __forceinline__ bool mbar_try_wait_lim(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+  return limit_ns < kShortWaitNs ? mbar_test_wait(bar, parity) : mbar_try_wait(bar, parity);
+}
+
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
 }
 
+// Bound of the waits that drain a kernel's own asynchronous work (MMAs, bulk
+// copies) before it releases tensor memory and exits after a failure: fixed,
+// and far above any completion time, so that no copy or MMA is still running
+// when the memory it targets goes away.
+constexpr uint64_t kDrainNs = 2000000000ull;
+
 // Bounded wait on a phase: gives up (returns false) once `limit_ns` of wall
 // time have passed without the phase completing.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+  if (limit_ns < kShortWaitNs) {  // short limits: check the SM clock after every bounded try
+    const uint64_t c0 = sm_clock();
+    for (;;) {
+      if (mbar_test_wait(bar, parity)) return true;
+      if (sm_clock() - c0 > 2 * limit_ns) return false;
+    }
+  }
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (;;) {

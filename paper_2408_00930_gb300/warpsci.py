@@ -33,7 +33,11 @@ EXPORTED = ["ws_query_bytes", "ws_create", "ws_reset", "ws_step", "ws_rollout", 
             "ws_policy_forward_noalloc", "ws_get_launch", "ws_set_launch", "ws_tune",
             "ws_server_create", "ws_server_submit",
             "ws_server_wait_chunk", "ws_server_fetch", "ws_server_ack", "ws_server_release",
-            "ws_server_get_stats", "ws_server_destroy"]
+            "ws_server_get_stats", "ws_server_destroy", "ws_probe_rate"]
+PROBE_OPS = ["tanh.approx.f32", "tanh.approx.bf16x2", "ex2.approx.ftz.f32",
+             "ex2.approx.ftz.bf16x2", "ex2.approx.f16x2", "rcp.approx.ftz.f32",
+             "sin.approx.ftz.f32", "fma.rn.f32", "fma.rn.f32x2", "lg2.approx.ftz.f32",
+             "rsqrt.approx.ftz.f32"]
 WS_REQ_CONSUME_ON_READY = 1
 WS_FLAG_DEBUG_LOGITS = 1
 WS_FLAG_ENERGY_TARGET = 2
@@ -57,7 +61,7 @@ class ws_launch(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("chunk_steps", C.c_uint32), ("grid", C.c_uint32),
                 ("econ_tiles", C.c_uint32), ("econ_lpt", C.c_uint32),
                 ("energy_chunks", C.c_uint32), ("env_threads", C.c_uint32),
-                ("tile_ctas", C.c_uint32)]
+                ("tile_ctas", C.c_uint32), ("wait_ns", C.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "struct_size"}
@@ -132,6 +136,7 @@ def lib():
         L.ws_server_ack.argtypes = [P, C.c_uint64, C.c_uint32]
         L.ws_server_release.argtypes = [P, C.c_uint64]
         L.ws_server_get_stats.argtypes = [P, C.POINTER(ws_server_stats)]
+        L.ws_probe_rate.argtypes = [C.c_int, C.c_uint32, P, C.c_size_t, C.POINTER(C.c_double), P]
         L.ws_server_destroy.argtypes = [P]
         L.ws_server_destroy.restype = None
         for n in EXPORTED:
@@ -237,6 +242,13 @@ def ws_policy_forward_noalloc(obs_ptr, n_rows, params_ptr, in_dim, hidden0, hidd
                               out_ptr, stream_ptr):
     return lib().ws_policy_forward_noalloc(obs_ptr, n_rows, params_ptr, in_dim, hidden0, hidden1,
                                            out_dim, out_ptr, stream_ptr)
+
+
+def ws_probe_rate(op, iters, dev_buf_ptr, buf_bytes, stream_ptr):
+    """Results per clock per SM of probe op (index into PROBE_OPS)."""
+    out = C.c_double()
+    st = lib().ws_probe_rate(op, iters, dev_buf_ptr, buf_bytes, C.byref(out), stream_ptr)
+    return st, out.value
 
 
 # --- convenience owner --------------------------------------------------------
