@@ -448,7 +448,25 @@ ws_status ws_server_release(ws_server *s, uint64_t id);
 
 ws_status ws_server_get_stats(ws_server *s, ws_server_stats *out);
 
-/* Stop the scheduler, release every request and free the arena. */
+/* Serve clients in other processes (trainer processes on the same machine)
+ * over a Unix-domain stream socket created at `path` (a file already there is
+ * replaced); one thread per connection.  Messages are [u32 op][u32 payload
+ * bytes][payload] in host byte order, every reply begins with an i32 ws_status:
+ *   1 SUBMIT  ws_request [+ i32 agents_per_env[n_envs]]  -> status, u64 id
+ *   2 WAIT    u64 id, u32 chunk, u32 timeout_ms (0: none)  -> status
+ *   3 FETCH   u64 id, i32 field, u32 chunk                 -> status, u64 n, n bytes
+ *             (the ws_fetch layout of the chunk's steps)
+ *   4 ACK     u64 id, u32 chunk                            -> status
+ *   5 RELEASE u64 id (one this connection submitted)       -> status
+ *   6 STATS                                                -> status, ws_server_stats
+ * When a connection closes (the client exited or was killed) the requests it
+ * submitted and did not release are released, freeing their bytes.  The
+ * socket is removed by ws_server_destroy.  WS_ERR_STATE if the socket cannot be
+ * created, WS_ERR_INVALID if the server already listens. */
+ws_status ws_server_listen(ws_server *s, const char *path);
+
+/* Stop the scheduler (and the socket of ws_server_listen), release every
+ * request and free the arena. */
 void ws_server_destroy(ws_server *s);
 
 /* Policy forward pass that allocates no device memory (the paper has no

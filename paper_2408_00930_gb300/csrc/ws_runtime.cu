@@ -974,6 +974,12 @@ ws_status ws_forces(ws_ctx *c, uint32_t n) {
 
 }  // extern "C"
 
+// Bytes per step of a ring field (0 if the context has no such field).
+size_t ws_field_step_bytes(const ws_ctx *c, ws_field f) {
+  size_t off = 0;
+  return c ? ring_field_step_bytes(c, f, &off) : 0;
+}
+
 // Fetch on an explicit stream, without waiting (the copy is ordered after the
 // work already enqueued on that stream only).
 ws_status ws_fetch_async(ws_ctx *c, ws_field f, uint64_t t0, uint32_t n, void *dst,

@@ -10,13 +10,20 @@
 // (chunk k ready minus chunk k-1 ready; chunk 0 from arrival) and aggregate
 // agent-steps/s can be reported.  (The paper describes no serving layer; this
 // is the multi-client front end of the roll-out loop of Sec. 2 / App. B.)
+#include <sys/socket.h>
+#include <sys/un.h>
+#include <unistd.h>
+
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
 #include <map>
 #include <mutex>
+#include <set>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -25,6 +32,11 @@
 // Internal helpers of ws_runtime.cu.
 ws_status ws_fetch_async(ws_ctx *ctx, ws_field field, uint64_t t0, uint32_t n_steps, void *dst,
                          size_t dst_bytes, int dst_on_device, cudaStream_t stream);
+size_t ws_field_step_bytes(const ws_ctx *ctx, ws_field field);
+
+namespace {
+struct Ipc;
+}
 
 namespace {
 
@@ -70,6 +82,7 @@ struct ws_server {
   uint64_t submitted = 0, admitted = 0, completed = 0, rejected = 0, failed = 0, chunks = 0;
   double agent_steps = 0, t_first = 0, t_last = 0;
   std::vector<float> lat_ms;
+  Ipc *ipc = nullptr;  // clients in other processes (ws_server_listen)
 };
 
 namespace {
@@ -238,9 +251,243 @@ void scheduler(ws_server *s) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Clients in other processes: a Unix-domain stream socket, one thread per
+// connection.  Messages are [u32 op][u32 payload bytes][payload] (host byte
+// order: both ends run on the same machine); every reply starts with an i32
+// status.  A connection that closes (the client exited, or was killed) has the
+// requests it submitted and did not release released, freeing their bytes.
+enum IpcOp : uint32_t {
+  kOpSubmit = 1,   // ws_request [+ i32 agents_per_env[n_envs]] -> status, u64 id
+  kOpWait = 2,     // u64 id, u32 chunk, u32 timeout_ms -> status
+  kOpFetch = 3,    // u64 id, i32 field, u32 chunk -> status, u64 bytes, bytes
+  kOpAck = 4,      // u64 id, u32 chunk -> status
+  kOpRelease = 5,  // u64 id -> status
+  kOpStats = 6     // -> status, ws_server_stats
+};
+
+struct Ipc {
+  int listen_fd = -1;
+  std::string path;
+  std::atomic<bool> stop{false};
+  std::thread acceptor;
+  std::mutex mu;
+  std::vector<std::thread> conns;
+  std::set<int> fds;
+};
+
+bool read_all(int fd, void *buf, size_t n) {
+  char *p = (char *)buf;
+  while (n) {
+    const ssize_t k = ::recv(fd, p, n, 0);
+    if (k <= 0) return false;
+    p += k;
+    n -= (size_t)k;
+  }
+  return true;
+}
+
+bool write_all(int fd, const void *buf, size_t n) {
+  const char *p = (const char *)buf;
+  while (n) {
+    const ssize_t k = ::send(fd, p, n, MSG_NOSIGNAL);
+    if (k <= 0) return false;
+    p += k;
+    n -= (size_t)k;
+  }
+  return true;
+}
+
+bool reply_status(int fd, ws_status st) {
+  const int32_t v = (int32_t)st;
+  return write_all(fd, &v, 4);
+}
+
+void serve_connection(ws_server *s, int fd) {
+  std::set<uint64_t> owned;
+  std::vector<char> payload;
+  for (;;) {
+    uint32_t hdr[2];
+    if (!read_all(fd, hdr, 8)) break;
+    if (hdr[1] > (64u << 20)) break;  // malformed
+    payload.resize(hdr[1]);
+    if (hdr[1] && !read_all(fd, payload.data(), hdr[1])) break;
+    const char *p = payload.data();
+    bool ok = true;
+    switch (hdr[0]) {
+      case kOpSubmit: {
+        ws_request q{};
+        if (hdr[1] < sizeof(ws_request)) {
+          ok = reply_status(fd, WS_ERR_INVALID) && write_all(fd, "\0\0\0\0\0\0\0\0", 8);
+          break;
+        }
+        std::memcpy(&q, p, sizeof(ws_request));
+        q.agents_per_env = nullptr;
+        std::vector<int32_t> agents;
+        if (hdr[1] > sizeof(ws_request)) {
+          const size_t n = (hdr[1] - sizeof(ws_request)) / 4;
+          agents.resize(n);
+          std::memcpy(agents.data(), p + sizeof(ws_request), n * 4);
+          if (n == q.n_envs) q.agents_per_env = agents.data();
+        }
+        uint64_t id = 0;
+        const ws_status st = ws_server_submit(s, &q, &id);
+        if (st == WS_OK) owned.insert(id);
+        ok = reply_status(fd, st) && write_all(fd, &id, 8);
+        break;
+      }
+      case kOpWait: {
+        if (hdr[1] < 16) { ok = reply_status(fd, WS_ERR_INVALID); break; }
+        uint64_t id;
+        uint32_t chunk, timeout_ms;
+        std::memcpy(&id, p, 8);
+        std::memcpy(&chunk, p + 8, 4);
+        std::memcpy(&timeout_ms, p + 12, 4);
+        // bounded slices, so that a closing server is never held up by a waiter
+        ws_status st = WS_ERR_TIMEOUT;
+        const auto t_end = Clock::now() + std::chrono::milliseconds(timeout_ms);
+        while (!s->ipc->stop.load()) {
+          st = ws_server_wait_chunk(s, id, chunk, 200);
+          if (st != WS_ERR_TIMEOUT) break;
+          if (timeout_ms && Clock::now() >= t_end) break;
+        }
+        ok = reply_status(fd, st);
+        break;
+      }
+      case kOpFetch: {
+        if (hdr[1] < 16) { ok = reply_status(fd, WS_ERR_INVALID) && write_all(fd, "\0\0\0\0\0\0\0\0", 8); break; }
+        uint64_t id;
+        int32_t field;
+        uint32_t chunk;
+        std::memcpy(&id, p, 8);
+        std::memcpy(&field, p + 8, 4);
+        std::memcpy(&chunk, p + 12, 4);
+        size_t bytes = 0;
+        ws_status st = WS_ERR_INVALID;
+        {
+          std::lock_guard<std::mutex> lk(s->mu);
+          auto it = s->reqs.find(id);
+          if (it != s->reqs.end() && it->second->ctx) {
+            const Req *r = it->second;
+            const uint32_t steps =
+                chunk < r->n_chunks ? std::min(r->q.chunk_steps, r->q.horizon - chunk * r->q.chunk_steps)
+                                    : 0u;
+            bytes = ws_field_step_bytes(r->ctx, (ws_field)field) * steps;
+            st = bytes ? WS_OK : WS_ERR_INVALID;
+          }
+        }
+        std::vector<char> buf(bytes);
+        if (st == WS_OK) st = ws_server_fetch(s, id, (ws_field)field, chunk, buf.data(), bytes, 0);
+        const uint64_t nb = st == WS_OK ? (uint64_t)bytes : 0u;
+        ok = reply_status(fd, st) && write_all(fd, &nb, 8) && (nb == 0 || write_all(fd, buf.data(), nb));
+        break;
+      }
+      case kOpAck: {
+        if (hdr[1] < 12) { ok = reply_status(fd, WS_ERR_INVALID); break; }
+        uint64_t id;
+        uint32_t chunk;
+        std::memcpy(&id, p, 8);
+        std::memcpy(&chunk, p + 8, 4);
+        ok = reply_status(fd, ws_server_ack(s, id, chunk));
+        break;
+      }
+      case kOpRelease: {
+        if (hdr[1] < 8) { ok = reply_status(fd, WS_ERR_INVALID); break; }
+        uint64_t id;
+        std::memcpy(&id, p, 8);
+        const ws_status st = owned.count(id) ? ws_server_release(s, id) : WS_ERR_INVALID;
+        owned.erase(id);
+        ok = reply_status(fd, st);
+        break;
+      }
+      case kOpStats: {
+        ws_server_stats st{};
+        st.struct_size = sizeof(st);
+        const ws_status rc = ws_server_get_stats(s, &st);
+        ok = reply_status(fd, rc) && write_all(fd, &st, sizeof(st));
+        break;
+      }
+      default:
+        ok = false;
+    }
+    if (!ok) break;
+  }
+  // the client is gone: its requests free their bytes
+  for (uint64_t id : owned) ws_server_release(s, id);
+  {
+    std::lock_guard<std::mutex> lk(s->ipc->mu);
+    s->ipc->fds.erase(fd);
+  }
+  ::close(fd);
+}
+
+void accept_loop(ws_server *s) {
+  Ipc *ipc = s->ipc;
+  cudaSetDevice(s->device);
+  while (!ipc->stop.load()) {
+    const int fd = ::accept(ipc->listen_fd, nullptr, nullptr);
+    if (fd < 0) {
+      if (ipc->stop.load()) break;
+      std::this_thread::sleep_for(std::chrono::milliseconds(1));
+      continue;
+    }
+    std::lock_guard<std::mutex> lk(ipc->mu);
+    if (ipc->stop.load()) {
+      ::close(fd);
+      break;
+    }
+    ipc->fds.insert(fd);
+    ipc->conns.emplace_back([s, fd] {
+      cudaSetDevice(s->device);
+      serve_connection(s, fd);
+    });
+  }
+}
+
+void ipc_stop(ws_server *s) {
+  Ipc *ipc = s->ipc;
+  if (!ipc) return;
+  ipc->stop.store(true);
+  if (ipc->listen_fd >= 0) ::shutdown(ipc->listen_fd, SHUT_RDWR);
+  if (ipc->acceptor.joinable()) ipc->acceptor.join();
+  if (ipc->listen_fd >= 0) ::close(ipc->listen_fd);
+  std::vector<std::thread> conns;
+  {
+    std::lock_guard<std::mutex> lk(ipc->mu);
+    for (int fd : ipc->fds) ::shutdown(fd, SHUT_RDWR);
+    conns.swap(ipc->conns);
+  }
+  for (auto &t : conns)
+    if (t.joinable()) t.join();
+  ::unlink(ipc->path.c_str());
+  delete ipc;
+  s->ipc = nullptr;
+}
+
 }  // namespace
 
 extern "C" {
+
+ws_status ws_server_listen(ws_server *s, const char *path) {
+  if (!s || !path || s->ipc) return WS_ERR_INVALID;
+  sockaddr_un addr{};
+  if (std::strlen(path) >= sizeof(addr.sun_path)) return WS_ERR_INVALID;
+  addr.sun_family = AF_UNIX;
+  std::strncpy(addr.sun_path, path, sizeof(addr.sun_path) - 1);
+  const int fd = ::socket(AF_UNIX, SOCK_STREAM, 0);
+  if (fd < 0) return WS_ERR_STATE;
+  ::unlink(path);
+  if (::bind(fd, (const sockaddr *)&addr, sizeof(addr)) != 0 || ::listen(fd, 64) != 0) {
+    ::close(fd);
+    return WS_ERR_STATE;
+  }
+  Ipc *ipc = new Ipc();
+  ipc->listen_fd = fd;
+  ipc->path = path;
+  s->ipc = ipc;
+  ipc->acceptor = std::thread(accept_loop, s);
+  return WS_OK;
+}
 
 ws_status ws_server_create(size_t budget_bytes, ws_server **out) {
   if (!out || budget_bytes < 4096) return WS_ERR_INVALID;
@@ -395,6 +642,7 @@ ws_status ws_server_get_stats(ws_server *s, ws_server_stats *out) {
 
 void ws_server_destroy(ws_server *s) {
   if (!s) return;
+  ipc_stop(s);  // no client thread touches the server after this
   {
     std::lock_guard<std::mutex> lk(s->mu);
     s->stop = true;

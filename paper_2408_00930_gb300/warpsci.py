@@ -33,7 +33,7 @@ EXPORTED = ["ws_query_bytes", "ws_create", "ws_reset", "ws_step", "ws_rollout", 
             "ws_policy_forward_noalloc", "ws_get_launch", "ws_set_launch", "ws_tune",
             "ws_server_create", "ws_server_submit",
             "ws_server_wait_chunk", "ws_server_fetch", "ws_server_ack", "ws_server_release",
-            "ws_server_get_stats", "ws_server_destroy", "ws_probe_rate"]
+            "ws_server_get_stats", "ws_server_destroy", "ws_probe_rate", "ws_server_listen"]
 PROBE_OPS = ["tanh.approx.f32", "tanh.approx.bf16x2", "ex2.approx.ftz.f32",
              "ex2.approx.ftz.bf16x2", "ex2.approx.f16x2", "rcp.approx.ftz.f32",
              "sin.approx.ftz.f32", "fma.rn.f32", "fma.rn.f32x2", "lg2.approx.ftz.f32",
@@ -137,6 +137,7 @@ def lib():
         L.ws_server_release.argtypes = [P, C.c_uint64]
         L.ws_server_get_stats.argtypes = [P, C.POINTER(ws_server_stats)]
         L.ws_probe_rate.argtypes = [C.c_int, C.c_uint32, P, C.c_size_t, C.POINTER(C.c_double), P]
+        L.ws_server_listen.argtypes = [P, C.c_char_p]
         L.ws_server_destroy.argtypes = [P]
         L.ws_server_destroy.restype = None
         for n in EXPORTED:
@@ -465,6 +466,12 @@ class Server:
 
     def release(self, rid):
         return lib().ws_server_release(self.s, rid)
+
+    def listen(self, path):
+        """Serve clients in other processes over a Unix-domain socket at path."""
+        rc = lib().ws_server_listen(self.s, path.encode())
+        if rc != WS_OK:
+            raise WarpSciError(rc, "ws_server_listen")
 
     def stats(self):
         st = ws_server_stats()
