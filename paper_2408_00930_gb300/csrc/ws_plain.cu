@@ -839,6 +839,113 @@ __global__ __launch_bounds__(T, MINB) void k_returns(Dev d, uint32_t n) {
   }
 }
 
+// S7 for rings with few slots (the landscape's 8,192, a small control run):
+// one serial chain per slot leaves most of the chip idle, so each slot's window
+// of n steps is cut into NSEG segments scanned at once.  The recurrence is the
+// affine map G_t = B_t + A_t G_{t_end} of a segment's carry-in G_{t_end}, and
+// such maps compose; per block, 32 consecutive slots (one per lane) times NSEG
+// segments (one per warp):
+//   pass 1  each segment scans its steps newest first with carry-in 0: B (the
+//           float-float return of the segment alone) and A (the product of
+//           gamma (1 - d) over the segment, float-float; 0 after a done)
+//   combine lane s of warp 0 walks its slot's segments newest first:
+//           carry_{j-1} = B_j + A_j carry_j (float-float), carry_last = 0
+//   pass 2  each segment scans its steps again from its carry-in, exactly as
+//           the serial kernel does, and writes the returns
+// The second read of the rewards and done flags mostly hits L2.
+__device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, float &ph, float &pl) {
+  ph = __fmul_rn(ah, bh);
+  pl = __fadd_rn(__fmaf_rn(ah, bh, -ph), __fadd_rn(__fmul_rn(ah, bl), __fmul_rn(al, bh)));
+}
+__device__ __forceinline__ void ff_add(float ah, float al, float bh, float bl, float &sh, float &sl) {
+  const float s = __fadd_rn(ah, bh);
+  const float bb = __fsub_rn(s, ah);
+  const float e = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+  const float t = __fadd_rn(e, __fadd_rn(al, bl));
+  sh = __fadd_rn(s, t);
+  sl = __fsub_rn(t, __fsub_rn(sh, s));
+}
+
+template <int NSEG>
+__global__ __launch_bounds__(32 * NSEG) void k_returns_seg(Dev d, uint32_t n) {
+  __shared__ float2 sA[NSEG][32], sB[NSEG][32], sC[NSEG][32];
+  const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
+  const size_t s = (size_t)blockIdx.x * 32 + (size_t)lane;
+  const bool valid = s < d.n_slots;
+  const size_t S = d.n_slots;
+  const uint32_t R = d.ring_steps;
+  const float g = d.gamma;
+  const uint32_t L = (n + NSEG - 1) / NSEG;
+  const uint32_t t_lo = min(n, (uint32_t)seg * L), t_hi = min(n, (uint32_t)(seg + 1) * L);
+  // ring row of window step t (t = 0 is step k - n)
+  const uint32_t row0 = (uint32_t)((d.k[0] - n) % R);
+  auto row_of = [&](uint32_t t) { const uint32_t r = row0 + t; return r >= R ? r - R : r; };
+  // steps are taken in batches of kRetU, all of a batch's loads issued first
+  float bh = 0.f, bl = 0.f, ah = 1.f, al = 0.f;
+  if (valid) {
+    for (uint32_t t = t_hi; t > t_lo;) {
+      const uint32_t m = min((uint32_t)kRetU, t - t_lo);
+      float rr[kRetU];
+      uint8_t dd[kRetU];
+#pragma unroll
+      for (int j = 0; j < kRetU; ++j)
+        if ((uint32_t)j < m) {
+          const size_t o = (size_t)row_of(t - 1 - (uint32_t)j) * S + s;
+          rr[j] = __ldcg(d.r_rew + o);
+          dd[j] = __ldcg(d.r_done + o);
+        }
+#pragma unroll
+      for (int j = 0; j < kRetU; ++j)
+        if ((uint32_t)j < m) {
+          const bool dn = dd[j] != 0;
+          ret_update(rr[j], dn, g, bh, bl);
+          float ph, pl;
+          ff_mul(g, 0.f, ah, al, ph, pl);
+          ah = dn ? 0.f : ph;
+          al = dn ? 0.f : pl;
+        }
+      t -= m;
+    }
+  }
+  sA[seg][lane] = make_float2(ah, al);
+  sB[seg][lane] = make_float2(bh, bl);
+  __syncthreads();
+  if (seg == 0) {
+    float ch = 0.f, cl = 0.f;
+#pragma unroll 1
+    for (int j = NSEG - 1; j >= 0; --j) {
+      sC[j][lane] = make_float2(ch, cl);
+      const float2 a = sA[j][lane], b = sB[j][lane];
+      float ph, pl;
+      ff_mul(a.x, a.y, ch, cl, ph, pl);
+      ff_add(b.x, b.y, ph, pl, ch, cl);
+    }
+  }
+  __syncthreads();
+  if (!valid) return;
+  const float2 c = sC[seg][lane];
+  float hi = c.x, lo = c.y;
+  for (uint32_t t = t_hi; t > t_lo;) {
+    const uint32_t m = min((uint32_t)kRetU, t - t_lo);
+    float rr[kRetU];
+    uint8_t dd[kRetU];
+#pragma unroll
+    for (int j = 0; j < kRetU; ++j)
+      if ((uint32_t)j < m) {
+        const size_t o = (size_t)row_of(t - 1 - (uint32_t)j) * S + s;
+        rr[j] = __ldcs(d.r_rew + o);
+        dd[j] = __ldcs(d.r_done + o);
+      }
+#pragma unroll
+    for (int j = 0; j < kRetU; ++j)
+      if ((uint32_t)j < m) {
+        const size_t o = (size_t)row_of(t - 1 - (uint32_t)j) * S + s;
+        __stcs(d.r_ret + o, ret_update(rr[j], dd[j] != 0, g, hi, lo));
+      }
+    t -= m;
+  }
+}
+
 inline unsigned blocks(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -921,6 +1028,12 @@ void launch_plain_step(const Dev &d, uint32_t off, cudaStream_t st, const Branch
 void launch_advance(const Dev &d, uint32_t n, cudaStream_t st) { k_advance<<<1, 32, 0, st>>>(d, n); }
 
 void launch_returns(const Dev &d, uint32_t n_steps, cudaStream_t st) {
+  // few slots: the segmented scan (16 segments per slot keep the chip busy;
+  // 32 measured no faster on 8,192 slots x 1,000 steps)
+  if (d.n_slots < 32768 && n_steps >= 64) {
+    k_returns_seg<16><<<blocks(d.n_slots, 32), 32 * 16, 0, st>>>(d, n_steps);
+    return;
+  }
   if (d.n_slots % 4 == 0)  // every ring row starts on a 16-byte boundary
     k_returns<4, 32, 8><<<blocks(d.n_slots / 4, 32), 32, 0, st>>>(d, n_steps);
   else
