@@ -733,9 +733,9 @@ def main():
         # the ncu captures summarised under profiles/ (*_ncu_full_*.md), beside the
         # algorithmic record bytes of the launch (control 29 B, economy 85 B,
         # landscape 205 B per agent-step)
-        ncu_bytes = {"control_scale": (3.396608 + 135.428608) * 1e6,
-                     "economy": 92.359424e6 + 1.189169e9,
-                     "landscape": (1.788928 + 24.135424) * 1e6}
+        ncu_bytes = {"control_scale": (3.420672 + 135.461888) * 1e6,
+                     "economy": 92.860928e6 + 1.191251e9,
+                     "landscape": (1.827328 + 24.201472) * 1e6}
         rec_bytes = {0: 29.0, 1: 85.0, 2: 205.0, 3: 37.0}[wl["env"]]
         if args.workload in ncu_bytes:
             roofline["traffic"] = ncu_bytes[args.workload]
