@@ -51,10 +51,12 @@ constexpr int kMaxD = 24;                     // coordinates (a multiple of 8, <
 constexpr int kN3 = 48;                       // layer-3 N (2 D, padded to 48)
 constexpr int kK1 = 32;                       // layer-1 K: D coordinates, 1, 1, zeros
 constexpr int kKE = 80;                       // energy K: 3 D + 5 <= 80, five K16 steps
-constexpr int kBlk = 64;                      // Gaussians per energy MMA block
+constexpr int kBlk = 64;                      // Gaussians per block of the energy image
 constexpr int kBlkBytes = kBlk * kKE * 2;     // block image, K = 80 without swizzle
-constexpr int kNS = 3;                        // shared-memory block buffers
-constexpr int kNT = 8;                        // TMEM accumulators (all of TMEM during a sweep)
+constexpr int kEB = 128;                      // Gaussians per energy MMA of the roll-out sweep
+constexpr int kEBBytes = kEB * kKE * 2;       // two consecutive image blocks
+constexpr int kNS = 2;                        // shared-memory sweep-block buffers
+constexpr int kNT = 3;                        // TMEM accumulators of the sweep (128 columns each)
 constexpr int kHdr = 256;                     // energy image header: {blocks, positive blocks}
 constexpr int kEpi = 256, kThreads = kEpi + 64;  // + a loader warp and an MMA warp
 constexpr uint64_t kWaitNs = 2000000000ull;
@@ -70,9 +72,9 @@ constexpr int PK_B3 = PK_B2 + kH * 4;
 constexpr int POLICY = PK_B3 + 64 * 4;
 
 // shared memory
-constexpr int OFF_AE = POLICY;                    // energy A [128][80] (also the layer-1 A [128][32])
-constexpr int OFF_BE = OFF_AE + kRows * kKE * 2;  // kNS energy B blocks
-constexpr int OFF_XCH = OFF_BE + kNS * kBlkBytes; // f32 [128] each: partial energy, log-probability,
+constexpr int OFF_AE = POLICY;                    // layer-1 A [128][32] (the energy A is in TMEM)
+constexpr int OFF_BE = OFF_AE + kRows * kK1 * 2;  // kNS energy B blocks of kEB Gaussians
+constexpr int OFF_XCH = OFF_BE + kNS * kEBBytes;  // f32 [128] each: partial energy, log-probability,
                                                   // |y|^2 of half 0 and of half 1
 constexpr int OFF_RECV = OFF_XCH + 4 * kRows * 4; // f32 [2][128] the cluster partner's partials
 constexpr int OFF_BAR = OFF_RECV + 2 * kRows * 4;
@@ -86,9 +88,11 @@ static_assert(PK_W3 % 1024 == 0 && (4 * kN3 * 128) % 1024 == 0 && (kN3 * 128) % 
 static_assert(OFF_AE % 128 == 0 && OFF_BE % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
 
 constexpr uint32_t TM_H = 256;   // TMEM columns of h1 / h2 (packed BF16 A operand)
+constexpr uint32_t TM_A = 448;   // TMEM columns of the energy A operand [128][80] (BF16 pairs)
 constexpr uint32_t TM_E = 0;     // TMEM columns of the energy accumulators (during a sweep the
                                  // policy's columns are free)
-static_assert(TM_E + kNT * kBlk <= 512, "energy accumulators");
+static_assert(TM_E + kNT * kEB <= TM_A && TM_A + kKE / 2 <= 512, "energy accumulators and A");
+static_assert(TM_H + kH / 2 <= TM_A, "the policy's A operand below the energy A");
 
 __device__ __forceinline__ uint16_t bf16_bits(float f) {
   return (uint16_t)(tc::pack_bf16x2(f, 0.f) & 0xFFFFu);
@@ -136,9 +140,11 @@ __global__ void k_land_tc_pack_policy(const float *__restrict__ p, int D, uint8_
 // operand row [y_hi | y_hi | y_lo | 1, 1 | yy_hi, yy_hi, yy_lo | 0...] (yy = |y|^2):
 // the dot product is log2(|a_m| exp(-|y - c_m|^2 / (2 w_m^2))).  Gaussians with
 // a >= 0 fill the first blocks and those with a < 0 the rest (each group padded
-// to whole blocks), so that a block's sign is one flag; padding slots carry
-// s = -200 (2^-200 flushes to zero).
-inline int land_slots(int M) { return ((M + kBlk - 1) / kBlk + 3) * kBlk; }
+// to whole sweep blocks of kEB = 2 image blocks, the block count a multiple of 4
+// so that the two CTAs of a pair sweep whole sweep blocks), so that a sweep
+// block's sign is one flag; padding slots carry s = -200 (2^-200 flushes to
+// zero).  The header counts image blocks of 64.
+inline int land_slots(int M) { return ((M + kBlk - 1) / kBlk + 8) * kBlk; }
 inline size_t land_order_off() { return (size_t)kHdr; }
 inline size_t land_blocks_off(int M) { return kHdr + ((size_t)land_slots(M) * 4 + 255) / 256 * 256; }
 
@@ -161,8 +167,8 @@ __global__ void k_land_tc_order(const float *__restrict__ a, int M, int slots,
       p += cnt[i];
       n += len - cnt[i];
     }
-    const int pb = (p + kBlk - 1) / kBlk, nb = (n + kBlk - 1) / kBlk;
-    hdr[0] = (pb + nb + 1) / 2 * 2;
+    const int pb = (p + kEB - 1) / kEB * 2, nb = (n + kEB - 1) / kEB * 2;
+    hdr[0] = (pb + nb + 3) / 4 * 4;
     hdr[1] = pb;
     cnt[0] = pb * kBlk;  // first slot of the negative group
   }
@@ -298,6 +304,25 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
 __device__ __forceinline__ void tmem_wait_st() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
+// NC consecutive 32-bit TMEM columns of this thread's lane from registers.
+template <int NC>
+__device__ __forceinline__ void tmem_st_cols(uint32_t taddr, const uint32_t (&w)[NC]) {
+  int c = 0;
+#pragma unroll
+  for (; c + 4 <= NC; c += 4)
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr + c),
+                 "r"(w[c]), "r"(w[c + 1]), "r"(w[c + 2]), "r"(w[c + 3])
+                 : "memory");
+#pragma unroll
+  for (; c + 2 <= NC; c += 2)
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr + c), "r"(w[c]),
+                 "r"(w[c + 1])
+                 : "memory");
+#pragma unroll
+  for (; c < NC; ++c)
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr + c), "r"(w[c])
+                 : "memory");
+}
 // D[tmem] (+)= A[tmem] * B[smem]^T (A: 128 lanes, two bf16 per column).
 __device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
                                       uint32_t idesc, bool acc) {
@@ -415,9 +440,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t N = d.n_envs;
   const int n_tiles = (int)((N + kRows - 1) / kRows);
   const int n_clus = (int)gridDim.x / CL, cid = (int)blockIdx.x / CL;
-  const int n_blk = ((const int32_t *)eimg)[0] / CL;  // this CTA's blocks per sweep
-  const int nb_pos = ((const int32_t *)eimg)[1];       // blocks before the first a < 0 block
-  const int blk0 = (int)rank * n_blk;                  // this CTA's first block
+  // in sweep blocks of kEB Gaussians (two image blocks each)
+  const int n_blk = ((const int32_t *)eimg)[0] / 2 / CL;  // this CTA's blocks per sweep
+  const int nb_pos = ((const int32_t *)eimg)[1] / 2;       // blocks before the first a < 0 block
+  const int blk0 = (int)rank * n_blk;                      // this CTA's first block
   const uint64_t wlim = d.wait_ns;
   bool fail = false;
 
@@ -435,7 +461,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int lane = tid & 31;
     if (warp == kEpi / 32) {
       if (lane == 0) {
-        const uint8_t *src0 = blocks + (size_t)blk0 * kBlkBytes;
+        const uint8_t *src0 = blocks + (size_t)blk0 * kEBBytes;
         uint32_t gl = 0;
         for (;;) {
           if (gl >= (uint32_t)kNS) {  // the MMA of block gl - kNS has read its buffer, or the end
@@ -458,9 +484,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!got) break;
           }
           const uint32_t sbuf = gl % kNS;
-          mbar_expect_tx(bar_b + sbuf, kBlkBytes);
-          bulk_g2s(sb + OFF_BE + sbuf * kBlkBytes, src0 + (size_t)(gl % (uint32_t)n_blk) * kBlkBytes,
-                   kBlkBytes, bar_b + sbuf);
+          mbar_expect_tx(bar_b + sbuf, kEBBytes);
+          bulk_g2s(sb + OFF_BE + sbuf * kEBBytes, src0 + (size_t)(gl % (uint32_t)n_blk) * kEBBytes,
+                   kEBBytes, bar_b + sbuf);
           ++gl;
         }
         *s_gl = gl;
@@ -470,7 +496,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
       uint32_t g = 0;
       if (lane == 0) {
-        constexpr uint32_t idesc = tc::idesc_bf16_f32(128, kBlk);
+        constexpr uint32_t idesc = tc::idesc_bf16_f32(128, kEB);
         uint32_t pa = 0;
         while (!fail) {
           if (!tc::mbar_wait(bar_ae, pa, wlim)) { fail = true; break; }
@@ -484,11 +510,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc::fence_after_sync();
 #pragma unroll
             for (int s = 0; s < kKE / 16; ++s) {
-              const uint64_t da = tc::smem_desc(sb + OFF_AE + (uint32_t)s * 256u, 128, kKE * 16,
-                                                tc::kSwizzleNone);
-              const uint64_t db = tc::smem_desc(sb + OFF_BE + sbuf * kBlkBytes + (uint32_t)s * 256u,
+              const uint64_t db = tc::smem_desc(sb + OFF_BE + sbuf * kEBBytes + (uint32_t)s * 256u,
                                                 128, kKE * 16, tc::kSwizzleNone);
-              tc::mma_bf16(tbase + TM_E + t * kBlk, da, db, idesc, s != 0);
+              mma_ts(tbase + TM_E + t * kEB, tbase + TM_A + (uint32_t)(8 * s), db, idesc, s != 0);
             }
             tc::mma_commit(bar_mma + t);
           }
@@ -541,7 +565,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t recv_remote = CL > 1 ? mapa(sb + OFF_RECV, partner) : 0u;
     const uint32_t barx_remote = CL > 1 ? mapa(tc::smem_u32(bar_x), partner) : 0u;
     const uint32_t a1_row = sb + OFF_AE + (uint32_t)(r >> 3) * (kK1 * 16) + (uint32_t)(r & 7) * 16u;
-    const uint32_t ae_row = sb + OFF_AE + (uint32_t)(r >> 3) * (kKE * 16) + (uint32_t)(r & 7) * 16u;
+    const uint32_t ae_tm = tbase + lane_sel + TM_A;  // this row's energy operand (TMEM lane r)
     // byte offset of element k within a row of a K-major operand without swizzle
     auto kofs = [](int k) -> uint32_t { return (uint32_t)((k >> 3) * 128 + (k & 7) * 2); };
 
@@ -550,38 +574,47 @@ __global__ void __launch_bounds__(kThreads, 1)
     // and on both CTAs of a pair).
     auto sweep = [&]() -> float {
       if (tid == 0) *cmd = 1u;
-      tc::fence_async_smem();
+      tmem_wait_st();  // the operand rows are in tensor memory before the MMAs read them
+      tc::fence_before_sync();
       mbar_arrive(bar_ae);
-      // Half h evaluates the blocks of parity h, all 64 columns of each, so that
+      // Half h evaluates the blocks of parity h, all kEB columns of each, so that
       // the two warps of an SMSP work on different blocks (one's TMEM load and
       // waits overlap the other's exponentials).  A block holds Gaussians of one
-      // sign; the two signs are summed apart.
-      // The loads are pipelined: a block's second 32 columns load while its
-      // first 32 are exponentiated, and the next block's first 32 while its
-      // second 32 are (two 32-register buffers).
+      // sign; the two signs are summed apart.  The loads are pipelined over the
+      // block's four 32-column chunks: each chunk loads while the one before it
+      // is exponentiated (two 32-register buffers), the next block's first
+      // chunk while the last is.
       float ap = 0.f, an = 0.f;
       uint32_t za[32], zb[32];
+      const uint32_t tm_e = tbase + lane_sel + TM_E;
       if (h < n_blk) {
         const uint32_t gb = ge + (uint32_t)h, t = gb % kNT;
         wait(bar_mma + t, (gb / kNT) & 1u);
         tc::fence_after_sync();
-        tc::tmem_ld32(tbase + lane_sel + TM_E + t * kBlk, za);
+        tc::tmem_ld32(tm_e + t * kEB, za);
         tmem_wait_ld_regs(za);
       }
       for (int i = h; i < n_blk; i += 2) {
         const uint32_t gb = ge + (uint32_t)i, t = gb % kNT;
-        tc::tmem_ld32(tbase + lane_sel + TM_E + t * kBlk + 32u, zb);
+        const uint32_t col = tm_e + t * kEB;
         float sv[4] = {0.f, 0.f, 0.f, 0.f};
+        tc::tmem_ld32(col + 32u, zb);
+        ex2_sum32(za, sv);
+        tmem_wait_ld_regs(zb);
+        tc::tmem_ld32(col + 64u, za);
+        ex2_sum32(zb, sv);
+        tmem_wait_ld_regs(za);
+        tc::tmem_ld32(col + 96u, zb);
         ex2_sum32(za, sv);
         tmem_wait_ld_regs(zb);
         tc::fence_before_sync();
-        mbar_arrive(bar_epi + t);
+        mbar_arrive(bar_epi + t);  // the accumulator is read out
         const int in = i + 2;
         if (in < n_blk) {
           const uint32_t gn = ge + (uint32_t)in, tn = gn % kNT;
           wait(bar_mma + tn, (gn / kNT) & 1u);
           tc::fence_after_sync();
-          tc::tmem_ld32(tbase + lane_sel + TM_E + tn * kBlk, za);
+          tc::tmem_ld32(tm_e + tn * kEB, za);
         }
         ex2_sum32(zb, sv);
         if (in < n_blk) tmem_wait_ld_regs(za);
@@ -612,27 +645,25 @@ __global__ void __launch_bounds__(kThreads, 1)
       return E;
     };
     // The energy operand row [v_hi | v_hi | v_lo | 1, 1 | vv_hi, vv_hi, vv_lo | 0]
-    // (K = 80): each half writes its coordinates in pieces of four; after the
-    // two halves' sums of squares meet, half 1 writes the constant and |v|^2
-    // columns and the zero tail.  lp (half 1's log-probability part) rides along
-    // to half 0.
+    // (K = 80) in tensor memory, the A operand of the sweep's MMAs: element k in
+    // column k / 2 of the row's lane (the lower k in the low half).  Each half
+    // writes its coordinates' columns of the three copies; after the two halves'
+    // sums of squares meet, half 1 writes the constant and |v|^2 columns and the
+    // zero tail.  lp (half 1's log-probability part) rides along to half 0.
     auto write_ae = [&](const float (&v)[DH], float lp_part) {
       float yy = 0.f;
+      uint32_t hw[DH / 2], lw[DH / 2];
 #pragma unroll
-      for (int q = 0; q < DH / 4; ++q) {
-        const float a0 = v[4 * q], a1 = v[4 * q + 1], a2 = v[4 * q + 2], a3 = v[4 * q + 3];
+      for (int q = 0; q < DH / 2; ++q) {
+        const float a0 = v[2 * q], a1 = v[2 * q + 1];
         yy = fmaf(a0, a0, yy);
         yy = fmaf(a1, a1, yy);
-        yy = fmaf(a2, a2, yy);
-        yy = fmaf(a3, a3, yy);
-        const uint32_t h01 = tc::pack_bf16x2(a0, a1), h23 = tc::pack_bf16x2(a2, a3);
-        const uint32_t l01 = tc::pack_bf16x2(a0 - tc::bf16_lo(h01), a1 - tc::bf16_hi(h01));
-        const uint32_t l23 = tc::pack_bf16x2(a2 - tc::bf16_lo(h23), a3 - tc::bf16_hi(h23));
-        const int j = j0 + 4 * q;
-        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(ae_row + kofs(j)), "r"(h01), "r"(h23) : "memory");
-        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(ae_row + kofs(D + j)), "r"(h01), "r"(h23) : "memory");
-        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(ae_row + kofs(2 * D + j)), "r"(l01), "r"(l23) : "memory");
+        hw[q] = tc::pack_bf16x2(a0, a1);
+        lw[q] = tc::pack_bf16x2(a0 - tc::bf16_lo(hw[q]), a1 - tc::bf16_hi(hw[q]));
       }
+      tmem_st_cols<DH / 2>(ae_tm + (uint32_t)(j0 / 2), hw);
+      tmem_st_cols<DH / 2>(ae_tm + (uint32_t)((D + j0) / 2), hw);
+      tmem_st_cols<DH / 2>(ae_tm + (uint32_t)((2 * D + j0) / 2), lw);
       if (!own) xch_lp[r] = lp_part;
       xch_yy[h * kRows + r] = yy;
       bar_sync_n(pair, 64);
@@ -640,13 +671,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float vv = xch_yy[r] + xch_yy[kRows + r];
         const uint32_t hv = tc::pack_bf16x2(vv, 0.f) & 0xFFFFu;
         const uint32_t lv = tc::pack_bf16x2(vv - __uint_as_float(hv << 16), 0.f) & 0xFFFFu;
+        constexpr int NT = kKE / 2 - 3 * D / 2;  // [1, 1 | vv_hi, vv_hi | vv_lo, 0 | 0 ...]
+        uint32_t tw[NT];
 #pragma unroll
-        for (int c = 3 * D / 8; c < kKE / 8; ++c) {
-          if (c == 3 * D / 8)  // [1, 1, vv_hi, vv_hi, vv_lo, 0, 0, 0]
-            tc::sts128(ae_row + (uint32_t)c * 128u, tc::pack_bf16x2(1.f, 1.f), hv | (hv << 16), lv, 0u);
-          else
-            tc::sts128(ae_row + (uint32_t)c * 128u, 0u, 0u, 0u, 0u);
-        }
+        for (int c = 0; c < NT; ++c) tw[c] = 0u;
+        tw[0] = tc::pack_bf16x2(1.f, 1.f);
+        tw[1] = hv | (hv << 16);
+        tw[2] = lv;
+        tmem_st_cols<NT>(ae_tm + (uint32_t)(3 * D / 2), tw);
       }
     };
 
