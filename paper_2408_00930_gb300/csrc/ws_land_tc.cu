@@ -26,9 +26,12 @@
 //            q |c|^2 + log2|a|, q], every product split BF16 hi+lo (FP32
 //            accumulate).  The Gaussians are grouped by the sign of a_m, so the
 //            epilogue is one ex2 per pair summed into a positive and a negative
-//            part.  Blocks of 64 Gaussians stream through three shared-memory
-//            buffers (a loader warp) into eight TMEM accumulators (an MMA warp);
-//            the two threads of a row take the blocks of even and odd index.
+//            part (each sign group padded to 128 Gaussians).  The operand row
+//            sits in tensor memory as the A operand; blocks of 128 Gaussians
+//            stream through two shared-memory buffers (a loader warp) into
+//            three 128-column TMEM accumulators (an MMA warp, one M = 128,
+//            N = 128 MMA per K step); the two threads of a row take the
+//            blocks of even and odd index.
 //   step     observed energy with Philox noise, reward Eobs(x) - Eobs(x'), done
 //            at the episode limit or when E(y) falls below the energy target
 //            (the product basin of App. C), reset to U(-3, 3)^D and a second
