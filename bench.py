@@ -330,7 +330,7 @@ def run_gpu(args, wl, world, rank, local):
     if path == W.WS_PATH_BATCHED_BF16:
         sfu_rates = probe_rates(local, ops=("tanh.approx.f32", "ex2.approx.ftz.f32",
                                             "sin.approx.ftz.f32", "lg2.approx.ftz.f32",
-                                            "rsqrt.approx.ftz.f32"))
+                                            "rsqrt.approx.ftz.f32", "fma.rn.f32"))
     main = one_path(path, args.steps, args.warmup, True)
     main["sfu_rates"] = sfu_rates
     r = main["rollout"]
@@ -694,12 +694,16 @@ def main():
 
         def teq(**ops):
             return sum(n * w[k] for k, n in ops.items())
+        lc = main_res.get("launch") or {}
+        cc = wl["env"] in (0, 3) and lc.get("ctrl_envs_per_cta", 0)
+        ctrl_kern = (f"ws_control_cc (CUDA cores, {lc.get('ctrl_envs_per_cta')} envs per CTA, "
+                     f"{lc.get('ctrl_threads_per_env')} threads per env)" if cc else "ws_control_tc")
         if wl["env"] == 0:
             per_step = n_slots * teq(tanh=H, ex2=2, lg2=1)
-            op, kern = "tanh (and the softmax's ex2, lg2) on the SFU", "ws_control_tc"
+            op, kern = "tanh (and the softmax's ex2, lg2) on the SFU", ctrl_kern
         elif wl["env"] == 3:
             per_step = n_slots * teq(tanh=H, ex2=3, lg2=1, sin=22)
-            op, kern = "tanh, ex2, lg2, sin, cos on the SFU", "ws_control_tc (acrobot)"
+            op, kern = "tanh, ex2, lg2, sin, cos on the SFU", ctrl_kern + " (acrobot)"
         elif wl["env"] == 1:
             n_pl = wl["n_envs"]
             per_step = ((n_slots - n_pl) * teq(tanh=H, ex2=20, lg2=2)
@@ -726,6 +730,17 @@ def main():
                     "tensor": {k: tensor[k] for k in ("achieved", "peak", "unit", "frac",
                                                       "peak_source")}}
         roofline["frac"] = roofline["achieved"] / roofline["peak"]
+        if cc:
+            # the CUDA-core kernel runs the policy GEMMs as FP32 FMAs: one per
+            # multiply-add of the three layers, against the measured FMA rate
+            r_f = rates.get("fma.rn.f32", 124.0) if rates else 124.0
+            fma_launch = flops_per_agent_step(wl) / 2 * n_slots * launch_steps
+            roofline["fma"] = {"achieved": fma_launch / (launch_ms * 1e-3) / 1e12,
+                               "peak": r_f * n_sms * sm_mhz * 1e6 / 1e12, "unit": "T FMA/s",
+                               "peak_source": f"fma.rn.f32 {r_f:.1f} / clock / SM x {n_sms} SMs x "
+                                              f"{sm_mhz:.0f} MHz"}
+            roofline["fma"]["frac"] = roofline["fma"]["achieved"] / roofline["fma"]["peak"]
+            roofline.pop("tensor", None)
     else:
         roofline = dict(tensor, traffic=None, kernel="plain per-step kernels")
     if bf16 and not args.horizon and not args.n_envs:

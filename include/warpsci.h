@@ -359,6 +359,21 @@ typedef struct {
                               tensor memory and leave, and ws_sync reports a
                               sticky WS_ERR_TIMEOUT naming the wait's site.  For
                               tests of that path; results do not depend on it    */
+  uint32_t ctrl_envs_per_cta; /* BF16 control / acrobot with hidden widths 64-64 or
+                              128-128: 0 = the tensor-core kernel (128-env tiles,
+                              two threads per env); else the CUDA-core kernels,
+                              for env counts that leave SMs idle under 128-env
+                              tiles, with this many envs per CTA (see
+                              ctrl_threads_per_env).  They round the same
+                              operands to BF16 (W2, h1) and accumulate in FP32;
+                              their records do not depend on the two ctrl_
+                              fields                                            */
+  uint32_t ctrl_threads_per_env; /* CUDA-core kernels: 4, 8 or 16 = GEMM register
+                              tiles of 16 / this envs x H / 16 units per thread,
+                              W2 in shared memory (ctrl_envs_per_cta 4, 8, 16 or
+                              32; 64..512 threads per CTA); 64 = one thread per
+                              hidden unit with its W2 column in registers (hidden
+                              width 64; ctrl_envs_per_cta 1, 2, 4 or 8)          */
 } ws_launch;
 
 /* The context's current launch configuration. */

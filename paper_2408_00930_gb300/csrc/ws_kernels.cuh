@@ -130,6 +130,12 @@ cudaError_t launch_control_tc(const Dev &d, const void *packed, uint32_t n_steps
                               cudaStream_t st);
 int control_tc_default_grid(const Dev &d);
 
+// ---- CUDA-core control path for small env counts (ws_control_cc.cu) ----------
+bool control_cc_supported(const PolicyShape &shape);
+bool control_cc_tile_ok(const PolicyShape &shape, int envs_per_cta, int threads_per_env);
+cudaError_t launch_control_cc(const Dev &d, uint32_t n_steps, int envs_per_cta, int threads_per_env,
+                              cudaStream_t st);
+
 }  // namespace ws
 
 namespace ws {

@@ -503,6 +503,8 @@ void default_launch(ws_ctx *c) {
   // fused landscape: a CTA pair per tile while the pairs fit the SMs at once
   const uint32_t tiles = (c->L.n_envs + 127) / 128;
   l.tile_ctas = 2 * tiles <= (uint32_t)sm_count() ? 2u : 1u;
+  l.ctrl_envs_per_cta = 0;  // the tensor-core kernel
+  l.ctrl_threads_per_env = 8;
 }
 
 // The fused kernels' device-wait limit of a launch configuration (0 = 2 s).
@@ -533,9 +535,15 @@ ws_status enqueue_steps(ws_ctx *c, uint32_t n, cudaStream_t st) {
     const uint32_t chunk = chunk_of(c);
     for (uint32_t done = 0; done < n;) {
       const uint32_t m = (n - done) < chunk ? (n - done) : chunk;
-      const int grid = c->lc.grid ? (int)c->lc.grid : c->tc_grid;
-      cudaError_t e = launch_control_tc(c->d, c->state + c->L.packed_off, m, grid, st);
-      if (e != cudaSuccess) return cuda_check(c, e, "control_tc launch");
+      cudaError_t e;
+      if (c->lc.ctrl_envs_per_cta) {
+        e = launch_control_cc(c->d, m, (int)c->lc.ctrl_envs_per_cta,
+                              (int)c->lc.ctrl_threads_per_env, st);
+      } else {
+        const int grid = c->lc.grid ? (int)c->lc.grid : c->tc_grid;
+        e = launch_control_tc(c->d, c->state + c->L.packed_off, m, grid, st);
+      }
+      if (e != cudaSuccess) return cuda_check(c, e, "control kernel launch");
       launch_advance(c->d, m, st);
       done += m;
     }
@@ -1147,6 +1155,13 @@ ws_status ws_set_launch(ws_ctx *c, const ws_launch *l) {
     return WS_ERR_INVALID;
   if (l->env_threads < 64 || l->env_threads > 1024 || l->env_threads % 32) return WS_ERR_INVALID;
   if (l->tile_ctas != 1 && l->tile_ctas != 2) return WS_ERR_INVALID;
+  const uint32_t tpe = l->ctrl_threads_per_env;
+  if (tpe != 4 && tpe != 8 && tpe != 16 && tpe != 64) return WS_ERR_INVALID;
+  if (l->ctrl_envs_per_cta > 32) return WS_ERR_INVALID;
+  if (l->ctrl_envs_per_cta && use_tc_control(&c->cfg) &&
+      (!control_cc_supported(c->L.pol) ||
+       !control_cc_tile_ok(c->L.pol, (int)l->ctrl_envs_per_cta, (int)tpe)))
+    return WS_ERR_INVALID;
   const ws_launch old = c->lc;
   c->lc = *l;
   drop_graphs(c);  // graphs bake the launch parameters in
@@ -1222,6 +1237,15 @@ std::vector<ws_launch> tune_candidates(const ws_ctx *c, uint32_t trial) {
       if (energy_tc_chunks_ok((int)c->cfg.n_gauss, (int)e)) echunks.push_back(e);
   }
   if (!fused(c)) threads = {128u, 256u, 512u};
+  // classic-control kernel choice: {0, -} the tensor-core tiles, else the
+  // CUDA-core kernel's (envs per CTA, envs per thread); offered while 128-env
+  // tiles would leave most SMs idle
+  std::vector<std::pair<uint32_t, uint32_t>> ctrl{{0u, c->lc.ctrl_threads_per_env}};
+  if (use_tc_control(&c->cfg) && control_cc_supported(c->L.pol) &&
+      c->L.n_envs <= 256u * (uint32_t)sm_count())
+    for (uint32_t ne : {1u, 2u, 4u, 8u, 16u, 32u})
+      for (uint32_t tpe : {4u, 8u, 16u, 64u})
+        if (control_cc_tile_ok(c->L.pol, (int)ne, (int)tpe)) ctrl.push_back({ne, tpe});
   std::vector<ws_launch> v;
   for (uint32_t ch : chunks)
     for (uint32_t g : grids)
@@ -1238,7 +1262,12 @@ std::vector<ws_launch> tune_candidates(const ws_ctx *c, uint32_t trial) {
               l.econ_lpt = lp;
               l.energy_chunks = ec;
               l.env_threads = th;
-              v.push_back(l);
+              for (const auto &cc : ctrl) {
+                if (cc.first && g) continue;  // the CUDA-core kernel has no grid knob
+                l.ctrl_envs_per_cta = cc.first;
+                l.ctrl_threads_per_env = cc.second;
+                v.push_back(l);
+              }
             }
   return v;
 }
