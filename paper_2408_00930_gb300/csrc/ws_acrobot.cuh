@@ -6,9 +6,10 @@
 
 namespace ws {
 
-// sin / cos for the physics.  FAST (the fused BF16 kernel): the SFU's
+// sin / cos for the physics.  FAST (the fused BF16 kernels): the SFU's
 // approximate sin and cos after reducing the argument to [-pi, pi] with
-// x - 2 pi rint(x / 2 pi); else CUDA's accurate functions (the FP32 paths).
+// x - 2 pi rint(x / 2 pi), and approximate divisions; else CUDA's accurate
+// functions and IEEE division (the FP32 paths).
 template <bool FAST>
 __device__ __forceinline__ void acro_sincos(float x, float *s, float *c) {
   if (FAST) {
@@ -30,6 +31,13 @@ __device__ __forceinline__ float acro_cos(float x) {
   return cosf(x);
 }
 
+// a / b: FAST the approximate division (two ulp, the SFU's reciprocal and one
+// product); else IEEE division.
+template <bool FAST>
+__device__ __forceinline__ float acro_div(float a, float b) {
+  return FAST ? __fdividef(a, b) : a / b;
+}
+
 // Two-link acrobot of Sutton & Barto (paper App. C, classic control), book
 // dynamics: m1 = m2 = l1 = I1 = I2 = 1, lc1 = lc2 = 0.5, g = 9.8, angles from
 // hanging down, torque tau on the second joint.
@@ -44,9 +52,9 @@ __device__ __forceinline__ void acro_accel(float th1, float th2, float w1, float
   const float phi2 = m2 * lc2 * g * acro_sin<FAST>(th1 + th2);
   const float phi1 = -m2 * l1 * lc2 * w2 * w2 * s2 - 2.f * m2 * l1 * lc2 * w2 * w1 * s2 +
                      (m1 * lc1 + m2 * l1) * g * acro_sin<FAST>(th1) + phi2;
-  acc2 = (tau + d2 / d1 * phi1 - m2 * l1 * lc2 * w1 * w1 * s2 - phi2) /
-         (m2 * lc2 * lc2 + I2 - d2 * d2 / d1);
-  acc1 = -(d2 * acc2 + phi1) / d1;
+  acc2 = acro_div<FAST>(tau + acro_div<FAST>(d2, d1) * phi1 - m2 * l1 * lc2 * w1 * w1 * s2 - phi2,
+                        m2 * lc2 * lc2 + I2 - acro_div<FAST>(d2 * d2, d1));
+  acc1 = acro_div<FAST>(-(d2 * acc2 + phi1), d1);
 }
 
 // One classic RK4 step of dt with tau held; angles wrapped into [-pi, pi],

@@ -11,7 +11,8 @@
 // Work split: a CTA holds two groups of 256 threads; each group owns a tile of
 // 128 envs and 256 of the CTA's 512 TMEM columns.  Env row r of a tile is served
 // by two threads ("halves" h = 0, 1; both in warps that may reach TMEM lane r),
-// which split the row's hidden units by 64-unit blocks.  Per step and tile:
+// which split the row's hidden units by 64-unit blocks (by 32-unit halves of a
+// 64-unit layer).  Per step and tile:
 //   layer 1  z1 = o W1 + b1 on the tensor core, K = 16 (acrobot 32): the
 //            operand row [o_hi, o_lo, o_hi, 1, 1, 0...] against [W1_hi; W1_hi;
 //            W1_lo; b1_hi; b1_lo] keeps FP32-level accuracy (missing term
@@ -207,10 +208,23 @@ __device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, ui
       : "memory");
 }
 
-// tanh of 64 accumulator columns at taddr, packed bf16x2 (two 32-column loads).
-__device__ __forceinline__ void tanh_block64(uint32_t taddr, uint32_t (&hp)[32]) {
+// 16 consecutive 32-bit TMEM columns of this thread's lane from registers.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15])
+      : "memory");
+}
+
+// tanh of NC (32 or 64) accumulator columns at taddr, packed bf16x2 (32-column
+// loads).
+template <int NC>
+__device__ __forceinline__ void tanh_block(uint32_t taddr, uint32_t (&hp)[NC / 2]) {
 #pragma unroll
-  for (int half = 0; half < 2; ++half) {
+  for (int half = 0; half < NC / 32; ++half) {
     uint32_t z[32];
     tc::tmem_ld32(taddr + half * 32, z);
     tc::tmem_wait_ld();
@@ -242,18 +256,18 @@ __device__ __forceinline__ float4 lds128f(uint32_t addr) {
   return v;
 }
 
-// Layer 3 over one 64-unit block: tanh of the block's z2 columns (FP32 SFU
+// Layer 3 over one block of NC (32 or 64) units: tanh of the block's z2 columns (FP32 SFU
 // tanh; the same SFU rate per value as the packed bf16x2 form, and no packing)
 // against W3 in FP32.  acc0 / acc1 / acc2 hold (even-unit, odd-unit) partial
 // sums of logits 0 / 1 / 2; w3 holds the block's unit pairs (W3P bytes each:
 // float4 {W3[k][0], W3[k+1][0], W3[k][1], W3[k+1][1]}, k even, then for three
 // actions float4 {W3[k][2], W3[k+1][2], 0, 0}).
-template <int NA>
+template <int NA, int NC>
 __device__ __forceinline__ void layer3_block(uint32_t taddr, uint32_t w3, uint64_t &acc0,
                                              uint64_t &acc1, uint64_t &acc2) {
   constexpr uint32_t W3P = NA == 2 ? 16u : 32u;
 #pragma unroll
-  for (int half = 0; half < 2; ++half) {
+  for (int half = 0; half < NC / 32; ++half) {
     uint32_t z[32];
     tc::tmem_ld32(taddr + half * 32, z);
     tc::tmem_wait_ld();
@@ -482,13 +496,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       // (and the pair barrier orders those reads) before anything is written.
       if (C::KB == 4) {
         uint32_t hp[32];
-        tanh_block64(tmem + lane + (uint32_t)((h + 2) * 64), hp);
+        tanh_block<64>(tmem + lane + (uint32_t)((h + 2) * 64), hp);
         pair_sync(pair_id);
         tmem_st32(a_tm + lane + (uint32_t)((h + 2) * 32), hp);
       }
-      if (h < C::KB) {
+      if (C::KB == 1) {
+        // 64 units: each half takes 32 (the SFU work of a row on both threads)
+        uint32_t hp[16];
+        tanh_block<32>(tmem + lane + (uint32_t)(h * 32), hp);
+        tmem_st16(a_tm + lane + (uint32_t)(h * 16), hp);
+      } else if (h < C::KB) {
         uint32_t hp[32];
-        tanh_block64(tmem + lane + (uint32_t)(h * 64), hp);
+        tanh_block<64>(tmem + lane + (uint32_t)(h * 64), hp);
         tmem_st32(a_tm + lane + (uint32_t)(h * 32), hp);
       }
       tmem_wait_st();
@@ -537,10 +556,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         ph_l2 ^= 1u;
         tc::fence_after_sync();
         tok_take(tok, wlim);
-        if (h < C::KBP)
-          layer3_block<E::NA>(tmem + lane + (uint32_t)(h * 64),
-                              w3s + (uint32_t)((p * C::NPW + h * 64) / 2 * C::W3P), acc0, acc1,
-                              acc2);
+        if (C::NPW == 64)  // 64 units per pass: each half takes 32
+          layer3_block<E::NA, 32>(tmem + lane + (uint32_t)(h * 32),
+                                  w3s + (uint32_t)((p * C::NPW + h * 32) / 2 * C::W3P), acc0, acc1,
+                                  acc2);
+        else if (h < C::KBP)
+          layer3_block<E::NA, 64>(tmem + lane + (uint32_t)(h * 64),
+                                  w3s + (uint32_t)((p * C::NPW + h * 64) / 2 * C::W3P), acc0,
+                                  acc1, acc2);
         tok_give(tok);
       }
       const float2 pa = unf2(acc0), pb = unf2(acc1), pc = unf2(acc2);
