@@ -21,7 +21,9 @@
 //       draw, env step, reward, done, auto-reset, the time-major record write
 //       and the next observation; meanwhile two threads per env of another warp
 //       draw the next step's action uniform and reset words (Philox, double-
-//       buffered by step parity), so that the draws leave the env lanes' chain.
+//       buffered by step parity) and, for the control env, take sin / cos of the
+//       next pole angle (the Euler step of the angle does not depend on the
+//       action), so that neither is on the env lanes' chain.
 // Two work splits ("threads per env", a launch parameter):
 //   tiled (4, 8 or 16 threads per env)  16 unit groups of H / 16 consecutive
 //       hidden units times NE / RE env groups of RE = 16 / threads-per-env envs;
@@ -35,12 +37,13 @@
 //       the SM's throughput, decides; the first lane of each group of four units
 //       forms the group's partial, the butterfly runs over those lanes inside
 //       each of the env's two warps, and the env lane adds the two warps' sums
-// Both run every accumulation in one fixed order: z from the bias over k in
-// order; per unit group of H / 16 units the layer-3 partial as an FMA chain over
-// its units from zero; the 16 group partials summed in the butterfly's pairing
-// (group g with g ^ 1, then g ^ 2, g ^ 4, g ^ 8).  Every split and every NE
-// therefore gives bit-identical records.  No device waits beyond the CTA
-// barriers.
+// Both run every accumulation in one fixed order: z1 from b1 over the inputs in
+// order; z2 as two chains in k order (from b2 over the first half of k, from
+// zero over the second) added; per unit group of H / 16 units the layer-3
+// partial as an FMA chain over its units from zero; the 16 group partials summed
+// in the butterfly's pairing (group g with g ^ 1, then g ^ 2, g ^ 4, g ^ 8).
+// Every split and every NE therefore gives bit-identical records.  No device
+// waits beyond the CTA barriers.
 #include "ws_acrobot.cuh"
 #include "ws_kernels.cuh"
 #include "ws_tc.cuh"
@@ -63,6 +66,7 @@ template <typename E>
 struct Lane {
   float x = 0.f, v = 0.f, th = 0.f, w = 0.f;  // acrobot: (th1, th2, w1, w2)
   int tep = 0;
+  bool fresh = true;  // the state is not the Euler step of the last one (start, reset)
   float ob[E::OBS] = {};
 };
 
@@ -151,7 +155,7 @@ __device__ __forceinline__ void lane_step(const Dev &d, Lane<E> &s, float l0, fl
     const float thacc = 9.8f * sin_th - 0.3f * cos_th * uf;
     ns[0] = s.x + 0.02f * s.v;
     ns[1] = s.v + 0.02f * xacc;
-    ns[2] = s.th + 0.02f * s.w;
+    ns[2] = __fmaf_rn(0.02f, s.w, s.th);  // the draw lanes predict sin / cos of this
     ns[3] = s.w + 0.02f * thacc;
     rew = 1.0f;
     done = fabsf(ns[0]) > 2.4f || fabsf(ns[2]) > 0.21f || t2 >= (int)d.episode_limit;
@@ -173,6 +177,7 @@ __device__ __forceinline__ void lane_step(const Dev &d, Lane<E> &s, float l0, fl
       if (ACRO) po[2 * (size_t)S] = l2;
     }
   }
+  s.fresh = done;
   if (done) {
     const float lim = ACRO ? 0.1f : 0.05f;
     s.x = uniform(rr[0], -lim, lim);
@@ -195,22 +200,66 @@ __host__ __device__ constexpr int draw_lane0(int ne) { return 32 * ((ne + 31) / 
 
 // Draw lane i = slot - draw_lane0(NE) < 2 NE: the action uniform (i < NE) or the
 // reset words (i >= NE) of step k for env base + i % NE, one Philox block each
-// (the same instructions on every lane of the warp).
+// (the same instructions on every lane of the warp).  For the control env the
+// lanes also take sin / cos of the next pole angle th + 0.02 w (the Euler step
+// does not depend on the action; (th, w) read during P3), into sc[0 .. 2 NE):
+// the env lane uses them unless its env was reset.
 __device__ __forceinline__ void draw_lanes(const Dev &d, int slot, int NE, uint32_t base, uint32_t k,
-                                           float *us, uint32_t *rrs) {
+                                           float *us, uint32_t *rrs, bool trig = false,
+                                           float th = 0.f, float w = 0.f, float *sc = nullptr) {
   const int i = slot - draw_lane0(NE);
   if (i < 0 || i >= 2 * NE) return;
   const bool act = i < NE;
   const int q = act ? i : i - NE;
   const uint4 r = draw(d.seed, k, d.env_base + base + (uint32_t)q, 0, act ? kTagAction : kTagReset, 0);
+  float sn = 0.f, cs = 0.f;
+  if (trig) {
+    const float th1 = __fmaf_rn(0.02f, w, th);
+    sn = sinf(th1);
+    cs = cosf(th1);
+  }
   if (act) {
     us[q] = u01(r.x);
+    if (trig) {
+      sc[q] = sn;
+      sc[NE + q] = cs;
+    }
   } else {
     uint32_t *o = rrs + q;
     o[0] = r.x;
     o[NE] = r.y;
     o[2 * NE] = r.z;
     o[3 * NE] = r.w;
+  }
+}
+
+// The pole angle and velocity of a draw lane's env (control env; read during
+// P3, while xo holds this step's observations).
+template <typename E>
+__device__ __forceinline__ void draw_lane_state(int slot, int NE, const float *xo, float &th,
+                                                float &w) {
+  th = w = 0.f;
+  const int i = slot - draw_lane0(NE);
+  if (E::NA == 3 || i < 0 || i >= 2 * NE) return;
+  const int q = i < NE ? i : i - NE;
+  th = xo[2 * NE + q];
+  w = xo[3 * NE + q];
+}
+
+// sin / cos of the env lane's pole angle: the draw lanes' prediction, or its
+// own after a start or a reset.
+template <typename E>
+__device__ __forceinline__ void lane_trig(const Lane<E> &s, const float *sc, int NE, int q,
+                                          float &sn, float &cs) {
+  sn = cs = 0.f;
+  if constexpr (E::NA == 2) {
+    if (s.fresh) {
+      sn = sinf(s.th);
+      cs = cosf(s.th);
+    } else {
+      sn = sc[q];
+      cs = sc[NE + q];
+    }
   }
 }
 
@@ -236,7 +285,8 @@ struct CtrlCc {
   static constexpr int S_LG = S_H1 + NE * HP;          // [4][NE] logit sums without b3
   static constexpr int S_U = S_LG + 4 * NE;            // [2][NE] action uniforms (step parity)
   static constexpr int S_RR = S_U + 2 * NE;            // [2][4][NE] reset words (step parity)
-  static constexpr int FLOATS = S_RR + 8 * NE;
+  static constexpr int S_SC = S_RR + 8 * NE;           // [2][2][NE] predicted sin, cos (parity)
+  static constexpr int FLOATS = S_SC + 4 * NE;
   static constexpr int SMEM = FLOATS * 4;
   static_assert(S_W2 % 4 == 0 && S_H1 % 4 == 0 && S_W3 % 4 == 0 && HP % 4 == 0, "alignment");
   static_assert(draw_lane0(NE) + 2 * NE <= THREADS, "env lanes, then the draw lanes' warps");
@@ -279,7 +329,7 @@ __global__ void __launch_bounds__(CtrlCc<E, H, NE, RE>::THREADS)
   const uint32_t R = d.ring_steps, N = d.n_envs;
   const uint32_t row0 = (uint32_t)(k0 % R);
   const int n_tiles = (int)((N + NE - 1) / NE);
-  float *xo = sm + C::S_XO, *h1s = sm + C::S_H1, *lg = sm + C::S_LG;
+  float *xo = sm + C::S_XO, *h1s = sm + C::S_H1, *lg = sm + C::S_LG, *sc = sm + C::S_SC;
   float *us = sm + C::S_U;
   uint32_t *rrs = (uint32_t *)(sm + C::S_RR);
 
@@ -332,8 +382,12 @@ __global__ void __launch_bounds__(CtrlCc<E, H, NE, RE>::THREADS)
       }
       __syncthreads();  // h1 complete
       // ---- P3: layer 2, act 2, layer-3 partials
+      float pth, pw;
+      draw_lane_state<E>(tid, NE, xo, pth, pw);
       {
-        float acc[RE][RU];
+        // z2 = (b2 + sum_{k < H/2} h1_k W2_k) + sum_{k >= H/2} h1_k W2_k: two
+        // chains in k order, added at the end
+        float acc[RE][RU], acc2[RE][RU];
 #pragma unroll
         for (int c = 0; c < RU; c += 4) {
           const float4 b = *(const float4 *)(sm + C::S_B2 + ug * RU + c);
@@ -343,12 +397,13 @@ __global__ void __launch_bounds__(CtrlCc<E, H, NE, RE>::THREADS)
             acc[r][c + 1] = b.y;
             acc[r][c + 2] = b.z;
             acc[r][c + 3] = b.w;
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) acc2[r][c + cc] = 0.f;
           }
         }
         const float *w2 = sm + C::S_W2 + ug * RU;
         const float *hr = h1s + eg * RE * C::HP;
-#pragma unroll 2
-        for (int k4 = 0; k4 < H; k4 += 4) {
+        auto chain = [&](float (&a)[RE][RU], int k4) {
           float4 hv[RE];
 #pragma unroll
           for (int r = 0; r < RE; ++r) hv[r] = *(const float4 *)(hr + r * C::HP + k4);
@@ -367,10 +422,19 @@ __global__ void __launch_bounds__(CtrlCc<E, H, NE, RE>::THREADS)
             for (int r = 0; r < RE; ++r) {
               const float hk = kk == 0 ? hv[r].x : kk == 1 ? hv[r].y : kk == 2 ? hv[r].z : hv[r].w;
 #pragma unroll
-              for (int c = 0; c < RU; ++c) acc[r][c] = __fmaf_rn(hk, wk[c], acc[r][c]);
+              for (int c = 0; c < RU; ++c) a[r][c] = __fmaf_rn(hk, wk[c], a[r][c]);
             }
           }
+        };
+#pragma unroll 2
+        for (int k4 = 0; k4 < H / 2; k4 += 4) {
+          chain(acc, k4);
+          chain(acc2, k4 + H / 2);
         }
+#pragma unroll
+        for (int r = 0; r < RE; ++r)
+#pragma unroll
+          for (int c = 0; c < RU; ++c) acc[r][c] = acc[r][c] + acc2[r][c];
         // h2 = tanh(z2) (FP32) and this thread's layer-3 partial sums, units in order
         float pl[RE][NA];
 #pragma unroll
@@ -406,9 +470,8 @@ __global__ void __launch_bounds__(CtrlCc<E, H, NE, RE>::THREADS)
       __syncthreads();  // logits complete
       // ---- P4: sampling, env step, records (env lanes); next step's draws
       if (lane_env) {
-        // the pole angle's sin / cos first: independent of the logits, they
-        // overlap the loads and the draw
-        const float sin_th = ACRO ? 0.f : sinf(s.th), cos_th = ACRO ? 0.f : cosf(s.th);
+        float sin_th, cos_th;
+        lane_trig(s, sc + par * 2 * NE, NE, tid, sin_th, cos_th);
         const float l0 = lg[tid] + sm[C::S_B3], l1v = lg[NE + tid] + sm[C::S_B3 + 1];
         const float l2 = ACRO ? lg[2 * NE + tid] + sm[C::S_B3 + 2] : 0.f;
         lane_step(d, s, l0, l1v, l2, us[par * NE + tid], rrs + par * 4 * NE + tid, NE, sin_th,
@@ -416,7 +479,8 @@ __global__ void __launch_bounds__(CtrlCc<E, H, NE, RE>::THREADS)
         lane_observe(s, xo + tid, NE);
       } else if (j + 1 < n_steps) {
         const int np = par ^ 1;
-        draw_lanes(d, tid, NE, base, k + 1, us + np * NE, rrs + np * 4 * NE);
+        draw_lanes(d, tid, NE, base, k + 1, us + np * NE, rrs + np * 4 * NE, !ACRO, pth, pw,
+                   sc + np * 2 * NE);
       }
       row = (row + 1 == R) ? 0 : row + 1;
     }
@@ -435,7 +499,8 @@ struct CtrlCu {
   static constexpr int S_PT = S_H1 + NE * HP;          // [NA][NE][2] per-warp partial sums
   static constexpr int S_U = S_PT + 3 * NE * 2;        // [2][NE]
   static constexpr int S_RR = S_U + 2 * NE;            // [2][4][NE]
-  static constexpr int FLOATS = S_RR + 8 * NE;
+  static constexpr int S_SC = S_RR + 8 * NE;           // [2][2][NE] predicted sin, cos
+  static constexpr int FLOATS = S_SC + 4 * NE;
   static constexpr int SMEM = FLOATS * 4;
   static_assert(S_H1 % 4 == 0 && HP % 4 == 0, "alignment");
   static_assert(NE <= 32 && draw_lane0(NE) + 2 * NE <= THREADS, "env lanes, then draw lanes");
@@ -474,7 +539,7 @@ __global__ void __launch_bounds__(CtrlCu<E, NE>::THREADS)
   const uint32_t R = d.ring_steps, N = d.n_envs;
   const uint32_t row0 = (uint32_t)(k0 % R);
   const int n_tiles = (int)((N + NE - 1) / NE);
-  float *xo = sm + C::S_XO, *h1s = sm + C::S_H1, *pt = sm + C::S_PT;
+  float *xo = sm + C::S_XO, *h1s = sm + C::S_H1, *pt = sm + C::S_PT, *sc = sm + C::S_SC;
   float *us = sm + C::S_U;
   uint32_t *rrs = (uint32_t *)(sm + C::S_RR);
 
@@ -502,19 +567,27 @@ __global__ void __launch_bounds__(CtrlCu<E, NE>::THREADS)
         h1s[q * C::HP + u] = tc::bf16_lo(tc::tanh_bf16x2(tc::pack_bf16x2(z, 0.f)));
       }
       __syncthreads();  // h1 complete
-      // ---- P3: layer 2 of unit u (k in order), act 2, layer-3 group partials
+      // ---- P3: layer 2 of unit u (two chains in k order: from b2 over the first
+      // half of k, from zero over the second, added), act 2, layer-3 partials
+      float pth, pw;
+      draw_lane_state<E>(tid, NE, xo, pth, pw);
       {
-        float z = b2u;
+        float za = b2u, zb = 0.f;
         const float *hr = h1s + q * C::HP;
 #pragma unroll
-        for (int k4 = 0; k4 < H; k4 += 4) {
-          const float4 hv = *(const float4 *)(hr + k4);
-          z = __fmaf_rn(hv.x, w2c[k4], z);
-          z = __fmaf_rn(hv.y, w2c[k4 + 1], z);
-          z = __fmaf_rn(hv.z, w2c[k4 + 2], z);
-          z = __fmaf_rn(hv.w, w2c[k4 + 3], z);
+        for (int k4 = 0; k4 < H / 2; k4 += 4) {
+          const float4 ha = *(const float4 *)(hr + k4);
+          const float4 hb = *(const float4 *)(hr + k4 + H / 2);
+          za = __fmaf_rn(ha.x, w2c[k4], za);
+          zb = __fmaf_rn(hb.x, w2c[k4 + H / 2], zb);
+          za = __fmaf_rn(ha.y, w2c[k4 + 1], za);
+          zb = __fmaf_rn(hb.y, w2c[k4 + H / 2 + 1], zb);
+          za = __fmaf_rn(ha.z, w2c[k4 + 2], za);
+          zb = __fmaf_rn(hb.z, w2c[k4 + H / 2 + 2], zb);
+          za = __fmaf_rn(ha.w, w2c[k4 + 3], za);
+          zb = __fmaf_rn(hb.w, w2c[k4 + H / 2 + 3], zb);
         }
-        const float h2 = tc::tanh_fast(z);
+        const float h2 = tc::tanh_fast(za + zb);
         // the group of units 4g .. 4g + 3 (four lanes of one warp): each of its
         // lanes forms the group's FMA chain over the four from zero
         float hg[4];
@@ -541,7 +614,8 @@ __global__ void __launch_bounds__(CtrlCu<E, NE>::THREADS)
       __syncthreads();  // group partials complete
       // ---- P4: sampling, env step, records (env lanes); next step's draws
       if (lane_env) {
-        const float sin_th = ACRO ? 0.f : sinf(s.th), cos_th = ACRO ? 0.f : cosf(s.th);
+        float sin_th, cos_th;
+        lane_trig(s, sc + par * 2 * NE, NE, tid, sin_th, cos_th);
         // the last butterfly level: the env's two warps (groups g and g ^ 8)
         const float l0 = (pt[tid * 2] + pt[tid * 2 + 1]) + b30;
         const float l1v = (pt[(NE + tid) * 2] + pt[(NE + tid) * 2 + 1]) + b31;
@@ -551,7 +625,8 @@ __global__ void __launch_bounds__(CtrlCu<E, NE>::THREADS)
         lane_observe(s, xo + tid, NE);
       } else if (j + 1 < n_steps) {
         const int np = par ^ 1;
-        draw_lanes(d, tid, NE, base, k + 1, us + np * NE, rrs + np * 4 * NE);
+        draw_lanes(d, tid, NE, base, k + 1, us + np * NE, rrs + np * 4 * NE, !ACRO, pth, pw,
+                   sc + np * 2 * NE);
       }
       row = (row + 1 == R) ? 0 : row + 1;
     }
