@@ -527,7 +527,11 @@ typedef enum {
   WS_PROBE_FMA_F32X2 = 8,    /* fma.rn.f32x2 (two results)                    */
   WS_PROBE_LG2_F32 = 9,      /* lg2.approx.ftz.f32 (with one FP32 FMA)        */
   WS_PROBE_RSQRT_F32 = 10,   /* rsqrt.approx.ftz.f32 (with one FP32 add)      */
-  WS_PROBE_COUNT = 11
+  WS_PROBE_TANH_F32_HALF = 11, /* tanh.approx.f32 on lanes 0-15 of every warp
+                                  only; counts the results of those lanes, so
+                                  half the full rate means a warp instruction
+                                  costs the same with half its lanes idle      */
+  WS_PROBE_COUNT = 12
 } ws_probe_op;
 
 ws_status ws_probe_rate(int op, uint32_t iters, void *dev_buf, size_t buf_bytes,

@@ -1,6 +1,7 @@
 // ws_probe.cu -- throughput probes of the arithmetic units the roll-out kernels
 // lean on (the SFU's tanh / ex2 / rcp / sin and the FMA pipe), in results per
-// clock per SM.  The rooflines of the fused kernels divide by these rates.
+// clock per SM.  The rooflines of the fused kernels divide by these rates; the
+// half-warp tanh probe tells whether idle lanes shorten an SFU instruction.
 //
 // Every thread runs 8 independent chains of the probed operation for `iters`
 // rounds; the grid holds 4 blocks of 256 threads per SM (32 warps, so that
@@ -99,6 +100,12 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(uint32_t iters, unsigne
     for (uint32_t i = 0; i < iters; ++i)
 #pragma unroll
       for (int j = 0; j < kChains; ++j) w[j] = probe_op2<op>(w[j]);
+  } else if constexpr (op == WS_PROBE_TANH_F32_HALF) {
+    if ((threadIdx.x & 31) < 16)
+      for (uint32_t i = 0; i < iters; ++i)
+#pragma unroll
+        for (int j = 0; j < kChains; ++j) v[j] = probe_op<WS_PROBE_TANH_F32>(v[j]);
+    __syncwarp();
   } else {
     for (uint32_t i = 0; i < iters; ++i)
 #pragma unroll
@@ -153,6 +160,7 @@ extern "C" ws_status ws_probe_rate(int op, uint32_t iters, void *dev_buf, size_t
     case WS_PROBE_LG2_F32: launch_probe<WS_PROBE_LG2_F32>(grid, iters, cyc, st); break;
     case WS_PROBE_RSQRT_F32: launch_probe<WS_PROBE_RSQRT_F32>(grid, iters, cyc, st); break;
     case WS_PROBE_FMA_F32: launch_probe<WS_PROBE_FMA_F32>(grid, iters, cyc, st); break;
+    case WS_PROBE_TANH_F32_HALF: launch_probe<WS_PROBE_TANH_F32_HALF>(grid, iters, cyc, st); break;
     default: launch_probe<WS_PROBE_FMA_F32X2>(grid, iters, cyc, st); break;
   }
   std::vector<unsigned long long> h((size_t)grid * 2);
@@ -166,7 +174,7 @@ extern "C" ws_status ws_probe_rate(int op, uint32_t iters, void *dev_buf, size_t
   const bool packed = op == WS_PROBE_TANH_BF16X2 || op == WS_PROBE_EX2_BF16X2 ||
                       op == WS_PROBE_EX2_F16X2 || op == WS_PROBE_FMA_F32X2;
   const double per_sm = (double)kProbeBlocksPerSm * kProbeThreads * kChains * (double)iters *
-                        (packed ? 2.0 : 1.0);
+                        (packed ? 2.0 : 1.0) * (op == WS_PROBE_TANH_F32_HALF ? 0.5 : 1.0);
   *per_clk_per_sm = per_sm / (double)span;
   return WS_OK;
 }

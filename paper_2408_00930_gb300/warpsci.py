@@ -37,7 +37,7 @@ EXPORTED = ["ws_query_bytes", "ws_create", "ws_reset", "ws_step", "ws_rollout", 
 PROBE_OPS = ["tanh.approx.f32", "tanh.approx.bf16x2", "ex2.approx.ftz.f32",
              "ex2.approx.ftz.bf16x2", "ex2.approx.f16x2", "rcp.approx.ftz.f32",
              "sin.approx.ftz.f32", "fma.rn.f32", "fma.rn.f32x2", "lg2.approx.ftz.f32",
-             "rsqrt.approx.ftz.f32"]
+             "rsqrt.approx.ftz.f32", "tanh.approx.f32 (lanes 0-15)"]
 WS_REQ_CONSUME_ON_READY = 1
 WS_FLAG_DEBUG_LOGITS = 1
 WS_FLAG_ENERGY_TARGET = 2
