@@ -436,12 +436,15 @@ def run_a2c(wl, local):
     return {"rows": rows, "ms": t, "rows_per_s": rows / (t * 1e-3), "unit": "rows/s",
             "roofline": {"bound": "fp32", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
+                         "note": "FP32-equivalent flops of the update over the FP32 CUDA-core "
+                                 "peak; the wide layers run on tcgen05 (three BF16 products "
+                                 "per FP32 product)",
                          "peak_source": f"128 FP32 lanes x 2 flops / clock / SM x {n_sms} SMs x "
                                         "2070 MHz"},
-            "kernels": "k_a2c_gather, k_sgemm (forward, weight and data gradients of the "
-                       "wide layers; packed f32x2 FMAs), k_fwd_thin, k_fwd_thin_k, k_dgrad_thin_k, "
-                       "k_wgrad_thin_n/_m, k_colsum_slices, k_reduce_slices, k_a2c_head, k_sgd; "
-                       "FP32 SIMT",
+            "kernels": "k_a2c_gather, k_gemm_tc (forward, weight and data gradients of the "
+                       "wide layers on tcgen05, FP32 operands split into BF16 hi + lo), "
+                       "k_fwd_thin, k_fwd_thin_k, k_dgrad_thin_k, k_wgrad_thin_n/_m, "
+                       "k_colsum_slices, k_reduce_slices, k_a2c_head, k_sgd",
             "ppo": {"advantages_ms": statistics.median(ms_adv),
                     "epoch_ms": statistics.median(ms_ppo),
                     "epoch_rows_per_s": rows / (statistics.median(ms_ppo) * 1e-3),

@@ -374,6 +374,10 @@ typedef struct {
                               32; 64..512 threads per CTA); 64 = one thread per
                               hidden unit with its W2 column in registers (hidden
                               width 64; ctrl_envs_per_cta 1, 2, 4 or 8)          */
+  uint32_t update_gemm;    /* ws_a2c_update / ws_advantages / ws_ppo_update: the
+                              hidden-by-hidden GEMMs on the tensor cores with
+                              FP32 operands split into BF16 hi + lo (0, the
+                              default), or on the FP32 CUDA cores (1)           */
 } ws_launch;
 
 /* The context's current launch configuration. */

@@ -52,6 +52,7 @@ struct Dev {
   // energy kernel's Gaussian chunks per env tile
   int env_threads;
   int energy_chunks;
+  int update_simt;  // the update's hidden-layer GEMMs on FP32 CUDA cores (else tcgen05)
   // limit of the fused kernels' device waits (MMA completions, the SFU token,
   // block loads, the cluster partner), in ns: a wait that runs out sets the
   // error flag (ws_sync reports it) and the kernel leaves after draining
@@ -129,6 +130,19 @@ void launch_control_tc_pack(const Dev &d, void *packed, cudaStream_t st);
 cudaError_t launch_control_tc(const Dev &d, const void *packed, uint32_t n_steps, int grid,
                               cudaStream_t st);
 int control_tc_default_grid(const Dev &d);
+
+// ---- FP32-accurate tensor-core GEMM of the update (ws_gemm_tc.cu) -------------
+// C = epi(A B) in 128 x 128 tiles, each FP32 operand split into BF16 hi + lo and
+// the three terms hi hi + hi lo + lo hi accumulated in FP32.  A(m, k) =
+// A[m lda + k] (ta: A[k lda + m]); B(k, n) = B[k ldb + n] (tb: B[n ldb + k]);
+// k over [k_lo, k_hi), or with k_slice > 0 in slices written at C + z
+// slice_stride.  Epilogues: bias + tanh, bias (aux = bias), tanh derivative
+// of the layer below (aux = its activations [M][N]), none.  Supported:
+// (!ta, !tb, bias + tanh | bias), (!ta, tb, tanh derivative), (ta, !tb, none).
+enum GemmEpi { kGemmBiasTanh = 0, kGemmBias = 1, kGemmDTanh = 2, kGemmNone = 3 };
+cudaError_t launch_gemm_tc(bool ta, bool tb, int epi, const float *A, int lda, const float *B,
+                           int ldb, float *C, int M, int N, int k_lo, int k_hi, int k_slice,
+                           size_t slice_stride, const float *aux, uint32_t *err, cudaStream_t st);
 
 // ---- CUDA-core control path for small env counts (ws_control_cc.cu) ----------
 bool control_cc_supported(const PolicyShape &shape);

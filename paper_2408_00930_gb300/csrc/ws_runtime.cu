@@ -782,6 +782,7 @@ ws_status ws_create(const ws_config *cfg, void *state_buf, size_t state_bytes, v
   make_dev(c);
   default_launch(c);
   c->d.env_threads = (int)c->lc.env_threads;
+  c->d.update_simt = (int)c->lc.update_gemm;
   c->d.energy_chunks = (int)c->lc.energy_chunks;
   c->d.wait_ns = device_wait_ns(c->lc);
   cudaError_t e = cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking);
@@ -1157,7 +1158,7 @@ ws_status ws_set_launch(ws_ctx *c, const ws_launch *l) {
   if (l->tile_ctas != 1 && l->tile_ctas != 2) return WS_ERR_INVALID;
   const uint32_t tpe = l->ctrl_threads_per_env;
   if (tpe != 4 && tpe != 8 && tpe != 16 && tpe != 64) return WS_ERR_INVALID;
-  if (l->ctrl_envs_per_cta > 32) return WS_ERR_INVALID;
+  if (l->ctrl_envs_per_cta > 32 || l->update_gemm > 1) return WS_ERR_INVALID;
   if (l->ctrl_envs_per_cta && use_tc_control(&c->cfg) &&
       (!control_cc_supported(c->L.pol) ||
        !control_cc_tile_ok(c->L.pol, (int)l->ctrl_envs_per_cta, (int)tpe)))
@@ -1167,6 +1168,7 @@ ws_status ws_set_launch(ws_ctx *c, const ws_launch *l) {
   drop_graphs(c);  // graphs bake the launch parameters in
   c->d.env_threads = (int)l->env_threads;
   c->d.energy_chunks = (int)l->energy_chunks;
+  c->d.update_simt = (int)l->update_gemm;
   c->d.wait_ns = device_wait_ns(*l);
   if (c->L.econ_fused && (old.econ_tiles != l->econ_tiles || old.econ_lpt != l->econ_lpt)) {
     ws_status s = set_econ_items(c);

@@ -682,10 +682,27 @@ inline dim3 ggrid(int M, int N, int z = 1) {
   return dim3((unsigned)((M + kGM - 1) / kGM), (unsigned)((N + kGN - 1) / kGN), (unsigned)z);
 }
 
+// A hidden-layer GEMM of the update: on tcgen05 with FP32 operands split into
+// BF16 hi + lo (ws_gemm_tc.cu), or on the FP32 CUDA cores when the launch asks
+// for them (ws_launch.update_gemm).  The epilogue codes are shared.
+static_assert((int)kEpiBiasTanh == (int)kGemmBiasTanh && (int)kEpiBias == (int)kGemmBias &&
+                  (int)kEpiDTanh == (int)kGemmDTanh && (int)kEpiNone == (int)kGemmNone,
+              "epilogue codes");
+template <bool TA, bool TB, int EPI>
+void hgemm(const Dev &d, dim3 g, cudaStream_t st, const float *A, int lda, const float *B, int ldb,
+           float *C, int M, int N, int k_lo, int k_hi, int k_slice, size_t slice_stride,
+           const float *aux) {
+  if (d.update_simt)
+    sgemm<TA, TB, EPI>(g, st, A, lda, B, ldb, C, M, N, k_lo, k_hi, k_slice, slice_stride, aux);
+  else
+    launch_gemm_tc(TA, TB, EPI, A, lda, B, ldb, C, M, N, k_lo, k_hi, k_slice, slice_stride, aux,
+                   d.err, st);
+}
+
 // Forward of one three-layer MLP for a chunk (rows x w0 row-major input),
 // keeping the tanh activations h1, h2.
-void mlp_forward(const PolicyShape &sh, const float *params, const float *X, float *h1, float *h2,
-                 float *out, int rows, cudaStream_t st) {
+void mlp_forward(const Dev &d, const PolicyShape &sh, const float *params, const float *X, float *h1,
+                 float *h2, float *out, int rows, cudaStream_t st) {
   const float *in[3] = {X, h1, h2};
   float *o[3] = {h1, h2, out};
   for (int l = 0; l < 3; ++l) {
@@ -714,10 +731,11 @@ void mlp_forward(const PolicyShape &sh, const float *params, const float *X, flo
 #undef WS_FWDK_TANH
 #undef WS_FWDK_LIN
     } else if (l < 2) {
-      sgemm<false, false, kEpiBiasTanh>(ggrid(rows, N), st, in[l], K, W, N, o[l], rows, N, 0, K, 0, 0,
-                                        b);
+      hgemm<false, false, kEpiBiasTanh>(d, ggrid(rows, N), st, in[l], K, W, N, o[l], rows, N, 0, K,
+                                        0, 0, b);
     } else {
-      sgemm<false, false, kEpiBias>(ggrid(rows, N), st, in[l], K, W, N, o[l], rows, N, 0, K, 0, 0, b);
+      hgemm<false, false, kEpiBias>(d, ggrid(rows, N), st, in[l], K, W, N, o[l], rows, N, 0, K, 0, 0,
+                                    b);
     }
   }
 }
@@ -726,8 +744,8 @@ void mlp_forward(const PolicyShape &sh, const float *params, const float *X, flo
 // tanh activations, dout [rows][w3] the gradient at the output.  Per layer the
 // weight gradient as 512-row slice partials (and the bias row), summed into
 // grad in slice order, then the data gradient into the layer below.
-void mlp_backward(const PolicyShape &sh, const float *params, const float *X, const float *h1,
-                  const float *h2, const float *dout, float *grad, float *d1, float *d2,
+void mlp_backward(const Dev &d, const PolicyShape &sh, const float *params, const float *X,
+                  const float *h1, const float *h2, const float *dout, float *grad, float *d1, float *d2,
                   float *part, int rows, cudaStream_t st) {
   const float *ain[3] = {X, h1, h2};
   float *dl[3] = {nullptr, d1, d2};
@@ -749,7 +767,7 @@ void mlp_backward(const PolicyShape &sh, const float *params, const float *X, co
       WS_THIN_DISPATCH(M, WS_WG_M)
 #undef WS_WG_M
     } else {
-      sgemm<true, false, kEpiNone>(ggrid(M, N, nz), st, ain[l], M, D, N, part, M, N, 0, rows,
+      hgemm<true, false, kEpiNone>(d, ggrid(M, N, nz), st, ain[l], M, D, N, part, M, N, 0, rows,
                                    kSliceRows, len, nullptr);
       k_colsum_slices<<<dim3(nblk(N, 32), (unsigned)nz), 256, 0, st>>>(D, part, rows, M, N);
     }
@@ -762,8 +780,8 @@ void mlp_backward(const PolicyShape &sh, const float *params, const float *X, co
       WS_THIN_DISPATCH(N, WS_DG)
 #undef WS_DG
     } else if (l > 0) {
-      sgemm<false, true, kEpiDTanh>(ggrid(rows, M), st, D, N, params + sh.layer_offset(l), N, dl[l],
-                                    rows, M, 0, N, 0, 0, ain[l]);
+      hgemm<false, true, kEpiDTanh>(d, ggrid(rows, M), st, D, N, params + sh.layer_offset(l), N,
+                                    dl[l], rows, M, 0, N, 0, 0, ain[l]);
     }
   }
 }
@@ -841,16 +859,17 @@ void run_update(const Dev &d, const TrainBufs &tb, const TrainGroup *groups, int
       const int rows = (int)((R - q0) < (size_t)kTrainChunk ? (R - q0) : (size_t)kTrainChunk);
       k_a2c_gather<<<nblk(rows, 256), 256, 0, st>>>(d, n, q0, (uint32_t)rows, G.slot0, G.n_slots,
                                                     G.pol.w[0], ppo ? 1 : 0, tb);
-      mlp_forward(G.pol, G.params, tb.x, tb.h1, tb.h2, tb.out, rows, st);
-      mlp_forward(G.crit, G.critic, tb.x, tb.c1, tb.c2, tb.vout, rows, st);
+      mlp_forward(d, G.pol, G.params, tb.x, tb.h1, tb.h2, tb.out, rows, st);
+      mlp_forward(d, G.crit, G.critic, tb.x, tb.c1, tb.c2, tb.vout, rows, st);
       if (ppo)
         k_ppo_head<<<nblk(rows, 256), 256, 0, st>>>(d, n, q0, (uint32_t)rows, G.n_slots,
                                                     G.pol.w[3], inv_r, eps, c_v, c_e, tb);
       else
         k_a2c_head<<<nblk(rows, 256), 256, 0, st>>>(d, n, q0, (uint32_t)rows, G.n_slots,
                                                     G.pol.w[3], inv_r, c_v, c_e, tb);
-      mlp_backward(G.pol, G.params, tb.x, tb.h1, tb.h2, tb.out, ga, tb.d1, tb.d2, tb.part, rows, st);
-      mlp_backward(G.crit, G.critic, tb.x, tb.c1, tb.c2, tb.vout, gc, tb.d1, tb.d2, tb.part, rows,
+      mlp_backward(d, G.pol, G.params, tb.x, tb.h1, tb.h2, tb.out, ga, tb.d1, tb.d2, tb.part, rows,
+                   st);
+      mlp_backward(d, G.crit, G.critic, tb.x, tb.c1, tb.c2, tb.vout, gc, tb.d1, tb.d2, tb.part, rows,
                    st);
     }
     k_sgd<<<nblk(na, 256), 256, 0, st>>>(G.params, ga, na, lr);
@@ -881,11 +900,11 @@ void launch_advantages(const Dev &d, const TrainBufs &tb, const TrainGroup *grou
       const int rows = (int)((R - q0) < (size_t)kTrainChunk ? (R - q0) : (size_t)kTrainChunk);
       k_a2c_gather<<<nblk(rows, 256), 256, 0, st>>>(d, n, q0, (uint32_t)rows, G.slot0, G.n_slots,
                                                     G.pol.w[0], 0, tb);
-      mlp_forward(G.crit, G.critic, tb.x, tb.c1, tb.c2, tb.vout, rows, st);
+      mlp_forward(d, G.crit, G.critic, tb.x, tb.c1, tb.c2, tb.vout, rows, st);
       k_adv_store<<<nblk(rows, 256), 256, 0, st>>>(d, n, q0, (uint32_t)rows, G.slot0, G.n_slots,
                                                    tb);
       if (d.env == WS_ENV_LANDSCAPE) {  // one group: every slot
-        mlp_forward(G.pol, G.params, tb.x, tb.h1, tb.h2, tb.out, rows, st);
+        mlp_forward(d, G.pol, G.params, tb.x, tb.h1, tb.h2, tb.out, rows, st);
         k_sample_store<<<nblk(rows, 256), 256, 0, st>>>(d, n, q0, (uint32_t)rows, G.n_slots, tb);
       }
     }

@@ -62,7 +62,8 @@ class ws_launch(C.Structure):
                 ("econ_tiles", C.c_uint32), ("econ_lpt", C.c_uint32),
                 ("energy_chunks", C.c_uint32), ("env_threads", C.c_uint32),
                 ("tile_ctas", C.c_uint32), ("wait_ns", C.c_uint32),
-                ("ctrl_envs_per_cta", C.c_uint32), ("ctrl_threads_per_env", C.c_uint32)]
+                ("ctrl_envs_per_cta", C.c_uint32), ("ctrl_threads_per_env", C.c_uint32),
+                ("update_gemm", C.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "struct_size"}

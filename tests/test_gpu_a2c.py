@@ -20,9 +20,10 @@ def torch():
     return need_gpu()
 
 
-def run_update(env, path, n, T, h, lr, c_v, c_e, seed=3):
+def run_update(env, path, n, T, h, lr, c_v, c_e, seed=3, gemm=0):
     od, na = (4, 2) if env == W.WS_ENV_CONTROL else (6, 3)
     r = W.Rollout(env, path, n, T, 25, h, h, param_seed=seed, flags=W.WS_FLAG_TRAIN, chunk_steps=10)
+    r.set_launch(update_gemm=gemm)
     r.reset(seed + 1)
     r.rollout(T)
     pa = r.fetch_raw(W.WS_F_PARAMS, 4 * oracle.policy_param_count([od, h, h, na])).view(np.float32).copy()
@@ -55,10 +56,24 @@ def check_grads(params, rows, stats, shape, h, lr, c_v, c_e):
         assert np.abs(g).max() > 0
 
 
-@pytest.mark.parametrize("env", [W.WS_ENV_CONTROL, W.WS_ENV_ACROBOT])
-def test_a2c_update_matches_oracle_fp32(torch, env):
+@pytest.mark.parametrize("env,gemm", [(W.WS_ENV_CONTROL, 0), (W.WS_ENV_ACROBOT, 0),
+                                      (W.WS_ENV_CONTROL, 1), (W.WS_ENV_ACROBOT, 1)])
+def test_a2c_update_matches_oracle_fp32(torch, env, gemm):
+    """gemm 0: the hidden GEMMs on tcgen05 (FP32 operands split into BF16 hi +
+    lo); 1: on the FP32 CUDA cores."""
     n, T, h, lr, c_v, c_e = 3000, 30, 64, 1.0, 0.5, 0.01  # 90,000 rows: two update chunks
-    r, params, rows, stats, shape = run_update(env, F32, n, T, h, lr, c_v, c_e)
+    r, params, rows, stats, shape = run_update(env, F32, n, T, h, lr, c_v, c_e, gemm=gemm)
+    check_grads(params, rows, stats, shape, h, lr, c_v, c_e)
+    r.close()
+
+
+def test_a2c_update_wide_layers_on_tensor_cores(torch):
+    """256-unit hidden layers (128 x 128 tiles with two N tiles per layer) over
+    two chunks, the second ragged: the split-BF16 tcgen05 GEMMs against the
+    oracle's FP64 gradients."""
+    n, T, h, lr, c_v, c_e = 2100, 40, 256, 1.0, 0.5, 0.01  # 84,000 rows
+    r, params, rows, stats, shape = run_update(W.WS_ENV_CONTROL, BF16, n, T, h, lr, c_v, c_e,
+                                               seed=11)
     check_grads(params, rows, stats, shape, h, lr, c_v, c_e)
     r.close()
 
