@@ -267,6 +267,11 @@ def run_gpu(args, wl, world, rank, local):
             launch, _ = r.tune(min(CHUNK, H))
         elif measure_kernel:
             launch = r.launch().as_dict()
+        if measure_kernel and args.launch:
+            # fixed launch fields (k=v,...), e.g. to profile one kernel choice
+            kv = dict(item.split("=") for item in args.launch.split(","))
+            r.set_launch(**{k: int(v) for k, v in kv.items()})
+            launch = r.launch().as_dict()
 
         def bench_step(i, evs=None):
             r.reset(1000 + i)
@@ -590,6 +595,8 @@ def main():
                     help="also time one actor-critic update (ws_a2c_update), the PPO advantages "
                          "and one PPO epoch over 50 steps "
                          "(control and acrobot workloads)")
+    ap.add_argument("--launch", default="",
+                    help="launch fields set after tuning, as k=v,... (ws_launch names)")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch configuration (profiling captures)")
     ap.add_argument("--horizon", type=int, default=0,
