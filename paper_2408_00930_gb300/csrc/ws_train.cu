@@ -692,11 +692,12 @@ template <bool TA, bool TB, int EPI>
 void hgemm(const Dev &d, dim3 g, cudaStream_t st, const float *A, int lda, const float *B, int ldb,
            float *C, int M, int N, int k_lo, int k_hi, int k_slice, size_t slice_stride,
            const float *aux) {
-  if (d.update_simt)
-    sgemm<TA, TB, EPI>(g, st, A, lda, B, ldb, C, M, N, k_lo, k_hi, k_slice, slice_stride, aux);
-  else
-    launch_gemm_tc(TA, TB, EPI, A, lda, B, ldb, C, M, N, k_lo, k_hi, k_slice, slice_stride, aux,
-                   d.err, st);
+  // a tensor-core launch that is refused (a shape it does not take) falls back
+  // to the CUDA-core GEMM
+  if (!d.update_simt && launch_gemm_tc(TA, TB, EPI, A, lda, B, ldb, C, M, N, k_lo, k_hi, k_slice,
+                                       slice_stride, aux, d.err, st) == cudaSuccess)
+    return;
+  sgemm<TA, TB, EPI>(g, st, A, lda, B, ldb, C, M, N, k_lo, k_hi, k_slice, slice_stride, aux);
 }
 
 // Forward of one three-layer MLP for a chunk (rows x w0 row-major input),
