@@ -230,29 +230,55 @@ __global__ void __launch_bounds__(kThreads)
     const int lane_id = tid & 31;
     const int n = n0 + lane_id * 4;
     const bool vec = (N & 3) == 0 && n + 3 < N;
-#pragma unroll 1
-    for (int rr = warp; rr < kTM; rr += kThreads / 32) {
-      const int m = m0 + rr;
-      if (m >= M) break;
-      const float4 a = *(const float4 *)(ct + rr * kCP + lane_id * 4);
-      float v[4] = {a.x, a.y, a.z, a.w};
+    // the bias of this thread's four columns, the same for every row
+    float bv[4] = {0.f, 0.f, 0.f, 0.f};
+    if (EPI == kGemmBiasTanh || EPI == kGemmBias) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        if (n + i >= N) break;
-        if (EPI == kGemmBiasTanh) v[i] = tanhf(v[i] + aux[n + i]);
-        if (EPI == kGemmBias) v[i] = v[i] + aux[n + i];
+      for (int i = 0; i < 4; ++i) bv[i] = n + i < N ? aux[n + i] : 0.f;
+    }
+    const bool avec = vec && ((uintptr_t)aux & 15) == 0;
+    // Each warp takes rows warp, warp + 8, ... in batches of kRB, whose operand
+    // loads (the layer's activations for tanh') are all issued before the first
+    // is used, so that a batch waits on one memory round trip, not kRB.
+    constexpr int kRB = 4, kWarps = kThreads / 32;
+#pragma unroll 1
+    for (int rb = warp; rb < kTM; rb += kRB * kWarps) {
+      if (m0 + rb >= M) break;
+      float v[kRB][4], hh[kRB][4];
+#pragma unroll
+      for (int u = 0; u < kRB; ++u) {
+        const int rr = rb + u * kWarps, m = m0 + rr;
+        const float4 a = *(const float4 *)(ct + rr * kCP + lane_id * 4);
+        v[u][0] = a.x; v[u][1] = a.y; v[u][2] = a.z; v[u][3] = a.w;
         if (EPI == kGemmDTanh) {
-          const float h = aux[(size_t)m * N + n + i];
-          v[i] = v[i] * (1.f - h * h);
+          const float *hp = aux + (size_t)m * N + n;
+          if (m < M && avec) {
+            const float4 h4 = __ldg((const float4 *)hp);
+            hh[u][0] = h4.x; hh[u][1] = h4.y; hh[u][2] = h4.z; hh[u][3] = h4.w;
+          } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) hh[u][i] = (m < M && n + i < N) ? __ldg(hp + i) : 0.f;
+          }
         }
       }
-      float *o = Cz + (size_t)m * N + n;
-      if (vec) {
-        *(float4 *)o = make_float4(v[0], v[1], v[2], v[3]);
-      } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-          if (n + i < N) o[i] = v[i];
+      for (int u = 0; u < kRB; ++u) {
+        const int m = m0 + rb + u * kWarps;
+        if (m >= M) break;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (EPI == kGemmBiasTanh) v[u][i] = tanhf(v[u][i] + bv[i]);
+          if (EPI == kGemmBias) v[u][i] = v[u][i] + bv[i];
+          if (EPI == kGemmDTanh) v[u][i] = v[u][i] * (1.f - hh[u][i] * hh[u][i]);
+        }
+        float *o = Cz + (size_t)m * N + n;
+        if (vec) {
+          *(float4 *)o = make_float4(v[u][0], v[u][1], v[u][2], v[u][3]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (n + i < N) o[i] = v[u][i];
+        }
       }
     }
   }

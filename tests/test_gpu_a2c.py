@@ -78,6 +78,18 @@ def test_a2c_update_wide_layers_on_tensor_cores(torch):
     r.close()
 
 
+@pytest.mark.parametrize("h", [150, 200])
+def test_a2c_update_ragged_wide_tile(torch, h):
+    """Hidden widths between 128 and 256: a second, ragged 128-column tile
+    whose columns past the width are masked, with rows whose length is a
+    multiple of 4 (16-byte loads and stores) and one that is not (element
+    loads and stores)."""
+    n, T, lr, c_v, c_e = 1300, 20, 1.0, 0.5, 0.01  # 26,000 rows
+    r, params, rows, stats, shape = run_update(W.WS_ENV_CONTROL, F32, n, T, h, lr, c_v, c_e, seed=5)
+    check_grads(params, rows, stats, shape, h, lr, c_v, c_e)
+    r.close()
+
+
 def test_a2c_update_bf16_acrobot_and_next_rollout(torch):
     n, T, h, lr, c_v, c_e = 257, 20, 64, 0.5, 0.5, 0.0
     r, params, rows, stats, shape = run_update(W.WS_ENV_ACROBOT, BF16, n, T, h, lr, c_v, c_e, seed=8)
