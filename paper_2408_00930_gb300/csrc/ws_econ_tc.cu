@@ -86,8 +86,10 @@ struct EconTc {
   static constexpr int OFF_ENVT = OFF_INC + ROWS * 8;       // i64 [64] tax pool
   static constexpr int OFF_WSUM = OFF_ENVT + kMaxEnvs * 8;  // i64 [64] pre-step wealth total
   static constexpr int OFF_ENVI = OFF_WSUM + kMaxEnvs * 8;  // int4 [64] {a0 in item, n, env, tau}
-  static constexpr int OFF_BAR = OFF_ENVI + kMaxEnvs * 16;  // [AT + 1] MMA barriers, drain
-  static constexpr int OFF_TM = OFF_BAR + 8 * (AT + 2);
+  // MMA barriers: [AT + 1] one per tile and the planner, the drain, [AT] a
+  // second one per tile
+  static constexpr int OFF_BAR = OFF_ENVI + kMaxEnvs * 16;
+  static constexpr int OFF_TM = OFF_BAR + 8 * (2 * AT + 2);
   static constexpr int OFF_ITEM = OFF_TM + 16;
   static constexpr int SMEM = OFF_ITEM + 16 + 1024;
   static_assert(SMEM <= 232448, "shared memory over the 227 KB per-CTA limit");
@@ -339,6 +341,7 @@ __global__ void __launch_bounds__((AT + 1) * 128, 1)
   if (tid == 0) {
     for (int i = 0; i <= AT; ++i) tc::mbar_init(bars + i, 1);
     tc::mbar_init(bars + AT + 1, AT + 1);
+    for (int i = 0; i < AT; ++i) tc::mbar_init(bars + AT + 2 + i, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tc::tmem_alloc(tm_holder, C::TMEM_COLS);
@@ -353,6 +356,7 @@ __global__ void __launch_bounds__((AT + 1) * 128, 1)
   const int r = tid & 127;
   const bool issuer = r == 0;
   uint64_t *bar = bars + tile;
+  uint64_t *bar2 = bars + AT + 2 + tile;  // an agent tile's second MMA barrier
   const uint32_t my_bar_id = kBarTile0 + (uint32_t)tile;  // tile or planner warpgroup barrier
   const uint32_t tcol = tbase + (uint32_t)tile * 128u;    // this warpgroup's TMEM columns (lane 0)
   const uint32_t hs = sb + C::OFF_HS + (uint32_t)(planner ? 0 : tile) * 32768u;
@@ -364,7 +368,7 @@ __global__ void __launch_bounds__((AT + 1) * 128, 1)
   const int4 *items = (const int4 *)d.items;
   const float inv_ln_1e6 = 0.0723824136505f;
 
-  uint32_t ph = 0u;
+  uint32_t ph = 0u, ph2 = 0u;
   bool ok = true, wfail = false;
   uint32_t fsite = 0;
 
@@ -408,6 +412,7 @@ __global__ void __launch_bounds__((AT + 1) * 128, 1)
       const uint64_t da1 = tc::smem_desc(hs, 128, 256, tc::kSwizzleNone);
       const uint64_t db1 = tc::smem_desc(sb + C::OFF_W1A, 128, 256, tc::kSwizzleNone);
       constexpr uint32_t id12 = tc::idesc_bf16_f32(128, kH);
+      constexpr uint32_t id2h = tc::idesc_bf16_f32(128, kH / 2);
       constexpr uint32_t id3 = tc::idesc_bf16_f32(128, kNAp);
       __syncthreads();
 
@@ -452,46 +457,85 @@ __global__ void __launch_bounds__((AT + 1) * 128, 1)
           if (!tc::mbar_wait(bar, ph, d.wait_ns) && !wfail) { wfail = true; fsite = 1; }
           ph ^= 1u;
           tc::fence_after_sync();
-#pragma unroll 1
-          for (int l = 0; l < 2; ++l) {
-            if (warp_on) {
+          // Layers 2 and 3 are pipelined over 64-column halves, so that the
+          // tensor core works while the tile's warps run their tanh: act 1 of
+          // columns 0-63 is h1's K block 0, whose layer-2 product into output
+          // columns 0-63 runs while act 1 reads columns 64-127; the rest of
+          // layer 2 is committed in two parts (output columns 0-63, then
+          // 64-127), and act 2 of each half (h2's K block) starts layer 3's
+          // product over that K block.  An MMA writes only columns that the
+          // warps have read out, and h1 / h2 share the tile's operand buffer
+          // by K block: a block is overwritten only after every MMA that reads
+          // it has completed (the commits waited on before).
+          //   commit   MMAs (output columns, K block)       waited before
+          //   bar      L2 (0-63, 0) (64-127, 0) (0-63, 1)   act 2 of 0-63
+          //   bar2     L2 (64-127, 1)                       act 2 of 64-127
+          //   bar      L3 (0-31, 0) (0-31, 1)               the logits
+          auto l2_mma = [&](int nh, int kb) {
 #pragma unroll
-              for (int kb = 0; kb < 2; ++kb) {
-                uint32_t hp[32];
-                act64(tm + (uint32_t)(kb * 64),
-                      bias + (uint32_t)(((l == 0 ? BO_B1A : BO_B2A) + kb * 64) * 4), hp);
-                store_row_sw128(hs + (uint32_t)kb * 16384u + (uint32_t)r * 128u, (uint32_t)(r & 7),
-                                hp);
-              }
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t ka = (uint32_t)(kb * 16384 + kk * 32);
+              const uint64_t da = tc::smem_desc(hs + ka, 16, 1024, tc::kSwizzle128B);
+              const uint64_t db = tc::smem_desc(sb + C::OFF_W2A + ka + (uint32_t)nh * 8192u, 16, 1024,
+                                                tc::kSwizzle128B);
+              tc::mma_bf16(tcol + (uint32_t)nh * 64u, da, db, id2h, (kb | kk) != 0);
+            }
+          };
+          auto l3_mma = [&](int kb) {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t ka = (uint32_t)(kb * 16384 + kk * 32);
+              const uint64_t da = tc::smem_desc(hs + ka, 16, 1024, tc::kSwizzle128B);
+              const uint64_t db = tc::smem_desc(
+                  sb + C::OFF_W3A + (uint32_t)(kb * kNAp * 128 + kk * 32), 16, 1024, tc::kSwizzle128B);
+              tc::mma_bf16(tcol, da, db, id3, (kb | kk) != 0);
+            }
+          };
+          auto act_half = [&](int l, int kb) {
+            if (warp_on) {
+              uint32_t hp[32];
+              act64(tm + (uint32_t)(kb * 64), bias + (uint32_t)(((l == 0 ? BO_B1A : BO_B2A) + kb * 64) * 4),
+                    hp);
+              store_row_sw128(hs + (uint32_t)kb * 16384u + (uint32_t)r * 128u, (uint32_t)(r & 7), hp);
             }
             tc::fence_async_smem();
             tc::fence_before_sync();
             bar_sync_n(my_bar_id, 128);
-            if (issuer) {
-              tc::fence_after_sync();
-#pragma unroll
-              for (int kb = 0; kb < 2; ++kb) {
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                  const uint32_t ka = (uint32_t)(kb * 16384 + kk * 32);
-                  const uint64_t da = tc::smem_desc(hs + ka, 16, 1024, tc::kSwizzle128B);
-                  if (l == 0) {
-                    const uint64_t db = tc::smem_desc(sb + C::OFF_W2A + ka, 16, 1024, tc::kSwizzle128B);
-                    tc::mma_bf16(tcol, da, db, id12, (kb | kk) != 0);
-                  } else {
-                    const uint64_t db = tc::smem_desc(
-                        sb + C::OFF_W3A + (uint32_t)(kb * kNAp * 128 + kk * 32), 16, 1024,
-                        tc::kSwizzle128B);
-                    tc::mma_bf16(tcol, da, db, id3, (kb | kk) != 0);
-                  }
-                }
-              }
-              tc::mma_commit(bar);
-            }
-            if (!tc::mbar_wait(bar, ph, d.wait_ns) && !wfail) { wfail = true; fsite = 2 + (uint32_t)l; }
-            ph ^= 1u;
+          };
+          act_half(0, 0);
+          if (issuer) {
             tc::fence_after_sync();
+            l2_mma(0, 0);
           }
+          act_half(0, 1);
+          if (issuer) {
+            tc::fence_after_sync();
+            l2_mma(1, 0);
+            l2_mma(0, 1);
+            tc::mma_commit(bar);
+            l2_mma(1, 1);
+            tc::mma_commit(bar2);
+          }
+          if (!tc::mbar_wait(bar, ph, d.wait_ns) && !wfail) { wfail = true; fsite = 2; }
+          ph ^= 1u;
+          tc::fence_after_sync();
+          act_half(1, 0);
+          if (issuer) {
+            tc::fence_after_sync();
+            l3_mma(0);
+          }
+          if (!tc::mbar_wait(bar2, ph2, d.wait_ns) && !wfail) { wfail = true; fsite = 2; }
+          ph2 ^= 1u;
+          tc::fence_after_sync();
+          act_half(1, 1);
+          if (issuer) {
+            tc::fence_after_sync();
+            l3_mma(1);
+            tc::mma_commit(bar);
+          }
+          if (!tc::mbar_wait(bar, ph, d.wait_ns) && !wfail) { wfail = true; fsite = 3; }
+          ph ^= 1u;
+          tc::fence_after_sync();
           if (warp_on) {
             uint32_t z0[16], z1[16];
             tmem_ld16(tm, z0);
