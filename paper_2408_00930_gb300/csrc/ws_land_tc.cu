@@ -62,6 +62,11 @@ constexpr int kNS = 2;                        // shared-memory sweep-block buffe
 constexpr int kNT = 3;                        // TMEM accumulators of the sweep (128 columns each)
 constexpr int kHdr = 256;                     // energy image header: {blocks, positive blocks}
 constexpr int kEpi = 256, kThreads = kEpi + 64;  // + a loader warp and an MMA warp
+// The roll-out kernel issues its sweep MMAs from two warps that take the even
+// and the odd blocks, so that one warp's waits run while the other's MMAs
+// keep the tensor core busy.
+constexpr int kMmaWarps = 2;
+constexpr int kRollThreads = kEpi + 32 * (1 + kMmaWarps);
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 // Packed policy image (copied verbatim to shared memory offset 0):
@@ -82,8 +87,9 @@ constexpr int OFF_XCH = OFF_BE + kNS * kEBBytes;  // f32 [128] each: partial ene
 constexpr int OFF_RECV = OFF_XCH + 4 * kRows * 4; // f32 [2][128] the cluster partner's partials
 constexpr int OFF_BAR = OFF_RECV + 2 * kRows * 4;
 constexpr int N_BAR = 5 + kNS + 2 * kNT;  // ae, b[kNS], mma[kNT], epi[kNT], pol, x, drain, drain_pol
-constexpr int OFF_CMD = OFF_BAR + N_BAR * 8;  // [0] sweep command, [1] end flag, [2] blocks loaded
-constexpr int OFF_TM = OFF_CMD + 16;
+// [0] sweep command, [1] end flag, [2] blocks loaded, [4 + w] blocks MMA warp w passed
+constexpr int OFF_CMD = OFF_BAR + N_BAR * 8;
+constexpr int OFF_TM = OFF_CMD + 32;
 constexpr int SMEM = OFF_TM + 16 + 1024;
 static_assert(SMEM <= 232448, "shared memory over the 227 KB per-CTA limit");
 static_assert(PK_W3 % 1024 == 0 && (4 * kN3 * 128) % 1024 == 0 && (kN3 * 128) % 1024 == 0,
@@ -391,11 +397,11 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t *bar, uint32_t parity
 }
 
 // Barrier ids: 1 the 256 epilogue threads; 2 + w the two warps (w, w + 4) of rows
-// 32w..; 6 the two producer warps.
+// 32w..; 6 the producer warps.
 constexpr uint32_t kBarEpi = 1, kBarPair0 = 2, kBarProd = 6;
 
 template <int D, int CL>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kRollThreads, 1)
     k_land_tc(Dev d, const uint8_t *__restrict__ pol, const uint8_t *__restrict__ eimg,
               const uint8_t *__restrict__ blocks, uint32_t n_steps) {
   constexpr int DH = D / 2;  // coordinates per thread of a row (two threads per row)
@@ -415,7 +421,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   {
     const uint4 *src = (const uint4 *)pol;
     uint4 *dst = (uint4 *)sm;
-    for (int i = tid; i < POLICY / 16; i += kThreads) dst[i] = __ldg(src + i);
+    for (int i = tid; i < POLICY / 16; i += kRollThreads) dst[i] = __ldg(src + i);
   }
   if (tid == 0) {
     tc::mbar_init(bar_ae, kEpi);
@@ -426,7 +432,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc::mbar_init(bar_pol, 1);
     tc::mbar_init(bar_x, kRows);
-    tc::mbar_init(bar_drain, 1);
+    tc::mbar_init(bar_drain, kMmaWarps);
     tc::mbar_init(bar_drain_pol, 1);
     cmd[0] = 0u;
     cmd[1] = 0u;
@@ -455,11 +461,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     // Block g of this CTA's sweep sequence lands in shared-memory buffer g % kNS
     // and accumulates in TMEM buffer g % kNT.  The loader (warp 8) refills a
     // shared-memory buffer as soon as the MMA that read it has completed, ahead of
-    // the sweeps (blocks do not depend on the env rows); the MMA warp (warp 9)
-    // issues block g once its bytes have landed, its accumulator has been read
-    // out, and the sweep's operand rows are ready.  The epilogue thus finds up to
-    // kNT blocks already multiplied.  A block's phase on one of these barriers is
-    // (g / buffers) & 1: no later phase can complete before the waiter acts.
+    // the sweeps (blocks do not depend on the env rows); MMA warp w (warp 9 + w)
+    // issues the blocks g = w mod 2 once their bytes have landed, their
+    // accumulator has been read out, and the sweep's operand rows are ready.
+    // The epilogue thus finds up to kNT blocks already multiplied.  A block's
+    // phase on one of these barriers is (g / buffers) & 1: no later phase can
+    // complete before the waiter acts (block g + kNT reuses g's accumulator only
+    // after the epilogue has read g, which follows g's completion, whichever
+    // warp issued either).
     volatile uint32_t *endf = cmd + 1, *s_gl = cmd + 2;
     const int lane = tid & 31;
     if (warp == kEpi / 32) {
@@ -468,21 +477,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t gl = 0;
         for (;;) {
           if (gl >= (uint32_t)kNS) {  // the MMA of block gl - kNS has read its buffer, or the end
+            // Polled with test_wait, which never suspends the thread, so that the
+            // copy starts within a few cycles of the MMA's completion (the next
+            // blocks' MMAs wait on it); the limit is counted on the SM clock
+            // (2 cycles per ns).
             const uint32_t gp = gl - kNS;
             bool got = false;
-            uint64_t t0 = 0;
-            for (int it = 0;; ++it) {
-              if (tc::mbar_try_wait_lim(bar_mma + gp % kNT, (gp / kNT) & 1u, wlim)) { got = true; break; }
+            const uint64_t c0 = tc::sm_clock();
+            for (;;) {
+              if (tc::mbar_test_wait(bar_mma + gp % kNT, (gp / kNT) & 1u)) { got = true; break; }
               if (*endf) break;
-              if (wlim < tc::kShortWaitNs) {  // short limits: the SM clock, 2 cycles per ns
-                if (it == 0) t0 = tc::sm_clock();
-                else if (tc::sm_clock() - t0 > 2 * wlim) { fail = true; break; }
-              } else if (it == 0) {
-                t0 = tc::global_ns();
-              } else if ((it & 255) == 0 && tc::global_ns() - t0 > wlim) {
-                fail = true;
-                break;
-              }
+              if (tc::sm_clock() - c0 > 2 * wlim) { fail = true; break; }
             }
             if (!got) break;
           }
@@ -495,9 +500,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         *s_gl = gl;
       }
       __syncwarp();
-      bar_sync_n(kBarProd, 64);
+      bar_sync_n(kBarProd, 32 * (1 + kMmaWarps));
     } else {
-      uint32_t g = 0;
+      const uint32_t mw = (uint32_t)(warp - kEpi / 32 - 1);  // this MMA warp
+      uint32_t g = 0;  // blocks passed (issued by either warp) in the sweep sequence
       if (lane == 0) {
         constexpr uint32_t idesc = tc::idesc_bf16_f32(128, kEB);
         uint32_t pa = 0;
@@ -506,6 +512,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           pa ^= 1u;
           if (*cmd == 0u) break;
           for (int i = 0; i < n_blk && !fail; ++i, ++g) {
+            if (g % kMmaWarps != mw) continue;  // the other warp's block
             const uint32_t sbuf = g % kNS, t = g % kNT;
             if (!tc::mbar_wait(bar_b + sbuf, (g / kNS) & 1u, wlim)) { fail = true; break; }
             if (g >= (uint32_t)kNT &&
@@ -520,15 +527,24 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc::mma_commit(bar_mma + t);
           }
         }
+        cmd[4 + mw] = g;
       }
       __syncwarp();
-      bar_sync_n(kBarProd, 64);
+      bar_sync_n(kBarProd, 32 * (1 + kMmaWarps));
       if (lane == 0) {
-        // blocks g .. gl - 1 were loaded ahead (or their MMA was never issued
-        // after a wait ran out): their copies finish before shared memory goes
-        // away, on every path
-        const uint32_t gl = *s_gl;
-        for (uint32_t q = g; q < gl; ++q) tc::mbar_wait(bar_b + q % kNS, (q / kNS) & 1u, tc::kDrainNs);
+        if (mw == 0) {
+          // blocks loaded ahead whose MMA was never issued (the sweeps' end, or
+          // a wait that ran out): their copies finish before shared memory goes
+          // away, on every path.  Block q belongs to warp q mod 2, which issued
+          // it if q is below the count that warp passed; a block never issued
+          // is the last one loaded into its buffer, so its phase is exact.
+          const uint32_t gl = *s_gl;
+          uint32_t g_min = cmd[4];
+          for (int w = 1; w < kMmaWarps; ++w) g_min = min(g_min, cmd[4 + w]);
+          for (uint32_t q = g_min; q < gl; ++q)
+            if (q >= cmd[4 + q % kMmaWarps])
+              tc::mbar_wait(bar_b + q % kNS, (q / kNS) & 1u, tc::kDrainNs);
+        }
         tc::mma_commit(bar_drain);
         tc::mbar_wait(bar_drain, 0, tc::kDrainNs);
       }
@@ -1299,14 +1315,14 @@ cudaError_t launch_land_d(const Dev &d, const uint8_t *pol, const uint8_t *eimg,
   const uint8_t *blocks = eimg + land_blocks_off((int)d.n_gauss);
   if (tile_ctas == 1) {
     const int grid = n_tiles < sms ? n_tiles : sms;
-    k_land_tc<D, 1><<<grid, kThreads, SMEM, st>>>(d, pol, eimg, blocks, n_steps);
+    k_land_tc<D, 1><<<grid, kRollThreads, SMEM, st>>>(d, pol, eimg, blocks, n_steps);
     return cudaGetLastError();
   }
   if (tile_ctas != 2) return cudaErrorInvalidValue;
   const int clusters = n_tiles < sms / 2 ? n_tiles : sms / 2;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(2 * clusters));
-  cfg.blockDim = dim3(kThreads);
+  cfg.blockDim = dim3(kRollThreads);
   cfg.dynamicSmemBytes = SMEM;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
