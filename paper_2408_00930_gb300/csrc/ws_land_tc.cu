@@ -746,8 +746,28 @@ __global__ void __launch_bounds__(kRollThreads, 1)
           }
           tc::mma_commit(bar_pol);
         }
+        // The step's Philox normals (this half's action coordinates, and the
+        // observation noise of the candidate) do not depend on the policy: they
+        // are drawn while the layer-2 MMA runs.
+        float zn[DH];
+        float zo = 0.f;
 #pragma unroll 1
         for (int l = 0; l < 3; ++l) {
+          if (l == 1) {
+#pragma unroll
+            for (int q = 0; q < DH / 4; ++q) {
+              const uint4 rw = draw(seed, k, d.env_base + e, 0, kTagAction, (uint32_t)((j0 + 4 * q) >> 2));
+              const float2 p = box_muller(rw.x, rw.y), p2 = box_muller(rw.z, rw.w);
+              zn[4 * q] = p.x;
+              zn[4 * q + 1] = p.y;
+              zn[4 * q + 2] = p2.x;
+              zn[4 * q + 3] = p2.y;
+            }
+            if (own) {
+              const uint4 rn = draw(seed, k, d.env_base + e, 0, kTagNoise, 0);
+              zo = box_muller(rn.x, rn.y).x;
+            }
+          }
           wait(bar_pol, pp);
           pp ^= 1u;
           tc::fence_after_sync();
@@ -824,13 +844,10 @@ __global__ void __launch_bounds__(kRollThreads, 1)
 #pragma unroll
           for (int q = 0; q < DH / 4; ++q) {
             const int j = j0 + 4 * q;
-            const uint4 rw = draw(seed, k, d.env_base + e, 0, kTagAction, (uint32_t)(j >> 2));
-            const float2 p = box_muller(rw.x, rw.y), p2 = box_muller(rw.z, rw.w);
-            const float z4[4] = {p.x, p.y, p2.x, p2.y};
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
               const int u = 4 * q + i;
-              const float zz = z4[i];
+              const float zz = zn[u];
               const float ls = fminf(fmaxf(lsr[u], -5.0f), 2.0f);
               const float smp = mu[u] + expf(ls) * zz;
               const float dx = fminf(fmaxf(smp, -clip), clip);
@@ -864,8 +881,7 @@ __global__ void __launch_bounds__(kRollThreads, 1)
           }
           // ---- step: observed energy, reward, done, auto-reset
           if (own) {
-            const uint4 rn = draw(seed, k, d.env_base + e, 0, kTagNoise, 0);
-            const float eobs2 = E + sig_n * box_muller(rn.x, rn.y).x;
+            const float eobs2 = E + sig_n * zo;
             if (rec) {
               const size_t o = rowR * S + e;
               d.r_energy[o] = E;
