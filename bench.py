@@ -759,8 +759,8 @@ def main():
         # algorithmic record bytes of the launch (control 29 B, economy 85 B,
         # landscape 205 B per agent-step)
         ncu_bytes = {"control_scale": (3.420672 + 135.461888) * 1e6,
-                     "economy": 92.860928e6 + 1.191251e9,
-                     "landscape": (1.816064 + 24.532480) * 1e6}
+                     "economy": 92.465664e6 + 1.185742e9,
+                     "landscape": (1.850368 + 25.001216) * 1e6}
         rec_bytes = {0: 29.0, 1: 85.0, 2: 205.0, 3: 37.0}[wl["env"]]
         if args.workload in ncu_bytes:
             roofline["traffic"] = ncu_bytes[args.workload]
