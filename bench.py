@@ -760,7 +760,7 @@ def main():
         # landscape 205 B per agent-step)
         ncu_bytes = {"control_scale": (3.420672 + 135.461888) * 1e6,
                      "economy": 92.465664e6 + 1.185742e9,
-                     "landscape": (1.867264 + 25.390592) * 1e6}
+                     "landscape": (1.850368 + 25.001216) * 1e6}
         rec_bytes = {0: 29.0, 1: 85.0, 2: 205.0, 3: 37.0}[wl["env"]]
         if args.workload in ncu_bytes:
             roofline["traffic"] = ncu_bytes[args.workload]

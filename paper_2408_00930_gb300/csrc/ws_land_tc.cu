@@ -8,17 +8,14 @@
 // landscape is a sum of M Gaussians, E(x) = sum_m a_m exp(-|x - c_m|^2 / (2 w_m^2)).
 //
 // A tile of 128 envs is served by a cluster of CL CTAs (CL = 1 or 2; a launch
-// parameter).  Both CTAs of a pair run layer 1 and the sampling for the whole
-// tile (identical inputs and instruction streams give identical results);
-// CTA r computes layer 2's units [128 r, 128 r + 128) and layer 3's partial
-// sums over them, and the two partial sums meet through distributed shared
-// memory (one bulk copy each way).  Each CTA sweeps its own 1/CL of the
-// Gaussians; the partial energies meet the same way.  A single CTA sums layer 3
-// as the same two halves, so the records do not depend on CL.  Per step:
+// parameter).  Every CTA of the cluster runs the same policy and sampling for
+// the tile (identical inputs and instruction streams give identical results)
+// and sweeps its own 1/CL of the Gaussians; the partial energies meet through
+// distributed shared memory.  Per step:
 //   policy   24-256-256-48 on tcgen05: layer 1 from the coordinates (K = 32,
 //            the bias in two constant columns), h1 and h2 written back to tensor
 //            memory as the A operand of the next layer (packed BF16), W2^T / W3^T
-//            (a pair: this CTA's units of them) resident in shared memory
+//            resident in shared memory
 //   sample   diagonal Gaussian head: mean, log sigma clamped to [-5, 2],
 //            dx = clip(mean + sigma z) with Philox normals; log-probability of the
 //            unclipped sample
@@ -31,18 +28,17 @@
 //            epilogue is one ex2 per pair summed into a positive and a negative
 //            part (each sign group padded to 128 Gaussians).  The operand row
 //            sits in tensor memory as the A operand; blocks of 128 Gaussians
-//            stream through shared-memory buffers (two; three in a pair; a
-//            loader warp) into three 128-column TMEM accumulators (two MMA
-//            warps taking the even and odd blocks, one M = 128, N = 128 MMA per
-//            K step); the two threads of a row take the blocks of even and odd
-//            index.
+//            stream through two shared-memory buffers (a loader warp) into
+//            three 128-column TMEM accumulators (an MMA warp, one M = 128,
+//            N = 128 MMA per K step); the two threads of a row take the
+//            blocks of even and odd index.
 //   step     observed energy with Philox noise, reward Eobs(x) - Eobs(x'), done
 //            at the episode limit or when E(y) falls below the energy target
 //            (the product basin of App. C), reset to U(-3, 3)^D and a second
 //            sweep for the fresh state's energy when a tile has a reset
 // Threads: warps 0-3 own the env rows (state, sampling, records); warps 4-7
 // take the other half of every tanh and exp epilogue; warp 8 loads the energy
-// blocks, warps 9 and 10 issue the energy MMAs.  Every wait is bounded; a wait that
+// blocks, warp 9 issues the energy MMAs.  Every wait is bounded; a wait that
 // runs out sets the error flag and the CTA leaves its loops at the next step
 // boundary.
 #include "ws_kernels.cuh"
@@ -62,6 +58,7 @@ constexpr int kBlk = 64;                      // Gaussians per block of the ener
 constexpr int kBlkBytes = kBlk * kKE * 2;     // block image, K = 80 without swizzle
 constexpr int kEB = 128;                      // Gaussians per energy MMA of the roll-out sweep
 constexpr int kEBBytes = kEB * kKE * 2;       // two consecutive image blocks
+constexpr int kNS = 2;                        // shared-memory sweep-block buffers
 constexpr int kNT = 3;                        // TMEM accumulators of the sweep (128 columns each)
 constexpr int kHdr = 256;                     // energy image header: {blocks, positive blocks}
 constexpr int kEpi = 256, kThreads = kEpi + 64;  // + a loader warp and an MMA warp
@@ -82,56 +79,22 @@ constexpr int PK_B2 = PK_W1 + kH * kK1 * 2;
 constexpr int PK_B3 = PK_B2 + kH * 4;
 constexpr int POLICY = PK_B3 + 64 * 4;
 
-// Packed policy image of one CTA of a tile pair, whose two CTAs split layer 2
-// by output unit (CTA r computes units [128 r, 128 r + 128)) and layer 3 by K
-// (the same units); copied verbatim to shared memory offset 0:
-//   W2^T SW128 [128 n][256 k] (this CTA's units) | W3^T SW128 [48 n][128 k]
-//   (the K rows of this CTA's units) | W1^T [256 n][32 k] as above | b2 f32 [256]
-//   | b3 f32 [64]
-constexpr int PK2_W2 = 0;
-constexpr int PK2_W3 = PK2_W2 + 4 * (kH / 2) * 128;
-constexpr int PK2_W1 = PK2_W3 + 2 * kN3 * 128;
-constexpr int PK2_B2 = PK2_W1 + kH * kK1 * 2;
-constexpr int PK2_B3 = PK2_B2 + kH * 4;
-constexpr int POLICY2 = PK2_B3 + 64 * 4;
-static_assert(PK_W3 % 1024 == 0 && (4 * kN3 * 128) % 1024 == 0 && (kN3 * 128) % 1024 == 0 &&
-                  PK2_W3 % 1024 == 0,
+// shared memory
+constexpr int OFF_AE = POLICY;                    // layer-1 A [128][32] (the energy A is in TMEM)
+constexpr int OFF_BE = OFF_AE + kRows * kK1 * 2;  // kNS energy B blocks of kEB Gaussians
+constexpr int OFF_XCH = OFF_BE + kNS * kEBBytes;  // f32 [128] each: partial energy, log-probability,
+                                                  // |y|^2 of half 0 and of half 1
+constexpr int OFF_RECV = OFF_XCH + 4 * kRows * 4; // f32 [2][128] the cluster partner's partials
+constexpr int OFF_BAR = OFF_RECV + 2 * kRows * 4;
+constexpr int N_BAR = 5 + kNS + 2 * kNT;  // ae, b[kNS], mma[kNT], epi[kNT], pol, x, drain, drain_pol
+// [0] sweep command, [1] end flag, [2] blocks loaded, [4 + w] blocks MMA warp w passed
+constexpr int OFF_CMD = OFF_BAR + N_BAR * 8;
+constexpr int OFF_TM = OFF_CMD + 32;
+constexpr int SMEM = OFF_TM + 16 + 1024;
+static_assert(SMEM <= 232448, "shared memory over the 227 KB per-CTA limit");
+static_assert(PK_W3 % 1024 == 0 && (4 * kN3 * 128) % 1024 == 0 && (kN3 * 128) % 1024 == 0,
               "SW128 alignment");
-static_assert(POLICY % 256 == 0 && POLICY2 % 256 == 0, "the images follow one another");
-
-// Shared memory of a CTA of a tile served by CL CTAs.  A pair (CL = 2) holds
-// half of W2^T, so it has room for four sweep-block buffers and a buffer for
-// the partner's layer-3 partial sums.
-template <int CL>
-struct LandSm {
-  static constexpr bool SPLIT = CL > 1;
-  static constexpr int POL = SPLIT ? POLICY2 : POLICY;
-  static constexpr int W1 = SPLIT ? PK2_W1 : PK_W1;
-  static constexpr int B2 = SPLIT ? PK2_B2 : PK_B2;
-  static constexpr int B3 = SPLIT ? PK2_B3 : PK_B3;
-  static constexpr int NS = SPLIT ? 3 : 2;            // shared-memory sweep-block buffers
-  static constexpr int OFF_AE = POL;                  // layer-1 A [128][32] (the energy A is in TMEM)
-  // f32 [2 halves][128 rows][D] each: the partner's layer-3 partial sums, and
-  // this CTA's, staged for the bulk copy to the partner
-  static constexpr int Z3_BYTES = SPLIT ? 2 * kRows * kMaxD * 4 : 0;
-  static constexpr int OFF_Z3 = OFF_AE + kRows * kK1 * 2;
-  static constexpr int OFF_Z3S = OFF_Z3 + Z3_BYTES;
-  static constexpr int OFF_BE = OFF_Z3S + Z3_BYTES;  // NS energy B blocks
-  static constexpr int OFF_XCH = OFF_BE + NS * kEBBytes;  // f32 [128] each: partial energy,
-                                                          // log-probability, |y|^2 of both halves
-  static constexpr int OFF_RECV = OFF_XCH + 4 * kRows * 4;  // f32 [2][128] the partner's energies
-  static constexpr int OFF_BAR = OFF_RECV + 2 * kRows * 4;
-  // ae, b[NS], mma[kNT], epi[kNT], pol, x, drain, drain_pol, z3
-  static constexpr int N_BAR = 6 + NS + 2 * kNT;
-  // [0] sweep command, [1] end flag, [2] blocks loaded, [4 + w] blocks MMA warp w passed
-  static constexpr int OFF_CMD = OFF_BAR + N_BAR * 8;
-  static constexpr int OFF_TM = OFF_CMD + 32;
-  static constexpr int SMEM = OFF_TM + 16 + 1024;
-  static_assert(SMEM <= 232448, "shared memory over the 227 KB per-CTA limit");
-  static_assert(OFF_AE % 128 == 0 && OFF_Z3 % 16 == 0 && OFF_Z3S % 16 == 0 && OFF_BE % 16 == 0 &&
-                    OFF_BAR % 8 == 0,
-                "alignment");
-};
+static_assert(OFF_AE % 128 == 0 && OFF_BE % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
 
 constexpr uint32_t TM_H = 256;   // TMEM columns of h1 / h2 (packed BF16 A operand)
 constexpr uint32_t TM_A = 448;   // TMEM columns of the energy A operand [128][80] (BF16 pairs)
@@ -176,36 +139,6 @@ __global__ void k_land_tc_pack_policy(const float *__restrict__ p, int D, uint8_
   }
   for (int i = tid; i < kH; i += stride) ((float *)(out + PK_B2))[i] = b2[i];
   for (int i = tid; i < 64; i += stride) ((float *)(out + PK_B3))[i] = i < 2 * D ? b3[i] : 0.f;
-}
-
-// The two images of a tile pair, rank r at out + r POLICY2.
-__global__ void k_land_tc_pack_policy2(const float *__restrict__ p, int D, uint8_t *__restrict__ out) {
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-  const float *W1 = p, *b1 = W1 + D * kH, *W2 = b1 + kH, *b2 = W2 + kH * kH;
-  const float *W3 = b2 + kH, *b3 = W3 + kH * 2 * D;
-  constexpr int HU = kH / 2;  // units per CTA
-  for (int r = 0; r < 2; ++r) {
-    uint8_t *o = out + (size_t)r * POLICY2;
-    for (int i = tid; i < HU * kH; i += stride) {
-      const int n = i / kH, k = i % kH;
-      *(uint16_t *)(o + PK2_W2 + sw128_off(n, k, HU)) = bf16_bits(W2[k * kH + r * HU + n]);
-    }
-    for (int i = tid; i < kN3 * HU; i += stride) {
-      const int n = i / HU, k = i % HU;
-      *(uint16_t *)(o + PK2_W3 + sw128_off(n, k, kN3)) =
-          bf16_bits(n < 2 * D ? W3[(r * HU + k) * 2 * D + n] : 0.f);
-    }
-    for (int i = tid; i < kH * kK1; i += stride) {
-      const int n = i / kK1, q = i % kK1;
-      float v = 0.f;
-      if (q < D) v = W1[q * kH + n];
-      else if (q == D) v = bf16_val(b1[n]);
-      else if (q == D + 1) v = b1[n] - bf16_val(b1[n]);
-      *(uint16_t *)(o + PK2_W1 + ns_off(n, q, kK1)) = bf16_bits(v);
-    }
-    for (int i = tid; i < kH; i += stride) ((float *)(o + PK2_B2))[i] = b2[i];
-    for (int i = tid; i < 64; i += stride) ((float *)(o + PK2_B3))[i] = i < 2 * D ? b3[i] : 0.f;
-  }
 }
 
 // Energy image: a header {block count (even), blocks of non-negative
@@ -425,14 +358,6 @@ __device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank) {
 __device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v) {
   asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
-// Bulk copy from this CTA's shared memory to the cluster partner's (dst and bar
-// are the partner's addresses); completes bytes on the partner's barrier.
-__device__ __forceinline__ void bulk_s2s_cluster(uint32_t dst, uint32_t src, uint32_t bytes, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-      "r"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
 __device__ __forceinline__ void arrive_remote(uint32_t addr) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
 }
@@ -479,26 +404,24 @@ template <int D, int CL>
 __global__ void __launch_bounds__(kRollThreads, 1)
     k_land_tc(Dev d, const uint8_t *__restrict__ pol, const uint8_t *__restrict__ eimg,
               const uint8_t *__restrict__ blocks, uint32_t n_steps) {
-  using C = LandSm<CL>;
-  constexpr int kNS = C::NS;
   constexpr int DH = D / 2;  // coordinates per thread of a row (two threads per row)
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = tc::smem_u32(smem_raw);
   uint8_t *sm = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
   const uint32_t sb = tc::smem_u32(sm);
   const int tid = threadIdx.x, warp = tid >> 5;
-  uint64_t *bars = (uint64_t *)(sm + C::OFF_BAR);
+  uint64_t *bars = (uint64_t *)(sm + OFF_BAR);
   uint64_t *bar_ae = bars, *bar_b = bars + 1, *bar_mma = bar_b + kNS, *bar_epi = bar_mma + kNT;
   uint64_t *bar_pol = bar_epi + kNT, *bar_x = bar_pol + 1, *bar_drain = bar_x + 1;
-  uint64_t *bar_drain_pol = bar_drain + 1, *bar_z3 = bar_drain_pol + 1;
-  volatile uint32_t *cmd = (volatile uint32_t *)(sm + C::OFF_CMD);
-  uint32_t *tm_holder = (uint32_t *)(sm + C::OFF_TM);
+  uint64_t *bar_drain_pol = bar_drain + 1;
+  volatile uint32_t *cmd = (volatile uint32_t *)(sm + OFF_CMD);
+  uint32_t *tm_holder = (uint32_t *)(sm + OFF_TM);
   const uint32_t rank = CL > 1 ? cluster_rank() : 0u;
 
   {
-    const uint4 *src = (const uint4 *)(CL > 1 ? pol + POLICY + (size_t)rank * POLICY2 : pol);
+    const uint4 *src = (const uint4 *)pol;
     uint4 *dst = (uint4 *)sm;
-    for (int i = tid; i < C::POL / 16; i += kRollThreads) dst[i] = __ldg(src + i);
+    for (int i = tid; i < POLICY / 16; i += kRollThreads) dst[i] = __ldg(src + i);
   }
   if (tid == 0) {
     tc::mbar_init(bar_ae, kEpi);
@@ -511,7 +434,6 @@ __global__ void __launch_bounds__(kRollThreads, 1)
     tc::mbar_init(bar_x, kRows);
     tc::mbar_init(bar_drain, kMmaWarps);
     tc::mbar_init(bar_drain_pol, 1);
-    tc::mbar_init(bar_z3, 1);  // this CTA's expect-tx; the partner's bulk copy completes the bytes
     cmd[0] = 0u;
     cmd[1] = 0u;
     cmd[2] = 0u;
@@ -571,7 +493,7 @@ __global__ void __launch_bounds__(kRollThreads, 1)
           }
           const uint32_t sbuf = gl % kNS;
           mbar_expect_tx(bar_b + sbuf, kEBBytes);
-          bulk_g2s(sb + C::OFF_BE + sbuf * kEBBytes, src0 + (size_t)(gl % (uint32_t)n_blk) * kEBBytes,
+          bulk_g2s(sb + OFF_BE + sbuf * kEBBytes, src0 + (size_t)(gl % (uint32_t)n_blk) * kEBBytes,
                    kEBBytes, bar_b + sbuf);
           ++gl;
         }
@@ -598,7 +520,7 @@ __global__ void __launch_bounds__(kRollThreads, 1)
             tc::fence_after_sync();
 #pragma unroll
             for (int s = 0; s < kKE / 16; ++s) {
-              const uint64_t db = tc::smem_desc(sb + C::OFF_BE + sbuf * kEBBytes + (uint32_t)s * 256u,
+              const uint64_t db = tc::smem_desc(sb + OFF_BE + sbuf * kEBBytes + (uint32_t)s * 256u,
                                                 128, kKE * 16, tc::kSwizzleNone);
               mma_ts(tbase + TM_E + t * kEB, tbase + TM_A + (uint32_t)(8 * s), db, idesc, s != 0);
             }
@@ -642,9 +564,8 @@ __global__ void __launch_bounds__(kRollThreads, 1)
     const int j0 = h * DH;
     const uint32_t lane_sel = (uint32_t)((warp & 3) * 32) << 16;
     const uint32_t pair = kBarPair0 + (uint32_t)(warp & 3);
-    float *xch_e = (float *)(sm + C::OFF_XCH), *xch_lp = xch_e + kRows, *xch_yy = xch_lp + kRows;
-    float *recv = (float *)(sm + C::OFF_RECV);
-    const float *z3recv = (const float *)(sm + C::OFF_Z3);
+    float *xch_e = (float *)(sm + OFF_XCH), *xch_lp = xch_e + kRows, *xch_yy = xch_lp + kRows;
+    float *recv = (float *)(sm + OFF_RECV);
     const uint64_t seed = d.seed;
     const uint64_t k0 = d.k[0];
     const uint32_t R = d.ring_steps;
@@ -652,23 +573,17 @@ __global__ void __launch_bounds__(kRollThreads, 1)
     const float sig_n = d.noise_sigma, clip = d.step_clip;
     const float half_log_2pi = 0.91893853320467274f;
     constexpr uint32_t id_pol = tc::idesc_bf16_f32(128, kH);
-    constexpr uint32_t id_pol2 = tc::idesc_bf16_f32(128, kH / CL);  // layer 2: this CTA's units
     constexpr uint32_t id_out = tc::idesc_bf16_f32(128, kN3);
-    uint32_t pp = 0, ge = 0, px = 0, par = 0, pz = 0;
+    uint32_t pp = 0, ge = 0, px = 0, par = 0;
     // After a wait has run out no other wait is attempted: the CTA runs on to the
     // vote at the next step boundary and leaves together.
     auto wait = [&](uint64_t *bar, uint32_t parity) {
       if (!fail && !tc::mbar_wait(bar, parity, wlim)) fail = true;
     };
     const uint32_t partner = rank ^ 1u;
-    const uint32_t recv_remote = CL > 1 ? mapa(sb + C::OFF_RECV, partner) : 0u;
+    const uint32_t recv_remote = CL > 1 ? mapa(sb + OFF_RECV, partner) : 0u;
     const uint32_t barx_remote = CL > 1 ? mapa(tc::smem_u32(bar_x), partner) : 0u;
-    // this thread's slot of the layer-3 buffers: [half][row][D]
-    const uint32_t z3_slot = (uint32_t)((h * kRows + r) * D) * 4u;
-    const uint32_t z3_remote = CL > 1 ? mapa(sb + C::OFF_Z3, partner) : 0u;
-    const uint32_t barz3_remote = CL > 1 ? mapa(tc::smem_u32(bar_z3), partner) : 0u;
-    constexpr uint32_t kZ3Copy = 2u * kRows * D * 4u;  // bytes of one exchange
-    const uint32_t a1_row = sb + C::OFF_AE + (uint32_t)(r >> 3) * (kK1 * 16) + (uint32_t)(r & 7) * 16u;
+    const uint32_t a1_row = sb + OFF_AE + (uint32_t)(r >> 3) * (kK1 * 16) + (uint32_t)(r & 7) * 16u;
     const uint32_t ae_tm = tbase + lane_sel + TM_A;  // this row's energy operand (TMEM lane r)
     // byte offset of element k within a row of a K-major operand without swizzle
     auto kofs = [](int k) -> uint32_t { return (uint32_t)((k >> 3) * 128 + (k & 7) * 2); };
@@ -825,8 +740,8 @@ __global__ void __launch_bounds__(kRollThreads, 1)
           tc::fence_after_sync();
 #pragma unroll
           for (int q = 0; q < kK1 / 16; ++q) {
-            const uint64_t da = tc::smem_desc(sb + C::OFF_AE + (uint32_t)q * 256u, 128, kK1 * 16, tc::kSwizzleNone);
-            const uint64_t db = tc::smem_desc(sb + C::W1 + (uint32_t)q * 256u, 128, kK1 * 16, tc::kSwizzleNone);
+            const uint64_t da = tc::smem_desc(sb + OFF_AE + (uint32_t)q * 256u, 128, kK1 * 16, tc::kSwizzleNone);
+            const uint64_t db = tc::smem_desc(sb + PK_W1 + (uint32_t)q * 256u, 128, kK1 * 16, tc::kSwizzleNone);
             tc::mma_bf16(tbase, da, db, id_pol, q != 0);
           }
           tc::mma_commit(bar_pol);
@@ -857,17 +772,13 @@ __global__ void __launch_bounds__(kRollThreads, 1)
           pp ^= 1u;
           tc::fence_after_sync();
           if (l == 2) break;
-          // ---- tanh epilogue of layer l + 1: columns [128 h, 128 h + 128) -> packed
-          // h (layer 2 of a pair: this CTA's 128 units, columns [64 h, 64 h + 64))
-          const bool half_w = CL > 1 && l == 1;
+          // ---- tanh epilogue of layer l + 1: columns [128 h, 128 h + 128) -> packed h
 #pragma unroll
           for (int q = 0; q < 2; ++q) {
-            if (half_w && q == 1) break;
             uint32_t hp[32];
 #pragma unroll
             for (int hf = 0; hf < 2; ++hf) {
-              const uint32_t c0 = half_w ? (uint32_t)(64 * h + 32 * hf) : (uint32_t)(128 * h + 64 * q + 32 * hf);
-              const uint32_t cb = half_w ? c0 + (uint32_t)(rank * (kH / 2)) : c0;  // the unit of b2
+              const uint32_t c0 = (uint32_t)(128 * h + 64 * q + 32 * hf);
               uint32_t z[32];
               tc::tmem_ld32(tbase + lane_sel + c0, z);
               tc::tmem_wait_ld();
@@ -875,52 +786,28 @@ __global__ void __launch_bounds__(kRollThreads, 1)
               for (int i = 0; i < 16; ++i) {
                 float z0 = __uint_as_float(z[2 * i]), z1 = __uint_as_float(z[2 * i + 1]);
                 if (l == 1) {
-                  const float2 bb = *(const float2 *)(sm + C::B2 + (cb + 2 * i) * 4);
+                  const float2 bb = *(const float2 *)(sm + PK_B2 + (c0 + 2 * i) * 4);
                   z0 += bb.x;
                   z1 += bb.y;
                 }
                 hp[hf * 16 + i] = tc::pack_bf16x2(tc::tanh_fast(z0), tc::tanh_fast(z1));
               }
             }
-            tmem_st32(tbase + lane_sel + TM_H + (uint32_t)(half_w ? 32 * h : 64 * h + 32 * q), hp);
+            tmem_st32(tbase + lane_sel + TM_H + (uint32_t)(64 * h + 32 * q), hp);
           }
           tmem_wait_st();
           tc::fence_before_sync();
           bar_sync_n(kBarEpi, kEpi);
           if (tid == 0) {
             tc::fence_after_sync();
-            if (CL == 1) {
-              // layer 2 (l = 0): N = 256 into columns [0, 256); layer 3 (l = 1): N = 48
+            // layer 2 (l = 0): N = 256 into columns [0, 256); layer 3 (l = 1): N = 48
 #pragma unroll
-              for (int q = 0; q < kH / 16; ++q) {
-                const int kb = q >> 2, kk = q & 3;
-                const uint32_t boff = l == 0 ? (uint32_t)(PK_W2 + kb * kH * 128 + kk * 32)
-                                             : (uint32_t)(PK_W3 + kb * kN3 * 128 + kk * 32);
-                const uint64_t db = tc::smem_desc(sb + boff, 16, 1024, tc::kSwizzle128B);
-                // layer 3 as two K halves (units 0-127 into columns [0, 48), units
-                // 128-255 into [64, 112)), summed after, as a tile pair sums them
-                const uint32_t dcol = (l == 1 && q >= kH / 32) ? 64u : 0u;
-                const bool acc = l == 0 ? q != 0 : (q % (kH / 32)) != 0;
-                mma_ts(tbase + dcol, tbase + TM_H + (uint32_t)(8 * q), db, l == 0 ? id_pol : id_out, acc);
-              }
-            } else if (l == 0) {
-              // layer 2 of a pair: this CTA's 128 units (N = 128) over all of h1 (K = 256)
-#pragma unroll
-              for (int q = 0; q < kH / 16; ++q) {
-                const int kb = q >> 2, kk = q & 3;
-                const uint64_t db = tc::smem_desc(sb + (uint32_t)(PK2_W2 + kb * (kH / 2) * 128 + kk * 32), 16,
-                                                  1024, tc::kSwizzle128B);
-                mma_ts(tbase, tbase + TM_H + (uint32_t)(8 * q), db, id_pol2, q != 0);
-              }
-            } else {
-              // layer 3 of a pair: this CTA's partial sums over its units' h2 (K = 128)
-#pragma unroll
-              for (int q = 0; q < kH / 32; ++q) {
-                const int kb = q >> 2, kk = q & 3;
-                const uint64_t db = tc::smem_desc(sb + (uint32_t)(PK2_W3 + kb * kN3 * 128 + kk * 32), 16,
-                                                  1024, tc::kSwizzle128B);
-                mma_ts(tbase, tbase + TM_H + (uint32_t)(8 * q), db, id_out, q != 0);
-              }
+            for (int q = 0; q < kH / 16; ++q) {
+              const int kb = q >> 2, kk = q & 3;
+              const uint32_t boff = l == 0 ? (uint32_t)(PK_W2 + kb * kH * 128 + kk * 32)
+                                           : (uint32_t)(PK_W3 + kb * kN3 * 128 + kk * 32);
+              const uint64_t db = tc::smem_desc(sb + boff, 16, 1024, tc::kSwizzle128B);
+              mma_ts(tbase, tbase + TM_H + (uint32_t)(8 * q), db, l == 0 ? id_pol : id_out, q != 0);
             }
             tc::mma_commit(bar_pol);
           }
@@ -932,65 +819,26 @@ __global__ void __launch_bounds__(kRollThreads, 1)
           float out[2 * D];
 #pragma unroll
           for (int q = 0; q < kN3 / 16; ++q) {
-            uint32_t z[16], z2[16];
+            uint32_t z[16];
             tmem_ld16(tbase + lane_sel + (uint32_t)(16 * q), z);
-            if (CL == 1) tmem_ld16(tbase + lane_sel + 64u + (uint32_t)(16 * q), z2);
             tc::tmem_wait_ld();
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
               const int c = 16 * q + i;
-              if (c < 2 * D)
-                out[c] = CL == 1 ? __uint_as_float(z[i]) + __uint_as_float(z2[i]) : __uint_as_float(z[i]);
+              if (c < 2 * D) out[c] = __uint_as_float(z[i]) + *(const float *)(sm + PK_B3 + c * 4);
             }
           }
-          // this half's coordinates: means j0 + i, log sigmas D + j0 + i
+          if (rec && own && d.dbg_logits) {
+#pragma unroll
+            for (int c = 0; c < 2 * D; ++c) d.out[(size_t)e * 2 * D + c] = out[c];
+#pragma unroll
+            for (int c = 0; c < 2 * D; ++c) d.r_pout[(rowR * 2 * D + c) * S + e] = out[c];
+          }
           float mu[DH], lsr[DH];
 #pragma unroll
-          for (int i = 0; i < DH; ++i) {  // (static indices: out stays in registers)
+          for (int i = 0; i < DH; ++i) {
             mu[i] = own ? out[i] : out[DH + i];
             lsr[i] = own ? out[D + i] : out[D + DH + i];
-          }
-          if (CL > 1) {
-            // the pair's two partial sums meet: every thread stages its partials,
-            // one bulk copy takes all of them to the partner's buffer and
-            // completes the partner's barrier by its byte count, and this CTA's
-            // barrier completes when the partner's copy has landed here (a sum
-            // of two terms is the same in either order, so both CTAs hold the
-            // same bits)
-            float *stg = (float *)(sm + C::OFF_Z3S + z3_slot);
-#pragma unroll
-            for (int q = 0; q < DH / 4; ++q) {
-              *(float4 *)(stg + 4 * q) = make_float4(mu[4 * q], mu[4 * q + 1], mu[4 * q + 2], mu[4 * q + 3]);
-              *(float4 *)(stg + DH + 4 * q) = make_float4(lsr[4 * q], lsr[4 * q + 1], lsr[4 * q + 2], lsr[4 * q + 3]);
-            }
-            tc::fence_async_smem();  // the staged partials before the bulk copy reads them
-            bar_sync_n(kBarEpi, kEpi);
-            if (tid == 0) {
-              mbar_expect_tx(bar_z3, kZ3Copy);
-              bulk_s2s_cluster(z3_remote, sb + C::OFF_Z3S, kZ3Copy, barz3_remote);
-            }
-            if (!fail && !mbar_wait_cluster(bar_z3, pz, wlim)) fail = true;
-            pz ^= 1u;
-            const float *o = z3recv + z3_slot / 4u;
-#pragma unroll
-            for (int i = 0; i < DH; ++i) {
-              mu[i] = mu[i] + o[i];
-              lsr[i] = lsr[i] + o[DH + i];
-            }
-          }
-#pragma unroll
-          for (int i = 0; i < DH; ++i) {
-            mu[i] += *(const float *)(sm + C::B3 + (j0 + i) * 4);
-            lsr[i] += *(const float *)(sm + C::B3 + (D + j0 + i) * 4);
-          }
-          if (rec && d.dbg_logits) {
-#pragma unroll
-            for (int i = 0; i < DH; ++i) {
-              d.out[(size_t)e * 2 * D + j0 + i] = mu[i];
-              d.out[(size_t)e * 2 * D + D + j0 + i] = lsr[i];
-              d.r_pout[(rowR * 2 * D + (size_t)(j0 + i)) * S + e] = mu[i];
-              d.r_pout[(rowR * 2 * D + (size_t)(D + j0 + i)) * S + e] = lsr[i];
-            }
           }
           float *act = (float *)d.r_act + rowR * (size_t)D * S + e;
 #pragma unroll
@@ -1427,7 +1275,7 @@ bool land_tc_supported(int D, int M, const PolicyShape &p) {
   return D >= 8 && D <= kMaxD && D % 8 == 0 && M >= 1 && p.w[0] == D && p.w[1] == kH &&
          p.w[2] == kH && p.w[3] == 2 * D;
 }
-size_t land_tc_policy_bytes() { return (size_t)POLICY + 2 * (size_t)POLICY2; }
+size_t land_tc_policy_bytes() { return (size_t)POLICY; }
 size_t land_tc_energy_bytes(int M) {
   return land_blocks_off(M) + (size_t)(land_slots(M) / kBlk) * kBlkBytes;
 }
@@ -1456,7 +1304,6 @@ void launch_land_tc_pack(const Dev &d, void *policy_img, void *energy_img, cudaS
   uint8_t *img = (uint8_t *)energy_img;
   int32_t *order = (int32_t *)(img + land_order_off());
   k_land_tc_pack_policy<<<64, 256, 0, st>>>(d.params, (int)d.dim, (uint8_t *)policy_img);
-  k_land_tc_pack_policy2<<<64, 256, 0, st>>>(d.params, (int)d.dim, (uint8_t *)policy_img + POLICY);
   k_land_tc_order<<<1, 1024, 0, st>>>(d.amps, M, slots, (int32_t *)img, order);
   k_land_tc_pack_energy<<<128, 256, 0, st>>>(d.centres, d.widths, d.amps, (int)d.dim, slots, order,
                                              img + land_blocks_off(M));
@@ -1464,8 +1311,8 @@ void launch_land_tc_pack(const Dev &d, void *policy_img, void *energy_img, cudaS
 
 template <int D>
 void land_attr() {
-  cudaFuncSetAttribute(k_land_tc<D, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, LandSm<1>::SMEM);
-  cudaFuncSetAttribute(k_land_tc<D, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, LandSm<2>::SMEM);
+  cudaFuncSetAttribute(k_land_tc<D, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+  cudaFuncSetAttribute(k_land_tc<D, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
 }
 
 void land_tc_init() {
@@ -1484,7 +1331,7 @@ cudaError_t launch_land_d(const Dev &d, const uint8_t *pol, const uint8_t *eimg,
   const uint8_t *blocks = eimg + land_blocks_off((int)d.n_gauss);
   if (tile_ctas == 1) {
     const int grid = n_tiles < sms ? n_tiles : sms;
-    k_land_tc<D, 1><<<grid, kRollThreads, LandSm<1>::SMEM, st>>>(d, pol, eimg, blocks, n_steps);
+    k_land_tc<D, 1><<<grid, kRollThreads, SMEM, st>>>(d, pol, eimg, blocks, n_steps);
     return cudaGetLastError();
   }
   if (tile_ctas != 2) return cudaErrorInvalidValue;
@@ -1492,7 +1339,7 @@ cudaError_t launch_land_d(const Dev &d, const uint8_t *pol, const uint8_t *eimg,
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(2 * clusters));
   cfg.blockDim = dim3(kRollThreads);
-  cfg.dynamicSmemBytes = LandSm<2>::SMEM;
+  cfg.dynamicSmemBytes = SMEM;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
