@@ -462,7 +462,18 @@ __global__ void k_fwd_thin(const float *__restrict__ X, const float *__restrict_
   float acc[NT];
 #pragma unroll
   for (int n = 0; n < NT; ++n) acc[n] = 0.f;
-  for (int k = lane; k < K; k += 32) {
+  int k = lane;
+  for (; k + 96 < K; k += 128) {  // four of the lane's inputs in flight, the sums in k order
+    float x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x[u] = X[(size_t)r * K + k + 32 * u];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int n = 0; n < NT; ++n)
+        if (n < N) acc[n] = fmaf(x[u], W[(size_t)(k + 32 * u) * N + n], acc[n]);
+  }
+  for (; k < K; k += 32) {
     const float x = X[(size_t)r * K + k];
 #pragma unroll
     for (int n = 0; n < NT; ++n)
@@ -501,7 +512,20 @@ __global__ __launch_bounds__(256) void k_fwd_thin_k(const float *__restrict__ X,
   for (int k = 0; k < KT; ++k) w[k] = k < K ? W[(size_t)k * N + n] : 0.f;
   const float bn = b[n];
   const int nr = min(kFwdRows, rows - r0);
-  for (int rr = 0; rr < nr; ++rr) {
+  int rr = 0;
+  for (; rr + 4 <= nr; rr += 4) {  // four independent rows in flight
+    float acc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      acc[u] = 0.f;
+#pragma unroll
+      for (int k = 0; k < KT; ++k)
+        if (k < K) acc[u] = fmaf(Xs[rr + u][k], w[k], acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) Y[(size_t)(r0 + rr + u) * N + n] = TANH ? tanhf(acc[u] + bn) : acc[u] + bn;
+  }
+  for (; rr < nr; ++rr) {
     float acc = 0.f;
 #pragma unroll
     for (int k = 0; k < KT; ++k)
@@ -565,12 +589,23 @@ __global__ __launch_bounds__(256) void k_wgrad_thin_n(const float *__restrict__ 
       Ds[rr][n] = (rr < nr && n < N) ? D[(size_t)(r0 + rr) * N + n] : 0.f;
     }
     __syncthreads();
-    if (m <= M)
-      for (int rr = 0; rr < nr; ++rr) {
+    if (m <= M) {
+      int rr = 0;
+      for (; rr + 8 <= nr; rr += 8) {  // eight rows' loads in flight, the sums in row order
+        float a[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = m == M ? 1.f : Ain[(size_t)(r0 + rr + u) * M + m];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int n = 0; n < NT; ++n) acc[n] = fmaf(a[u], Ds[rr + u][n], acc[n]);
+      }
+      for (; rr < nr; ++rr) {
         const float a = m == M ? 1.f : Ain[(size_t)(r0 + rr) * M + m];
 #pragma unroll
         for (int n = 0; n < NT; ++n) acc[n] = fmaf(a, Ds[rr][n], acc[n]);
       }
+    }
   }
   if (m > M) return;
   float *out = P + (size_t)z * (M + 1) * N + (size_t)m * N;
@@ -601,12 +636,23 @@ __global__ __launch_bounds__(256) void k_wgrad_thin_m(const float *__restrict__ 
       As[rr][m] = (rr < nr && m < M) ? Ain[(size_t)(r0 + rr) * M + m] : (rr < nr && m == M ? 1.f : 0.f);
     }
     __syncthreads();
-    if (n < N)
-      for (int rr = 0; rr < nr; ++rr) {
+    if (n < N) {
+      int rr = 0;
+      for (; rr + 8 <= nr; rr += 8) {  // eight rows' loads in flight, the sums in row order
+        float dv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) dv[u] = D[(size_t)(r0 + rr + u) * N + n];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int m = 0; m <= MT; ++m) acc[m] = fmaf(As[rr + u][m], dv[u], acc[m]);
+      }
+      for (; rr < nr; ++rr) {
         const float dv = D[(size_t)(r0 + rr) * N + n];
 #pragma unroll
         for (int m = 0; m <= MT; ++m) acc[m] = fmaf(As[rr][m], dv, acc[m]);
       }
+    }
   }
   if (n >= N) return;
   float *out = P + (size_t)z * (M + 1) * N + n;
