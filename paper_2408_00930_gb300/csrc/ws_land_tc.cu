@@ -282,13 +282,6 @@ __device__ __forceinline__ void tmem_wait_ld_regs(uint32_t (&z)[32]) {
       :
       : "memory");
 }
-__device__ __forceinline__ float4 lds128f(uint32_t addr) {
-  float4 v;
-  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "r"(addr));
-  return v;
-}
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&z)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
