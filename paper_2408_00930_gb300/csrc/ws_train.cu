@@ -29,7 +29,7 @@ namespace ws {
 
 namespace {
 
-constexpr int kSliceRows = 512;    // rows per weight-gradient partial (128 x 128 GEMM)
+constexpr int kSliceRows = 1024;   // rows per weight-gradient partial (128 x 128 GEMM)
 constexpr int kThinSlice = 128;    // rows per partial of the thin kernels (more blocks)
 
 // Ring offset (row of step, slot) of row i of the chunk starting at global
@@ -789,7 +789,7 @@ void mlp_forward(const Dev &d, const PolicyShape &sh, const float *params, const
 
 // Backward through one three-layer MLP for a chunk: X [rows][w0], h1, h2 the
 // tanh activations, dout [rows][w3] the gradient at the output.  Per layer the
-// weight gradient as 512-row slice partials (and the bias row), summed into
+// weight gradient as row-slice partials (and the bias row), summed into
 // grad in slice order, then the data gradient into the layer below.
 void mlp_backward(const Dev &d, const PolicyShape &sh, const float *params, const float *X,
                   const float *h1, const float *h2, const float *dout, float *grad, float *d1, float *d2,
