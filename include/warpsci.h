@@ -389,8 +389,9 @@ ws_status ws_get_launch(const ws_ctx *ctx, ws_launch *out);
 ws_status ws_set_launch(ws_ctx *ctx, const ws_launch *l);
 
 /* Autotune: run each candidate launch configuration of the context's path for
- * trial_steps steps (after one untimed run of the same length), timed with
- * CUDA events on the context's stream, and keep the fastest.  The choice is
+ * trial_steps steps (after one untimed run of the same length), three times,
+ * timed with CUDA events on the context's stream, and keep the candidate with
+ * the fastest of its three runs.  The choice is
  * cached per process for the configuration's shape (env, path, sizes, agent
  * counts, device), so a later context of the same shape reuses it without
  * timing.  The trials advance the envs, so the call ends with ws_reset under
