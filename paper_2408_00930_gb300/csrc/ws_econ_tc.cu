@@ -16,7 +16,8 @@
 //             wealth totals (segmented warp sums, then shared-memory atomics)
 //   agents    16-128-128-20 MLP per tile on tcgen05 (FP32 accumulators in
 //             TMEM, bias + tanh epilogues writing the next layer's 128B-swizzled
-//             operand), then the categorical draw (Philox, inverse CDF in FP32)
+//             operand; layers 2 and 3 pipelined over 64-column halves), then
+//             the categorical draw (Philox, inverse CDF in FP32)
 //   planner   its own warpgroup: mean agent features per env (fixed-order warp
 //             sums), then the 16-128-128-10 MLP with the operands swapped
 //             (D[hidden][env] = W^T obs^T: the envs of the item become the N

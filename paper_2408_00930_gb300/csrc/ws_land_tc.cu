@@ -28,17 +28,19 @@
 //            epilogue is one ex2 per pair summed into a positive and a negative
 //            part (each sign group padded to 128 Gaussians).  The operand row
 //            sits in tensor memory as the A operand; blocks of 128 Gaussians
-//            stream through two shared-memory buffers (a loader warp) into
-//            three 128-column TMEM accumulators (an MMA warp, one M = 128,
-//            N = 128 MMA per K step); the two threads of a row take the
-//            blocks of even and odd index.
+//            stream through two shared-memory buffers (a loader warp that
+//            polls each block's MMA completion) into three 128-column TMEM
+//            accumulators (two MMA warps taking the even and the odd blocks,
+//            one M = 128, N = 128 MMA per K step); the two threads of a row
+//            take the blocks of even and odd index.
 //   step     observed energy with Philox noise, reward Eobs(x) - Eobs(x'), done
 //            at the episode limit or when E(y) falls below the energy target
 //            (the product basin of App. C), reset to U(-3, 3)^D and a second
 //            sweep for the fresh state's energy when a tile has a reset
 // Threads: warps 0-3 own the env rows (state, sampling, records); warps 4-7
 // take the other half of every tanh and exp epilogue; warp 8 loads the energy
-// blocks, warp 9 issues the energy MMAs.  Every wait is bounded; a wait that
+// blocks, warps 9 and 10 issue the energy MMAs.  The step's Philox normals are
+// drawn while the layer-2 MMA runs.  Every wait is bounded; a wait that
 // runs out sets the error flag and the CTA leaves its loops at the next step
 // boundary.
 #include "ws_kernels.cuh"
